@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark: 30-qubit gate-stream QFT and 30-qubit second-order TFIM Trotter
+evolution on one GB300, through the C ABI.
+
+One step = one 30q QFT circuit (30 H + 435 CP + 15 SWAP = 480 gates) applied
+to the resident state, then |0..0> preparation and one 30q TFIM circuit (100
+Strang steps, J = 1, h_i ~ U[0.5, 1.5] seed 3, dt = 0.05; 8800 gates).  The
+8 GiB state is far larger than L2 (129 MB), so no flush is needed between
+steps.  The metric is seconds per step (QFT + TFIM circuit pair), lower is
+better; the JSON line also carries each circuit's time, the plain per-gate GPU
+path's time for the same circuits, the HBM roofline of the dominant kernel,
+the oracle's CPU baseline and an end-to-end (host buffer) figure.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+N_QUBITS = 30
+TFIM_STEPS, TFIM_DT = 100, 0.05
+METRIC = "30q QFT & TFIM s/circuit vs per-gate path; layer HBM GB/s vs 8 TB/s; grads/s"
+WORKLOAD = ("30q gate-stream QFT (480 gates incl. 15 SWAPs) + 30q 2nd-order TFIM Trotter "
+            "(100 Strang steps, J=1, h_i~U[0.5,1.5] seed 3, dt=0.05, from |0..0>), complex64")
+
+
+def workload_gates():
+    qft = W.qft_gates(N_QUBITS, swaps=True)
+    tfim = W.tfim_gates(N_QUBITS, TFIM_STEPS, TFIM_DT, 1.0, W.tfim_fields(N_QUBITS, 3), order=2)
+    return qft, tfim
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic():
+    """DRAM bytes per launch of the tile kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    src = open(os.path.join(ROOT, "paper_2609_19147_gb300", "csrc", "k_tile.cu"), "rb").read()
+    if d.get("k_tile_sha1") != hashlib.sha1(src).hexdigest():
+        return None
+    return d.get("tile_pass_bytes_per_launch_30q")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) timing: bounded samples of the same workload
+# ---------------------------------------------------------------------------
+def oracle_sample(n_qft_gates=40, n_tfim_gates=40):
+    """Time the complex128 oracle on a bounded sample at full size and scale
+    per gate to the whole step: the oracle applies every gate as one full
+    pass, so its cost is linear in the gate count."""
+    import oracle
+    n = N_QUBITS
+    avail = 0
+    try:
+        for ln in open("/proc/meminfo"):
+            if ln.startswith("MemAvailable"):
+                avail = int(ln.split()[1]) * 1024
+    except Exception:
+        pass
+    if avail and avail < 3 * (16 << n):
+        n = 28   # not enough host RAM for a 30q complex128 state: sample at 28q and scale by 4
+    scale_n = 2.0 ** (N_QUBITS - n)
+    qft, tfim = workload_gates()
+    if n != N_QUBITS:
+        qft = W.qft_gates(n, swaps=True)
+        tfim = W.tfim_gates(n, TFIM_STEPS, TFIM_DT, 1.0, W.tfim_fields(N_QUBITS, 3)[:n], order=2)
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[0] = 1.0
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.apply_gates(psi, n, qft[:n_qft_gates])
+    t_qft = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.apply_gates(psi, n, tfim[:n_tfim_gates])
+    t_tfim = time.perf_counter() - t0
+    qft_full = t_qft * len(qft) / n_qft_gates * scale_n
+    tfim_full = t_tfim * len(tfim) / n_tfim_gates * scale_n
+    sample = (f"first {n_qft_gates} of {len(qft)} QFT gates and first {n_tfim_gates} of {len(tfim)} TFIM gates "
+              f"at n={n}, complex128, time scaled by gate count" +
+              (f" and x{scale_n:g} for n={N_QUBITS}" if scale_n != 1 else ""))
+    return {"s_per_step": qft_full + tfim_full, "qft_s": qft_full, "tfim_s": tfim_full, "cores": oracle.threads(),
+            "sample": sample, "measured_s": t_qft + t_tfim}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(1, 1)
+    last = None
+    for _ in range(args.steps):
+        last = oracle_sample(8, 8)
+        vals.append(last["s_per_step"])
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/step (QFT+TFIM 30q)",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": v, "unit": "s/step (QFT+TFIM 30q)", "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": v, "unit": "s/step (QFT+TFIM 30q)", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import paper_2609_19147_gb300 as qs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    qft, tfim = workload_gates()
+    cq, ct = qs.CGates(qft), qs.CGates(tfim)
+    n = N_QUBITS
+    st = qs.State(n)
+    st.provide_scratch()
+    # resident input: Haar product state prepared on the device (outside timing)
+    rng = np.random.default_rng(4)
+    st.apply([W.Gate("U", (q,), (), W.haar_u2(rng)) for q in range(n)])
+    torch.cuda.synchronize()
+    stream = st.stream
+
+    def step():
+        st.apply(cq)
+        st.zero()
+        st.apply(ct)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, library profiling on (events on the state's stream)
+    st.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    qe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for k in range(args.steps):
+            qe[k][0].record(stream)
+            st.apply(cq)
+            qe[k][1].record(stream)
+            st.zero()
+            st.apply(ct)
+            qe[k][2].record(stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = st.profile_read()
+    st.profile(False)
+    qft_ms = float(np.mean([a.elapsed_time(b) for a, b, _ in qe]))
+    tfim_ms = float(np.mean([b.elapsed_time(c) for _, b, c in qe]))
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = ms_per_step / 1e3
+
+    # per-gate GPU path (the baseline): full QFT; TFIM on 5 Strang steps, scaled x20
+    pg = {}
+    if rank == 0 and not args.no_pergate:
+        per_step = len(tfim) // TFIM_STEPS
+        cts = qs.CGates(tfim[:5 * per_step])
+        for name, cg, scale in (("qft", cq, 1.0), ("tfim", cts, TFIM_STEPS / 5)):
+            st.apply(cg, mode="pergate")
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st.apply(cg, mode="pergate")
+            b.record(stream)
+            torch.cuda.synchronize()
+            pg[name] = a.elapsed_time(b) * scale / 1e3
+        pg["tfim_note"] = "5 of 100 Strang steps timed, scaled x20"
+
+    # end to end through the public API with host buffers: h2d input, QFT,
+    # d2h result, |0> + TFIM, d2h result
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        host = torch.empty((1 << n,), dtype=torch.complex64, pin_memory=True)
+        import ctypes
+        lib = qs._lib
+        nbytes = (1 << n) * 8
+
+        def e2e_step():
+            qs._check(lib.qs_set_amplitudes(st.h, ctypes.c_void_p(host.data_ptr()), 0))
+            st.apply(cq)
+            qs._check(lib.qs_get_amplitudes(st.h, ctypes.c_void_p(host.data_ptr()), 0))
+            st.zero()
+            st.apply(ct)
+            qs._check(lib.qs_get_amplitudes(st.h, ctypes.c_void_p(host.data_ptr()), 0))
+
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ke = max(1, min(args.steps, 3))
+        for _ in range(ke):
+            e2e_step()
+        torch.cuda.synchronize()
+        es = (time.perf_counter() - t0) / ke
+        e2e = {"value": es, "unit": "s/step (QFT+TFIM 30q)", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": 2 * nbytes}
+
+    if rank != 0:
+        st.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = peaks()
+    tp = prof.get("tile_pass", (0, 0.0, 0.0))
+    roof = None
+    if tp[0] > 0:
+        avg_ms = tp[1] / tp[0]
+        bytes_per_launch = tp[2] / tp[0]
+        achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": kernel_traffic(),
+                "kernel": "tile_pass_kernel", "launches": int(tp[0]), "avg_ms": round(avg_ms, 4),
+                "bytes_per_launch": bytes_per_launch, "peak_kind": f"{peak_kind} hbm_gbs (copy)"}
+    launches = int(sum(v[0] for v in prof.values()))
+    cpu = None
+    if not args.no_cpu:
+        o = oracle_sample()
+        cpu = {"value": o["s_per_step"], "unit": "s/step (QFT+TFIM 30q)", "cores": o["cores"], "kind": "oracle",
+               "sample": o["sample"]}
+    line = {
+        "metric": METRIC, "value": value, "unit": "s/step (QFT+TFIM 30q)", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_qubits": n, "state_bytes": (1 << n) * 8,
+                   "l2_flush": "none: 8 GiB state > 129 MB L2", "parallelism": f"replicas x{world}"},
+        "qft_s": qft_ms / 1e3, "tfim_s": tfim_ms / 1e3,
+        "pergate_s": pg or None,
+        "speedup_vs_pergate": ({"qft": pg["qft"] / (qft_ms / 1e3), "tfim": pg["tfim"] / (tfim_ms / 1e3)}
+                               if pg else None),
+        "kernels": {k: {"launches": int(v[0]), "ms": round(v[1], 3), "GB/s": round(v[2] / (v[1] * 1e-3) / 1e9, 1)
+                        if v[1] > 0 else None} for k, v in prof.items()},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    st.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-pergate", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * qs.h -- C ABI of the structured-layer state-vector engine (libqs.so).
+ *
+ * The engine applies gate lists to 2^n-amplitude complex64 state vectors on
+ * one CUDA GPU (sm_103a).  A fusion detector routes the gate stream into the
+ * layer families of the paper's Sec. 5.1 (phase-LUT diagonals, GF(2) affine
+ * permutation gathers, fused tensor-product single-qubit layers, radix-2^r
+ * QFT / Walsh butterflies, basis-conjugated XX/YY layers) plus dense blocks,
+ * each run by a hand-written CUDA kernel.  The calls follow the paper's
+ * statement of the problem: state initialisation, gate application and Pauli
+ * expectation (Sec. 3.2.1-3.2.2), gradients of parameterised circuits (Sec.
+ * 3.2.3; here by the adjoint method rather than parameter shift).
+ *
+ * Conventions (all calls):
+ *  - State: complex64 interleaved (re, im) float pairs, 2^n amplitudes per
+ *    state, `batch` states stored back to back (state b starts at element
+ *    b * 2^n).  Qubit q is bit n-1-q of the basis index (most significant
+ *    first; Sec. 3.2.2 reshape (2^q, 2, 2^(n-q-1)) and App. A).
+ *  - Gate matrices follow the gate library of Sec. 3.2.2 and the OpenQASM
+ *    table of Sec. 3.3: R_P(t) = exp(-i t P / 2); RZZ(t) = exp(-i t/2 Z(x)Z)
+ *    (the theta = -2 J dt mapping of Sec. 4.1); CP(t) = diag(1,1,1,e^{it});
+ *    P(l) = U1(l) = diag(1, e^{il}); U2/U3 as in OpenQASM 2.0.  For multi-qubit
+ *    gates w[0] is the most significant bit of the gate matrix index (the
+ *    control for controlled gates).
+ *  - Pauli masks: bit q of x_mask / z_mask refers to qubit q; a qubit with both
+ *    bits set carries Y.
+ *  - Errors: every call returns a qs_status.  On failure nothing of the
+ *    requested operation has been applied (validation precedes any launch),
+ *    and qs_last_error() gives a message for the calling thread.  Asynchronous
+ *    CUDA faults surface as QS_ERR_CUDA on the next synchronous call.
+ *  - Streams: all device work of a state runs on the state's stream (set at
+ *    qs_wrap / qs_set_stream; the legacy default stream otherwise).
+ *    qs_apply_circuit is asynchronous with respect to the host; qs_expect,
+ *    qs_grad and the amplitude copies synchronise the state's stream.
+ *  - Threads: a qs_state must not be used from two host threads at once.
+ */
+#ifndef QS_ABI_H_INCLUDED
+#define QS_ABI_H_INCLUDED
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t qs_status;
+enum {
+    QS_OK = 0,
+    QS_ERR_INVALID_ARG = 1,  /* bad pointer, size, wire, kind or arity      */
+    QS_ERR_UNSUPPORTED = 2,  /* valid request outside what this build does  */
+    QS_ERR_OOM = 3,          /* device allocation failed / cap exceeded     */
+    QS_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed        */
+    QS_ERR_TIMEOUT = 5,      /* a bounded device wait ran out               */
+    QS_ERR_INTERNAL = 6      /* a device-side consistency check failed      */
+};
+
+/* Gate kinds: the gate library of Sec. 3.2.2, the OpenQASM 2.0 coverage table
+ * of Sec. 3.3 and the Trotter-term gates of Sec. 5.1. */
+enum qs_gate_kind {
+    QS_I = 0, QS_X = 1, QS_Y = 2, QS_Z = 3, QS_H = 4, QS_S = 5, QS_SDG = 6,
+    QS_T = 7, QS_TDG = 8, QS_SX = 9,
+    QS_RX = 10, QS_RY = 11, QS_RZ = 12,   /* p[0] = theta                   */
+    QS_P = 13,                            /* U1 / phase gate, p[0] = lambda */
+    QS_U2 = 14,                           /* p[0] = phi, p[1] = lambda      */
+    QS_U3 = 15,                           /* p[0..2] = theta, phi, lambda   */
+    QS_U = 16,                            /* dense 2x2: `dense` -> 8 doubles */
+    QS_CX = 32, QS_CY = 33, QS_CZ = 34, QS_CH = 35, QS_SWAP = 36,
+    QS_ISWAP = 37, QS_CRX = 38, QS_CRY = 39, QS_CRZ = 40,
+    QS_CP = 41,                           /* CPHASE, p[0] = theta           */
+    QS_RZZ = 42, QS_RXX = 43, QS_RYY = 44,/* exp(-i p[0]/2 P(x)P)           */
+    QS_CCX = 64, QS_CSWAP = 65            /* Toffoli, Fredkin               */
+};
+
+/* One gate record.  Arrays of records are owned by the caller, read during
+ * the call and not retained. */
+typedef struct qs_gate {
+    uint16_t kind;       /* enum qs_gate_kind                                */
+    uint8_t nw;          /* number of wires; must equal the kind's arity     */
+    uint8_t flags;       /* reserved, 0                                      */
+    int32_t w[3];        /* wires (qubit indices), distinct, in [0, n)       */
+    double p[3];         /* angles in radians                                */
+    int32_t param_idx;   /* -1: fixed; else p[0] := params[b*n_params + idx] */
+    int32_t reserved;    /* 0                                                */
+    const double *dense; /* QS_U only: row-major 2x2 complex128 as (re, im)  */
+} qs_gate;
+
+/* One Pauli term coeff * P, P = prod_q sigma_q from (x_mask, z_mask). */
+typedef struct qs_pauli {
+    double coeff;
+    uint64_t x_mask;
+    uint64_t z_mask;
+} qs_pauli;
+
+enum qs_mode {
+    QS_MODE_FUSED = 0,   /* detector + fused layer kernels (default)         */
+    QS_MODE_PERGATE = 1  /* one kernel launch per gate: the baseline path    */
+};
+
+/* Options for qs_apply_circuit / qs_plan_describe; NULL means defaults. */
+typedef struct qs_opts {
+    int32_t mode;         /* enum qs_mode                                    */
+    int32_t tile_qubits;  /* qubits per tile pass, 0 = default (13)          */
+    int32_t low_qubits;   /* contiguous low bits per tile row, 0 = default   */
+    int32_t flags;        /* reserved, 0                                     */
+} qs_opts;
+
+typedef struct qs_state qs_state;
+
+/* Allocate `batch` states of n qubits in device memory owned by the library,
+ * each initialised to |0...0>.  n in [1, 33]; batch >= 1.  Errors:
+ * QS_ERR_INVALID_ARG (out == NULL, batch < 1), QS_ERR_UNSUPPORTED (n out of
+ * range), QS_ERR_OOM (allocation failed).  Free with qs_free. */
+qs_status qs_alloc(int n, int batch, qs_state **out);
+
+/* Wrap caller-owned device memory (e.g. a torch tensor) of batch * 2^n
+ * complex64 amplitudes, 16-byte aligned.  The library never frees
+ * `dev_ptr`; `cuda_stream` (a cudaStream_t, may be NULL) becomes the state's
+ * stream.  The contents are left as they are. */
+qs_status qs_wrap(void *dev_ptr, int n, int batch, void *cuda_stream, qs_state **out);
+
+/* Release the handle, library-owned memory and scratch buffers.  NULL is a
+ * no-op.  Waits for the state's stream first. */
+qs_status qs_free(qs_state *st);
+
+/* Replace the state's stream (cudaStream_t, NULL = legacy default). */
+qs_status qs_set_stream(qs_state *st, void *cuda_stream);
+
+/* Hand the library a caller-owned device scratch buffer of `bytes` bytes
+ * (>= batch * 2^n * 8 for out-of-place gathers).  Without one the library
+ * allocates its own on first need.  The buffer must stay valid until
+ * qs_free or the next qs_set_scratch. */
+qs_status qs_set_scratch(qs_state *st, void *dev_ptr, size_t bytes);
+
+/* Device pointer of the amplitudes (batch * 2^n complex64). */
+qs_status qs_device_ptr(const qs_state *st, void **out);
+
+/* Reset every state of the batch to |0...0>; asynchronous. */
+qs_status qs_init_zero(qs_state *st);
+
+/* Copy batch * 2^n complex64 amplitudes in (src) or out (dst); `is_device`
+ * says whether the pointer is device memory.  Synchronous: returns after
+ * the copy is complete. */
+qs_status qs_set_amplitudes(qs_state *st, const void *src, int is_device);
+qs_status qs_get_amplitudes(const qs_state *st, void *dst, int is_device);
+
+/* Apply the gate list to every state of the batch, in order.
+ * params: NULL, or batch x n_params doubles (row b resolves param_idx for
+ * state b).  Every gate is validated before anything runs: kind and nw
+ * consistent, wires distinct and in [0, n), param_idx < n_params, dense != NULL
+ * for QS_U; a failure returns QS_ERR_INVALID_ARG with the state untouched.
+ * In QS_MODE_FUSED the detector builds layer passes whose result equals the
+ * gate-by-gate product up to float rounding (permutations exactly).
+ * Asynchronous on the state's stream. */
+qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates,
+                           const double *params, int n_params, const qs_opts *opts);
+
+/* out[b] = <psi_b| sum_k coeff_k P_k |psi_b> (real part) for each state b,
+ * accumulated in FP64 on the device (Sec. 3.2.1 Pauli expectation).
+ * Masks must lie within the n qubits.  Synchronous. */
+qs_status qs_expect(qs_state *st, const qs_pauli *terms, size_t n_terms, double *out);
+
+/* Adjoint-method gradient of E_b(theta) = <psi_b(theta)|H|psi_b(theta)> with
+ * psi_b(theta) = U(theta_b)|0...0>, H = sum_k coeff_k P_k.  The state is
+ * overwritten: on return it holds psi_b(theta).  energy: batch doubles;
+ * grad: batch x n_params doubles (zero for unused indices).  Parameterised
+ * gates must be QS_RX, QS_RY, QS_RZ, QS_RZZ or QS_CP (else
+ * QS_ERR_UNSUPPORTED); each index may feed several gates (contributions add).
+ * Needs device memory for one extra state per batch item.  Synchronous. */
+qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates,
+                  const double *params, int n_params,
+                  const qs_pauli *terms, size_t n_terms,
+                  double *energy, double *grad);
+
+/* Test hook: write the detector's plan for an n-qubit circuit as text
+ * (one line per pass: family, qubits, op count) into buf (NUL-terminated,
+ * truncated to len).  Needs no GPU.  *passes (if non-NULL) receives the
+ * number of full-state HBM passes the plan makes. */
+qs_status qs_plan_describe(int n, const qs_gate *gates, size_t n_gates,
+                           const qs_opts *opts, char *buf, size_t len, int *passes);
+
+/* Per-kernel-family timing with CUDA events recorded on the state's stream
+ * around each launch.  enable != 0 turns it on and clears the counters. */
+qs_status qs_profile_enable(qs_state *st, int enable);
+/* Copy up to `cap` records: name (NUL-terminated, 32 bytes), launches,
+ * total milliseconds, algorithmic bytes moved.  *count = records written.
+ * Synchronises the state's stream. */
+typedef struct qs_profile_record {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+    double bytes;
+} qs_profile_record;
+qs_status qs_profile_read(qs_state *st, qs_profile_record *out, int cap, int *count);
+
+/* Message for the last failed call on this host thread ("" if none). */
+const char *qs_last_error(void);
+
+/* Library version string. */
+const char *qs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QS_ABI_H_INCLUDED */

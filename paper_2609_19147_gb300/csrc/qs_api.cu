@@ -1,0 +1,1036 @@
+// C ABI (include/qs.h): state handles, plan cache, executor, expectation and
+// adjoint gradients.  All arithmetic on amplitudes runs in the CUDA kernels;
+// this file validates, plans, routes buffers and launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <list>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "qs.h"
+#include "qs_internal.h"
+#include "qs_kernels.h"
+#include "qs_plan.h"
+
+using namespace qs;
+
+namespace {
+thread_local std::string g_last_error;
+
+qs_status fail(qs_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+#define QS_CUDA(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(e_ == cudaErrorMemoryAllocation ? QS_ERR_OOM : QS_ERR_CUDA,          \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                \
+    } while (0)
+
+struct DevicePlan {          // a plan uploaded to the device
+    Plan host;
+    std::vector<TilePass *> d_tile;
+    std::vector<float2 *> d_consts;
+    std::vector<GatherPass *> d_gather;
+    PgOp *d_pg = nullptr;
+    size_t bytes = 0;
+    std::list<uint64_t>::iterator lru;
+};
+
+struct ProfRec {
+    int64_t launches = 0;
+    double ms = 0.0, bytes = 0.0;
+};
+struct PendingEv {
+    std::string name;
+    cudaEvent_t a, b;
+    double bytes;
+};
+
+float2 *g_roots[16] = {nullptr};   // per device
+int g_num_sms[16] = {0};
+std::mutex g_mu;
+
+int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+
+qs_status ensure_device_tables(int dev) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_roots[dev]) return QS_OK;
+    std::vector<float2> r(kRootsEntries);
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < 4; ++k)
+        for (int c = 0; c < 256; ++c) {
+            // exp(i pi c 2^(8k) / 2^32)
+            double ang = pi * std::ldexp((double)c, 8 * k - 32);
+            r[k * 256 + c] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        }
+    float2 *d = nullptr;
+    QS_CUDA(cudaMalloc(&d, kRootsEntries * sizeof(float2)));
+    QS_CUDA(cudaMemcpy(d, r.data(), kRootsEntries * sizeof(float2), cudaMemcpyHostToDevice));
+    cudaDeviceProp prop;
+    QS_CUDA(cudaGetDeviceProperties(&prop, dev));
+    g_num_sms[dev] = prop.multiProcessorCount;
+    g_roots[dev] = d;
+    return QS_OK;
+}
+
+uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
+    const unsigned char *c = (const unsigned char *)p;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= c[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+uint64_t plan_key(int n, const std::vector<RGate> &g, const qs_opts &o) {
+    uint64_t h = fnv1a(&n, sizeof n);
+    h = fnv1a(&o, sizeof o, h);
+    for (const RGate &r : g) {
+        h = fnv1a(&r.kind, sizeof r.kind, h);
+        h = fnv1a(r.q, sizeof r.q, h);
+        h = fnv1a(r.p, sizeof r.p, h);
+        if (r.kind == QS_U) h = fnv1a(r.dense, sizeof r.dense, h);
+    }
+    return h;
+}
+
+qs_opts default_opts(const qs_opts *o) {
+    qs_opts d;
+    std::memset(&d, 0, sizeof d);
+    if (o) d = *o;
+    return d;
+}
+}  // namespace
+
+struct qs_state {
+    int n = 0, batch = 1, dev = 0;
+    long long elems = 0;
+    float2 *home = nullptr;      // where results live between calls
+    bool owned = false;
+    float2 *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    bool scratch_owned = false;
+    cudaStream_t stream = nullptr;
+    int *d_err = nullptr;
+    double *d_partial = nullptr;
+    size_t partial_cap = 0;      // doubles
+    double *d_out = nullptr;
+    size_t out_cap = 0;
+    PauliDev *d_terms = nullptr;
+    size_t terms_cap = 0;
+    std::unordered_map<uint64_t, std::unique_ptr<DevicePlan>> cache;
+    std::list<uint64_t> lru;
+    size_t cache_bytes = 0;
+    bool prof = false;
+    std::map<std::string, ProfRec> prof_recs;
+    std::vector<PendingEv> prof_pending;
+};
+
+namespace {
+
+void free_plan(qs_state *st, DevicePlan *dp) {
+    for (auto p : dp->d_tile) cudaFreeAsync(p, st->stream);
+    for (auto p : dp->d_consts)
+        if (p) cudaFreeAsync(p, st->stream);
+    for (auto p : dp->d_gather)
+        if (p) cudaFreeAsync(p, st->stream);
+    if (dp->d_pg) cudaFreeAsync(dp->d_pg, st->stream);
+}
+
+qs_status upload_plan(qs_state *st, DevicePlan &dp) {
+    const Plan &p = dp.host;
+    if (p.mode == QS_MODE_PERGATE) {
+        if (!p.pg.empty()) {
+            size_t b = p.pg.size() * sizeof(PgOp);
+            QS_CUDA(cudaMallocAsync((void **)&dp.d_pg, b, st->stream));
+            QS_CUDA(cudaMemcpyAsync(dp.d_pg, p.pg.data(), b, cudaMemcpyHostToDevice, st->stream));
+            dp.bytes += b;
+        }
+        return QS_OK;
+    }
+    dp.d_tile.assign(p.passes.size(), nullptr);
+    dp.d_consts.assign(p.passes.size(), nullptr);
+    dp.d_gather.assign(p.passes.size(), nullptr);
+    for (size_t i = 0; i < p.passes.size(); ++i) {
+        const HostPass &hp = p.passes[i];
+        if (hp.type == HostPass::TILE) {
+            QS_CUDA(cudaMallocAsync((void **)&dp.d_tile[i], sizeof(TilePass), st->stream));
+            QS_CUDA(cudaMemcpyAsync(dp.d_tile[i], &hp.tile, sizeof(TilePass), cudaMemcpyHostToDevice, st->stream));
+            dp.bytes += sizeof(TilePass);
+            if (!hp.consts.empty()) {
+                size_t b = hp.consts.size() * sizeof(float2);
+                QS_CUDA(cudaMallocAsync((void **)&dp.d_consts[i], b, st->stream));
+                QS_CUDA(cudaMemcpyAsync(dp.d_consts[i], hp.consts.data(), b, cudaMemcpyHostToDevice, st->stream));
+                dp.bytes += b;
+            }
+        } else if (hp.type == HostPass::GATHER) {
+            QS_CUDA(cudaMallocAsync((void **)&dp.d_gather[i], sizeof(GatherPass), st->stream));
+            QS_CUDA(cudaMemcpyAsync(dp.d_gather[i], &hp.gather, sizeof(GatherPass), cudaMemcpyHostToDevice,
+                                    st->stream));
+            dp.bytes += sizeof(GatherPass);
+        }
+    }
+    // host staging buffers of cudaMemcpyAsync are pageable: make sure the
+    // copies have read them before the host Plan can change
+    QS_CUDA(cudaStreamSynchronize(st->stream));
+    return QS_OK;
+}
+
+qs_status get_plan(qs_state *st, const std::vector<RGate> &gates, const qs_opts &o, DevicePlan **out) {
+    uint64_t key = plan_key(st->n, gates, o);
+    auto it = st->cache.find(key);
+    if (it != st->cache.end()) {
+        st->lru.erase(it->second->lru);
+        st->lru.push_front(key);
+        it->second->lru = st->lru.begin();
+        *out = it->second.get();
+        return QS_OK;
+    }
+    std::unique_ptr<DevicePlan> dp(new DevicePlan());
+    std::string err;
+    qs_status s = (o.mode == QS_MODE_PERGATE) ? build_pergate_plan(st->n, gates, dp->host, err)
+                                              : build_fused_plan(st->n, gates, o, dp->host, err);
+    if (s != QS_OK) return fail(s, err);
+    s = upload_plan(st, *dp);
+    if (s != QS_OK) {
+        free_plan(st, dp.get());
+        return s;
+    }
+    st->lru.push_front(key);
+    dp->lru = st->lru.begin();
+    st->cache_bytes += dp->bytes;
+    *out = dp.get();
+    st->cache[key] = std::move(dp);
+    // bound the cache (entries and bytes)
+    while (st->cache.size() > 64 || st->cache_bytes > (256ull << 20)) {
+        uint64_t victim = st->lru.back();
+        if (victim == key) break;
+        st->lru.pop_back();
+        auto v = st->cache.find(victim);
+        st->cache_bytes -= v->second->bytes;
+        free_plan(st, v->second.get());
+        st->cache.erase(v);
+    }
+    return QS_OK;
+}
+
+qs_status ensure_scratch(qs_state *st) {
+    size_t need = (size_t)st->elems * st->batch * sizeof(float2);
+    if (st->scratch && st->scratch_bytes >= need) return QS_OK;
+    if (st->scratch && st->scratch_owned) cudaFree(st->scratch);
+    st->scratch = nullptr;
+    QS_CUDA(cudaMalloc(&st->scratch, need));
+    st->scratch_bytes = need;
+    st->scratch_owned = true;
+    return QS_OK;
+}
+
+void prof_begin(qs_state *st, cudaEvent_t *a) {
+    if (!st->prof) return;
+    cudaEventCreate(a);
+    cudaEventRecord(*a, st->stream);
+}
+void prof_end(qs_state *st, cudaEvent_t a, const char *name, double bytes) {
+    if (!st->prof) return;
+    cudaEvent_t b;
+    cudaEventCreate(&b);
+    cudaEventRecord(b, st->stream);
+    st->prof_pending.push_back({name, a, b, bytes});
+}
+
+qs_status check_err_word(qs_state *st) {
+    int h = 0;
+    QS_CUDA(cudaMemcpyAsync(&h, st->d_err, sizeof(int), cudaMemcpyDeviceToHost, st->stream));
+    QS_CUDA(cudaStreamSynchronize(st->stream));
+    if (h != 0) {
+        cudaMemsetAsync(st->d_err, 0, sizeof(int), st->stream);
+        return fail(h, h == QS_ERR_TIMEOUT ? "a bounded device wait expired" : "device-side check failed");
+    }
+    return QS_OK;
+}
+
+// -------- executor --------
+qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *src, float2 *dst, float2 *base_off,
+                   int batch) {
+    (void)base_off;
+    const HostPass &hp = dp.host.passes[i];
+    const TilePass &tp = hp.tile;
+    TileArgs A;
+    std::memset(&A, 0, sizeof A);
+    A.pass = dp.d_tile[i];
+    A.consts = dp.d_consts[i];
+    A.roots = g_roots[st->dev];
+    A.src = src;
+    A.dst = dst;
+    A.state_elems = st->elems;
+    A.n_tiles = 1ll << (st->n - tp.T);
+    A.batch = batch;
+    uint64_t tilebits = (1ull << tp.L) - 1;
+    for (int k = 0; k < tp.H; ++k) tilebits |= 1ull << tp.hb[k];
+    A.n_outer = 0;
+    for (int b = 0; b < st->n; ++b)
+        if (!((tilebits >> b) & 1)) A.outer_pos[A.n_outer++] = b;
+    A.err = st->d_err;
+    int off = 128;
+    A.off_consts = off;
+    off += ((int)hp.consts.size() * 8 + 127) / 128 * 128;
+    if (hp.uses_roots) {
+        A.off_roots = off;
+        off += kRootsEntries * 8;
+    }
+    const int buf_bytes = ((1 << tp.H) * tp.row_stride * 8 + 127) / 128 * 128;
+    A.off_buf0 = off;
+    off += buf_bytes;
+    A.off_buf1 = off;
+    off += buf_bytes;
+    if (off > 227 * 1024) return fail(QS_ERR_INTERNAL, "tile pass needs too much shared memory");
+    static int configured[16] = {0};
+    if (configured[st->dev] < off) {
+        tile_kernel_smem_config(227 * 1024);
+        configured[st->dev] = 227 * 1024;
+    }
+    long long total = A.n_tiles * batch;
+    int grid = (int)std::min<long long>(total, g_num_sms[st->dev] > 0 ? g_num_sms[st->dev] : 148);
+    cudaEvent_t ev;
+    prof_begin(st, &ev);
+    QS_CUDA(launch_tile_pass(A, grid, off, st->stream));
+    prof_end(st, ev, "tile_pass", 16.0 * (double)st->elems * batch);
+    return QS_OK;
+}
+
+qs_status run_perm(qs_state *st, const PermPass &pp, const float2 *src, float2 *dst, int batch) {
+    const int n = st->n;
+    PermArgs A;
+    std::memset(&A, 0, sizeof A);
+    A.src = src;
+    A.dst = dst;
+    A.state_elems = st->elems;
+    A.batch = batch;
+    const int L = std::min(pp.L, n);
+    // input tile bits: low L, then input bits landing on output low bits, then
+    // more low-positioned bits up to 10 tile bits
+    std::vector<int> in_bits;
+    uint64_t in_mask = 0;
+    for (int b = 0; b < L; ++b) {
+        in_bits.push_back(b);
+        in_mask |= 1ull << b;
+    }
+    for (int b = L; b < n; ++b)
+        if (pp.out_pos[b] < L) {
+            in_bits.push_back(b);
+            in_mask |= 1ull << b;
+        }
+    for (int b = L; b < n && (int)in_bits.size() < 10; ++b)
+        if (!((in_mask >> b) & 1)) {
+            in_bits.push_back(b);
+            in_mask |= 1ull << b;
+        }
+    A.TB = (int)in_bits.size();
+    for (int k = 0; k < A.TB; ++k) A.in_pos[k] = in_bits[k];
+    std::vector<int> outs;
+    uint64_t qmask = 0;
+    for (int k = 0; k < A.TB; ++k) {
+        outs.push_back(pp.out_pos[in_bits[k]]);
+        qmask |= 1ull << pp.out_pos[in_bits[k]];
+    }
+    std::sort(outs.begin(), outs.end());
+    for (int k = 0; k < A.TB; ++k) {
+        A.out_pos_loc[k] = outs[k];
+        for (int m = 0; m < A.TB; ++m)
+            if (pp.out_pos[in_bits[m]] == outs[k]) A.out_to_in[k] = m;
+        if ((pp.xor_mask >> outs[k]) & 1) A.xor_loc |= 1u << k;
+    }
+    A.n_outer = 0;
+    for (int b = 0; b < n; ++b)
+        if (!((in_mask >> b) & 1)) {
+            A.outer_in[A.n_outer] = b;
+            A.outer_out[A.n_outer] = pp.out_pos[b];
+            A.n_outer++;
+        }
+    A.xor_outer = pp.xor_mask & ~qmask;
+    cudaEvent_t ev;
+    prof_begin(st, &ev);
+    QS_CUDA(launch_perm(A, st->stream));
+    prof_end(st, ev, "perm", 16.0 * (double)st->elems * batch);
+    return QS_OK;
+}
+
+qs_status run_gather(qs_state *st, const GatherPass *dg, const float2 *src, float2 *dst, int batch) {
+    GatherArgs A;
+    A.g = dg;
+    A.src = src;
+    A.dst = dst;
+    A.state_elems = st->elems;
+    A.batch = batch;
+    cudaEvent_t ev;
+    prof_begin(st, &ev);
+    QS_CUDA(launch_gather(A, st->stream));
+    prof_end(st, ev, "gather", 16.0 * (double)st->elems * batch);
+    return QS_OK;
+}
+
+void pg_fixed(const PgOp &op, int n, PgArgs &A) {
+    uint64_t fixed = op.cmask;
+    if (op.kind == PG_U1) fixed |= 1ull << op.t0;
+    if (op.kind == PG_U2 || op.kind == PG_SWAP) fixed |= (1ull << op.t0) | (1ull << op.t1);
+    A.n_fixed = 0;
+    for (int b = 0; b < n; ++b)
+        if ((fixed >> b) & 1) A.fixed_pos[A.n_fixed++] = b;
+    A.n_work = 1ll << (n - A.n_fixed);
+    A.vec2 = !(fixed & 1ull) && A.n_work >= 2;
+}
+
+double pg_bytes(const PgOp &op, int n) {
+    // bytes the op reads + writes
+    int fixed = __builtin_popcountll(op.cmask);
+    double touched;
+    switch (op.kind) {
+        case PG_U1: touched = std::ldexp(1.0, n - fixed); break;
+        case PG_SWAP: touched = std::ldexp(1.0, n - fixed - 1); break;
+        case PG_U2: touched = std::ldexp(1.0, n); break;
+        default: touched = std::ldexp(1.0, n - fixed); break;
+    }
+    return 16.0 * touched;
+}
+
+qs_status run_pergate(qs_state *st, const DevicePlan &dp, float2 *psi, int batch) {
+    const Plan &p = dp.host;
+    for (size_t i = 0; i < p.pg.size(); ++i) {
+        PgArgs A;
+        std::memset(&A, 0, sizeof A);
+        A.ops = dp.d_pg + i;
+        A.op_stride = 0;
+        A.psi[0] = psi;
+        A.n_arrays = 1;
+        A.state_elems = st->elems;
+        A.batch = batch;
+        A.n = st->n;
+        pg_fixed(p.pg[i], st->n, A);
+        cudaEvent_t ev;
+        prof_begin(st, &ev);
+        QS_CUDA(launch_pergate(A, st->stream));
+        prof_end(st, ev, "pergate", pg_bytes(p.pg[i], st->n) * batch);
+    }
+    return QS_OK;
+}
+
+// Execute a fused plan on `batch` states starting at `home` (results land
+// back in `home`); out-of-place passes ping-pong with `other`.
+qs_status run_fused(qs_state *st, const DevicePlan &dp, float2 *home, float2 *other, int batch) {
+    const Plan &p = dp.host;
+    int n_oop = 0, first_tile = -1;
+    for (size_t i = 0; i < p.passes.size(); ++i) {
+        if (p.passes[i].type != HostPass::TILE) n_oop++;
+        else if (first_tile < 0) first_tile = (int)i;
+    }
+    // parity: results must end in `home`
+    bool flip_tile = (n_oop % 2 == 1) && first_tile >= 0;
+    bool final_copy = (n_oop % 2 == 1) && first_tile < 0;
+    float2 *cur = home, *oth = other;
+    for (size_t i = 0; i < p.passes.size(); ++i) {
+        const HostPass &hp = p.passes[i];
+        qs_status s = QS_OK;
+        if (hp.type == HostPass::TILE) {
+            if (flip_tile && (int)i == first_tile) {
+                s = run_tile(st, dp, i, cur, oth, nullptr, batch);
+                std::swap(cur, oth);
+            } else {
+                s = run_tile(st, dp, i, cur, cur, nullptr, batch);
+            }
+        } else if (hp.type == HostPass::PERM) {
+            s = run_perm(st, hp.perm, cur, oth, batch);
+            std::swap(cur, oth);
+        } else {
+            s = run_gather(st, dp.d_gather[i], cur, oth, batch);
+            std::swap(cur, oth);
+        }
+        if (s != QS_OK) return s;
+    }
+    if (final_copy) {
+        QS_CUDA(cudaMemcpyAsync(home, cur, (size_t)st->elems * batch * sizeof(float2), cudaMemcpyDeviceToDevice,
+                                st->stream));
+    }
+    return QS_OK;
+}
+
+bool plan_needs_scratch(const Plan &p) {
+    if (p.mode == QS_MODE_PERGATE) return false;
+    for (auto &hp : p.passes)
+        if (hp.type != HostPass::TILE) return true;
+    return false;
+}
+
+qs_status apply_resolved(qs_state *st, const std::vector<RGate> &gates, const qs_opts &o, float2 *home, int batch) {
+    DevicePlan *dp = nullptr;
+    qs_status s = get_plan(st, gates, o, &dp);
+    if (s != QS_OK) return s;
+    if (dp->host.mode == QS_MODE_PERGATE) return run_pergate(st, *dp, home, batch);
+    if (plan_needs_scratch(dp->host)) {
+        s = ensure_scratch(st);
+        if (s != QS_OK) return s;
+    }
+    float2 *other = st->scratch ? st->scratch + (home - st->home) : nullptr;
+    return run_fused(st, *dp, home, other, batch);
+}
+
+bool has_param_gates(const qs_gate *g, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (g[i].param_idx >= 0) return true;
+    return false;
+}
+
+qs_status ensure_partial(qs_state *st, size_t doubles) {
+    if (st->partial_cap >= doubles) return QS_OK;
+    if (st->d_partial) cudaFree(st->d_partial);
+    st->d_partial = nullptr;
+    QS_CUDA(cudaMalloc(&st->d_partial, doubles * sizeof(double)));
+    st->partial_cap = doubles;
+    return QS_OK;
+}
+qs_status ensure_out(qs_state *st, size_t doubles) {
+    if (st->out_cap >= doubles) return QS_OK;
+    if (st->d_out) cudaFree(st->d_out);
+    st->d_out = nullptr;
+    QS_CUDA(cudaMalloc(&st->d_out, doubles * sizeof(double)));
+    st->out_cap = doubles;
+    return QS_OK;
+}
+qs_status ensure_terms(qs_state *st, size_t n) {
+    if (st->terms_cap >= n) return QS_OK;
+    if (st->d_terms) cudaFree(st->d_terms);
+    st->d_terms = nullptr;
+    QS_CUDA(cudaMalloc(&st->d_terms, n * sizeof(PauliDev)));
+    st->terms_cap = n;
+    return QS_OK;
+}
+
+// Pauli terms in index-bit space
+struct TermIdx {
+    double coeff;
+    uint64_t x, z;
+    int ny;
+};
+
+qs_status convert_terms(int n, const qs_pauli *terms, size_t n_terms, std::vector<TermIdx> &out) {
+    out.clear();
+    const uint64_t lim = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+    for (size_t k = 0; k < n_terms; ++k) {
+        if ((terms[k].x_mask & ~lim) || (terms[k].z_mask & ~lim))
+            return fail(QS_ERR_INVALID_ARG, "Pauli mask outside the register");
+        if (!std::isfinite(terms[k].coeff)) return fail(QS_ERR_INVALID_ARG, "non-finite Pauli coefficient");
+        TermIdx t;
+        t.coeff = terms[k].coeff;
+        t.x = t.z = 0;
+        for (int q = 0; q < n; ++q) {
+            if ((terms[k].x_mask >> q) & 1) t.x |= 1ull << (n - 1 - q);
+            if ((terms[k].z_mask >> q) & 1) t.z |= 1ull << (n - 1 - q);
+        }
+        t.ny = __builtin_popcountll(t.x & t.z) & 3;
+        out.push_back(t);
+    }
+    return QS_OK;
+}
+
+// S[b][k] (complex) = sum_x conj(phi[x ^ x_k]) (-1)^popcount(x & z_k) psi[x]
+// for every term; results to host `S` (batch x n_terms x 2).
+qs_status overlaps(qs_state *st, const float2 *psi, const float2 *phi, int batch, const std::vector<TermIdx> &t,
+                   std::vector<double> &S) {
+    const int nt = (int)t.size();
+    S.assign((size_t)batch * nt * 2, 0.0);
+    if (nt == 0) return QS_OK;
+    // group by x mask, chunks of <= 16 terms
+    std::map<uint64_t, std::vector<int>> groups;
+    for (int k = 0; k < nt; ++k) groups[t[k].x].push_back(k);
+    const int grid = std::max(1, std::min<int>((int)((st->elems + 255) / 256), g_num_sms[st->dev] * 4));
+    qs_status s = ensure_partial(st, (size_t)batch * grid * 16 * 2);
+    if (s != QS_OK) return s;
+    s = ensure_out(st, (size_t)batch * nt * 2);
+    if (s != QS_OK) return s;
+    s = ensure_terms(st, (size_t)nt);
+    if (s != QS_OK) return s;
+    std::vector<PauliDev> hterms;
+    std::vector<std::pair<int, int>> chunks;   // (first index in hterms, count)
+    std::vector<uint64_t> chunk_x;
+    std::vector<int> order;
+    for (auto &g : groups) {
+        for (size_t i = 0; i < g.second.size(); i += 16) {
+            int c = (int)std::min<size_t>(16, g.second.size() - i);
+            chunks.push_back({(int)hterms.size(), c});
+            chunk_x.push_back(g.first);
+            for (int j = 0; j < c; ++j) {
+                int k = g.second[i + j];
+                hterms.push_back({t[k].coeff, t[k].x, t[k].z});
+                order.push_back(k);
+            }
+        }
+    }
+    QS_CUDA(cudaMemcpyAsync(st->d_terms, hterms.data(), hterms.size() * sizeof(PauliDev), cudaMemcpyHostToDevice,
+                            st->stream));
+    for (size_t c = 0; c < chunks.size(); ++c) {
+        ExpectArgs A;
+        A.psi = psi;
+        A.lam = phi;
+        A.state_elems = st->elems;
+        A.batch = batch;
+        A.xmask = chunk_x[c];
+        A.n_terms = chunks[c].second;
+        A.terms = st->d_terms + chunks[c].first;
+        A.partial = st->d_partial;
+        A.grid = grid;
+        cudaEvent_t ev;
+        prof_begin(st, &ev);
+        QS_CUDA(launch_expect_group(A, st->stream));
+        prof_end(st, ev, "expect", 8.0 * (double)st->elems * batch * (phi && phi != psi ? 2 : 1));
+        // partial -> out slots [chunk offset .. ) in hterms order
+        QS_CUDA(launch_expect_finish(st->d_partial, st->d_out + 0, batch, grid, A.n_terms, st->stream));
+        std::vector<double> h((size_t)batch * A.n_terms * 2);
+        QS_CUDA(cudaMemcpyAsync(h.data(), st->d_out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+        QS_CUDA(cudaStreamSynchronize(st->stream));
+        for (int b = 0; b < batch; ++b)
+            for (int j = 0; j < A.n_terms; ++j) {
+                int k = order[chunks[c].first + j];
+                S[((size_t)b * nt + k) * 2] = h[((size_t)b * A.n_terms + j) * 2];
+                S[((size_t)b * nt + k) * 2 + 1] = h[((size_t)b * A.n_terms + j) * 2 + 1];
+            }
+    }
+    return check_err_word(st);
+}
+
+// multiply (re, im) by i^ny
+inline void times_i_pow(double &re, double &im, int ny) {
+    double r = re, i = im;
+    switch (ny & 3) {
+        case 0: break;
+        case 1: re = -i; im = r; break;
+        case 2: re = -r; im = -i; break;
+        default: re = i; im = -r; break;
+    }
+}
+
+}  // namespace
+
+// ===========================================================================
+// exported C ABI
+// ===========================================================================
+extern "C" {
+
+const char *qs_last_error(void) { return g_last_error.c_str(); }
+
+const char *qs_version(void) { return "qs 0.1 (sm_103a)"; }
+
+static qs_status make_state(int n, int batch, qs_state **out) {
+    if (!out) return fail(QS_ERR_INVALID_ARG, "out == NULL");
+    *out = nullptr;
+    if (batch < 1) return fail(QS_ERR_INVALID_ARG, "batch < 1");
+    if (n < 1 || n > kMaxQubits) return fail(QS_ERR_UNSUPPORTED, "n must be in [1, 33]");
+    std::unique_ptr<qs_state> st(new qs_state());
+    st->n = n;
+    st->batch = batch;
+    st->elems = 1ll << n;
+    st->dev = current_device();
+    qs_status s = ensure_device_tables(st->dev);
+    if (s != QS_OK) return s;
+    QS_CUDA(cudaMalloc(&st->d_err, sizeof(int)));
+    QS_CUDA(cudaMemset(st->d_err, 0, sizeof(int)));
+    *out = st.release();
+    return QS_OK;
+}
+
+qs_status qs_alloc(int n, int batch, qs_state **out) {
+    qs_state *st = nullptr;
+    qs_status s = make_state(n, batch, &st);
+    if (s != QS_OK) return s;
+    size_t bytes = (size_t)st->elems * batch * sizeof(float2);
+    cudaError_t e = cudaMalloc(&st->home, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(st->d_err);
+        delete st;
+        return fail(QS_ERR_OOM, "cudaMalloc of the state failed");
+    }
+    st->owned = true;
+    e = (cudaError_t)launch_init_zero(st->home, st->elems, batch, st->stream);
+    if (e != cudaSuccess) {
+        qs_free(st);
+        return fail(QS_ERR_CUDA, cudaGetErrorString(e));
+    }
+    *out = st;
+    return QS_OK;
+}
+
+qs_status qs_wrap(void *dev_ptr, int n, int batch, void *cuda_stream, qs_state **out) {
+    if (!dev_ptr) return fail(QS_ERR_INVALID_ARG, "dev_ptr == NULL");
+    if (((uintptr_t)dev_ptr) & 15) return fail(QS_ERR_INVALID_ARG, "dev_ptr must be 16-byte aligned");
+    qs_state *st = nullptr;
+    qs_status s = make_state(n, batch, &st);
+    if (s != QS_OK) return s;
+    st->home = (float2 *)dev_ptr;
+    st->owned = false;
+    st->stream = (cudaStream_t)cuda_stream;
+    *out = st;
+    return QS_OK;
+}
+
+qs_status qs_free(qs_state *st) {
+    if (!st) return QS_OK;
+    cudaStreamSynchronize(st->stream);
+    for (auto &kv : st->cache) free_plan(st, kv.second.get());
+    cudaStreamSynchronize(st->stream);
+    for (auto &pe : st->prof_pending) {
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    if (st->owned && st->home) cudaFree(st->home);
+    if (st->scratch_owned && st->scratch) cudaFree(st->scratch);
+    if (st->d_err) cudaFree(st->d_err);
+    if (st->d_partial) cudaFree(st->d_partial);
+    if (st->d_out) cudaFree(st->d_out);
+    if (st->d_terms) cudaFree(st->d_terms);
+    delete st;
+    return QS_OK;
+}
+
+qs_status qs_set_stream(qs_state *st, void *cuda_stream) {
+    if (!st) return fail(QS_ERR_INVALID_ARG, "st == NULL");
+    st->stream = (cudaStream_t)cuda_stream;
+    return QS_OK;
+}
+
+qs_status qs_set_scratch(qs_state *st, void *dev_ptr, size_t bytes) {
+    if (!st) return fail(QS_ERR_INVALID_ARG, "st == NULL");
+    if (dev_ptr && (((uintptr_t)dev_ptr) & 15)) return fail(QS_ERR_INVALID_ARG, "scratch must be 16-byte aligned");
+    if (dev_ptr && bytes < (size_t)st->elems * st->batch * sizeof(float2))
+        return fail(QS_ERR_INVALID_ARG, "scratch smaller than the state");
+    if (st->scratch_owned && st->scratch) cudaFree(st->scratch);
+    st->scratch = (float2 *)dev_ptr;
+    st->scratch_bytes = dev_ptr ? bytes : 0;
+    st->scratch_owned = false;
+    return QS_OK;
+}
+
+qs_status qs_device_ptr(const qs_state *st, void **out) {
+    if (!st || !out) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+    *out = st->home;
+    return QS_OK;
+}
+
+qs_status qs_init_zero(qs_state *st) {
+    if (!st) return fail(QS_ERR_INVALID_ARG, "st == NULL");
+    QS_CUDA(launch_init_zero(st->home, st->elems, st->batch, st->stream));
+    return QS_OK;
+}
+
+qs_status qs_set_amplitudes(qs_state *st, const void *src, int is_device) {
+    if (!st || !src) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+    size_t bytes = (size_t)st->elems * st->batch * sizeof(float2);
+    QS_CUDA(cudaMemcpyAsync(st->home, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            st->stream));
+    QS_CUDA(cudaStreamSynchronize(st->stream));
+    return QS_OK;
+}
+
+qs_status qs_get_amplitudes(const qs_state *st, void *dst, int is_device) {
+    if (!st || !dst) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+    size_t bytes = (size_t)st->elems * st->batch * sizeof(float2);
+    QS_CUDA(cudaMemcpyAsync(dst, st->home, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            st->stream));
+    QS_CUDA(cudaStreamSynchronize(st->stream));
+    return QS_OK;
+}
+
+qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, const double *params, int n_params,
+                           const qs_opts *opts) {
+    if (!st) return fail(QS_ERR_INVALID_ARG, "st == NULL");
+    if (n_params < 0) return fail(QS_ERR_INVALID_ARG, "n_params < 0");
+    qs_opts o = default_opts(opts);
+    if (o.mode != QS_MODE_FUSED && o.mode != QS_MODE_PERGATE) return fail(QS_ERR_INVALID_ARG, "unknown mode");
+    const bool per_item = params && has_param_gates(gates, n_gates) && st->batch > 1;
+    // validate every batch item before launching anything
+    std::vector<std::vector<RGate>> resolved(per_item ? st->batch : 1);
+    for (size_t bi = 0; bi < resolved.size(); ++bi) {
+        std::string err;
+        qs_status s = resolve_gates(st->n, gates, n_gates, params, n_params, (int)bi, resolved[bi], err);
+        if (s != QS_OK) return fail(s, err);
+    }
+    if (n_gates == 0) return QS_OK;
+    if (!per_item) return apply_resolved(st, resolved[0], o, st->home, st->batch);
+    for (int bi = 0; bi < st->batch; ++bi) {
+        qs_status s = apply_resolved(st, resolved[bi], o, st->home + (size_t)bi * st->elems, 1);
+        if (s != QS_OK) return s;
+    }
+    return QS_OK;
+}
+
+qs_status qs_expect(qs_state *st, const qs_pauli *terms, size_t n_terms, double *out) {
+    if (!st || !out || (n_terms && !terms)) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+    std::vector<TermIdx> t;
+    qs_status s = convert_terms(st->n, terms, n_terms, t);
+    if (s != QS_OK) return s;
+    std::vector<double> S;
+    s = overlaps(st, st->home, nullptr, st->batch, t, S);
+    if (s != QS_OK) return s;
+    for (int b = 0; b < st->batch; ++b) {
+        double e = 0.0;
+        for (size_t k = 0; k < t.size(); ++k) {
+            double re = S[((size_t)b * t.size() + k) * 2], im = S[((size_t)b * t.size() + k) * 2 + 1];
+            times_i_pow(re, im, t[k].ny);
+            e += t[k].coeff * re;
+        }
+        out[b] = e;
+    }
+    return QS_OK;
+}
+
+qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const double *params, int n_params,
+                  const qs_pauli *terms, size_t n_terms, double *energy, double *grad) {
+    if (!st || !energy || !grad || (n_terms && !terms) || (n_gates && !gates))
+        return fail(QS_ERR_INVALID_ARG, "NULL argument");
+    if (n_params < 0 || (n_params > 0 && !params)) return fail(QS_ERR_INVALID_ARG, "bad params");
+    for (size_t i = 0; i < n_gates; ++i)
+        if (gates[i].param_idx >= 0) {
+            int k = gates[i].kind;
+            if (k != QS_RX && k != QS_RY && k != QS_RZ && k != QS_RZZ && k != QS_CP)
+                return fail(QS_ERR_UNSUPPORTED, "qs_grad: parameterised gates must be RX, RY, RZ, RZZ or CP");
+        }
+    const int B = st->batch;
+    std::vector<std::vector<RGate>> rg(B);
+    for (int b = 0; b < B; ++b) {
+        std::string err;
+        qs_status s = resolve_gates(st->n, gates, n_gates, params, n_params, b, rg[b], err);
+        if (s != QS_OK) return fail(s, err);
+    }
+    std::vector<TermIdx> t;
+    qs_status s = convert_terms(st->n, terms, n_terms, t);
+    if (s != QS_OK) return s;
+    // 1. forward: psi = U(theta)|0>
+    QS_CUDA(launch_init_zero(st->home, st->elems, B, st->stream));
+    qs_opts o = default_opts(nullptr);
+    for (int b = 0; b < B; ++b) {
+        s = apply_resolved(st, rg[b], o, st->home + (size_t)b * st->elems, 1);
+        if (s != QS_OK) return s;
+    }
+    // 2. energy
+    s = qs_expect(st, terms, n_terms, energy);
+    if (s != QS_OK) return s;
+    // 3. lambda = H psi (needs a second state per item: the scratch buffer) and a
+    //    working copy of psi, so the caller's state keeps psi(theta)
+    size_t bytes = (size_t)st->elems * B * sizeof(float2);
+    float2 *work = nullptr, *lam = nullptr;
+    QS_CUDA(cudaMallocAsync((void **)&work, bytes, st->stream));
+    cudaError_t e = cudaMallocAsync((void **)&lam, bytes, st->stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(work, st->stream);
+        return fail(QS_ERR_OOM, "qs_grad: no memory for the adjoint state");
+    }
+    struct Guard {
+        qs_state *st;
+        float2 *a, *b;
+        ~Guard() {
+            cudaFreeAsync(a, st->stream);
+            cudaFreeAsync(b, st->stream);
+        }
+    } guard{st, work, lam};
+    QS_CUDA(cudaMemcpyAsync(work, st->home, bytes, cudaMemcpyDeviceToDevice, st->stream));
+    {
+        std::vector<PauliDev> hp;
+        for (auto &x : t) hp.push_back({x.coeff, x.x, x.z});
+        s = ensure_terms(st, std::max<size_t>(hp.size(), 1));
+        if (s != QS_OK) return s;
+        if (!hp.empty())
+            QS_CUDA(cudaMemcpyAsync(st->d_terms, hp.data(), hp.size() * sizeof(PauliDev), cudaMemcpyHostToDevice,
+                                    st->stream));
+        QS_CUDA(cudaStreamSynchronize(st->stream));
+        if (!hp.empty()) {
+            cudaEvent_t ev;
+            prof_begin(st, &ev);
+            QS_CUDA(launch_apply_pauli_sum(work, lam, st->elems, B, st->d_terms, (int)hp.size(), st->stream));
+            prof_end(st, ev, "pauli_sum", 16.0 * (double)st->elems * B);
+        } else {
+            QS_CUDA(cudaMemsetAsync(lam, 0, bytes, st->stream));
+        }
+    }
+    // 4. reverse sweep: per gate, gradient overlap then un-apply on psi and lambda
+    for (size_t i = 0; i < (size_t)B * n_params; ++i) grad[i] = 0.0;
+    std::vector<PgOp> ops(B);
+    PgOp *d_ops = nullptr;
+    QS_CUDA(cudaMallocAsync((void **)&d_ops, sizeof(PgOp) * B, st->stream));
+    struct Guard2 {
+        qs_state *st;
+        PgOp *p;
+        ~Guard2() { cudaFreeAsync(p, st->stream); }
+    } guard2{st, d_ops};
+    for (size_t gi = n_gates; gi-- > 0;) {
+        const qs_gate &g = gates[gi];
+        if (g.param_idx >= 0) {
+            // generator overlaps  G = X, Y, Z, ZZ on the gate's bits (CP: P11 = (1 - Za - Zb + ZaZb)/4)
+            const RGate &r0 = rg[0][gi];
+            std::vector<TermIdx> gt;
+            auto term = [&](double c, uint64_t x, uint64_t z) {
+                TermIdx q;
+                q.coeff = c;
+                q.x = x;
+                q.z = z;
+                q.ny = __builtin_popcountll(x & z) & 3;
+                gt.push_back(q);
+            };
+            uint64_t ba = 1ull << r0.b[0], bb = r0.nw > 1 ? (1ull << r0.b[1]) : 0;
+            switch (g.kind) {
+                case QS_RX: term(1.0, ba, 0); break;
+                case QS_RY: term(1.0, ba, ba); break;
+                case QS_RZ: term(1.0, 0, ba); break;
+                case QS_RZZ: term(1.0, 0, ba | bb); break;
+                case QS_CP:
+                    term(0.25, 0, 0);
+                    term(-0.25, 0, ba);
+                    term(-0.25, 0, bb);
+                    term(0.25, 0, ba | bb);
+                    break;
+            }
+            std::vector<double> S;
+            s = overlaps(st, work, lam, B, gt, S);
+            if (s != QS_OK) return s;
+            for (int b = 0; b < B; ++b) {
+                double re_tot = 0.0, im_tot = 0.0;
+                for (size_t k = 0; k < gt.size(); ++k) {
+                    double re = S[((size_t)b * gt.size() + k) * 2], im = S[((size_t)b * gt.size() + k) * 2 + 1];
+                    times_i_pow(re, im, gt[k].ny);
+                    re_tot += gt[k].coeff * re;
+                    im_tot += gt[k].coeff * im;
+                }
+                // R(t) = exp(-i t G/2): dE/dt = Im<lam|G|psi>;  CP(t) = exp(i t P11): dE/dt = -2 Im<lam|P11|psi>
+                double d = (g.kind == QS_CP) ? -2.0 * im_tot : im_tot;
+                grad[(size_t)b * n_params + g.param_idx] += d;
+            }
+        }
+        // un-apply gate gi on both states (per-item matrices)
+        bool skip = false;
+        for (int b = 0; b < B; ++b) {
+            Plan tmp;
+            std::string err;
+            std::vector<RGate> one(1, rg[b][gi]);
+            build_pergate_plan(st->n, one, tmp, err);
+            if (tmp.pg.empty()) {
+                skip = true;
+                break;
+            }
+            PgOp op = tmp.pg[0];
+            // inverse: conjugate transpose / conjugate phases
+            if (op.kind == PG_U1) {
+                float2 m[4] = {op.m[0], op.m[1], op.m[2], op.m[3]};
+                op.m[0] = make_float2(m[0].x, -m[0].y);
+                op.m[1] = make_float2(m[2].x, -m[2].y);
+                op.m[2] = make_float2(m[1].x, -m[1].y);
+                op.m[3] = make_float2(m[3].x, -m[3].y);
+            } else if (op.kind == PG_U2) {
+                float2 m[16];
+                for (int e2 = 0; e2 < 16; ++e2) m[e2] = op.m[e2];
+                for (int r = 0; r < 4; ++r)
+                    for (int c = 0; c < 4; ++c) op.m[r * 4 + c] = make_float2(m[c * 4 + r].x, -m[c * 4 + r].y);
+            } else if (op.kind == PG_PHASE) {
+                for (int e2 = 0; e2 < 4; ++e2) op.m[e2].y = -op.m[e2].y;
+            }
+            ops[b] = op;
+        }
+        if (skip) continue;
+        QS_CUDA(cudaMemcpyAsync(d_ops, ops.data(), sizeof(PgOp) * B, cudaMemcpyHostToDevice, st->stream));
+        PgArgs A;
+        std::memset(&A, 0, sizeof A);
+        A.ops = d_ops;
+        A.op_stride = 1;
+        A.psi[0] = work;
+        A.psi[1] = lam;
+        A.n_arrays = 2;
+        A.state_elems = st->elems;
+        A.batch = B;
+        A.n = st->n;
+        pg_fixed(ops[0], st->n, A);
+        cudaEvent_t ev;
+        prof_begin(st, &ev);
+        QS_CUDA(launch_pergate(A, st->stream));
+        prof_end(st, ev, "adjoint_unapply", 2.0 * pg_bytes(ops[0], st->n) * B);
+        // the host op array is reused next iteration: wait for the copy
+        QS_CUDA(cudaStreamSynchronize(st->stream));
+    }
+    return check_err_word(st);
+}
+
+qs_status qs_plan_describe(int n, const qs_gate *gates, size_t n_gates, const qs_opts *opts, char *buf, size_t len,
+                           int *passes) {
+    if (n < 1 || n > kMaxQubits) return fail(QS_ERR_UNSUPPORTED, "n must be in [1, 33]");
+    qs_opts o = default_opts(opts);
+    std::vector<RGate> rg;
+    std::string err;
+    qs_status s = resolve_gates(n, gates, n_gates, nullptr, 0, 0, rg, err);
+    if (s != QS_OK) return fail(s, err);
+    Plan p;
+    s = (o.mode == QS_MODE_PERGATE) ? build_pergate_plan(n, rg, p, err) : build_fused_plan(n, rg, o, p, err);
+    if (s != QS_OK) return fail(s, err);
+    std::string d = p.describe();
+    if (buf && len) {
+        size_t c = std::min(len - 1, d.size());
+        std::memcpy(buf, d.data(), c);
+        buf[c] = 0;
+    }
+    if (passes) *passes = p.hbm_passes();
+    return QS_OK;
+}
+
+qs_status qs_profile_enable(qs_state *st, int enable) {
+    if (!st) return fail(QS_ERR_INVALID_ARG, "st == NULL");
+    cudaStreamSynchronize(st->stream);
+    for (auto &pe : st->prof_pending) {
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    st->prof_pending.clear();
+    st->prof_recs.clear();
+    st->prof = enable != 0;
+    return QS_OK;
+}
+
+qs_status qs_profile_read(qs_state *st, qs_profile_record *out, int cap, int *count) {
+    if (!st || !count || (cap > 0 && !out)) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+    QS_CUDA(cudaStreamSynchronize(st->stream));
+    for (auto &pe : st->prof_pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, pe.a, pe.b);
+        ProfRec &r = st->prof_recs[pe.name];
+        r.launches++;
+        r.ms += ms;
+        r.bytes += pe.bytes;
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    st->prof_pending.clear();
+    int i = 0;
+    for (auto &kv : st->prof_recs) {
+        if (i >= cap) break;
+        std::memset(&out[i], 0, sizeof(qs_profile_record));
+        std::strncpy(out[i].name, kv.first.c_str(), 31);
+        out[i].launches = kv.second.launches;
+        out[i].total_ms = kv.second.ms;
+        out[i].bytes = kv.second.bytes;
+        ++i;
+    }
+    *count = i;
+    return QS_OK;
+}
+
+}  // extern "C"

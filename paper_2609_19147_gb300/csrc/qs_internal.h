@@ -1,0 +1,145 @@
+// Internal definitions shared by the planner (host C++) and the CUDA kernels.
+//
+// Plan model.  The detector turns a gate list into an ordered list of fused
+// ops (the layer families of Sec. 5.1-5.2), and the scheduler packs them into
+// full-state HBM passes:
+//   * TILE pass   -- one read + one write of the state.  A CTA stages a tile
+//                    of 2^T amplitudes (the L lowest index bits, contiguous,
+//                    plus T-L chosen high bits) in shared memory with
+//                    bulk-async (TMA engine) copies, runs a list of "sweeps"
+//                    over it and writes it back.  A sweep gives every thread
+//                    2^r amplitudes that differ in r tile bits (held in
+//                    registers) and applies micro-ops to them: 2x2 / 4x4
+//                    unitaries on tile bits with optional controls on any
+//                    bits, diagonal phase layers, and QFT stages (Hadamard
+//                    butterfly + the stage's controlled-phase ladder in closed
+//                    form, Sec. 5.1 "Radix-4 butterflies").
+//   * PERM pass   -- out-of-place bit permutation plus XOR mask (runs of
+//                    SWAP / X; the QFT's final swaps), tile-transposed through
+//                    shared memory so that reads and writes are both
+//                    row-contiguous.
+//   * GATHER pass -- out-of-place GF(2) affine gather out[y] = in[A y ^ c]
+//                    (Sec. 5.1 "GF(2) affine permutation gathers").
+//   * PERGATE op  -- one launch per gate: the plain per-gate path (Sec. 3.2.2
+//                    structured dispatch), used as the baseline and for gates
+//                    no family covers.
+#pragma once
+
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#include "qs.h"
+
+namespace qs {
+
+constexpr int kMaxQubits = 33;
+constexpr int kMaxTileBits = 14;     // T
+constexpr int kMaxGroup = 5;         // r: amplitudes per thread = 2^r
+constexpr int kMaxSweeps = 40;
+constexpr int kMaxMicro = 320;
+constexpr int kMaxConst = 5120;      // complex64 constants per pass (40 KB)
+constexpr int kMaxDiag = 4;
+constexpr int kTileThreads = 256;
+
+// Diagonal phase (Sec. 5.1 "Phase-LUT diagonal layers").  The phase of basis
+// index x is
+//   gphase * prod_s SLICE_s[(x >> lo_s) & (2^w_s - 1)]
+//          * prod_g LUT_g[popcount(f_g(x) & m_g)]
+//          * prod_t TW(x_{p_t} * (x & bits[lo_t, p_t)), p_t)
+// with f_g(x) = x ^ (x >> d_g) (ZZ-type mismatch count) or x & (x >> d_g)
+// (CZ-type both-set count), and TW(u, p) = exp(i pi u / 2^p) (the QFT ladder
+// angle).  Tables are built on the host in FP64, reduced mod 2 pi and rounded
+// once to complex64.
+constexpr int kMaxSlices = 6;
+constexpr int kMaxLutGroups = 8;
+constexpr int kMaxTwiddles = 4;
+
+struct DiagDesc {
+    int32_t n_slices, n_groups, n_tw, pad0;
+    float gph_re, gph_im;
+    int32_t slice_lo[kMaxSlices], slice_w[kMaxSlices], slice_off[kMaxSlices];
+    int32_t grp_type[kMaxLutGroups], grp_d[kMaxLutGroups], grp_off[kMaxLutGroups];
+    uint64_t grp_mask[kMaxLutGroups];
+    int32_t tw_p[kMaxTwiddles], tw_lo[kMaxTwiddles];
+};
+
+enum MicroKind : int32_t {
+    MK_U1 = 0,    // 2x2 on group bit a where (x & cmask) == cval
+    MK_U2 = 1,    // 4x4 on group bits (a = matrix MSB, b = LSB) where (x & cmask) == cval
+    MK_DIAG = 2,  // diagonal phase, diag index = cst
+    MK_QFT = 3,   // QFT stage: H on group bit a (= global bit p), then twiddle
+                  // exp(i pi x_p (x & bits[lo, p)) / 2^p); group part at cst
+    MK_H = 4,     // Hadamard on group bit a (sign-only butterfly)
+};
+
+struct MicroOp {
+    int32_t kind;
+    int32_t a, b;          // group-local bit indices
+    int32_t p, lo;         // QFT: global bit p, lowest ladder bit
+    int32_t cst;           // constant offset (complex64 entries) / diag index
+    uint64_t cmask, cval;  // control condition on the global index
+};
+
+struct Sweep {
+    int32_t r;                   // group size (1..kMaxGroup)
+    int32_t op_begin, op_end;    // micro-op range [begin, end)
+    int32_t gbit[kMaxGroup];     // tile-local bit of group bit j
+    int32_t tbit[kMaxTileBits];  // tile-local bit of item bit i (i < T - r)
+};
+
+// One tile pass.  Tile-local bits 0..L-1 are the low index bits (one smem row
+// of 2^L amplitudes, padded to row_stride); tile-local bit L+k is global bit
+// hb[k].  Tiles are indexed by the remaining n-T bits (ascending).
+struct TilePass {
+    int32_t n, L, H, T;
+    int32_t row_stride;
+    int32_t n_sweeps, n_micro, n_const;
+    int32_t hb[kMaxTileBits];
+    Sweep sweeps[kMaxSweeps];
+    MicroOp micro[kMaxMicro];
+    DiagDesc diags[kMaxDiag];
+};
+
+// Roots-of-unity tables used by TW(u, p): R_k[c] = exp(i pi c 2^(8k) / 2^32)
+// for k = 0..3, c < 256, so that exp(i pi v / 2^32) = prod_k R_k[byte_k(v)].
+constexpr int kRootsEntries = 4 * 256;
+
+// ---------------------------------------------------------------------------
+// PERM pass: out[pi(x) ^ c] = in[x] for a bit permutation pi (out bit
+// out_pos[b] <- in bit b).  Tile = in-bits {0..L-1} U pi^-1({0..L-1}).
+// ---------------------------------------------------------------------------
+struct PermPass {
+    int32_t n, L;
+    int32_t out_pos[kMaxQubits];
+    uint64_t xor_mask;
+};
+
+// ---------------------------------------------------------------------------
+// GATHER pass: out[y] = in[c ^ T_0[y & 255] ^ T_1[(y >> 8) & 255] ^ ...]
+// with T_k[b] = A (b << 8k) (byte-sliced XOR tables of the inverse map).
+// ---------------------------------------------------------------------------
+struct GatherPass {
+    int32_t n, n_slices;
+    uint64_t c;
+    uint64_t tab[5][256];
+};
+
+// ---------------------------------------------------------------------------
+// Per-gate kernels: generic forms of the paper's structured pure tier.
+// ---------------------------------------------------------------------------
+enum PgKind : int32_t {
+    PG_U1 = 0,     // 2x2 on bit t over the subspace (x & cmask) == cval
+    PG_U2 = 1,     // 4x4 on bits (t0 msb, t1 lsb) over the subspace
+    PG_PHASE = 2,  // amp *= ph[(bit t0 of x) | (bit t1 of x) << 1] over subspace
+    PG_SWAP = 3,   // swap bits t0, t1 over the subspace
+};
+
+struct PgOp {
+    int32_t kind;
+    int32_t t0, t1;
+    int32_t nbits_phase;   // PG_PHASE: 1 (bit t0) or 2 (t0, t1)
+    uint64_t cmask, cval;
+    float2 m[16];          // matrix or phases
+};
+
+}  // namespace qs

@@ -1,0 +1,96 @@
+// Launch interfaces of the CUDA kernels (host <-> device argument blocks).
+#pragma once
+
+#include <cuda_runtime.h>
+#include "qs_internal.h"
+
+namespace qs {
+
+struct TileArgs {
+    const TilePass *pass;      // device copy of the pass descriptor
+    const float2 *consts;      // device copy of the pass constants
+    const float2 *roots;       // device roots-of-unity tables (kRootsEntries)
+    const float2 *src;         // read tiles from
+    float2 *dst;               // write tiles to (== src for in-place)
+    long long state_elems;     // 2^n
+    long long n_tiles;         // tiles per state, 2^(n - T)
+    int batch;
+    int n_outer;               // number of non-tile index bits
+    int outer_pos[kMaxQubits]; // their positions, ascending
+    int off_consts, off_roots, off_buf0, off_buf1;   // dynamic smem layout
+    int *err;                  // device status word
+};
+
+cudaError_t launch_tile_pass(const TileArgs &A, int grid, int smem_bytes, cudaStream_t st);
+void tile_kernel_smem_config(int bytes);
+
+// per-gate kernels: op per state (op_stride = 1) or shared (op_stride = 0)
+struct PgArgs {
+    const PgOp *ops;
+    int op_stride;
+    float2 *psi[2];            // up to two state arrays processed by one launch
+    int n_arrays;
+    long long state_elems;
+    int batch;
+    int n;
+    int n_fixed;               // fixed (non-enumerated) bit positions, ascending
+    int fixed_pos[4];
+    long long n_work;          // enumerated indices per state
+    int vec2;                  // 1: bit 0 is free -> two consecutive indices per thread
+};
+cudaError_t launch_pergate(const PgArgs &A, cudaStream_t st);
+
+struct PermArgs {
+    const float2 *src;
+    float2 *dst;
+    long long state_elems;
+    int batch;
+    int TB;                    // tile bits
+    int in_pos[12];            // global input position of input-local bit k
+    int out_pos_loc[12];       // global output position of output-local bit k
+    int out_to_in[12];         // input-local bit index feeding output-local bit k
+    int n_outer;
+    int outer_in[kMaxQubits];  // outer input bit positions (ascending)
+    int outer_out[kMaxQubits]; // their output positions
+    uint64_t xor_outer;        // xor mask on non-tile output bits
+    uint32_t xor_loc;          // xor mask in output-local coordinates
+};
+cudaError_t launch_perm(const PermArgs &A, cudaStream_t st);
+
+struct GatherArgs {
+    const GatherPass *g;       // device copy (tables)
+    const float2 *src;
+    float2 *dst;
+    long long state_elems;
+    int batch;
+};
+cudaError_t launch_gather(const GatherArgs &A, cudaStream_t st);
+
+// expectation / reductions (FP64 accumulation)
+struct PauliDev {
+    double coeff;
+    uint64_t x, z;             // index-bit masks
+};
+struct ExpectArgs {
+    const float2 *psi;         // states
+    const float2 *lam;         // second states (NULL: <psi|P|psi>)
+    long long state_elems;
+    int batch;
+    uint64_t xmask;            // common x mask of the group
+    int n_terms;
+    const PauliDev *terms;     // device
+    double *partial;           // [batch][grid][n_terms][2]
+    int grid;
+};
+cudaError_t launch_expect_group(const ExpectArgs &A, cudaStream_t st);
+// out[b*n_terms + k] (complex, 2 doubles) = sum over blocks of partial
+cudaError_t launch_expect_finish(const double *partial, double *out, int batch, int grid, int n_terms,
+                                 cudaStream_t st);
+
+// lam = sum_k coeff_k P_k psi  (one launch over all terms)
+cudaError_t launch_apply_pauli_sum(const float2 *psi, float2 *lam, long long state_elems, int batch,
+                                   const PauliDev *terms, int n_terms, cudaStream_t st);
+
+cudaError_t launch_init_zero(float2 *psi, long long state_elems, int batch, cudaStream_t st);
+
+}  // namespace qs

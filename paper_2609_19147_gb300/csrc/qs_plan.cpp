@@ -1,0 +1,1256 @@
+// Host-side planner: validation, FP64 gate matrices, the fusion detector and
+// the HBM-pass scheduler (see qs_plan.h).
+#include "qs_plan.h"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <sstream>
+
+namespace qs {
+
+static const double kPi = 3.14159265358979323846;
+static const double kSqrtHalf = 0.70710678118654752440;
+
+static int popc64(uint64_t v) { return __builtin_popcountll(v); }
+
+// ---------------------------------------------------------------------------
+// gate library (Sec. 3.2.2; OpenQASM table of Sec. 3.3; Sec. 5.1 terms)
+// ---------------------------------------------------------------------------
+static int kind_arity(int k) {
+    switch (k) {
+        case QS_I: case QS_X: case QS_Y: case QS_Z: case QS_H: case QS_S: case QS_SDG:
+        case QS_T: case QS_TDG: case QS_SX: case QS_RX: case QS_RY: case QS_RZ: case QS_P:
+        case QS_U2: case QS_U3: case QS_U:
+            return 1;
+        case QS_CX: case QS_CY: case QS_CZ: case QS_CH: case QS_SWAP: case QS_ISWAP:
+        case QS_CRX: case QS_CRY: case QS_CRZ: case QS_CP: case QS_RZZ: case QS_RXX: case QS_RYY:
+            return 2;
+        case QS_CCX: case QS_CSWAP:
+            return 3;
+        default:
+            return -1;
+    }
+}
+
+bool gate_is_diagonal(int k) {
+    switch (k) {
+        case QS_I: case QS_Z: case QS_S: case QS_SDG: case QS_T: case QS_TDG: case QS_RZ: case QS_P:
+        case QS_CZ: case QS_CRZ: case QS_CP: case QS_RZZ:
+            return true;
+        default:
+            return false;
+    }
+}
+
+static bool kind_takes_param(int k) {
+    switch (k) {
+        case QS_RX: case QS_RY: case QS_RZ: case QS_P: case QS_U2: case QS_U3: case QS_CRX:
+        case QS_CRY: case QS_CRZ: case QS_CP: case QS_RZZ: case QS_RXX: case QS_RYY:
+            return true;
+        default:
+            return false;
+    }
+}
+
+qs_status resolve_gates(int n, const qs_gate *gates, size_t n_gates, const double *params,
+                        int n_params, int bi, std::vector<RGate> &out, std::string &err) {
+    out.clear();
+    out.reserve(n_gates);
+    if (n_gates && !gates) {
+        err = "gates == NULL with n_gates > 0";
+        return QS_ERR_INVALID_ARG;
+    }
+    for (size_t i = 0; i < n_gates; ++i) {
+        const qs_gate &g = gates[i];
+        int ar = kind_arity(g.kind);
+        char buf[160];
+        if (ar < 0) {
+            snprintf(buf, sizeof buf, "gate %zu: unknown kind %d", i, (int)g.kind);
+            err = buf;
+            return QS_ERR_INVALID_ARG;
+        }
+        if ((int)g.nw != ar) {
+            snprintf(buf, sizeof buf, "gate %zu: kind %d takes %d wires, got %d", i, (int)g.kind, ar, (int)g.nw);
+            err = buf;
+            return QS_ERR_INVALID_ARG;
+        }
+        RGate r;
+        r.kind = g.kind;
+        r.nw = ar;
+        for (int m = 0; m < ar; ++m) {
+            if (g.w[m] < 0 || g.w[m] >= n) {
+                snprintf(buf, sizeof buf, "gate %zu: wire %d out of range [0,%d)", i, g.w[m], n);
+                err = buf;
+                return QS_ERR_INVALID_ARG;
+            }
+            for (int j = 0; j < m; ++j)
+                if (g.w[j] == g.w[m]) {
+                    snprintf(buf, sizeof buf, "gate %zu: duplicate wire %d", i, g.w[m]);
+                    err = buf;
+                    return QS_ERR_INVALID_ARG;
+                }
+            r.q[m] = g.w[m];
+            r.b[m] = n - 1 - g.w[m];
+        }
+        for (int m = 0; m < 3; ++m) r.p[m] = g.p[m];
+        if (g.param_idx >= 0) {
+            if (!kind_takes_param(g.kind)) {
+                snprintf(buf, sizeof buf, "gate %zu: kind %d has no angle to parameterise", i, (int)g.kind);
+                err = buf;
+                return QS_ERR_INVALID_ARG;
+            }
+            if (!params || g.param_idx >= n_params) {
+                snprintf(buf, sizeof buf, "gate %zu: param_idx %d outside params[%d]", i, g.param_idx, n_params);
+                err = buf;
+                return QS_ERR_INVALID_ARG;
+            }
+            r.p[0] = params[(size_t)bi * n_params + g.param_idx];
+        } else if (g.param_idx < -1) {
+            snprintf(buf, sizeof buf, "gate %zu: param_idx %d < -1", i, g.param_idx);
+            err = buf;
+            return QS_ERR_INVALID_ARG;
+        }
+        if (g.kind == QS_U) {
+            if (!g.dense) {
+                snprintf(buf, sizeof buf, "gate %zu: QS_U needs a dense matrix", i);
+                err = buf;
+                return QS_ERR_INVALID_ARG;
+            }
+            for (int e = 0; e < 4; ++e) r.dense[e] = cd(g.dense[2 * e], g.dense[2 * e + 1]);
+        }
+        for (int m = 0; m < 3; ++m)
+            if (!std::isfinite(r.p[m])) {
+                snprintf(buf, sizeof buf, "gate %zu: non-finite angle", i);
+                err = buf;
+                return QS_ERR_INVALID_ARG;
+            }
+        out.push_back(r);
+    }
+    return QS_OK;
+}
+
+// 2x2 unitary of a one-qubit kind.
+static void mat1(int k, const double *p, const cd *dense, cd M[4]) {
+    const cd I(0, 1);
+    auto set = [&](cd a, cd b, cd c, cd d) { M[0] = a; M[1] = b; M[2] = c; M[3] = d; };
+    double c, s;
+    switch (k) {
+        case QS_I: set(1, 0, 0, 1); break;
+        case QS_X: set(0, 1, 1, 0); break;
+        case QS_Y: set(0, -I, I, 0); break;
+        case QS_Z: set(1, 0, 0, -1); break;
+        case QS_H: set(kSqrtHalf, kSqrtHalf, kSqrtHalf, -kSqrtHalf); break;
+        case QS_S: set(1, 0, 0, I); break;
+        case QS_SDG: set(1, 0, 0, -I); break;
+        case QS_T: set(1, 0, 0, std::polar(1.0, kPi / 4)); break;
+        case QS_TDG: set(1, 0, 0, std::polar(1.0, -kPi / 4)); break;
+        case QS_SX: set(cd(0.5, 0.5), cd(0.5, -0.5), cd(0.5, -0.5), cd(0.5, 0.5)); break;
+        case QS_RX: c = cos(p[0] / 2); s = sin(p[0] / 2); set(c, -I * s, -I * s, c); break;
+        case QS_RY: c = cos(p[0] / 2); s = sin(p[0] / 2); set(c, -s, s, c); break;
+        case QS_RZ: set(std::polar(1.0, -p[0] / 2), 0, 0, std::polar(1.0, p[0] / 2)); break;
+        case QS_P: set(1, 0, 0, std::polar(1.0, p[0])); break;
+        case QS_U2: case QS_U3: {
+            double th = (k == QS_U2) ? kPi / 2 : p[0];
+            double ph = (k == QS_U2) ? p[0] : p[1];
+            double la = (k == QS_U2) ? p[1] : p[2];
+            c = cos(th / 2);
+            s = sin(th / 2);
+            set(c, -std::polar(1.0, la) * s, std::polar(1.0, ph) * s, std::polar(1.0, ph + la) * c);
+            break;
+        }
+        case QS_U: for (int e = 0; e < 4; ++e) M[e] = dense[e]; break;
+        default: set(1, 0, 0, 1);
+    }
+}
+
+void gate_matrix(const RGate &g, cd *M) {
+    if (g.nw == 1) {
+        mat1(g.kind, g.p, g.dense, M);
+        return;
+    }
+    const int K = 1 << g.nw;
+    for (int i = 0; i < K * K; ++i) M[i] = 0;
+    for (int i = 0; i < K; ++i) M[i * K + i] = 1;
+    const cd I(0, 1);
+    auto ctrl1 = [&](int kind1, double ang) {   // controlled 2x2 in the lower-right block
+        cd U[4];
+        double pp[3] = {ang, 0, 0};
+        mat1(kind1, pp, nullptr, U);
+        M[2 * 4 + 2] = U[0]; M[2 * 4 + 3] = U[1]; M[3 * 4 + 2] = U[2]; M[3 * 4 + 3] = U[3];
+    };
+    double c, s;
+    switch (g.kind) {
+        case QS_CX: ctrl1(QS_X, 0); break;
+        case QS_CY: ctrl1(QS_Y, 0); break;
+        case QS_CZ: ctrl1(QS_Z, 0); break;
+        case QS_CH: ctrl1(QS_H, 0); break;
+        case QS_CRX: ctrl1(QS_RX, g.p[0]); break;
+        case QS_CRY: ctrl1(QS_RY, g.p[0]); break;
+        case QS_CRZ: ctrl1(QS_RZ, g.p[0]); break;
+        case QS_CP: M[15] = std::polar(1.0, g.p[0]); break;
+        case QS_SWAP: M[5] = 0; M[10] = 0; M[6] = 1; M[9] = 1; break;
+        case QS_ISWAP: M[5] = 0; M[10] = 0; M[6] = I; M[9] = I; break;
+        case QS_RZZ:
+            M[0] = M[15] = std::polar(1.0, -g.p[0] / 2);
+            M[5] = M[10] = std::polar(1.0, g.p[0] / 2);
+            break;
+        case QS_RXX: case QS_RYY: {
+            c = cos(g.p[0] / 2);
+            s = sin(g.p[0] / 2);
+            // exp(-i t/2 P(x)P) = c I - i s P(x)P; XX flips both bits (+1),
+            // YY = -XX on |00>,|11> and +XX on |01>,|10>
+            double sg03 = (g.kind == QS_RXX) ? 1.0 : -1.0;
+            for (int i = 0; i < 4; ++i) M[i * 4 + i] = c;
+            M[0 * 4 + 3] = M[3 * 4 + 0] = -I * s * sg03;
+            M[1 * 4 + 2] = M[2 * 4 + 1] = -I * s;
+            break;
+        }
+        case QS_CCX:
+            M[6 * 8 + 6] = 0; M[7 * 8 + 7] = 0; M[6 * 8 + 7] = 1; M[7 * 8 + 6] = 1;
+            break;
+        case QS_CSWAP:
+            M[5 * 8 + 5] = 0; M[6 * 8 + 6] = 0; M[5 * 8 + 6] = 1; M[6 * 8 + 5] = 1;
+            break;
+        default: break;
+    }
+}
+
+// phases of diagonal kinds (radians): 1q -> ph[0..1]; 2q -> ph[0..3], index x_w0*2 + x_w1
+static void diag_phases(const RGate &g, double *ph) {
+    const double t = g.p[0];
+    switch (g.kind) {
+        case QS_I: ph[0] = 0; ph[1] = 0; break;
+        case QS_Z: ph[0] = 0; ph[1] = kPi; break;
+        case QS_S: ph[0] = 0; ph[1] = kPi / 2; break;
+        case QS_SDG: ph[0] = 0; ph[1] = -kPi / 2; break;
+        case QS_T: ph[0] = 0; ph[1] = kPi / 4; break;
+        case QS_TDG: ph[0] = 0; ph[1] = -kPi / 4; break;
+        case QS_RZ: ph[0] = -t / 2; ph[1] = t / 2; break;
+        case QS_P: ph[0] = 0; ph[1] = t; break;
+        case QS_CZ: ph[0] = ph[1] = ph[2] = 0; ph[3] = kPi; break;
+        case QS_CP: ph[0] = ph[1] = ph[2] = 0; ph[3] = t; break;
+        case QS_CRZ: ph[0] = ph[1] = 0; ph[2] = -t / 2; ph[3] = t / 2; break;
+        case QS_RZZ: ph[0] = ph[3] = -t / 2; ph[1] = ph[2] = t / 2; break;
+        default: ph[0] = ph[1] = ph[2] = ph[3] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Diag
+// ---------------------------------------------------------------------------
+uint64_t Diag::support() const {
+    uint64_t s = 0;
+    for (auto &kv : a) s |= 1ull << kv.first;
+    for (auto &kv : pairs) s |= (1ull << kv.first.first) | (1ull << kv.first.second);
+    return s;
+}
+void Diag::add1(int b, double ph0, double ph1) {
+    g0 += ph0;
+    if (ph1 - ph0 != 0.0) a[b] += ph1 - ph0;
+}
+void Diag::add2(int b0, int b1, const double ph[4]) {
+    g0 += ph[0];
+    if (ph[2] - ph[0] != 0.0) a[b0] += ph[2] - ph[0];
+    if (ph[1] - ph[0] != 0.0) a[b1] += ph[1] - ph[0];
+    double gam = ph[3] - ph[2] - ph[1] + ph[0];
+    if (gam != 0.0) pairs[{std::min(b0, b1), std::max(b0, b1)}] += gam;
+}
+void Diag::merge(const Diag &o) {
+    g0 += o.g0;
+    for (auto &kv : o.a) a[kv.first] += kv.second;
+    for (auto &kv : o.pairs) pairs[kv.first] += kv.second;
+}
+
+uint64_t FOp::N() const {
+    switch (kind) {
+        case F_U1: return 1ull << t0;
+        case F_U2: return (1ull << t0) | (1ull << t1);
+        case F_DIAG: return 0;
+        case F_QFT: return 1ull << p;
+        case F_GF2: return ~0ull;
+    }
+    return ~0ull;
+}
+uint64_t FOp::D() const {
+    switch (kind) {
+        case F_U1: case F_U2: return cmask;
+        case F_DIAG: return diag.support();
+        case F_QFT: return (p > lo) ? (((1ull << p) - 1) & ~((1ull << lo) - 1)) : 0;
+        case F_GF2: return ~0ull;
+    }
+    return ~0ull;
+}
+
+static bool commute(const FOp &x, const FOp &y) {
+    if (x.kind == F_GF2 || y.kind == F_GF2) return false;
+    uint64_t nx = x.N(), ny = y.N();
+    return (nx & (ny | y.D())) == 0 && (ny & (nx | x.D())) == 0;
+}
+
+// ---------------------------------------------------------------------------
+// detector (Sec. 5.2): per-wire 1q window collapse with symbolic cancellation
+// of involution pairs, commuting diagonal runs, QFT stages, GF(2) runs
+// ---------------------------------------------------------------------------
+namespace {
+struct Window {
+    std::vector<std::array<cd, 4>> mats;
+    std::vector<int> kinds;
+    int n_gates = 0;
+};
+
+bool is_involution_kind(int k) { return k == QS_H || k == QS_X || k == QS_Y || k == QS_Z; }
+
+void mat2x2_mul(const cd A[4], const cd B[4], cd C[4]) {   // C = A B
+    cd c0 = A[0] * B[0] + A[1] * B[2], c1 = A[0] * B[1] + A[1] * B[3];
+    cd c2 = A[2] * B[0] + A[3] * B[2], c3 = A[2] * B[1] + A[3] * B[3];
+    C[0] = c0; C[1] = c1; C[2] = c2; C[3] = c3;
+}
+
+struct Detector {
+    int n;
+    std::vector<FOp> &ops;
+    Diag D;
+    int D_gates = 0;
+    std::vector<Window> pend;
+    Detector(int n_, std::vector<FOp> &o) : n(n_), ops(o), pend(n_) {}
+
+    void emit_diag() {
+        if (!D.empty() || D_gates) {
+            if (!D.empty()) {
+                FOp f;
+                f.kind = F_DIAG;
+                f.diag = D;
+                f.n_gates = D_gates;
+                ops.push_back(f);
+            }
+            D = Diag();
+            D_gates = 0;
+        }
+    }
+    // Emit the open diagonal, then every pending window (non-diagonal
+    // products as U1 ops; exactly diagonal products seed the next diagonal).
+    void flush_all() {
+        emit_diag();
+        Diag nd;
+        int nd_gates = 0;
+        for (int q = 0; q < n; ++q) {
+            Window &w = pend[q];
+            if (w.mats.empty()) {
+                w.n_gates = 0;
+                continue;
+            }
+            cd P[4] = {1, 0, 0, 1};
+            for (auto &m : w.mats) mat2x2_mul(m.data(), P, P);
+            int b = n - 1 - q;
+            bool ident = P[0] == cd(1, 0) && P[1] == cd(0, 0) && P[2] == cd(0, 0) && P[3] == cd(1, 0);
+            bool diag = P[1] == cd(0, 0) && P[2] == cd(0, 0);
+            if (ident) {
+                // exact identity (rtol = 0): nothing to apply
+            } else if (diag) {
+                nd.g0 += std::arg(P[0]);
+                nd.a[b] += std::arg(P[3]) - std::arg(P[0]);
+                nd_gates += w.n_gates;
+            } else {
+                FOp f;
+                f.kind = F_U1;
+                f.t0 = b;
+                for (int e = 0; e < 4; ++e) f.m[e] = P[e];
+                f.n_gates = w.n_gates;
+                ops.push_back(f);
+            }
+            w.mats.clear();
+            w.kinds.clear();
+            w.n_gates = 0;
+        }
+        D = nd;
+        D_gates = nd_gates;
+        if (D.empty() && nd_gates) {   // diagonal windows that multiplied out to phase 0
+            D_gates = 0;
+        }
+    }
+    bool any_pending(const RGate &g) const {
+        for (int m = 0; m < g.nw; ++m)
+            if (!pend[g.q[m]].mats.empty()) return true;
+        return false;
+    }
+    void gate(const RGate &g) {
+        if (g.nw == 1) {
+            Window &w = pend[g.q[0]];
+            if (gate_is_diagonal(g.kind) && w.mats.empty()) {
+                double ph[2];
+                diag_phases(g, ph);
+                D.add1(g.b[0], ph[0], ph[1]);
+                D_gates++;
+                return;
+            }
+            if (g.kind == QS_I && w.mats.empty()) return;
+            // symbolic cancellation of an involution pair (H H, X X, Y Y, Z Z)
+            if (is_involution_kind(g.kind) && !w.kinds.empty() && w.kinds.back() == g.kind) {
+                w.kinds.pop_back();
+                w.mats.pop_back();
+                w.n_gates++;
+                return;
+            }
+            std::array<cd, 4> M;
+            mat1(g.kind, g.p, g.dense, M.data());
+            w.mats.push_back(M);
+            w.kinds.push_back(g.kind);
+            w.n_gates++;
+            return;
+        }
+        if (gate_is_diagonal(g.kind)) {
+            if (any_pending(g)) flush_all();
+            double ph[4];
+            diag_phases(g, ph);
+            D.add2(g.b[0], g.b[1], ph);
+            D_gates++;
+            return;
+        }
+        flush_all();
+        emit_diag();
+        FOp f;
+        f.n_gates = 1;
+        cd M[64];
+        gate_matrix(g, M);
+        switch (g.kind) {
+            case QS_CX: case QS_CY: case QS_CH: case QS_CRX: case QS_CRY:
+                f.kind = F_U1;
+                f.t0 = g.b[1];
+                f.cmask = f.cval = 1ull << g.b[0];
+                f.m[0] = M[10]; f.m[1] = M[11]; f.m[2] = M[14]; f.m[3] = M[15];
+                break;
+            case QS_CCX:
+                f.kind = F_U1;
+                f.t0 = g.b[2];
+                f.cmask = f.cval = (1ull << g.b[0]) | (1ull << g.b[1]);
+                f.m[0] = 0; f.m[1] = 1; f.m[2] = 1; f.m[3] = 0;
+                break;
+            case QS_CSWAP:
+                f.kind = F_U2;
+                f.t0 = g.b[1];
+                f.t1 = g.b[2];
+                f.cmask = f.cval = 1ull << g.b[0];
+                for (int e = 0; e < 16; ++e) f.m[e] = 0;
+                f.m[0] = f.m[15] = 1;
+                f.m[1 * 4 + 2] = f.m[2 * 4 + 1] = 1;
+                break;
+            default:   // SWAP, ISWAP, RXX, RYY: 4x4 on (w0 = MSB, w1)
+                f.kind = F_U2;
+                f.t0 = g.b[0];
+                f.t1 = g.b[1];
+                for (int e = 0; e < 16; ++e) f.m[e] = M[e];
+        }
+        ops.push_back(f);
+    }
+    void finish() {
+        flush_all();
+        emit_diag();
+    }
+};
+
+bool is_exact_h(const FOp &f) {
+    return f.kind == F_U1 && f.cmask == 0 && f.m[0] == cd(kSqrtHalf, 0) && f.m[1] == cd(kSqrtHalf, 0) &&
+           f.m[2] == cd(kSqrtHalf, 0) && f.m[3] == cd(-kSqrtHalf, 0);
+}
+bool is_exact_x(const FOp &f) {
+    return f.kind == F_U1 && f.m[0] == cd(0, 0) && f.m[1] == cd(1, 0) && f.m[2] == cd(1, 0) &&
+           f.m[3] == cd(0, 0);
+}
+bool is_exact_swap(const FOp &f) {
+    if (f.kind != F_U2 || f.cmask) return false;
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            int want = ((i == 0 && j == 0) || (i == 3 && j == 3) || (i == 1 && j == 2) || (i == 2 && j == 1));
+            if (f.m[i * 4 + j] != cd(want, 0)) return false;
+        }
+    return true;
+}
+// X, CNOT (one control) or SWAP: affine over GF(2)
+bool is_gf2(const FOp &f) {
+    if (is_exact_x(f) && popc64(f.cmask) <= 1 && f.cmask == f.cval) return true;
+    return is_exact_swap(f);
+}
+
+// QFT stage: an exact H on bit p followed by a diagonal that is exactly the
+// stage's controlled-phase ladder sum_{b in [lo,p)} x_b x_p pi / 2^(p-b).
+bool match_ladder(const Diag &d, int p, int &lo) {
+    if (d.g0 != 0.0 || d.pairs.empty()) return false;
+    for (auto &kv : d.a)
+        if (kv.second != 0.0) return false;
+    int cnt = 0;
+    int mn = p;
+    for (auto &kv : d.pairs) {
+        int b = kv.first.first, c = kv.first.second;
+        if (c != p || b >= p) return false;
+        if (kv.second != std::ldexp(kPi, -(p - b))) return false;
+        mn = std::min(mn, b);
+        cnt++;
+    }
+    if (cnt != p - mn) return false;   // contiguous bits [mn, p)
+    lo = mn;
+    return true;
+}
+}  // namespace
+
+void detect(int n, const std::vector<RGate> &gates, std::vector<FOp> &ops) {
+    std::vector<FOp> raw;
+    Detector det(n, raw);
+    for (const RGate &g : gates) det.gate(g);
+    det.finish();
+
+    // QFT stages
+    std::vector<FOp> s1;
+    for (size_t i = 0; i < raw.size(); ++i) {
+        if (is_exact_h(raw[i]) && i + 1 < raw.size() && raw[i + 1].kind == F_DIAG) {
+            int lo;
+            if (match_ladder(raw[i + 1].diag, raw[i].t0, lo)) {
+                FOp f;
+                f.kind = F_QFT;
+                f.p = raw[i].t0;
+                f.lo = lo;
+                f.n_gates = raw[i].n_gates + raw[i + 1].n_gates;
+                s1.push_back(f);
+                ++i;
+                continue;
+            }
+        }
+        s1.push_back(raw[i]);
+    }
+    // GF(2) runs of length >= 2
+    ops.clear();
+    for (size_t i = 0; i < s1.size();) {
+        size_t j = i;
+        while (j < s1.size() && is_gf2(s1[j])) ++j;
+        if (j - i < 2) {
+            ops.push_back(s1[i]);
+            ++i;
+            continue;
+        }
+        {
+            FOp f;
+            f.kind = F_GF2;
+            f.rows.resize(n);
+            for (int b = 0; b < n; ++b) f.rows[b] = 1ull << b;
+            f.c = 0;
+            f.n_gates = 0;
+            for (size_t k = i; k < j; ++k) {
+                const FOp &g = s1[k];
+                f.n_gates += g.n_gates;
+                if (g.kind == F_U1 && g.cmask == 0) {
+                    f.c ^= 1ull << g.t0;
+                } else if (g.kind == F_U1) {
+                    int cb = __builtin_ctzll(g.cmask);
+                    f.rows[g.t0] ^= f.rows[cb];
+                    if ((f.c >> cb) & 1) f.c ^= 1ull << g.t0;
+                } else {
+                    std::swap(f.rows[g.t0], f.rows[g.t1]);
+                    uint64_t ba = (f.c >> g.t0) & 1, bb = (f.c >> g.t1) & 1;
+                    if (ba != bb) f.c ^= (1ull << g.t0) | (1ull << g.t1);
+                }
+            }
+            ops.push_back(f);
+            i = j;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// diagonal -> device descriptors and tables
+// ---------------------------------------------------------------------------
+namespace {
+double wrap_angle(double x) {
+    double r = std::remainder(x, 2.0 * kPi);
+    return r;
+}
+float2 cexp_f(double ph) {
+    double r = wrap_angle(ph);
+    float2 v;
+    v.x = (float)std::cos(r);
+    v.y = (float)std::sin(r);
+    return v;
+}
+
+struct DiagPlan {            // one Diag split into device descriptors
+    std::vector<DiagDesc> descs;
+    std::vector<std::vector<float2>> tables;   // per desc: its constants (offsets relative)
+};
+
+// Slices: window s covers bits [8s, 8s+w), w = min(9, n-8s).  A single-bit
+// term on b goes to slice b/8; a pair (b, c) goes to slice b/8 when c is
+// inside that window; other pairs are grouped by (distance, angle) into
+// popcount LUTs of the CZ type.
+void plan_diag(int n, const Diag &d, DiagPlan &out) {
+    const int ns = (n + 7) / 8;
+    std::vector<std::map<int, double>> s_single(ns);
+    std::vector<std::map<std::pair<int, int>, double>> s_pair(ns);
+    std::map<std::pair<int, double>, uint64_t> groups;   // (d, gamma) -> mask of low bits
+    for (auto &kv : d.a) {
+        if (kv.second == 0.0) continue;
+        s_single[kv.first / 8][kv.first] += kv.second;
+    }
+    for (auto &kv : d.pairs) {
+        if (kv.second == 0.0) continue;
+        int b = kv.first.first, c = kv.first.second;
+        int s = b / 8;
+        if (c < 8 * s + 9) {
+            s_pair[s][kv.first] += kv.second;
+        } else {
+            groups[{c - b, kv.second}] |= 1ull << b;
+        }
+    }
+    DiagDesc cur;
+    std::memset(&cur, 0, sizeof cur);
+    std::vector<float2> tab;
+    bool g0_done = false;
+    for (int s = 0; s < ns; ++s) {
+        if (s_single[s].empty() && s_pair[s].empty()) continue;
+        int lo = 8 * s, w = std::min(9, n - 8 * s);
+        int k = cur.n_slices++;
+        cur.slice_lo[k] = lo;
+        cur.slice_w[k] = w;
+        cur.slice_off[k] = (int)tab.size();
+        for (int v = 0; v < (1 << w); ++v) {
+            double ph = 0.0;
+            if (!g0_done) ph += d.g0;
+            for (auto &kv : s_single[s])
+                if ((v >> (kv.first - lo)) & 1) ph += kv.second;
+            for (auto &kv : s_pair[s])
+                if (((v >> (kv.first.first - lo)) & 1) && ((v >> (kv.first.second - lo)) & 1)) ph += kv.second;
+            tab.push_back(cexp_f(ph));
+        }
+        g0_done = true;
+    }
+    if (!g0_done && d.g0 != 0.0) {
+        cur.gph_re = (float)std::cos(wrap_angle(d.g0));
+        cur.gph_im = (float)std::sin(wrap_angle(d.g0));
+        cur.pad0 = 1;   // has global phase
+    }
+    for (auto &kv : groups) {
+        if (cur.n_groups == kMaxLutGroups) {
+            out.descs.push_back(cur);
+            out.tables.push_back(tab);
+            std::memset(&cur, 0, sizeof cur);
+            tab.clear();
+        }
+        int k = cur.n_groups++;
+        cur.grp_type[k] = 1;   // CZ-type: popcount(x & (x >> d) & m)
+        cur.grp_d[k] = kv.first.first;
+        cur.grp_mask[k] = kv.second;
+        cur.grp_off[k] = (int)tab.size();
+        int cnt = popc64(kv.second);
+        for (int c = 0; c <= cnt; ++c) tab.push_back(cexp_f(c * kv.first.second));
+    }
+    out.descs.push_back(cur);
+    out.tables.push_back(tab);
+}
+
+size_t diag_const_size(const DiagPlan &dp) {
+    size_t s = 0;
+    for (auto &t : dp.tables) s += t.size();
+    return s;
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// scheduler: greedy commutation-aware packing of fused ops into tile passes
+// ---------------------------------------------------------------------------
+namespace {
+struct OpCost {
+    int n_const = 0;
+    int n_micro = 1;
+    int n_diag = 0;
+};
+
+OpCost op_cost(int n, const FOp &f, int R, const DiagPlan *dp) {
+    OpCost c;
+    switch (f.kind) {
+        case F_U1: c.n_const = 4; break;
+        case F_U2: c.n_const = 16; break;
+        case F_QFT: c.n_const = 1 << R; break;
+        case F_DIAG:
+            c.n_const = (int)diag_const_size(*dp);
+            c.n_diag = (int)dp->descs.size();
+            c.n_micro = c.n_diag;
+            break;
+        default: break;
+    }
+    (void)n;
+    return c;
+}
+
+int tile_local(const TilePass &tp, int b) {
+    if (b < tp.L) return b;
+    for (int k = 0; k < tp.H; ++k)
+        if (tp.hb[k] == b) return tp.L + k;
+    return -1;
+}
+
+uint64_t glob_of_local(const TilePass &tp, int tb) {
+    return tb < tp.L ? (1ull << tb) : (1ull << tp.hb[tb - tp.L]);
+}
+
+int smem_of_local(const TilePass &tp, int tb) {
+    return tb < tp.L ? (1 << tb) : (tp.row_stride << (tb - tp.L));
+}
+
+// choose item-bit order so that a warp's 32 lanes hit distinct banks
+void choose_item_bits(const TilePass &tp, Sweep &sw) {
+    std::vector<int> cand;
+    uint64_t gmask = 0;
+    for (int j = 0; j < sw.r; ++j) gmask |= 1ull << sw.gbit[j];
+    for (int tb = 0; tb < tp.T; ++tb)
+        if (!((gmask >> tb) & 1)) cand.push_back(tb);
+    int k = (int)cand.size();
+    int nl = std::min(5, k);
+    std::vector<int> best;
+    int best_cost = 1 << 30;
+    // enumerate subsets of size nl (k <= 13)
+    std::vector<int> idx(nl);
+    for (int i = 0; i < nl; ++i) idx[i] = i;
+    while (true) {
+        // cost: max number of distinct 8-byte words per 4-byte bank pair
+        int words[32];
+        for (int l = 0; l < (1 << nl); ++l) {
+            int w = 0;
+            for (int i = 0; i < nl; ++i)
+                if ((l >> i) & 1) w += smem_of_local(tp, cand[idx[i]]);
+            words[l] = w;
+        }
+        int bank_cnt[32] = {0};
+        for (int l = 0; l < (1 << nl); ++l) {
+            bool dup = false;
+            for (int m = 0; m < l; ++m)
+                if (words[m] == words[l]) dup = true;
+            if (dup) continue;
+            bank_cnt[(2 * words[l]) & 31]++;
+            bank_cnt[(2 * words[l] + 1) & 31]++;
+        }
+        int cost = 0;
+        for (int b = 0; b < 32; ++b) cost = std::max(cost, bank_cnt[b]);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best.assign(idx.begin(), idx.end());
+        }
+        int i = nl - 1;
+        while (i >= 0 && idx[i] == k - nl + i) --i;
+        if (i < 0) break;
+        idx[i]++;
+        for (int j = i + 1; j < nl; ++j) idx[j] = idx[j - 1] + 1;
+    }
+    std::vector<int> order;
+    std::vector<bool> used(k, false);
+    for (int i : best) {
+        order.push_back(cand[i]);
+        used[i] = true;
+    }
+    for (int i = 0; i < k; ++i)
+        if (!used[i]) order.push_back(cand[i]);
+    for (int i = 0; i < k; ++i) sw.tbit[i] = order[i];
+}
+
+struct PassBuilder {
+    int n, L, T, R;
+    HostPass hp;
+    TilePass &tp;
+    std::vector<float2> &cst;
+    uint64_t cur_group = 0;   // tile-local bits of the open sweep
+    int open = -1;
+    PassBuilder(int n_, int L_, int T_, int R_, uint64_t S)
+        : n(n_), L(L_), T(T_), R(R_), tp(hp.tile), cst(hp.consts) {
+        std::memset(&tp, 0, sizeof(TilePass));
+        hp.type = HostPass::TILE;
+        tp.n = n;
+        tp.L = L;
+        tp.T = T;
+        tp.H = T - L;
+        tp.row_stride = (1 << L) + 2;
+        int k = 0;
+        for (int b = L; b < n; ++b)
+            if ((S >> b) & 1) tp.hb[k++] = b;
+    }
+    int group_index(int tb) {
+        for (int j = 0; j < tp.sweeps[open].r; ++j)
+            if (tp.sweeps[open].gbit[j] == tb) return j;
+        return -1;
+    }
+    // ensure the open sweep's group holds tile-local bits `need`
+    void need_bits(uint64_t need) {
+        if (open >= 0 && (popc64(cur_group | need) <= R)) {
+            Sweep &sw = tp.sweeps[open];
+            for (int tb = 0; tb < T; ++tb)
+                if (((need >> tb) & 1) && !((cur_group >> tb) & 1)) sw.gbit[sw.r++] = tb;
+            cur_group |= need;
+            return;
+        }
+        close_sweep();
+        open = tp.n_sweeps++;
+        Sweep &sw = tp.sweeps[open];
+        std::memset(&sw, 0, sizeof sw);
+        sw.op_begin = sw.op_end = tp.n_micro;
+        cur_group = need;
+        for (int tb = 0; tb < T; ++tb)
+            if ((need >> tb) & 1) sw.gbit[sw.r++] = tb;
+    }
+    void close_sweep() {
+        if (open < 0) return;
+        Sweep &sw = tp.sweeps[open];
+        // pad the group to R bits with unused tile bits (highest first)
+        for (int tb = T - 1; tb >= 0 && sw.r < std::min(R, T); --tb)
+            if (!((cur_group >> tb) & 1)) {
+                sw.gbit[sw.r++] = tb;
+                cur_group |= 1ull << tb;
+            }
+        std::sort(sw.gbit, sw.gbit + sw.r);
+        // micro ops reference group indices: remap after sorting
+        sw.op_end = tp.n_micro;
+        choose_item_bits(tp, sw);
+        open = -1;
+        cur_group = 0;
+    }
+    void add(const FOp &f, const DiagPlan *dp) {
+        switch (f.kind) {
+            case F_U1: case F_U2: case F_QFT: {
+                uint64_t need = 0;
+                int ta = tile_local(tp, f.kind == F_QFT ? f.p : f.t0);
+                need |= 1ull << ta;
+                int tb2 = -1;
+                if (f.kind == F_U2) {
+                    tb2 = tile_local(tp, f.t1);
+                    need |= 1ull << tb2;
+                }
+                need_bits(need);
+                MicroOp mo;
+                std::memset(&mo, 0, sizeof mo);
+                mo.a = ta;   // tile-local for now; converted to group index at finalize
+                mo.b = tb2;
+                mo.cmask = f.cmask;
+                mo.cval = f.cval;
+                mo.cst = (int)cst.size();
+                if (f.kind == F_U1) {
+                    bool h = f.cmask == 0 && f.m[0] == cd(kSqrtHalf, 0) && f.m[1] == cd(kSqrtHalf, 0) &&
+                             f.m[2] == cd(kSqrtHalf, 0) && f.m[3] == cd(-kSqrtHalf, 0);
+                    mo.kind = h ? MK_H : MK_U1;
+                    if (!h)
+                        for (int e = 0; e < 4; ++e) {
+                            float2 v;
+                            v.x = (float)f.m[e].real();
+                            v.y = (float)f.m[e].imag();
+                            cst.push_back(v);
+                        }
+                } else if (f.kind == F_U2) {
+                    mo.kind = MK_U2;
+                    for (int e = 0; e < 16; ++e) {
+                        float2 v;
+                        v.x = (float)f.m[e].real();
+                        v.y = (float)f.m[e].imag();
+                        cst.push_back(v);
+                    }
+                } else {
+                    mo.kind = MK_QFT;
+                    mo.p = f.p;
+                    mo.lo = f.lo;
+                    hp.uses_roots = 1;
+                    // group twiddle table filled at finalize (needs final group)
+                    for (int e = 0; e < (1 << R); ++e) cst.push_back(float2{1.f, 0.f});
+                }
+                tp.micro[tp.n_micro++] = mo;
+                tp.sweeps[open].op_end = tp.n_micro;
+                break;
+            }
+            case F_DIAG: {
+                if (open < 0) need_bits(0);
+                for (size_t k = 0; k < dp->descs.size(); ++k) {
+                    DiagDesc dd = dp->descs[k];
+                    int base = (int)cst.size();
+                    for (int s = 0; s < dd.n_slices; ++s) dd.slice_off[s] += base;
+                    for (int g = 0; g < dd.n_groups; ++g) dd.grp_off[g] += base;
+                    cst.insert(cst.end(), dp->tables[k].begin(), dp->tables[k].end());
+                    int di = count_diags++;
+                    tp.diags[di] = dd;
+                    MicroOp mo;
+                    std::memset(&mo, 0, sizeof mo);
+                    mo.kind = MK_DIAG;
+                    mo.cst = di;
+                    tp.micro[tp.n_micro++] = mo;
+                }
+                tp.sweeps[open].op_end = tp.n_micro;
+                break;
+            }
+            default: break;
+        }
+    }
+    int count_diags = 0;
+    void finalize() {
+        close_sweep();
+        // convert tile-local bit references to group indices and fill QFT tables
+        for (int s = 0; s < tp.n_sweeps; ++s) {
+            Sweep &sw = tp.sweeps[s];
+            for (int i = sw.op_begin; i < sw.op_end; ++i) {
+                MicroOp &mo = tp.micro[i];
+                if (mo.kind == MK_DIAG) continue;
+                int ga = -1, gb = -1;
+                for (int j = 0; j < sw.r; ++j) {
+                    if (sw.gbit[j] == mo.a) ga = j;
+                    if (mo.kind == MK_U2 && sw.gbit[j] == mo.b) gb = j;
+                }
+                mo.a = ga;
+                if (mo.kind == MK_U2) mo.b = gb;
+                if (mo.kind == MK_QFT) {
+                    uint64_t M = (mo.p > mo.lo) ? (((1ull << mo.p) - 1) & ~((1ull << mo.lo) - 1)) : 0;
+                    for (int jj = 0; jj < (1 << R); ++jj) {
+                        uint64_t u = 0;
+                        for (int m = 0; m < sw.r; ++m)
+                            if ((jj >> m) & 1) u |= glob_of_local(tp, sw.gbit[m]);
+                        u &= M;
+                        double ph = kPi * std::ldexp((double)u, -mo.p);
+                        cst[mo.cst + jj] = cexp_f(ph);
+                    }
+                }
+            }
+        }
+        tp.n_const = (int)cst.size();
+    }
+};
+}  // namespace
+
+static void build_perm_or_gather(int n, const FOp &f, HostPass &hp) {
+    bool perm = true;
+    for (int i = 0; i < n; ++i)
+        if (popc64(f.rows[i]) != 1) perm = false;
+    if (perm) {
+        hp.type = HostPass::PERM;
+        std::memset(&hp.perm, 0, sizeof hp.perm);
+        hp.perm.n = n;
+        hp.perm.L = std::min(5, n);
+        for (int i = 0; i < n; ++i) hp.perm.out_pos[__builtin_ctzll(f.rows[i])] = i;
+        hp.perm.xor_mask = f.c;
+        return;
+    }
+    // inverse of the forward matrix over GF(2): columns of M^-1 via Gauss-Jordan
+    hp.type = HostPass::GATHER;
+    std::memset(&hp.gather, 0, sizeof hp.gather);
+    hp.gather.n = n;
+    std::vector<uint64_t> A(f.rows.begin(), f.rows.end());   // row i: coefficients of x
+    std::vector<uint64_t> Inv(n);
+    for (int i = 0; i < n; ++i) Inv[i] = 1ull << i;
+    for (int col = 0; col < n; ++col) {
+        int piv = -1;
+        for (int r = col; r < n; ++r)
+            if ((A[r] >> col) & 1) {
+                piv = r;
+                break;
+            }
+        std::swap(A[col], A[piv]);
+        std::swap(Inv[col], Inv[piv]);
+        for (int r = 0; r < n; ++r)
+            if (r != col && ((A[r] >> col) & 1)) {
+                A[r] ^= A[col];
+                Inv[r] ^= Inv[col];
+            }
+    }
+    // Inv rows: x_i = parity(Inv[i] & (y ^ c)); column j of M^-1 = bits i with Inv[i] bit j
+    auto apply_inv = [&](uint64_t v) {
+        uint64_t x = 0;
+        for (int i = 0; i < n; ++i)
+            if (popc64(Inv[i] & v) & 1) x |= 1ull << i;
+        return x;
+    };
+    hp.gather.c = apply_inv(f.c);
+    hp.gather.n_slices = (n + 7) / 8;
+    for (int k = 0; k < hp.gather.n_slices; ++k)
+        for (int bte = 0; bte < 256; ++bte) {
+            uint64_t v = (uint64_t)bte << (8 * k);
+            if (8 * k + 8 > n) v &= (n >= 64 ? ~0ull : ((1ull << n) - 1));
+            hp.gather.tab[k][bte] = apply_inv(v);
+        }
+}
+
+qs_status build_fused_plan(int n, const std::vector<RGate> &gates, const qs_opts &o, Plan &plan,
+                           std::string &err) {
+    plan = Plan();
+    plan.n = n;
+    plan.mode = QS_MODE_FUSED;
+    plan.n_gates = (int)gates.size();
+    std::vector<FOp> ops;
+    detect(n, gates, ops);
+
+    int T = o.tile_qubits > 0 ? o.tile_qubits : 13;
+    int L = o.low_qubits > 0 ? o.low_qubits : 4;
+    if (T > 13) T = 13;   // two 2^13-amplitude buffers fill the 227 KB of shared memory
+    if (T > n) T = n;
+    if (L > T) L = T;
+    if (L < 1) L = 1;
+    const int R = std::min(kMaxGroup, T);
+
+    // split oversized diagonals; pre-plan each diagonal's tables
+    std::vector<FOp> ops2;
+    for (auto &f : ops) {
+        if (f.kind != F_DIAG) {
+            ops2.push_back(f);
+            continue;
+        }
+        DiagPlan dp;
+        plan_diag(n, f.diag, dp);
+        if ((int)dp.descs.size() <= kMaxDiag && (int)diag_const_size(dp) <= kMaxConst / 2) {
+            ops2.push_back(f);
+            continue;
+        }
+        // split pairs into chunks (diagonal factors commute)
+        FOp base = f;
+        base.diag.pairs.clear();
+        std::vector<std::pair<std::pair<int, int>, double>> prs(f.diag.pairs.begin(), f.diag.pairs.end());
+        const size_t chunk = 16;
+        ops2.push_back(base);
+        for (size_t i = 0; i < prs.size(); i += chunk) {
+            FOp g;
+            g.kind = F_DIAG;
+            g.n_gates = 0;
+            for (size_t k = i; k < std::min(prs.size(), i + chunk); ++k) g.diag.pairs[prs[k].first] = prs[k].second;
+            ops2.push_back(g);
+        }
+    }
+    ops.swap(ops2);
+    std::vector<DiagPlan> dplans(ops.size());
+    for (size_t i = 0; i < ops.size(); ++i)
+        if (ops[i].kind == F_DIAG) plan_diag(n, ops[i].diag, dplans[i]);
+
+    std::vector<int> rem(ops.size());
+    for (size_t i = 0; i < ops.size(); ++i) rem[i] = (int)i;
+    const uint64_t lowmask = (L >= 64) ? ~0ull : ((1ull << L) - 1);
+    const int kLookahead = 4096, kMaxDeferred = 96;
+
+    while (!rem.empty()) {
+        const FOp &f0 = ops[rem[0]];
+        if (f0.kind == F_GF2) {
+            HostPass hp;
+            build_perm_or_gather(n, f0, hp);
+            hp.note = hp.type == HostPass::PERM ? "perm" : "gather";
+            plan.passes.push_back(hp);
+            rem.erase(rem.begin());
+            continue;
+        }
+        uint64_t S = lowmask;
+        int slots = T - L;
+        std::vector<int> taken, deferred;
+        size_t j = 0;
+        int c_const = 0, c_micro = 0, c_diag = 0;
+        int sim_sweeps = 0;          // mirrors PassBuilder::need_bits grouping
+        uint64_t sim_group = 0;
+        bool sim_open = false;
+        for (; j < rem.size() && (int)j < kLookahead; ++j) {
+            const FOp &f = ops[rem[j]];
+            if (f.kind == F_GF2) break;
+            bool ok = true;
+            for (int d : deferred)
+                if (!commute(f, ops[d])) {
+                    ok = false;
+                    break;
+                }
+            if (ok) {
+                uint64_t need = f.N() & ~S;
+                OpCost c = op_cost(n, f, R, f.kind == F_DIAG ? &dplans[rem[j]] : nullptr);
+                uint64_t nb = f.N();
+                int ns = sim_sweeps;
+                uint64_t ng = sim_group;
+                bool no = sim_open;
+                if (nb) {
+                    if (no && popc64(ng | nb) <= R) {
+                        ng |= nb;
+                    } else {
+                        ns++;
+                        ng = nb;
+                        no = true;
+                    }
+                } else if (!no) {
+                    ns++;
+                    ng = 0;
+                    no = true;
+                }
+                bool fits = popc64(need) <= slots - (popc64(S) - L) && c_const + c.n_const <= kMaxConst &&
+                            c_micro + c.n_micro <= kMaxMicro - 8 && c_diag + c.n_diag <= kMaxDiag &&
+                            ns <= kMaxSweeps - 1;
+                if (fits) {
+                    sim_sweeps = ns;
+                    sim_group = ng;
+                    sim_open = no;
+                    S |= need;
+                    c_const += c.n_const;
+                    c_micro += c.n_micro;
+                    c_diag += c.n_diag;
+                    taken.push_back(rem[j]);
+                    continue;
+                }
+            }
+            deferred.push_back(rem[j]);
+            if ((int)deferred.size() >= kMaxDeferred) {
+                ++j;
+                break;
+            }
+        }
+        if (taken.empty()) {
+            err = "scheduler could not place an op (internal)";
+            return QS_ERR_INTERNAL;
+        }
+        // pad the tile to T bits with the lowest unused high bits
+        for (int b = L; b < n && popc64(S) < T; ++b) S |= 1ull << b;
+        PassBuilder pb(n, L, T, R, S);
+        for (int id : taken) {
+            pb.add(ops[id], ops[id].kind == F_DIAG ? &dplans[id] : nullptr);
+            if (pb.tp.n_sweeps >= kMaxSweeps - 1) break;   // guarded by taken limit
+        }
+        pb.finalize();
+        pb.hp.note = "tile";
+        plan.passes.push_back(pb.hp);
+        std::vector<int> nrem(deferred);
+        nrem.insert(nrem.end(), rem.begin() + j, rem.end());
+        rem.swap(nrem);
+    }
+    return QS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// per-gate plan: the structured pure path (Sec. 3.2.2; Sec. 4.1 dispatch)
+// ---------------------------------------------------------------------------
+qs_status build_pergate_plan(int n, const std::vector<RGate> &gates, Plan &plan, std::string &err) {
+    (void)err;
+    plan = Plan();
+    plan.n = n;
+    plan.mode = QS_MODE_PERGATE;
+    plan.n_gates = (int)gates.size();
+    for (const RGate &g : gates) {
+        PgOp op;
+        std::memset(&op, 0, sizeof op);
+        auto setm = [&](const cd *M, int cnt) {
+            for (int e = 0; e < cnt; ++e) {
+                op.m[e].x = (float)M[e].real();
+                op.m[e].y = (float)M[e].imag();
+            }
+        };
+        cd M[64];
+        gate_matrix(g, M);
+        double ph[4];
+        switch (g.kind) {
+            case QS_I:
+                continue;
+            case QS_Z: case QS_S: case QS_SDG: case QS_T: case QS_TDG: case QS_P:
+                op.kind = PG_PHASE;   // touch only the bit = 1 half
+                op.t0 = g.b[0];
+                op.cmask = op.cval = 1ull << g.b[0];
+                op.nbits_phase = 0;
+                diag_phases(g, ph);
+                op.m[0] = cexp_f(ph[1]);
+                break;
+            case QS_RZ:
+                op.kind = PG_PHASE;
+                op.t0 = g.b[0];
+                op.nbits_phase = 1;
+                diag_phases(g, ph);
+                op.m[0] = cexp_f(ph[0]);
+                op.m[1] = cexp_f(ph[1]);
+                break;
+            case QS_CZ: case QS_CP:
+                op.kind = PG_PHASE;   // only the |11> quarter
+                op.cmask = op.cval = (1ull << g.b[0]) | (1ull << g.b[1]);
+                op.nbits_phase = 0;
+                diag_phases(g, ph);
+                op.m[0] = cexp_f(ph[3]);
+                break;
+            case QS_CRZ:
+                op.kind = PG_PHASE;   // control = 1 half, phase by target
+                op.t0 = g.b[1];
+                op.cmask = op.cval = 1ull << g.b[0];
+                op.nbits_phase = 1;
+                diag_phases(g, ph);
+                op.m[0] = cexp_f(ph[2]);
+                op.m[1] = cexp_f(ph[3]);
+                break;
+            case QS_RZZ:
+                op.kind = PG_PHASE;
+                op.t0 = g.b[0];
+                op.t1 = g.b[1];
+                op.nbits_phase = 2;
+                diag_phases(g, ph);
+                // table index = bit t0 | bit t1 << 1; ph index = x_w0*2 + x_w1
+                op.m[0] = cexp_f(ph[0]);
+                op.m[1] = cexp_f(ph[2]);
+                op.m[2] = cexp_f(ph[1]);
+                op.m[3] = cexp_f(ph[3]);
+                break;
+            case QS_CX: case QS_CY: case QS_CH: case QS_CRX: case QS_CRY: {
+                op.kind = PG_U1;   // masked half-state update
+                op.t0 = g.b[1];
+                op.cmask = op.cval = 1ull << g.b[0];
+                cd U[4] = {M[10], M[11], M[14], M[15]};
+                setm(U, 4);
+                break;
+            }
+            case QS_CCX: {
+                op.kind = PG_U1;
+                op.t0 = g.b[2];
+                op.cmask = op.cval = (1ull << g.b[0]) | (1ull << g.b[1]);
+                cd U[4] = {0, 1, 1, 0};
+                setm(U, 4);
+                break;
+            }
+            case QS_SWAP:
+                op.kind = PG_SWAP;
+                op.t0 = g.b[0];
+                op.t1 = g.b[1];
+                break;
+            case QS_CSWAP:
+                op.kind = PG_SWAP;
+                op.t0 = g.b[1];
+                op.t1 = g.b[2];
+                op.cmask = op.cval = 1ull << g.b[0];
+                break;
+            case QS_ISWAP: case QS_RXX: case QS_RYY:
+                op.kind = PG_U2;
+                op.t0 = g.b[0];
+                op.t1 = g.b[1];
+                setm(M, 16);
+                break;
+            default:   // remaining 1q kinds: general 2x2
+                op.kind = PG_U1;
+                op.t0 = g.b[0];
+                setm(M, 4);
+        }
+        plan.pg.push_back(op);
+    }
+    return QS_OK;
+}
+
+int Plan::hbm_passes() const {
+    if (mode == QS_MODE_PERGATE) return (int)pg.size();
+    return (int)passes.size();
+}
+
+std::string Plan::describe() const {
+    std::ostringstream os;
+    if (mode == QS_MODE_PERGATE) {
+        os << "PERGATE n=" << n << " gates=" << n_gates << " launches=" << pg.size() << "\n";
+        return os.str();
+    }
+    os << "FUSED n=" << n << " gates=" << n_gates << " passes=" << passes.size() << "\n";
+    for (size_t i = 0; i < passes.size(); ++i) {
+        const HostPass &hp = passes[i];
+        if (hp.type == HostPass::TILE) {
+            const TilePass &t = hp.tile;
+            int cnt[5] = {0, 0, 0, 0, 0};
+            for (int k = 0; k < t.n_micro; ++k) cnt[t.micro[k].kind]++;
+            os << "TILE T=" << t.T << " L=" << t.L << " hb=[";
+            for (int k = 0; k < t.H; ++k) os << (k ? "," : "") << t.hb[k];
+            os << "] sweeps=" << t.n_sweeps << " U1=" << cnt[MK_U1] + cnt[MK_H] << " U2=" << cnt[MK_U2]
+               << " DIAG=" << cnt[MK_DIAG] << " QFT=" << cnt[MK_QFT] << " consts=" << t.n_const << "\n";
+        } else if (hp.type == HostPass::PERM) {
+            os << "PERM xor=" << hp.perm.xor_mask << "\n";
+        } else {
+            os << "GATHER\n";
+        }
+    }
+    return os.str();
+}
+
+}  // namespace qs

@@ -1,0 +1,146 @@
+"""CPU tests of the C-ABI library: it loads, exports every symbol include/qs.h
+declares, validates arguments without touching a GPU, and its fusion detector
+produces the expected pass structure (Sec. 5.1-5.2 pass-count arguments;
+App. A H-layer accounting)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def qs():
+    from paper_2609_19147_gb300 import build_lib
+    build_lib.build()
+    import paper_2609_19147_gb300 as m
+    return m
+
+
+def _header_functions():
+    src = open(os.path.join(ROOT, "include", "qs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qs_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(qs):
+    import ctypes
+    lib = ctypes.CDLL(qs.LIB_PATH)
+    declared = _header_functions()
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(declared) == set(qs.EXPORTED)
+
+
+def test_version_and_no_error(qs):
+    assert "sm_103a" in qs.version()
+
+
+def _status(qs, n, gates):
+    try:
+        qs.plan_describe(n, gates)
+        return qs.QS_OK
+    except qs.QsError as e:
+        return e.status
+
+
+def test_validation_rejects_bad_gates(qs):
+    assert _status(qs, 4, [W.Gate("CX", (1, 1))]) == qs.QS_ERR_INVALID_ARG      # duplicate wire
+    assert _status(qs, 4, [W.Gate("H", (4,))]) == qs.QS_ERR_INVALID_ARG         # out of range
+    assert _status(qs, 4, [W.Gate("H", (-1,))]) == qs.QS_ERR_INVALID_ARG
+    assert _status(qs, 40, [W.Gate("H", (0,))]) == qs.QS_ERR_UNSUPPORTED        # n > 33
+    g = qs.CGates([W.Gate("H", (0,))])
+    g.arr[0].nw = 2                                                              # wrong arity
+    assert _status(qs, 4, g) == qs.QS_ERR_INVALID_ARG
+    g = qs.CGates([W.Gate("H", (0,))])
+    g.arr[0].kind = 999
+    assert _status(qs, 4, g) == qs.QS_ERR_INVALID_ARG
+    g = qs.CGates([W.Gate("U", (0,), (), np.eye(2))])
+    g.arr[0].dense = None
+    assert _status(qs, 4, g) == qs.QS_ERR_INVALID_ARG
+    g = qs.CGates([W.Gate("RX", (0,), (np.nan,))])
+    assert _status(qs, 4, g) == qs.QS_ERR_INVALID_ARG
+    # parameter index without a parameter vector
+    assert _status(qs, 4, [W.Gate("RX", (0,), (0.0,), None, 0)]) == qs.QS_ERR_INVALID_ARG
+
+
+def _passes(qs, n, gates, **kw):
+    return qs.plan_describe(n, gates, **kw)
+
+
+def test_qft_stages_fuse_into_few_passes(qs):
+    # every stage (H + its CP ladder) is recognised: 30 stages -> 3 tile passes
+    # plus one permutation pass for the final swaps (bit reversal)
+    text, p = _passes(qs, 30, W.qft_gates(30, swaps=True))
+    assert p == 4
+    assert text.count("QFT=") == 3 and "PERM" in text
+    assert sum(int(x) for x in re.findall(r"QFT=(\d+)", text)) == 29   # last stage has no ladder
+    text, p = _passes(qs, 30, W.qft_gates(30, swaps=False))
+    assert p == 3 and "PERM" not in text
+    _, p = _passes(qs, 30, W.qft_gates(30, swaps=True), mode="pergate")
+    assert p == 480
+
+
+def test_h_layer_pass_count_app_a(qs):
+    # App. A: radix-4 Walsh takes ceil(25/4) = 7 passes; tiles of 13 qubits take 3
+    text, p = _passes(qs, 25, W.wht_gates(25))
+    assert p == 3
+    _, p = _passes(qs, 25, W.wht_gates(25), tile_qubits=6, low_qubits=2)
+    assert p == 6
+
+
+def test_gf2_runs_become_one_pass(qs):
+    text, p = _passes(qs, 24, W.cnot_ladder(24))
+    assert p == 1 and "GATHER" in text
+    # SWAP run -> permutation pass
+    text, p = _passes(qs, 24, [W.Gate("SWAP", (i, 23 - i)) for i in range(12)])
+    assert p == 1 and "PERM" in text
+    # GHZ: H then one gather for the 23-gate CNOT chain (Sec. 5.1: 24-gate chain -> one pass)
+    text, p = _passes(qs, 24, W.ghz_gates(24))
+    assert p == 2 and "GATHER" in text
+
+
+def test_diagonal_runs_fuse(qs):
+    rng = np.random.default_rng(0)
+    gl = [W.Gate("RZZ", (b, b + 1), (float(rng.uniform(0, 6.28)),)) for b in range(27)]
+    text, p = _passes(qs, 28, gl)
+    assert p == 1 and "DIAG=1" in text
+    # the paper's long-range Ising layer: 300 all-to-all bonds at 25 qubits, one pass
+    gl = [W.Gate("RZZ", (i, j), (0.1 / (j - i),)) for i in range(25) for j in range(i + 1, 25)]
+    assert len(gl) == 300
+    _, p = _passes(qs, 25, gl)
+    assert p == 1
+
+
+def test_identity_windows_vanish_and_small_angles_survive(qs):
+    # H H and X X cancel symbolically (Sec. 5.2 exact collapse); RZ(1e-6) is kept (rtol = 0)
+    text, p = _passes(qs, 10, [W.Gate("H", (3,)), W.Gate("H", (3,)), W.Gate("X", (2,)), W.Gate("X", (2,))])
+    assert p == 0
+    text, p = _passes(qs, 10, [W.Gate("RZ", (3,), (1e-6,))])
+    assert p == 1 and "DIAG=1" in text
+
+
+def test_no_cross_family_merge_for_ladder_heisenberg(qs):
+    # interleaved XX / YY / ZZ on the same bonds must keep their order: the
+    # detector may not reorder non-commuting terms (Sec. 5.2, App. B ladder)
+    n = 8
+    gl = []
+    for b in range(n - 1):
+        gl += [W.Gate("RXX", (b, b + 1), (0.3,)), W.Gate("RYY", (b, b + 1), (0.3,)),
+               W.Gate("RZZ", (b, b + 1), (0.3,))]
+    text, p = _passes(qs, n, gl)
+    assert p >= 1   # correctness of the order is checked on the GPU against the oracle
+
+
+def test_tfim_trotter_steps_pack(qs):
+    h = W.tfim_fields(30, 3)
+    gl = W.tfim_gates(30, 10, 0.05, 1.0, h, order=2)
+    _, p = _passes(qs, 30, gl)
+    _, pg = _passes(qs, 30, gl, mode="pergate")
+    assert pg == len(gl) == 10 * (29 * 2 + 30)
+    assert p <= 3 * 10          # <= 3 HBM passes per Strang step

@@ -1,0 +1,280 @@
+"""GPU parity: the CUDA path (through the C ABI) against the complex128 oracle.
+
+Tolerances (from the stated target and the paper's parity budgets, Sec. 5.3
+and Sec. 6.2): max |d amplitude| <= 2e-5, fidelity >= 1 - 1e-6, relative L2
+<= 1e-5 (<= 1e-4 for the 100-step TFIM run, where ~10^4 complex64 roundings
+accumulate); permutation layers bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2609_19147_gb300 as qs  # noqa: E402
+
+
+def _metrics(got, ref):
+    got = np.asarray(got, dtype=np.complex128)
+    d = np.max(np.abs(got - ref))
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    fid = abs(np.vdot(ref, got)) ** 2 / (np.vdot(got, got).real * np.vdot(ref, ref).real)
+    return d, rel, fid
+
+
+def _run(n, gates, psi0=None, mode="fused", **kw):
+    st = qs.State(n)
+    if psi0 is not None:
+        st.set(psi0.astype(np.complex64))
+    st.apply(gates, mode=mode, **kw)
+    out = st.get()[0]
+    st.close()
+    return out
+
+
+def _ref(n, gates, psi0=None):
+    p = None if psi0 is None else psi0.astype(np.complex64).astype(np.complex128)
+    return oracle.simulate(n, gates, p)
+
+
+def _assert_close(got, ref, tol_rel=1e-5):
+    d, rel, fid = _metrics(got, ref)
+    assert d <= 2e-5, d
+    assert rel <= tol_rel, rel
+    assert fid >= 1 - 1e-6, fid
+
+
+@pytest.mark.parametrize("mode", ["fused", "pergate"])
+def test_qft12_random_state(mode):
+    n = 12
+    psi0 = W.random_state(n, 1)
+    gl = W.qft_gates(n, swaps=True)
+    _assert_close(_run(n, gl, psi0, mode), _ref(n, gl, psi0))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 9, 12, 13, 14, 17])
+@pytest.mark.parametrize("mode", ["fused", "pergate"])
+def test_random_circuits_all_kinds(n, mode):
+    gl = W.random_circuit(n, 150, 1000 + n)
+    psi0 = W.random_state(n, 2000 + n)
+    _assert_close(_run(n, gl, psi0, mode), _ref(n, gl, psi0))
+
+
+@pytest.mark.parametrize("tq,lq", [(13, 4), (12, 5), (10, 3), (8, 2), (13, 6)])
+def test_tile_shapes(tq, lq):
+    n = 18
+    gl = W.random_circuit(n, 200, 77, kinds=["H", "RX", "U", "CX", "CZ", "RZZ", "SWAP", "CP", "RY", "CCX"])
+    psi0 = W.random_state(n, 78)
+    _assert_close(_run(n, gl, psi0, tile_qubits=tq, low_qubits=lq), _ref(n, gl, psi0))
+
+
+@pytest.mark.parametrize("n", [16, 20])
+def test_haar_layers(n):
+    gl = []
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        gl += [W.Gate("U", (q,), (), W.haar_u2(rng)) for q in range(n)]
+    psi0 = W.random_state(n, 6)
+    _assert_close(_run(n, gl, psi0), _ref(n, gl, psi0))
+
+
+@pytest.mark.parametrize("n", [10, 19, 21])
+def test_qft_random_state(n):
+    psi0 = W.random_state(n, 40 + n)
+    gl = W.qft_gates(n, swaps=True)
+    _assert_close(_run(n, gl, psi0), _ref(n, gl, psi0))
+    gl2 = W.qft_gates(n, swaps=False)
+    _assert_close(_run(n, gl2, psi0), _ref(n, gl2, psi0))
+
+
+@pytest.mark.parametrize("n", [6, 15, 22])
+def test_permutation_layers_bit_exact(n):
+    psi0 = W.random_state(n, 9).astype(np.complex64)
+    y = np.arange(1 << n)
+    # ascending CNOT ladder: out[y] = in[y ^ (y >> 1)], exact copy of amplitudes
+    got = _run(n, W.cnot_ladder(n), psi0)
+    assert np.array_equal(got, psi0[y ^ (y >> 1)])
+    # SWAP / X run (bit permutation + xor): compare with the oracle on the widened input
+    rng = np.random.default_rng(n)
+    gl = []
+    for _ in range(3 * n):
+        a, b = rng.choice(n, 2, replace=False)
+        gl.append(W.Gate("SWAP", (int(a), int(b))))
+        gl.append(W.Gate("X", (int(rng.integers(n)),)))
+    ref = oracle.simulate(n, gl, psi0.astype(np.complex128)).astype(np.complex64)
+    assert np.array_equal(_run(n, gl, psi0), ref)
+    # mixed X / CNOT / SWAP run through the general gather
+    gl = []
+    for _ in range(2 * n):
+        a, b = (int(v) for v in rng.choice(n, 2, replace=False))
+        gl.append(W.Gate("CX", (a, b)))
+        gl.append(W.Gate("X", (b,)))
+    ref = oracle.simulate(n, gl, psi0.astype(np.complex128)).astype(np.complex64)
+    assert np.array_equal(_run(n, gl, psi0), ref)
+    assert np.array_equal(_run(n, gl, psi0, mode="pergate"), ref)
+
+
+def test_ghz_and_wht():
+    n = 20
+    got = _run(n, W.ghz_gates(n))
+    assert abs(got[0] - 2 ** -0.5) < 1e-7 and abs(got[-1] - 2 ** -0.5) < 1e-7
+    assert np.count_nonzero(got) == 2
+    psi0 = W.random_state(n, 3)
+    _assert_close(_run(n, W.wht_gates(n) + W.wht_gates(n), psi0), psi0.astype(np.complex64).astype(complex))
+
+
+@pytest.mark.parametrize("n", [12, 20])
+def test_random_zz_and_long_range_diagonals(n):
+    rng = np.random.default_rng(n)
+    gl = [W.Gate("RZZ", (b, b + 1), (float(rng.uniform(0, 2 * np.pi)),)) for b in range(n - 1)]
+    # all-distinct-angle all-to-all layer (Sec. 6.2 worst case)
+    gl += [W.Gate("RZZ", (i, j), (float(rng.uniform(0, 2 * np.pi)),)) for i in range(n) for j in range(i + 1, n)]
+    gl += [W.Gate("CP", (i, j), (float(rng.uniform(0, 2 * np.pi)),)) for i in range(0, n, 3) for j in range(1, n, 4) if i != j]
+    gl += [W.Gate(k, (int(q),), (float(rng.uniform(0, 6)),) if k in ("RZ", "P") else ())
+           for k, q in zip(["RZ", "P", "S", "T", "Z", "SDG"] * 3, rng.integers(0, n, 18))]
+    psi0 = W.random_state(n, 8)
+    _assert_close(_run(n, gl, psi0), _ref(n, gl, psi0))
+
+
+def test_suite_layers_n18():
+    n = 18
+    gl = W.suite28_gates(n, 3, 2, tail=True)
+    psi0 = W.random_state(n, 12)
+    _assert_close(_run(n, gl, psi0), _ref(n, gl, psi0))
+
+
+def test_tfim_second_order_n20():
+    # config-3 parity size: 100 Strang steps, dt = 0.05, h_i ~ U[0.5, 1.5] (seed 3)
+    n = 20
+    gl = W.tfim_gates(n, 100, 0.05, 1.0, W.tfim_fields(n, 3), order=2)
+    ref = _ref(n, gl)
+    for mode in ("fused", "pergate"):
+        got = _run(n, gl, mode=mode)
+        d, rel, fid = _metrics(got, ref)
+        assert d <= 2e-5 and rel <= 1e-4 and fid >= 1 - 1e-6, (mode, d, rel, fid)
+
+
+def test_heisenberg_ladder_order_preserved():
+    n = 10
+    gl = []
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        for b in range(n - 1):
+            t = float(rng.uniform(0, 1))
+            gl += [W.Gate("RXX", (b, b + 1), (t,)), W.Gate("RYY", (b, b + 1), (t,)), W.Gate("RZZ", (b, b + 1), (t,))]
+    psi0 = W.random_state(n, 4)
+    _assert_close(_run(n, gl, psi0), _ref(n, gl, psi0))
+
+
+def test_small_angle_not_dropped():
+    n = 4
+    psi0 = W.random_state(n, 5)
+    gl = [W.Gate("RZ", (1,), (1e-6,)), W.Gate("H", (2,)), W.Gate("RZ", (2,), (1e-6,)), W.Gate("H", (2,))]
+    got = _run(n, gl, psi0)
+    ref = _ref(n, gl, psi0)
+    _assert_close(got, ref)
+
+
+def test_batched_states_and_params():
+    n, L, B = 8, 2, 3
+    gl = W.vqe_ansatz_gates(n, L)
+    theta = W.vqe_params(n, L, B, 6)
+    st = qs.State(n, batch=B)
+    st.apply(gl, params=theta)
+    got = st.get()
+    st.close()
+    for b in range(B):
+        _assert_close(got[b], oracle.simulate(n, gl, theta=theta[b]))
+
+
+def test_expectation_values():
+    n, B = 14, 2
+    psis = [W.random_state(n, 30 + b) for b in range(B)]
+    st = qs.State(n, batch=B)
+    st.set(np.stack(psis).astype(np.complex64))
+    rng = np.random.default_rng(4)
+    terms = W.tfim_paulis(n, 1.0, 0.7) + [(float(rng.normal()), int(rng.integers(1 << n)), int(rng.integers(1 << n)))
+                                          for _ in range(20)]
+    got = st.expect(terms)
+    st.close()
+    for b in range(B):
+        ref = oracle.expect(psis[b].astype(np.complex64).astype(complex), n, terms)
+        assert abs(got[b] - ref) < 1e-5 * max(1.0, sum(abs(t[0]) for t in terms)) / 10
+
+
+def test_adjoint_gradient_matches_parameter_shift():
+    n, L, B = 6, 2, 2
+    gl = W.vqe_ansatz_gates(n, L)
+    theta = W.vqe_params(n, L, B, 6)
+    terms = W.tfim_paulis(n, 1.0, 1.0)
+    st = qs.State(n, batch=B)
+    e, g = st.grad(gl, theta, terms)
+    st.close()
+    for b in range(B):
+        assert abs(e[b] - oracle.energy(n, gl, theta[b], terms)) < 1e-5
+        ps = oracle.param_shift_grad(n, gl, theta[b], terms)
+        assert np.max(np.abs(g[b] - ps)) < 2e-5, np.max(np.abs(g[b] - ps))
+
+
+def test_adjoint_gradient_rzz_and_cp():
+    n = 5
+    gl = [W.Gate("H", (q,)) for q in range(n)]
+    gl += [W.Gate("RZZ", (q, q + 1), (0.0,), None, q) for q in range(n - 1)]
+    gl += [W.Gate("CP", (0, 3), (0.0,), None, n - 1), W.Gate("RX", (2,), (0.0,), None, n)]
+    theta = np.random.default_rng(1).uniform(0, 2 * np.pi, size=(1, n + 1))
+    terms = W.tfim_paulis(n, 1.0, 0.6) + [(0.4, 0b10010, 0b00110)]
+    st = qs.State(n)
+    e, g = st.grad(gl, theta, terms)
+    st.close()
+    ps = oracle.param_shift_grad(n, gl, theta[0], terms)
+    assert np.max(np.abs(g[0] - ps)) < 2e-5
+
+
+# ---------------------------------------------------------------------------
+# full size (30 qubits, the bench's launch configuration): sampled outputs
+# ---------------------------------------------------------------------------
+def _qft_product_closed_form(us, n, k):
+    # input psi_x = prod_q u_q[x_q]; QFT output at k = prod_q (u_q[0] + u_q[1] e^{2 pi i k / 2^(q+1)}) / sqrt 2
+    out = np.ones(len(k), dtype=np.complex128)
+    for q in range(n):
+        out *= (us[q][0] + us[q][1] * np.exp(2j * np.pi * (k % (1 << (q + 1))) / (1 << (q + 1)))) / np.sqrt(2)
+    return out
+
+
+@pytest.mark.parametrize("mode", ["fused", "pergate"])
+def test_qft30_full_size_sampled(mode):
+    n = 30
+    rng = np.random.default_rng(44)
+    haar = [W.haar_u2(rng) for _ in range(n)]
+    gl = [W.Gate("U", (q,), (), haar[q]) for q in range(n)] + W.qft_gates(n, swaps=True)
+    st = qs.State(n)
+    st.apply(gl, mode=mode)
+    k = np.concatenate([np.arange(64), rng.integers(0, 1 << n, 4096), (1 << n) - 1 - np.arange(64)])
+    got = st.tensor[0, torch.from_numpy(k).cuda()].cpu().numpy().astype(np.complex128)
+    norm = float(torch.linalg.vector_norm(st.tensor[0]).item())
+    st.close()
+    ref = _qft_product_closed_form([h[:, 0] for h in haar], n, k)
+    assert np.max(np.abs(got - ref)) <= 2e-5
+    assert abs(norm - 1) < 1e-5
+
+
+def test_tfim30_full_size_properties():
+    n = 30
+    gl = W.tfim_gates(n, 4, 0.05, 1.0, W.tfim_fields(n, 3), order=2)
+    st = qs.State(n)
+    st.apply(gl)
+    a = st.tensor[0].clone()
+    st.zero()
+    st.apply(gl, mode="pergate")
+    b = st.tensor[0]
+    diff = float(torch.max(torch.abs(a - b)).item())
+    norm = float(torch.linalg.vector_norm(a).item())
+    st.close()
+    assert abs(norm - 1) < 1e-5
+    assert diff < 2e-6
