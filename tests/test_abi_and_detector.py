@@ -15,8 +15,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def qs():
-    from paper_2609_19147_gb300 import build_lib
-    build_lib.build()
+    import __graft_entry__
+    __graft_entry__._build_lib_module().build()
     import paper_2609_19147_gb300 as m
     return m
 
