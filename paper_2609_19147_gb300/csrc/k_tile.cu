@@ -1,17 +1,28 @@
 // Tile-pass engine (sm_103a).
 //
-// One launch = one full-state HBM pass.  Each persistent CTA walks its tiles:
-// a tile is 2^T amplitudes = 2^H rows of 2^L contiguous amplitudes (the L low
-// index bits) at the row offsets spanned by the pass's high bits hb[].  Rows
-// are moved HBM <-> shared memory with bulk-async copies (cp.async.bulk, the
-// TMA engine), double-buffered: the next tile's rows land while the current
-// tile is computed, and the previous tile's rows drain asynchronously.
+// One launch = one full-state HBM pass.  Each persistent CTA walks its tiles.
+// A tile is 2^T amplitudes: the L low index bits plus the pass's high bits
+// hb[].  It moves HBM <-> shared memory as ONE multi-dimensional TMA tensor
+// copy (cp.async.bulk.tensor, 128-byte swizzle): the state is described to the
+// TMA unit as a <=5-D tensor whose dims are the low bits, the contiguous runs
+// of tile bits and the gaps of non-tile bits between them (the tile selects a
+// box of extent 1 in every gap).  When the bit set needs more than 5 dims the
+// pass falls back to one bulk copy per 2^L-amplitude row.  Loads are
+// double-buffered: the next tile lands while the current one is processed and
+// the previous one drains.
+//
 // Between load and store the tile goes through "sweeps": every thread holds
-// 2^R amplitudes that differ in R tile bits and applies the sweep's micro-ops
-// in registers (2x2 / 4x4 unitaries with controls, diagonal phase tables,
-// QFT stages = Hadamard butterfly + closed-form ladder twiddle, Sec. 5.1).
-// All waits are bounded; on expiry the kernel records QS_ERR_TIMEOUT, drains
-// its own copies and returns.
+// 2^R amplitudes that differ in R tile bits (registers) and applies the
+// sweep's micro-ops: 2x2 / 4x4 unitaries with controls, diagonal phase tables
+// (factored into an item part and a group part), and QFT stages (Hadamard
+// butterfly + closed-form ladder twiddle; Sec. 5.1).  Butterfly
+// normalisations are folded into one scale per sweep.  Shared-memory offsets
+// are XOR-linear in the tile bits, which covers the swizzled layout.
+//
+// All waits are bounded; on expiry the kernel records QS_ERR_TIMEOUT, lets its
+// own copies land and returns.
+#include <cuda.h>
+
 #include "qs_internal.h"
 #include "qs_kernels.h"
 
@@ -67,6 +78,21 @@ __device__ __forceinline__ void bulk_s2g(void *dst_gmem, const void *src_smem, u
                  "r"(smem_u32(src_smem)), "r"(bytes)
                  : "memory");
 }
+__device__ __forceinline__ void tma_load_5d(void *dst_smem, const CUtensorMap *tm, const int c[5], uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst_smem)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap *tm, const int c[5], const void *src_smem) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5, %6}], [%1];" ::"l"(
+            reinterpret_cast<uint64_t>(tm)),
+        "r"(smem_u32(src_smem)), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4])
+        : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read0() {
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
@@ -100,21 +126,17 @@ __device__ __forceinline__ float2 twiddle(uint64_t u, int p, const float2 *roots
     return w;
 }
 
-__device__ __forceinline__ float2 diag_phase(const DiagDesc &d, uint64_t x, const float2 *cs) {
-    float2 ph;
-    int s0 = 0;
-    if (d.n_slices > 0) {
-        ph = cs[d.slice_off[0] + (int)((x >> d.slice_lo[0]) & ((1u << d.slice_w[0]) - 1))];
-        s0 = 1;
-    } else {
-        ph = d.pad0 ? make_float2(d.gph_re, d.gph_im) : make_float2(1.f, 0.f);
-    }
-    for (int s = s0; s < d.n_slices; ++s)
-        ph = cmul(ph, cs[d.slice_off[s] + (int)((x >> d.slice_lo[s]) & ((1u << d.slice_w[s]) - 1))]);
-    for (int g = 0; g < d.n_groups; ++g) {
-        uint64_t f = d.grp_type[g] ? (x & (x >> d.grp_d[g])) : (x ^ (x >> d.grp_d[g]));
-        ph = cmul(ph, cs[d.grp_off[g] + __popcll(f & d.grp_mask[g])]);
-    }
+// product of the diagonal's slice/group factors selected by the masks
+__device__ __forceinline__ float2 diag_part(const DiagDesc &d, uint64_t x, const float2 *cs, uint32_t smask,
+                                            uint32_t gmask, float2 ph) {
+    for (int s = 0; s < d.n_slices; ++s)
+        if ((smask >> s) & 1)
+            ph = cmul(ph, cs[d.slice_off[s] + (int)((x >> d.slice_lo[s]) & ((1u << d.slice_w[s]) - 1))]);
+    for (int g = 0; g < d.n_groups; ++g)
+        if ((gmask >> g) & 1) {
+            uint64_t f = d.grp_type[g] ? (x & (x >> d.grp_d[g])) : (x ^ (x >> d.grp_d[g]));
+            ph = cmul(ph, cs[d.grp_off[g] + __popcll(f & d.grp_mask[g])]);
+        }
     return ph;
 }
 
@@ -145,41 +167,39 @@ __device__ __forceinline__ void op_u1(float2 (&a)[1 << R], const float2 *mat, ui
         float2 b0 = cmad(m01, a1, cmul(m00, a0));
         float2 b1 = cmad(m11, a1, cmul(m10, a0));
         if (cmask) {
-            bool c = (G.gidx(base, j) & cmask) == cval;
-            if (!c) {
-                b0 = a0;
-                b1 = a1;
-            }
+            const bool c = (G.gidx(base, j) & cmask) == cval;
+            b0 = c ? b0 : a0;
+            b1 = c ? b1 : a1;
         }
         a[j] = b0;
         a[k] = b1;
     }
 }
 
+// unnormalised Hadamard butterfly (the 1/sqrt 2 is folded into the sweep scale)
 template <int R, int M>
 __device__ __forceinline__ void op_h(float2 (&a)[1 << R]) {
-    const float s = 0.70710678118654752440f;
 #pragma unroll
     for (int j = 0; j < (1 << R); ++j) {
         if ((j >> M) & 1) continue;
         const int k = j | (1 << M);
-        float2 a0 = a[j], a1 = a[k];
-        a[j] = make_float2((a0.x + a1.x) * s, (a0.y + a1.y) * s);
-        a[k] = make_float2((a0.x - a1.x) * s, (a0.y - a1.y) * s);
+        const float2 a0 = a[j], a1 = a[k];
+        a[j] = make_float2(a0.x + a1.x, a0.y + a1.y);
+        a[k] = make_float2(a0.x - a1.x, a0.y - a1.y);
     }
 }
 
+// QFT stage: butterfly on bit M, then the ladder phase on the bit-M = 1 half:
+// item twiddle w times the group-bit twiddle gtab[k]
 template <int R, int M>
 __device__ __forceinline__ void op_qft(float2 (&a)[1 << R], const float2 *gtab, float2 w) {
-    const float s = 0.70710678118654752440f;
 #pragma unroll
     for (int j = 0; j < (1 << R); ++j) {
         if ((j >> M) & 1) continue;
         const int k = j | (1 << M);
-        float2 a0 = a[j], a1 = a[k];
-        a[j] = make_float2((a0.x + a1.x) * s, (a0.y + a1.y) * s);
-        float2 d = make_float2((a0.x - a1.x) * s, (a0.y - a1.y) * s);
-        a[k] = cmul(d, cmul(w, gtab[k]));
+        const float2 a0 = a[j], a1 = a[k];
+        a[j] = make_float2(a0.x + a1.x, a0.y + a1.y);
+        a[k] = cmul(make_float2(a0.x - a1.x, a0.y - a1.y), cmul(w, gtab[k]));
     }
 }
 
@@ -191,20 +211,15 @@ __device__ __forceinline__ void op_u2(float2 (&a)[1 << R], const float2 *mat, ui
         if (((j >> MA) & 1) || ((j >> MB) & 1)) continue;
         if (cmask && (G.gidx(base, j) & cmask) != cval) continue;   // control bits are never MA/MB
         const int i0 = j, i1 = j | (1 << MB), i2 = j | (1 << MA), i3 = j | (1 << MA) | (1 << MB);
-        float2 v[4] = {a[i0], a[i1], a[i2], a[i3]};
-        float2 o[4];
+        const float2 v0 = a[i0], v1 = a[i1], v2 = a[i2], v3 = a[i3];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            float2 acc = cmul(mat[r * 4 + 0], v[0]);
-            acc = cmad(mat[r * 4 + 1], v[1], acc);
-            acc = cmad(mat[r * 4 + 2], v[2], acc);
-            acc = cmad(mat[r * 4 + 3], v[3], acc);
-            o[r] = acc;
+            float2 acc = cmul(mat[r * 4 + 0], v0);
+            acc = cmad(mat[r * 4 + 1], v1, acc);
+            acc = cmad(mat[r * 4 + 2], v2, acc);
+            acc = cmad(mat[r * 4 + 3], v3, acc);
+            a[r == 0 ? i0 : r == 1 ? i1 : r == 2 ? i2 : i3] = acc;
         }
-        a[i0] = o[0];
-        a[i1] = o[1];
-        a[i2] = o[2];
-        a[i3] = o[3];
     }
 }
 
@@ -257,52 +272,97 @@ __device__ __forceinline__ void disp_u2(int ma, int mb, float2 (&a)[1 << R], con
 // one sweep over the tile in shared memory
 // ---------------------------------------------------------------------------
 struct SweepCtx {
-    int L, T, RS;
-    const int *hb;           // smem copy of pass hb
+    int T;
+    const int *contrib;      // smem: XOR offset of each tile-local bit (float2 units)
+    const int *hb;           // smem: global bit of tile-local bit L + k
+    int L;
     float2 *buf;
     const float2 *cs;
     const float2 *roots;
-    uint64_t tile_gbase;     // global index of tile-local 0
+    const MicroOp *micro;    // smem
+    const DiagDesc *diags;   // smem
+    uint64_t tile_gbase;     // global index of tile-local 0 (within the state)
 };
 
-__device__ __forceinline__ int smem_contrib(const SweepCtx &c, int tb) {
-    return tb < c.L ? (1 << tb) : (c.RS << (tb - c.L));
-}
 __device__ __forceinline__ uint64_t glob_contrib(const SweepCtx &c, int tb) {
     return tb < c.L ? (1ull << tb) : (1ull << c.hb[tb - c.L]);
 }
 
 template <int R>
-__device__ void run_sweep(const SweepCtx &c, const Sweep &S, const MicroOp *micro, const DiagDesc *diags) {
+__device__ __forceinline__ void sweep_load(const SweepCtx &c, bool vec, int saddr, const int (&gs)[R],
+                                           float2 (&a)[1 << R]) {
+    if (vec) {   // group bit 0 = tile-local bit 0: pairs are adjacent and 16-byte aligned
+#pragma unroll
+        for (int j = 0; j < (1 << R); j += 2) {
+            int o = saddr;
+#pragma unroll
+            for (int m = 1; m < R; ++m)
+                if ((j >> m) & 1) o ^= gs[m];
+            const float4 v = *reinterpret_cast<const float4 *>(c.buf + o);
+            a[j] = make_float2(v.x, v.y);
+            a[j + 1] = make_float2(v.z, v.w);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j) {
+            int o = saddr;
+#pragma unroll
+            for (int m = 0; m < R; ++m)
+                if ((j >> m) & 1) o ^= gs[m];
+            a[j] = c.buf[o];
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void sweep_store(const SweepCtx &c, bool vec, int saddr, const int (&gs)[R],
+                                            const float2 (&a)[1 << R]) {
+    if (vec) {
+#pragma unroll
+        for (int j = 0; j < (1 << R); j += 2) {
+            int o = saddr;
+#pragma unroll
+            for (int m = 1; m < R; ++m)
+                if ((j >> m) & 1) o ^= gs[m];
+            *reinterpret_cast<float4 *>(c.buf + o) = make_float4(a[j].x, a[j].y, a[j + 1].x, a[j + 1].y);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j) {
+            int o = saddr;
+#pragma unroll
+            for (int m = 0; m < R; ++m)
+                if ((j >> m) & 1) o ^= gs[m];
+            c.buf[o] = a[j];
+        }
+    }
+}
+
+template <int R>
+__device__ __noinline__ void run_sweep(const SweepCtx &c, const Sweep &S) {
     int gs[R];
     Grp<R> G;
 #pragma unroll
     for (int m = 0; m < R; ++m) {
-        gs[m] = smem_contrib(c, S.gbit[m]);
+        gs[m] = c.contrib[S.gbit[m]];
         G.gg[m] = glob_contrib(c, S.gbit[m]);
     }
     const int nb = c.T - R;
     const int n_items = 1 << nb;
+    const bool vec = S.vec != 0;
     for (int item = threadIdx.x; item < n_items; item += blockDim.x) {
         int saddr = 0;
         uint64_t gbase = c.tile_gbase;
         for (int i = 0; i < nb; ++i)
             if ((item >> i) & 1) {
                 const int tb = S.tbit[i];
-                saddr += smem_contrib(c, tb);
+                saddr ^= c.contrib[tb];
                 gbase |= glob_contrib(c, tb);
             }
         float2 a[1 << R];
-#pragma unroll
-        for (int j = 0; j < (1 << R); ++j) {
-            int o = saddr;
-#pragma unroll
-            for (int m = 0; m < R; ++m)
-                if ((j >> m) & 1) o += gs[m];
-            a[j] = c.buf[o];
-        }
+        sweep_load<R>(c, vec, saddr, gs, a);
         for (int oi = S.op_begin; oi < S.op_end; ++oi) {
-            const MicroOp &op = micro[oi];
+            const MicroOp &op = c.micro[oi];
             switch (op.kind) {
                 case MK_U1:
                     disp_u1<R>(op.a, a, c.cs + op.cst, op.cmask, op.cval, gbase, G);
@@ -320,33 +380,39 @@ __device__ void run_sweep(const SweepCtx &c, const Sweep &S, const MicroOp *micr
                     break;
                 }
                 case MK_DIAG: {
-                    const DiagDesc &d = diags[op.cst];
+                    const DiagDesc &d = c.diags[op.cst];
+                    const uint32_t dyn_s = (uint32_t)op.a, dyn_g = (uint32_t)op.b;
+                    float2 stat = d.pad0 ? make_float2(d.gph_re, d.gph_im) : make_float2(1.f, 0.f);
+                    stat = diag_part(d, gbase, c.cs, ~dyn_s, ~dyn_g, stat);
+                    if (dyn_s | dyn_g) {
 #pragma unroll
-                    for (int j = 0; j < (1 << R); ++j) a[j] = cmul(a[j], diag_phase(d, G.gidx(gbase, j), c.cs));
+                        for (int j = 0; j < (1 << R); ++j)
+                            a[j] = cmul(a[j], diag_part(d, G.gidx(gbase, j), c.cs, dyn_s, dyn_g, stat));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < (1 << R); ++j) a[j] = cmul(a[j], stat);
+                    }
                     break;
                 }
                 default:
                     break;
             }
         }
+        if (S.scale != 1.f) {
 #pragma unroll
-        for (int j = 0; j < (1 << R); ++j) {
-            int o = saddr;
-#pragma unroll
-            for (int m = 0; m < R; ++m)
-                if ((j >> m) & 1) o += gs[m];
-            c.buf[o] = a[j];
+            for (int j = 0; j < (1 << R); ++j) a[j] = make_float2(a[j].x * S.scale, a[j].y * S.scale);
         }
+        sweep_store<R>(c, vec, saddr, gs, a);
     }
 }
 
-__device__ void run_sweep_r(int r, const SweepCtx &c, const Sweep &S, const MicroOp *micro, const DiagDesc *diags) {
+__device__ void run_sweep_r(int r, const SweepCtx &c, const Sweep &S) {
     switch (r) {
-        case 5: run_sweep<5>(c, S, micro, diags); break;
-        case 4: run_sweep<4>(c, S, micro, diags); break;
-        case 3: run_sweep<3>(c, S, micro, diags); break;
-        case 2: run_sweep<2>(c, S, micro, diags); break;
-        default: run_sweep<1>(c, S, micro, diags); break;
+        case 5: run_sweep<5>(c, S); break;
+        case 4: run_sweep<4>(c, S); break;
+        case 3: run_sweep<3>(c, S); break;
+        case 2: run_sweep<2>(c, S); break;
+        default: run_sweep<1>(c, S); break;
     }
 }
 
@@ -367,24 +433,62 @@ __device__ __forceinline__ uint64_t tile_base(const TileArgs &A, long long ti) {
     return g;
 }
 
-__global__ void __launch_bounds__(kTileThreads, 1) tile_pass_kernel(const TileArgs A) {
-    extern __shared__ __align__(128) unsigned char sm[];
+__device__ __forceinline__ void tile_coords(const TmaGeom &g, long long ti, long long bi, int c[5]) {
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+        long long v = 0;
+        if (d < g.ndims) {
+            if (g.kind[d] == 1) v = (ti >> g.off[d]) & ((1ll << g.w[d]) - 1);
+            if (d == g.batch_dim) v += bi << g.w[d];
+        }
+        c[d] = (int)v;
+    }
+}
+
+__global__ void __launch_bounds__(kTileThreads, 1)
+    tile_pass_kernel(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst,
+                     const TileArgs A) {
+    extern __shared__ __align__(1024) unsigned char sm[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
     int *s_hb = reinterpret_cast<int *>(sm + 16);
+    int *s_contrib = reinterpret_cast<int *>(sm + 16 + 4 * kMaxTileBits);
+    Sweep *s_sweeps = reinterpret_cast<Sweep *>(sm + A.off_desc);
+    const TilePass &P = *A.pass;
+    const int n_sweeps = P.n_sweeps, n_micro = P.n_micro;
+    MicroOp *s_micro = reinterpret_cast<MicroOp *>(s_sweeps + n_sweeps);
+    DiagDesc *s_diags = reinterpret_cast<DiagDesc *>(s_micro + n_micro);
     float2 *cs = reinterpret_cast<float2 *>(sm + A.off_consts);
     float2 *roots = reinterpret_cast<float2 *>(sm + A.off_roots);
     float2 *bufs[2] = {reinterpret_cast<float2 *>(sm + A.off_buf0), reinterpret_cast<float2 *>(sm + A.off_buf1)};
-    const TilePass &P = *A.pass;
     const int tid = threadIdx.x;
-    const int L = P.L, H = P.H, T = P.T, RS = P.row_stride;
+    const int L = P.L, H = P.H, T = P.T;
     const int rows = 1 << H;
     const uint32_t row_bytes = 8u << L;
+    const uint32_t tile_bytes = 8u << T;
     const long long total = A.n_tiles * (long long)A.batch;
 
+    // stage the pass descriptor and constants in shared memory
+    {
+        const int *src = reinterpret_cast<const int *>(P.sweeps);
+        int *dst = reinterpret_cast<int *>(s_sweeps);
+        const int nw_s = n_sweeps * (int)(sizeof(Sweep) / 4);
+        for (int i = tid; i < nw_s; i += blockDim.x) dst[i] = src[i];
+        src = reinterpret_cast<const int *>(P.micro);
+        dst = reinterpret_cast<int *>(s_micro);
+        const int nw_m = n_micro * (int)(sizeof(MicroOp) / 4);
+        for (int i = tid; i < nw_m; i += blockDim.x) dst[i] = src[i];
+        src = reinterpret_cast<const int *>(P.diags);
+        dst = reinterpret_cast<int *>(s_diags);
+        const int nw_d = kMaxDiag * (int)(sizeof(DiagDesc) / 4);
+        for (int i = tid; i < nw_d; i += blockDim.x) dst[i] = src[i];
+    }
     for (int i = tid; i < P.n_const; i += blockDim.x) cs[i] = A.consts[i];
     if (A.off_roots)
         for (int i = tid; i < kRootsEntries; i += blockDim.x) roots[i] = A.roots[i];
-    if (tid < kMaxTileBits) s_hb[tid] = P.hb[tid];
+    if (tid < kMaxTileBits) {
+        s_hb[tid] = P.hb[tid];
+        s_contrib[tid] = P.smem_contrib[tid];
+    }
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -397,21 +501,52 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_pass_kernel(const TileAr
     if (tile >= total) return;
     const int warp = tid >> 5, lane = tid & 31;
 
+    // warp 0 issues the copies
     auto issue_load = [&](long long t, float2 *dstbuf, uint64_t *b) {
         const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
-        const float2 *src = A.src + bi * A.state_elems + tile_base(A, ti);
-        if (lane == 0) mbar_arrive_expect_tx(b, (uint32_t)rows * row_bytes);
-        __syncwarp();
-        for (int r = lane; r < rows; r += 32) bulk_g2s(dstbuf + (size_t)r * RS, src + row_offset(r, H, s_hb), row_bytes, b);
+        if (A.use_tma) {
+            if (lane == 0) {
+                mbar_arrive_expect_tx(b, tile_bytes);
+                int c[5];
+                tile_coords(A.geo, ti, bi, c);
+                tma_load_5d(dstbuf, &tm_src, c, b);
+            }
+        } else {
+            const float2 *src = A.src + bi * A.state_elems + tile_base(A, ti);
+            if (lane == 0) mbar_arrive_expect_tx(b, tile_bytes);
+            __syncwarp();
+            for (int r = lane; r < rows; r += 32)
+                bulk_g2s(dstbuf + ((size_t)r << L), src + row_offset(r, H, s_hb), row_bytes, b);
+        }
     };
     auto issue_store = [&](long long t, float2 *srcbuf) {
         const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
-        float2 *dst = A.dst + bi * A.state_elems + tile_base(A, ti);
-        for (int r = lane; r < rows; r += 32) bulk_s2g(dst + row_offset(r, H, s_hb), srcbuf + (size_t)r * RS, row_bytes);
-        bulk_commit();
+        if (A.use_tma) {
+            if (lane == 0) {
+                int c[5];
+                tile_coords(A.geo, ti, bi, c);
+                tma_store_5d(&tm_dst, c, srcbuf);
+                bulk_commit();
+            }
+        } else {
+            float2 *dst = A.dst + bi * A.state_elems + tile_base(A, ti);
+            for (int r = lane; r < rows; r += 32)
+                bulk_s2g(dst + row_offset(r, H, s_hb), srcbuf + ((size_t)r << L), row_bytes);
+            bulk_commit();
+        }
     };
 
     if (warp == 0) issue_load(tile, bufs[0], &bar[0]);
+
+    SweepCtx c;
+    c.T = T;
+    c.L = L;
+    c.contrib = s_contrib;
+    c.hb = s_hb;
+    c.cs = cs;
+    c.roots = roots;
+    c.micro = s_micro;
+    c.diags = s_diags;
 
     bool failed = false;
     int fail_k = 0;
@@ -420,7 +555,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_pass_kernel(const TileAr
         float2 *B = bufs[cur];
         const long long next = tile + gridDim.x;
         if (next < total && warp == 0) {
-            bulk_wait_read0();   // buffer cur^1: its previous tile's stores have read smem
+            bulk_wait_read0();   // buffer cur^1: the previous tile's stores have read it
             __syncwarp();
             issue_load(next, bufs[cur ^ 1], &bar[cur ^ 1]);
         }
@@ -431,20 +566,13 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_pass_kernel(const TileAr
             break;
         }
         const long long bi = tile / A.n_tiles, ti = tile - bi * A.n_tiles;
-        SweepCtx c;
-        c.L = L;
-        c.T = T;
-        c.RS = RS;
-        c.hb = s_hb;
         c.buf = B;
-        c.cs = cs;
-        c.roots = roots;
         c.tile_gbase = tile_base(A, ti);
-        for (int s = 0; s < P.n_sweeps; ++s) {
-            const Sweep &S = P.sweeps[s];
-            run_sweep_r(S.r, c, S, P.micro, P.diags);
+        for (int s = 0; s < n_sweeps; ++s) {
+            run_sweep_r(s_sweeps[s].r, c, s_sweeps[s]);
             __syncthreads();
         }
+        (void)bi;
         fence_proxy_async();
         __syncthreads();
         if (warp == 0) issue_store(tile, B);
@@ -465,8 +593,10 @@ void tile_kernel_smem_config(int bytes) {
     cudaFuncSetAttribute(tile_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-cudaError_t launch_tile_pass(const TileArgs &A, int grid, int smem_bytes, cudaStream_t st) {
-    tile_pass_kernel<<<grid, kTileThreads, smem_bytes, st>>>(A);
+cudaError_t launch_tile_pass(const TileArgs &A, const void *tm_src, const void *tm_dst, int grid, int smem_bytes,
+                             cudaStream_t st) {
+    tile_pass_kernel<<<grid, kTileThreads, smem_bytes, st>>>(*reinterpret_cast<const CUtensorMap *>(tm_src),
+                                                             *reinterpret_cast<const CUtensorMap *>(tm_dst), A);
     return cudaGetLastError();
 }
 

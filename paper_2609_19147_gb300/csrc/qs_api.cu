@@ -1,7 +1,9 @@
 // C ABI (include/qs.h): state handles, plan cache, executor, expectation and
 // adjoint gradients.  All arithmetic on amplitudes runs in the CUDA kernels;
 // this file validates, plans, routes buffers and launches.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <chrono>
@@ -99,8 +101,9 @@ uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
     return h;
 }
 
-uint64_t plan_key(int n, const std::vector<RGate> &g, const qs_opts &o) {
+uint64_t plan_key(int n, int batch, const std::vector<RGate> &g, const qs_opts &o) {
     uint64_t h = fnv1a(&n, sizeof n);
+    h = fnv1a(&batch, sizeof batch, h);
     h = fnv1a(&o, sizeof o, h);
     for (const RGate &r : g) {
         h = fnv1a(&r.kind, sizeof r.kind, h);
@@ -193,8 +196,8 @@ qs_status upload_plan(qs_state *st, DevicePlan &dp) {
     return QS_OK;
 }
 
-qs_status get_plan(qs_state *st, const std::vector<RGate> &gates, const qs_opts &o, DevicePlan **out) {
-    uint64_t key = plan_key(st->n, gates, o);
+qs_status get_plan(qs_state *st, const std::vector<RGate> &gates, const qs_opts &o, int batch, DevicePlan **out) {
+    uint64_t key = plan_key(st->n, batch, gates, o);
     auto it = st->cache.find(key);
     if (it != st->cache.end()) {
         st->lru.erase(it->second->lru);
@@ -206,7 +209,7 @@ qs_status get_plan(qs_state *st, const std::vector<RGate> &gates, const qs_opts 
     std::unique_ptr<DevicePlan> dp(new DevicePlan());
     std::string err;
     qs_status s = (o.mode == QS_MODE_PERGATE) ? build_pergate_plan(st->n, gates, dp->host, err)
-                                              : build_fused_plan(st->n, gates, o, dp->host, err);
+                                              : build_fused_plan(st->n, batch, gates, o, dp->host, err);
     if (s != QS_OK) return fail(s, err);
     s = upload_plan(st, *dp);
     if (s != QS_OK) {
@@ -267,9 +270,39 @@ qs_status check_err_word(qs_state *st) {
 }
 
 // -------- executor --------
-qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *src, float2 *dst, float2 *base_off,
-                   int batch) {
-    (void)base_off;
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+qs_status get_encoder() {
+    if (g_encode) return QS_OK;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+        return fail(QS_ERR_CUDA, "cuTensorMapEncodeTiled entry point not available");
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    return QS_OK;
+}
+
+qs_status encode_map(const TmaPlan &g, const void *base, bool swizzle, CUtensorMap *out) {
+    qs_status s = get_encoder();
+    if (s != QS_OK) return s;
+    cuuint64_t gdim[5], gstr[4];
+    cuuint32_t box[5], es[5];
+    for (int d = 0; d < 5; ++d) {
+        gdim[d] = g.gdim[d];
+        box[d] = g.box[d];
+        es[d] = 1;
+        if (d >= 1) gstr[d - 1] = g.gstride[d];
+    }
+    CUresult r = g_encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, const_cast<void *>(base), gdim, gstr, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(QS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return QS_OK;
+}
+
+qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *src, float2 *dst, int batch) {
     const HostPass &hp = dp.host.passes[i];
     const TilePass &tp = hp.tile;
     TileArgs A;
@@ -288,29 +321,52 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     for (int b = 0; b < st->n; ++b)
         if (!((tilebits >> b) & 1)) A.outer_pos[A.n_outer++] = b;
     A.err = st->d_err;
+    // shared memory: [barriers, hb, contrib | descriptor | constants | roots | 2 tile buffers]
+    auto al = [](int v, int a) { return (v + a - 1) / a * a; };
     int off = 128;
+    A.off_desc = off;
+    off += tp.n_sweeps * (int)sizeof(Sweep) + tp.n_micro * (int)sizeof(MicroOp) + kMaxDiag * (int)sizeof(DiagDesc);
+    off = al(off, 128);
     A.off_consts = off;
-    off += ((int)hp.consts.size() * 8 + 127) / 128 * 128;
+    off = al(off + (int)hp.consts.size() * 8, 128);
     if (hp.uses_roots) {
         A.off_roots = off;
         off += kRootsEntries * 8;
     }
-    const int buf_bytes = ((1 << tp.H) * tp.row_stride * 8 + 127) / 128 * 128;
+    const int buf_bytes = 8 << tp.T;
+    off = al(off, 1024);
     A.off_buf0 = off;
     off += buf_bytes;
     A.off_buf1 = off;
     off += buf_bytes;
     if (off > 227 * 1024) return fail(QS_ERR_INTERNAL, "tile pass needs too much shared memory");
     static int configured[16] = {0};
-    if (configured[st->dev] < off) {
+    if (configured[st->dev] < 227 * 1024) {
         tile_kernel_smem_config(227 * 1024);
         configured[st->dev] = 227 * 1024;
+    }
+    CUtensorMap tms, tmd;
+    std::memset(&tms, 0, sizeof tms);
+    std::memset(&tmd, 0, sizeof tmd);
+    A.use_tma = hp.tma.ok ? 1 : 0;
+    if (A.use_tma) {
+        A.geo.ndims = hp.tma.ndims;
+        A.geo.batch_dim = hp.tma.batch_dim;
+        for (int d = 0; d < 5; ++d) {
+            A.geo.kind[d] = hp.tma.kind[d];
+            A.geo.off[d] = hp.tma.off[d];
+            A.geo.w[d] = hp.tma.w[d];
+        }
+        qs_status s = encode_map(hp.tma, src, tp.swizzle != 0, &tms);
+        if (s != QS_OK) return s;
+        s = encode_map(hp.tma, dst, tp.swizzle != 0, &tmd);
+        if (s != QS_OK) return s;
     }
     long long total = A.n_tiles * batch;
     int grid = (int)std::min<long long>(total, g_num_sms[st->dev] > 0 ? g_num_sms[st->dev] : 148);
     cudaEvent_t ev;
     prof_begin(st, &ev);
-    QS_CUDA(launch_tile_pass(A, grid, off, st->stream));
+    QS_CUDA(launch_tile_pass(A, &tms, &tmd, grid, off, st->stream));
     prof_end(st, ev, "tile_pass", 16.0 * (double)st->elems * batch);
     return QS_OK;
 }
@@ -449,10 +505,10 @@ qs_status run_fused(qs_state *st, const DevicePlan &dp, float2 *home, float2 *ot
         qs_status s = QS_OK;
         if (hp.type == HostPass::TILE) {
             if (flip_tile && (int)i == first_tile) {
-                s = run_tile(st, dp, i, cur, oth, nullptr, batch);
+                s = run_tile(st, dp, i, cur, oth, batch);
                 std::swap(cur, oth);
             } else {
-                s = run_tile(st, dp, i, cur, cur, nullptr, batch);
+                s = run_tile(st, dp, i, cur, cur, batch);
             }
         } else if (hp.type == HostPass::PERM) {
             s = run_perm(st, hp.perm, cur, oth, batch);
@@ -479,7 +535,7 @@ bool plan_needs_scratch(const Plan &p) {
 
 qs_status apply_resolved(qs_state *st, const std::vector<RGate> &gates, const qs_opts &o, float2 *home, int batch) {
     DevicePlan *dp = nullptr;
-    qs_status s = get_plan(st, gates, o, &dp);
+    qs_status s = get_plan(st, gates, o, batch, &dp);
     if (s != QS_OK) return s;
     if (dp->host.mode == QS_MODE_PERGATE) return run_pergate(st, *dp, home, batch);
     if (plan_needs_scratch(dp->host)) {
@@ -980,7 +1036,7 @@ qs_status qs_plan_describe(int n, const qs_gate *gates, size_t n_gates, const qs
     qs_status s = resolve_gates(n, gates, n_gates, nullptr, 0, 0, rg, err);
     if (s != QS_OK) return fail(s, err);
     Plan p;
-    s = (o.mode == QS_MODE_PERGATE) ? build_pergate_plan(n, rg, p, err) : build_fused_plan(n, rg, o, p, err);
+    s = (o.mode == QS_MODE_PERGATE) ? build_pergate_plan(n, rg, p, err) : build_fused_plan(n, 1, rg, o, p, err);
     if (s != QS_OK) return fail(s, err);
     std::string d = p.describe();
     if (buf && len) {

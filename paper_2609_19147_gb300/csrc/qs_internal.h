@@ -66,7 +66,8 @@ struct DiagDesc {
 enum MicroKind : int32_t {
     MK_U1 = 0,    // 2x2 on group bit a where (x & cmask) == cval
     MK_U2 = 1,    // 4x4 on group bits (a = matrix MSB, b = LSB) where (x & cmask) == cval
-    MK_DIAG = 2,  // diagonal phase, diag index = cst
+    MK_DIAG = 2,  // diagonal phase, diag index = cst; a = mask of slices and
+                  // b = mask of LUT groups that depend on the sweep's group bits
     MK_QFT = 3,   // QFT stage: H on group bit a (= global bit p), then twiddle
                   // exp(i pi x_p (x & bits[lo, p)) / 2^p); group part at cst
     MK_H = 4,     // Hadamard on group bit a (sign-only butterfly)
@@ -83,18 +84,23 @@ struct MicroOp {
 struct Sweep {
     int32_t r;                   // group size (1..kMaxGroup)
     int32_t op_begin, op_end;    // micro-op range [begin, end)
+    int32_t vec;                 // group bit 0 is tile-local bit 0: 16-byte pair accesses
+    float scale;                 // folded butterfly normalisation, applied once at the end
     int32_t gbit[kMaxGroup];     // tile-local bit of group bit j
     int32_t tbit[kMaxTileBits];  // tile-local bit of item bit i (i < T - r)
 };
 
-// One tile pass.  Tile-local bits 0..L-1 are the low index bits (one smem row
-// of 2^L amplitudes, padded to row_stride); tile-local bit L+k is global bit
-// hb[k].  Tiles are indexed by the remaining n-T bits (ascending).
+// One tile pass.  Tile-local bits 0..L-1 are the low index bits; tile-local
+// bit L+k is global bit hb[k] (hb ascending).  In shared memory the tile is
+// dense in tile-local order, optionally with the 128-byte TMA swizzle; the
+// float2 offset of a tile element is the XOR of smem_contrib[] over its set
+// tile-local bits.  Tiles are indexed by the remaining n-T bits (ascending).
 struct TilePass {
     int32_t n, L, H, T;
-    int32_t row_stride;
+    int32_t swizzle;                     // 1: 128-byte swizzle (TMA tensor path)
     int32_t n_sweeps, n_micro, n_const;
     int32_t hb[kMaxTileBits];
+    int32_t smem_contrib[kMaxTileBits];
     Sweep sweeps[kMaxSweeps];
     MicroOp micro[kMaxMicro];
     DiagDesc diags[kMaxDiag];

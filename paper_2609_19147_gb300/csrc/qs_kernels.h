@@ -6,6 +6,18 @@
 
 namespace qs {
 
+// Tensor-map geometry of a tile pass: up to 5 dims in ascending bit order.
+// kind 0: tile range (coordinate 0); kind 1: gap of non-tile bits, coordinate
+// = bits [off, off + w) of the tile index (plus batch * 2^w on the top dim);
+// kind 2: batch only.
+struct TmaGeom {
+    int ndims;
+    int kind[5];
+    int off[5];
+    int w[5];
+    int batch_dim;          // dim that carries the batch index, -1 if none
+};
+
 struct TileArgs {
     const TilePass *pass;      // device copy of the pass descriptor
     const float2 *consts;      // device copy of the pass constants
@@ -17,11 +29,14 @@ struct TileArgs {
     int batch;
     int n_outer;               // number of non-tile index bits
     int outer_pos[kMaxQubits]; // their positions, ascending
-    int off_consts, off_roots, off_buf0, off_buf1;   // dynamic smem layout
+    int off_desc, off_consts, off_roots, off_buf0, off_buf1;   // dynamic smem layout
+    int use_tma;               // 1: one tensor copy per tile; 0: one bulk copy per row
+    TmaGeom geo;
     int *err;                  // device status word
 };
 
-cudaError_t launch_tile_pass(const TileArgs &A, int grid, int smem_bytes, cudaStream_t st);
+cudaError_t launch_tile_pass(const TileArgs &A, const void *tm_src, const void *tm_dst, int grid, int smem_bytes,
+                             cudaStream_t st);
 void tile_kernel_smem_config(int bytes);
 
 // per-gate kernels: op per state (op_stride = 1) or shared (op_stride = 0)

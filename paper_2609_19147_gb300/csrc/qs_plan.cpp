@@ -692,31 +692,27 @@ uint64_t glob_of_local(const TilePass &tp, int tb) {
     return tb < tp.L ? (1ull << tb) : (1ull << tp.hb[tb - tp.L]);
 }
 
-int smem_of_local(const TilePass &tp, int tb) {
-    return tb < tp.L ? (1 << tb) : (tp.row_stride << (tb - tp.L));
-}
-
-// choose item-bit order so that a warp's 32 lanes hit distinct banks
+// choose item-bit order so that a warp's 32 lanes hit distinct banks; smem
+// offsets are XOR-linear (tp.smem_contrib); vec sweeps access 16 bytes
 void choose_item_bits(const TilePass &tp, Sweep &sw) {
     std::vector<int> cand;
     uint64_t gmask = 0;
     for (int j = 0; j < sw.r; ++j) gmask |= 1ull << sw.gbit[j];
     for (int tb = 0; tb < tp.T; ++tb)
         if (!((gmask >> tb) & 1)) cand.push_back(tb);
-    int k = (int)cand.size();
-    int nl = std::min(5, k);
+    const int k = (int)cand.size();
+    const int nl = std::min(5, k);
+    const int words_per = sw.vec ? 2 : 1;
     std::vector<int> best;
     int best_cost = 1 << 30;
-    // enumerate subsets of size nl (k <= 13)
     std::vector<int> idx(nl);
     for (int i = 0; i < nl; ++i) idx[i] = i;
     while (true) {
-        // cost: max number of distinct 8-byte words per 4-byte bank pair
         int words[32];
         for (int l = 0; l < (1 << nl); ++l) {
             int w = 0;
             for (int i = 0; i < nl; ++i)
-                if ((l >> i) & 1) w += smem_of_local(tp, cand[idx[i]]);
+                if ((l >> i) & 1) w ^= tp.smem_contrib[cand[idx[i]]];
             words[l] = w;
         }
         int bank_cnt[32] = {0};
@@ -725,8 +721,7 @@ void choose_item_bits(const TilePass &tp, Sweep &sw) {
             for (int m = 0; m < l; ++m)
                 if (words[m] == words[l]) dup = true;
             if (dup) continue;
-            bank_cnt[(2 * words[l]) & 31]++;
-            bank_cnt[(2 * words[l] + 1) & 31]++;
+            for (int e = 0; e < 2 * words_per; ++e) bank_cnt[(2 * words[l] + e) & 31]++;
         }
         int cost = 0;
         for (int b = 0; b < 32; ++b) cost = std::max(cost, bank_cnt[b]);
@@ -751,6 +746,64 @@ void choose_item_bits(const TilePass &tp, Sweep &sw) {
     for (int i = 0; i < k; ++i) sw.tbit[i] = order[i];
 }
 
+// TMA geometry for the tile bit set S: dims = low bits, runs of tile bits
+// (split into <= 8-bit boxes), gaps of non-tile bits; the batch rides on the
+// top gap or gets a dim of its own.
+TmaPlan tma_geometry(int n, int L, uint64_t S, int batch) {
+    TmaPlan g;
+    int nd = 0;
+    auto add = [&](int kind, int lo_bit, int bits, int off) {
+        if (nd >= 5) {
+            nd = 6;
+            return;
+        }
+        g.kind[nd] = kind;
+        g.off[nd] = off;
+        g.w[nd] = bits;
+        g.gdim[nd] = kind == 2 ? (uint64_t)batch : (1ull << bits);
+        g.gstride[nd] = kind == 2 ? (8ull << n) : (8ull << lo_bit);
+        g.box[nd] = kind == 0 ? (1u << bits) : 1u;
+        nd++;
+    };
+    add(0, 0, L, 0);
+    int b = L, outer = 0;
+    while (b < n && nd <= 5) {
+        bool t = (S >> b) & 1;
+        int e = b;
+        while (e < n && (((S >> e) & 1) != 0) == t) ++e;
+        if (t) {
+            for (int c = b; c < e; c += 8) add(0, c, std::min(8, e - c), 0);
+        } else {
+            add(1, b, e - b, outer);
+            outer += e - b;
+        }
+        b = e;
+    }
+    if (nd <= 5 && batch > 1) {
+        if (g.kind[nd - 1] == 1 && !((S >> (n - 1)) & 1)) {
+            g.batch_dim = nd - 1;
+            g.gdim[nd - 1] *= (uint64_t)batch;
+        } else {
+            add(2, n, 0, 0);
+            g.batch_dim = nd - 1;
+        }
+    }
+    if (nd > 5) return TmaPlan();
+    g.ndims = nd;
+    for (int d = nd; d < 5; ++d) {   // pad to 5-D with extent-1 dims
+        g.kind[d] = 0;
+        g.w[d] = 0;
+        g.gdim[d] = 1;
+        g.box[d] = 1;
+        const uint64_t prev = (d - 1 == 0) ? 8ull : g.gstride[d - 1];
+        g.gstride[d] = prev * g.gdim[d - 1];
+    }
+    for (int d = 1; d < 5; ++d)
+        if (g.gstride[d] >= (1ull << 40) || (g.gstride[d] & 15)) return TmaPlan();
+    g.ok = true;
+    return g;
+}
+
 struct PassBuilder {
     int n, L, T, R;
     HostPass hp;
@@ -758,7 +811,7 @@ struct PassBuilder {
     std::vector<float2> &cst;
     uint64_t cur_group = 0;   // tile-local bits of the open sweep
     int open = -1;
-    PassBuilder(int n_, int L_, int T_, int R_, uint64_t S)
+    PassBuilder(int n_, int L_, int T_, int R_, uint64_t S, int batch)
         : n(n_), L(L_), T(T_), R(R_), tp(hp.tile), cst(hp.consts) {
         std::memset(&tp, 0, sizeof(TilePass));
         hp.type = HostPass::TILE;
@@ -766,10 +819,18 @@ struct PassBuilder {
         tp.L = L;
         tp.T = T;
         tp.H = T - L;
-        tp.row_stride = (1 << L) + 2;
         int k = 0;
         for (int b = L; b < n; ++b)
             if ((S >> b) & 1) tp.hb[k++] = b;
+        hp.tma = tma_geometry(n, L, S, batch);
+        // 128-byte swizzle: 16-byte chunk bits [1,4) of the float2 offset are
+        // XORed with row bits [4,7) (rows of 128 bytes = 16 amplitudes)
+        tp.swizzle = (hp.tma.ok && L == 4 && T >= 7) ? 1 : 0;
+        for (int tb = 0; tb < T; ++tb) {
+            int c = 1 << tb;
+            if (tp.swizzle && tb >= 4 && tb < 7) c ^= 1 << (tb - 3);
+            tp.smem_contrib[tb] = c;
+        }
     }
     int group_index(int tb) {
         for (int j = 0; j < tp.sweeps[open].r; ++j)
@@ -797,14 +858,19 @@ struct PassBuilder {
     void close_sweep() {
         if (open < 0) return;
         Sweep &sw = tp.sweeps[open];
-        // pad the group to R bits with unused tile bits (highest first)
+        // pad the group to R bits: tile bit 0 first (16-byte pair accesses),
+        // then unused tile bits, highest first
+        if (sw.r < std::min(R, T) && !(cur_group & 1ull)) {
+            sw.gbit[sw.r++] = 0;
+            cur_group |= 1ull;
+        }
         for (int tb = T - 1; tb >= 0 && sw.r < std::min(R, T); --tb)
             if (!((cur_group >> tb) & 1)) {
                 sw.gbit[sw.r++] = tb;
                 cur_group |= 1ull << tb;
             }
         std::sort(sw.gbit, sw.gbit + sw.r);
-        // micro ops reference group indices: remap after sorting
+        sw.vec = (sw.r >= 2 && sw.gbit[0] == 0) ? 1 : 0;
         sw.op_end = tp.n_micro;
         choose_item_bits(tp, sw);
         open = -1;
@@ -885,12 +951,32 @@ struct PassBuilder {
     int count_diags = 0;
     void finalize() {
         close_sweep();
-        // convert tile-local bit references to group indices and fill QFT tables
+        // convert tile-local bit references to group indices, fill QFT
+        // tables, fold butterfly normalisations, mark diagonal factors that
+        // depend on the group bits
         for (int s = 0; s < tp.n_sweeps; ++s) {
             Sweep &sw = tp.sweeps[s];
+            uint64_t ggl = 0;
+            for (int m = 0; m < sw.r; ++m) ggl |= glob_of_local(tp, sw.gbit[m]);
+            int n_butterfly = 0;
             for (int i = sw.op_begin; i < sw.op_end; ++i) {
                 MicroOp &mo = tp.micro[i];
-                if (mo.kind == MK_DIAG) continue;
+                if (mo.kind == MK_H || mo.kind == MK_QFT) n_butterfly++;
+                if (mo.kind == MK_DIAG) {
+                    const DiagDesc &d = tp.diags[mo.cst];
+                    uint32_t ds = 0, dg = 0;
+                    for (int k = 0; k < d.n_slices; ++k) {
+                        uint64_t win = (((1ull << d.slice_w[k]) - 1) << d.slice_lo[k]);
+                        if (win & ggl) ds |= 1u << k;
+                    }
+                    for (int k = 0; k < d.n_groups; ++k) {
+                        uint64_t bits = d.grp_mask[k] | (d.grp_mask[k] << d.grp_d[k]);
+                        if (bits & ggl) dg |= 1u << k;
+                    }
+                    mo.a = (int)ds;
+                    mo.b = (int)dg;
+                    continue;
+                }
                 int ga = -1, gb = -1;
                 for (int j = 0; j < sw.r; ++j) {
                     if (sw.gbit[j] == mo.a) ga = j;
@@ -910,6 +996,7 @@ struct PassBuilder {
                     }
                 }
             }
+            sw.scale = (float)std::pow(kSqrtHalf, (double)n_butterfly);
         }
         tp.n_const = (int)cst.size();
     }
@@ -968,7 +1055,7 @@ static void build_perm_or_gather(int n, const FOp &f, HostPass &hp) {
         }
 }
 
-qs_status build_fused_plan(int n, const std::vector<RGate> &gates, const qs_opts &o, Plan &plan,
+qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, const qs_opts &o, Plan &plan,
                            std::string &err) {
     plan = Plan();
     plan.n = n;
@@ -1096,7 +1183,7 @@ qs_status build_fused_plan(int n, const std::vector<RGate> &gates, const qs_opts
         }
         // pad the tile to T bits with the lowest unused high bits
         for (int b = L; b < n && popc64(S) < T; ++b) S |= 1ull << b;
-        PassBuilder pb(n, L, T, R, S);
+        PassBuilder pb(n, L, T, R, S, batch);
         for (int id : taken) {
             pb.add(ops[id], ops[id].kind == F_DIAG ? &dplans[id] : nullptr);
             if (pb.tp.n_sweeps >= kMaxSweeps - 1) break;   // guarded by taken limit

@@ -60,10 +60,25 @@ struct FOp {
     uint64_t D() const;            // bits the op depends on diagonally
 };
 
+// TMA tensor geometry of a tile pass (see TmaGeom): dims in ascending bit
+// order with their global extents, byte strides and box extents.
+struct TmaPlan {
+    bool ok = false;
+    int ndims = 0;
+    int kind[5] = {0, 0, 0, 0, 0};
+    int off[5] = {0, 0, 0, 0, 0};
+    int w[5] = {0, 0, 0, 0, 0};
+    int batch_dim = -1;
+    uint64_t gdim[5] = {1, 1, 1, 1, 1};
+    uint64_t gstride[5] = {0, 0, 0, 0, 0};   // bytes, dims 1..4
+    uint32_t box[5] = {1, 1, 1, 1, 1};
+};
+
 struct HostPass {
     enum Type { TILE = 0, PERM = 1, GATHER = 2 } type = TILE;
     TilePass tile;                 // TILE
     std::vector<float2> consts;    // TILE constants
+    TmaPlan tma;                   // TILE: tensor-copy geometry
     int uses_roots = 0;
     PermPass perm;                 // PERM
     GatherPass gather;             // GATHER
@@ -90,7 +105,7 @@ qs_status resolve_gates(int n, const qs_gate *gates, size_t n_gates, const doubl
 void gate_matrix(const RGate &g, cd *M);
 bool gate_is_diagonal(int kind);
 
-qs_status build_fused_plan(int n, const std::vector<RGate> &gates, const qs_opts &o, Plan &plan,
+qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, const qs_opts &o, Plan &plan,
                            std::string &err);
 qs_status build_pergate_plan(int n, const std::vector<RGate> &gates, Plan &plan, std::string &err);
 
