@@ -102,7 +102,8 @@ typedef struct qs_opts {
     int32_t mode;         /* enum qs_mode                                    */
     int32_t tile_qubits;  /* qubits per tile pass, 0 = default (13)          */
     int32_t low_qubits;   /* contiguous low bits per tile row, 0 = default   */
-    int32_t flags;        /* reserved, 0                                     */
+    int32_t group_qubits; /* tile bits held in registers per sweep (1..5),
+                             0 = default (5)                                 */
 } qs_opts;
 
 typedef struct qs_state qs_state;

@@ -7,17 +7,22 @@
 // TMA unit as a <=5-D tensor whose dims are the low bits, the contiguous runs
 // of tile bits and the gaps of non-tile bits between them (the tile selects a
 // box of extent 1 in every gap).  When the bit set needs more than 5 dims the
-// pass falls back to one bulk copy per 2^L-amplitude row.  Loads are
-// double-buffered: the next tile lands while the current one is processed and
-// the previous one drains.
+// pass falls back to one bulk copy per 2^L-amplitude row.
 //
-// Between load and store the tile goes through "sweeps": every thread holds
-// 2^R amplitudes that differ in R tile bits (registers) and applies the
-// sweep's micro-ops: 2x2 / 4x4 unitaries with controls, diagonal phase tables
-// (factored into an item part and a group part), and QFT stages (Hadamard
-// butterfly + closed-form ladder twiddle; Sec. 5.1).  Butterfly
-// normalisations are folded into one scale per sweep.  Shared-memory offsets
-// are XOR-linear in the tile bits, which covers the swizzled layout.
+// Warp roles: one producer warp issues every copy and waits on nothing but
+// mbarriers; 8 compute warps process tiles.  Tiles rotate through 2-3 shared
+// buffers with "full" (TMA complete_tx) and "empty" (compute done) mbarriers,
+// so loads of the next tiles and the store of the previous one overlap the
+// compute of the current tile.
+//
+// Between load and store the tile goes through "sweeps": every compute thread
+// holds 2^R amplitudes that differ in R tile bits (registers) and applies the
+// sweep's micro-ops: 2x2 / 4x4 unitaries with controls (with cheaper forms for
+// real and RX-type matrices), diagonal phase tables (factored into an item part
+// and a group part), and QFT stages (Hadamard butterfly + closed-form ladder
+// twiddle; Sec. 5.1).  Butterfly normalisations are folded into one scale per
+// sweep.  Shared-memory offsets are XOR-linear in the tile bits, which covers
+// the swizzled layout.
 //
 // All waits are bounded; on expiry the kernel records QS_ERR_TIMEOUT, lets its
 // own copies land and returns.
@@ -104,6 +109,13 @@ __device__ __forceinline__ void fence_proxy_async() {
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// barrier among the compute warps only (the producer warp never joins)
+__device__ __forceinline__ void compute_sync() {
+    asm volatile("bar.sync 1, %0;" ::"r"(kTileThreads) : "memory");
+}
 
 // ---------------------------------------------------------------------------
 // complex helpers
@@ -176,6 +188,34 @@ __device__ __forceinline__ void op_u1(float2 (&a)[1 << R], const float2 *mat, ui
     }
 }
 
+// [[c, i s], [i s, c]] (RX(t): c = cos t/2, s = -sin t/2): 4 FP32 ops per amplitude
+template <int R, int M>
+__device__ __forceinline__ void op_rxc(float2 (&a)[1 << R], const float2 *cs) {
+    const float c = cs[0].x, s = cs[0].y;
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) {
+        if ((j >> M) & 1) continue;
+        const int k = j | (1 << M);
+        const float2 a0 = a[j], a1 = a[k];
+        a[j] = make_float2(fmaf(c, a0.x, -s * a1.y), fmaf(c, a0.y, s * a1.x));
+        a[k] = make_float2(fmaf(c, a1.x, -s * a0.y), fmaf(c, a1.y, s * a0.x));
+    }
+}
+
+// real 2x2 (RY family): 4 FP32 ops per amplitude
+template <int R, int M>
+__device__ __forceinline__ void op_u1r(float2 (&a)[1 << R], const float2 *cs) {
+    const float m00 = cs[0].x, m01 = cs[0].y, m10 = cs[1].x, m11 = cs[1].y;
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) {
+        if ((j >> M) & 1) continue;
+        const int k = j | (1 << M);
+        const float2 a0 = a[j], a1 = a[k];
+        a[j] = make_float2(fmaf(m00, a0.x, m01 * a1.x), fmaf(m00, a0.y, m01 * a1.y));
+        a[k] = make_float2(fmaf(m10, a0.x, m11 * a1.x), fmaf(m10, a0.y, m11 * a1.y));
+    }
+}
+
 // unnormalised Hadamard butterfly (the 1/sqrt 2 is folded into the sweep scale)
 template <int R, int M>
 __device__ __forceinline__ void op_h(float2 (&a)[1 << R]) {
@@ -230,6 +270,20 @@ __device__ __forceinline__ void disp_u1(int m, float2 (&a)[1 << R], const float2
     if constexpr (M < R) {
         if (m == M) op_u1<R, M>(a, mat, cm, cv, base, G);
         else disp_u1<R, M + 1>(m, a, mat, cm, cv, base, G);
+    }
+}
+template <int R, int M = 0>
+__device__ __forceinline__ void disp_rxc(int m, float2 (&a)[1 << R], const float2 *cs) {
+    if constexpr (M < R) {
+        if (m == M) op_rxc<R, M>(a, cs);
+        else disp_rxc<R, M + 1>(m, a, cs);
+    }
+}
+template <int R, int M = 0>
+__device__ __forceinline__ void disp_u1r(int m, float2 (&a)[1 << R], const float2 *cs) {
+    if constexpr (M < R) {
+        if (m == M) op_u1r<R, M>(a, cs);
+        else disp_u1r<R, M + 1>(m, a, cs);
     }
 }
 template <int R, int M = 0>
@@ -339,7 +393,7 @@ __device__ __forceinline__ void sweep_store(const SweepCtx &c, bool vec, int sad
 }
 
 template <int R>
-__device__ __noinline__ void run_sweep(const SweepCtx &c, const Sweep &S) {
+__device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S) {
     int gs[R];
     Grp<R> G;
 #pragma unroll
@@ -350,7 +404,7 @@ __device__ __noinline__ void run_sweep(const SweepCtx &c, const Sweep &S) {
     const int nb = c.T - R;
     const int n_items = 1 << nb;
     const bool vec = S.vec != 0;
-    for (int item = threadIdx.x; item < n_items; item += blockDim.x) {
+    for (int item = threadIdx.x; item < n_items; item += kTileThreads) {
         int saddr = 0;
         uint64_t gbase = c.tile_gbase;
         for (int i = 0; i < nb; ++i)
@@ -369,6 +423,12 @@ __device__ __noinline__ void run_sweep(const SweepCtx &c, const Sweep &S) {
                     break;
                 case MK_H:
                     disp_h<R>(op.a, a);
+                    break;
+                case MK_RXC:
+                    disp_rxc<R>(op.a, a, c.cs + op.cst);
+                    break;
+                case MK_U1R:
+                    disp_u1r<R>(op.a, a, c.cs + op.cst);
                     break;
                 case MK_U2:
                     disp_u2<R>(op.a, op.b, a, c.cs + op.cst, op.cmask, op.cval, gbase, G);
@@ -406,16 +466,6 @@ __device__ __noinline__ void run_sweep(const SweepCtx &c, const Sweep &S) {
     }
 }
 
-__device__ void run_sweep_r(int r, const SweepCtx &c, const Sweep &S) {
-    switch (r) {
-        case 5: run_sweep<5>(c, S); break;
-        case 4: run_sweep<4>(c, S); break;
-        case 3: run_sweep<3>(c, S); break;
-        case 2: run_sweep<2>(c, S); break;
-        default: run_sweep<1>(c, S); break;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // the persistent tile kernel
 // ---------------------------------------------------------------------------
@@ -445,13 +495,18 @@ __device__ __forceinline__ void tile_coords(const TmaGeom &g, long long ti, long
     }
 }
 
-__global__ void __launch_bounds__(kTileThreads, 1)
+template <int R>
+__global__ void __maxnreg__(224)
     tile_pass_kernel(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst,
                      const TileArgs A) {
-    extern __shared__ __align__(1024) unsigned char sm[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
-    int *s_hb = reinterpret_cast<int *>(sm + 16);
-    int *s_contrib = reinterpret_cast<int *>(sm + 16 + 4 * kMaxTileBits);
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    // the 128-byte swizzle needs 1024-byte aligned tile buffers: align the base
+    unsigned char *sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm);          // [kMaxTileBuffers]
+    uint64_t *empty = full + kMaxTileBuffers;                    // [kMaxTileBuffers]
+    int *s_bad = reinterpret_cast<int *>(sm + 48);
+    int *s_hb = reinterpret_cast<int *>(sm + 64);
+    int *s_contrib = s_hb + kMaxTileBits;
     Sweep *s_sweeps = reinterpret_cast<Sweep *>(sm + A.off_desc);
     const TilePass &P = *A.pass;
     const int n_sweeps = P.n_sweeps, n_micro = P.n_micro;
@@ -459,15 +514,15 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     DiagDesc *s_diags = reinterpret_cast<DiagDesc *>(s_micro + n_micro);
     float2 *cs = reinterpret_cast<float2 *>(sm + A.off_consts);
     float2 *roots = reinterpret_cast<float2 *>(sm + A.off_roots);
-    float2 *bufs[2] = {reinterpret_cast<float2 *>(sm + A.off_buf0), reinterpret_cast<float2 *>(sm + A.off_buf1)};
+    float2 *buf0 = reinterpret_cast<float2 *>(sm + A.off_buf0);
+    const int NB = A.n_buf;
     const int tid = threadIdx.x;
     const int L = P.L, H = P.H, T = P.T;
-    const int rows = 1 << H;
-    const uint32_t row_bytes = 8u << L;
+    const int tile_elems = 1 << T;
     const uint32_t tile_bytes = 8u << T;
     const long long total = A.n_tiles * (long long)A.batch;
 
-    // stage the pass descriptor and constants in shared memory
+    // stage the pass descriptor and constants in shared memory (all threads)
     {
         const int *src = reinterpret_cast<const int *>(P.sweeps);
         int *dst = reinterpret_cast<int *>(s_sweeps);
@@ -490,54 +545,85 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         s_contrib[tid] = P.smem_contrib[tid];
     }
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int b = 0; b < kMaxTileBuffers; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], 1);
+        }
         fence_mbar_init();
     }
     fence_proxy_async();
     __syncthreads();
-
-    long long tile = blockIdx.x;
-    if (tile >= total) return;
+    if ((long long)blockIdx.x >= total) return;
     const int warp = tid >> 5, lane = tid & 31;
+    const long long stride = gridDim.x;
+    const int n_mine = (int)((total - 1 - blockIdx.x) / stride + 1);   // tiles of this CTA
 
-    // warp 0 issues the copies
-    auto issue_load = [&](long long t, float2 *dstbuf, uint64_t *b) {
-        const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
-        if (A.use_tma) {
-            if (lane == 0) {
-                mbar_arrive_expect_tx(b, tile_bytes);
-                int c[5];
-                tile_coords(A.geo, ti, bi, c);
-                tma_load_5d(dstbuf, &tm_src, c, b);
+    if (warp == kTileThreads / 32) {
+        // ------------------------------ producer ------------------------------
+        const int rows = 1 << H;
+        const uint32_t row_bytes = 8u << L;
+        auto load = [&](int k, float2 *dstbuf, uint64_t *b) {
+            const long long t = blockIdx.x + (long long)k * stride;
+            const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
+            if (A.use_tma) {
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(b, tile_bytes);
+                    int c[5];
+                    tile_coords(A.geo, ti, bi, c);
+                    tma_load_5d(dstbuf, &tm_src, c, b);
+                }
+            } else {
+                const float2 *src = A.src + bi * A.state_elems + tile_base(A, ti);
+                if (lane == 0) mbar_arrive_expect_tx(b, tile_bytes);
+                __syncwarp();
+                for (int r = lane; r < rows; r += 32)
+                    bulk_g2s(dstbuf + ((size_t)r << L), src + row_offset(r, H, s_hb), row_bytes, b);
             }
-        } else {
-            const float2 *src = A.src + bi * A.state_elems + tile_base(A, ti);
-            if (lane == 0) mbar_arrive_expect_tx(b, tile_bytes);
-            __syncwarp();
-            for (int r = lane; r < rows; r += 32)
-                bulk_g2s(dstbuf + ((size_t)r << L), src + row_offset(r, H, s_hb), row_bytes, b);
-        }
-    };
-    auto issue_store = [&](long long t, float2 *srcbuf) {
-        const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
-        if (A.use_tma) {
-            if (lane == 0) {
-                int c[5];
-                tile_coords(A.geo, ti, bi, c);
-                tma_store_5d(&tm_dst, c, srcbuf);
-                bulk_commit();
+        };
+        auto store = [&](int k, float2 *srcbuf) {
+            const long long t = blockIdx.x + (long long)k * stride;
+            const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
+            if (A.use_tma) {
+                if (lane == 0) {
+                    int c[5];
+                    tile_coords(A.geo, ti, bi, c);
+                    tma_store_5d(&tm_dst, c, srcbuf);
+                }
+            } else {
+                float2 *dst = A.dst + bi * A.state_elems + tile_base(A, ti);
+                for (int r = lane; r < rows; r += 32)
+                    bulk_s2g(dst + row_offset(r, H, s_hb), srcbuf + ((size_t)r << L), row_bytes);
             }
-        } else {
-            float2 *dst = A.dst + bi * A.state_elems + tile_base(A, ti);
-            for (int r = lane; r < rows; r += 32)
-                bulk_s2g(dst + row_offset(r, H, s_hb), srcbuf + ((size_t)r << L), row_bytes);
             bulk_commit();
+        };
+        bool ok = true;
+        int k = 0;
+        for (; k < n_mine && ok; ++k) {
+            const int b = k % NB, use = k / NB;
+            float2 *B = buf0 + (size_t)b * tile_elems;
+            if (use > 0) {
+                // tile k-NB in this buffer: wait until computed, store it, wait until the store has read smem
+                ok = mbar_wait_bounded(&empty[b], (uint32_t)((use - 1) & 1));
+                if (!ok) break;
+                store(k - NB, B);
+                bulk_wait_read0();
+                __syncwarp();
+            }
+            load(k, B, &full[b]);
         }
-    };
+        // drain the last tiles
+        for (int kk = (n_mine > NB ? n_mine - NB : 0); kk < n_mine && ok; ++kk) {
+            const int b = kk % NB, use = kk / NB;
+            ok = mbar_wait_bounded(&empty[b], (uint32_t)(use & 1));
+            if (!ok) break;
+            store(kk, buf0 + (size_t)b * tile_elems);
+        }
+        if (!ok && lane == 0) atomicCAS(A.err, 0, (int)QS_ERR_TIMEOUT);
+        bulk_wait_all0();
+        return;
+    }
 
-    if (warp == 0) issue_load(tile, bufs[0], &bar[0]);
-
+    // ------------------------------ compute ------------------------------
     SweepCtx c;
     c.T = T;
     c.L = L;
@@ -547,56 +633,55 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     c.roots = roots;
     c.micro = s_micro;
     c.diags = s_diags;
-
-    bool failed = false;
-    int fail_k = 0;
-    for (int k = 0; tile < total; tile += gridDim.x, ++k) {
-        const int cur = k & 1;
-        float2 *B = bufs[cur];
-        const long long next = tile + gridDim.x;
-        if (next < total && warp == 0) {
-            bulk_wait_read0();   // buffer cur^1: the previous tile's stores have read it
-            __syncwarp();
-            issue_load(next, bufs[cur ^ 1], &bar[cur ^ 1]);
+    for (int k = 0; k < n_mine; ++k) {
+        const int b = k % NB, use = k / NB;
+        float2 *B = buf0 + (size_t)b * tile_elems;
+        const bool ok = mbar_wait_bounded(&full[b], (uint32_t)(use & 1));
+        // uniform decision among the compute warps
+        if (tid == 0) *s_bad = 0;
+        compute_sync();
+        if (!ok) *s_bad = 1;
+        compute_sync();
+        const int bad = *s_bad;
+        if (bad) {
+            if (tid == 0) atomicCAS(A.err, 0, (int)QS_ERR_TIMEOUT);
+            return;
         }
-        const bool ok = mbar_wait_bounded(&bar[cur], (uint32_t)((k >> 1) & 1));
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            fail_k = k;
-            break;
-        }
-        const long long bi = tile / A.n_tiles, ti = tile - bi * A.n_tiles;
+        const long long t = blockIdx.x + (long long)k * stride;
+        const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
+        (void)bi;
         c.buf = B;
         c.tile_gbase = tile_base(A, ti);
         for (int s = 0; s < n_sweeps; ++s) {
-            run_sweep_r(s_sweeps[s].r, c, s_sweeps[s]);
-            __syncthreads();
+            run_sweep<R>(c, s_sweeps[s]);
+            compute_sync();
         }
-        (void)bi;
         fence_proxy_async();
-        __syncthreads();
-        if (warp == 0) issue_store(tile, B);
+        compute_sync();
+        if (tid == 0) mbar_arrive(&empty[b]);
     }
-    if (failed) {
-        if (tid == 0) atomicCAS(A.err, 0, (int)QS_ERR_TIMEOUT);
-        // let this tile's load and the prefetched one land (bounded) before leaving
-        if (warp == 0 && lane == 0) {
-            mbar_wait_bounded(&bar[fail_k & 1], (uint32_t)((fail_k >> 1) & 1));
-            if (tile + gridDim.x < total)
-                mbar_wait_bounded(&bar[(fail_k + 1) & 1], (uint32_t)(((fail_k + 1) >> 1) & 1));
-        }
-    }
-    if (warp == 0) bulk_wait_all0();
 }
 
 void tile_kernel_smem_config(int bytes) {
-    cudaFuncSetAttribute(tile_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(tile_pass_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(tile_pass_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(tile_pass_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(tile_pass_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(tile_pass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-cudaError_t launch_tile_pass(const TileArgs &A, const void *tm_src, const void *tm_dst, int grid, int smem_bytes,
-                             cudaStream_t st) {
-    tile_pass_kernel<<<grid, kTileThreads, smem_bytes, st>>>(*reinterpret_cast<const CUtensorMap *>(tm_src),
-                                                             *reinterpret_cast<const CUtensorMap *>(tm_dst), A);
+cudaError_t launch_tile_pass(int R, const TileArgs &A, const void *tm_src, const void *tm_dst, int grid,
+                             int smem_bytes, cudaStream_t st) {
+    const CUtensorMap &ms = *reinterpret_cast<const CUtensorMap *>(tm_src);
+    const CUtensorMap &md = *reinterpret_cast<const CUtensorMap *>(tm_dst);
+    const int nt = kTileThreads + 32;
+    switch (R) {
+        case 5: tile_pass_kernel<5><<<grid, nt, smem_bytes, st>>>(ms, md, A); break;
+        case 4: tile_pass_kernel<4><<<grid, nt, smem_bytes, st>>>(ms, md, A); break;
+        case 3: tile_pass_kernel<3><<<grid, nt, smem_bytes, st>>>(ms, md, A); break;
+        case 2: tile_pass_kernel<2><<<grid, nt, smem_bytes, st>>>(ms, md, A); break;
+        default: tile_pass_kernel<1><<<grid, nt, smem_bytes, st>>>(ms, md, A); break;
+    }
     return cudaGetLastError();
 }
 

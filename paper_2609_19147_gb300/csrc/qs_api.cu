@@ -321,9 +321,10 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     for (int b = 0; b < st->n; ++b)
         if (!((tilebits >> b) & 1)) A.outer_pos[A.n_outer++] = b;
     A.err = st->d_err;
-    // shared memory: [barriers, hb, contrib | descriptor | constants | roots | 2 tile buffers]
+    // shared memory (after aligning the base to 1024 bytes in the kernel):
+    // [mbarriers, flags, hb, contrib | descriptor | constants | roots | 2-3 tile buffers]
     auto al = [](int v, int a) { return (v + a - 1) / a * a; };
-    int off = 128;
+    int off = 256;
     A.off_desc = off;
     off += tp.n_sweeps * (int)sizeof(Sweep) + tp.n_micro * (int)sizeof(MicroOp) + kMaxDiag * (int)sizeof(DiagDesc);
     off = al(off, 128);
@@ -336,10 +337,11 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     const int buf_bytes = 8 << tp.T;
     off = al(off, 1024);
     A.off_buf0 = off;
-    off += buf_bytes;
-    A.off_buf1 = off;
-    off += buf_bytes;
-    if (off > 227 * 1024) return fail(QS_ERR_INTERNAL, "tile pass needs too much shared memory");
+    const int limit = 227 * 1024 - 1024;   // 1 KB reserved for the base alignment
+    A.n_buf = (off + 3 * buf_bytes <= limit) ? 3 : 2;
+    off += A.n_buf * buf_bytes;
+    if (off > limit) return fail(QS_ERR_INTERNAL, "tile pass needs too much shared memory");
+    off += 1024;
     static int configured[16] = {0};
     if (configured[st->dev] < 227 * 1024) {
         tile_kernel_smem_config(227 * 1024);
@@ -366,7 +368,7 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     int grid = (int)std::min<long long>(total, g_num_sms[st->dev] > 0 ? g_num_sms[st->dev] : 148);
     cudaEvent_t ev;
     prof_begin(st, &ev);
-    QS_CUDA(launch_tile_pass(A, &tms, &tmd, grid, off, st->stream));
+    QS_CUDA(launch_tile_pass(tp.sweeps[0].r, A, &tms, &tmd, grid, off, st->stream));
     prof_end(st, ev, "tile_pass", 16.0 * (double)st->elems * batch);
     return QS_OK;
 }

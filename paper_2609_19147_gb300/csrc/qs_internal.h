@@ -39,7 +39,8 @@ constexpr int kMaxSweeps = 40;
 constexpr int kMaxMicro = 320;
 constexpr int kMaxConst = 5120;      // complex64 constants per pass (40 KB)
 constexpr int kMaxDiag = 4;
-constexpr int kTileThreads = 256;
+constexpr int kTileThreads = 256;     // compute threads per CTA (plus one producer warp)
+constexpr int kMaxTileBuffers = 3;
 
 // Diagonal phase (Sec. 5.1 "Phase-LUT diagonal layers").  The phase of basis
 // index x is
@@ -71,6 +72,8 @@ enum MicroKind : int32_t {
     MK_QFT = 3,   // QFT stage: H on group bit a (= global bit p), then twiddle
                   // exp(i pi x_p (x & bits[lo, p)) / 2^p); group part at cst
     MK_H = 4,     // Hadamard on group bit a (sign-only butterfly)
+    MK_RXC = 5,   // [[c, i s], [i s, c]] on group bit a (RX family): consts c, s
+    MK_U1R = 6,   // real 2x2 on group bit a (RY family): consts m00, m01, m10, m11
 };
 
 struct MicroOp {

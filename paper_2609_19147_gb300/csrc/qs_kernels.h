@@ -29,14 +29,15 @@ struct TileArgs {
     int batch;
     int n_outer;               // number of non-tile index bits
     int outer_pos[kMaxQubits]; // their positions, ascending
-    int off_desc, off_consts, off_roots, off_buf0, off_buf1;   // dynamic smem layout
+    int off_desc, off_consts, off_roots, off_buf0;   // dynamic smem layout
+    int n_buf;                 // tile buffers (2 or 3), each 8 * 2^T bytes from off_buf0
     int use_tma;               // 1: one tensor copy per tile; 0: one bulk copy per row
     TmaGeom geo;
     int *err;                  // device status word
 };
 
-cudaError_t launch_tile_pass(const TileArgs &A, const void *tm_src, const void *tm_dst, int grid, int smem_bytes,
-                             cudaStream_t st);
+cudaError_t launch_tile_pass(int R, const TileArgs &A, const void *tm_src, const void *tm_dst, int grid,
+                             int smem_bytes, cudaStream_t st);
 void tile_kernel_smem_config(int bytes);
 
 // per-gate kernels: op per state (op_stride = 1) or shared (op_stride = 0)

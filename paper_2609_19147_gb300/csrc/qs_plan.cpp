@@ -896,16 +896,32 @@ struct PassBuilder {
                 mo.cval = f.cval;
                 mo.cst = (int)cst.size();
                 if (f.kind == F_U1) {
-                    bool h = f.cmask == 0 && f.m[0] == cd(kSqrtHalf, 0) && f.m[1] == cd(kSqrtHalf, 0) &&
-                             f.m[2] == cd(kSqrtHalf, 0) && f.m[3] == cd(-kSqrtHalf, 0);
-                    mo.kind = h ? MK_H : MK_U1;
-                    if (!h)
+                    const cd *m = f.m;
+                    bool h = f.cmask == 0 && m[0] == cd(kSqrtHalf, 0) && m[1] == cd(kSqrtHalf, 0) &&
+                             m[2] == cd(kSqrtHalf, 0) && m[3] == cd(-kSqrtHalf, 0);
+                    // RX family [[c, i s], [i s, c]] and real matrices have cheaper forms
+                    bool rxc = f.cmask == 0 && m[0].imag() == 0 && m[0] == m[3] && m[1].real() == 0 &&
+                               m[1] == m[2];
+                    bool real = f.cmask == 0 && m[0].imag() == 0 && m[1].imag() == 0 && m[2].imag() == 0 &&
+                                m[3].imag() == 0;
+                    if (h) {
+                        mo.kind = MK_H;
+                    } else if (rxc) {
+                        mo.kind = MK_RXC;
+                        cst.push_back(float2{(float)m[0].real(), (float)m[1].imag()});
+                    } else if (real) {
+                        mo.kind = MK_U1R;
+                        cst.push_back(float2{(float)m[0].real(), (float)m[1].real()});
+                        cst.push_back(float2{(float)m[2].real(), (float)m[3].real()});
+                    } else {
+                        mo.kind = MK_U1;
                         for (int e = 0; e < 4; ++e) {
                             float2 v;
-                            v.x = (float)f.m[e].real();
-                            v.y = (float)f.m[e].imag();
+                            v.x = (float)m[e].real();
+                            v.y = (float)m[e].imag();
                             cst.push_back(v);
                         }
+                    }
                 } else if (f.kind == F_U2) {
                     mo.kind = MK_U2;
                     for (int e = 0; e < 16; ++e) {
@@ -1070,7 +1086,8 @@ qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, co
     if (T > n) T = n;
     if (L > T) L = T;
     if (L < 1) L = 1;
-    const int R = std::min(kMaxGroup, T);
+    int R = o.group_qubits > 0 ? std::min(o.group_qubits, kMaxGroup) : kMaxGroup;
+    R = std::min(R, T);
 
     // split oversized diagonals; pre-plan each diagonal's tables
     std::vector<FOp> ops2;
@@ -1325,11 +1342,12 @@ std::string Plan::describe() const {
         const HostPass &hp = passes[i];
         if (hp.type == HostPass::TILE) {
             const TilePass &t = hp.tile;
-            int cnt[5] = {0, 0, 0, 0, 0};
+            int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             for (int k = 0; k < t.n_micro; ++k) cnt[t.micro[k].kind]++;
             os << "TILE T=" << t.T << " L=" << t.L << " hb=[";
             for (int k = 0; k < t.H; ++k) os << (k ? "," : "") << t.hb[k];
-            os << "] sweeps=" << t.n_sweeps << " U1=" << cnt[MK_U1] + cnt[MK_H] << " U2=" << cnt[MK_U2]
+            os << "] tma=" << (hp.tma.ok ? 1 : 0) << " sweeps=" << t.n_sweeps
+               << " U1=" << cnt[MK_U1] + cnt[MK_H] + cnt[MK_RXC] + cnt[MK_U1R] << " U2=" << cnt[MK_U2]
                << " DIAG=" << cnt[MK_DIAG] << " QFT=" << cnt[MK_QFT] << " consts=" << t.n_const << "\n";
         } else if (hp.type == HostPass::PERM) {
             os << "PERM xor=" << hp.perm.xor_mask << "\n";
