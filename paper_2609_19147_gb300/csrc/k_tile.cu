@@ -28,6 +28,8 @@
 // own copies land and returns.
 #include <cuda.h>
 
+#include <string>
+
 #include "qs_internal.h"
 #include "qs_kernels.h"
 
@@ -496,7 +498,7 @@ __device__ __forceinline__ void tile_coords(const TmaGeom &g, long long ti, long
 }
 
 template <int R>
-__global__ void __maxnreg__(224)
+__global__ void __maxnreg__(208)
     tile_pass_kernel(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst,
                      const TileArgs A) {
     extern __shared__ __align__(1024) unsigned char sm_raw[];
@@ -675,6 +677,7 @@ cudaError_t launch_tile_pass(int R, const TileArgs &A, const void *tm_src, const
     const CUtensorMap &ms = *reinterpret_cast<const CUtensorMap *>(tm_src);
     const CUtensorMap &md = *reinterpret_cast<const CUtensorMap *>(tm_dst);
     const int nt = kTileThreads + 32;
+    cudaGetLastError();
     switch (R) {
         case 5: tile_pass_kernel<5><<<grid, nt, smem_bytes, st>>>(ms, md, A); break;
         case 4: tile_pass_kernel<4><<<grid, nt, smem_bytes, st>>>(ms, md, A); break;
@@ -683,6 +686,22 @@ cudaError_t launch_tile_pass(int R, const TileArgs &A, const void *tm_src, const
         default: tile_pass_kernel<1><<<grid, nt, smem_bytes, st>>>(ms, md, A); break;
     }
     return cudaGetLastError();
+}
+
+std::string tile_kernel_attrs(int R) {
+    cudaFuncAttributes fa;
+    cudaError_t e;
+    switch (R) {
+        case 5: e = cudaFuncGetAttributes(&fa, tile_pass_kernel<5>); break;
+        case 4: e = cudaFuncGetAttributes(&fa, tile_pass_kernel<4>); break;
+        case 3: e = cudaFuncGetAttributes(&fa, tile_pass_kernel<3>); break;
+        case 2: e = cudaFuncGetAttributes(&fa, tile_pass_kernel<2>); break;
+        default: e = cudaFuncGetAttributes(&fa, tile_pass_kernel<1>); break;
+    }
+    if (e != cudaSuccess) return "attrs unavailable";
+    return "regs=" + std::to_string(fa.numRegs) + " maxThreads=" + std::to_string(fa.maxThreadsPerBlock) +
+           " maxDynSmem=" + std::to_string(fa.maxDynamicSharedSizeBytes) +
+           " staticSmem=" + std::to_string(fa.sharedSizeBytes) + " localBytes=" + std::to_string(fa.localSizeBytes);
 }
 
 }  // namespace qs

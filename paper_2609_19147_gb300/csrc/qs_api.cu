@@ -368,7 +368,12 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     int grid = (int)std::min<long long>(total, g_num_sms[st->dev] > 0 ? g_num_sms[st->dev] : 148);
     cudaEvent_t ev;
     prof_begin(st, &ev);
-    QS_CUDA(launch_tile_pass(tp.sweeps[0].r, A, &tms, &tmd, grid, off, st->stream));
+    {
+        cudaError_t e = launch_tile_pass(tp.sweeps[0].r, A, &tms, &tmd, grid, off, st->stream);
+        if (e != cudaSuccess)
+            return fail(QS_ERR_CUDA, std::string("tile pass launch: ") + cudaGetErrorString(e) + " (smem=" +
+                                         std::to_string(off) + " " + tile_kernel_attrs(tp.sweeps[0].r) + ")");
+    }
     prof_end(st, ev, "tile_pass", 16.0 * (double)st->elems * batch);
     return QS_OK;
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <string>
 #include "qs_internal.h"
 
 namespace qs {
@@ -39,6 +40,7 @@ struct TileArgs {
 cudaError_t launch_tile_pass(int R, const TileArgs &A, const void *tm_src, const void *tm_dst, int grid,
                              int smem_bytes, cudaStream_t st);
 void tile_kernel_smem_config(int bytes);
+std::string tile_kernel_attrs(int R);
 
 // per-gate kernels: op per state (op_stride = 1) or shared (op_stride = 0)
 struct PgArgs {
