@@ -9,11 +9,11 @@
 // box of extent 1 in every gap).  When the bit set needs more than 5 dims the
 // pass falls back to one bulk copy per 2^L-amplitude row.
 //
-// Warp roles: one producer warp issues every copy and waits on nothing but
-// mbarriers; 8 compute warps process tiles.  Tiles rotate through 2-3 shared
-// buffers with "full" (TMA complete_tx) and "empty" (compute done) mbarriers,
-// so loads of the next tiles and the store of the previous one overlap the
-// compute of the current tile.
+// Tiles rotate through 2-3 shared buffers: while the 8 warps process tile k,
+// the load of tile k+1 and the stores of tiles k-1 (and k-2) are in flight.
+// Thread 0 issues the copies; with 3 buffers the buffer it refills was
+// stored two tiles ago, so waiting for that store to have read shared memory
+// does not stall.
 //
 // Between load and store the tile goes through "sweeps": every compute thread
 // holds 2^R amplitudes that differ in R tile bits (registers) and applies the
@@ -111,13 +111,7 @@ __device__ __forceinline__ void fence_proxy_async() {
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-// barrier among the compute warps only (the producer warp never joins)
-__device__ __forceinline__ void compute_sync() {
-    asm volatile("bar.sync 1, %0;" ::"r"(kTileThreads) : "memory");
-}
+
 
 // ---------------------------------------------------------------------------
 // complex helpers
@@ -498,15 +492,13 @@ __device__ __forceinline__ void tile_coords(const TmaGeom &g, long long ti, long
 }
 
 template <int R>
-__global__ void __maxnreg__(208)
+__global__ void __launch_bounds__(kTileThreads, 1)
     tile_pass_kernel(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst,
                      const TileArgs A) {
     extern __shared__ __align__(1024) unsigned char sm_raw[];
     // the 128-byte swizzle needs 1024-byte aligned tile buffers: align the base
     unsigned char *sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
     uint64_t *full = reinterpret_cast<uint64_t *>(sm);          // [kMaxTileBuffers]
-    uint64_t *empty = full + kMaxTileBuffers;                    // [kMaxTileBuffers]
-    int *s_bad = reinterpret_cast<int *>(sm + 48);
     int *s_hb = reinterpret_cast<int *>(sm + 64);
     int *s_contrib = s_hb + kMaxTileBits;
     Sweep *s_sweeps = reinterpret_cast<Sweep *>(sm + A.off_desc);
@@ -524,108 +516,75 @@ __global__ void __maxnreg__(208)
     const uint32_t tile_bytes = 8u << T;
     const long long total = A.n_tiles * (long long)A.batch;
 
-    // stage the pass descriptor and constants in shared memory (all threads)
+    // stage the pass descriptor and constants in shared memory
     {
         const int *src = reinterpret_cast<const int *>(P.sweeps);
         int *dst = reinterpret_cast<int *>(s_sweeps);
         const int nw_s = n_sweeps * (int)(sizeof(Sweep) / 4);
-        for (int i = tid; i < nw_s; i += blockDim.x) dst[i] = src[i];
+        for (int i = tid; i < nw_s; i += kTileThreads) dst[i] = src[i];
         src = reinterpret_cast<const int *>(P.micro);
         dst = reinterpret_cast<int *>(s_micro);
         const int nw_m = n_micro * (int)(sizeof(MicroOp) / 4);
-        for (int i = tid; i < nw_m; i += blockDim.x) dst[i] = src[i];
+        for (int i = tid; i < nw_m; i += kTileThreads) dst[i] = src[i];
         src = reinterpret_cast<const int *>(P.diags);
         dst = reinterpret_cast<int *>(s_diags);
         const int nw_d = kMaxDiag * (int)(sizeof(DiagDesc) / 4);
-        for (int i = tid; i < nw_d; i += blockDim.x) dst[i] = src[i];
+        for (int i = tid; i < nw_d; i += kTileThreads) dst[i] = src[i];
     }
-    for (int i = tid; i < P.n_const; i += blockDim.x) cs[i] = A.consts[i];
+    for (int i = tid; i < P.n_const; i += kTileThreads) cs[i] = A.consts[i];
     if (A.off_roots)
-        for (int i = tid; i < kRootsEntries; i += blockDim.x) roots[i] = A.roots[i];
+        for (int i = tid; i < kRootsEntries; i += kTileThreads) roots[i] = A.roots[i];
     if (tid < kMaxTileBits) {
         s_hb[tid] = P.hb[tid];
         s_contrib[tid] = P.smem_contrib[tid];
     }
     if (tid == 0) {
-        for (int b = 0; b < kMaxTileBuffers; ++b) {
-            mbar_init(&full[b], 1);
-            mbar_init(&empty[b], 1);
-        }
+        for (int b = 0; b < kMaxTileBuffers; ++b) mbar_init(&full[b], 1);
         fence_mbar_init();
     }
     fence_proxy_async();
     __syncthreads();
     if ((long long)blockIdx.x >= total) return;
-    const int warp = tid >> 5, lane = tid & 31;
     const long long stride = gridDim.x;
     const int n_mine = (int)((total - 1 - blockIdx.x) / stride + 1);   // tiles of this CTA
+    const int rows = 1 << H;
+    const uint32_t row_bytes = 8u << L;
 
-    if (warp == kTileThreads / 32) {
-        // ------------------------------ producer ------------------------------
-        const int rows = 1 << H;
-        const uint32_t row_bytes = 8u << L;
-        auto load = [&](int k, float2 *dstbuf, uint64_t *b) {
-            const long long t = blockIdx.x + (long long)k * stride;
-            const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
-            if (A.use_tma) {
-                if (lane == 0) {
-                    mbar_arrive_expect_tx(b, tile_bytes);
-                    int c[5];
-                    tile_coords(A.geo, ti, bi, c);
-                    tma_load_5d(dstbuf, &tm_src, c, b);
-                }
-            } else {
-                const float2 *src = A.src + bi * A.state_elems + tile_base(A, ti);
-                if (lane == 0) mbar_arrive_expect_tx(b, tile_bytes);
-                __syncwarp();
-                for (int r = lane; r < rows; r += 32)
-                    bulk_g2s(dstbuf + ((size_t)r << L), src + row_offset(r, H, s_hb), row_bytes, b);
-            }
-        };
-        auto store = [&](int k, float2 *srcbuf) {
-            const long long t = blockIdx.x + (long long)k * stride;
-            const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
-            if (A.use_tma) {
-                if (lane == 0) {
-                    int c[5];
-                    tile_coords(A.geo, ti, bi, c);
-                    tma_store_5d(&tm_dst, c, srcbuf);
-                }
-            } else {
-                float2 *dst = A.dst + bi * A.state_elems + tile_base(A, ti);
-                for (int r = lane; r < rows; r += 32)
-                    bulk_s2g(dst + row_offset(r, H, s_hb), srcbuf + ((size_t)r << L), row_bytes);
-            }
-            bulk_commit();
-        };
-        bool ok = true;
-        int k = 0;
-        for (; k < n_mine && ok; ++k) {
-            const int b = k % NB, use = k / NB;
-            float2 *B = buf0 + (size_t)b * tile_elems;
-            if (use > 0) {
-                // tile k-NB in this buffer: wait until computed, store it, wait until the store has read smem
-                ok = mbar_wait_bounded(&empty[b], (uint32_t)((use - 1) & 1));
-                if (!ok) break;
-                store(k - NB, B);
-                bulk_wait_read0();
-                __syncwarp();
-            }
-            load(k, B, &full[b]);
+    // thread 0 issues every copy (TMA path: one instruction per tile)
+    auto load = [&](int k) {
+        const int b = k % NB;
+        float2 *dstbuf = buf0 + (size_t)b * tile_elems;
+        const long long t = blockIdx.x + (long long)k * stride;
+        const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
+        mbar_arrive_expect_tx(&full[b], tile_bytes);
+        if (A.use_tma) {
+            int c[5];
+            tile_coords(A.geo, ti, bi, c);
+            tma_load_5d(dstbuf, &tm_src, c, &full[b]);
+        } else {
+            const float2 *src = A.src + bi * A.state_elems + tile_base(A, ti);
+            for (int r = 0; r < rows; ++r)
+                bulk_g2s(dstbuf + ((size_t)r << L), src + row_offset(r, H, s_hb), row_bytes, &full[b]);
         }
-        // drain the last tiles
-        for (int kk = (n_mine > NB ? n_mine - NB : 0); kk < n_mine && ok; ++kk) {
-            const int b = kk % NB, use = kk / NB;
-            ok = mbar_wait_bounded(&empty[b], (uint32_t)(use & 1));
-            if (!ok) break;
-            store(kk, buf0 + (size_t)b * tile_elems);
+    };
+    auto store = [&](int k) {
+        const float2 *srcbuf = buf0 + (size_t)(k % NB) * tile_elems;
+        const long long t = blockIdx.x + (long long)k * stride;
+        const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
+        if (A.use_tma) {
+            int c[5];
+            tile_coords(A.geo, ti, bi, c);
+            tma_store_5d(&tm_dst, c, srcbuf);
+        } else {
+            float2 *dst = A.dst + bi * A.state_elems + tile_base(A, ti);
+            for (int r = 0; r < rows; ++r)
+                bulk_s2g(dst + row_offset(r, H, s_hb), srcbuf + ((size_t)r << L), row_bytes);
         }
-        if (!ok && lane == 0) atomicCAS(A.err, 0, (int)QS_ERR_TIMEOUT);
-        bulk_wait_all0();
-        return;
-    }
+        bulk_commit();
+    };
 
-    // ------------------------------ compute ------------------------------
+    if (tid == 0) load(0);
+
     SweepCtx c;
     c.T = T;
     c.L = L;
@@ -636,32 +595,35 @@ __global__ void __maxnreg__(208)
     c.micro = s_micro;
     c.diags = s_diags;
     for (int k = 0; k < n_mine; ++k) {
-        const int b = k % NB, use = k / NB;
-        float2 *B = buf0 + (size_t)b * tile_elems;
-        const bool ok = mbar_wait_bounded(&full[b], (uint32_t)(use & 1));
-        // uniform decision among the compute warps
-        if (tid == 0) *s_bad = 0;
-        compute_sync();
-        if (!ok) *s_bad = 1;
-        compute_sync();
-        const int bad = *s_bad;
-        if (bad) {
-            if (tid == 0) atomicCAS(A.err, 0, (int)QS_ERR_TIMEOUT);
+        if (tid == 0 && k + 1 < n_mine) {
+            // buffer (k+1) % NB last held tile k+1-NB: its store must have read smem.
+            // With 3 buffers that store is the older of the two outstanding ones.
+            if (NB >= 3) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+            else bulk_wait_read0();
+            load(k + 1);
+        }
+        const bool ok = mbar_wait_bounded(&full[k % NB], (uint32_t)((k / NB) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicCAS(A.err, 0, (int)QS_ERR_TIMEOUT);
+                if (k + 1 < n_mine) mbar_wait_bounded(&full[(k + 1) % NB], (uint32_t)(((k + 1) / NB) & 1));
+                bulk_wait_all0();
+            }
             return;
         }
         const long long t = blockIdx.x + (long long)k * stride;
-        const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
-        (void)bi;
-        c.buf = B;
+        const long long ti = t % A.n_tiles;
+        c.buf = buf0 + (size_t)(k % NB) * tile_elems;
         c.tile_gbase = tile_base(A, ti);
         for (int s = 0; s < n_sweeps; ++s) {
             run_sweep<R>(c, s_sweeps[s]);
-            compute_sync();
+            __syncthreads();
         }
         fence_proxy_async();
-        compute_sync();
-        if (tid == 0) mbar_arrive(&empty[b]);
+        __syncthreads();
+        if (tid == 0) store(k);
     }
+    if (tid == 0) bulk_wait_all0();
 }
 
 void tile_kernel_smem_config(int bytes) {
@@ -676,7 +638,7 @@ cudaError_t launch_tile_pass(int R, const TileArgs &A, const void *tm_src, const
                              int smem_bytes, cudaStream_t st) {
     const CUtensorMap &ms = *reinterpret_cast<const CUtensorMap *>(tm_src);
     const CUtensorMap &md = *reinterpret_cast<const CUtensorMap *>(tm_dst);
-    const int nt = kTileThreads + 32;
+    const int nt = kTileThreads;
     cudaGetLastError();
     switch (R) {
         case 5: tile_pass_kernel<5><<<grid, nt, smem_bytes, st>>>(ms, md, A); break;
