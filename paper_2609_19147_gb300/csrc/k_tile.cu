@@ -440,7 +440,48 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S) {
                     const uint32_t dyn_s = (uint32_t)op.a, dyn_g = (uint32_t)op.b;
                     float2 stat = d.pad0 ? make_float2(d.gph_re, d.gph_im) : make_float2(1.f, 0.f);
                     stat = diag_part(d, gbase, c.cs, ~dyn_s, ~dyn_g, stat);
-                    if (dyn_s | dyn_g) {
+                    if (dyn_g == 0 && __popc(dyn_s) <= 2 && dyn_s) {
+                        // fast path: the varying tables' indices are the item's base
+                        // index OR the group bits' contributions (disjoint bits)
+                        const int s0 = __ffs(dyn_s) - 1;
+                        const int s1 = (dyn_s & (dyn_s - 1)) ? __ffs(dyn_s & (dyn_s - 1)) - 1 : -1;
+                        const uint32_t m0 = (1u << d.slice_w[s0]) - 1;
+                        const int lo0 = d.slice_lo[s0];
+                        const float2 *t0 = c.cs + d.slice_off[s0];
+                        const uint32_t b0 = (uint32_t)(gbase >> lo0) & m0;
+                        uint32_t q0[R];
+#pragma unroll
+                        for (int m = 0; m < R; ++m) q0[m] = (uint32_t)(G.gg[m] >> lo0) & m0;
+                        if (s1 < 0) {
+#pragma unroll
+                            for (int j = 0; j < (1 << R); ++j) {
+                                uint32_t i0 = b0;
+#pragma unroll
+                                for (int m = 0; m < R; ++m)
+                                    if ((j >> m) & 1) i0 |= q0[m];
+                                a[j] = cmul(a[j], cmul(stat, t0[i0]));
+                            }
+                        } else {
+                            const uint32_t m1 = (1u << d.slice_w[s1]) - 1;
+                            const int lo1 = d.slice_lo[s1];
+                            const float2 *t1 = c.cs + d.slice_off[s1];
+                            const uint32_t b1 = (uint32_t)(gbase >> lo1) & m1;
+                            uint32_t q1[R];
+#pragma unroll
+                            for (int m = 0; m < R; ++m) q1[m] = (uint32_t)(G.gg[m] >> lo1) & m1;
+#pragma unroll
+                            for (int j = 0; j < (1 << R); ++j) {
+                                uint32_t i0 = b0, i1 = b1;
+#pragma unroll
+                                for (int m = 0; m < R; ++m)
+                                    if ((j >> m) & 1) {
+                                        i0 |= q0[m];
+                                        i1 |= q1[m];
+                                    }
+                                a[j] = cmul(a[j], cmul(stat, cmul(t0[i0], t1[i1])));
+                            }
+                        }
+                    } else if (dyn_s | dyn_g) {
 #pragma unroll
                         for (int j = 0; j < (1 << R); ++j)
                             a[j] = cmul(a[j], diag_part(d, G.gidx(gbase, j), c.cs, dyn_s, dyn_g, stat));
@@ -583,7 +624,9 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         bulk_commit();
     };
 
-    if (tid == 0) load(0);
+    const int D = A.prefetch;
+    if (tid == 0)
+        for (int k = 0; k < D && k < n_mine; ++k) load(k);
 
     SweepCtx c;
     c.T = T;
@@ -595,18 +638,23 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     c.micro = s_micro;
     c.diags = s_diags;
     for (int k = 0; k < n_mine; ++k) {
-        if (tid == 0 && k + 1 < n_mine) {
-            // buffer (k+1) % NB last held tile k+1-NB: its store must have read smem.
-            // With 3 buffers that store is the older of the two outstanding ones.
-            if (NB >= 3) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-            else bulk_wait_read0();
-            load(k + 1);
+        if (tid == 0 && k + D < n_mine) {
+            // buffer (k+D) % NB last held tile k+D-NB, stored at the end of
+            // iteration k+D-NB: allow the NB-D-1 newer stores to stay in flight
+            switch (NB - D - 1) {
+                case 0: asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); break;
+                case 1: asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); break;
+                case 2: asm volatile("cp.async.bulk.wait_group.read 2;" ::: "memory"); break;
+                default: asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory"); break;
+            }
+            load(k + D);
         }
         const bool ok = mbar_wait_bounded(&full[k % NB], (uint32_t)((k / NB) & 1));
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicCAS(A.err, 0, (int)QS_ERR_TIMEOUT);
-                if (k + 1 < n_mine) mbar_wait_bounded(&full[(k + 1) % NB], (uint32_t)(((k + 1) / NB) & 1));
+                for (int kk = k + 1; kk < k + D && kk < n_mine; ++kk)
+                    mbar_wait_bounded(&full[kk % NB], (uint32_t)((kk / NB) & 1));
                 bulk_wait_all0();
             }
             return;

@@ -338,7 +338,11 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     off = al(off, 1024);
     A.off_buf0 = off;
     const int limit = 227 * 1024 - 1024;   // 1 KB reserved for the base alignment
-    A.n_buf = (off + 3 * buf_bytes <= limit) ? 3 : 2;
+    // as many tile buffers as fit (<= 6); keep ~128 KB of loads in flight
+    A.n_buf = std::min(6, (limit - off) / buf_bytes);
+    if (A.n_buf > kMaxTileBuffers) A.n_buf = kMaxTileBuffers;
+    if (A.n_buf < 2) return fail(QS_ERR_INTERNAL, "tile pass needs too much shared memory");
+    A.prefetch = std::max(1, A.n_buf - 2);
     off += A.n_buf * buf_bytes;
     if (off > limit) return fail(QS_ERR_INTERNAL, "tile pass needs too much shared memory");
     off += 1024;

@@ -40,7 +40,7 @@ constexpr int kMaxMicro = 320;
 constexpr int kMaxConst = 5120;      // complex64 constants per pass (40 KB)
 constexpr int kMaxDiag = 4;
 constexpr int kTileThreads = 256;     // threads per tile CTA
-constexpr int kMaxTileBuffers = 3;
+constexpr int kMaxTileBuffers = 8;
 
 // Diagonal phase (Sec. 5.1 "Phase-LUT diagonal layers").  The phase of basis
 // index x is
