@@ -388,7 +388,7 @@ __device__ __forceinline__ void sweep_store(const SweepCtx &c, bool vec, int sad
     }
 }
 
-template <int R>
+template <int R, int NT>
 __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S) {
     int gs[R];
     Grp<R> G;
@@ -400,7 +400,7 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S) {
     const int nb = c.T - R;
     const int n_items = 1 << nb;
     const bool vec = S.vec != 0;
-    for (int item = threadIdx.x; item < n_items; item += kTileThreads) {
+    for (int item = threadIdx.x; item < n_items; item += NT) {
         int saddr = 0;
         uint64_t gbase = c.tile_gbase;
         for (int i = 0; i < nb; ++i)
@@ -532,8 +532,8 @@ __device__ __forceinline__ void tile_coords(const TmaGeom &g, long long ti, long
     }
 }
 
-template <int R>
-__global__ void __launch_bounds__(kTileThreads, 1)
+template <int R, int NT>
+__global__ void __launch_bounds__(NT, 1)
     tile_pass_kernel(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst,
                      const TileArgs A) {
     extern __shared__ __align__(1024) unsigned char sm_raw[];
@@ -562,19 +562,19 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         const int *src = reinterpret_cast<const int *>(P.sweeps);
         int *dst = reinterpret_cast<int *>(s_sweeps);
         const int nw_s = n_sweeps * (int)(sizeof(Sweep) / 4);
-        for (int i = tid; i < nw_s; i += kTileThreads) dst[i] = src[i];
+        for (int i = tid; i < nw_s; i += NT) dst[i] = src[i];
         src = reinterpret_cast<const int *>(P.micro);
         dst = reinterpret_cast<int *>(s_micro);
         const int nw_m = n_micro * (int)(sizeof(MicroOp) / 4);
-        for (int i = tid; i < nw_m; i += kTileThreads) dst[i] = src[i];
+        for (int i = tid; i < nw_m; i += NT) dst[i] = src[i];
         src = reinterpret_cast<const int *>(P.diags);
         dst = reinterpret_cast<int *>(s_diags);
         const int nw_d = kMaxDiag * (int)(sizeof(DiagDesc) / 4);
-        for (int i = tid; i < nw_d; i += kTileThreads) dst[i] = src[i];
+        for (int i = tid; i < nw_d; i += NT) dst[i] = src[i];
     }
-    for (int i = tid; i < P.n_const; i += kTileThreads) cs[i] = A.consts[i];
+    for (int i = tid; i < P.n_const; i += NT) cs[i] = A.consts[i];
     if (A.off_roots)
-        for (int i = tid; i < kRootsEntries; i += kTileThreads) roots[i] = A.roots[i];
+        for (int i = tid; i < kRootsEntries; i += NT) roots[i] = A.roots[i];
     if (tid < kMaxTileBits) {
         s_hb[tid] = P.hb[tid];
         s_contrib[tid] = P.smem_contrib[tid];
@@ -664,7 +664,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         c.buf = buf0 + (size_t)(k % NB) * tile_elems;
         c.tile_gbase = tile_base(A, ti);
         for (int s = 0; s < n_sweeps; ++s) {
-            run_sweep<R>(c, s_sweeps[s]);
+            run_sweep<R, NT>(c, s_sweeps[s]);
             __syncthreads();
         }
         fence_proxy_async();
@@ -674,26 +674,35 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     if (tid == 0) bulk_wait_all0();
 }
 
-void tile_kernel_smem_config(int bytes) {
-    cudaFuncSetAttribute(tile_pass_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(tile_pass_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(tile_pass_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(tile_pass_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(tile_pass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+template <int R, int NT>
+static void set_smem(int bytes) {
+    cudaFuncSetAttribute(tile_pass_kernel<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+void tile_kernel_smem_config(int bytes) {
+    set_smem<5, 256>(bytes);
+    set_smem<4, 256>(bytes);
+    set_smem<4, 512>(bytes);
+    set_smem<3, 256>(bytes);
+    set_smem<2, 256>(bytes);
+    set_smem<1, 256>(bytes);
+}
+
+// R = register group size; 4-bit groups run 512 threads (16 warps per SM)
 cudaError_t launch_tile_pass(int R, const TileArgs &A, const void *tm_src, const void *tm_dst, int grid,
                              int smem_bytes, cudaStream_t st) {
     const CUtensorMap &ms = *reinterpret_cast<const CUtensorMap *>(tm_src);
     const CUtensorMap &md = *reinterpret_cast<const CUtensorMap *>(tm_dst);
-    const int nt = kTileThreads;
     cudaGetLastError();
     switch (R) {
-        case 5: tile_pass_kernel<5><<<grid, nt, smem_bytes, st>>>(ms, md, A); break;
-        case 4: tile_pass_kernel<4><<<grid, nt, smem_bytes, st>>>(ms, md, A); break;
-        case 3: tile_pass_kernel<3><<<grid, nt, smem_bytes, st>>>(ms, md, A); break;
-        case 2: tile_pass_kernel<2><<<grid, nt, smem_bytes, st>>>(ms, md, A); break;
-        default: tile_pass_kernel<1><<<grid, nt, smem_bytes, st>>>(ms, md, A); break;
+        case 5: tile_pass_kernel<5, 256><<<grid, 256, smem_bytes, st>>>(ms, md, A); break;
+        case 4:
+            if (A.threads == 512) tile_pass_kernel<4, 512><<<grid, 512, smem_bytes, st>>>(ms, md, A);
+            else tile_pass_kernel<4, 256><<<grid, 256, smem_bytes, st>>>(ms, md, A);
+            break;
+        case 3: tile_pass_kernel<3, 256><<<grid, 256, smem_bytes, st>>>(ms, md, A); break;
+        case 2: tile_pass_kernel<2, 256><<<grid, 256, smem_bytes, st>>>(ms, md, A); break;
+        default: tile_pass_kernel<1, 256><<<grid, 256, smem_bytes, st>>>(ms, md, A); break;
     }
     return cudaGetLastError();
 }
@@ -702,11 +711,11 @@ std::string tile_kernel_attrs(int R) {
     cudaFuncAttributes fa;
     cudaError_t e;
     switch (R) {
-        case 5: e = cudaFuncGetAttributes(&fa, tile_pass_kernel<5>); break;
-        case 4: e = cudaFuncGetAttributes(&fa, tile_pass_kernel<4>); break;
-        case 3: e = cudaFuncGetAttributes(&fa, tile_pass_kernel<3>); break;
-        case 2: e = cudaFuncGetAttributes(&fa, tile_pass_kernel<2>); break;
-        default: e = cudaFuncGetAttributes(&fa, tile_pass_kernel<1>); break;
+        case 5: e = cudaFuncGetAttributes(&fa, tile_pass_kernel<5, 256>); break;
+        case 4: e = cudaFuncGetAttributes(&fa, tile_pass_kernel<4, 512>); break;
+        case 3: e = cudaFuncGetAttributes(&fa, tile_pass_kernel<3, 256>); break;
+        case 2: e = cudaFuncGetAttributes(&fa, tile_pass_kernel<2, 256>); break;
+        default: e = cudaFuncGetAttributes(&fa, tile_pass_kernel<1, 256>); break;
     }
     if (e != cudaSuccess) return "attrs unavailable";
     return "regs=" + std::to_string(fa.numRegs) + " maxThreads=" + std::to_string(fa.maxThreadsPerBlock) +

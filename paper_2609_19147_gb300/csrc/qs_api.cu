@@ -368,6 +368,7 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
         s = encode_map(hp.tma, dst, tp.swizzle != 0, &tmd);
         if (s != QS_OK) return s;
     }
+    A.threads = (tp.sweeps[0].r == 4 && tp.T >= 13) ? 512 : 256;
     long long total = A.n_tiles * batch;
     int grid = (int)std::min<long long>(total, g_num_sms[st->dev] > 0 ? g_num_sms[st->dev] : 148);
     cudaEvent_t ev;
