@@ -101,6 +101,14 @@ __device__ __forceinline__ void tma_store_5d(const CUtensorMap *tm, const int c[
         : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src_gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src_gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 __device__ __forceinline__ void bulk_wait_read0() {
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
@@ -520,6 +528,23 @@ __device__ __forceinline__ uint64_t tile_base(const TileArgs &A, long long ti) {
     return g;
 }
 
+// 16-byte chunk q of a tile (tile-local index 2q, 2q+1): its shared-memory
+// float2 offset (XOR-linear layout) and its global offset within the state
+__device__ __forceinline__ int chunk_smem(int q, int T, const int *contrib) {
+    int o = 0;
+    for (int tb = 1; tb < T; ++tb)
+        if ((q >> (tb - 1)) & 1) o ^= contrib[tb];
+    return o;
+}
+__device__ __forceinline__ uint64_t chunk_glob(int q, int L, int H, const int *hb) {
+    const int t = q << 1;
+    uint64_t g = (uint64_t)(t & ((1 << L) - 1));
+    const int r = t >> L;
+    for (int k = 0; k < H; ++k)
+        if ((r >> k) & 1) g |= 1ull << hb[k];
+    return g;
+}
+
 __device__ __forceinline__ void tile_coords(const TmaGeom &g, long long ti, long long bi, int c[5]) {
 #pragma unroll
     for (int d = 0; d < 5; ++d) {
@@ -592,6 +617,29 @@ __global__ void __launch_bounds__(NT, 1)
     const uint32_t row_bytes = 8u << L;
 
     // thread 0 issues every copy (TMA path: one instruction per tile)
+    const int io = A.io_mode;
+    const int n_chunks = tile_elems >> 1;
+    // cp.async path: every thread copies its 16-byte chunks (coalesced rows)
+    auto load_threads = [&](int k) {
+        float2 *dstbuf = buf0 + (size_t)(k % NB) * tile_elems;
+        const long long t = blockIdx.x + (long long)k * stride;
+        const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
+        const float2 *src = A.src + bi * A.state_elems + tile_base(A, ti);
+        for (int q = tid; q < n_chunks; q += NT)
+            cp_async16(dstbuf + chunk_smem(q, T, s_contrib), src + chunk_glob(q, L, H, s_hb));
+        cp_async_commit();
+    };
+    // thread stores: 16-byte chunks straight from shared memory to HBM
+    auto store_threads = [&](int k) {
+        const float2 *srcbuf = buf0 + (size_t)(k % NB) * tile_elems;
+        const long long t = blockIdx.x + (long long)k * stride;
+        const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
+        float2 *dst = A.dst + bi * A.state_elems + tile_base(A, ti);
+        for (int q = tid; q < n_chunks; q += NT) {
+            const float4 v = *reinterpret_cast<const float4 *>(srcbuf + chunk_smem(q, T, s_contrib));
+            *reinterpret_cast<float4 *>(dst + chunk_glob(q, L, H, s_hb)) = v;
+        }
+    };
     auto load = [&](int k) {
         const int b = k % NB;
         float2 *dstbuf = buf0 + (size_t)b * tile_elems;
@@ -625,8 +673,14 @@ __global__ void __launch_bounds__(NT, 1)
     };
 
     const int D = A.prefetch;
-    if (tid == 0)
+    if (io == 2) {
+        for (int k = 0; k < D; ++k) {
+            if (k < n_mine) load_threads(k);
+            else cp_async_commit();   // keep one group per tile slot
+        }
+    } else if (tid == 0) {
         for (int k = 0; k < D && k < n_mine; ++k) load(k);
+    }
 
     SweepCtx c;
     c.T = T;
@@ -638,18 +692,34 @@ __global__ void __launch_bounds__(NT, 1)
     c.micro = s_micro;
     c.diags = s_diags;
     for (int k = 0; k < n_mine; ++k) {
-        if (tid == 0 && k + D < n_mine) {
-            // buffer (k+D) % NB last held tile k+D-NB, stored at the end of
-            // iteration k+D-NB: allow the NB-D-1 newer stores to stay in flight
-            switch (NB - D - 1) {
-                case 0: asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); break;
-                case 1: asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); break;
-                case 2: asm volatile("cp.async.bulk.wait_group.read 2;" ::: "memory"); break;
-                default: asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory"); break;
+        bool ok = true;
+        if (io == 2) {
+            // buffer (k+D) % NB held tile k+D-NB <= k-1, already stored by the threads
+            if (k + D < n_mine) load_threads(k + D);
+            else cp_async_commit();
+            // groups are committed per tile in order: tile k is done when at most D remain
+            switch (D) {
+                case 1: cp_async_wait<1>(); break;
+                case 2: cp_async_wait<2>(); break;
+                case 3: cp_async_wait<3>(); break;
+                default: cp_async_wait<4>(); break;
             }
-            load(k + D);
+        } else {
+            if (tid == 0 && k + D < n_mine) {
+                // buffer (k+D) % NB last held tile k+D-NB, stored at the end of
+                // iteration k+D-NB: allow the NB-D-1 newer stores to stay in flight
+                if (io == 0) {
+                    switch (NB - D - 1) {
+                        case 0: asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); break;
+                        case 1: asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); break;
+                        case 2: asm volatile("cp.async.bulk.wait_group.read 2;" ::: "memory"); break;
+                        default: asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory"); break;
+                    }
+                }
+                load(k + D);
+            }
+            ok = mbar_wait_bounded(&full[k % NB], (uint32_t)((k / NB) & 1));
         }
-        const bool ok = mbar_wait_bounded(&full[k % NB], (uint32_t)((k / NB) & 1));
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicCAS(A.err, 0, (int)QS_ERR_TIMEOUT);
@@ -667,10 +737,21 @@ __global__ void __launch_bounds__(NT, 1)
             run_sweep<R, NT>(c, s_sweeps[s]);
             __syncthreads();
         }
-        fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) store(k);
+        if (io == 0) {
+            fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) store(k);
+        } else {
+            store_threads(k);
+            // the buffer is reloaded D iterations later, after this barrier
+            if (io == 2) __syncthreads();
+            else {
+                fence_proxy_async();   // generic reads before the async-proxy refill
+                __syncthreads();
+            }
+        }
     }
+    if (io == 2) cp_async_wait<0>();
     if (tid == 0) bulk_wait_all0();
 }
 

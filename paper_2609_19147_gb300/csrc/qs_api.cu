@@ -6,6 +6,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -369,6 +370,19 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
         if (s != QS_OK) return s;
     }
     A.threads = (tp.sweeps[0].r == 4 && tp.T >= 13) ? 512 : 256;
+    {
+        static int io_env = -2;
+        if (io_env == -2) {
+            const char *e = getenv("QS_TILE_IO");
+            io_env = e ? atoi(e) : -1;
+        }
+        A.io_mode = io_env >= 0 ? io_env : 1;
+        if (!A.use_tma && A.io_mode != 2) A.io_mode = 0;   // row-copy fallback pairs with bulk stores
+    }
+    if (A.io_mode != 0) {   // thread stores: the refilled buffer is free right after its iteration
+        A.n_buf = std::min(A.n_buf, 4);
+        A.prefetch = A.n_buf - 1;
+    }
     long long total = A.n_tiles * batch;
     int grid = (int)std::min<long long>(total, g_num_sms[st->dev] > 0 ? g_num_sms[st->dev] : 148);
     cudaEvent_t ev;
