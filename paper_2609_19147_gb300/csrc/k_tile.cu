@@ -619,14 +619,45 @@ __global__ void __launch_bounds__(NT, 1)
     // thread 0 issues every copy (TMA path: one instruction per tile)
     const int io = A.io_mode;
     const int n_chunks = tile_elems >> 1;
+    // 16-byte chunk q = tid + i * NT of a tile: offsets are XOR/OR-linear in the
+    // bits of q, so split them into a per-thread part (computed once) and the
+    // parts of the (at most 4) loop bits
+    int c_smem = 0;
+    uint64_t c_glob = 0;
+    int i_smem[4] = {0, 0, 0, 0};
+    uint64_t i_glob[4] = {0, 0, 0, 0};
+    int n_ib = 0;
+    if (io != 0) {
+        if (tid < n_chunks) {
+            c_smem = chunk_smem(tid, T, s_contrib);
+            c_glob = chunk_glob(tid, L, H, s_hb);
+        }
+        for (int m = 0; (NT << m) < n_chunks && m < 4; ++m) {
+            i_smem[m] = chunk_smem(NT << m, T, s_contrib);
+            i_glob[m] = chunk_glob(NT << m, L, H, s_hb);
+            n_ib = m + 1;
+        }
+    }
+    const int per_thread = n_chunks > NT ? n_chunks / NT : 1;
     // cp.async path: every thread copies its 16-byte chunks (coalesced rows)
     auto load_threads = [&](int k) {
         float2 *dstbuf = buf0 + (size_t)(k % NB) * tile_elems;
         const long long t = blockIdx.x + (long long)k * stride;
         const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
         const float2 *src = A.src + bi * A.state_elems + tile_base(A, ti);
-        for (int q = tid; q < n_chunks; q += NT)
-            cp_async16(dstbuf + chunk_smem(q, T, s_contrib), src + chunk_glob(q, L, H, s_hb));
+        if (tid < n_chunks) {
+#pragma unroll 4
+            for (int i = 0; i < per_thread; ++i) {
+                int so = c_smem;
+                uint64_t go = c_glob;
+                for (int m = 0; m < n_ib; ++m)
+                    if ((i >> m) & 1) {
+                        so ^= i_smem[m];
+                        go |= i_glob[m];
+                    }
+                cp_async16(dstbuf + so, src + go);
+            }
+        }
         cp_async_commit();
     };
     // thread stores: 16-byte chunks straight from shared memory to HBM
@@ -635,9 +666,19 @@ __global__ void __launch_bounds__(NT, 1)
         const long long t = blockIdx.x + (long long)k * stride;
         const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
         float2 *dst = A.dst + bi * A.state_elems + tile_base(A, ti);
-        for (int q = tid; q < n_chunks; q += NT) {
-            const float4 v = *reinterpret_cast<const float4 *>(srcbuf + chunk_smem(q, T, s_contrib));
-            *reinterpret_cast<float4 *>(dst + chunk_glob(q, L, H, s_hb)) = v;
+        if (tid < n_chunks) {
+#pragma unroll 4
+            for (int i = 0; i < per_thread; ++i) {
+                int so = c_smem;
+                uint64_t go = c_glob;
+                for (int m = 0; m < n_ib; ++m)
+                    if ((i >> m) & 1) {
+                        so ^= i_smem[m];
+                        go |= i_glob[m];
+                    }
+                const float4 v = *reinterpret_cast<const float4 *>(srcbuf + so);
+                *reinterpret_cast<float4 *>(dst + go) = v;
+            }
         }
     };
     auto load = [&](int k) {
