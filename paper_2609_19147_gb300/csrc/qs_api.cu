@@ -376,7 +376,7 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
             const char *e = getenv("QS_TILE_IO");
             io_env = e ? atoi(e) : -1;
         }
-        A.io_mode = io_env >= 0 ? io_env : 1;
+        A.io_mode = io_env >= 0 ? io_env : 0;
         if (!A.use_tma && A.io_mode != 2) A.io_mode = 0;   // row-copy fallback pairs with bulk stores
     }
     if (A.io_mode != 0) {   // thread stores: the refilled buffer is free right after its iteration
