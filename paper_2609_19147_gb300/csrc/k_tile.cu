@@ -48,14 +48,16 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
+// try_wait with a suspend-time hint: a waiting thread sleeps (up to the hint)
+// instead of spinning and stealing issue slots from the warps that compute
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
         : "memory");
     return ok != 0;
 }
@@ -99,6 +101,12 @@ __device__ __forceinline__ void tma_store_5d(const CUtensorMap *tm, const int c[
             reinterpret_cast<uint64_t>(tm)),
         "r"(smem_u32(src_smem)), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4])
         : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_l2_5d(const CUtensorMap *tm, const int c[5]) {
+    asm volatile("cp.async.bulk.prefetch.tensor.5d.L2.global.tile [%0, {%1, %2, %3, %4, %5}];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4])
+                 : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async16(void *dst_smem, const void *src_gmem) {
@@ -714,6 +722,16 @@ __global__ void __launch_bounds__(NT, 1)
     };
 
     const int D = A.prefetch;
+    const int PF = A.l2_prefetch;   // tiles beyond the smem prefetch warmed in L2
+    auto l2pf = [&](int k) {
+        const long long t = blockIdx.x + (long long)k * stride;
+        const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
+        int c[5];
+        tile_coords(A.geo, ti, bi, c);
+        tma_prefetch_l2_5d(&tm_src, c);
+    };
+    if (tid == 0 && io != 2 && A.use_tma)
+        for (int k = D; k < D + PF && k < n_mine; ++k) l2pf(k);
     if (io == 2) {
         for (int k = 0; k < D; ++k) {
             if (k < n_mine) load_threads(k);
@@ -759,6 +777,7 @@ __global__ void __launch_bounds__(NT, 1)
                 }
                 load(k + D);
             }
+            if (tid == 0 && A.use_tma && k + D + PF < n_mine) l2pf(k + D + PF);
             ok = mbar_wait_bounded(&full[k % NB], (uint32_t)((k / NB) & 1));
         }
         if (__syncthreads_or(!ok)) {

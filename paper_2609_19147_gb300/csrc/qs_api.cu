@@ -383,6 +383,17 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
         A.n_buf = std::min(A.n_buf, 4);
         A.prefetch = A.n_buf - 1;
     }
+    {
+        static int pf_env = -2, d_env = -2;
+        if (pf_env == -2) {
+            const char *e = getenv("QS_TILE_L2PF");
+            pf_env = e ? atoi(e) : -1;
+            e = getenv("QS_TILE_PREFETCH");
+            d_env = e ? atoi(e) : -1;
+        }
+        A.l2_prefetch = pf_env >= 0 ? pf_env : 2;
+        if (d_env > 0 && d_env < A.n_buf) A.prefetch = d_env;
+    }
     long long total = A.n_tiles * batch;
     int grid = (int)std::min<long long>(total, g_num_sms[st->dev] > 0 ? g_num_sms[st->dev] : 148);
     cudaEvent_t ev;
