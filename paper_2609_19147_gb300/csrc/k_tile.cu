@@ -48,16 +48,14 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
-// try_wait with a suspend-time hint: a waiting thread sleeps (up to the hint)
-// instead of spinning and stealing issue slots from the warps that compute
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+        : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return ok != 0;
 }
@@ -565,8 +563,8 @@ __device__ __forceinline__ void tile_coords(const TmaGeom &g, long long ti, long
     }
 }
 
-template <int R, int NT>
-__global__ void __launch_bounds__(NT, 1)
+template <int R, int NT, int MINB = 1>
+__global__ void __launch_bounds__(NT, MINB)
     tile_pass_kernel(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst,
                      const TileArgs A) {
     extern __shared__ __align__(1024) unsigned char sm_raw[];
@@ -815,15 +813,16 @@ __global__ void __launch_bounds__(NT, 1)
     if (tid == 0) bulk_wait_all0();
 }
 
-template <int R, int NT>
+template <int R, int NT, int MINB = 1>
 static void set_smem(int bytes) {
-    cudaFuncSetAttribute(tile_pass_kernel<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(tile_pass_kernel<R, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 void tile_kernel_smem_config(int bytes) {
     set_smem<5, 256>(bytes);
     set_smem<4, 256>(bytes);
     set_smem<4, 512>(bytes);
+    set_smem<4, 256, 2>(bytes);
     set_smem<3, 256>(bytes);
     set_smem<2, 256>(bytes);
     set_smem<1, 256>(bytes);
@@ -839,6 +838,7 @@ cudaError_t launch_tile_pass(int R, const TileArgs &A, const void *tm_src, const
         case 5: tile_pass_kernel<5, 256><<<grid, 256, smem_bytes, st>>>(ms, md, A); break;
         case 4:
             if (A.threads == 512) tile_pass_kernel<4, 512><<<grid, 512, smem_bytes, st>>>(ms, md, A);
+            else if (A.ctas_per_sm == 2) tile_pass_kernel<4, 256, 2><<<grid, 256, smem_bytes, st>>>(ms, md, A);
             else tile_pass_kernel<4, 256><<<grid, 256, smem_bytes, st>>>(ms, md, A);
             break;
         case 3: tile_pass_kernel<3, 256><<<grid, 256, smem_bytes, st>>>(ms, md, A); break;

@@ -338,9 +338,12 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     const int buf_bytes = 8 << tp.T;
     off = al(off, 1024);
     A.off_buf0 = off;
-    const int limit = 227 * 1024 - 1024;   // 1 KB reserved for the base alignment
-    // as many tile buffers as fit (<= 6); keep ~128 KB of loads in flight
-    A.n_buf = std::min(6, (limit - off) / buf_bytes);
+    // two co-resident CTAs per SM for 12-bit tiles with 4-bit groups: one
+    // computes while the other waits on its copies
+    A.ctas_per_sm = (tp.T == 12 && tp.sweeps[0].r == 4) ? 2 : 1;
+    const int limit = (A.ctas_per_sm == 2 ? 113 * 1024 : 227 * 1024) - 1024;   // 1 KB for the base alignment
+    // as many tile buffers as fit (<= 6)
+    A.n_buf = std::min(A.ctas_per_sm == 2 ? 3 : 6, (limit - off) / buf_bytes);
     if (A.n_buf > kMaxTileBuffers) A.n_buf = kMaxTileBuffers;
     if (A.n_buf < 2) return fail(QS_ERR_INTERNAL, "tile pass needs too much shared memory");
     A.prefetch = std::max(1, A.n_buf - 2);
@@ -395,7 +398,7 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
         if (d_env > 0 && d_env < A.n_buf) A.prefetch = d_env;
     }
     long long total = A.n_tiles * batch;
-    int grid = (int)std::min<long long>(total, g_num_sms[st->dev] > 0 ? g_num_sms[st->dev] : 148);
+    int grid = (int)std::min<long long>(total, (long long)A.ctas_per_sm * (g_num_sms[st->dev] > 0 ? g_num_sms[st->dev] : 148));
     cudaEvent_t ev;
     prof_begin(st, &ev);
     {

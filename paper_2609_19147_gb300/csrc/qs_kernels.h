@@ -34,6 +34,7 @@ struct TileArgs {
     int n_buf;                 // tile buffers (2..8), each 8 * 2^T bytes from off_buf0
     int prefetch;              // tiles loaded ahead of the one being processed (1..n_buf-1)
     int threads;               // 256, or 512 for 4-bit register groups on 13-bit tiles
+    int ctas_per_sm;           // 2: two co-resident CTAs (12-bit tiles, 4-bit groups)
     int l2_prefetch;           // tiles warmed in L2 beyond the shared-memory prefetch
     int io_mode;               // 0: TMA load + TMA store; 1: TMA load + thread stores;
                                // 2: cp.async loads + thread stores
