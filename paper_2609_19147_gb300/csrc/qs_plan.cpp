@@ -1071,8 +1071,41 @@ static void build_perm_or_gather(int n, const FOp &f, HostPass &hp) {
         }
 }
 
+static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<RGate> &gates, const qs_opts &o,
+                                      Plan &plan, std::string &err);
+
+// Default tile shape: 12-bit tiles with 4-bit register groups (two CTAs per
+// SM hide each other's copy latency) unless they need more HBM passes than
+// 13-bit tiles with 5-bit groups.
 qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, const qs_opts &o, Plan &plan,
                            std::string &err) {
+    if (o.tile_qubits > 0 || o.group_qubits > 0 || n < 13) return build_fused_plan_cfg(n, batch, gates, o, plan, err);
+    // candidates in order of measured per-pass speed for layer-type passes;
+    // QFT-stage passes run fastest with 5-bit groups
+    const int cfg[3][2] = {{12, 4}, {13, 4}, {13, 5}};
+    Plan cand[3];
+    for (int i = 0; i < 3; ++i) {
+        qs_opts c = o;
+        c.tile_qubits = cfg[i][0];
+        c.group_qubits = cfg[i][1];
+        qs_status s = build_fused_plan_cfg(n, batch, gates, c, cand[i], err);
+        if (s != QS_OK) return s;
+    }
+    bool has_qft = false;
+    for (auto &hp : cand[2].passes)
+        if (hp.type == HostPass::TILE)
+            for (int k = 0; k < hp.tile.n_micro; ++k)
+                if (hp.tile.micro[k].kind == MK_QFT) has_qft = true;
+    int best = 0;
+    for (int i = 1; i < 3; ++i)
+        if (cand[i].passes.size() < cand[best].passes.size()) best = i;
+    if (best != 0 && has_qft && cand[2].passes.size() == cand[best].passes.size()) best = 2;
+    plan = std::move(cand[best]);
+    return QS_OK;
+}
+
+static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<RGate> &gates, const qs_opts &o,
+                                      Plan &plan, std::string &err) {
     plan = Plan();
     plan.n = n;
     plan.mode = QS_MODE_FUSED;
