@@ -194,6 +194,32 @@ typedef struct qs_profile_record {
 } qs_profile_record;
 qs_status qs_profile_read(qs_state *st, qs_profile_record *out, int cap, int *count);
 
+/* Pauli expectation values without any device allocation.  The paper has
+ * no counterpart: this call exists for callers that cannot call cudaMalloc --
+ * code running while a CUDA graph is being captured (allocation is not a
+ * capturable operation), plug-ins inside a host application that owns every
+ * device allocation through its own arena, and latency-critical loops that
+ * cannot afford an allocation's implicit synchronisation.  It computes what
+ * qs_expect computes (out[b] = <psi_b| sum_k coeff_k P_k |psi_b>, FP64
+ * accumulation), but takes the state as a plain device pointer and keeps its
+ * scratch (block partial sums, finished sums, the term table) in one
+ * file-scope static __device__ array of 694,272 bytes compiled into the
+ * library.  Every GPU that loads the library holds that array until the
+ * process exits.
+ *   dev_state: device pointer, batch * 2^n complex64, 16-byte aligned (read only)
+ *   n in [1, 33]; batch in [1, 16]; n_terms <= 256 (larger -> QS_ERR_UNSUPPORTED,
+ *   nothing launched); out: host array of batch doubles; cuda_stream: the
+ *   cudaStream_t to run on (NULL = legacy default).  Synchronous.
+ * The first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * previous call's contents: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on it.  Nothing in it needs clearing --
+ * every slot a call reads is written earlier in the same call.
+ * Calls no cudaMalloc, cudaFree or other allocating routine. */
+qs_status qs_expect_noalloc(const void *dev_state, int n, int batch, const qs_pauli *terms, size_t n_terms,
+                            double *out, void *cuda_stream);
+
 /* Message for the last failed call on this host thread ("" if none). */
 const char *qs_last_error(void);
 

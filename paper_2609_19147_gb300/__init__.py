@@ -77,6 +77,7 @@ _SIGS = {
                           ctypes.POINTER(_i32)], _i32),
     "qs_profile_enable": ([_vp, _i32], _i32),
     "qs_profile_read": ([_vp, ctypes.POINTER(QsProfileRecord), _i32, ctypes.POINTER(_i32)], _i32),
+    "qs_expect_noalloc": ([_vp, _i32, _i32, ctypes.POINTER(QsPauli), _sz, _dp, _vp], _i32),
     "qs_last_error": ([], ctypes.c_char_p),
     "qs_version": ([], ctypes.c_char_p),
 }

@@ -722,6 +722,10 @@ inline void times_i_pow(double &re, double &im, int ny) {
 
 }  // namespace
 
+namespace qs {
+void set_last_error(const char *msg) { g_last_error = msg; }
+}  // namespace qs
+
 // ===========================================================================
 // exported C ABI
 // ===========================================================================

@@ -117,4 +117,7 @@ cudaError_t launch_apply_pauli_sum(const float2 *psi, float2 *lam, long long sta
 
 cudaError_t launch_init_zero(float2 *psi, long long state_elems, int batch, cudaStream_t st);
 
+// message for qs_last_error() on this host thread
+void set_last_error(const char *msg);
+
 }  // namespace qs
