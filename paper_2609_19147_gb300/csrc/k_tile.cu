@@ -332,6 +332,49 @@ __device__ __forceinline__ void disp_u2(int ma, int mb, float2 (&a)[1 << R], con
     }
 }
 
+// layers: the same 2x2 family on every group bit in `mask`, straight-line code
+template <int R, int M = 0>
+__device__ __forceinline__ void layer_rxc(float2 (&a)[1 << R], const float2 *k0, uint32_t mask) {
+    if constexpr (M < R) {
+        if ((mask >> M) & 1) op_rxc<R, M>(a, k0 + M);
+        layer_rxc<R, M + 1>(a, k0, mask);
+    }
+}
+template <int R, int M = 0>
+__device__ __forceinline__ void layer_u1r(float2 (&a)[1 << R], const float2 *k0, uint32_t mask) {
+    if constexpr (M < R) {
+        if ((mask >> M) & 1) op_u1r<R, M>(a, k0 + 2 * M);
+        layer_u1r<R, M + 1>(a, k0, mask);
+    }
+}
+template <int R, int M = 0>
+__device__ __forceinline__ void layer_u1(float2 (&a)[1 << R], const float2 *k0, uint32_t mask, const Grp<R> &G) {
+    if constexpr (M < R) {
+        if ((mask >> M) & 1) op_u1<R, M>(a, k0 + 4 * M, 0ull, 0ull, 0ull, G);
+        layer_u1<R, M + 1>(a, k0, mask, G);
+    }
+}
+template <int R, int M = 0>
+__device__ __forceinline__ void layer_h(float2 (&a)[1 << R], uint32_t mask) {
+    if constexpr (M < R) {
+        if ((mask >> M) & 1) op_h<R, M>(a);
+        layer_h<R, M + 1>(a, mask);
+    }
+}
+// QFT stages from the highest group bit down (the gate stream's order)
+template <int R, int M = R - 1>
+__device__ __forceinline__ void layer_qft(float2 (&a)[1 << R], const float2 *k0, uint32_t mask, uint64_t ppack,
+                                          uint64_t gbase, const float2 *roots) {
+    if constexpr (M >= 0) {
+        if ((mask >> M) & 1) {
+            const int p = (int)((ppack >> (6 * M)) & 63);
+            const float2 w = twiddle(gbase & ((1ull << p) - 1), p, roots);
+            op_qft<R, M>(a, k0 + M * (1 << R), w);
+        }
+        layer_qft<R, M - 1>(a, k0, mask, ppack, gbase, roots);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // one sweep over the tile in shared memory
 // ---------------------------------------------------------------------------
@@ -345,6 +388,8 @@ struct SweepCtx {
     const float2 *roots;
     const MicroOp *micro;    // smem
     const DiagDesc *diags;   // smem
+    const int *tab_s;        // smem: per-sweep item-address tables (shared-memory offsets)
+    const uint64_t *tab_g;   // smem: per-sweep item-address tables (global index bits)
     uint64_t tile_gbase;     // global index of tile-local 0 (within the state)
 };
 
@@ -403,7 +448,7 @@ __device__ __forceinline__ void sweep_store(const SweepCtx &c, bool vec, int sad
 }
 
 template <int R, int NT>
-__device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S) {
+__device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int sidx) {
     int gs[R];
     Grp<R> G;
 #pragma unroll
@@ -414,15 +459,12 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S) {
     const int nb = c.T - R;
     const int n_items = 1 << nb;
     const bool vec = S.vec != 0;
+    const int *ts = c.tab_s + sidx * kItemTab;
+    const uint64_t *tg = c.tab_g + sidx * kItemTab;
     for (int item = threadIdx.x; item < n_items; item += NT) {
-        int saddr = 0;
-        uint64_t gbase = c.tile_gbase;
-        for (int i = 0; i < nb; ++i)
-            if ((item >> i) & 1) {
-                const int tb = S.tbit[i];
-                saddr ^= c.contrib[tb];
-                gbase |= glob_contrib(c, tb);
-            }
+        const int i0 = item & 31, i1 = 32 + ((item >> 5) & 31), i2 = 64 + ((item >> 10) & 15);
+        const int saddr = ts[i0] ^ ts[i1] ^ ts[i2];
+        const uint64_t gbase = c.tile_gbase | tg[i0] | tg[i1] | tg[i2];
         float2 a[1 << R];
         sweep_load<R>(c, vec, saddr, gs, a);
         for (int oi = S.op_begin; oi < S.op_end; ++oi) {
@@ -449,6 +491,20 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S) {
                     disp_qft<R>(op.a, a, c.cs + op.cst, w);
                     break;
                 }
+                case MK_LAYER: {
+                    const float2 *k0 = c.cs + op.cst;
+                    const uint32_t mask = (uint32_t)op.b;
+                    switch (op.a) {
+                        case MK_RXC: layer_rxc<R>(a, k0, mask); break;
+                        case MK_U1R: layer_u1r<R>(a, k0, mask); break;
+                        case MK_U1: layer_u1<R>(a, k0, mask, G); break;
+                        default: layer_h<R>(a, mask); break;
+                    }
+                    break;
+                }
+                case MK_QFTL:
+                    layer_qft<R>(a, c.cs + op.cst, (uint32_t)op.b, op.cmask, gbase, c.roots);
+                    break;
                 case MK_DIAG: {
                     const DiagDesc &d = c.diags[op.cst];
                     const uint32_t dyn_s = (uint32_t)op.a, dyn_g = (uint32_t)op.b;
@@ -578,6 +634,8 @@ __global__ void __launch_bounds__(NT, MINB)
     const int n_sweeps = P.n_sweeps, n_micro = P.n_micro;
     MicroOp *s_micro = reinterpret_cast<MicroOp *>(s_sweeps + n_sweeps);
     DiagDesc *s_diags = reinterpret_cast<DiagDesc *>(s_micro + n_micro);
+    uint64_t *s_tab_g = reinterpret_cast<uint64_t *>(s_diags + kMaxDiag);
+    int *s_tab_s = reinterpret_cast<int *>(s_tab_g + n_sweeps * kItemTab);
     float2 *cs = reinterpret_cast<float2 *>(sm + A.off_consts);
     float2 *roots = reinterpret_cast<float2 *>(sm + A.off_roots);
     float2 *buf0 = reinterpret_cast<float2 *>(sm + A.off_buf0);
@@ -613,6 +671,27 @@ __global__ void __launch_bounds__(NT, MINB)
     if (tid == 0) {
         for (int b = 0; b < kMaxTileBuffers; ++b) mbar_init(&full[b], 1);
         fence_mbar_init();
+    }
+    __syncthreads();
+    // item-address tables: item bits 0-4, 5-9, 10-13 of each sweep -> XOR of the
+    // shared-memory offsets and OR of the global index bits of those tile bits
+    for (int e = tid; e < n_sweeps * kItemTab; e += NT) {
+        const int sw = e / kItemTab, idx = e - sw * kItemTab;
+        const int part = idx < 32 ? 0 : (idx < 64 ? 1 : 2);
+        const int v = idx - 32 * part;
+        const int nb = T - s_sweeps[sw].r;
+        int so = 0;
+        uint64_t go = 0;
+        for (int b = 0; b < 5; ++b) {
+            const int i = 5 * part + b;
+            if (((v >> b) & 1) && i < nb) {
+                const int tb = s_sweeps[sw].tbit[i];
+                so ^= s_contrib[tb];
+                go |= tb < L ? (1ull << tb) : (1ull << s_hb[tb - L]);
+            }
+        }
+        s_tab_s[e] = so;
+        s_tab_g[e] = go;
     }
     fence_proxy_async();
     __syncthreads();
@@ -748,6 +827,8 @@ __global__ void __launch_bounds__(NT, MINB)
     c.roots = roots;
     c.micro = s_micro;
     c.diags = s_diags;
+    c.tab_s = s_tab_s;
+    c.tab_g = s_tab_g;
     for (int k = 0; k < n_mine; ++k) {
         bool ok = true;
         if (io == 2) {
@@ -792,7 +873,7 @@ __global__ void __launch_bounds__(NT, MINB)
         c.buf = buf0 + (size_t)(k % NB) * tile_elems;
         c.tile_gbase = tile_base(A, ti);
         for (int s = 0; s < n_sweeps; ++s) {
-            run_sweep<R, NT>(c, s_sweeps[s]);
+            run_sweep<R, NT>(c, s_sweeps[s], s);
             __syncthreads();
         }
         if (io == 0) {

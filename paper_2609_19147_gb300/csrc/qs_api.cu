@@ -328,6 +328,7 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     int off = 256;
     A.off_desc = off;
     off += tp.n_sweeps * (int)sizeof(Sweep) + tp.n_micro * (int)sizeof(MicroOp) + kMaxDiag * (int)sizeof(DiagDesc);
+    off += tp.n_sweeps * kItemTab * (8 + 4);   // item-address tables
     off = al(off, 128);
     A.off_consts = off;
     off = al(off + (int)hp.consts.size() * 8, 128);

@@ -74,7 +74,15 @@ enum MicroKind : int32_t {
     MK_H = 4,     // Hadamard on group bit a (sign-only butterfly)
     MK_RXC = 5,   // [[c, i s], [i s, c]] on group bit a (RX family): consts c, s
     MK_U1R = 6,   // real 2x2 on group bit a (RY family): consts m00, m01, m10, m11
+    MK_LAYER = 7, // commuting 2x2 ops of one kind (a = MK_RXC / MK_U1R / MK_U1 / MK_H)
+                  // on the group bits in mask b; constants per bit m at cst + m * stride
+    MK_QFTL = 8,  // QFT stages (ladders down to bit 0) on the group bits in mask b,
+                  // applied from the highest group bit down; p of bit m = (p >> 6m) & 63
+                  // (p is a packed 64-bit field: use cmask); group table of bit m at cst + m * 2^R
 };
+
+// item-address tables per sweep (shared memory): item bits 0-4, 5-9, 10-13
+constexpr int kItemTab = 32 + 32 + 16;
 
 struct MicroOp {
     int32_t kind;

@@ -1014,7 +1014,88 @@ struct PassBuilder {
             }
             sw.scale = (float)std::pow(kSqrtHalf, (double)n_butterfly);
         }
+        merge_layers();
         tp.n_const = (int)cst.size();
+    }
+    // Merge runs of consecutive micro-ops that act on distinct group bits and
+    // commute (same 2x2 family, no controls) into one layer op, and runs of
+    // QFT stages in descending bit order into one QFT layer: the kernel then
+    // runs them as straight-line code with one dispatch.
+    void merge_layers() {
+        std::vector<MicroOp> out;
+        for (int s = 0; s < tp.n_sweeps; ++s) {
+            Sweep &sw = tp.sweeps[s];
+            const int begin = (int)out.size();
+            int i = sw.op_begin;
+            while (i < sw.op_end) {
+                const MicroOp &m0 = tp.micro[i];
+                auto layer_kind = [&](const MicroOp &m) {
+                    if (m.cmask) return -1;
+                    if (m.kind == MK_RXC || m.kind == MK_U1R || m.kind == MK_U1 || m.kind == MK_H) return (int)m.kind;
+                    return -1;
+                };
+                const int lk = layer_kind(m0);
+                if (lk >= 0) {
+                    uint32_t mask = 0;
+                    int j = i;
+                    while (j < sw.op_end && layer_kind(tp.micro[j]) == lk && !((mask >> tp.micro[j].a) & 1)) {
+                        mask |= 1u << tp.micro[j].a;
+                        ++j;
+                    }
+                    const int stride = lk == MK_RXC ? 1 : lk == MK_U1R ? 2 : lk == MK_U1 ? 4 : 0;
+                    if (j - i >= 2 && (int)cst.size() + R * stride <= kMaxConst) {
+                        MicroOp L;
+                        std::memset(&L, 0, sizeof L);
+                        L.kind = MK_LAYER;
+                        L.a = lk;
+                        L.b = (int)mask;
+                        L.cst = (int)cst.size();
+                        for (int m = 0; m < R * stride; ++m) cst.push_back(float2{0.f, 0.f});
+                        for (int k = i; k < j; ++k) {
+                            const MicroOp &mk = tp.micro[k];
+                            for (int e = 0; e < stride; ++e) cst[L.cst + mk.a * stride + e] = cst[mk.cst + e];
+                        }
+                        out.push_back(L);
+                        i = j;
+                        continue;
+                    }
+                }
+                if (m0.kind == MK_QFT && m0.lo == 0) {
+                    uint32_t mask = 0;
+                    int j = i, last = 1 << 30;
+                    while (j < sw.op_end && tp.micro[j].kind == MK_QFT && tp.micro[j].lo == 0 &&
+                           tp.micro[j].a < last) {
+                        last = tp.micro[j].a;
+                        mask |= 1u << last;
+                        ++j;
+                    }
+                    if (j - i >= 2 && (int)cst.size() + R * (1 << R) <= kMaxConst) {
+                        MicroOp L;
+                        std::memset(&L, 0, sizeof L);
+                        L.kind = MK_QFTL;
+                        L.b = (int)mask;
+                        L.cst = (int)cst.size();
+                        uint64_t pp = 0;
+                        for (int m = 0; m < R * (1 << R); ++m) cst.push_back(float2{1.f, 0.f});
+                        for (int k = i; k < j; ++k) {
+                            const MicroOp &mk = tp.micro[k];
+                            pp |= (uint64_t)(mk.p & 63) << (6 * mk.a);
+                            for (int e = 0; e < (1 << R); ++e) cst[L.cst + mk.a * (1 << R) + e] = cst[mk.cst + e];
+                        }
+                        L.cmask = pp;
+                        out.push_back(L);
+                        i = j;
+                        continue;
+                    }
+                }
+                out.push_back(m0);
+                ++i;
+            }
+            sw.op_begin = begin;
+            sw.op_end = (int)out.size();
+        }
+        tp.n_micro = (int)out.size();
+        for (int k = 0; k < tp.n_micro; ++k) tp.micro[k] = out[k];
     }
 };
 }  // namespace
@@ -1095,7 +1176,7 @@ qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, co
     for (auto &hp : cand[2].passes)
         if (hp.type == HostPass::TILE)
             for (int k = 0; k < hp.tile.n_micro; ++k)
-                if (hp.tile.micro[k].kind == MK_QFT) has_qft = true;
+                if (hp.tile.micro[k].kind == MK_QFT || hp.tile.micro[k].kind == MK_QFTL) has_qft = true;
     int best = 0;
     for (int i = 1; i < 3; ++i)
         if (cand[i].passes.size() < cand[best].passes.size()) best = i;
@@ -1375,8 +1456,13 @@ std::string Plan::describe() const {
         const HostPass &hp = passes[i];
         if (hp.type == HostPass::TILE) {
             const TilePass &t = hp.tile;
-            int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int k = 0; k < t.n_micro; ++k) cnt[t.micro[k].kind]++;
+            int cnt[16] = {0};
+            for (int k = 0; k < t.n_micro; ++k) {
+                const MicroOp &mo = t.micro[k];
+                if (mo.kind == MK_LAYER) cnt[mo.a] += __builtin_popcount((unsigned)mo.b);
+                else if (mo.kind == MK_QFTL) cnt[MK_QFT] += __builtin_popcount((unsigned)mo.b);
+                else cnt[mo.kind]++;
+            }
             os << "TILE T=" << t.T << " L=" << t.L << " hb=[";
             for (int k = 0; k < t.H; ++k) os << (k ? "," : "") << t.hb[k];
             os << "] tma=" << (hp.tma.ok ? 1 : 0) << " sweeps=" << t.n_sweeps
