@@ -173,6 +173,26 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates,
                   const qs_pauli *terms, size_t n_terms,
                   double *energy, double *grad);
 
+/* One MaxCut graph: n vertices (one qubit each), edges as 2 * n_edges
+ * vertex indices (u0, v0, u1, v1, ...), no self-loops. */
+typedef struct qs_graph {
+    int32_t n;
+    int32_t n_edges;
+    const int32_t *edges;
+} qs_graph;
+
+/* Batched QAOA MaxCut (Sec. 3.2.3: H_C = 1/2 sum_edges (I - Z_u Z_v),
+ * H_M = sum_q X_q).  For graph g and angle set a (n_sets per graph):
+ *   |psi> = prod_{l=1..p} e^{-i beta_l H_M} e^{-i gamma_l H_C} |+>^n,
+ *   out[g * n_sets + a] = <psi|H_C|psi>   (FP64 accumulation).
+ * gammas / betas: n_graphs x n_sets x p doubles (row-major).  Graphs with
+ * n <= 14 run in one persistent launch with the state in shared memory;
+ * larger ones (n <= 30) run through the fused tile-pass executor, one graph
+ * (all its angle sets as a batch) at a time.  Limits: p <= 16, <= 64 edges
+ * per graph.  Allocates its own device memory; synchronous on cuda_stream. */
+qs_status qs_qaoa_maxcut(const qs_graph *graphs, size_t n_graphs, int n_sets, int p, const double *gammas,
+                         const double *betas, double *out, void *cuda_stream);
+
 /* Test hook: write the detector's plan for an n-qubit circuit as text
  * (one line per pass: family, qubits, op count) into buf (NUL-terminated,
  * truncated to len).  Needs no GPU.  *passes (if non-NULL) receives the

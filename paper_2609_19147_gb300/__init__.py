@@ -50,6 +50,10 @@ class QsOpts(ctypes.Structure):
                 ("group_qubits", ctypes.c_int32)]
 
 
+class QsGraph(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_edges", ctypes.c_int32), ("edges", ctypes.POINTER(ctypes.c_int32))]
+
+
 class QsProfileRecord(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
                 ("bytes", ctypes.c_double)]
@@ -78,6 +82,7 @@ _SIGS = {
     "qs_profile_enable": ([_vp, _i32], _i32),
     "qs_profile_read": ([_vp, ctypes.POINTER(QsProfileRecord), _i32, ctypes.POINTER(_i32)], _i32),
     "qs_expect_noalloc": ([_vp, _i32, _i32, ctypes.POINTER(QsPauli), _sz, _dp, _vp], _i32),
+    "qs_qaoa_maxcut": ([ctypes.POINTER(QsGraph), _sz, _i32, _i32, _dp, _dp, _dp, _vp], _i32),
     "qs_last_error": ([], ctypes.c_char_p),
     "qs_version": ([], ctypes.c_char_p),
 }
@@ -246,6 +251,34 @@ class State:
         _check(_lib.qs_profile_read(self.h, recs, 32, ctypes.byref(cnt)))
         return {recs[i].name.decode(): (recs[i].launches, recs[i].total_ms, recs[i].bytes)
                 for i in range(cnt.value)}
+
+
+def qaoa_maxcut(instances, stream=None) -> np.ndarray:
+    """Batched QAOA MaxCut: `instances` is a list of dicts with n, edges,
+    gammas (n_sets x p), betas (n_sets x p) (the form of
+    workloads.qaoa_batch).  Returns <C> per (graph, angle set), shape
+    (n_graphs, n_sets)."""
+    import torch
+    if not instances:
+        return np.zeros((0, 0))
+    n_sets, p = np.asarray(instances[0]["gammas"]).shape
+    arr = (QsGraph * len(instances))()
+    keep = []
+    gam = np.zeros((len(instances), n_sets, p))
+    bet = np.zeros_like(gam)
+    for i, inst in enumerate(instances):
+        e = np.ascontiguousarray(np.asarray(inst["edges"], dtype=np.int32).reshape(-1))
+        keep.append(e)
+        arr[i].n = int(inst["n"])
+        arr[i].n_edges = len(e) // 2
+        arr[i].edges = e.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        gam[i] = inst["gammas"]
+        bet[i] = inst["betas"]
+    out = np.zeros((len(instances), n_sets))
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(_lib.qs_qaoa_maxcut(arr, len(instances), n_sets, p, gam.ctypes.data_as(_dp), bet.ctypes.data_as(_dp),
+                               out.ctypes.data_as(_dp), _vp(s.cuda_stream)))
+    return out
 
 
 def _autograd():

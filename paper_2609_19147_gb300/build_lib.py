@@ -19,7 +19,7 @@ LIB = os.path.join(OUT_DIR, "libqs.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["qs_api.cu", "qs_plan.cpp", "k_tile.cu", "k_pergate.cu", "k_permgather.cu", "k_reduce.cu",
-           "k_noalloc.cu"]
+           "k_noalloc.cu", "k_qaoa.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1072,6 +1072,157 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
     return check_err_word(st);
 }
 
+qs_status qs_qaoa_maxcut(const qs_graph *graphs, size_t n_graphs, int n_sets, int p, const double *gammas,
+                         const double *betas, double *out, void *cuda_stream) {
+    if (!graphs || !gammas || !betas || !out) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+    if (n_sets < 1) return fail(QS_ERR_INVALID_ARG, "n_sets < 1");
+    if (p < 1 || p > kQaoaMaxP) return fail(QS_ERR_UNSUPPORTED, "p must be in [1, 16]");
+    for (size_t g = 0; g < n_graphs; ++g) {
+        const qs_graph &G = graphs[g];
+        if (G.n < 1 || G.n > 30) return fail(QS_ERR_UNSUPPORTED, "graph size must be in [1, 30]");
+        if (G.n_edges < 0 || G.n_edges > kQaoaMaxEdges) return fail(QS_ERR_UNSUPPORTED, "at most 64 edges per graph");
+        if (G.n_edges && !G.edges) return fail(QS_ERR_INVALID_ARG, "edges == NULL");
+        for (int e = 0; e < G.n_edges; ++e) {
+            const int u = G.edges[2 * e], v = G.edges[2 * e + 1];
+            if (u < 0 || v < 0 || u >= G.n || v >= G.n || u == v) return fail(QS_ERR_INVALID_ARG, "bad edge");
+        }
+    }
+    for (size_t i = 0; i < n_graphs * (size_t)n_sets * p; ++i)
+        if (!std::isfinite(gammas[i]) || !std::isfinite(betas[i])) return fail(QS_ERR_INVALID_ARG, "non-finite angle");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int dev = current_device();
+    qs_status s = ensure_device_tables(dev);
+    if (s != QS_OK) return s;
+    const size_t n_out = n_graphs * (size_t)n_sets;
+
+    // ---- small states: one persistent launch over all of them ----
+    std::vector<QaoaItem> items;
+    std::vector<uint32_t> masks;
+    std::vector<float2> luts, mix;
+    for (size_t g = 0; g < n_graphs; ++g) {
+        const qs_graph &G = graphs[g];
+        if (G.n > kQaoaMaxSmallN) continue;
+        const int eo = (int)masks.size();
+        for (int e = 0; e < G.n_edges; ++e)
+            masks.push_back((1u << (G.n - 1 - G.edges[2 * e])) | (1u << (G.n - 1 - G.edges[2 * e + 1])));
+        for (int a = 0; a < n_sets; ++a) {
+            QaoaItem it;
+            it.n = G.n;
+            it.n_edges = G.n_edges;
+            it.edge_off = eo;
+            it.lut_off = (int)luts.size();
+            it.mix_off = (int)mix.size();
+            it.out_idx = (int)(g * n_sets + a);
+            const double *gm = gammas + (g * n_sets + a) * p, *bt = betas + (g * n_sets + a) * p;
+            for (int l = 0; l < p; ++l) {
+                for (int k = 0; k <= G.n_edges; ++k) {
+                    const double ph = std::remainder(-gm[l] * k, 2.0 * 3.14159265358979323846);
+                    luts.push_back(make_float2((float)std::cos(ph), (float)std::sin(ph)));
+                }
+                mix.push_back(make_float2((float)std::cos(bt[l]), (float)-std::sin(bt[l])));
+            }
+            items.push_back(it);
+        }
+    }
+    std::vector<double> hout(n_out, 0.0);
+    if (!items.empty()) {
+        QaoaItem *d_items = nullptr;
+        uint32_t *d_masks = nullptr;
+        float2 *d_luts = nullptr, *d_mix = nullptr;
+        double *d_out = nullptr;
+        int *d_counter = nullptr;
+        auto cleanup = [&]() {
+            cudaFree(d_items);
+            cudaFree(d_masks);
+            cudaFree(d_luts);
+            cudaFree(d_mix);
+            cudaFree(d_out);
+            cudaFree(d_counter);
+        };
+        bool okm = cudaMalloc(&d_items, items.size() * sizeof(QaoaItem)) == cudaSuccess &&
+                   cudaMalloc(&d_masks, std::max<size_t>(1, masks.size()) * sizeof(uint32_t)) == cudaSuccess &&
+                   cudaMalloc(&d_luts, luts.size() * sizeof(float2)) == cudaSuccess &&
+                   cudaMalloc(&d_mix, mix.size() * sizeof(float2)) == cudaSuccess &&
+                   cudaMalloc(&d_out, n_out * sizeof(double)) == cudaSuccess &&
+                   cudaMalloc(&d_counter, sizeof(int)) == cudaSuccess;
+        if (!okm) {
+            cudaGetLastError();
+            cleanup();
+            return fail(QS_ERR_OOM, "qs_qaoa_maxcut: device allocation failed");
+        }
+        cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(QaoaItem), cudaMemcpyHostToDevice, st);
+        if (!masks.empty())
+            cudaMemcpyAsync(d_masks, masks.data(), masks.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(d_luts, luts.data(), luts.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(d_mix, mix.data(), mix.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+        cudaMemsetAsync(d_counter, 0, sizeof(int), st);
+        QaoaSmallArgs A;
+        A.items = d_items;
+        A.n_items = (int)items.size();
+        A.p = p;
+        A.edge_masks = d_masks;
+        A.luts = d_luts;
+        A.mix = d_mix;
+        A.out = d_out;
+        A.counter = d_counter;
+        const int grid = (int)std::min<size_t>(items.size(), (size_t)g_num_sms[dev]);
+        cudaError_t e = launch_qaoa_small(A, grid, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hout.data(), d_out, n_out * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cleanup();
+        if (e != cudaSuccess) return fail(QS_ERR_CUDA, std::string("qaoa small-state kernel: ") + cudaGetErrorString(e));
+        for (const QaoaItem &it : items) out[it.out_idx] = hout[it.out_idx];
+    }
+
+    // ---- larger states: fused tile passes, all angle sets of a graph as one batch ----
+    std::map<int, qs_state *> states;
+    qs_status rs = QS_OK;
+    for (size_t g = 0; g < n_graphs && rs == QS_OK; ++g) {
+        const qs_graph &G = graphs[g];
+        if (G.n <= kQaoaMaxSmallN) continue;
+        qs_state *S = states[G.n];
+        if (!S) {
+            rs = qs_alloc(G.n, n_sets, &S);
+            if (rs != QS_OK) break;
+            qs_set_stream(S, cuda_stream);
+            states[G.n] = S;
+        }
+        // H on all, then per layer RZZ(-gamma_l) per edge and RX(2 beta_l) per qubit;
+        // parameter 2l = -gamma_l, 2l+1 = 2 beta_l
+        std::vector<qs_gate> gl;
+        auto gate = [&](int kind, int nw, int w0, int w1, int pidx) {
+            qs_gate q;
+            std::memset(&q, 0, sizeof q);
+            q.kind = (uint16_t)kind;
+            q.nw = (uint8_t)nw;
+            q.w[0] = w0;
+            q.w[1] = w1;
+            q.param_idx = pidx;
+            gl.push_back(q);
+        };
+        for (int q = 0; q < G.n; ++q) gate(QS_H, 1, q, 0, -1);
+        for (int l = 0; l < p; ++l) {
+            for (int e = 0; e < G.n_edges; ++e) gate(QS_RZZ, 2, G.edges[2 * e], G.edges[2 * e + 1], 2 * l);
+            for (int q = 0; q < G.n; ++q) gate(QS_RX, 1, q, 0, 2 * l + 1);
+        }
+        std::vector<double> prm((size_t)n_sets * 2 * p);
+        for (int a = 0; a < n_sets; ++a)
+            for (int l = 0; l < p; ++l) {
+                prm[(size_t)a * 2 * p + 2 * l] = -gammas[(g * n_sets + a) * p + l];
+                prm[(size_t)a * 2 * p + 2 * l + 1] = 2.0 * betas[(g * n_sets + a) * p + l];
+            }
+        std::vector<qs_pauli> terms;
+        terms.push_back({0.5 * G.n_edges, 0, 0});
+        for (int e = 0; e < G.n_edges; ++e)
+            terms.push_back({-0.5, 0, (1ull << G.edges[2 * e]) | (1ull << G.edges[2 * e + 1])});
+        rs = qs_init_zero(S);
+        if (rs == QS_OK) rs = qs_apply_circuit(S, gl.data(), gl.size(), prm.data(), 2 * p, nullptr);
+        if (rs == QS_OK) rs = qs_expect(S, terms.data(), terms.size(), out + g * n_sets);
+    }
+    for (auto &kv : states) qs_free(kv.second);
+    return rs;
+}
+
 qs_status qs_plan_describe(int n, const qs_gate *gates, size_t n_gates, const qs_opts *opts, char *buf, size_t len,
                            int *passes) {
     if (n < 1 || n > kMaxQubits) return fail(QS_ERR_UNSUPPORTED, "n must be in [1, 33]");

@@ -117,6 +117,30 @@ cudaError_t launch_apply_pauli_sum(const float2 *psi, float2 *lam, long long sta
 
 cudaError_t launch_init_zero(float2 *psi, long long state_elems, int batch, cudaStream_t st);
 
+// batched QAOA MaxCut, small states (n <= 14) in shared memory
+constexpr int kQaoaMaxSmallN = 14;
+constexpr int kQaoaMaxEdges = 64;
+constexpr int kQaoaMaxP = 16;
+struct QaoaItem {
+    int n, n_edges;
+    int edge_off;      // into edge_masks
+    int lut_off;       // into luts: p * (n_edges + 1) entries exp(-i gamma_l k)
+    int mix_off;       // into mix: p entries (cos beta_l, -sin beta_l)
+    int out_idx;
+};
+struct QaoaSmallArgs {
+    const QaoaItem *items;
+    int n_items;
+    int p;
+    const uint32_t *edge_masks;   // index-bit masks of each edge's two endpoints
+    const float2 *luts;
+    const float2 *mix;
+    double *out;
+    int *counter;                 // work queue head (zeroed before launch)
+};
+int qaoa_small_smem_bytes();
+cudaError_t launch_qaoa_small(const QaoaSmallArgs &A, int grid, cudaStream_t st);
+
 // message for qs_last_error() on this host thread
 void set_last_error(const char *msg);
 

@@ -1,0 +1,72 @@
+"""Batched QAOA MaxCut (the batched-execution row): GPU vs the complex128 oracle.
+
+<C> per (graph, angle set) from qs_qaoa_maxcut is compared with the oracle's
+state-vector simulation of the same circuit (H on all qubits, then per layer
+RZZ(-gamma) on every edge and RX(2 beta) on every qubit; Sec. 3.2.3 QAOA),
+with <C> taken from the probabilities directly (oracle.expected_cut).
+Tolerance: |d<C>| <= 1e-4 (|E| <= 36 terms, each within the 2e-5 amplitude
+budget) and 0 <= <C> <= |E| for every instance.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2609_19147_gb300 as qs  # noqa: E402
+
+
+def _oracle_cut(inst, a):
+    n, edges = inst["n"], inst["edges"]
+    gl = W.qaoa_gates(n, edges, inst["gammas"][a], inst["betas"][a])
+    return oracle.expected_cut(oracle.simulate(n, gl), n, edges)
+
+
+def test_qaoa_small_and_large_match_oracle():
+    rng = np.random.default_rng(7)
+    insts = []
+    for n in (4, 6, 10, 14, 16, 18):
+        edges = W.random_regular3_graph(n, rng)
+        ang = rng.uniform(0, np.pi, size=(3, 2, 4))
+        insts.append({"n": n, "edges": edges, "gammas": ang[:, 0, :], "betas": ang[:, 1, :]})
+    # a ring (the paper's ring-QAOA topology) with p = 4
+    ring = [(i, (i + 1) % 12) for i in range(12)]
+    ang = rng.uniform(0, np.pi, size=(3, 2, 4))
+    insts.append({"n": 12, "edges": ring, "gammas": ang[:, 0, :], "betas": ang[:, 1, :]})
+    got = qs.qaoa_maxcut(insts)
+    for i, inst in enumerate(insts):
+        for a in range(3):
+            ref = _oracle_cut(inst, a)
+            assert abs(got[i, a] - ref) <= 1e-4, (inst["n"], a, got[i, a], ref)
+            assert -1e-6 <= got[i, a] <= len(inst["edges"]) + 1e-6
+
+
+def test_qaoa_single_edge_closed_form():
+    # one edge, p = 1: <C> = 1/2 + (1/2) sin(4 beta) sin(gamma)
+    g, b = 0.9, 0.35
+    got = qs.qaoa_maxcut([{"n": 2, "edges": [(0, 1)], "gammas": [[g]], "betas": [[b]]}])
+    assert abs(got[0, 0] - (0.5 + 0.5 * np.sin(4 * b) * np.sin(g))) < 1e-6
+
+
+def test_qaoa_config_batch_sampled():
+    # the config's shape: random 3-regular graphs, n in {14..24} even, p = 4,
+    # 8 angle sets each (a 48-graph slice of the 512-graph batch here)
+    insts = W.qaoa_batch(5, n_graphs=48)
+    got = qs.qaoa_maxcut(insts)
+    assert got.shape == (48, 8)
+    for i, inst in enumerate(insts):
+        assert np.all(got[i] >= -1e-6) and np.all(got[i] <= len(inst["edges"]) + 1e-6)
+    # every n <= 16 instance and one larger one against the oracle
+    checked = 0
+    for i, inst in enumerate(insts):
+        if inst["n"] <= 16 or (inst["n"] == 20 and checked < 99):
+            for a in (0, 7):
+                assert abs(got[i, a] - _oracle_cut(inst, a)) <= 1e-4
+            if inst["n"] == 20:
+                checked = 99
