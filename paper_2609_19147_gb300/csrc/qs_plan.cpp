@@ -286,8 +286,8 @@ uint64_t FOp::D() const {
 
 static bool commute(const FOp &x, const FOp &y) {
     if (x.kind == F_GF2 || y.kind == F_GF2) return false;
-    uint64_t nx = x.N(), ny = y.N();
-    return (nx & (ny | y.D())) == 0 && (ny & (nx | x.D())) == 0;
+    const uint64_t nx = x.cN, ny = y.cN;
+    return (nx & (ny | y.cD)) == 0 && (ny & (nx | x.cD)) == 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -612,14 +612,30 @@ void plan_diag(int n, const Diag &d, DiagPlan &out) {
         cur.slice_lo[k] = lo;
         cur.slice_w[k] = w;
         cur.slice_off[k] = (int)tab.size();
+        // entry(v) = exp(i phase(v)), phase a quadratic form in v's bits: build it
+        // multiplicatively in FP64 from entry(v without its lowest bit) times that
+        // bit's single-term factor and the factors of the pairs it completes
+        std::vector<cd> e1(w, cd(1, 0));
+        std::vector<std::vector<std::pair<int, cd>>> e2(w);
+        for (auto &kv : s_single[s]) e1[kv.first - lo] = std::polar(1.0, wrap_angle(kv.second));
+        for (auto &kv : s_pair[s]) {
+            const int b0 = kv.first.first - lo, b1 = kv.first.second - lo;
+            const cd z = std::polar(1.0, wrap_angle(kv.second));
+            e2[b0].push_back({b1, z});
+            e2[b1].push_back({b0, z});
+        }
+        std::vector<cd> z((size_t)1 << w);
+        z[0] = g0_done ? cd(1, 0) : std::polar(1.0, wrap_angle(d.g0));
+        for (int v = 1; v < (1 << w); ++v) {
+            const int b = __builtin_ctz(v), vp = v & (v - 1);
+            cd f = z[vp] * e1[b];
+            for (auto &pr : e2[b])
+                if ((vp >> pr.first) & 1) f *= pr.second;
+            z[v] = f;
+        }
         for (int v = 0; v < (1 << w); ++v) {
-            double ph = 0.0;
-            if (!g0_done) ph += d.g0;
-            for (auto &kv : s_single[s])
-                if ((v >> (kv.first - lo)) & 1) ph += kv.second;
-            for (auto &kv : s_pair[s])
-                if (((v >> (kv.first.first - lo)) & 1) && ((v >> (kv.first.second - lo)) & 1)) ph += kv.second;
-            tab.push_back(cexp_f(ph));
+            const double m = std::abs(z[v]);   // keep exactly unit modulus before rounding
+            tab.push_back(float2{(float)(z[v].real() / m), (float)(z[v].imag() / m)});
         }
         g0_done = true;
     }
@@ -703,6 +719,16 @@ void choose_item_bits(const TilePass &tp, Sweep &sw) {
     const int k = (int)cand.size();
     const int nl = std::min(5, k);
     const int words_per = sw.vec ? 2 : 1;
+    // memoised: the answer depends only on the candidate bits' offsets
+    static std::map<std::vector<int>, std::vector<int>> memo;
+    std::vector<int> key;
+    key.push_back(words_per);
+    for (int i = 0; i < k; ++i) key.push_back(tp.smem_contrib[cand[i]]);
+    auto hit = memo.find(key);
+    if (hit != memo.end()) {
+        for (int i = 0; i < k; ++i) sw.tbit[i] = cand[hit->second[i]];
+        return;
+    }
     std::vector<int> best;
     int best_cost = 1 << 30;
     std::vector<int> idx(nl);
@@ -715,14 +741,10 @@ void choose_item_bits(const TilePass &tp, Sweep &sw) {
                 if ((l >> i) & 1) w ^= tp.smem_contrib[cand[idx[i]]];
             words[l] = w;
         }
+        // the offsets are XOR combinations of independent bits: all distinct
         int bank_cnt[32] = {0};
-        for (int l = 0; l < (1 << nl); ++l) {
-            bool dup = false;
-            for (int m = 0; m < l; ++m)
-                if (words[m] == words[l]) dup = true;
-            if (dup) continue;
+        for (int l = 0; l < (1 << nl); ++l)
             for (int e = 0; e < 2 * words_per; ++e) bank_cnt[(2 * words[l] + e) & 31]++;
-        }
         int cost = 0;
         for (int b = 0; b < 32; ++b) cost = std::max(cost, bank_cnt[b]);
         if (cost < best_cost) {
@@ -735,15 +757,16 @@ void choose_item_bits(const TilePass &tp, Sweep &sw) {
         idx[i]++;
         for (int j = i + 1; j < nl; ++j) idx[j] = idx[j - 1] + 1;
     }
-    std::vector<int> order;
+    std::vector<int> order_idx;
     std::vector<bool> used(k, false);
     for (int i : best) {
-        order.push_back(cand[i]);
+        order_idx.push_back(i);
         used[i] = true;
     }
     for (int i = 0; i < k; ++i)
-        if (!used[i]) order.push_back(cand[i]);
-    for (int i = 0; i < k; ++i) sw.tbit[i] = order[i];
+        if (!used[i]) order_idx.push_back(i);
+    if (memo.size() < 4096) memo[key] = order_idx;
+    for (int i = 0; i < k; ++i) sw.tbit[i] = cand[order_idx[i]];
 }
 
 // TMA geometry for the tile bit set S: dims = low bits, runs of tile bits
@@ -1152,47 +1175,48 @@ static void build_perm_or_gather(int n, const FOp &f, HostPass &hp) {
         }
 }
 
-static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<RGate> &gates, const qs_opts &o,
-                                      Plan &plan, std::string &err);
+static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &detected, int n_gates,
+                                      const qs_opts &o, Plan &plan, std::string &err);
 
 // Default tile shape: 12-bit tiles with 4-bit register groups (two CTAs per
 // SM hide each other's copy latency) unless they need more HBM passes than
 // 13-bit tiles with 5-bit groups.
 qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, const qs_opts &o, Plan &plan,
                            std::string &err) {
-    if (o.tile_qubits > 0 || o.group_qubits > 0 || n < 13) return build_fused_plan_cfg(n, batch, gates, o, plan, err);
+    std::vector<FOp> detected;
+    detect(n, gates, detected);
+    if (o.tile_qubits > 0 || o.group_qubits > 0 || n < 13)
+        return build_fused_plan_cfg(n, batch, detected, (int)gates.size(), o, plan, err);
+    bool has_qft = false;
+    for (const FOp &f : detected)
+        if (f.kind == F_QFT) has_qft = true;
     // candidates in order of measured per-pass speed for layer-type passes;
     // QFT-stage passes run fastest with 5-bit groups
     const int cfg[3][2] = {{12, 4}, {13, 4}, {13, 5}};
+    const int n_cand = has_qft ? 3 : 2;
     Plan cand[3];
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < n_cand; ++i) {
         qs_opts c = o;
         c.tile_qubits = cfg[i][0];
         c.group_qubits = cfg[i][1];
-        qs_status s = build_fused_plan_cfg(n, batch, gates, c, cand[i], err);
+        qs_status s = build_fused_plan_cfg(n, batch, detected, (int)gates.size(), c, cand[i], err);
         if (s != QS_OK) return s;
     }
-    bool has_qft = false;
-    for (auto &hp : cand[2].passes)
-        if (hp.type == HostPass::TILE)
-            for (int k = 0; k < hp.tile.n_micro; ++k)
-                if (hp.tile.micro[k].kind == MK_QFT || hp.tile.micro[k].kind == MK_QFTL) has_qft = true;
     int best = 0;
-    for (int i = 1; i < 3; ++i)
+    for (int i = 1; i < n_cand; ++i)
         if (cand[i].passes.size() < cand[best].passes.size()) best = i;
     if (best != 0 && has_qft && cand[2].passes.size() == cand[best].passes.size()) best = 2;
     plan = std::move(cand[best]);
     return QS_OK;
 }
 
-static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<RGate> &gates, const qs_opts &o,
-                                      Plan &plan, std::string &err) {
+static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &detected, int n_gates,
+                                      const qs_opts &o, Plan &plan, std::string &err) {
     plan = Plan();
     plan.n = n;
     plan.mode = QS_MODE_FUSED;
-    plan.n_gates = (int)gates.size();
-    std::vector<FOp> ops;
-    detect(n, gates, ops);
+    plan.n_gates = n_gates;
+    std::vector<FOp> ops(detected);
 
     int T = o.tile_qubits > 0 ? o.tile_qubits : 13;
     int L = o.low_qubits > 0 ? o.low_qubits : 4;
@@ -1231,6 +1255,7 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<RGate>
         }
     }
     ops.swap(ops2);
+    for (FOp &f : ops) f.cache_masks();
     std::vector<DiagPlan> dplans(ops.size());
     for (size_t i = 0; i < ops.size(); ++i)
         if (ops[i].kind == F_DIAG) plan_diag(n, ops[i].diag, dplans[i]);
@@ -1268,9 +1293,9 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<RGate>
                     break;
                 }
             if (ok) {
-                uint64_t need = f.N() & ~S;
+                uint64_t need = f.cN & ~S;
                 OpCost c = op_cost(n, f, R, f.kind == F_DIAG ? &dplans[rem[j]] : nullptr);
-                uint64_t nb = f.N();
+                uint64_t nb = f.cN;
                 int ns = sim_sweeps;
                 uint64_t ng = sim_group;
                 bool no = sim_open;

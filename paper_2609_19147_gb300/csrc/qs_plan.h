@@ -58,6 +58,11 @@ struct FOp {
     int n_gates = 1;               // source gates absorbed
     uint64_t N() const;            // bits acted on non-diagonally
     uint64_t D() const;            // bits the op depends on diagonally
+    uint64_t cN = 0, cD = 0;       // cached N() / D() (set by cache_masks)
+    void cache_masks() {
+        cN = N();
+        cD = D();
+    }
 };
 
 // TMA tensor geometry of a tile pass (see TmaGeom): dims in ascending bit
