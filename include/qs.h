@@ -97,6 +97,30 @@ enum qs_mode {
     QS_MODE_PERGATE = 1  /* one kernel launch per gate: the baseline path    */
 };
 
+/* Dense k-qubit blocks (fused mode only).  With dense_prec != QS_DENSE_OFF
+ * the detector's output is regrouped into dense blocks of at most
+ * block_qubits qubits (generic matrix fusion, which the paper's appendix
+ * "Complete Per-Workload Speedups" names as the next extension):
+ * consecutive 1- and 2-qubit ops and the in-block part of diagonal layers
+ * are multiplied into one 2^k x 2^k complex matrix in FP64; the parts of
+ * diagonal layers that cross blocks (the boundary bonds of a ZZ layer) stay
+ * diagonal.  Blocks of 3..5 qubits are applied inside the tile pass as
+ * out = U X over 5 tile bits (smaller blocks padded with the identity), in
+ * the chosen arithmetic:
+ *   QS_DENSE_FP32   -- FP32 FMA on the CUDA cores;
+ *   QS_DENSE_TF32X3 -- tensor cores, split precision: U = U_hi + U_lo and
+ *                      X = X_hi + X_lo in TF32, U_hi X_hi + U_hi X_lo +
+ *                      U_lo X_hi accumulated in FP32 (about FP32 accuracy);
+ *   QS_DENSE_BF16   -- tensor cores, U and X rounded to BF16 with FP32
+ *                      accumulation (about 3 significant digits per block).
+ * Blocks of 1-2 qubits run as the ordinary FP32 2x2 / 4x4 micro-ops. */
+enum qs_dense_prec {
+    QS_DENSE_OFF = 0,
+    QS_DENSE_FP32 = 1,
+    QS_DENSE_TF32X3 = 2,
+    QS_DENSE_BF16 = 3
+};
+
 /* Options for qs_apply_circuit / qs_plan_describe; NULL means defaults. */
 typedef struct qs_opts {
     int32_t mode;         /* enum qs_mode                                    */
@@ -104,6 +128,8 @@ typedef struct qs_opts {
     int32_t low_qubits;   /* contiguous low bits per tile row, 0 = default   */
     int32_t group_qubits; /* tile bits held in registers per sweep (1..5),
                              0 = default (5)                                 */
+    int32_t dense_prec;   /* enum qs_dense_prec, 0 = off                      */
+    int32_t block_qubits; /* largest dense block (3..5), 0 = default (5)      */
 } qs_opts;
 
 typedef struct qs_state qs_state;

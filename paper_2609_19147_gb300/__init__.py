@@ -47,7 +47,11 @@ class QsPauli(ctypes.Structure):
 
 class QsOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("tile_qubits", ctypes.c_int32), ("low_qubits", ctypes.c_int32),
-                ("group_qubits", ctypes.c_int32)]
+                ("group_qubits", ctypes.c_int32), ("dense_prec", ctypes.c_int32), ("block_qubits", ctypes.c_int32)]
+
+
+# qs_dense_prec: arithmetic of the dense k-qubit blocks (None / "off" = no dense blocks)
+DENSE_PREC = {None: 0, "off": 0, "fp32": 1, "tf32x3": 2, "bf16": 3}
 
 
 class QsGraph(ctypes.Structure):
@@ -142,22 +146,26 @@ def _paulis(terms) -> Tuple[ctypes.Array, int]:
     return arr, len(terms)
 
 
-def _opts(mode="fused", tile_qubits=0, low_qubits=0, group_qubits=0) -> QsOpts:
+def _opts(mode="fused", tile_qubits=0, low_qubits=0, group_qubits=0, dense=None, block_qubits=0) -> QsOpts:
     o = QsOpts()
     o.mode = MODE_PERGATE if mode == "pergate" else MODE_FUSED
     o.tile_qubits = int(tile_qubits)
     o.low_qubits = int(low_qubits)
     o.group_qubits = int(group_qubits)
+    if dense not in DENSE_PREC:
+        raise ValueError(f"dense must be one of {sorted(k for k in DENSE_PREC if k)}, got {dense!r}")
+    o.dense_prec = DENSE_PREC[dense]
+    o.block_qubits = int(block_qubits)
     return o
 
 
 def plan_describe(n: int, gates, mode: str = "fused", tile_qubits: int = 0, low_qubits: int = 0,
-                  group_qubits: int = 0):
+                  group_qubits: int = 0, dense=None, block_qubits: int = 0):
     """The detector's plan as text and its number of HBM passes (no GPU needed)."""
     cg = gates if isinstance(gates, CGates) else CGates(gates)
     buf = ctypes.create_string_buffer(1 << 20)
     passes = ctypes.c_int(0)
-    o = _opts(mode, tile_qubits, low_qubits, group_qubits)
+    o = _opts(mode, tile_qubits, low_qubits, group_qubits, dense, block_qubits)
     _check(_lib.qs_plan_describe(n, cg.arr, cg.n, ctypes.byref(o), buf, len(buf), ctypes.byref(passes)))
     return buf.value.decode(), passes.value
 
@@ -215,9 +223,10 @@ class State:
         return out
 
     def apply(self, gates, params: Optional[np.ndarray] = None, mode: str = "fused",
-              tile_qubits: int = 0, low_qubits: int = 0, group_qubits: int = 0):
+              tile_qubits: int = 0, low_qubits: int = 0, group_qubits: int = 0, dense=None,
+              block_qubits: int = 0):
         cg = gates if isinstance(gates, CGates) else CGates(gates)
-        o = _opts(mode, tile_qubits, low_qubits, group_qubits)
+        o = _opts(mode, tile_qubits, low_qubits, group_qubits, dense, block_qubits)
         if params is not None:
             p = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(self.batch, -1))
             self._params = p

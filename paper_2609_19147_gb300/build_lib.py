@@ -18,8 +18,10 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libqs.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["qs_api.cu", "qs_plan.cpp", "k_tile.cu", "k_pergate.cu", "k_permgather.cu", "k_reduce.cu",
-           "k_noalloc.cu", "k_qaoa.cu"]
+# the tile-pass kernel instantiations are split over several units (compiled
+# in parallel): k_tile_r5.cu and k_tile_dense.cu take the longest
+SOURCES = ["k_tile_dense.cu", "k_tile_r5.cu", "k_tile_r4.cu", "k_tile_r123.cu", "qs_api.cu", "qs_plan.cpp",
+           "k_tile.cu", "k_pergate.cu", "k_permgather.cu", "k_reduce.cu", "k_noalloc.cu", "k_qaoa.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,7 +41,7 @@ def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")] + \
+    deps = [src] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))] + \
         [os.path.join(INCLUDE, "qs.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 

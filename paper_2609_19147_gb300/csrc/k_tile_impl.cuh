@@ -1,0 +1,1143 @@
+// Tile-pass engine (sm_103a): the kernel template, included by the
+// translation units that instantiate it (k_tile_*.cu) so that they compile in
+// parallel.
+//
+// One launch = one full-state HBM pass.  Each persistent CTA walks its tiles.
+// A tile is 2^T amplitudes: the L low index bits plus the pass's high bits
+// hb[].  It moves HBM <-> shared memory as ONE multi-dimensional TMA tensor
+// copy (cp.async.bulk.tensor, 128-byte swizzle): the state is described to the
+// TMA unit as a <=5-D tensor whose dims are the low bits, the contiguous runs
+// of tile bits and the gaps of non-tile bits between them (the tile selects a
+// box of extent 1 in every gap).  When the bit set needs more than 5 dims the
+// pass falls back to one bulk copy per 2^L-amplitude row.
+//
+// Tiles rotate through 2-3 shared buffers: while the 8 warps process tile k,
+// the load of tile k+1 and the stores of tiles k-1 (and k-2) are in flight.
+// Thread 0 issues the copies; with 3 buffers the buffer it refills was
+// stored two tiles ago, so waiting for that store to have read shared memory
+// does not stall.
+//
+// Between load and store the tile goes through "sweeps": every compute thread
+// holds 2^R amplitudes that differ in R tile bits (registers) and applies the
+// sweep's micro-ops: 2x2 / 4x4 unitaries with controls (with cheaper forms for
+// real and RX-type matrices), diagonal phase tables (factored into an item part
+// and a group part), and QFT stages (Hadamard butterfly + closed-form ladder
+// twiddle; Sec. 5.1).  Butterfly normalisations are folded into one scale per
+// sweep.  Shared-memory offsets are XOR-linear in the tile bits, which covers
+// the swizzled layout.
+//
+// All waits are bounded; on expiry the kernel records QS_ERR_TIMEOUT, lets its
+// own copies land and returns.
+#pragma once
+
+#include <cuda.h>
+
+#include <string>
+
+#include "qs_internal.h"
+#include "qs_kernels.h"
+
+namespace qs {
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait: gives up after ~2 s of wall time
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 255 && globaltimer() - t0 > 2000000000ull) return false;
+    }
+}
+__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void *dst_gmem, const void *src_smem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem),
+                 "r"(smem_u32(src_smem)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_5d(void *dst_smem, const CUtensorMap *tm, const int c[5], uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst_smem)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap *tm, const int c[5], const void *src_smem) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5, %6}], [%1];" ::"l"(
+            reinterpret_cast<uint64_t>(tm)),
+        "r"(smem_u32(src_smem)), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4])
+        : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_l2_5d(const CUtensorMap *tm, const int c[5]) {
+    asm volatile("cp.async.bulk.prefetch.tensor.5d.L2.global.tile [%0, {%1, %2, %3, %4, %5}];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4])
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src_gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src_gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_read0() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmad(float2 a, float2 b, float2 c) {   // a*b + c
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+
+// exp(i pi u / 2^p) for 0 <= u < 2^p, p <= 32, from the FP64-built roots
+__device__ __forceinline__ float2 twiddle(uint64_t u, int p, const float2 *roots) {
+    if (p == 0 || u == 0) return make_float2(1.f, 0.f);
+    uint32_t v = (uint32_t)(u << (32 - p));
+    float2 w = roots[v & 255];
+    w = cmul(w, roots[256 + ((v >> 8) & 255)]);
+    w = cmul(w, roots[512 + ((v >> 16) & 255)]);
+    w = cmul(w, roots[768 + (v >> 24)]);
+    return w;
+}
+
+// product of the diagonal's slice/group factors selected by the masks
+__device__ __forceinline__ float2 diag_part(const DiagDesc &d, uint64_t x, const float2 *cs, uint32_t smask,
+                                            uint32_t gmask, float2 ph) {
+    for (int s = 0; s < d.n_slices; ++s)
+        if ((smask >> s) & 1)
+            ph = cmul(ph, cs[d.slice_off[s] + (int)((x >> d.slice_lo[s]) & ((1u << d.slice_w[s]) - 1))]);
+    for (int g = 0; g < d.n_groups; ++g)
+        if ((gmask >> g) & 1) {
+            uint64_t f = d.grp_type[g] ? (x & (x >> d.grp_d[g])) : (x ^ (x >> d.grp_d[g]));
+            ph = cmul(ph, cs[d.grp_off[g] + __popcll(f & d.grp_mask[g])]);
+        }
+    return ph;
+}
+
+// ---------------------------------------------------------------------------
+// micro-ops on a register group a[0 .. 2^R)
+// ---------------------------------------------------------------------------
+template <int R>
+struct Grp {
+    uint64_t gg[R];   // global-index contribution of each group bit
+    __device__ __forceinline__ uint64_t gidx(uint64_t base, int j) const {
+        uint64_t x = base;
+#pragma unroll
+        for (int m = 0; m < R; ++m)
+            if ((j >> m) & 1) x |= gg[m];
+        return x;
+    }
+};
+
+template <int R, int M>
+__device__ __forceinline__ void op_u1(float2 (&a)[1 << R], const float2 *mat, uint64_t cmask, uint64_t cval,
+                                      uint64_t base, const Grp<R> &G) {
+    const float2 m00 = mat[0], m01 = mat[1], m10 = mat[2], m11 = mat[3];
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) {
+        if ((j >> M) & 1) continue;
+        const int k = j | (1 << M);
+        float2 a0 = a[j], a1 = a[k];
+        float2 b0 = cmad(m01, a1, cmul(m00, a0));
+        float2 b1 = cmad(m11, a1, cmul(m10, a0));
+        if (cmask) {
+            const bool c = (G.gidx(base, j) & cmask) == cval;
+            b0 = c ? b0 : a0;
+            b1 = c ? b1 : a1;
+        }
+        a[j] = b0;
+        a[k] = b1;
+    }
+}
+
+// [[c, i s], [i s, c]] (RX(t): c = cos t/2, s = -sin t/2): 4 FP32 ops per amplitude
+template <int R, int M>
+__device__ __forceinline__ void op_rxc(float2 (&a)[1 << R], const float2 *cs) {
+    const float c = cs[0].x, s = cs[0].y;
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) {
+        if ((j >> M) & 1) continue;
+        const int k = j | (1 << M);
+        const float2 a0 = a[j], a1 = a[k];
+        a[j] = make_float2(fmaf(c, a0.x, -s * a1.y), fmaf(c, a0.y, s * a1.x));
+        a[k] = make_float2(fmaf(c, a1.x, -s * a0.y), fmaf(c, a1.y, s * a0.x));
+    }
+}
+
+// real 2x2 (RY family): 4 FP32 ops per amplitude
+template <int R, int M>
+__device__ __forceinline__ void op_u1r(float2 (&a)[1 << R], const float2 *cs) {
+    const float m00 = cs[0].x, m01 = cs[0].y, m10 = cs[1].x, m11 = cs[1].y;
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) {
+        if ((j >> M) & 1) continue;
+        const int k = j | (1 << M);
+        const float2 a0 = a[j], a1 = a[k];
+        a[j] = make_float2(fmaf(m00, a0.x, m01 * a1.x), fmaf(m00, a0.y, m01 * a1.y));
+        a[k] = make_float2(fmaf(m10, a0.x, m11 * a1.x), fmaf(m10, a0.y, m11 * a1.y));
+    }
+}
+
+// unnormalised Hadamard butterfly (the 1/sqrt 2 is folded into the sweep scale)
+template <int R, int M>
+__device__ __forceinline__ void op_h(float2 (&a)[1 << R]) {
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) {
+        if ((j >> M) & 1) continue;
+        const int k = j | (1 << M);
+        const float2 a0 = a[j], a1 = a[k];
+        a[j] = make_float2(a0.x + a1.x, a0.y + a1.y);
+        a[k] = make_float2(a0.x - a1.x, a0.y - a1.y);
+    }
+}
+
+// QFT stage: butterfly on bit M, then the ladder phase on the bit-M = 1 half:
+// item twiddle w times the group-bit twiddle gtab[k]
+template <int R, int M>
+__device__ __forceinline__ void op_qft(float2 (&a)[1 << R], const float2 *gtab, float2 w) {
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) {
+        if ((j >> M) & 1) continue;
+        const int k = j | (1 << M);
+        const float2 a0 = a[j], a1 = a[k];
+        a[j] = make_float2(a0.x + a1.x, a0.y + a1.y);
+        a[k] = cmul(make_float2(a0.x - a1.x, a0.y - a1.y), cmul(w, gtab[k]));
+    }
+}
+
+template <int R, int MA, int MB>
+__device__ __forceinline__ void op_u2(float2 (&a)[1 << R], const float2 *mat, uint64_t cmask, uint64_t cval,
+                                      uint64_t base, const Grp<R> &G) {
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) {
+        if (((j >> MA) & 1) || ((j >> MB) & 1)) continue;
+        if (cmask && (G.gidx(base, j) & cmask) != cval) continue;   // control bits are never MA/MB
+        const int i0 = j, i1 = j | (1 << MB), i2 = j | (1 << MA), i3 = j | (1 << MA) | (1 << MB);
+        const float2 v0 = a[i0], v1 = a[i1], v2 = a[i2], v3 = a[i3];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            float2 acc = cmul(mat[r * 4 + 0], v0);
+            acc = cmad(mat[r * 4 + 1], v1, acc);
+            acc = cmad(mat[r * 4 + 2], v2, acc);
+            acc = cmad(mat[r * 4 + 3], v3, acc);
+            a[r == 0 ? i0 : r == 1 ? i1 : r == 2 ? i2 : i3] = acc;
+        }
+    }
+}
+
+// runtime group bit -> template dispatch
+template <int R, int M = 0>
+__device__ __forceinline__ void disp_u1(int m, float2 (&a)[1 << R], const float2 *mat, uint64_t cm, uint64_t cv,
+                                        uint64_t base, const Grp<R> &G) {
+    if constexpr (M < R) {
+        if (m == M) op_u1<R, M>(a, mat, cm, cv, base, G);
+        else disp_u1<R, M + 1>(m, a, mat, cm, cv, base, G);
+    }
+}
+template <int R, int M = 0>
+__device__ __forceinline__ void disp_rxc(int m, float2 (&a)[1 << R], const float2 *cs) {
+    if constexpr (M < R) {
+        if (m == M) op_rxc<R, M>(a, cs);
+        else disp_rxc<R, M + 1>(m, a, cs);
+    }
+}
+template <int R, int M = 0>
+__device__ __forceinline__ void disp_u1r(int m, float2 (&a)[1 << R], const float2 *cs) {
+    if constexpr (M < R) {
+        if (m == M) op_u1r<R, M>(a, cs);
+        else disp_u1r<R, M + 1>(m, a, cs);
+    }
+}
+template <int R, int M = 0>
+__device__ __forceinline__ void disp_h(int m, float2 (&a)[1 << R]) {
+    if constexpr (M < R) {
+        if (m == M) op_h<R, M>(a);
+        else disp_h<R, M + 1>(m, a);
+    }
+}
+template <int R, int M = 0>
+__device__ __forceinline__ void disp_qft(int m, float2 (&a)[1 << R], const float2 *gtab, float2 w) {
+    if constexpr (M < R) {
+        if (m == M) op_qft<R, M>(a, gtab, w);
+        else disp_qft<R, M + 1>(m, a, gtab, w);
+    }
+}
+template <int R, int MA, int MB = 0>
+__device__ __forceinline__ void disp_u2b(int mb, float2 (&a)[1 << R], const float2 *mat, uint64_t cm, uint64_t cv,
+                                         uint64_t base, const Grp<R> &G) {
+    if constexpr (MB < R) {
+        if constexpr (MB != MA) {
+            if (mb == MB) {
+                op_u2<R, MA, MB>(a, mat, cm, cv, base, G);
+                return;
+            }
+        }
+        disp_u2b<R, MA, MB + 1>(mb, a, mat, cm, cv, base, G);
+    }
+}
+template <int R, int MA = 0>
+__device__ __forceinline__ void disp_u2(int ma, int mb, float2 (&a)[1 << R], const float2 *mat, uint64_t cm,
+                                        uint64_t cv, uint64_t base, const Grp<R> &G) {
+    if constexpr (MA < R) {
+        if (ma == MA) disp_u2b<R, MA>(mb, a, mat, cm, cv, base, G);
+        else disp_u2<R, MA + 1>(ma, mb, a, mat, cm, cv, base, G);
+    }
+}
+
+// layers: the same 2x2 family on every group bit in `mask`, straight-line code
+template <int R, int M = 0>
+__device__ __forceinline__ void layer_rxc(float2 (&a)[1 << R], const float2 *k0, uint32_t mask) {
+    if constexpr (M < R) {
+        if ((mask >> M) & 1) op_rxc<R, M>(a, k0 + M);
+        layer_rxc<R, M + 1>(a, k0, mask);
+    }
+}
+template <int R, int M = 0>
+__device__ __forceinline__ void layer_u1r(float2 (&a)[1 << R], const float2 *k0, uint32_t mask) {
+    if constexpr (M < R) {
+        if ((mask >> M) & 1) op_u1r<R, M>(a, k0 + 2 * M);
+        layer_u1r<R, M + 1>(a, k0, mask);
+    }
+}
+template <int R, int M = 0>
+__device__ __forceinline__ void layer_u1(float2 (&a)[1 << R], const float2 *k0, uint32_t mask, const Grp<R> &G) {
+    if constexpr (M < R) {
+        if ((mask >> M) & 1) op_u1<R, M>(a, k0 + 4 * M, 0ull, 0ull, 0ull, G);
+        layer_u1<R, M + 1>(a, k0, mask, G);
+    }
+}
+template <int R, int M = 0>
+__device__ __forceinline__ void layer_h(float2 (&a)[1 << R], uint32_t mask) {
+    if constexpr (M < R) {
+        if ((mask >> M) & 1) op_h<R, M>(a);
+        layer_h<R, M + 1>(a, mask);
+    }
+}
+// QFT stages from the highest group bit down (the gate stream's order)
+template <int R, int M = R - 1>
+__device__ __forceinline__ void layer_qft(float2 (&a)[1 << R], const float2 *k0, uint32_t mask, uint64_t ppack,
+                                          uint64_t gbase, const float2 *roots) {
+    if constexpr (M >= 0) {
+        if ((mask >> M) & 1) {
+            const int p = (int)((ppack >> (6 * M)) & 63);
+            const float2 w = twiddle(gbase & ((1ull << p) - 1), p, roots);
+            op_qft<R, M>(a, k0 + M * (1 << R), w);
+        }
+        layer_qft<R, M - 1>(a, k0, mask, ppack, gbase, roots);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// one sweep over the tile in shared memory
+// ---------------------------------------------------------------------------
+struct SweepCtx {
+    int T;
+    const int *contrib;      // smem: XOR offset of each tile-local bit (float2 units)
+    const int *hb;           // smem: global bit of tile-local bit L + k
+    int L;
+    float2 *buf;
+    const float2 *cs;
+    const float2 *roots;
+    const MicroOp *micro;    // smem
+    const DiagDesc *diags;   // smem
+    const int *tab_s;        // smem: per-sweep item-address tables (shared-memory offsets)
+    const uint64_t *tab_g;   // smem: per-sweep item-address tables (global index bits)
+    uint64_t tile_gbase;     // global index of tile-local 0 (within the state)
+};
+
+__device__ __forceinline__ uint64_t glob_contrib(const SweepCtx &c, int tb) {
+    return tb < c.L ? (1ull << tb) : (1ull << c.hb[tb - c.L]);
+}
+
+template <int R>
+__device__ __forceinline__ void sweep_load(const SweepCtx &c, bool vec, int saddr, const int (&gs)[R],
+                                           float2 (&a)[1 << R]) {
+    if (vec) {   // group bit 0 = tile-local bit 0: pairs are adjacent and 16-byte aligned
+#pragma unroll
+        for (int j = 0; j < (1 << R); j += 2) {
+            int o = saddr;
+#pragma unroll
+            for (int m = 1; m < R; ++m)
+                if ((j >> m) & 1) o ^= gs[m];
+            const float4 v = *reinterpret_cast<const float4 *>(c.buf + o);
+            a[j] = make_float2(v.x, v.y);
+            a[j + 1] = make_float2(v.z, v.w);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j) {
+            int o = saddr;
+#pragma unroll
+            for (int m = 0; m < R; ++m)
+                if ((j >> m) & 1) o ^= gs[m];
+            a[j] = c.buf[o];
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void sweep_store(const SweepCtx &c, bool vec, int saddr, const int (&gs)[R],
+                                            const float2 (&a)[1 << R]) {
+    if (vec) {
+#pragma unroll
+        for (int j = 0; j < (1 << R); j += 2) {
+            int o = saddr;
+#pragma unroll
+            for (int m = 1; m < R; ++m)
+                if ((j >> m) & 1) o ^= gs[m];
+            *reinterpret_cast<float4 *>(c.buf + o) = make_float4(a[j].x, a[j].y, a[j + 1].x, a[j + 1].y);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j) {
+            int o = saddr;
+#pragma unroll
+            for (int m = 0; m < R; ++m)
+                if ((j >> m) & 1) o ^= gs[m];
+            c.buf[o] = a[j];
+        }
+    }
+}
+
+template <int R, int NT>
+__device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int sidx) {
+    int gs[R];
+    Grp<R> G;
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+        gs[m] = c.contrib[S.gbit[m]];
+        G.gg[m] = glob_contrib(c, S.gbit[m]);
+    }
+    const int nb = c.T - R;
+    const int n_items = 1 << nb;
+    const bool vec = S.vec != 0;
+    const int *ts = c.tab_s + sidx * kItemTab;
+    const uint64_t *tg = c.tab_g + sidx * kItemTab;
+    for (int item = threadIdx.x; item < n_items; item += NT) {
+        const int i0 = item & 31, i1 = 32 + ((item >> 5) & 31), i2 = 64 + ((item >> 10) & 15);
+        const int saddr = ts[i0] ^ ts[i1] ^ ts[i2];
+        const uint64_t gbase = c.tile_gbase | tg[i0] | tg[i1] | tg[i2];
+        float2 a[1 << R];
+        sweep_load<R>(c, vec, saddr, gs, a);
+        for (int oi = S.op_begin; oi < S.op_end; ++oi) {
+            const MicroOp &op = c.micro[oi];
+            switch (op.kind) {
+                case MK_U1:
+                    disp_u1<R>(op.a, a, c.cs + op.cst, op.cmask, op.cval, gbase, G);
+                    break;
+                case MK_H:
+                    disp_h<R>(op.a, a);
+                    break;
+                case MK_RXC:
+                    disp_rxc<R>(op.a, a, c.cs + op.cst);
+                    break;
+                case MK_U1R:
+                    disp_u1r<R>(op.a, a, c.cs + op.cst);
+                    break;
+                case MK_U2:
+                    disp_u2<R>(op.a, op.b, a, c.cs + op.cst, op.cmask, op.cval, gbase, G);
+                    break;
+                case MK_QFT: {
+                    const uint64_t Mk = (op.p > op.lo) ? (((1ull << op.p) - 1) & ~((1ull << op.lo) - 1)) : 0ull;
+                    const float2 w = twiddle(gbase & Mk, op.p, c.roots);
+                    disp_qft<R>(op.a, a, c.cs + op.cst, w);
+                    break;
+                }
+                case MK_LAYER: {
+                    const float2 *k0 = c.cs + op.cst;
+                    const uint32_t mask = (uint32_t)op.b;
+                    switch (op.a) {
+                        case MK_RXC: layer_rxc<R>(a, k0, mask); break;
+                        case MK_U1R: layer_u1r<R>(a, k0, mask); break;
+                        case MK_U1: layer_u1<R>(a, k0, mask, G); break;
+                        default: layer_h<R>(a, mask); break;
+                    }
+                    break;
+                }
+                case MK_QFTL:
+                    layer_qft<R>(a, c.cs + op.cst, (uint32_t)op.b, op.cmask, gbase, c.roots);
+                    break;
+                case MK_DIAG: {
+                    const DiagDesc &d = c.diags[op.cst];
+                    const uint32_t dyn_s = (uint32_t)op.a, dyn_g = (uint32_t)op.b;
+                    float2 stat = d.pad0 ? make_float2(d.gph_re, d.gph_im) : make_float2(1.f, 0.f);
+                    stat = diag_part(d, gbase, c.cs, ~dyn_s, ~dyn_g, stat);
+                    if (dyn_g == 0 && __popc(dyn_s) <= 2 && dyn_s) {
+                        // fast path: the varying tables' indices are the item's base
+                        // index OR the group bits' contributions (disjoint bits)
+                        const int s0 = __ffs(dyn_s) - 1;
+                        const int s1 = (dyn_s & (dyn_s - 1)) ? __ffs(dyn_s & (dyn_s - 1)) - 1 : -1;
+                        const uint32_t m0 = (1u << d.slice_w[s0]) - 1;
+                        const int lo0 = d.slice_lo[s0];
+                        const float2 *t0 = c.cs + d.slice_off[s0];
+                        const uint32_t b0 = (uint32_t)(gbase >> lo0) & m0;
+                        uint32_t q0[R];
+#pragma unroll
+                        for (int m = 0; m < R; ++m) q0[m] = (uint32_t)(G.gg[m] >> lo0) & m0;
+                        if (s1 < 0) {
+#pragma unroll
+                            for (int j = 0; j < (1 << R); ++j) {
+                                uint32_t i0 = b0;
+#pragma unroll
+                                for (int m = 0; m < R; ++m)
+                                    if ((j >> m) & 1) i0 |= q0[m];
+                                a[j] = cmul(a[j], cmul(stat, t0[i0]));
+                            }
+                        } else {
+                            const uint32_t m1 = (1u << d.slice_w[s1]) - 1;
+                            const int lo1 = d.slice_lo[s1];
+                            const float2 *t1 = c.cs + d.slice_off[s1];
+                            const uint32_t b1 = (uint32_t)(gbase >> lo1) & m1;
+                            uint32_t q1[R];
+#pragma unroll
+                            for (int m = 0; m < R; ++m) q1[m] = (uint32_t)(G.gg[m] >> lo1) & m1;
+#pragma unroll
+                            for (int j = 0; j < (1 << R); ++j) {
+                                uint32_t i0 = b0, i1 = b1;
+#pragma unroll
+                                for (int m = 0; m < R; ++m)
+                                    if ((j >> m) & 1) {
+                                        i0 |= q0[m];
+                                        i1 |= q1[m];
+                                    }
+                                a[j] = cmul(a[j], cmul(stat, cmul(t0[i0], t1[i1])));
+                            }
+                        }
+                    } else if (dyn_s | dyn_g) {
+#pragma unroll
+                        for (int j = 0; j < (1 << R); ++j)
+                            a[j] = cmul(a[j], diag_part(d, G.gidx(gbase, j), c.cs, dyn_s, dyn_g, stat));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < (1 << R); ++j) a[j] = cmul(a[j], stat);
+                    }
+                    break;
+                }
+                default:
+                    break;
+            }
+        }
+        if (S.scale != 1.f) {
+#pragma unroll
+            for (int j = 0; j < (1 << R); ++j) a[j] = make_float2(a[j].x * S.scale, a[j].y * S.scale);
+        }
+        sweep_store<R>(c, vec, saddr, gs, a);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// dense-block sweeps: out = U X, X = the tile as a 32 x 2^(T-5) matrix (row =
+// the sweep's 5 group bits, column = its item bits), in place
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int dense_coloff(const int *ts, int m) {
+    return ts[m & 31] ^ ts[32 + ((m >> 5) & 31)] ^ ts[64 + ((m >> 10) & 15)];
+}
+// shared-memory offset of block row r: XOR of the group bits' offsets
+__device__ __forceinline__ int dense_rowoff(const int (&g)[5], int r) {
+    int o = 0;
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+        if ((r >> q) & 1) o ^= g[q];
+    return o;
+}
+
+// FP32 on the CUDA cores: a thread owns whole columns (32 amplitudes in
+// registers); rows of U are read as broadcasts from shared memory
+template <int NT>
+__device__ __forceinline__ void dense_fp32(const SweepCtx &c, const Sweep &S, int sidx) {
+    int g[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) g[q] = c.contrib[S.gbit[q]];
+    const int ncols = 1 << (c.T - 5);
+    const int *ts = c.tab_s + sidx * kItemTab;
+    const float4 *U = reinterpret_cast<const float4 *>(c.cs + S.dcst);
+    for (int m = threadIdx.x; m < ncols; m += NT) {
+        const int co = dense_coloff(ts, m);
+        float2 x[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) x[r] = c.buf[co ^ dense_rowoff(g, r)];
+#pragma unroll 1
+        for (int i = 0; i < 32; i += 4) {
+            float2 y[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) y[e] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float4 u = U[((i + e) * 32 + j) >> 1];
+                    y[e] = cmad(make_float2(u.x, u.y), x[j], y[e]);
+                    y[e] = cmad(make_float2(u.z, u.w), x[j + 1], y[e]);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) c.buf[co ^ dense_rowoff(g, i + e)] = y[e];
+        }
+    }
+}
+
+// x rounded to TF32 (10 explicit mantissa bits, ties away from zero) with
+// integer operations; x - hi is then exact in FP32
+__device__ __forceinline__ uint32_t tf32_hi(float x) { return (__float_as_uint(x) + 0x1000u) & 0xffffe000u; }
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// (re, im) -> packed BF16 pair, re in the low half
+__device__ __forceinline__ uint32_t pack_bf16(float2 v) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(v.y), "f"(v.x));
+    return r;
+}
+
+// Tensor cores, as the real GEMM Y^T = X^T B with X^T the columns x 64 matrix
+// of (re, im) parts and B the 64 x 64 real form of U^T.  A warp takes 16 * MT
+// columns (MT m16 tiles) and all 64 outputs (8 n8 tiles).  Operand order
+// within a TF32 k-step s (block rows 4s..4s+3): k = 0-3 real parts, 4-7
+// imaginary parts, so that one 8-byte load gives a lane both halves of an
+// amplitude; n = 2 * output row + (re, im), so that the accumulator pair of a
+// lane is one output amplitude.  Split precision: X = X_hi + X_lo in TF32
+// (both rounded to nearest here), U = U_hi + U_lo (rounded on the host from
+// FP64); the product keeps U_hi X_hi + U_hi X_lo + U_lo X_hi.
+template <int MT, int NT>
+__device__ __forceinline__ void dense_tf32x3(const SweepCtx &c, const Sweep &S, int sidx) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = lane & 3, gq = lane >> 2;
+    const bool lane_im = (gq & 1) != 0;   // this lane's B column is an imaginary part
+    const int rlo = ((q & 1) ? c.contrib[S.gbit[0]] : 0) ^ ((q & 2) ? c.contrib[S.gbit[1]] : 0);
+    const int g2 = c.contrib[S.gbit[2]], g3 = c.contrib[S.gbit[3]], g4 = c.contrib[S.gbit[4]];
+    int rhi[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) rhi[s] = ((s & 1) ? g2 : 0) ^ ((s & 2) ? g3 : 0) ^ ((s & 4) ? g4 : 0);
+    // U[4t + lane/8][4s + q] as (hi, lo) at pair (4t + lane/8) * 32 + 4 (s ^ f) + q,
+    // f = bit 0 of the row
+    const float4 *Ut = reinterpret_cast<const float4 *>(c.cs + S.dcst);
+    const int ub = (lane >> 3) * 32 + q, uf = (lane >> 3) & 1;
+    const int ncols = 1 << (c.T - 5);
+    const int *ts = c.tab_s + sidx * kItemTab;
+    for (int mb = warp * 16 * MT; mb < ncols; mb += (NT / 32) * 16 * MT) {
+        int co[MT][2];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            co[mt][0] = dense_coloff(ts, mb + 16 * mt + gq) ^ rlo;
+            co[mt][1] = dense_coloff(ts, mb + 16 * mt + gq + 8) ^ rlo;
+        }
+        // U_hi X_hi and the two small cross terms accumulate apart: the tensor
+        // core's FP32 accumulation truncates, and chaining the cross terms
+        // onto the large sum would truncate at full magnitude 3x as often
+        // (a norm shrink that compounds over many blocks)
+        float acc[MT][8][4], acs[MT][8][4];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[mt][t][e] = acs[mt][t][e] = 0.f;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            uint32_t ah[MT][4], al[MT][4];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                const float2 x0 = c.buf[rhi[s] ^ co[mt][0]], x1 = c.buf[rhi[s] ^ co[mt][1]];
+                const float v[4] = {x0.x, x1.x, x0.y, x1.y};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    ah[mt][e] = tf32_hi(v[e]);
+                    // rounded too: the tensor core would truncate (a bias toward
+                    // zero that compounds over many blocks)
+                    al[mt][e] = tf32_hi(v[e] - __uint_as_float(ah[mt][e]));
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const float4 u = Ut[ub + 128 * t + 4 * (s ^ uf)];   // (hi.re, hi.im, lo.re, lo.im)
+                const uint32_t bh0 = __float_as_uint(lane_im ? u.y : u.x);
+                const uint32_t bh1 = __float_as_uint(lane_im ? u.x : -u.y);
+                const uint32_t bl0 = __float_as_uint(lane_im ? u.w : u.z);
+                const uint32_t bl1 = __float_as_uint(lane_im ? u.z : -u.w);
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    mma_tf32(acs[mt][t], al[mt], bh0, bh1);
+                    mma_tf32(acs[mt][t], ah[mt], bl0, bl1);
+                    mma_tf32(acc[mt][t], ah[mt], bh0, bh1);
+                }
+            }
+        }
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[mt][t][e] += acs[mt][t][e];
+        // every load of these columns precedes the stores (in place); tiles of
+        // fewer than 16 columns (T < 9) alias columns >= ncols onto real ones,
+        // which only the lanes of real columns store
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                if (mb + 16 * mt + gq < ncols) c.buf[rhi[t] ^ co[mt][0]] = make_float2(acc[mt][t][0], acc[mt][t][1]);
+                if (mb + 16 * mt + gq + 8 < ncols) c.buf[rhi[t] ^ co[mt][1]] = make_float2(acc[mt][t][2], acc[mt][t][3]);
+            }
+    }
+}
+
+// Tensor cores in BF16 (m16n8k16): k = 2 * block row + (re, im) over rows
+// 8s..8s+7; U's operand registers come pre-packed from the host.
+template <int MT, int NT>
+__device__ __forceinline__ void dense_bf16(const SweepCtx &c, const Sweep &S, int sidx) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int q = lane & 3, gq = lane >> 2;
+    const int rlo = ((q & 1) ? c.contrib[S.gbit[0]] : 0) ^ ((q & 2) ? c.contrib[S.gbit[1]] : 0);
+    const int g2 = c.contrib[S.gbit[2]], g3 = c.contrib[S.gbit[3]], g4 = c.contrib[S.gbit[4]];
+    int rhi[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) rhi[s] = ((s & 1) ? g2 : 0) ^ ((s & 2) ? g3 : 0) ^ ((s & 4) ? g4 : 0);
+    const uint2 *B = reinterpret_cast<const uint2 *>(c.cs + S.dcst) + lane;
+    const int ncols = 1 << (c.T - 5);
+    const int *ts = c.tab_s + sidx * kItemTab;
+    for (int mb = warp * 16 * MT; mb < ncols; mb += (NT / 32) * 16 * MT) {
+        int co[MT][2];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            co[mt][0] = dense_coloff(ts, mb + 16 * mt + gq) ^ rlo;
+            co[mt][1] = dense_coloff(ts, mb + 16 * mt + gq + 8) ^ rlo;
+        }
+        float acc[MT][8][4];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[mt][t][e] = 0.f;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            uint32_t a[MT][4];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                // rows 8s + q (block-row bit 2 clear) and 8s + 4 + q (set)
+                a[mt][0] = pack_bf16(c.buf[rhi[2 * s] ^ co[mt][0]]);
+                a[mt][1] = pack_bf16(c.buf[rhi[2 * s] ^ co[mt][1]]);
+                a[mt][2] = pack_bf16(c.buf[rhi[2 * s + 1] ^ co[mt][0]]);
+                a[mt][3] = pack_bf16(c.buf[rhi[2 * s + 1] ^ co[mt][1]]);
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const uint2 b = B[(s * 8 + t) * 32];
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) mma_bf16(acc[mt][t], a[mt], b.x, b.y);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                if (mb + 16 * mt + gq < ncols) c.buf[rhi[t] ^ co[mt][0]] = make_float2(acc[mt][t][0], acc[mt][t][1]);
+                if (mb + 16 * mt + gq + 8 < ncols) c.buf[rhi[t] ^ co[mt][1]] = make_float2(acc[mt][t][2], acc[mt][t][3]);
+            }
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void run_dense(const SweepCtx &c, const Sweep &S, int sidx) {
+    // two m16 tiles per warp when every warp still gets work
+    const bool two = (1 << (c.T - 5)) >= 32 * (NT / 32);
+    switch (S.dense) {
+        case DS_FP32: dense_fp32<NT>(c, S, sidx); break;
+        case DS_TF32X3:   // one m16 tile per warp: two accumulator sets fit in registers
+            dense_tf32x3<1, NT>(c, S, sidx);
+            break;
+        default:
+            if (two) dense_bf16<2, NT>(c, S, sidx);
+            else dense_bf16<1, NT>(c, S, sidx);
+            break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the persistent tile kernel
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t row_offset(int r, int H, const int *hb) {
+    uint64_t o = 0;
+    for (int k = 0; k < H; ++k)
+        if ((r >> k) & 1) o |= 1ull << hb[k];
+    return o;
+}
+
+__device__ __forceinline__ uint64_t tile_base(const TileArgs &A, long long ti) {
+    uint64_t g = 0;
+    for (int i = 0; i < A.n_outer; ++i)
+        if ((ti >> i) & 1) g |= 1ull << A.outer_pos[i];
+    return g;
+}
+
+// 16-byte chunk q of a tile (tile-local index 2q, 2q+1): its shared-memory
+// float2 offset (XOR-linear layout) and its global offset within the state
+__device__ __forceinline__ int chunk_smem(int q, int T, const int *contrib) {
+    int o = 0;
+    for (int tb = 1; tb < T; ++tb)
+        if ((q >> (tb - 1)) & 1) o ^= contrib[tb];
+    return o;
+}
+__device__ __forceinline__ uint64_t chunk_glob(int q, int L, int H, const int *hb) {
+    const int t = q << 1;
+    uint64_t g = (uint64_t)(t & ((1 << L) - 1));
+    const int r = t >> L;
+    for (int k = 0; k < H; ++k)
+        if ((r >> k) & 1) g |= 1ull << hb[k];
+    return g;
+}
+
+__device__ __forceinline__ void tile_coords(const TmaGeom &g, long long ti, long long bi, int c[5]) {
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+        long long v = 0;
+        if (d < g.ndims) {
+            if (g.kind[d] == 1) v = (ti >> g.off[d]) & ((1ll << g.w[d]) - 1);
+            if (d == g.batch_dim) v += bi << g.w[d];
+        }
+        c[d] = (int)v;
+    }
+}
+
+// DENSE: the pass has dense-block sweeps (a separate instantiation, so that
+// the register budget of the other passes does not grow with the dense code)
+template <int R, int NT, int MINB = 1, bool DENSE = false>
+__global__ void __launch_bounds__(NT, MINB)
+    tile_pass_kernel(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst,
+                     const TileArgs A) {
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    // the 128-byte swizzle needs 1024-byte aligned tile buffers: align the base
+    unsigned char *sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm);          // [kMaxTileBuffers]
+    int *s_hb = reinterpret_cast<int *>(sm + 64);
+    int *s_contrib = s_hb + kMaxTileBits;
+    Sweep *s_sweeps = reinterpret_cast<Sweep *>(sm + A.off_desc);
+    const TilePass &P = *A.pass;
+    const int n_sweeps = P.n_sweeps, n_micro = P.n_micro;
+    MicroOp *s_micro = reinterpret_cast<MicroOp *>(s_sweeps + n_sweeps);
+    DiagDesc *s_diags = reinterpret_cast<DiagDesc *>(s_micro + n_micro);
+    uint64_t *s_tab_g = reinterpret_cast<uint64_t *>(s_diags + kMaxDiag);
+    int *s_tab_s = reinterpret_cast<int *>(s_tab_g + n_sweeps * kItemTab);
+    float2 *cs = reinterpret_cast<float2 *>(sm + A.off_consts);
+    float2 *roots = reinterpret_cast<float2 *>(sm + A.off_roots);
+    float2 *buf0 = reinterpret_cast<float2 *>(sm + A.off_buf0);
+    const int NB = A.n_buf;
+    const int tid = threadIdx.x;
+    const int L = P.L, H = P.H, T = P.T;
+    const int tile_elems = 1 << T;
+    const uint32_t tile_bytes = 8u << T;
+    const long long total = A.n_tiles * (long long)A.batch;
+
+    // stage the pass descriptor and constants in shared memory
+    {
+        const int *src = reinterpret_cast<const int *>(P.sweeps);
+        int *dst = reinterpret_cast<int *>(s_sweeps);
+        const int nw_s = n_sweeps * (int)(sizeof(Sweep) / 4);
+        for (int i = tid; i < nw_s; i += NT) dst[i] = src[i];
+        src = reinterpret_cast<const int *>(P.micro);
+        dst = reinterpret_cast<int *>(s_micro);
+        const int nw_m = n_micro * (int)(sizeof(MicroOp) / 4);
+        for (int i = tid; i < nw_m; i += NT) dst[i] = src[i];
+        src = reinterpret_cast<const int *>(P.diags);
+        dst = reinterpret_cast<int *>(s_diags);
+        const int nw_d = kMaxDiag * (int)(sizeof(DiagDesc) / 4);
+        for (int i = tid; i < nw_d; i += NT) dst[i] = src[i];
+    }
+    for (int i = tid; i < P.n_const; i += NT) cs[i] = A.consts[i];
+    if (A.off_roots)
+        for (int i = tid; i < kRootsEntries; i += NT) roots[i] = A.roots[i];
+    if (tid < kMaxTileBits) {
+        s_hb[tid] = P.hb[tid];
+        s_contrib[tid] = P.smem_contrib[tid];
+    }
+    if (tid == 0) {
+        for (int b = 0; b < kMaxTileBuffers; ++b) mbar_init(&full[b], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // item-address tables: item bits 0-4, 5-9, 10-13 of each sweep -> XOR of the
+    // shared-memory offsets and OR of the global index bits of those tile bits
+    for (int e = tid; e < n_sweeps * kItemTab; e += NT) {
+        const int sw = e / kItemTab, idx = e - sw * kItemTab;
+        const int part = idx < 32 ? 0 : (idx < 64 ? 1 : 2);
+        const int v = idx - 32 * part;
+        const int nb = T - s_sweeps[sw].r;
+        int so = 0;
+        uint64_t go = 0;
+        for (int b = 0; b < 5; ++b) {
+            const int i = 5 * part + b;
+            if (((v >> b) & 1) && i < nb) {
+                const int tb = s_sweeps[sw].tbit[i];
+                so ^= s_contrib[tb];
+                go |= tb < L ? (1ull << tb) : (1ull << s_hb[tb - L]);
+            }
+        }
+        s_tab_s[e] = so;
+        s_tab_g[e] = go;
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if ((long long)blockIdx.x >= total) return;
+    const long long stride = gridDim.x;
+    const int n_mine = (int)((total - 1 - blockIdx.x) / stride + 1);   // tiles of this CTA
+    const int rows = 1 << H;
+    const uint32_t row_bytes = 8u << L;
+
+    // thread 0 issues every copy (TMA path: one instruction per tile)
+    const int io = A.io_mode;
+    const int n_chunks = tile_elems >> 1;
+    // 16-byte chunk q = tid + i * NT of a tile: offsets are XOR/OR-linear in the
+    // bits of q, so split them into a per-thread part (computed once) and the
+    // parts of the (at most 4) loop bits
+    int c_smem = 0;
+    uint64_t c_glob = 0;
+    int i_smem[4] = {0, 0, 0, 0};
+    uint64_t i_glob[4] = {0, 0, 0, 0};
+    int n_ib = 0;
+    if (io != 0) {
+        if (tid < n_chunks) {
+            c_smem = chunk_smem(tid, T, s_contrib);
+            c_glob = chunk_glob(tid, L, H, s_hb);
+        }
+        for (int m = 0; (NT << m) < n_chunks && m < 4; ++m) {
+            i_smem[m] = chunk_smem(NT << m, T, s_contrib);
+            i_glob[m] = chunk_glob(NT << m, L, H, s_hb);
+            n_ib = m + 1;
+        }
+    }
+    const int per_thread = n_chunks > NT ? n_chunks / NT : 1;
+    // cp.async path: every thread copies its 16-byte chunks (coalesced rows)
+    auto load_threads = [&](int k) {
+        float2 *dstbuf = buf0 + (size_t)(k % NB) * tile_elems;
+        const long long t = blockIdx.x + (long long)k * stride;
+        const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
+        const float2 *src = A.src + bi * A.state_elems + tile_base(A, ti);
+        if (tid < n_chunks) {
+#pragma unroll 4
+            for (int i = 0; i < per_thread; ++i) {
+                int so = c_smem;
+                uint64_t go = c_glob;
+                for (int m = 0; m < n_ib; ++m)
+                    if ((i >> m) & 1) {
+                        so ^= i_smem[m];
+                        go |= i_glob[m];
+                    }
+                cp_async16(dstbuf + so, src + go);
+            }
+        }
+        cp_async_commit();
+    };
+    // thread stores: 16-byte chunks straight from shared memory to HBM
+    auto store_threads = [&](int k) {
+        const float2 *srcbuf = buf0 + (size_t)(k % NB) * tile_elems;
+        const long long t = blockIdx.x + (long long)k * stride;
+        const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
+        float2 *dst = A.dst + bi * A.state_elems + tile_base(A, ti);
+        if (tid < n_chunks) {
+#pragma unroll 4
+            for (int i = 0; i < per_thread; ++i) {
+                int so = c_smem;
+                uint64_t go = c_glob;
+                for (int m = 0; m < n_ib; ++m)
+                    if ((i >> m) & 1) {
+                        so ^= i_smem[m];
+                        go |= i_glob[m];
+                    }
+                const float4 v = *reinterpret_cast<const float4 *>(srcbuf + so);
+                *reinterpret_cast<float4 *>(dst + go) = v;
+            }
+        }
+    };
+    auto load = [&](int k) {
+        const int b = k % NB;
+        float2 *dstbuf = buf0 + (size_t)b * tile_elems;
+        const long long t = blockIdx.x + (long long)k * stride;
+        const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
+        mbar_arrive_expect_tx(&full[b], tile_bytes);
+        if (A.use_tma) {
+            int c[5];
+            tile_coords(A.geo, ti, bi, c);
+            tma_load_5d(dstbuf, &tm_src, c, &full[b]);
+        } else {
+            const float2 *src = A.src + bi * A.state_elems + tile_base(A, ti);
+            for (int r = 0; r < rows; ++r)
+                bulk_g2s(dstbuf + ((size_t)r << L), src + row_offset(r, H, s_hb), row_bytes, &full[b]);
+        }
+    };
+    auto store = [&](int k) {
+        const float2 *srcbuf = buf0 + (size_t)(k % NB) * tile_elems;
+        const long long t = blockIdx.x + (long long)k * stride;
+        const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
+        if (A.use_tma) {
+            int c[5];
+            tile_coords(A.geo, ti, bi, c);
+            tma_store_5d(&tm_dst, c, srcbuf);
+        } else {
+            float2 *dst = A.dst + bi * A.state_elems + tile_base(A, ti);
+            for (int r = 0; r < rows; ++r)
+                bulk_s2g(dst + row_offset(r, H, s_hb), srcbuf + ((size_t)r << L), row_bytes);
+        }
+        bulk_commit();
+    };
+
+    const int D = A.prefetch;
+    const int PF = A.l2_prefetch;   // tiles beyond the smem prefetch warmed in L2
+    auto l2pf = [&](int k) {
+        const long long t = blockIdx.x + (long long)k * stride;
+        const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
+        int c[5];
+        tile_coords(A.geo, ti, bi, c);
+        tma_prefetch_l2_5d(&tm_src, c);
+    };
+    if (tid == 0 && io != 2 && A.use_tma)
+        for (int k = D; k < D + PF && k < n_mine; ++k) l2pf(k);
+    if (io == 2) {
+        for (int k = 0; k < D; ++k) {
+            if (k < n_mine) load_threads(k);
+            else cp_async_commit();   // keep one group per tile slot
+        }
+    } else if (tid == 0) {
+        for (int k = 0; k < D && k < n_mine; ++k) load(k);
+    }
+
+    SweepCtx c;
+    c.T = T;
+    c.L = L;
+    c.contrib = s_contrib;
+    c.hb = s_hb;
+    c.cs = cs;
+    c.roots = roots;
+    c.micro = s_micro;
+    c.diags = s_diags;
+    c.tab_s = s_tab_s;
+    c.tab_g = s_tab_g;
+    for (int k = 0; k < n_mine; ++k) {
+        bool ok = true;
+        if (io == 2) {
+            // buffer (k+D) % NB held tile k+D-NB <= k-1, already stored by the threads
+            if (k + D < n_mine) load_threads(k + D);
+            else cp_async_commit();
+            // groups are committed per tile in order: tile k is done when at most D remain
+            switch (D) {
+                case 1: cp_async_wait<1>(); break;
+                case 2: cp_async_wait<2>(); break;
+                case 3: cp_async_wait<3>(); break;
+                default: cp_async_wait<4>(); break;
+            }
+        } else {
+            if (tid == 0 && k + D < n_mine) {
+                // buffer (k+D) % NB last held tile k+D-NB, stored at the end of
+                // iteration k+D-NB: allow the NB-D-1 newer stores to stay in flight
+                if (io == 0) {
+                    switch (NB - D - 1) {
+                        case 0: asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); break;
+                        case 1: asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); break;
+                        case 2: asm volatile("cp.async.bulk.wait_group.read 2;" ::: "memory"); break;
+                        default: asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory"); break;
+                    }
+                }
+                load(k + D);
+            }
+            if (tid == 0 && A.use_tma && k + D + PF < n_mine) l2pf(k + D + PF);
+            ok = mbar_wait_bounded(&full[k % NB], (uint32_t)((k / NB) & 1));
+        }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicCAS(A.err, 0, (int)QS_ERR_TIMEOUT);
+                for (int kk = k + 1; kk < k + D && kk < n_mine; ++kk)
+                    mbar_wait_bounded(&full[kk % NB], (uint32_t)((kk / NB) & 1));
+                bulk_wait_all0();
+            }
+            return;
+        }
+        const long long t = blockIdx.x + (long long)k * stride;
+        const long long ti = t % A.n_tiles;
+        c.buf = buf0 + (size_t)(k % NB) * tile_elems;
+        c.tile_gbase = tile_base(A, ti);
+        for (int s = 0; s < n_sweeps; ++s) {
+            if (DENSE && s_sweeps[s].dense) run_dense<NT>(c, s_sweeps[s], s);
+            else run_sweep<R, NT>(c, s_sweeps[s], s);
+            __syncthreads();
+        }
+        if (io == 0) {
+            fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) store(k);
+        } else {
+            store_threads(k);
+            // the buffer is reloaded D iterations later, after this barrier
+            if (io == 2) __syncthreads();
+            else {
+                fence_proxy_async();   // generic reads before the async-proxy refill
+                __syncthreads();
+            }
+        }
+    }
+    if (io == 2) cp_async_wait<0>();
+    if (tid == 0) bulk_wait_all0();
+}
+
+}  // namespace qs

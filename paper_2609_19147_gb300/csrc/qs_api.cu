@@ -340,7 +340,7 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     A.off_buf0 = off;
     // two co-resident CTAs per SM for 12-bit tiles with 4-bit groups: one
     // computes while the other waits on its copies
-    A.ctas_per_sm = (tp.T == 12 && tp.sweeps[0].r == 4) ? 2 : 1;
+    A.ctas_per_sm = (tp.T == 12 && tp.R == 4) ? 2 : 1;
     const int limit = (A.ctas_per_sm == 2 ? 113 * 1024 : 227 * 1024) - 1024;   // 1 KB for the base alignment
     // as many tile buffers as fit (<= 6)
     A.n_buf = std::min(A.ctas_per_sm == 2 ? 3 : 6, (limit - off) / buf_bytes);
@@ -372,7 +372,11 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
         s = encode_map(hp.tma, dst, tp.swizzle != 0, &tmd);
         if (s != QS_OK) return s;
     }
-    A.threads = (tp.sweeps[0].r == 4 && tp.T >= 13) ? 512 : 256;
+    A.threads = (tp.R == 4 && tp.T >= 13) ? 512 : 256;
+    for (int k = 0; k < tp.n_sweeps; ++k)
+        if (tp.sweeps[k].dense) A.dense = 1;
+    if (A.dense && (tp.R != 5 || A.ctas_per_sm != 1)) return fail(QS_ERR_INTERNAL, "dense pass without 5-bit groups");
+    if (A.dense) A.threads = 256;
     {
         static int io_env = -2;
         if (io_env == -2) {
@@ -402,10 +406,10 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     cudaEvent_t ev;
     prof_begin(st, &ev);
     {
-        cudaError_t e = launch_tile_pass(tp.sweeps[0].r, A, &tms, &tmd, grid, off, st->stream);
+        cudaError_t e = launch_tile_pass(tp.R, A, &tms, &tmd, grid, off, st->stream);
         if (e != cudaSuccess)
             return fail(QS_ERR_CUDA, std::string("tile pass launch: ") + cudaGetErrorString(e) + " (smem=" +
-                                         std::to_string(off) + " " + tile_kernel_attrs(tp.sweeps[0].r) + ")");
+                                         std::to_string(off) + " " + tile_kernel_attrs(tp.R, A) + ")");
     }
     prof_end(st, ev, "tile_pass", 16.0 * (double)st->elems * batch);
     return QS_OK;

@@ -38,6 +38,7 @@ constexpr int kMaxGroup = 5;         // r: amplitudes per thread = 2^r
 constexpr int kMaxSweeps = 40;
 constexpr int kMaxMicro = 320;
 constexpr int kMaxConst = 5120;      // complex64 constants per pass (40 KB)
+constexpr int kMaxConstDense = 10240; // ... in plans with dense blocks (80 KB: 13-bit tiles, 2 buffers)
 constexpr int kMaxDiag = 4;
 constexpr int kTileThreads = 256;     // threads per tile CTA
 constexpr int kMaxTileBuffers = 8;
@@ -92,11 +93,24 @@ struct MicroOp {
     uint64_t cmask, cval;  // control condition on the global index
 };
 
+// Dense-block sweeps (qs_dense_prec): out = U X on the 5 group bits, where X
+// is the tile viewed as a 32 x 2^(T-5) matrix (row = the group bits, column =
+// the item bits).  Constants at dcst:
+//   DS_FP32    U as 32 x 32 complex64, row-major (row = output index);
+//   DS_TF32X3  32 x 32 pairs (U_hi, U_lo) of complex64, TF32-rounded on the
+//              host from FP64: entry (i, j) at pair i * 32 + (j ^ 4 (i & 1)) (the
+//              XOR makes the tensor-core operand loads conflict-free);
+//   DS_BF16    U in the m16n8k16 B-operand register order: for k-step s < 4,
+//              n-tile t < 8 and lane l, one float2 holding 4 packed BF16.
+enum DenseKind : int32_t { DS_NONE = 0, DS_FP32 = 1, DS_TF32X3 = 2, DS_BF16 = 3 };
+
 struct Sweep {
     int32_t r;                   // group size (1..kMaxGroup)
     int32_t op_begin, op_end;    // micro-op range [begin, end)
     int32_t vec;                 // group bit 0 is tile-local bit 0: 16-byte pair accesses
     float scale;                 // folded butterfly normalisation, applied once at the end
+    int32_t dense;               // DenseKind: a dense-block sweep (r = 5, no micro-ops)
+    int32_t dcst;                // dense sweep: constant offset of the block's tables
     int32_t gbit[kMaxGroup];     // tile-local bit of group bit j
     int32_t tbit[kMaxTileBits];  // tile-local bit of item bit i (i < T - r)
 };
@@ -108,6 +122,7 @@ struct Sweep {
 // tile-local bits.  Tiles are indexed by the remaining n-T bits (ascending).
 struct TilePass {
     int32_t n, L, H, T;
+    int32_t R;                           // register group size of the micro-op sweeps
     int32_t swizzle;                     // 1: 128-byte swizzle (TMA tensor path)
     int32_t n_sweeps, n_micro, n_const;
     int32_t hb[kMaxTileBits];

@@ -39,6 +39,7 @@ struct TileArgs {
     int io_mode;               // 0: TMA load + TMA store; 1: TMA load + thread stores;
                                // 2: cp.async loads + thread stores
     int use_tma;               // 1: one tensor copy per tile; 0: one bulk copy per row
+    int dense;                 // 1: the pass has dense-block sweeps (kernel with the dense paths)
     TmaGeom geo;
     int *err;                  // device status word
 };
@@ -46,7 +47,7 @@ struct TileArgs {
 cudaError_t launch_tile_pass(int R, const TileArgs &A, const void *tm_src, const void *tm_dst, int grid,
                              int smem_bytes, cudaStream_t st);
 void tile_kernel_smem_config(int bytes);
-std::string tile_kernel_attrs(int R);
+std::string tile_kernel_attrs(int R, const TileArgs &A);
 
 // per-gate kernels: op per state (op_stride = 1) or shared (op_stride = 0)
 struct PgArgs {

@@ -271,6 +271,11 @@ uint64_t FOp::N() const {
         case F_DIAG: return 0;
         case F_QFT: return 1ull << p;
         case F_GF2: return ~0ull;
+        case F_DENSE: {
+            uint64_t m = 0;
+            for (int b : dbits) m |= 1ull << b;
+            return m;
+        }
     }
     return ~0ull;
 }
@@ -280,6 +285,7 @@ uint64_t FOp::D() const {
         case F_DIAG: return diag.support();
         case F_QFT: return (p > lo) ? (((1ull << p) - 1) & ~((1ull << lo) - 1)) : 0;
         case F_GF2: return ~0ull;
+        case F_DENSE: return 0;
     }
     return ~0ull;
 }
@@ -558,6 +564,299 @@ void detect(int n, const std::vector<RGate> &gates, std::vector<FOp> &ops) {
 }
 
 // ---------------------------------------------------------------------------
+// dense blocks: greedy, order-preserving regrouping of the detector's output
+// into blocks of at most k index bits (generic matrix fusion).
+//
+// The output is a sequence of items: blocks and ops passed through.  A block
+// is "open" while no later item touches its bits; an open block can therefore
+// move to the end of the sequence, so merging open blocks with each other and
+// with the next op is exact.  A 1q/2q op joins the open blocks on its bits
+// (and, while there is room, the most recent open block, which packs a layer
+// of 1q ops into blocks of k neighbouring bits).  A diagonal splits: terms
+// whose bits lie in one open block fold into it, the rest (global phase,
+// bonds across blocks) passes through and closes the blocks it touches.
+// Everything else passes through and closes the blocks on its bits.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct DBlock {
+    std::vector<int> bits;   // local bit j <-> index bit bits[j]
+    std::vector<cd> m;       // 2^k x 2^k row-major
+    int slot = -1;           // position in the item sequence
+    bool open = true;
+    int n_gates = 0;
+};
+
+uint64_t dblock_glob(const std::vector<int> &bits, int i) {
+    uint64_t g = 0;
+    for (size_t j = 0; j < bits.size(); ++j)
+        if ((i >> j) & 1) g |= 1ull << bits[j];
+    return g;
+}
+
+int dblock_local(const std::vector<int> &bits, int b) {
+    for (size_t j = 0; j < bits.size(); ++j)
+        if (bits[j] == b) return (int)j;
+    return -1;
+}
+
+// M <- I (x) M : append index bits as the new most significant local bits
+void dblock_grow(DBlock &b, const std::vector<int> &extra) {
+    if (extra.empty()) return;
+    const int k0 = (int)b.bits.size(), d0 = 1 << k0;
+    const int k1 = k0 + (int)extra.size(), d1 = 1 << k1;
+    std::vector<cd> m(d1 * d1, cd(0, 0));
+    for (int i = 0; i < d1; ++i)
+        for (int j = 0; j < d1; ++j)
+            if ((i >> k0) == (j >> k0)) m[i * d1 + j] = b.m[(i & (d0 - 1)) * d0 + (j & (d0 - 1))];
+    b.m.swap(m);
+    b.bits.insert(b.bits.end(), extra.begin(), extra.end());
+}
+
+// M <- F M for a 1q / 2q op on bits inside the block
+void dblock_apply(DBlock &b, const FOp &f) {
+    const int k = (int)b.bits.size(), d = 1 << k;
+    if (f.kind == F_U1) {
+        const int ja = dblock_local(b.bits, f.t0);
+        for (int i = 0; i < d; ++i) {
+            if ((i >> ja) & 1) continue;
+            if ((dblock_glob(b.bits, i) & f.cmask) != f.cval) continue;
+            const int i1 = i | (1 << ja);
+            for (int col = 0; col < d; ++col) {
+                const cd v0 = b.m[i * d + col], v1 = b.m[i1 * d + col];
+                b.m[i * d + col] = f.m[0] * v0 + f.m[1] * v1;
+                b.m[i1 * d + col] = f.m[2] * v0 + f.m[3] * v1;
+            }
+        }
+    } else {   // F_U2: matrix index = x_t0 * 2 + x_t1
+        const int ja = dblock_local(b.bits, f.t0), jb = dblock_local(b.bits, f.t1);
+        for (int i = 0; i < d; ++i) {
+            if (((i >> ja) & 1) || ((i >> jb) & 1)) continue;
+            if ((dblock_glob(b.bits, i) & f.cmask) != f.cval) continue;
+            int idx[4];
+            for (int q = 0; q < 4; ++q) idx[q] = i | (((q >> 1) & 1) << ja) | ((q & 1) << jb);
+            for (int col = 0; col < d; ++col) {
+                cd v[4], w[4];
+                for (int q = 0; q < 4; ++q) v[q] = b.m[idx[q] * d + col];
+                for (int r = 0; r < 4; ++r) {
+                    w[r] = 0;
+                    for (int q = 0; q < 4; ++q) w[r] += f.m[r * 4 + q] * v[q];
+                }
+                for (int q = 0; q < 4; ++q) b.m[idx[q] * d + col] = w[q];
+            }
+        }
+    }
+}
+
+// M <- diag(e^{i phase}) M for a quadratic-form diagonal on the block's bits
+void dblock_diag(DBlock &b, const Diag &dg) {
+    const int k = (int)b.bits.size(), d = 1 << k;
+    for (int i = 0; i < d; ++i) {
+        const uint64_t x = dblock_glob(b.bits, i);
+        double ph = dg.g0;
+        for (auto &kv : dg.a)
+            if ((x >> kv.first) & 1) ph += kv.second;
+        for (auto &kv : dg.pairs)
+            if (((x >> kv.first.first) & 1) && ((x >> kv.first.second) & 1)) ph += kv.second;
+        const cd e = std::polar(1.0, ph);
+        for (int col = 0; col < d; ++col) b.m[i * d + col] *= e;
+    }
+}
+
+}  // namespace
+
+void dense_cells(int n, int T, int L, int k, int *cell_of) {
+    int id = 0;
+    const int W = T - L;
+    int top = n;
+    while (top > 0) {
+        // windows of T - L high bits from the top; the last one takes the low bits
+        int lo = top - W;
+        if (lo <= L) lo = 0;
+        const int sz = top - lo, nc = (sz + k - 1) / k;
+        int b = top;
+        for (int c = 0; c < nc; ++c) {   // near-equal cells, larger ones on top
+            const int w = sz / nc + (c < sz % nc ? 1 : 0);
+            for (int x = b - w; x < b; ++x) cell_of[x] = id;
+            b -= w;
+            id++;
+        }
+        top = lo;
+    }
+}
+
+void fuse_dense(int n, int k, const int *cell_of, const std::vector<FOp> &in, std::vector<FOp> &out) {
+    (void)n;
+    std::vector<DBlock> blocks;
+    struct Item {
+        int block = -1;   // block id, or -1: the op below
+        bool live = true;
+        FOp op;
+    };
+    std::vector<Item> items;
+    int last_touch[64], open_of[64];
+    for (int b = 0; b < 64; ++b) last_touch[b] = open_of[b] = -1;
+    auto close_block = [&](int id) {
+        DBlock &b = blocks[id];
+        if (!b.open) return;
+        b.open = false;
+        for (int x : b.bits) {
+            open_of[x] = -1;
+            last_touch[x] = std::max(last_touch[x], b.slot);
+        }
+    };
+    auto close_touching = [&](uint64_t S) {
+        for (int x = 0; x < 64; ++x)
+            if (((S >> x) & 1) && open_of[x] >= 0) close_block(open_of[x]);
+    };
+    auto emit = [&](const FOp &f, uint64_t S) {
+        close_touching(S);
+        Item it;
+        it.op = f;
+        items.push_back(it);
+        const int slot = (int)items.size() - 1;
+        for (int x = 0; x < 64; ++x)
+            if ((S >> x) & 1) last_touch[x] = slot;
+    };
+    // move open block `id` to the end of the sequence
+    auto to_end = [&](int id) {
+        DBlock &b = blocks[id];
+        if (b.slot >= 0) items[b.slot].live = false;
+        Item it;
+        it.block = id;
+        items.push_back(it);
+        b.slot = (int)items.size() - 1;
+    };
+    int recent = -1;   // most recently created or grown open block
+    for (const FOp &f : in) {
+        if (f.kind == F_U1 || f.kind == F_U2) {
+            uint64_t S = (1ull << f.t0) | f.cmask;
+            if (f.kind == F_U2) S |= 1ull << f.t1;
+            if (__builtin_popcountll(S) > k) {
+                emit(f, S);
+                continue;
+            }
+            std::vector<int> B;
+            uint64_t U = S;
+            for (int x = 0; x < 64; ++x)
+                if (((S >> x) & 1) && open_of[x] >= 0 &&
+                    std::find(B.begin(), B.end(), open_of[x]) == B.end()) {
+                    B.push_back(open_of[x]);
+                    for (int y : blocks[open_of[x]].bits) U |= 1ull << y;
+                }
+            if (__builtin_popcountll(U) > k) {
+                for (int id : B) close_block(id);
+                B.clear();
+                U = S;
+            }
+            // pack into the most recent open block while there is room in its cell
+            bool same_cell = recent >= 0 && blocks[recent].open;
+            if (same_cell) {
+                const int cc = cell_of[blocks[recent].bits[0]];
+                for (int x = 0; x < 64; ++x)
+                    if (((S >> x) & 1) && cell_of[x] != cc) same_cell = false;
+            }
+            if (B.empty() && same_cell && (int)blocks[recent].bits.size() + __builtin_popcountll(S) <= k) {
+                B.push_back(recent);
+                for (int y : blocks[recent].bits) U |= 1ull << y;
+            }
+            int id;
+            if (B.empty()) {
+                id = (int)blocks.size();
+                blocks.emplace_back();
+                blocks[id].m.assign(1, cd(1, 0));
+            } else {
+                id = B[0];
+                for (size_t i = 1; i < B.size(); ++i) {   // merge: M = M_i (x) M_id (disjoint bits)
+                    DBlock &a = blocks[id], &o = blocks[B[i]];
+                    const int ka = (int)a.bits.size(), da = 1 << ka, dob = 1 << o.bits.size(), dd = da * dob;
+                    std::vector<cd> m(dd * dd);
+                    for (int r = 0; r < dd; ++r)
+                        for (int c = 0; c < dd; ++c)
+                            m[r * dd + c] = a.m[(r & (da - 1)) * da + (c & (da - 1))] * o.m[(r >> ka) * dob + (c >> ka)];
+                    a.m.swap(m);
+                    a.bits.insert(a.bits.end(), o.bits.begin(), o.bits.end());
+                    a.n_gates += o.n_gates;
+                    o.open = false;
+                    if (o.slot >= 0) items[o.slot].live = false;
+                    for (int y : o.bits) open_of[y] = id;
+                }
+            }
+            to_end(id);
+            DBlock &b = blocks[id];
+            std::vector<int> extra;
+            for (int x = 0; x < 64; ++x)
+                if (((S >> x) & 1) && dblock_local(b.bits, x) < 0) extra.push_back(x);
+            dblock_grow(b, extra);
+            for (int x : b.bits) open_of[x] = id;
+            dblock_apply(b, f);
+            b.n_gates += f.n_gates;
+            recent = id;
+            continue;
+        }
+        if (f.kind == F_DIAG) {
+            std::map<int, Diag> part;
+            Diag rest;
+            rest.g0 = f.diag.g0;
+            for (auto &kv : f.diag.a) {
+                const int id = open_of[kv.first];
+                if (id >= 0) part[id].a[kv.first] += kv.second;
+                else rest.a[kv.first] += kv.second;
+            }
+            for (auto &kv : f.diag.pairs) {
+                const int i0 = open_of[kv.first.first], i1 = open_of[kv.first.second];
+                if (i0 >= 0 && i0 == i1) part[i0].pairs[kv.first] += kv.second;
+                else rest.pairs[kv.first] += kv.second;
+            }
+            for (auto &kv : part) dblock_diag(blocks[kv.first], kv.second);
+            if (rest.a.empty() && rest.pairs.empty() && !part.empty()) {
+                // only a global phase is left: it commutes with everything
+                DBlock &b0 = blocks[part.begin()->first];
+                if (rest.g0 != 0.0) {
+                    Diag g;
+                    g.g0 = rest.g0;
+                    dblock_diag(b0, g);
+                }
+                b0.n_gates += f.n_gates;
+                continue;
+            }
+            FOp r = f;
+            r.diag = rest;
+            emit(r, rest.support());
+            continue;
+        }
+        emit(f, f.kind == F_GF2 ? ~0ull : (f.N() | f.D()));
+    }
+    out.clear();
+    for (const Item &it : items) {
+        if (!it.live) continue;
+        if (it.block < 0) {
+            out.push_back(it.op);
+            continue;
+        }
+        const DBlock &b = blocks[it.block];
+        FOp f;
+        f.n_gates = b.n_gates;
+        const int kb = (int)b.bits.size();
+        if (kb == 1) {
+            f.kind = F_U1;
+            f.t0 = b.bits[0];
+            for (int e = 0; e < 4; ++e) f.m[e] = b.m[e];
+        } else if (kb == 2) {   // F_U2 index = x_t0 * 2 + x_t1: t0 is local bit 1
+            f.kind = F_U2;
+            f.t0 = b.bits[1];
+            f.t1 = b.bits[0];
+            for (int e = 0; e < 16; ++e) f.m[e] = b.m[e];
+        } else {
+            f.kind = F_DENSE;
+            f.dbits = b.bits;
+            f.dm = b.m;
+        }
+        out.push_back(f);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // diagonal -> device descriptors and tables
 // ---------------------------------------------------------------------------
 namespace {
@@ -680,9 +979,19 @@ struct OpCost {
     int n_diag = 0;
 };
 
-OpCost op_cost(int n, const FOp &f, int R, const DiagPlan *dp) {
+// constants (complex64 entries) of one dense block's tables (see DenseKind)
+int dense_const_size(int dprec) {
+    switch (dprec) {
+        case DS_FP32: return 32 * 32;
+        case DS_TF32X3: return 2 * 32 * 32;
+        default: return 4 * 8 * 32;   // DS_BF16
+    }
+}
+
+OpCost op_cost(int n, const FOp &f, int R, const DiagPlan *dp, int dprec) {
     OpCost c;
     switch (f.kind) {
+        case F_DENSE: c.n_const = dense_const_size(dprec) + 1; break;   // + alignment padding
         case F_U1: c.n_const = 4; break;
         case F_U2: c.n_const = 16; break;
         case F_QFT: c.n_const = 1 << R; break;
@@ -827,20 +1136,43 @@ TmaPlan tma_geometry(int n, int L, uint64_t S, int batch) {
     return g;
 }
 
+// FP64 -> TF32 (FP32 with 10 explicit mantissa bits), round to nearest even
+float tf32_round(double x) {
+    float f = (float)x;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) {
+        u += 0xfffu + ((u >> 13) & 1u);
+        u &= 0xffffe000u;
+    }
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// FP64 -> BF16 bits, round to nearest even (through FP32)
+uint16_t bf16_bits(double x) {
+    float f = (float)x;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
 struct PassBuilder {
-    int n, L, T, R;
+    int n, L, T, R, dprec;
     HostPass hp;
     TilePass &tp;
     std::vector<float2> &cst;
     uint64_t cur_group = 0;   // tile-local bits of the open sweep
     int open = -1;
-    PassBuilder(int n_, int L_, int T_, int R_, uint64_t S, int batch)
-        : n(n_), L(L_), T(T_), R(R_), tp(hp.tile), cst(hp.consts) {
+    PassBuilder(int n_, int L_, int T_, int R_, uint64_t S, int batch, int dprec_)
+        : n(n_), L(L_), T(T_), R(R_), dprec(dprec_), tp(hp.tile), cst(hp.consts) {
         std::memset(&tp, 0, sizeof(TilePass));
         hp.type = HostPass::TILE;
         tp.n = n;
         tp.L = L;
         tp.T = T;
+        tp.R = R;
         tp.H = T - L;
         int k = 0;
         for (int b = L; b < n; ++b)
@@ -899,8 +1231,154 @@ struct PassBuilder {
         open = -1;
         cur_group = 0;
     }
+    // A dense block gets a sweep of its own: 5 group bits (the block's tile
+    // bits, padded with the identity on the lowest free tile bits) and the
+    // block's tables in the layout its arithmetic reads (DenseKind).
+    void add_dense(const FOp &f) {
+        close_sweep();
+        const int si = tp.n_sweeps++;
+        Sweep &sw = tp.sweeps[si];
+        std::memset(&sw, 0, sizeof sw);
+        sw.dense = dprec;
+        sw.r = 5;
+        sw.scale = 1.f;
+        sw.op_begin = sw.op_end = tp.n_micro;
+        const int kb = (int)f.dbits.size();
+        int G[5];
+        uint64_t used = 0;
+        for (int j = 0; j < kb; ++j) {
+            G[j] = tile_local(tp, f.dbits[j]);
+            used |= 1ull << G[j];
+        }
+        int ng = kb;
+        for (int tb = 0; tb < T && ng < 5; ++tb)
+            if (!((used >> tb) & 1)) {
+                G[ng++] = tb;
+                used |= 1ull << tb;
+            }
+        std::vector<int> cols;
+        for (int tb = 0; tb < T; ++tb)
+            if (!((used >> tb) & 1)) cols.push_back(tb);
+        int order[5] = {0, 1, 2, 3, 4};   // group bit q is G[order[q]]
+        if (dprec == DS_FP32) {
+            for (int q = 0; q < 5; ++q) sw.gbit[q] = G[q];
+            sw.vec = 0;
+            choose_item_bits(tp, sw);
+        } else {
+            // tensor-core operand loads: lane bits 0-1 are group bits 0-1 (block
+            // rows), lane bits 2-4 are item bits 0-2 (columns); pick the five
+            // bits whose 8-byte accesses spread over the most banks
+            const int nc = (int)cols.size(), m = std::min(3, nc);
+            int best = 1 << 30, ba = 0, bb = 1;
+            uint32_t bmask = (1u << m) - 1;
+            // memoised on the bits' shared-memory offsets
+            static std::map<std::vector<int>, std::array<int, 3>> memo;
+            std::vector<int> key;
+            for (int e = 0; e < 5; ++e) key.push_back(tp.smem_contrib[G[e]]);
+            for (int i = 0; i < nc; ++i) key.push_back(tp.smem_contrib[cols[i]]);
+            auto hit = memo.find(key);
+            if (hit != memo.end()) {
+                best = 0;
+                ba = hit->second[0];
+                bb = hit->second[1];
+                bmask = (uint32_t)hit->second[2];
+            }
+            for (int a = 0; a < 5 && best > 0; ++a)
+                for (int b = a + 1; b < 5; ++b)
+                    for (uint32_t cm = 0; cm < (1u << nc); ++cm) {
+                        if (__builtin_popcount(cm) != m) continue;
+                        int v[5] = {tp.smem_contrib[G[a]], tp.smem_contrib[G[b]], 0, 0, 0}, e = 2;
+                        for (int i = 0; i < nc; ++i)
+                            if ((cm >> i) & 1) v[e++] = tp.smem_contrib[cols[i]];
+                        // distinct 8-byte words per bank pair (with fewer than 3
+                        // column bits, lanes alias onto the same words)
+                        const int nl = 1 << (2 + m);
+                        int cnt[16] = {0}, cost = 0;
+                        for (int lane = 0; lane < nl; ++lane) {
+                            int o = 0;
+                            for (int x = 0; x < 2 + m; ++x)
+                                if ((lane >> x) & 1) o ^= v[x];
+                            cost = std::max(cost, ++cnt[o & 15]);
+                        }
+                        if (cost < best) {
+                            best = cost;
+                            ba = a;
+                            bb = b;
+                            bmask = cm;
+                        }
+                    }
+            if (memo.size() < 4096) memo[key] = {ba, bb, (int)bmask};
+            order[0] = ba;
+            order[1] = bb;
+            int q = 2;
+            for (int e = 0; e < 5; ++e)
+                if (e != ba && e != bb) order[q++] = e;
+            for (int e = 0; e < 5; ++e) sw.gbit[e] = G[order[e]];
+            int t = 0;
+            for (int i = 0; i < nc; ++i)
+                if ((bmask >> i) & 1) sw.tbit[t++] = cols[i];
+            for (int i = 0; i < nc; ++i)
+                if (!((bmask >> i) & 1)) sw.tbit[t++] = cols[i];
+        }
+        // the 32 x 32 matrix in group-bit order (identity on the padding bits)
+        const int dim = 1 << kb;
+        std::vector<cd> U(32 * 32, cd(0, 0));
+        for (int i = 0; i < 32; ++i)
+            for (int j = 0; j < 32; ++j) {
+                int bi = 0, bj = 0, pi = 0, pj = 0;
+                for (int q = 0; q < 5; ++q) {
+                    const int e = order[q];
+                    if (e < kb) {
+                        bi |= ((i >> q) & 1) << e;
+                        bj |= ((j >> q) & 1) << e;
+                    } else {
+                        pi |= ((i >> q) & 1) << (e - kb);
+                        pj |= ((j >> q) & 1) << (e - kb);
+                    }
+                }
+                if (pi == pj) U[i * 32 + j] = f.dm[bi * dim + bj];
+            }
+        if (cst.size() & 1) cst.push_back(float2{0.f, 0.f});   // 16-byte aligned tables (float4 reads)
+        sw.dcst = (int)cst.size();
+        if (dprec == DS_FP32) {
+            for (int e = 0; e < 32 * 32; ++e) cst.push_back(float2{(float)U[e].real(), (float)U[e].imag()});
+        } else if (dprec == DS_TF32X3) {
+            std::vector<float2> t(2 * 32 * 32, float2{0.f, 0.f});
+            for (int i = 0; i < 32; ++i)
+                for (int j = 0; j < 32; ++j) {
+                    const cd u = U[i * 32 + j];
+                    const float hr = tf32_round(u.real()), hm = tf32_round(u.imag());
+                    const int e = 2 * (i * 32 + (j ^ ((i & 1) << 2)));
+                    t[e] = float2{hr, hm};
+                    t[e + 1] = float2{tf32_round(u.real() - (double)hr), tf32_round(u.imag() - (double)hm)};
+                }
+            cst.insert(cst.end(), t.begin(), t.end());
+        } else {
+            // m16n8k16 B operand: k = 2 * row + (0: re, 1: im) within a 16-wide
+            // k-step, n = 2 * out_row + (0: re, 1: im) within an 8-wide n-tile
+            for (int s = 0; s < 4; ++s)
+                for (int t = 0; t < 8; ++t)
+                    for (int lane = 0; lane < 32; ++lane) {
+                        const int g = lane >> 2, q = lane & 3, orow = 4 * t + (g >> 1);
+                        const bool im = (g & 1) != 0;
+                        uint32_t w[2];
+                        for (int h = 0; h < 2; ++h) {
+                            const cd u = U[orow * 32 + 8 * s + 4 * h + q];
+                            const double b0 = im ? u.imag() : u.real(), b1 = im ? u.real() : -u.imag();
+                            w[h] = (uint32_t)bf16_bits(b0) | ((uint32_t)bf16_bits(b1) << 16);
+                        }
+                        float2 v;
+                        std::memcpy(&v.x, &w[0], 4);
+                        std::memcpy(&v.y, &w[1], 4);
+                        cst.push_back(v);
+                    }
+        }
+    }
     void add(const FOp &f, const DiagPlan *dp) {
         switch (f.kind) {
+            case F_DENSE:
+                add_dense(f);
+                break;
             case F_U1: case F_U2: case F_QFT: {
                 uint64_t need = 0;
                 int ta = tile_local(tp, f.kind == F_QFT ? f.p : f.t0);
@@ -1183,10 +1661,37 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
 // 13-bit tiles with 5-bit groups.
 qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, const qs_opts &o, Plan &plan,
                            std::string &err) {
+    if (o.dense_prec < QS_DENSE_OFF || o.dense_prec > QS_DENSE_BF16) {
+        err = "dense_prec must be one of QS_DENSE_OFF / FP32 / TF32X3 / BF16";
+        return QS_ERR_INVALID_ARG;
+    }
+    if (o.block_qubits != 0 && (o.block_qubits < 3 || o.block_qubits > 5)) {
+        err = "block_qubits must be 0 (default 5) or in [3, 5]";
+        return QS_ERR_INVALID_ARG;
+    }
     std::vector<FOp> detected;
     detect(n, gates, detected);
+    if (o.dense_prec != QS_DENSE_OFF && n >= 5) {
+        // dense blocks: cells of <= k bits laid out so that the cells of one
+        // tile window (the low bits plus T - L high bits) share a pass
+        qs_opts c = o;
+        if (c.tile_qubits <= 0) c.tile_qubits = 13;
+        c.tile_qubits = std::max(5, std::min(c.tile_qubits, std::min(n, 13)));
+        if (c.low_qubits <= 0) c.low_qubits = 4;
+        c.low_qubits = std::min(c.low_qubits, c.tile_qubits);
+        c.group_qubits = 5;   // dense passes run in the 5-bit-group kernel
+        const int k = o.block_qubits > 0 ? o.block_qubits : 5;
+        int cell_of[64];
+        for (int b = 0; b < 64; ++b) cell_of[b] = 63;
+        dense_cells(n, c.tile_qubits, c.low_qubits, k, cell_of);
+        std::vector<FOp> blocks;
+        fuse_dense(n, k, cell_of, detected, blocks);
+        return build_fused_plan_cfg(n, batch, blocks, (int)gates.size(), c, plan, err);
+    }
+    qs_opts od = o;
+    od.dense_prec = QS_DENSE_OFF;
     if (o.tile_qubits > 0 || o.group_qubits > 0 || n < 13)
-        return build_fused_plan_cfg(n, batch, detected, (int)gates.size(), o, plan, err);
+        return build_fused_plan_cfg(n, batch, detected, (int)gates.size(), od, plan, err);
     bool has_qft = false;
     for (const FOp &f : detected)
         if (f.kind == F_QFT) has_qft = true;
@@ -1196,7 +1701,7 @@ qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, co
     const int n_cand = has_qft ? 3 : 2;
     Plan cand[3];
     for (int i = 0; i < n_cand; ++i) {
-        qs_opts c = o;
+        qs_opts c = od;
         c.tile_qubits = cfg[i][0];
         c.group_qubits = cfg[i][1];
         qs_status s = build_fused_plan_cfg(n, batch, detected, (int)gates.size(), c, cand[i], err);
@@ -1226,6 +1731,8 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
     if (L < 1) L = 1;
     int R = o.group_qubits > 0 ? std::min(o.group_qubits, kMaxGroup) : kMaxGroup;
     R = std::min(R, T);
+    const int dprec = o.dense_prec;
+    const int max_const = dprec ? kMaxConstDense : kMaxConst;
 
     // split oversized diagonals; pre-plan each diagonal's tables
     std::vector<FOp> ops2;
@@ -1294,12 +1801,16 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
                 }
             if (ok) {
                 uint64_t need = f.cN & ~S;
-                OpCost c = op_cost(n, f, R, f.kind == F_DIAG ? &dplans[rem[j]] : nullptr);
+                OpCost c = op_cost(n, f, R, f.kind == F_DIAG ? &dplans[rem[j]] : nullptr, dprec);
                 uint64_t nb = f.cN;
                 int ns = sim_sweeps;
                 uint64_t ng = sim_group;
                 bool no = sim_open;
-                if (nb) {
+                if (f.kind == F_DENSE) {   // a sweep of its own
+                    ns++;
+                    ng = 0;
+                    no = false;
+                } else if (nb) {
                     if (no && popc64(ng | nb) <= R) {
                         ng |= nb;
                     } else {
@@ -1312,7 +1823,7 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
                     ng = 0;
                     no = true;
                 }
-                bool fits = popc64(need) <= slots - (popc64(S) - L) && c_const + c.n_const <= kMaxConst &&
+                bool fits = popc64(need) <= slots - (popc64(S) - L) && c_const + c.n_const <= max_const &&
                             c_micro + c.n_micro <= kMaxMicro - 8 && c_diag + c.n_diag <= kMaxDiag &&
                             ns <= kMaxSweeps - 1;
                 if (fits) {
@@ -1339,7 +1850,7 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
         }
         // pad the tile to T bits with the lowest unused high bits
         for (int b = L; b < n && popc64(S) < T; ++b) S |= 1ull << b;
-        PassBuilder pb(n, L, T, R, S, batch);
+        PassBuilder pb(n, L, T, R, S, batch, dprec);
         for (int id : taken) {
             pb.add(ops[id], ops[id].kind == F_DIAG ? &dplans[id] : nullptr);
             if (pb.tp.n_sweeps >= kMaxSweeps - 1) break;   // guarded by taken limit
@@ -1492,7 +2003,11 @@ std::string Plan::describe() const {
             for (int k = 0; k < t.H; ++k) os << (k ? "," : "") << t.hb[k];
             os << "] tma=" << (hp.tma.ok ? 1 : 0) << " sweeps=" << t.n_sweeps
                << " U1=" << cnt[MK_U1] + cnt[MK_H] + cnt[MK_RXC] + cnt[MK_U1R] << " U2=" << cnt[MK_U2]
-               << " DIAG=" << cnt[MK_DIAG] << " QFT=" << cnt[MK_QFT] << " consts=" << t.n_const << "\n";
+               << " DIAG=" << cnt[MK_DIAG] << " QFT=" << cnt[MK_QFT];
+            int nd = 0;
+            for (int k = 0; k < t.n_sweeps; ++k) nd += t.sweeps[k].dense ? 1 : 0;
+            if (nd) os << " DENSE=" << nd;
+            os << " consts=" << t.n_const << "\n";
         } else if (hp.type == HostPass::PERM) {
             os << "PERM xor=" << hp.perm.xor_mask << "\n";
         } else {

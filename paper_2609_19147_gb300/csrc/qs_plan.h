@@ -41,7 +41,7 @@ struct Diag {
     void merge(const Diag &o);
 };
 
-enum FKind { F_U1 = 0, F_U2, F_DIAG, F_QFT, F_GF2 };
+enum FKind { F_U1 = 0, F_U2, F_DIAG, F_QFT, F_GF2, F_DENSE };
 
 // A fused op in index-bit space.
 struct FOp {
@@ -55,6 +55,10 @@ struct FOp {
     // parity(rows[i] & x) ^ bit i of c); the state moves psi'[f(x)] = psi[x].
     std::vector<uint64_t> rows;
     uint64_t c = 0;
+    // F_DENSE: block on index bits dbits (k <= 5); dm is 2^k x 2^k row-major,
+    // bit j of a matrix index is the value of index bit dbits[j]
+    std::vector<int> dbits;
+    std::vector<cd> dm;
     int n_gates = 1;               // source gates absorbed
     uint64_t N() const;            // bits acted on non-diagonally
     uint64_t D() const;            // bits the op depends on diagonally
@@ -116,5 +120,13 @@ qs_status build_pergate_plan(int n, const std::vector<RGate> &gates, Plan &plan,
 
 // Fusion detector only (exposed for tests through qs_plan_describe).
 void detect(int n, const std::vector<RGate> &gates, std::vector<FOp> &ops);
+
+// Regroup detected ops into dense blocks of at most k index bits (qs_opts
+// dense_prec / block_qubits); blocks of 1-2 bits come back as F_U1 / F_U2.
+// cell_of[b] partitions the index bits: ops on disjoint bits share a block
+// only within one cell (dense_cells: cells that fill the tile windows of
+// T-bit tiles with L low bits).
+void dense_cells(int n, int T, int L, int k, int *cell_of);
+void fuse_dense(int n, int k, const int *cell_of, const std::vector<FOp> &in, std::vector<FOp> &out);
 
 }  // namespace qs

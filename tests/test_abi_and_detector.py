@@ -144,3 +144,44 @@ def test_tfim_trotter_steps_pack(qs):
     _, pg = _passes(qs, 30, gl, mode="pergate")
     assert pg == len(gl) == 10 * (29 * 2 + 30)
     assert p <= 3 * 10          # <= 3 HBM passes per Strang step
+
+
+# --- dense k-qubit blocks (qs_opts dense_prec / block_qubits) -----------------
+def test_dense_blocks_tfim_plan(qs):
+    # 30q TFIM, 100 Strang steps: per step the X layer and the in-cell ZZ bonds
+    # become 7 dense blocks (cells of 4-5 bits filling the 13-bit tile windows)
+    # and the 6 cross-cell bonds stay diagonal; the dense plans take no more
+    # HBM passes than the structured one
+    h = W.tfim_fields(30, 3)
+    gl = W.tfim_gates(30, 100, 0.05, 1.0, h, order=2)
+    _, p0 = _passes(qs, 30, gl)
+    for d in ("fp32", "tf32x3", "bf16"):
+        text, p = _passes(qs, 30, gl, dense=d)
+        blocks = sum(int(m) for m in re.findall(r"DENSE=(\d+)", text))
+        assert blocks == 7 * 100, (d, blocks)
+        assert p <= p0, (d, p, p0)
+
+
+def test_dense_blocks_general_circuits_plan(qs):
+    gl = W.random_circuit(14, 300, 4242)
+    for k in (3, 4, 5):
+        text, p = _passes(qs, 14, gl, dense="tf32x3", block_qubits=k)
+        assert "DENSE=" in text and p >= 1
+    # a state smaller than a 13-bit tile: the tile is the whole state
+    text, _ = _passes(qs, 6, W.random_circuit(6, 60, 1), dense="bf16")
+    assert "T=6" in text and "DENSE=" in text
+
+
+def test_dense_options_validated(qs):
+    import ctypes
+    gl = [W.Gate("H", (0,))]
+    for k in (1, 2, 6, -1):
+        with pytest.raises(qs.QsError) as e:
+            qs.plan_describe(8, gl, dense="fp32", block_qubits=k)
+        assert e.value.status == qs.QS_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        qs.plan_describe(8, gl, dense="fp64")
+    cg = qs.CGates(gl)
+    o = qs._opts()
+    o.dense_prec = 9
+    assert qs._lib.qs_plan_describe(8, cg.arr, cg.n, ctypes.byref(o), None, 0, None) == qs.QS_ERR_INVALID_ARG
