@@ -1,6 +1,7 @@
 // Tile-pass launcher: picks the kernel instantiation for the pass (register
-// group size R, threads, CTAs per SM, dense sweeps); the instantiations live
-// in k_tile_r123.cu, k_tile_r4.cu, k_tile_r5.cu and k_tile_dense.cu.
+// group size R, threads, CTAs per SM, dense sweeps, op set); the
+// instantiations live in k_tile_r123.cu, k_tile_r4.cu, k_tile_r5.cu,
+// k_tile_layer4.cu, k_tile_layer5.cu and k_tile_dense.cu.
 #include <cuda.h>
 
 #include <string>
@@ -19,6 +20,8 @@ QS_TILE_TU(r123)
 QS_TILE_TU(r4)
 QS_TILE_TU(r5)
 QS_TILE_TU(dense)
+QS_TILE_TU(layer4)
+QS_TILE_TU(layer5)
 #undef QS_TILE_TU
 
 void tile_kernel_smem_config(int bytes) {
@@ -26,6 +29,8 @@ void tile_kernel_smem_config(int bytes) {
     tile_smem_config_r4(bytes);
     tile_smem_config_r5(bytes);
     tile_smem_config_dense(bytes);
+    tile_smem_config_layer4(bytes);
+    tile_smem_config_layer5(bytes);
 }
 
 // R = register group size; 4-bit groups on 13-bit tiles run 512 threads (16
@@ -36,6 +41,8 @@ cudaError_t launch_tile_pass(int R, const TileArgs &A, const void *tm_src, const
     const CUtensorMap &md = *reinterpret_cast<const CUtensorMap *>(tm_dst);
     cudaGetLastError();
     if (A.dense) return launch_tile_dense(R, A, ms, md, grid, smem_bytes, st);
+    if (A.kset == 1 && R == 4) return launch_tile_layer4(R, A, ms, md, grid, smem_bytes, st);
+    if (A.kset == 1 && R == 5) return launch_tile_layer5(R, A, ms, md, grid, smem_bytes, st);
     if (R == 5) return launch_tile_r5(R, A, ms, md, grid, smem_bytes, st);
     if (R == 4) return launch_tile_r4(R, A, ms, md, grid, smem_bytes, st);
     return launch_tile_r123(R, A, ms, md, grid, smem_bytes, st);
@@ -43,7 +50,9 @@ cudaError_t launch_tile_pass(int R, const TileArgs &A, const void *tm_src, const
 
 std::string tile_kernel_attrs(int R, const TileArgs &A) {
     cudaFuncAttributes fa;
-    cudaError_t e = A.dense   ? tile_attrs_dense(R, A, &fa)
+    cudaError_t e = A.dense                ? tile_attrs_dense(R, A, &fa)
+                    : A.kset == 1 && R == 4 ? tile_attrs_layer4(R, A, &fa)
+                    : A.kset == 1 && R == 5 ? tile_attrs_layer5(R, A, &fa)
                     : R == 5 ? tile_attrs_r5(R, A, &fa)
                     : R == 4 ? tile_attrs_r4(R, A, &fa)
                              : tile_attrs_r123(R, A, &fa);

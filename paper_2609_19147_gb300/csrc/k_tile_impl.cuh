@@ -11,11 +11,15 @@
 // box of extent 1 in every gap).  When the bit set needs more than 5 dims the
 // pass falls back to one bulk copy per 2^L-amplitude row.
 //
-// Tiles rotate through 2-3 shared buffers: while the 8 warps process tile k,
-// the load of tile k+1 and the stores of tiles k-1 (and k-2) are in flight.
-// Thread 0 issues the copies; with 3 buffers the buffer it refills was
-// stored two tiles ago, so waiting for that store to have read shared memory
-// does not stall.
+// Tiles rotate through 2-6 shared buffers: while the warps process tile k,
+// the loads of the next tiles and the stores of the previous ones are in
+// flight.  Thread 0 issues the copies; the buffer it refills was stored
+// NB - D tiles ago (D = tiles loaded ahead), so waiting for that store to
+// have read shared memory rarely stalls.
+//
+// Passes with dense-block sweeps and passes whose micro-ops are all 1q-layer
+// or diagonal ops run in their own instantiations (DENSE, KS), which keeps
+// the code and register budget of each kernel small.
 //
 // Between load and store the tile goes through "sweeps": every compute thread
 // holds 2^R amplitudes that differ in R tile bits (registers) and applies the
@@ -111,17 +115,6 @@ __device__ __forceinline__ void tma_prefetch_l2_5d(const CUtensorMap *tm, const 
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src_gmem) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src_gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void bulk_wait_read0() {
-    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
 __device__ __forceinline__ void bulk_wait_all0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -216,30 +209,35 @@ __device__ __forceinline__ void op_rxc(float2 (&a)[1 << R], const float2 *cs) {
     }
 }
 
-// real 2x2 (RY family): 4 FP32 ops per amplitude
+// real 2x2 (RY family): a real factor scales (re, im) alike, so the packed
+// FP32x2 pipe does both halves of an amplitude in one instruction (2 per
+// amplitude; the same roundings as the scalar FMUL + FFMA)
 template <int R, int M>
 __device__ __forceinline__ void op_u1r(float2 (&a)[1 << R], const float2 *cs) {
-    const float m00 = cs[0].x, m01 = cs[0].y, m10 = cs[1].x, m11 = cs[1].y;
+    const float2 m00 = make_float2(cs[0].x, cs[0].x), m01 = make_float2(cs[0].y, cs[0].y);
+    const float2 m10 = make_float2(cs[1].x, cs[1].x), m11 = make_float2(cs[1].y, cs[1].y);
 #pragma unroll
     for (int j = 0; j < (1 << R); ++j) {
         if ((j >> M) & 1) continue;
         const int k = j | (1 << M);
         const float2 a0 = a[j], a1 = a[k];
-        a[j] = make_float2(fmaf(m00, a0.x, m01 * a1.x), fmaf(m00, a0.y, m01 * a1.y));
-        a[k] = make_float2(fmaf(m10, a0.x, m11 * a1.x), fmaf(m10, a0.y, m11 * a1.y));
+        a[j] = __ffma2_rn(m00, a0, __fmul2_rn(m01, a1));
+        a[k] = __ffma2_rn(m10, a0, __fmul2_rn(m11, a1));
     }
 }
 
-// unnormalised Hadamard butterfly (the 1/sqrt 2 is folded into the sweep scale)
+// unnormalised Hadamard butterfly (the 1/sqrt 2 is folded into the sweep
+// scale): one packed add and one packed a0 - a1 (an exact FMA with -1)
 template <int R, int M>
 __device__ __forceinline__ void op_h(float2 (&a)[1 << R]) {
+    const float2 neg1 = make_float2(-1.f, -1.f);
 #pragma unroll
     for (int j = 0; j < (1 << R); ++j) {
         if ((j >> M) & 1) continue;
         const int k = j | (1 << M);
         const float2 a0 = a[j], a1 = a[k];
-        a[j] = make_float2(a0.x + a1.x, a0.y + a1.y);
-        a[k] = make_float2(a0.x - a1.x, a0.y - a1.y);
+        a[j] = __fadd2_rn(a0, a1);
+        a[k] = __ffma2_rn(a1, neg1, a0);
     }
 }
 
@@ -252,8 +250,8 @@ __device__ __forceinline__ void op_qft(float2 (&a)[1 << R], const float2 *gtab, 
         if ((j >> M) & 1) continue;
         const int k = j | (1 << M);
         const float2 a0 = a[j], a1 = a[k];
-        a[j] = make_float2(a0.x + a1.x, a0.y + a1.y);
-        a[k] = cmul(make_float2(a0.x - a1.x, a0.y - a1.y), cmul(w, gtab[k]));
+        a[j] = __fadd2_rn(a0, a1);
+        a[k] = cmul(__ffma2_rn(a1, make_float2(-1.f, -1.f), a0), cmul(w, gtab[k]));
     }
 }
 
@@ -451,7 +449,73 @@ __device__ __forceinline__ void sweep_store(const SweepCtx &c, bool vec, int sad
     }
 }
 
-template <int R, int NT>
+// MK_DIAG on a register group: the static factor (slices / LUT groups that do
+// not see the group bits) once per item, the rest per amplitude
+template <int R>
+__device__ __forceinline__ void apply_diag(const SweepCtx &c, const MicroOp &op, uint64_t gbase, const Grp<R> &G,
+                                           float2 (&a)[1 << R]) {
+    const DiagDesc &d = c.diags[op.cst];
+    const uint32_t dyn_s = (uint32_t)op.a, dyn_g = (uint32_t)op.b;
+    float2 stat = d.pad0 ? make_float2(d.gph_re, d.gph_im) : make_float2(1.f, 0.f);
+    stat = diag_part(d, gbase, c.cs, ~dyn_s, ~dyn_g, stat);
+    if (dyn_g == 0 && __popc(dyn_s) <= 2 && dyn_s) {
+        // fast path: the varying tables' indices are the item's base
+        // index OR the group bits' contributions (disjoint bits)
+        const int s0 = __ffs(dyn_s) - 1;
+        const int s1 = (dyn_s & (dyn_s - 1)) ? __ffs(dyn_s & (dyn_s - 1)) - 1 : -1;
+        const uint32_t m0 = (1u << d.slice_w[s0]) - 1;
+        const int lo0 = d.slice_lo[s0];
+        const float2 *t0 = c.cs + d.slice_off[s0];
+        const uint32_t b0 = (uint32_t)(gbase >> lo0) & m0;
+        uint32_t q0[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) q0[m] = (uint32_t)(G.gg[m] >> lo0) & m0;
+        if (s1 < 0) {
+#pragma unroll
+            for (int j = 0; j < (1 << R); ++j) {
+                uint32_t i0 = b0;
+#pragma unroll
+                for (int m = 0; m < R; ++m)
+                    if ((j >> m) & 1) i0 |= q0[m];
+                a[j] = cmul(a[j], cmul(stat, t0[i0]));
+            }
+        } else {
+            const uint32_t m1 = (1u << d.slice_w[s1]) - 1;
+            const int lo1 = d.slice_lo[s1];
+            const float2 *t1 = c.cs + d.slice_off[s1];
+            const uint32_t b1 = (uint32_t)(gbase >> lo1) & m1;
+            uint32_t q1[R];
+#pragma unroll
+            for (int m = 0; m < R; ++m) q1[m] = (uint32_t)(G.gg[m] >> lo1) & m1;
+#pragma unroll
+            for (int j = 0; j < (1 << R); ++j) {
+                uint32_t i0 = b0, i1 = b1;
+#pragma unroll
+                for (int m = 0; m < R; ++m)
+                    if ((j >> m) & 1) {
+                        i0 |= q0[m];
+                        i1 |= q1[m];
+                    }
+                a[j] = cmul(a[j], cmul(stat, cmul(t0[i0], t1[i1])));
+            }
+        }
+    } else if (dyn_s | dyn_g) {
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j)
+            a[j] = cmul(a[j], diag_part(d, G.gidx(gbase, j), c.cs, dyn_s, dyn_g, stat));
+    } else {
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j) a[j] = cmul(a[j], stat);
+    }
+}
+
+// Kernel op sets: KS_ALL compiles every micro-op kind; KS_LAYER only those of
+// 1q-layer and diagonal passes (Trotter / QAOA / random-layer circuits),
+// which keeps the code small and the register allocation tight.
+constexpr int KS_ALL = 0;
+constexpr int KS_LAYER = 1;
+
+template <int R, int NT, int KS = KS_ALL>
 __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int sidx) {
     int gs[R];
     Grp<R> G;
@@ -465,113 +529,87 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
     const bool vec = S.vec != 0;
     const int *ts = c.tab_s + sidx * kItemTab;
     const uint64_t *tg = c.tab_g + sidx * kItemTab;
+    const int op_begin = S.op_begin, op_end = S.op_end;
+    const float scale = S.scale;
     for (int item = threadIdx.x; item < n_items; item += NT) {
         const int i0 = item & 31, i1 = 32 + ((item >> 5) & 31), i2 = 64 + ((item >> 10) & 15);
         const int saddr = ts[i0] ^ ts[i1] ^ ts[i2];
-        const uint64_t gbase = c.tile_gbase | tg[i0] | tg[i1] | tg[i2];
+        // global index of the item's group element 0 (only ops with controls,
+        // diagonals and QFT twiddles read it)
+        auto gbase = [&]() { return c.tile_gbase | tg[i0] | tg[i1] | tg[i2]; };
         float2 a[1 << R];
         sweep_load<R>(c, vec, saddr, gs, a);
-        for (int oi = S.op_begin; oi < S.op_end; ++oi) {
+        for (int oi = op_begin; oi < op_end; ++oi) {
             const MicroOp &op = c.micro[oi];
-            switch (op.kind) {
-                case MK_U1:
-                    disp_u1<R>(op.a, a, c.cs + op.cst, op.cmask, op.cval, gbase, G);
-                    break;
-                case MK_H:
-                    disp_h<R>(op.a, a);
-                    break;
-                case MK_RXC:
-                    disp_rxc<R>(op.a, a, c.cs + op.cst);
-                    break;
-                case MK_U1R:
-                    disp_u1r<R>(op.a, a, c.cs + op.cst);
-                    break;
-                case MK_U2:
-                    disp_u2<R>(op.a, op.b, a, c.cs + op.cst, op.cmask, op.cval, gbase, G);
-                    break;
-                case MK_QFT: {
-                    const uint64_t Mk = (op.p > op.lo) ? (((1ull << op.p) - 1) & ~((1ull << op.lo) - 1)) : 0ull;
-                    const float2 w = twiddle(gbase & Mk, op.p, c.roots);
-                    disp_qft<R>(op.a, a, c.cs + op.cst, w);
-                    break;
-                }
-                case MK_LAYER: {
-                    const float2 *k0 = c.cs + op.cst;
-                    const uint32_t mask = (uint32_t)op.b;
-                    switch (op.a) {
-                        case MK_RXC: layer_rxc<R>(a, k0, mask); break;
-                        case MK_U1R: layer_u1r<R>(a, k0, mask); break;
-                        case MK_U1: layer_u1<R>(a, k0, mask, G); break;
-                        default: layer_h<R>(a, mask); break;
-                    }
-                    break;
-                }
-                case MK_QFTL:
-                    layer_qft<R>(a, c.cs + op.cst, (uint32_t)op.b, op.cmask, gbase, c.roots);
-                    break;
-                case MK_DIAG: {
-                    const DiagDesc &d = c.diags[op.cst];
-                    const uint32_t dyn_s = (uint32_t)op.a, dyn_g = (uint32_t)op.b;
-                    float2 stat = d.pad0 ? make_float2(d.gph_re, d.gph_im) : make_float2(1.f, 0.f);
-                    stat = diag_part(d, gbase, c.cs, ~dyn_s, ~dyn_g, stat);
-                    if (dyn_g == 0 && __popc(dyn_s) <= 2 && dyn_s) {
-                        // fast path: the varying tables' indices are the item's base
-                        // index OR the group bits' contributions (disjoint bits)
-                        const int s0 = __ffs(dyn_s) - 1;
-                        const int s1 = (dyn_s & (dyn_s - 1)) ? __ffs(dyn_s & (dyn_s - 1)) - 1 : -1;
-                        const uint32_t m0 = (1u << d.slice_w[s0]) - 1;
-                        const int lo0 = d.slice_lo[s0];
-                        const float2 *t0 = c.cs + d.slice_off[s0];
-                        const uint32_t b0 = (uint32_t)(gbase >> lo0) & m0;
-                        uint32_t q0[R];
-#pragma unroll
-                        for (int m = 0; m < R; ++m) q0[m] = (uint32_t)(G.gg[m] >> lo0) & m0;
-                        if (s1 < 0) {
-#pragma unroll
-                            for (int j = 0; j < (1 << R); ++j) {
-                                uint32_t i0 = b0;
-#pragma unroll
-                                for (int m = 0; m < R; ++m)
-                                    if ((j >> m) & 1) i0 |= q0[m];
-                                a[j] = cmul(a[j], cmul(stat, t0[i0]));
-                            }
-                        } else {
-                            const uint32_t m1 = (1u << d.slice_w[s1]) - 1;
-                            const int lo1 = d.slice_lo[s1];
-                            const float2 *t1 = c.cs + d.slice_off[s1];
-                            const uint32_t b1 = (uint32_t)(gbase >> lo1) & m1;
-                            uint32_t q1[R];
-#pragma unroll
-                            for (int m = 0; m < R; ++m) q1[m] = (uint32_t)(G.gg[m] >> lo1) & m1;
-#pragma unroll
-                            for (int j = 0; j < (1 << R); ++j) {
-                                uint32_t i0 = b0, i1 = b1;
-#pragma unroll
-                                for (int m = 0; m < R; ++m)
-                                    if ((j >> m) & 1) {
-                                        i0 |= q0[m];
-                                        i1 |= q1[m];
-                                    }
-                                a[j] = cmul(a[j], cmul(stat, cmul(t0[i0], t1[i1])));
-                            }
+            if constexpr (KS == KS_LAYER) {
+                switch (op.kind) {
+                    case MK_LAYER: {
+                        const float2 *k0 = c.cs + op.cst;
+                        const uint32_t mask = (uint32_t)op.b;
+                        switch (op.a) {
+                            case MK_RXC: layer_rxc<R>(a, k0, mask); break;
+                            case MK_U1R: layer_u1r<R>(a, k0, mask); break;
+                            case MK_U1: layer_u1<R>(a, k0, mask, G); break;
+                            default: layer_h<R>(a, mask); break;
                         }
-                    } else if (dyn_s | dyn_g) {
-#pragma unroll
-                        for (int j = 0; j < (1 << R); ++j)
-                            a[j] = cmul(a[j], diag_part(d, G.gidx(gbase, j), c.cs, dyn_s, dyn_g, stat));
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < (1 << R); ++j) a[j] = cmul(a[j], stat);
+                        break;
                     }
-                    break;
+                    case MK_RXC: disp_rxc<R>(op.a, a, c.cs + op.cst); break;
+                    case MK_U1R: disp_u1r<R>(op.a, a, c.cs + op.cst); break;
+                    case MK_H: disp_h<R>(op.a, a); break;
+                    case MK_U1: disp_u1<R>(op.a, a, c.cs + op.cst, op.cmask, op.cval, gbase(), G); break;
+                    case MK_DIAG: apply_diag<R>(c, op, gbase(), G, a); break;
+                    default: break;
                 }
-                default:
-                    break;
+            } else {
+                switch (op.kind) {
+                    case MK_U1:
+                        disp_u1<R>(op.a, a, c.cs + op.cst, op.cmask, op.cval, gbase(), G);
+                        break;
+                    case MK_H:
+                        disp_h<R>(op.a, a);
+                        break;
+                    case MK_RXC:
+                        disp_rxc<R>(op.a, a, c.cs + op.cst);
+                        break;
+                    case MK_U1R:
+                        disp_u1r<R>(op.a, a, c.cs + op.cst);
+                        break;
+                    case MK_U2:
+                        disp_u2<R>(op.a, op.b, a, c.cs + op.cst, op.cmask, op.cval, gbase(), G);
+                        break;
+                    case MK_QFT: {
+                        const uint64_t Mk = (op.p > op.lo) ? (((1ull << op.p) - 1) & ~((1ull << op.lo) - 1)) : 0ull;
+                        const float2 w = twiddle(gbase() & Mk, op.p, c.roots);
+                        disp_qft<R>(op.a, a, c.cs + op.cst, w);
+                        break;
+                    }
+                    case MK_LAYER: {
+                        const float2 *k0 = c.cs + op.cst;
+                        const uint32_t mask = (uint32_t)op.b;
+                        switch (op.a) {
+                            case MK_RXC: layer_rxc<R>(a, k0, mask); break;
+                            case MK_U1R: layer_u1r<R>(a, k0, mask); break;
+                            case MK_U1: layer_u1<R>(a, k0, mask, G); break;
+                            default: layer_h<R>(a, mask); break;
+                        }
+                        break;
+                    }
+                    case MK_QFTL:
+                        layer_qft<R>(a, c.cs + op.cst, (uint32_t)op.b, op.cmask, gbase(), c.roots);
+                        break;
+                    case MK_DIAG:
+                        apply_diag<R>(c, op, gbase(), G, a);
+                        break;
+                    default:
+                        break;
+                }
             }
         }
-        if (S.scale != 1.f) {
+        if (scale != 1.f) {
+            const float2 sc = make_float2(scale, scale);
 #pragma unroll
-            for (int j = 0; j < (1 << R); ++j) a[j] = make_float2(a[j].x * S.scale, a[j].y * S.scale);
+            for (int j = 0; j < (1 << R); ++j) a[j] = __fmul2_rn(a[j], sc);
         }
         sweep_store<R>(c, vec, saddr, gs, a);
     }
@@ -833,23 +871,6 @@ __device__ __forceinline__ uint64_t tile_base(const TileArgs &A, long long ti) {
     return g;
 }
 
-// 16-byte chunk q of a tile (tile-local index 2q, 2q+1): its shared-memory
-// float2 offset (XOR-linear layout) and its global offset within the state
-__device__ __forceinline__ int chunk_smem(int q, int T, const int *contrib) {
-    int o = 0;
-    for (int tb = 1; tb < T; ++tb)
-        if ((q >> (tb - 1)) & 1) o ^= contrib[tb];
-    return o;
-}
-__device__ __forceinline__ uint64_t chunk_glob(int q, int L, int H, const int *hb) {
-    const int t = q << 1;
-    uint64_t g = (uint64_t)(t & ((1 << L) - 1));
-    const int r = t >> L;
-    for (int k = 0; k < H; ++k)
-        if ((r >> k) & 1) g |= 1ull << hb[k];
-    return g;
-}
-
 __device__ __forceinline__ void tile_coords(const TmaGeom &g, long long ti, long long bi, int c[5]) {
 #pragma unroll
     for (int d = 0; d < 5; ++d) {
@@ -864,7 +885,7 @@ __device__ __forceinline__ void tile_coords(const TmaGeom &g, long long ti, long
 
 // DENSE: the pass has dense-block sweeps (a separate instantiation, so that
 // the register budget of the other passes does not grow with the dense code)
-template <int R, int NT, int MINB = 1, bool DENSE = false>
+template <int R, int NT, int MINB = 1, bool DENSE = false, int KS = KS_ALL>
 __global__ void __launch_bounds__(NT, MINB)
     tile_pass_kernel(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst,
                      const TileArgs A) {
@@ -947,70 +968,6 @@ __global__ void __launch_bounds__(NT, MINB)
     const uint32_t row_bytes = 8u << L;
 
     // thread 0 issues every copy (TMA path: one instruction per tile)
-    const int io = A.io_mode;
-    const int n_chunks = tile_elems >> 1;
-    // 16-byte chunk q = tid + i * NT of a tile: offsets are XOR/OR-linear in the
-    // bits of q, so split them into a per-thread part (computed once) and the
-    // parts of the (at most 4) loop bits
-    int c_smem = 0;
-    uint64_t c_glob = 0;
-    int i_smem[4] = {0, 0, 0, 0};
-    uint64_t i_glob[4] = {0, 0, 0, 0};
-    int n_ib = 0;
-    if (io != 0) {
-        if (tid < n_chunks) {
-            c_smem = chunk_smem(tid, T, s_contrib);
-            c_glob = chunk_glob(tid, L, H, s_hb);
-        }
-        for (int m = 0; (NT << m) < n_chunks && m < 4; ++m) {
-            i_smem[m] = chunk_smem(NT << m, T, s_contrib);
-            i_glob[m] = chunk_glob(NT << m, L, H, s_hb);
-            n_ib = m + 1;
-        }
-    }
-    const int per_thread = n_chunks > NT ? n_chunks / NT : 1;
-    // cp.async path: every thread copies its 16-byte chunks (coalesced rows)
-    auto load_threads = [&](int k) {
-        float2 *dstbuf = buf0 + (size_t)(k % NB) * tile_elems;
-        const long long t = blockIdx.x + (long long)k * stride;
-        const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
-        const float2 *src = A.src + bi * A.state_elems + tile_base(A, ti);
-        if (tid < n_chunks) {
-#pragma unroll 4
-            for (int i = 0; i < per_thread; ++i) {
-                int so = c_smem;
-                uint64_t go = c_glob;
-                for (int m = 0; m < n_ib; ++m)
-                    if ((i >> m) & 1) {
-                        so ^= i_smem[m];
-                        go |= i_glob[m];
-                    }
-                cp_async16(dstbuf + so, src + go);
-            }
-        }
-        cp_async_commit();
-    };
-    // thread stores: 16-byte chunks straight from shared memory to HBM
-    auto store_threads = [&](int k) {
-        const float2 *srcbuf = buf0 + (size_t)(k % NB) * tile_elems;
-        const long long t = blockIdx.x + (long long)k * stride;
-        const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
-        float2 *dst = A.dst + bi * A.state_elems + tile_base(A, ti);
-        if (tid < n_chunks) {
-#pragma unroll 4
-            for (int i = 0; i < per_thread; ++i) {
-                int so = c_smem;
-                uint64_t go = c_glob;
-                for (int m = 0; m < n_ib; ++m)
-                    if ((i >> m) & 1) {
-                        so ^= i_smem[m];
-                        go |= i_glob[m];
-                    }
-                const float4 v = *reinterpret_cast<const float4 *>(srcbuf + so);
-                *reinterpret_cast<float4 *>(dst + go) = v;
-            }
-        }
-    };
     auto load = [&](int k) {
         const int b = k % NB;
         float2 *dstbuf = buf0 + (size_t)b * tile_elems;
@@ -1052,16 +1009,10 @@ __global__ void __launch_bounds__(NT, MINB)
         tile_coords(A.geo, ti, bi, c);
         tma_prefetch_l2_5d(&tm_src, c);
     };
-    if (tid == 0 && io != 2 && A.use_tma)
+    if (tid == 0 && A.use_tma)
         for (int k = D; k < D + PF && k < n_mine; ++k) l2pf(k);
-    if (io == 2) {
-        for (int k = 0; k < D; ++k) {
-            if (k < n_mine) load_threads(k);
-            else cp_async_commit();   // keep one group per tile slot
-        }
-    } else if (tid == 0) {
+    if (tid == 0)
         for (int k = 0; k < D && k < n_mine; ++k) load(k);
-    }
 
     SweepCtx c;
     c.T = T;
@@ -1075,35 +1026,19 @@ __global__ void __launch_bounds__(NT, MINB)
     c.tab_s = s_tab_s;
     c.tab_g = s_tab_g;
     for (int k = 0; k < n_mine; ++k) {
-        bool ok = true;
-        if (io == 2) {
-            // buffer (k+D) % NB held tile k+D-NB <= k-1, already stored by the threads
-            if (k + D < n_mine) load_threads(k + D);
-            else cp_async_commit();
-            // groups are committed per tile in order: tile k is done when at most D remain
-            switch (D) {
-                case 1: cp_async_wait<1>(); break;
-                case 2: cp_async_wait<2>(); break;
-                case 3: cp_async_wait<3>(); break;
-                default: cp_async_wait<4>(); break;
+        if (tid == 0 && k + D < n_mine) {
+            // buffer (k+D) % NB last held tile k+D-NB, stored at the end of
+            // iteration k+D-NB: allow the NB-D-1 newer stores to stay in flight
+            switch (NB - D - 1) {
+                case 0: asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); break;
+                case 1: asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); break;
+                case 2: asm volatile("cp.async.bulk.wait_group.read 2;" ::: "memory"); break;
+                default: asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory"); break;
             }
-        } else {
-            if (tid == 0 && k + D < n_mine) {
-                // buffer (k+D) % NB last held tile k+D-NB, stored at the end of
-                // iteration k+D-NB: allow the NB-D-1 newer stores to stay in flight
-                if (io == 0) {
-                    switch (NB - D - 1) {
-                        case 0: asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); break;
-                        case 1: asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); break;
-                        case 2: asm volatile("cp.async.bulk.wait_group.read 2;" ::: "memory"); break;
-                        default: asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory"); break;
-                    }
-                }
-                load(k + D);
-            }
-            if (tid == 0 && A.use_tma && k + D + PF < n_mine) l2pf(k + D + PF);
-            ok = mbar_wait_bounded(&full[k % NB], (uint32_t)((k / NB) & 1));
+            load(k + D);
         }
+        if (tid == 0 && A.use_tma && k + D + PF < n_mine) l2pf(k + D + PF);
+        const bool ok = mbar_wait_bounded(&full[k % NB], (uint32_t)((k / NB) & 1));
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicCAS(A.err, 0, (int)QS_ERR_TIMEOUT);
@@ -1116,27 +1051,16 @@ __global__ void __launch_bounds__(NT, MINB)
         const long long t = blockIdx.x + (long long)k * stride;
         const long long ti = t % A.n_tiles;
         c.buf = buf0 + (size_t)(k % NB) * tile_elems;
-        c.tile_gbase = tile_base(A, ti);
+        c.tile_gbase = A.needs_gidx ? tile_base(A, ti) : 0;
         for (int s = 0; s < n_sweeps; ++s) {
             if (DENSE && s_sweeps[s].dense) run_dense<NT>(c, s_sweeps[s], s);
-            else run_sweep<R, NT>(c, s_sweeps[s], s);
-            __syncthreads();
+            else run_sweep<R, NT, KS>(c, s_sweeps[s], s);
+            if (s + 1 < n_sweeps) __syncthreads();
         }
-        if (io == 0) {
-            fence_proxy_async();
-            __syncthreads();
-            if (tid == 0) store(k);
-        } else {
-            store_threads(k);
-            // the buffer is reloaded D iterations later, after this barrier
-            if (io == 2) __syncthreads();
-            else {
-                fence_proxy_async();   // generic reads before the async-proxy refill
-                __syncthreads();
-            }
-        }
+        fence_proxy_async();   // generic-proxy writes before the async-proxy store
+        __syncthreads();
+        if (tid == 0) store(k);
     }
-    if (io == 2) cp_async_wait<0>();
     if (tid == 0) bulk_wait_all0();
 }
 

@@ -375,21 +375,16 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     A.threads = (tp.R == 4 && tp.T >= 13) ? 512 : 256;
     for (int k = 0; k < tp.n_sweeps; ++k)
         if (tp.sweeps[k].dense) A.dense = 1;
+    A.kset = 1;
+    for (int k = 0; k < tp.n_micro; ++k) {
+        const MicroOp &mo = tp.micro[k];
+        if (mo.kind == MK_DIAG || mo.kind == MK_QFT || mo.kind == MK_QFTL || mo.cmask) A.needs_gidx = 1;
+        if (!(mo.kind == MK_LAYER || mo.kind == MK_RXC || mo.kind == MK_U1R || mo.kind == MK_H || mo.kind == MK_U1 ||
+              mo.kind == MK_DIAG))
+            A.kset = 0;
+    }
     if (A.dense && (tp.R != 5 || A.ctas_per_sm != 1)) return fail(QS_ERR_INTERNAL, "dense pass without 5-bit groups");
     if (A.dense) A.threads = 256;
-    {
-        static int io_env = -2;
-        if (io_env == -2) {
-            const char *e = getenv("QS_TILE_IO");
-            io_env = e ? atoi(e) : -1;
-        }
-        A.io_mode = io_env >= 0 ? io_env : 0;
-        if (!A.use_tma && A.io_mode != 2) A.io_mode = 0;   // row-copy fallback pairs with bulk stores
-    }
-    if (A.io_mode != 0) {   // thread stores: the refilled buffer is free right after its iteration
-        A.n_buf = std::min(A.n_buf, 4);
-        A.prefetch = A.n_buf - 1;
-    }
     {
         static int pf_env = -2, d_env = -2;
         if (pf_env == -2) {

@@ -36,10 +36,10 @@ struct TileArgs {
     int threads;               // 256, or 512 for 4-bit register groups on 13-bit tiles
     int ctas_per_sm;           // 2: two co-resident CTAs (12-bit tiles, 4-bit groups)
     int l2_prefetch;           // tiles warmed in L2 beyond the shared-memory prefetch
-    int io_mode;               // 0: TMA load + TMA store; 1: TMA load + thread stores;
-                               // 2: cp.async loads + thread stores
     int use_tma;               // 1: one tensor copy per tile; 0: one bulk copy per row
     int dense;                 // 1: the pass has dense-block sweeps (kernel with the dense paths)
+    int kset;                  // 1: every micro-op is a 1q / layer / diagonal op (KS_LAYER kernels)
+    int needs_gidx;            // 1: some micro-op reads global indices (controls, diagonals, QFT)
     TmaGeom geo;
     int *err;                  // device status word
 };

@@ -501,6 +501,49 @@ bool match_ladder(const Diag &d, int p, int &lo) {
 }
 }  // namespace
 
+// RX-type 1q ops between two diagonal runs: U = [[c, i s], [i s, c]] equals
+// S M S^dagger with S = diag(1, i) and the real M = [[c, -s], [s, c]] (a basis
+// conjugation, as for the XX / YY layers of Sec. 5.1).  S^dagger commutes with
+// the 1q ops on other bits back to the previous diagonal and S forward to the
+// next one, so both fold into diagonals that run anyway; in a Trotter stream
+// the S of one step and the S^dagger of the next cancel exactly (the phase
+// adjustments are counted in units of pi/2).  The real M runs on the packed
+// FP32x2 pipe at half the instructions of the complex form.
+static void conjugate_rx_runs(std::vector<FOp> &ops) {
+    std::vector<std::map<int, int>> adj(ops.size());
+    for (size_t i = 0; i < ops.size(); ++i) {
+        if (ops[i].kind != F_DIAG) continue;
+        size_t j = i + 1;
+        uint64_t seen = 0;
+        bool distinct = true;
+        while (j < ops.size() && ops[j].kind == F_U1 && ops[j].cmask == 0) {
+            if ((seen >> ops[j].t0) & 1) distinct = false;
+            seen |= 1ull << ops[j].t0;
+            ++j;
+        }
+        if (j >= ops.size() || ops[j].kind != F_DIAG || j == i + 1 || !distinct) continue;
+        for (size_t k = i + 1; k < j; ++k) {
+            FOp &f = ops[k];
+            const cd *m = f.m;
+            const bool rxc = m[0].imag() == 0 && m[0] == m[3] && m[1].real() == 0 && m[1] == m[2] && m[1].imag() != 0;
+            if (!rxc) continue;
+            const double c = m[0].real(), sv = m[1].imag();
+            f.m[0] = cd(c, 0);
+            f.m[1] = cd(-sv, 0);
+            f.m[2] = cd(sv, 0);
+            f.m[3] = cd(c, 0);
+            adj[i][f.t0] -= 1;   // S^dagger, applied before M
+            adj[j][f.t0] += 1;   // S, applied after M
+        }
+        i = j - 1;
+    }
+    for (size_t i = 0; i < ops.size(); ++i)
+        for (auto &kv : adj[i]) {
+            const int q = ((kv.second % 4) + 4) % 4;   // multiples of pi/2, mod 2 pi
+            if (q) ops[i].diag.a[kv.first] += q * (kPi / 2);
+        }
+}
+
 void detect(int n, const std::vector<RGate> &gates, std::vector<FOp> &ops) {
     std::vector<FOp> raw;
     Detector det(n, raw);
@@ -561,6 +604,7 @@ void detect(int n, const std::vector<RGate> &gates, std::vector<FOp> &ops) {
             i = j;
         }
     }
+    conjugate_rx_runs(ops);
 }
 
 // ---------------------------------------------------------------------------
@@ -2004,9 +2048,13 @@ std::string Plan::describe() const {
             os << "] tma=" << (hp.tma.ok ? 1 : 0) << " sweeps=" << t.n_sweeps
                << " U1=" << cnt[MK_U1] + cnt[MK_H] + cnt[MK_RXC] + cnt[MK_U1R] << " U2=" << cnt[MK_U2]
                << " DIAG=" << cnt[MK_DIAG] << " QFT=" << cnt[MK_QFT];
-            int nd = 0;
+            int nd = 0, slow = 0;
             for (int k = 0; k < t.n_sweeps; ++k) nd += t.sweeps[k].dense ? 1 : 0;
+            for (int k = 0; k < t.n_micro; ++k)
+                if (t.micro[k].kind == MK_DIAG && (t.micro[k].b != 0 || __builtin_popcount((unsigned)t.micro[k].a) > 2))
+                    slow++;
             if (nd) os << " DENSE=" << nd;
+            if (slow) os << " DIAG_GENERAL=" << slow;
             os << " consts=" << t.n_const << "\n";
         } else if (hp.type == HostPass::PERM) {
             os << "PERM xor=" << hp.perm.xor_mask << "\n";
