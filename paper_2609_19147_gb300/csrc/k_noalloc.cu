@@ -132,6 +132,7 @@ extern "C" qs_status qs_expect_noalloc(const void *dev_state, int n, int batch, 
     const long long elems = 1ll << n;
     for (int c = 0; c < n_chunks; ++c) {
         qs::ExpectArgs A;
+        std::memset(&A, 0, sizeof A);
         A.psi = static_cast<const float2 *>(dev_state);
         A.lam = nullptr;
         A.state_elems = elems;

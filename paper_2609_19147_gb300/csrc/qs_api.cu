@@ -6,6 +6,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <array>
 #include <cstdlib>
 #include <chrono>
 #include <cmath>
@@ -18,6 +19,8 @@
 #include <string>
 #include <unordered_map>
 #include <vector>
+#include <thread>
+#include <atomic>
 
 #include "qs.h"
 #include "qs_internal.h"
@@ -196,22 +199,33 @@ qs_status upload_plan(qs_state *st, DevicePlan &dp) {
     return QS_OK;
 }
 
+DevicePlan *cache_lookup(qs_state *st, uint64_t key) {
+    auto it = st->cache.find(key);
+    if (it == st->cache.end()) return nullptr;
+    st->lru.erase(it->second->lru);
+    st->lru.push_front(key);
+    it->second->lru = st->lru.begin();
+    return it->second.get();
+}
+
+qs_status cache_insert(qs_state *st, uint64_t key, Plan &&plan, DevicePlan **out);
+
 qs_status get_plan(qs_state *st, const std::vector<RGate> &gates, const qs_opts &o, int batch, DevicePlan **out) {
     uint64_t key = plan_key(st->n, batch, gates, o);
-    auto it = st->cache.find(key);
-    if (it != st->cache.end()) {
-        st->lru.erase(it->second->lru);
-        st->lru.push_front(key);
-        it->second->lru = st->lru.begin();
-        *out = it->second.get();
-        return QS_OK;
-    }
-    std::unique_ptr<DevicePlan> dp(new DevicePlan());
+    if ((*out = cache_lookup(st, key)) != nullptr) return QS_OK;
+    Plan plan;
     std::string err;
-    qs_status s = (o.mode == QS_MODE_PERGATE) ? build_pergate_plan(st->n, gates, dp->host, err)
-                                              : build_fused_plan(st->n, batch, gates, o, dp->host, err);
+    qs_status s = (o.mode == QS_MODE_PERGATE) ? build_pergate_plan(st->n, gates, plan, err)
+                                              : build_fused_plan(st->n, batch, gates, o, plan, err);
     if (s != QS_OK) return fail(s, err);
-    s = upload_plan(st, *dp);
+    return cache_insert(st, key, std::move(plan), out);
+}
+
+// upload a host plan and add it to the state's plan cache (bounded LRU)
+qs_status cache_insert(qs_state *st, uint64_t key, Plan &&plan, DevicePlan **out) {
+    std::unique_ptr<DevicePlan> dp(new DevicePlan());
+    dp->host = std::move(plan);
+    qs_status s = upload_plan(st, *dp);
     if (s != QS_OK) {
         free_plan(st, dp.get());
         return s;
@@ -646,7 +660,7 @@ qs_status convert_terms(int n, const qs_pauli *terms, size_t n_terms, std::vecto
 // S[b][k] (complex) = sum_x conj(phi[x ^ x_k]) (-1)^popcount(x & z_k) psi[x]
 // for every term; results to host `S` (batch x n_terms x 2).
 qs_status overlaps(qs_state *st, const float2 *psi, const float2 *phi, int batch, const std::vector<TermIdx> &t,
-                   std::vector<double> &S) {
+                   std::vector<double> &S, long long bstride = 0) {
     const int nt = (int)t.size();
     S.assign((size_t)batch * nt * 2, 0.0);
     if (nt == 0) return QS_OK;
@@ -680,9 +694,11 @@ qs_status overlaps(qs_state *st, const float2 *psi, const float2 *phi, int batch
                             st->stream));
     for (size_t c = 0; c < chunks.size(); ++c) {
         ExpectArgs A;
+        std::memset(&A, 0, sizeof A);
         A.psi = psi;
         A.lam = phi;
         A.state_elems = st->elems;
+        A.bstride = bstride;
         A.batch = batch;
         A.xmask = chunk_x[c];
         A.n_terms = chunks[c].second;
@@ -854,6 +870,52 @@ qs_status qs_get_amplitudes(const qs_state *st, void *dst, int is_device) {
     return QS_OK;
 }
 
+namespace {
+// Upload and run a plan built outside the cache (per-item plans of the
+// adjoint sweep are used once); the device copies are freed in stream order.
+qs_status run_host_plan(qs_state *st, Plan &&plan, float2 *home, int batch) {
+    DevicePlan dp;
+    dp.host = std::move(plan);
+    qs_status s = upload_plan(st, dp);
+    if (s == QS_OK) {
+        if (dp.host.mode == QS_MODE_PERGATE) {
+            s = run_pergate(st, dp, home, batch);
+        } else {
+            if (plan_needs_scratch(dp.host)) s = ensure_scratch(st);
+            if (s == QS_OK) s = run_fused(st, dp, home, st->scratch ? st->scratch + (home - st->home) : nullptr, batch);
+        }
+    }
+    free_plan(st, &dp);
+    return s;
+}
+
+// Fused plans for many gate lists at once, on up to 16 host threads (the
+// planner keeps no shared state between calls).
+qs_status build_plans_parallel(int n, int batch, const std::vector<std::vector<RGate>> &lists, const qs_opts &o,
+                               std::vector<Plan> &out, std::string &err) {
+    out.assign(lists.size(), Plan());
+    std::vector<qs_status> st(lists.size(), QS_OK);
+    std::vector<std::string> errs(lists.size());
+    std::atomic<size_t> next(0);
+    auto work = [&]() {
+        for (size_t i; (i = next.fetch_add(1)) < lists.size();)
+            st[i] = build_fused_plan(n, batch, lists[i], o, out[i], errs[i]);
+    };
+    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const size_t nt = std::min<size_t>(hw, lists.size());
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < nt; ++t) pool.emplace_back(work);
+    work();
+    for (auto &th : pool) th.join();
+    for (size_t i = 0; i < lists.size(); ++i)
+        if (st[i] != QS_OK) {
+            err = errs[i];
+            return st[i];
+        }
+    return QS_OK;
+}
+}  // namespace
+
 qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, const double *params, int n_params,
                            const qs_opts *opts) {
     if (!st) return fail(QS_ERR_INVALID_ARG, "st == NULL");
@@ -870,6 +932,41 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, c
     }
     if (n_gates == 0) return QS_OK;
     if (!per_item) return apply_resolved(st, resolved[0], o, st->home, st->batch);
+    if (o.mode == QS_MODE_FUSED) {
+        // per-item plans: the ones not cached are built on host threads first
+        std::vector<uint64_t> keys(st->batch);
+        std::vector<std::vector<RGate>> missing;
+        std::vector<int> miss_item;
+        for (int bi = 0; bi < st->batch; ++bi) {
+            keys[bi] = plan_key(st->n, 1, resolved[bi], o);
+            if (!st->cache.count(keys[bi]) &&
+                std::find(keys.begin(), keys.begin() + bi, keys[bi]) == keys.begin() + bi) {
+                missing.push_back(resolved[bi]);
+                miss_item.push_back(bi);
+            }
+        }
+        std::vector<Plan> built;
+        std::string err;
+        qs_status s = build_plans_parallel(st->n, 1, missing, o, built, err);
+        if (s != QS_OK) return fail(s, err);
+        size_t next = 0;
+        for (int bi = 0; bi < st->batch; ++bi) {
+            DevicePlan *dp = cache_lookup(st, keys[bi]);
+            if (!dp) {
+                if (next >= built.size() || miss_item[next] != bi) return fail(QS_ERR_INTERNAL, "plan bookkeeping");
+                s = cache_insert(st, keys[bi], std::move(built[next++]), &dp);
+                if (s != QS_OK) return s;
+            }
+            float2 *home = st->home + (size_t)bi * st->elems;
+            if (plan_needs_scratch(dp->host)) {
+                s = ensure_scratch(st);
+                if (s != QS_OK) return s;
+            }
+            s = run_fused(st, *dp, home, st->scratch ? st->scratch + (home - st->home) : nullptr, 1);
+            if (s != QS_OK) return s;
+        }
+        return QS_OK;
+    }
     for (int bi = 0; bi < st->batch; ++bi) {
         qs_status s = apply_resolved(st, resolved[bi], o, st->home + (size_t)bi * st->elems, 1);
         if (s != QS_OK) return s;
@@ -897,6 +994,50 @@ qs_status qs_expect(qs_state *st, const qs_pauli *terms, size_t n_terms, double 
     return QS_OK;
 }
 
+namespace {
+// The inverse of a resolved gate as gates of the library, in application
+// order: 1q gates as their conjugate-transposed 2x2 (QS_U), angle gates with
+// the angle negated, ISWAP^dagger = ISWAP (Z (x) Z), the rest self-inverse.
+void invert_gate(const RGate &g, std::vector<RGate> &out) {
+    if (g.nw == 1) {
+        cd M[4];
+        gate_matrix(g, M);
+        RGate u = g;
+        u.kind = QS_U;
+        u.dense[0] = std::conj(M[0]);
+        u.dense[1] = std::conj(M[2]);
+        u.dense[2] = std::conj(M[1]);
+        u.dense[3] = std::conj(M[3]);
+        out.push_back(u);
+        return;
+    }
+    switch (g.kind) {
+        case QS_CRX: case QS_CRY: case QS_CRZ: case QS_CP: case QS_RZZ: case QS_RXX: case QS_RYY: {
+            RGate r = g;
+            r.p[0] = -g.p[0];
+            out.push_back(r);
+            return;
+        }
+        case QS_ISWAP: {
+            for (int w = 0; w < 2; ++w) {
+                RGate z;
+                z.kind = QS_Z;
+                z.nw = 1;
+                z.q[0] = g.q[w];
+                z.b[0] = g.b[w];
+                out.push_back(z);
+            }
+            out.push_back(g);
+            return;
+        }
+        default:   // CX, CY, CZ, CH, SWAP, CCX, CSWAP
+            out.push_back(g);
+            return;
+    }
+}
+}  // namespace
+
+
 qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const double *params, int n_params,
                   const qs_pauli *terms, size_t n_terms, double *energy, double *grad) {
     if (!st || !energy || !grad || (n_terms && !terms) || (n_gates && !gates))
@@ -918,68 +1059,255 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
     std::vector<TermIdx> t;
     qs_status s = convert_terms(st->n, terms, n_terms, t);
     if (s != QS_OK) return s;
-    // 1. forward: psi = U(theta)|0>
+    // 1. forward: psi = U(theta)|0>, one fused plan per item (built in parallel)
     QS_CUDA(launch_init_zero(st->home, st->elems, B, st->stream));
     qs_opts o = default_opts(nullptr);
-    for (int b = 0; b < B; ++b) {
-        s = apply_resolved(st, rg[b], o, st->home + (size_t)b * st->elems, 1);
-        if (s != QS_OK) return s;
+    {
+        std::vector<Plan> fwd;
+        std::string err;
+        s = build_plans_parallel(st->n, 1, rg, o, fwd, err);
+        if (s != QS_OK) return fail(s, err);
+        for (int b = 0; b < B; ++b) {
+            s = run_host_plan(st, std::move(fwd[b]), st->home + (size_t)b * st->elems, 1);
+            if (s != QS_OK) return s;
+        }
     }
     // 2. energy
     s = qs_expect(st, terms, n_terms, energy);
     if (s != QS_OK) return s;
-    // 3. lambda = H psi (needs a second state per item: the scratch buffer) and a
-    //    working copy of psi, so the caller's state keeps psi(theta)
-    size_t bytes = (size_t)st->elems * B * sizeof(float2);
-    float2 *work = nullptr, *lam = nullptr;
-    QS_CUDA(cudaMallocAsync((void **)&work, bytes, st->stream));
-    cudaError_t e = cudaMallocAsync((void **)&lam, bytes, st->stream);
-    if (e != cudaSuccess) {
-        cudaFreeAsync(work, st->stream);
-        return fail(QS_ERR_OOM, "qs_grad: no memory for the adjoint state");
-    }
+    // 3. the reverse sweep works on pairs (psi_b, lam_b) stored next to each
+    //    other, so that an item's pair is a batch of two states for the fused
+    //    executor; the caller's state keeps psi(theta)
+    const long long E = st->elems;
+    const size_t pair_bytes = (size_t)E * 2 * B * sizeof(float2);
+    float2 *W = nullptr;
+    if (cudaMallocAsync((void **)&W, pair_bytes, st->stream) != cudaSuccess)
+        return fail(QS_ERR_OOM, "qs_grad: no memory for the adjoint states");
+    qs_state *aux = nullptr;
     struct Guard {
         qs_state *st;
-        float2 *a, *b;
+        float2 *w;
+        qs_state **aux;
         ~Guard() {
-            cudaFreeAsync(a, st->stream);
-            cudaFreeAsync(b, st->stream);
+            if (*aux) qs_free(*aux);
+            cudaFreeAsync(w, st->stream);
         }
-    } guard{st, work, lam};
-    QS_CUDA(cudaMemcpyAsync(work, st->home, bytes, cudaMemcpyDeviceToDevice, st->stream));
+    } guard{st, W, &aux};
+    QS_CUDA(cudaMemcpy2DAsync(W, 2 * E * sizeof(float2), st->home, E * sizeof(float2), E * sizeof(float2), B,
+                              cudaMemcpyDeviceToDevice, st->stream));
     {
         std::vector<PauliDev> hp;
         for (auto &x : t) hp.push_back({x.coeff, x.x, x.z});
+        std::stable_sort(hp.begin(), hp.end(), [](const PauliDev &a, const PauliDev &b) { return a.x < b.x; });
         s = ensure_terms(st, std::max<size_t>(hp.size(), 1));
         if (s != QS_OK) return s;
-        if (!hp.empty())
+        if (!hp.empty()) {
             QS_CUDA(cudaMemcpyAsync(st->d_terms, hp.data(), hp.size() * sizeof(PauliDev), cudaMemcpyHostToDevice,
                                     st->stream));
-        QS_CUDA(cudaStreamSynchronize(st->stream));
-        if (!hp.empty()) {
             cudaEvent_t ev;
             prof_begin(st, &ev);
-            QS_CUDA(launch_apply_pauli_sum(work, lam, st->elems, B, st->d_terms, (int)hp.size(), st->stream));
-            prof_end(st, ev, "pauli_sum", 16.0 * (double)st->elems * B);
+            QS_CUDA(launch_apply_pauli_sum(W, W + E, E, B, st->d_terms, (int)hp.size(), st->stream, 2 * E));
+            prof_end(st, ev, "pauli_sum", 16.0 * (double)E * B);
+            QS_CUDA(cudaStreamSynchronize(st->stream));   // the host term array goes out of scope
         } else {
-            QS_CUDA(cudaMemsetAsync(lam, 0, bytes, st->stream));
+            QS_CUDA(cudaMemset2DAsync(W + E, 2 * E * sizeof(float2), 0, E * sizeof(float2), B, st->stream));
         }
     }
-    // 4. reverse sweep: per gate, gradient overlap then un-apply on psi and lambda
+    s = qs_wrap(W, st->n, 2 * B, st->stream, &aux);
+    if (s != QS_OK) return s;
     for (size_t i = 0; i < (size_t)B * n_params; ++i) grad[i] = 0.0;
-    std::vector<PgOp> ops(B);
-    PgOp *d_ops = nullptr;
-    QS_CUDA(cudaMallocAsync((void **)&d_ops, sizeof(PgOp) * B, st->stream));
-    struct Guard2 {
-        qs_state *st;
-        PgOp *p;
-        ~Guard2() { cudaFreeAsync(p, st->stream); }
-    } guard2{st, d_ops};
+
+    // 4. reverse sweep (Jones & Gacon 2020), a layer at a time.  A maximal run
+    //    of 1q gates is one layer: every parameterised gate in it has
+    //    dE/dtheta = Im<lam|V G V^dagger|psi> at the post-layer states, V the
+    //    later gates of the run on its wire (those on other wires commute
+    //    with G); V G V^dagger = c_x X + c_y Y + c_z Z (FP64, per item), so one
+    //    X / Y / Z overlap pass per 4 wires serves the whole layer.  The gates
+    //    between gradient points are un-applied with the fused executor:
+    //    per item (batch = the pair) when they carry parameters, otherwise
+    //    once for all pairs.  Parameterised 2q gates (RZZ, CP) take their own
+    //    overlap of generator terms.
+    qs_opts fo = default_opts(nullptr);
+    // Un-apply segments: the gates between two gradient points, latest first.
+    // Their plans (per item when the segment carries parameters, else one for
+    // all pairs) are built up front on host threads.
+    struct Segment {
+        std::vector<size_t> gates;
+        bool per_item = false;
+        size_t first_plan = 0;
+    };
+    std::vector<Segment> segs;
+    std::vector<size_t> pending;   // gates to un-apply, latest first
+    auto close_segment = [&]() {
+        if (pending.empty()) return;
+        Segment sg;
+        sg.gates.swap(pending);
+        for (size_t gi : sg.gates)
+            if (gates[gi].param_idx >= 0) sg.per_item = true;
+        segs.push_back(std::move(sg));
+    };
+    size_t next_seg = 0;
+    std::vector<Plan> seg_plans;
+    auto flush = [&]() -> qs_status {
+        if (pending.empty()) return QS_OK;
+        pending.clear();
+        const Segment &sg = segs[next_seg++];
+        if (!sg.per_item) return run_host_plan(aux, std::move(seg_plans[sg.first_plan]), W, 2 * B);
+        for (int b = 0; b < B; ++b) {
+            qs_status r = run_host_plan(aux, std::move(seg_plans[sg.first_plan + b]), W + (size_t)2 * b * E, 2);
+            if (r != QS_OK) return r;
+        }
+        return QS_OK;
+    };
+    // dry run of the sweep: the segments in execution order
     for (size_t gi = n_gates; gi-- > 0;) {
-        const qs_gate &g = gates[gi];
-        if (g.param_idx >= 0) {
-            // generator overlaps  G = X, Y, Z, ZZ on the gate's bits (CP: P11 = (1 - Za - Zb + ZaZb)/4)
-            const RGate &r0 = rg[0][gi];
+        if (rg[0][gi].nw == 1) {
+            size_t lo = gi;
+            while (lo > 0 && rg[0][lo - 1].nw == 1) --lo;
+            bool has_param = false;
+            for (size_t k = lo; k <= gi; ++k)
+                if (gates[k].param_idx >= 0) has_param = true;
+            if (has_param) close_segment();
+            for (size_t k = gi + 1; k-- > lo;) pending.push_back(k);
+            gi = lo;
+            continue;
+        }
+        if (gates[gi].param_idx >= 0) close_segment();
+        pending.push_back(gi);
+    }
+    pending.clear();   // the gates before the first gradient point are never un-applied
+    {
+        std::vector<std::vector<RGate>> lists;
+        for (Segment &sg : segs) {
+            sg.first_plan = lists.size();
+            for (int b = 0; b < (sg.per_item ? B : 1); ++b) {
+                std::vector<RGate> inv;
+                for (size_t gi : sg.gates) invert_gate(rg[b][gi], inv);
+                lists.push_back(std::move(inv));
+            }
+        }
+        // per-item segments run on a pair (batch 2), shared ones on all pairs
+        std::vector<std::vector<RGate>> l2, lB;
+        std::vector<size_t> i2, iB;
+        for (const Segment &sg : segs)
+            for (int b = 0; b < (sg.per_item ? B : 1); ++b) {
+                const size_t i = sg.first_plan + b;
+                if (sg.per_item) {
+                    i2.push_back(i);
+                    l2.push_back(lists[i]);
+                } else {
+                    iB.push_back(i);
+                    lB.push_back(lists[i]);
+                }
+            }
+        std::vector<Plan> p2, pB;
+        std::string err;
+        s = build_plans_parallel(st->n, 2, l2, fo, p2, err);
+        if (s == QS_OK) s = build_plans_parallel(st->n, 2 * B, lB, fo, pB, err);
+        if (s != QS_OK) return fail(s, err);
+        seg_plans.resize(lists.size());
+        for (size_t j = 0; j < i2.size(); ++j) seg_plans[i2[j]] = std::move(p2[j]);
+        for (size_t j = 0; j < iB.size(); ++j) seg_plans[iB[j]] = std::move(pB[j]);
+    }
+    struct XyzLaunch {
+        int k;
+        int gbit[kXyzGroup];
+        uint64_t zmask;
+    };
+    struct LayerRec {
+        std::vector<size_t> gates;          // the run, in circuit order
+        std::vector<XyzLaunch> launches;    // results at d_res[first + i]
+        size_t first;
+    };
+    std::vector<LayerRec> layers;
+    size_t n_launch = 0;
+    // first pass: plan the layers and their overlap launches
+    for (size_t gi = n_gates; gi-- > 0;) {
+        if (rg[0][gi].nw != 1) continue;
+        size_t lo = gi;
+        while (lo > 0 && rg[0][lo - 1].nw == 1) --lo;
+        LayerRec L;
+        uint64_t wires = 0;
+        for (size_t k = lo; k <= gi; ++k) {
+            L.gates.push_back(k);
+            if (gates[k].param_idx >= 0) wires |= 1ull << rg[0][k].b[0];
+        }
+        if (wires) {
+            std::vector<int> bits;
+            for (int q = 0; q < st->n; ++q)
+                if ((wires >> q) & 1) bits.push_back(q);
+            for (size_t c = 0; c < bits.size(); c += kXyzGroup) {
+                XyzLaunch x;
+                x.k = (int)std::min<size_t>(kXyzGroup, bits.size() - c);
+                uint64_t gm = 0;
+                for (int j = 0; j < x.k; ++j) {
+                    x.gbit[j] = bits[c + j];
+                    gm |= 1ull << bits[c + j];
+                }
+                x.zmask = c == 0 ? (wires & ~gm) : 0;
+                L.launches.push_back(x);
+            }
+            L.first = n_launch;
+            n_launch += L.launches.size();
+            layers.push_back(L);
+        }
+        gi = lo;
+    }
+    const int xgrid = xyz_grid(E, 1);   // enough blocks for every group size
+    double *d_res = nullptr;
+    if (n_launch) {
+        s = ensure_partial(st, (size_t)B * xgrid * kXyzSlots);
+        if (s != QS_OK) return s;
+        QS_CUDA(cudaMallocAsync((void **)&d_res, n_launch * B * kXyzSlots * sizeof(double), st->stream));
+    }
+    struct Guard3 {
+        qs_state *st;
+        double *p;
+        ~Guard3() {
+            if (p) cudaFreeAsync(p, st->stream);
+        }
+    } guard3{st, d_res};
+    size_t li = 0;
+    for (size_t gi = n_gates; gi-- > 0;) {
+        const RGate &r0 = rg[0][gi];
+        if (r0.nw == 1) {
+            size_t lo = gi;
+            while (lo > 0 && rg[0][lo - 1].nw == 1) --lo;
+            bool has_param = false;
+            for (size_t k = lo; k <= gi; ++k)
+                if (gates[k].param_idx >= 0) has_param = true;
+            if (has_param) {
+                s = flush();
+                if (s != QS_OK) return s;
+                const LayerRec &L = layers[li++];
+                for (size_t c = 0; c < L.launches.size(); ++c) {
+                    XyzArgs A;
+                    std::memset(&A, 0, sizeof A);
+                    A.psi = W;
+                    A.lam = W + E;
+                    A.elems = E;
+                    A.bstride = 2 * E;
+                    A.batch = B;
+                    A.k = L.launches[c].k;
+                    for (int j = 0; j < A.k; ++j) A.gbit[j] = L.launches[c].gbit[j];
+                    A.zmask = L.launches[c].zmask;
+                    A.partial = st->d_partial;
+                    A.grid = xgrid;
+                    cudaEvent_t ev;
+                    prof_begin(st, &ev);
+                    QS_CUDA(launch_xyz_overlaps(A, st->stream));
+                    prof_end(st, ev, "xyz_overlap", 16.0 * (double)E * B);
+                    QS_CUDA(launch_expect_finish(st->d_partial, d_res + (L.first + c) * B * kXyzSlots, B, xgrid,
+                                                 kXyzSlots / 2, st->stream));
+                }
+            }
+            for (size_t k = gi + 1; k-- > lo;) pending.push_back(k);
+            gi = lo;
+            continue;
+        }
+        if (gates[gi].param_idx >= 0) {   // RZZ / CP: generator overlap at the post-gate states
+            s = flush();
+            if (s != QS_OK) return s;
             std::vector<TermIdx> gt;
             auto term = [&](double c, uint64_t x, uint64_t z) {
                 TermIdx q;
@@ -989,84 +1317,95 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
                 q.ny = __builtin_popcountll(x & z) & 3;
                 gt.push_back(q);
             };
-            uint64_t ba = 1ull << r0.b[0], bb = r0.nw > 1 ? (1ull << r0.b[1]) : 0;
-            switch (g.kind) {
-                case QS_RX: term(1.0, ba, 0); break;
-                case QS_RY: term(1.0, ba, ba); break;
-                case QS_RZ: term(1.0, 0, ba); break;
-                case QS_RZZ: term(1.0, 0, ba | bb); break;
-                case QS_CP:
-                    term(0.25, 0, 0);
-                    term(-0.25, 0, ba);
-                    term(-0.25, 0, bb);
-                    term(0.25, 0, ba | bb);
-                    break;
+            const uint64_t ba = 1ull << r0.b[0], bb = 1ull << r0.b[1];
+            if (gates[gi].kind == QS_RZZ) {
+                term(1.0, 0, ba | bb);
+            } else {   // CP(t) = exp(i t P11), P11 = (1 - Za - Zb + ZaZb) / 4
+                term(0.25, 0, 0);
+                term(-0.25, 0, ba);
+                term(-0.25, 0, bb);
+                term(0.25, 0, ba | bb);
             }
             std::vector<double> S;
-            s = overlaps(st, work, lam, B, gt, S);
+            s = overlaps(st, W, W + E, B, gt, S, 2 * E);
             if (s != QS_OK) return s;
             for (int b = 0; b < B; ++b) {
-                double re_tot = 0.0, im_tot = 0.0;
+                double im_tot = 0.0;
                 for (size_t k = 0; k < gt.size(); ++k) {
                     double re = S[((size_t)b * gt.size() + k) * 2], im = S[((size_t)b * gt.size() + k) * 2 + 1];
                     times_i_pow(re, im, gt[k].ny);
-                    re_tot += gt[k].coeff * re;
                     im_tot += gt[k].coeff * im;
                 }
                 // R(t) = exp(-i t G/2): dE/dt = Im<lam|G|psi>;  CP(t) = exp(i t P11): dE/dt = -2 Im<lam|P11|psi>
-                double d = (g.kind == QS_CP) ? -2.0 * im_tot : im_tot;
-                grad[(size_t)b * n_params + g.param_idx] += d;
+                grad[(size_t)b * n_params + gates[gi].param_idx] += gates[gi].kind == QS_CP ? -2.0 * im_tot : im_tot;
             }
         }
-        // un-apply gate gi on both states (per-item matrices)
-        bool skip = false;
-        for (int b = 0; b < B; ++b) {
-            Plan tmp;
-            std::string err;
-            std::vector<RGate> one(1, rg[b][gi]);
-            build_pergate_plan(st->n, one, tmp, err);
-            if (tmp.pg.empty()) {
-                skip = true;
-                break;
-            }
-            PgOp op = tmp.pg[0];
-            // inverse: conjugate transpose / conjugate phases
-            if (op.kind == PG_U1) {
-                float2 m[4] = {op.m[0], op.m[1], op.m[2], op.m[3]};
-                op.m[0] = make_float2(m[0].x, -m[0].y);
-                op.m[1] = make_float2(m[2].x, -m[2].y);
-                op.m[2] = make_float2(m[1].x, -m[1].y);
-                op.m[3] = make_float2(m[3].x, -m[3].y);
-            } else if (op.kind == PG_U2) {
-                float2 m[16];
-                for (int e2 = 0; e2 < 16; ++e2) m[e2] = op.m[e2];
-                for (int r = 0; r < 4; ++r)
-                    for (int c = 0; c < 4; ++c) op.m[r * 4 + c] = make_float2(m[c * 4 + r].x, -m[c * 4 + r].y);
-            } else if (op.kind == PG_PHASE) {
-                for (int e2 = 0; e2 < 4; ++e2) op.m[e2].y = -op.m[e2].y;
-            }
-            ops[b] = op;
-        }
-        if (skip) continue;
-        QS_CUDA(cudaMemcpyAsync(d_ops, ops.data(), sizeof(PgOp) * B, cudaMemcpyHostToDevice, st->stream));
-        PgArgs A;
-        std::memset(&A, 0, sizeof A);
-        A.ops = d_ops;
-        A.op_stride = 1;
-        A.psi[0] = work;
-        A.psi[1] = lam;
-        A.n_arrays = 2;
-        A.state_elems = st->elems;
-        A.batch = B;
-        A.n = st->n;
-        pg_fixed(ops[0], st->n, A);
-        cudaEvent_t ev;
-        prof_begin(st, &ev);
-        QS_CUDA(launch_pergate(A, st->stream));
-        prof_end(st, ev, "adjoint_unapply", 2.0 * pg_bytes(ops[0], st->n) * B);
-        // the host op array is reused next iteration: wait for the copy
-        QS_CUDA(cudaStreamSynchronize(st->stream));
+        pending.push_back(gi);
     }
+    // 5. gradients of the 1q layers from their X / Y / Z overlaps
+    if (n_launch) {
+        std::vector<double> res(n_launch * B * kXyzSlots);
+        QS_CUDA(cudaMemcpyAsync(res.data(), d_res, res.size() * sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+        QS_CUDA(cudaStreamSynchronize(st->stream));
+        for (const LayerRec &L : layers) {
+            for (int b = 0; b < B; ++b) {
+                // Im<X_q>, Im<Y_q>, Im<Z_q> of the layer's wires for item b
+                std::map<int, std::array<double, 3>> ov;
+                double total = 0.0;
+                std::map<int, double> sq;
+                for (size_t c = 0; c < L.launches.size(); ++c) {
+                    const double *r = &res[((L.first + c) * B + b) * kXyzSlots];
+                    const XyzLaunch &x = L.launches[c];
+                    if (c == 0) total = r[3 * kXyzGroup + kXyzZBits];
+                    for (int j = 0; j < x.k; ++j) {
+                        ov[x.gbit[j]][0] = r[j];
+                        ov[x.gbit[j]][1] = r[kXyzGroup + j];
+                        sq[x.gbit[j]] = r[2 * kXyzGroup + j];
+                    }
+                    for (int q = 0; q < kXyzZBits; ++q)
+                        if ((x.zmask >> q) & 1) sq[q] = r[3 * kXyzGroup + q];
+                }
+                for (auto &kv : sq) ov[kv.first][2] = total - 2.0 * kv.second;
+                for (size_t a = 0; a < L.gates.size(); ++a) {
+                    const size_t gi = L.gates[a];
+                    if (gates[gi].param_idx < 0) continue;
+                    const RGate &g = rg[b][gi];
+                    // V = product of the later gates of the run on this wire
+                    cd V[4] = {1, 0, 0, 1};
+                    for (size_t c2 = a + 1; c2 < L.gates.size(); ++c2) {
+                        const RGate &h = rg[b][L.gates[c2]];
+                        if (h.b[0] != g.b[0]) continue;
+                        cd M[4], T[4];
+                        gate_matrix(h, M);
+                        T[0] = M[0] * V[0] + M[1] * V[2];
+                        T[1] = M[0] * V[1] + M[1] * V[3];
+                        T[2] = M[2] * V[0] + M[3] * V[2];
+                        T[3] = M[2] * V[1] + M[3] * V[3];
+                        for (int e2 = 0; e2 < 4; ++e2) V[e2] = T[e2];
+                    }
+                    cd Gm[4];
+                    switch (g.kind) {
+                        case QS_RX: Gm[0] = 0; Gm[1] = 1; Gm[2] = 1; Gm[3] = 0; break;
+                        case QS_RY: Gm[0] = 0; Gm[1] = cd(0, -1); Gm[2] = cd(0, 1); Gm[3] = 0; break;
+                        default: Gm[0] = 1; Gm[1] = 0; Gm[2] = 0; Gm[3] = -1; break;
+                    }
+                    // Ge = V G V^dagger
+                    cd VG[4], Ge[4];
+                    VG[0] = V[0] * Gm[0] + V[1] * Gm[2];
+                    VG[1] = V[0] * Gm[1] + V[1] * Gm[3];
+                    VG[2] = V[2] * Gm[0] + V[3] * Gm[2];
+                    VG[3] = V[2] * Gm[1] + V[3] * Gm[3];
+                    Ge[0] = VG[0] * std::conj(V[0]) + VG[1] * std::conj(V[1]);
+                    Ge[2] = VG[2] * std::conj(V[0]) + VG[3] * std::conj(V[1]);
+                    const double cx = Ge[2].real(), cy = Ge[2].imag(), cz = Ge[0].real();
+                    const auto &o3 = ov[g.b[0]];
+                    grad[(size_t)b * n_params + gates[gi].param_idx] += cx * o3[0] + cy * o3[1] + cz * o3[2];
+                }
+            }
+        }
+    }
+    s = check_err_word(aux);
+    if (s != QS_OK) return s;
     return check_err_word(st);
 }
 

@@ -100,6 +100,7 @@ struct ExpectArgs {
     const float2 *psi;         // states
     const float2 *lam;         // second states (NULL: <psi|P|psi>)
     long long state_elems;
+    long long bstride;         // elements between batch items (0: state_elems)
     int batch;
     uint64_t xmask;            // common x mask of the group
     int n_terms;
@@ -112,9 +113,30 @@ cudaError_t launch_expect_group(const ExpectArgs &A, cudaStream_t st);
 cudaError_t launch_expect_finish(const double *partial, double *out, int batch, int grid, int n_terms,
                                  cudaStream_t st);
 
-// lam = sum_k coeff_k P_k psi  (one launch over all terms)
+// lam = sum_k coeff_k P_k psi  (one launch over all terms; terms sorted by x
+// mask share one load per amplitude)
 cudaError_t launch_apply_pauli_sum(const float2 *psi, float2 *lam, long long state_elems, int batch,
-                                   const PauliDev *terms, int n_terms, cudaStream_t st);
+                                   const PauliDev *terms, int n_terms, cudaStream_t st, long long bstride = 0);
+
+// Adjoint-method overlaps of one state pair (psi_b, lam_b) per batch item:
+// for the k <= 4 group bits g_j, Im<lam|X_j|psi> and Im<lam|Y_j|psi> (pairs in
+// registers) and S_j = sum_{x_gj = 1} Im(conj(lam_x) psi_x); for the bits of
+// zmask (outside the group) S_q likewise; and the total sum_x Im(conj(lam_x)
+// psi_x), so that Im<lam|Z_q|psi> = total - 2 S_q.
+constexpr int kXyzGroup = 4;
+constexpr int kXyzZBits = 34;
+constexpr int kXyzSlots = 3 * kXyzGroup + kXyzZBits + 2;   // 48: [ImX | ImY | S_g | S_q | total | pad]
+struct XyzArgs {
+    const float2 *psi, *lam;   // item b at psi + b * bstride, lam + b * bstride
+    long long elems, bstride;
+    int batch, k;
+    int gbit[kXyzGroup];       // ascending index bits
+    uint64_t zmask;            // bits outside the group whose S_q is wanted
+    double *partial;           // [batch][grid][kXyzSlots]
+    int grid;
+};
+int xyz_grid(long long elems, int k);   // minimum blocks per item
+cudaError_t launch_xyz_overlaps(const XyzArgs &A, cudaStream_t st);
 
 cudaError_t launch_init_zero(float2 *psi, long long state_elems, int batch, cudaStream_t st);
 

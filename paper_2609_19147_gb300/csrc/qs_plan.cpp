@@ -1073,7 +1073,7 @@ void choose_item_bits(const TilePass &tp, Sweep &sw) {
     const int nl = std::min(5, k);
     const int words_per = sw.vec ? 2 : 1;
     // memoised: the answer depends only on the candidate bits' offsets
-    static std::map<std::vector<int>, std::vector<int>> memo;
+    thread_local std::map<std::vector<int>, std::vector<int>> memo;
     std::vector<int> key;
     key.push_back(words_per);
     for (int i = 0; i < k; ++i) key.push_back(tp.smem_contrib[cand[i]]);
@@ -1316,7 +1316,7 @@ struct PassBuilder {
             int best = 1 << 30, ba = 0, bb = 1;
             uint32_t bmask = (1u << m) - 1;
             // memoised on the bits' shared-memory offsets
-            static std::map<std::vector<int>, std::array<int, 3>> memo;
+            thread_local std::map<std::vector<int>, std::array<int, 3>> memo;
             std::vector<int> key;
             for (int e = 0; e < 5; ++e) key.push_back(tp.smem_contrib[G[e]]);
             for (int i = 0; i < nc; ++i) key.push_back(tp.smem_contrib[cols[i]]);
