@@ -9,7 +9,11 @@ Strang steps, J = 1, h_i ~ U[0.5, 1.5] seed 3, dt = 0.05; 8800 gates).  The
 steps.  The metric is seconds per step (QFT + TFIM circuit pair), lower is
 better; the JSON line also carries each circuit's time, the plain per-gate GPU
 path's time for the same circuits, the HBM roofline of the dominant kernel,
-the oracle's CPU baseline and an end-to-end (host buffer) figure.
+the oracle's CPU baseline and an end-to-end (host buffer) figure.  Outside
+the timed step it reports the metric's other rows: adjoint gradients per
+second on the VQE config (n = 24, 576 parameters, batch 32), the dense
+5-qubit-block precisions on 30q TFIM (10 Strang steps), and batched QAOA
+instances per second (512 graphs x 8 angle sets).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -66,7 +70,7 @@ def kernel_traffic():
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    src = open(os.path.join(ROOT, "paper_2609_19147_gb300", "csrc", "k_tile.cu"), "rb").read()
+    src = open(os.path.join(ROOT, "paper_2609_19147_gb300", "csrc", "k_tile_impl.cuh"), "rb").read()
     if d.get("k_tile_sha1") != hashlib.sha1(src).hexdigest():
         return None
     return d.get("tile_pass_bytes_per_launch_30q")
@@ -194,6 +198,74 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def _time_cuda(torch, stream, fn, reps=1):
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps
+
+
+def extra_rows(qs, torch, st, tfim, stream):
+    """grads/s of the adjoint config, the dense-block precisions on 30q TFIM
+    and the batched QAOA config; each after one untimed call."""
+    out = {}
+    n = N_QUBITS
+    # adjoint gradients: n = 24, 12 layers of RY.RZ + CNOT ring, 576 params, batch 32
+    gn, gl_layers, gb = 24, 12, 32
+    gl = W.vqe_ansatz_gates(gn, gl_layers)
+    theta = W.vqe_params(gn, gl_layers, gb, 6)
+    terms = W.tfim_paulis(gn, 1.0, 1.0)
+    gs = qs.State(gn, batch=gb)
+    cg = qs.CGates(gl)
+    gs.grad(cg, theta, terms)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gs.grad(cg, theta, terms)
+    torch.cuda.synchronize()
+    gt = time.perf_counter() - t0
+    gs.close()
+    out["grads"] = {"config": "VQE n=24, 12 layers RY.RZ + CNOT ring, 576 params ~U[0,2pi) seed 6, batch 32, "
+                              "H = TFIM J=1 h=1 (47 terms)", "s_per_batch": gt, "grads_per_s": gb / gt,
+                    "param_grads_per_s": gb * 2 * gn * gl_layers / gt}
+    # dense 5-qubit blocks on 30q TFIM (10 Strang steps; 7 blocks per step)
+    steps10 = tfim[:10 * (len(tfim) // TFIM_STEPS)]
+    c10 = qs.CGates(steps10)
+    dense = {"workload": "30q TFIM, first 10 of the 100 Strang steps, from |0..0>"}
+    ref = None
+    for prec in (None, "fp32", "tf32x3", "bf16"):
+        st.zero()
+        st.apply(c10, dense=prec)
+        torch.cuda.synchronize()
+        st.zero()
+        t = _time_cuda(torch, stream, lambda: st.apply(c10, dense=prec))
+        txt, passes = qs.plan_describe(n, c10, dense=prec)
+        blocks = sum(int(x.split("DENSE=")[1].split()[0]) for x in txt.splitlines() if "DENSE=" in x)
+        row = {"s": t, "passes": passes, "blocks": blocks}
+        if prec is None:
+            ref = st.tensor.clone()
+        else:
+            # 8 * 32 real flop per amplitude per 5-qubit block (U X, 32 x 32 complex)
+            row["dense_tflops_algorithmic"] = blocks * 256.0 * (1 << n) / t / 1e12
+            d = torch.linalg.vector_norm((st.tensor - ref).view(torch.complex64)).item()
+            row["rel_l2_vs_structured"] = d / torch.linalg.vector_norm(ref).item()
+        dense[str(prec) if prec else "structured"] = row
+    del ref
+    out["dense"] = dense
+    # batched QAOA MaxCut: 512 3-regular graphs, n in {14..24}, p = 4, 8 angle sets
+    insts = W.qaoa_batch(5)
+    qs.qaoa_maxcut(insts[:16])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cut = qs.qaoa_maxcut(insts)
+    qt = time.perf_counter() - t0
+    out["qaoa"] = {"config": "512 random 3-regular graphs (seed 5), n ~ U{14,...,24} even, p=4, 8 angle sets",
+                   "instances": int(cut.size), "s": qt, "items_per_s": cut.size / qt}
+    return out
+
+
 def run_gpu(args):
     import torch
     import paper_2609_19147_gb300 as qs
@@ -304,6 +376,11 @@ def run_gpu(args):
         e2e = {"value": es, "unit": "s/step (QFT+TFIM 30q)", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": 2 * nbytes}
 
+    # the other rows of the metric, reported beside the step (not in `value`)
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        extra = extra_rows(qs, torch, st, tfim, stream)
+
     if rank != 0:
         st.close()
         if dist is not None:
@@ -342,6 +419,7 @@ def run_gpu(args):
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
     st.close()
     if dist is not None:
@@ -358,6 +436,7 @@ def main():
     ap.add_argument("--no-pergate", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the grads / dense / QAOA rows")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
