@@ -509,6 +509,34 @@ __device__ __forceinline__ void apply_diag(const SweepCtx &c, const MicroOp &op,
     }
 }
 
+// MK_DIAGQ: the diagonal's tables at the item's base index (group bits 0),
+// times Q[j] for the group bits' own terms, times the couplings of each set
+// group bit to the other index bits (products built by doubling over the
+// group bits: two complex multiplies per amplitude)
+template <int R>
+__device__ __forceinline__ void apply_diagq(const SweepCtx &c, const MicroOp &op, uint64_t gbase,
+                                            float2 (&a)[1 << R]) {
+    const DiagDesc &d = c.diags[op.cst];
+    float2 z[1 << R];
+    z[0] = d.pad0 ? make_float2(d.gph_re, d.gph_im) : make_float2(1.f, 0.f);
+    z[0] = diag_part(d, gbase, c.cs, ~0u, ~0u, z[0]);
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+        float2 e = make_float2(1.f, 0.f);
+        const int cnt = (int)((op.cmask >> (6 * m)) & 63);
+        const float2 *ent = c.cs + op.lo + 2 * m * kMaxCouple;
+        for (int k = 0; k < cnt; ++k) {
+            const int b = __float_as_int(ent[2 * k].x);
+            if ((gbase >> b) & 1) e = cmul(e, ent[2 * k + 1]);
+        }
+#pragma unroll
+        for (int j = 0; j < (1 << m); ++j) z[j | (1 << m)] = cmul(z[j], e);
+    }
+    const float2 *q = c.cs + op.p;
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) a[j] = cmul(a[j], cmul(z[j], q[j]));
+}
+
 // Kernel op sets: KS_ALL compiles every micro-op kind; KS_LAYER only those of
 // 1q-layer and diagonal passes (Trotter / QAOA / random-layer circuits),
 // which keeps the code small and the register allocation tight.
@@ -559,6 +587,7 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
                     case MK_H: disp_h<R>(op.a, a); break;
                     case MK_U1: disp_u1<R>(op.a, a, c.cs + op.cst, op.cmask, op.cval, gbase(), G); break;
                     case MK_DIAG: apply_diag<R>(c, op, gbase(), G, a); break;
+                    case MK_DIAGQ: apply_diagq<R>(c, op, gbase(), a); break;
                     default: break;
                 }
             } else {
@@ -600,6 +629,9 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
                         break;
                     case MK_DIAG:
                         apply_diag<R>(c, op, gbase(), G, a);
+                        break;
+                    case MK_DIAGQ:
+                        apply_diagq<R>(c, op, gbase(), a);
                         break;
                     default:
                         break;

@@ -392,9 +392,10 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     A.kset = 1;
     for (int k = 0; k < tp.n_micro; ++k) {
         const MicroOp &mo = tp.micro[k];
-        if (mo.kind == MK_DIAG || mo.kind == MK_QFT || mo.kind == MK_QFTL || mo.cmask) A.needs_gidx = 1;
+        if (mo.kind == MK_DIAG || mo.kind == MK_DIAGQ || mo.kind == MK_QFT || mo.kind == MK_QFTL || mo.cmask)
+            A.needs_gidx = 1;
         if (!(mo.kind == MK_LAYER || mo.kind == MK_RXC || mo.kind == MK_U1R || mo.kind == MK_H || mo.kind == MK_U1 ||
-              mo.kind == MK_DIAG))
+              mo.kind == MK_DIAG || mo.kind == MK_DIAGQ))
             A.kset = 0;
     }
     if (A.dense && (tp.R != 5 || A.ctas_per_sm != 1)) return fail(QS_ERR_INTERNAL, "dense pass without 5-bit groups");

@@ -80,7 +80,13 @@ enum MicroKind : int32_t {
     MK_QFTL = 8,  // QFT stages (ladders down to bit 0) on the group bits in mask b,
                   // applied from the highest group bit down; p of bit m = (p >> 6m) & 63
                   // (p is a packed 64-bit field: use cmask); group table of bit m at cst + m * 2^R
+    MK_DIAGQ = 9, // diagonal factored per sweep: the tables of diag cst at the item's base
+                  // index (group bits 0), times Q[j] (2^R entries at p: the group bits' own
+                  // terms), times prod over set group bits m of the couplings of bit m to
+                  // other bits: (cmask >> 6m) & 63 entries at lo + 2 m kMaxCouple, each a
+                  // pair (bit index as int bits, exp(i beta)) applied where that bit is set
 };
+constexpr int kMaxCouple = 16;
 
 // item-address tables per sweep (shared memory): item bits 0-4, 5-9, 10-13
 constexpr int kItemTab = 32 + 32 + 16;

@@ -1497,6 +1497,7 @@ struct PassBuilder {
                     cst.insert(cst.end(), dp->tables[k].begin(), dp->tables[k].end());
                     int di = count_diags++;
                     tp.diags[di] = dd;
+                    diag_src[di] = (dp->descs.size() == 1 && dd.n_tw == 0) ? &f.diag : nullptr;
                     MicroOp mo;
                     std::memset(&mo, 0, sizeof mo);
                     mo.kind = MK_DIAG;
@@ -1510,6 +1511,67 @@ struct PassBuilder {
         }
     }
     int count_diags = 0;
+    const Diag *diag_src[kMaxDiag] = {nullptr, nullptr, nullptr, nullptr};
+    // A diagonal whose sweep group spans more than two slice tables (or a LUT
+    // group) would take the per-amplitude general path; factor it instead as
+    // (tables at group bits 0) x Q(group bits) x couplings(group bit, other bit).
+    bool to_diagq(MicroOp &mo, const Sweep &sw) {
+        const Diag *dg = diag_src[mo.cst];
+        if (!dg) return false;
+        int gb[kMaxGroup];
+        uint64_t gm = 0;
+        for (int m = 0; m < sw.r; ++m) {
+            gb[m] = __builtin_ctzll(glob_of_local(tp, sw.gbit[m]));
+            gm |= 1ull << gb[m];
+        }
+        std::vector<std::vector<std::pair<int, double>>> cpl(sw.r);
+        for (auto &kv : dg->pairs) {
+            const int b0 = kv.first.first, b1 = kv.first.second;
+            const bool i0 = (gm >> b0) & 1, i1 = (gm >> b1) & 1;
+            if (i0 == i1) continue;
+            const int gbit = i0 ? b0 : b1, other = i0 ? b1 : b0;
+            for (int m = 0; m < sw.r; ++m)
+                if (gb[m] == gbit) cpl[m].push_back({other, kv.second});
+        }
+        for (int m = 0; m < sw.r; ++m)
+            if ((int)cpl[m].size() > kMaxCouple) return false;
+        const int qoff = (int)cst.size();
+        for (int j = 0; j < (1 << sw.r); ++j) {
+            double ph = 0.0;
+            for (int m = 0; m < sw.r; ++m) {
+                if (!((j >> m) & 1)) continue;
+                auto it = dg->a.find(gb[m]);
+                if (it != dg->a.end()) ph += it->second;
+                for (int m2 = m + 1; m2 < sw.r; ++m2) {
+                    if (!((j >> m2) & 1)) continue;
+                    auto pt = dg->pairs.find({std::min(gb[m], gb[m2]), std::max(gb[m], gb[m2])});
+                    if (pt != dg->pairs.end()) ph += pt->second;
+                }
+            }
+            cst.push_back(cexp_f(ph));
+        }
+        const int coff = (int)cst.size();
+        uint64_t counts = 0;
+        for (int m = 0; m < sw.r; ++m) {
+            for (int e = 0; e < kMaxCouple; ++e) {
+                float2 idx{0.f, 0.f}, w{1.f, 0.f};
+                if (e < (int)cpl[m].size()) {
+                    const int b = cpl[m][e].first;
+                    std::memcpy(&idx.x, &b, 4);
+                    w = cexp_f(cpl[m][e].second);
+                }
+                cst.push_back(idx);
+                cst.push_back(w);
+            }
+            counts |= (uint64_t)cpl[m].size() << (6 * m);
+        }
+        mo.kind = MK_DIAGQ;
+        mo.p = qoff;
+        mo.lo = coff;
+        mo.cmask = counts;
+        mo.cval = 0;
+        return true;
+    }
     void finalize() {
         close_sweep();
         // convert tile-local bit references to group indices, fill QFT
@@ -1536,6 +1598,10 @@ struct PassBuilder {
                     }
                     mo.a = (int)ds;
                     mo.b = (int)dg;
+                    const int cap = dprec ? kMaxConstDense : kMaxConst;
+                    if ((dg != 0 || __builtin_popcount(ds) > 2) &&
+                        (int)cst.size() + (1 << sw.r) + 2 * kMaxCouple * sw.r <= cap)
+                        to_diagq(mo, sw);
                     continue;
                 }
                 int ga = -1, gb = -1;
@@ -2041,6 +2107,7 @@ std::string Plan::describe() const {
                 const MicroOp &mo = t.micro[k];
                 if (mo.kind == MK_LAYER) cnt[mo.a] += __builtin_popcount((unsigned)mo.b);
                 else if (mo.kind == MK_QFTL) cnt[MK_QFT] += __builtin_popcount((unsigned)mo.b);
+                else if (mo.kind == MK_DIAGQ) cnt[MK_DIAG]++;
                 else cnt[mo.kind]++;
             }
             os << "TILE T=" << t.T << " L=" << t.L << " hb=[";
@@ -2048,12 +2115,15 @@ std::string Plan::describe() const {
             os << "] tma=" << (hp.tma.ok ? 1 : 0) << " sweeps=" << t.n_sweeps
                << " U1=" << cnt[MK_U1] + cnt[MK_H] + cnt[MK_RXC] + cnt[MK_U1R] << " U2=" << cnt[MK_U2]
                << " DIAG=" << cnt[MK_DIAG] << " QFT=" << cnt[MK_QFT];
-            int nd = 0, slow = 0;
+            int nd = 0, slow = 0, fq = 0;
             for (int k = 0; k < t.n_sweeps; ++k) nd += t.sweeps[k].dense ? 1 : 0;
-            for (int k = 0; k < t.n_micro; ++k)
+            for (int k = 0; k < t.n_micro; ++k) {
                 if (t.micro[k].kind == MK_DIAG && (t.micro[k].b != 0 || __builtin_popcount((unsigned)t.micro[k].a) > 2))
                     slow++;
+                if (t.micro[k].kind == MK_DIAGQ) fq++;
+            }
             if (nd) os << " DENSE=" << nd;
+            if (fq) os << " DIAGQ=" << fq;
             if (slow) os << " DIAG_GENERAL=" << slow;
             os << " consts=" << t.n_const << "\n";
         } else if (hp.type == HostPass::PERM) {

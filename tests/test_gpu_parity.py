@@ -278,3 +278,23 @@ def test_tfim30_full_size_properties():
     st.close()
     assert abs(norm - 1) < 1e-5
     assert diff <= 2e-5   # both paths in complex64; the stated amplitude tolerance
+
+
+@pytest.mark.parametrize("n,degree", [(16, 3), (22, 6), (22, 14)])
+def test_factored_diagonals_in_layer_sweeps(n, degree):
+    # random-angle ZZ couplings of the given degree interleaved with RX / RY
+    # layers on scattered qubits: the diagonals' register groups span several
+    # slice tables, which the planner factors per sweep (MK_DIAGQ) while each
+    # group bit has at most 16 couplings, and keeps the general path above
+    rng = np.random.default_rng(100 + n + degree)
+    gl = []
+    for layer in range(3):
+        for i in range(n):
+            for j in rng.choice(n, size=degree, replace=False):
+                if i < j:
+                    gl.append(W.Gate("RZZ", (i, int(j)), (float(rng.uniform(0, 2 * np.pi)),)))
+        for q in rng.choice(n, size=n // 2, replace=False):
+            gl.append(W.Gate("RX" if layer % 2 else "RY", (int(q),), (float(rng.uniform(0, 6)),)))
+    psi0 = W.random_state(n, 9)
+    _assert_close(_run(n, gl, psi0), _ref(n, gl, psi0))
+    _assert_close(_run(n, gl, psi0, dense="tf32x3"), _ref(n, gl, psi0))
