@@ -544,10 +544,59 @@ static void conjugate_rx_runs(std::vector<FOp> &ops) {
         }
 }
 
+// Basis-conjugated Pauli-pair layers (Sec. 5.1): a run of >= 2 consecutive
+// RXX gates commutes term by term, so it equals H^{(x)S} exp(-i sum t/2 Z Z)
+// H^{(x)S} over the run's qubits S; a run of RYY gates the same with V = S H
+// (V Z V^dagger = Y): S^dagger then H before the ZZ phases, H then S after.
+// The ZZ phases then form one diagonal run and the outer 1q gates merge with
+// their neighbours (H H pairs between consecutive layers cancel symbolically).
+static void conjugate_pauli_pair_runs(int n, const std::vector<RGate> &in, std::vector<RGate> &out) {
+    out.clear();
+    auto one = [&](int kind, int q) {
+        RGate g;
+        g.kind = kind;
+        g.nw = 1;
+        g.q[0] = q;
+        g.b[0] = n - 1 - q;
+        return g;
+    };
+    for (size_t i = 0; i < in.size();) {
+        const int k = in[i].kind;
+        size_t j = i;
+        if (k == QS_RXX || k == QS_RYY)
+            while (j < in.size() && in[j].kind == k) ++j;
+        if (j - i < 2) {
+            out.push_back(in[i]);
+            ++i;
+            continue;
+        }
+        std::vector<int> qs;
+        for (size_t t = i; t < j; ++t)
+            for (int w = 0; w < 2; ++w)
+                if (std::find(qs.begin(), qs.end(), in[t].q[w]) == qs.end()) qs.push_back(in[t].q[w]);
+        for (int q : qs) {
+            if (k == QS_RYY) out.push_back(one(QS_SDG, q));
+            out.push_back(one(QS_H, q));
+        }
+        for (size_t t = i; t < j; ++t) {
+            RGate z = in[t];
+            z.kind = QS_RZZ;
+            out.push_back(z);
+        }
+        for (int q : qs) {
+            out.push_back(one(QS_H, q));
+            if (k == QS_RYY) out.push_back(one(QS_S, q));
+        }
+        i = j;
+    }
+}
+
 void detect(int n, const std::vector<RGate> &gates, std::vector<FOp> &ops) {
+    std::vector<RGate> conj;
+    conjugate_pauli_pair_runs(n, gates, conj);
     std::vector<FOp> raw;
     Detector det(n, raw);
-    for (const RGate &g : gates) det.gate(g);
+    for (const RGate &g : conj) det.gate(g);
     det.finish();
 
     // QFT stages

@@ -185,3 +185,16 @@ def test_dense_options_validated(qs):
     o = qs._opts()
     o.dense_prec = 9
     assert qs._lib.qs_plan_describe(8, cg.arr, cg.n, ctypes.byref(o), None, 0, None) == qs.QS_ERR_INVALID_ARG
+
+
+def test_pauli_pair_layers_are_basis_conjugated(qs):
+    # a run of RXX (or RYY) gates becomes 1q layers around one ZZ diagonal:
+    # no 4x4 ops remain; a lone RXX stays a 4x4 op
+    n = 16
+    for kind in ("RXX", "RYY"):
+        gl = [W.Gate(kind, (i, i + 1), (0.2 + 0.01 * i,)) for i in range(n - 1)]
+        text, p = _passes(qs, n, gl)
+        assert sum(int(m) for m in re.findall(r"U2=(\d+)", text)) == 0, text
+        assert sum(int(m) for m in re.findall(r"DIAG=(\d+)", text)) >= 1
+    text, _ = _passes(qs, n, [W.Gate("RXX", (3, 9), (0.4,))])
+    assert sum(int(m) for m in re.findall(r"U2=(\d+)", text)) == 1

@@ -298,3 +298,20 @@ def test_factored_diagonals_in_layer_sweeps(n, degree):
     psi0 = W.random_state(n, 9)
     _assert_close(_run(n, gl, psi0), _ref(n, gl, psi0))
     _assert_close(_run(n, gl, psi0, dense="tf32x3"), _ref(n, gl, psi0))
+
+
+@pytest.mark.parametrize("n", [9, 18])
+def test_heisenberg_layers_basis_conjugated(n):
+    # XXZ / random-field Heisenberg steps as same-family layers: each RXX run
+    # becomes H (x) ZZ-phases (x) H and each RYY run (SH) ZZ (SH)^dagger
+    # (Sec. 5.1 basis conjugation); plus single RXX / RYY gates that stay 4x4
+    rng = np.random.default_rng(40 + n)
+    gl = []
+    for step in range(4):
+        gl += [W.Gate("RXX", (i, i + 1), (float(rng.uniform(-1, 1)),)) for i in range(n - 1)]
+        gl += [W.Gate("RYY", (i, i + 1), (float(rng.uniform(-1, 1)),)) for i in range(n - 1)]
+        gl += [W.Gate("RZZ", (i, i + 1), (float(rng.uniform(-1, 1)),)) for i in range(n - 1)]
+        gl += [W.Gate("RZ", (q,), (float(rng.uniform(-1, 1)),)) for q in range(n)]
+        gl += [W.Gate("RXX", (0, n - 1), (0.3,)), W.Gate("H", (n // 2,)), W.Gate("RYY", (1, n - 2), (0.7,))]
+    psi0 = W.random_state(n, 41)
+    _assert_close(_run(n, gl, psi0), _ref(n, gl, psi0))
