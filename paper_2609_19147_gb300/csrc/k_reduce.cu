@@ -278,4 +278,277 @@ cudaError_t launch_xyz_overlaps(const XyzArgs &A, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// X / Y / Z overlaps over shared-memory tiles: up to 12 pair bits per read of
+// the two states (the register-group kernel above takes 4).  A tile holds
+// rows of 16 amplitudes (the low index bits) for 2^H combinations of the high
+// tile bits; 16-byte chunks of a row are XOR-swizzled with the row's low 3
+// bits.  Three sweeps give every thread a 16-amplitude group over 4 tile bits
+// (low bits 0-3, high bits 0-3, high bits 4-7); the X / Y sums of a pair are
+// 4 FMAs each, chained per thread in FP32 and reduced in FP64 per CTA.
+// ---------------------------------------------------------------------------
+constexpr int kXyzTThreads = 128;
+
+__device__ __forceinline__ int xt_off(int row, int col) {   // float2 offset of (row, amplitude col)
+    return (row << 4) | ((((col >> 1) ^ row) & 7) << 1) | (col & 1);
+}
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Tiles are double-buffered: the copies of tile k+1 are in flight while tile k
+// is reduced.  Every sum stays in FP32 registers of its thread across the
+// CTA's tiles (a thread adds a few thousand terms); FP64 starts at the block
+// reduction (FP64 arithmetic is slow on this part, FP64 atomics slower).
+template <int H>
+__global__ void __launch_bounds__(kXyzTThreads) xyz_tile_kernel(const XyzTileArgs A) {
+    constexpr int T = 4 + H, E = 1 << T, ROWS = 1 << H;
+    extern __shared__ __align__(16) float2 xts[];   // [2 buffers][psi, lam][E]
+    const int b = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float2 *psi = A.psi + (long long)b * A.bstride;
+    const float2 *lam = A.lam + (long long)b * A.bstride;
+    const long long n_tiles = A.elems >> T;
+    int outer[kXyzZBits];
+    int n_outer = 0;
+    {
+        uint64_t tb = 15ull;
+        for (int k = 0; k < H; ++k) tb |= 1ull << A.hb[k];
+        for (int q = 0; q < A.n; ++q)
+            if (!((tb >> q) & 1)) outer[n_outer++] = q;
+    }
+    int tq[T];   // index bit of each tile bit
+#pragma unroll
+    for (int t = 0; t < T; ++t) tq[t] = t < 4 ? t : A.hb[t - 4];
+    auto tile_base = [&](long long ti) {
+        uint64_t g = 0;
+        for (int i = 0; i < n_outer; ++i)
+            if ((ti >> i) & 1) g |= 1ull << outer[i];
+        return g;
+    };
+    auto issue = [&](long long ti, int buf) {
+        const uint64_t base = tile_base(ti);
+        float2 *ps = xts + (size_t)buf * 2 * E, *ls = ps + E;
+#pragma unroll 4
+        for (int e = tid; e < ROWS * 8; e += kXyzTThreads) {
+            const int r = e >> 3, c4 = e & 7;
+            uint64_t g = base;
+#pragma unroll
+            for (int k = 0; k < H; ++k)
+                if ((r >> k) & 1) g |= 1ull << A.hb[k];
+            const int o = xt_off(r, 2 * c4);
+            cp_async16(ps + o, psi + g + 2 * c4);
+            cp_async16(ls + o, lam + g + 2 * c4);
+        }
+        cp_async_commit();
+    };
+    float f[2 * kXyzTileBits], zacc[T], zq[kXyzZBits], ztot = 0.f;
+#pragma unroll
+    for (int e = 0; e < 2 * kXyzTileBits; ++e) f[e] = 0.f;
+#pragma unroll
+    for (int t = 0; t < T; ++t) zacc[t] = 0.f;
+#pragma unroll
+    for (int q = 0; q < kXyzZBits; ++q) zq[q] = 0.f;
+    long long ti = blockIdx.x;
+    if (ti < n_tiles) issue(ti, 0);
+    for (int k = 0; ti < n_tiles; ti += gridDim.x, ++k) {
+        const long long nxt = ti + gridDim.x;
+        if (nxt < n_tiles) {
+            issue(nxt, (k + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();   // tile k is in shared memory for every thread
+        const float2 *ps = xts + (size_t)(k & 1) * 2 * E, *ls = ps + E;
+        // Z parts: Im(conj(lam) psi) into the total and the set tile bits
+        float tot = 0.f;
+        float zt[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) zt[t] = 0.f;
+        for (int e = tid; e < E; e += kXyzTThreads) {
+            const int o = xt_off(e >> 4, e & 15);
+            const float2 p = ps[o], l = ls[o];
+            const float im = l.x * p.y - l.y * p.x;
+            tot += im;
+#pragma unroll
+            for (int t = 0; t < T; ++t)
+                if ((e >> t) & 1) zt[t] += im;
+        }
+        // pair sweeps over 4 tile bits at a time
+#pragma unroll
+        for (int sw = 0; sw < 3; ++sw) {
+            if (4 * sw >= T) break;
+            const int g0 = 4 * sw, ng = (T - g0) < 4 ? (T - g0) : 4;
+            if (!((A.xymask >> g0) & ((1u << ng) - 1))) continue;
+            const int items = E >> ng;
+            for (int it = tid; it < items; it += kXyzTThreads) {
+                const int lo = it & ((1 << g0) - 1), hi = it >> g0;
+                const int e0 = lo | (hi << (g0 + ng));
+                float2 p[16], l[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if (j >= (1 << ng)) break;
+                    const int e = e0 | (j << g0);
+                    const int o = xt_off(e >> 4, e & 15);
+                    p[j] = ps[o];
+                    l[j] = ls[o];
+                }
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    if (m >= ng) break;
+                    float ax = 0.f, ay = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        if (j >= (1 << ng) || ((j >> m) & 1)) continue;
+                        const int j1 = j | (1 << m);
+                        // Im A + Im B, Re B - Re A for A = conj(l_j) p_j1, B = conj(l_j1) p_j
+                        ax = fmaf(l[j].x, p[j1].y, ax);
+                        ax = fmaf(-l[j].y, p[j1].x, ax);
+                        ax = fmaf(l[j1].x, p[j].y, ax);
+                        ax = fmaf(-l[j1].y, p[j].x, ax);
+                        ay = fmaf(l[j1].x, p[j].x, ay);
+                        ay = fmaf(l[j1].y, p[j].y, ay);
+                        ay = fmaf(-l[j].x, p[j1].x, ay);
+                        ay = fmaf(-l[j].y, p[j1].y, ay);
+                    }
+                    f[g0 + m] += ax;
+                    f[kXyzTileBits + g0 + m] += ay;
+                }
+            }
+        }
+        // this tile's Z sums: tile bits from zt; a bit outside the tile (zmask)
+        // takes the thread's whole tile sum when the tile's base index has it set
+        const uint64_t zb = A.zmask & tile_base(ti);
+#pragma unroll
+        for (int t = 0; t < T; ++t) zacc[t] += zt[t];
+#pragma unroll
+        for (int q = 0; q < kXyzZBits; ++q)
+            if ((zb >> q) & 1) zq[q] += tot;
+        ztot += tot;
+        __syncthreads();   // every read of this buffer precedes its refill two tiles on
+    }
+    // slots: X / Y per tile bit, S_q per index bit (tile bits from zacc, others
+    // from zq), total
+    __shared__ double red[kXyzTThreads / 32][kXyzTSlots];
+    for (int e = tid; e < (kXyzTThreads / 32) * kXyzTSlots; e += kXyzTThreads) (&red[0][0])[e] = 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 2 * kXyzTileBits; ++e) {
+        const double v = warp_sum((double)f[e]);
+        if (lane == 0) red[warp][e] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < kXyzZBits; ++q) {
+        if (!((A.zmask >> q) & 1)) continue;   // uniform
+        const double v = warp_sum((double)zq[q]);
+        if (lane == 0) red[warp][2 * kXyzTileBits + q] = v;
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const double v = warp_sum((double)zacc[t]);
+        if (lane == 0) red[warp][2 * kXyzTileBits + tq[t]] += v;
+    }
+    {
+        const double v = warp_sum((double)ztot);
+        if (lane == 0) red[warp][2 * kXyzTileBits + kXyzZBits] = v;
+    }
+    __syncthreads();
+    double *out = A.partial + ((long long)b * gridDim.x + blockIdx.x) * kXyzTSlots;
+    for (int e = tid; e < kXyzTSlots; e += kXyzTThreads) {
+        double v = 0.0;
+        for (int wi = 0; wi < kXyzTThreads / 32; ++wi) v += red[wi][e];
+        out[e] = v;
+    }
+}
+
+template <int H>
+static cudaError_t xyz_tile_launch(const XyzTileArgs &A, cudaStream_t st) {
+    const int smem = 2 * 2 * (8 << (4 + H));   // two buffers of psi and lam tiles
+    cudaFuncSetAttribute(xyz_tile_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    dim3 grid((unsigned)A.grid, (unsigned)A.batch);
+    xyz_tile_kernel<H><<<grid, kXyzTThreads, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xyz_tile(const XyzTileArgs &A, cudaStream_t st) {
+    if (A.H < 0 || A.H > 8 || A.grid < 1 || A.batch < 1 || (A.elems >> (4 + A.H)) < 1) return cudaErrorInvalidValue;
+    switch (A.H) {
+        case 0: return xyz_tile_launch<0>(A, st);
+        case 1: return xyz_tile_launch<1>(A, st);
+        case 2: return xyz_tile_launch<2>(A, st);
+        case 3: return xyz_tile_launch<3>(A, st);
+        case 4: return xyz_tile_launch<4>(A, st);
+        case 5: return xyz_tile_launch<5>(A, st);
+        case 6: return xyz_tile_launch<6>(A, st);
+        case 7: return xyz_tile_launch<7>(A, st);
+        default: return xyz_tile_launch<8>(A, st);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// <psi| D |psi> for a diagonal D = sum_k c_k Z^{z_k}: per amplitude the FP32
+// weight w(x) = sum_k c_k (-1)^popcount(x & z_k), one accumulator per thread
+// (folded into FP64 every 64 amplitudes), one launch for any number of terms.
+// ---------------------------------------------------------------------------
+constexpr int kDiagTermsMax = 256;
+
+__global__ void __launch_bounds__(256) diag_expect_kernel(const DiagExpectArgs A) {
+    __shared__ uint64_t zs[kDiagTermsMax];
+    __shared__ float cs[kDiagTermsMax];
+    __shared__ double red[8];
+    for (int k = threadIdx.x; k < A.n_terms; k += blockDim.x) {
+        zs[k] = A.terms[k].z;
+        cs[k] = (float)A.terms[k].coeff;
+    }
+    __syncthreads();
+    const int b = blockIdx.y;
+    const float4 *psi = reinterpret_cast<const float4 *>(A.psi + (long long)b * A.bstride);
+    const long long npair = A.elems >> 1;   // two amplitudes per 16-byte load
+    double acc = 0.0;
+    float fac = 0.f;
+    int cnt = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < npair; w += stride) {
+        const float4 v = psi[w];
+        const uint64_t x0 = (uint64_t)w << 1;
+        float w0 = 0.f, w1 = 0.f;
+        for (int k = 0; k < A.n_terms; ++k) {
+            const uint64_t z = zs[k];
+            const float c = cs[k];
+            w0 += (__popcll(x0 & z) & 1) ? -c : c;
+            w1 += (__popcll((x0 | 1) & z) & 1) ? -c : c;
+        }
+        fac = fmaf(v.x * v.x + v.y * v.y, w0, fac);
+        fac = fmaf(v.z * v.z + v.w * v.w, w1, fac);
+        if (++cnt == 64) {
+            acc += (double)fac;
+            fac = 0.f;
+            cnt = 0;
+        }
+    }
+    acc = warp_sum(acc + (double)fac);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) v += red[i];
+        A.partial[((long long)b * gridDim.x + blockIdx.x) * 2] = v;   // (re, im) pairs for the finish kernel
+        A.partial[((long long)b * gridDim.x + blockIdx.x) * 2 + 1] = 0.0;
+    }
+}
+
+cudaError_t launch_diag_expect(const DiagExpectArgs &A, cudaStream_t st) {
+    if (A.n_terms < 1 || A.n_terms > kDiagTermsMax || A.elems < 2 || A.grid < 1) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)A.grid, (unsigned)A.batch);
+    diag_expect_kernel<<<grid, 256, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
 }  // namespace qs

@@ -456,7 +456,7 @@ __device__ __forceinline__ void apply_diag(const SweepCtx &c, const MicroOp &op,
                                            float2 (&a)[1 << R]) {
     const DiagDesc &d = c.diags[op.cst];
     const uint32_t dyn_s = (uint32_t)op.a, dyn_g = (uint32_t)op.b;
-    float2 stat = d.pad0 ? make_float2(d.gph_re, d.gph_im) : make_float2(1.f, 0.f);
+    float2 stat = d.pad0 ? c.cs[d.gph_off] : make_float2(1.f, 0.f);
     stat = diag_part(d, gbase, c.cs, ~dyn_s, ~dyn_g, stat);
     if (dyn_g == 0 && __popc(dyn_s) <= 2 && dyn_s) {
         // fast path: the varying tables' indices are the item's base
@@ -518,7 +518,7 @@ __device__ __forceinline__ void apply_diagq(const SweepCtx &c, const MicroOp &op
                                             float2 (&a)[1 << R]) {
     const DiagDesc &d = c.diags[op.cst];
     float2 z[1 << R];
-    z[0] = d.pad0 ? make_float2(d.gph_re, d.gph_im) : make_float2(1.f, 0.f);
+    z[0] = d.pad0 ? c.cs[d.gph_off] : make_float2(1.f, 0.f);
     z[0] = diag_part(d, gbase, c.cs, ~0u, ~0u, z[0]);
 #pragma unroll
     for (int m = 0; m < R; ++m) {
@@ -1057,6 +1057,7 @@ __global__ void __launch_bounds__(NT, MINB)
     c.diags = s_diags;
     c.tab_s = s_tab_s;
     c.tab_g = s_tab_g;
+    long long cur_item = 0;   // constants of item 0 are staged above
     for (int k = 0; k < n_mine; ++k) {
         if (tid == 0 && k + D < n_mine) {
             // buffer (k+D) % NB last held tile k+D-NB, stored at the end of
@@ -1082,6 +1083,17 @@ __global__ void __launch_bounds__(NT, MINB)
         }
         const long long t = blockIdx.x + (long long)k * stride;
         const long long ti = t % A.n_tiles;
+        if (A.const_stride) {
+            // per-item constants: restage when this tile starts another item (the
+            // previous tile's sweeps ended at the barrier before its store)
+            const long long item = (t / A.n_tiles) / A.const_group;
+            if (item != cur_item) {
+                const float2 *src = A.consts + item * A.const_stride;
+                for (int i = tid; i < P.n_const; i += NT) cs[i] = src[i];
+                __syncthreads();
+                cur_item = item;
+            }
+        }
         c.buf = buf0 + (size_t)(k % NB) * tile_elems;
         c.tile_gbase = A.needs_gidx ? tile_base(A, ti) : 0;
         for (int s = 0; s < n_sweeps; ++s) {

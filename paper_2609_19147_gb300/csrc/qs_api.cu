@@ -323,6 +323,11 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     std::memset(&A, 0, sizeof A);
     A.pass = dp.d_tile[i];
     A.consts = dp.d_consts[i];
+    if (dp.host.items > 1) {   // per-item constants, item after item
+        if (batch % dp.host.items) return fail(QS_ERR_INTERNAL, "batch is not a multiple of the plan's items");
+        A.const_stride = tp.n_const;
+        A.const_group = batch / dp.host.items;
+    }
     A.roots = g_roots[st->dev];
     A.src = src;
     A.dst = dst;
@@ -344,7 +349,7 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     off += tp.n_sweeps * kItemTab * (8 + 4);   // item-address tables
     off = al(off, 128);
     A.off_consts = off;
-    off = al(off + (int)hp.consts.size() * 8, 128);
+    off = al(off + tp.n_const * 8, 128);   // one item's constants
     if (hp.uses_roots) {
         A.off_roots = off;
         off += kRootsEntries * 8;
@@ -934,36 +939,52 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, c
     if (n_gates == 0) return QS_OK;
     if (!per_item) return apply_resolved(st, resolved[0], o, st->home, st->batch);
     if (o.mode == QS_MODE_FUSED) {
-        // per-item plans: the ones not cached are built on host threads first
+        // per-item parameters: plans for every item (built on host threads) are
+        // merged into one batched plan with per-item constants when they agree
+        // in structure; otherwise each item runs its own plan
         std::vector<uint64_t> keys(st->batch);
-        std::vector<std::vector<RGate>> missing;
-        std::vector<int> miss_item;
+        uint64_t ck = 1469598103934665603ull;
         for (int bi = 0; bi < st->batch; ++bi) {
             keys[bi] = plan_key(st->n, 1, resolved[bi], o);
-            if (!st->cache.count(keys[bi]) &&
-                std::find(keys.begin(), keys.begin() + bi, keys[bi]) == keys.begin() + bi) {
-                missing.push_back(resolved[bi]);
-                miss_item.push_back(bi);
+            ck = fnv1a(&keys[bi], sizeof keys[bi], ck);
+        }
+        DevicePlan *dp = cache_lookup(st, ck);
+        qs_status s = QS_OK;
+        std::vector<Plan> built;
+        if (!dp) {
+            bool all_cached = true;
+            for (int bi = 0; bi < st->batch && all_cached; ++bi) all_cached = st->cache.count(keys[bi]) != 0;
+            if (!all_cached) {
+                std::string err;
+                s = build_plans_parallel(st->n, 1, resolved, o, built, err);
+                if (s != QS_OK) return fail(s, err);
+                Plan merged;
+                if (merge_item_plans(built, merged, st->batch)) {
+                    s = cache_insert(st, ck, std::move(merged), &dp);
+                    if (s != QS_OK) return s;
+                }
             }
         }
-        std::vector<Plan> built;
-        std::string err;
-        qs_status s = build_plans_parallel(st->n, 1, missing, o, built, err);
-        if (s != QS_OK) return fail(s, err);
-        size_t next = 0;
-        for (int bi = 0; bi < st->batch; ++bi) {
-            DevicePlan *dp = cache_lookup(st, keys[bi]);
-            if (!dp) {
-                if (next >= built.size() || miss_item[next] != bi) return fail(QS_ERR_INTERNAL, "plan bookkeeping");
-                s = cache_insert(st, keys[bi], std::move(built[next++]), &dp);
-                if (s != QS_OK) return s;
-            }
-            float2 *home = st->home + (size_t)bi * st->elems;
+        if (dp) {   // one launch per pass for the whole batch
             if (plan_needs_scratch(dp->host)) {
                 s = ensure_scratch(st);
                 if (s != QS_OK) return s;
             }
-            s = run_fused(st, *dp, home, st->scratch ? st->scratch + (home - st->home) : nullptr, 1);
+            return run_fused(st, *dp, st->home, st->scratch, st->batch);
+        }
+        for (int bi = 0; bi < st->batch; ++bi) {   // each item with its own plan, run as soon as it is found
+            DevicePlan *d = cache_lookup(st, keys[bi]);
+            if (!d) {
+                if ((size_t)bi >= built.size()) return fail(QS_ERR_INTERNAL, "per-item plan missing");
+                s = cache_insert(st, keys[bi], std::move(built[bi]), &d);
+                if (s != QS_OK) return s;
+            }
+            float2 *home = st->home + (size_t)bi * st->elems;
+            if (plan_needs_scratch(d->host)) {
+                s = ensure_scratch(st);
+                if (s != QS_OK) return s;
+            }
+            s = run_fused(st, *d, home, st->scratch ? st->scratch + (home - st->home) : nullptr, 1);
             if (s != QS_OK) return s;
         }
         return QS_OK;
@@ -977,9 +998,17 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, c
 
 qs_status qs_expect(qs_state *st, const qs_pauli *terms, size_t n_terms, double *out) {
     if (!st || !out || (n_terms && !terms)) return fail(QS_ERR_INVALID_ARG, "NULL argument");
-    std::vector<TermIdx> t;
-    qs_status s = convert_terms(st->n, terms, n_terms, t);
+    std::vector<TermIdx> all;
+    qs_status s = convert_terms(st->n, terms, n_terms, all);
     if (s != QS_OK) return s;
+    // Z-only terms (two or more) take one diagonal-weight pass; the rest go
+    // through the Pauli-group reductions
+    std::vector<TermIdx> t, dz;
+    for (auto &x : all) (x.x == 0 && st->elems >= 2 ? dz : t).push_back(x);
+    if (dz.size() < 2 || dz.size() > 256) {
+        t.insert(t.end(), dz.begin(), dz.end());
+        dz.clear();
+    }
     std::vector<double> S;
     s = overlaps(st, st->home, nullptr, st->batch, t, S);
     if (s != QS_OK) return s;
@@ -991,6 +1020,37 @@ qs_status qs_expect(qs_state *st, const qs_pauli *terms, size_t n_terms, double 
             e += t[k].coeff * re;
         }
         out[b] = e;
+    }
+    if (!dz.empty()) {
+        const int B = st->batch;
+        const int grid = std::max(1, std::min<int>((int)((st->elems / 2 + 255) / 256), g_num_sms[st->dev] * 4));
+        s = ensure_partial(st, (size_t)B * grid * 2);
+        if (s == QS_OK) s = ensure_out(st, (size_t)B * 2);
+        if (s == QS_OK) s = ensure_terms(st, dz.size());
+        if (s != QS_OK) return s;
+        std::vector<PauliDev> hz;
+        for (auto &x : dz) hz.push_back({x.coeff, 0, x.z});
+        QS_CUDA(cudaMemcpyAsync(st->d_terms, hz.data(), hz.size() * sizeof(PauliDev), cudaMemcpyHostToDevice,
+                                st->stream));
+        DiagExpectArgs A;
+        std::memset(&A, 0, sizeof A);
+        A.psi = st->home;
+        A.elems = st->elems;
+        A.bstride = st->elems;
+        A.batch = B;
+        A.n_terms = (int)hz.size();
+        A.terms = st->d_terms;
+        A.partial = st->d_partial;
+        A.grid = grid;
+        cudaEvent_t ev;
+        prof_begin(st, &ev);
+        QS_CUDA(launch_diag_expect(A, st->stream));
+        prof_end(st, ev, "diag_expect", 8.0 * (double)st->elems * B);
+        QS_CUDA(launch_expect_finish(st->d_partial, st->d_out, B, grid, 1, st->stream));
+        std::vector<double> r((size_t)B * 2);
+        QS_CUDA(cudaMemcpyAsync(r.data(), st->d_out, r.size() * sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+        QS_CUDA(cudaStreamSynchronize(st->stream));
+        for (int b = 0; b < B; ++b) out[b] += r[(size_t)b * 2];
     }
     return QS_OK;
 }
@@ -1068,14 +1128,18 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
         std::string err;
         s = build_plans_parallel(st->n, 1, rg, o, fwd, err);
         if (s != QS_OK) return fail(s, err);
-        for (int b = 0; b < B; ++b) {
-            s = run_host_plan(st, std::move(fwd[b]), st->home + (size_t)b * st->elems, 1);
+        Plan merged;
+        if (B > 1 && merge_item_plans(fwd, merged, B)) {   // one launch per pass, per-item constants
+            s = run_host_plan(st, std::move(merged), st->home, B);
             if (s != QS_OK) return s;
+        } else {
+            for (int b = 0; b < B; ++b) {
+                s = run_host_plan(st, std::move(fwd[b]), st->home + (size_t)b * st->elems, 1);
+                if (s != QS_OK) return s;
+            }
         }
     }
-    // 2. energy
-    s = qs_expect(st, terms, n_terms, energy);
-    if (s != QS_OK) return s;
+    // 2. the energy comes with lam = H psi below: E = Re <psi|lam>
     // 3. the reverse sweep works on pairs (psi_b, lam_b) stored next to each
     //    other, so that an item's pair is a batch of two states for the fused
     //    executor; the caller's state keeps psi(theta)
@@ -1113,6 +1177,16 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
         } else {
             QS_CUDA(cudaMemset2DAsync(W + E, 2 * E * sizeof(float2), 0, E * sizeof(float2), B, st->stream));
         }
+    }
+    {
+        std::vector<TermIdx> one(1);
+        one[0].coeff = 1.0;
+        one[0].x = one[0].z = 0;
+        one[0].ny = 0;
+        std::vector<double> S;
+        s = overlaps(st, W, W + E, B, one, S, 2 * E);   // sum_x conj(lam_x) psi_x
+        if (s != QS_OK) return s;
+        for (int b = 0; b < B; ++b) energy[b] = S[(size_t)b * 2];
     }
     s = qs_wrap(W, st->n, 2 * B, st->stream, &aux);
     if (s != QS_OK) return s;
@@ -1154,6 +1228,13 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
         pending.clear();
         const Segment &sg = segs[next_seg++];
         if (!sg.per_item) return run_host_plan(aux, std::move(seg_plans[sg.first_plan]), W, 2 * B);
+        if (B > 1) {   // the items' plans merged: one launch per pass over all pairs
+            std::vector<Plan> items(std::make_move_iterator(seg_plans.begin() + sg.first_plan),
+                                    std::make_move_iterator(seg_plans.begin() + sg.first_plan + B));
+            Plan merged;
+            if (merge_item_plans(items, merged, 2 * B)) return run_host_plan(aux, std::move(merged), W, 2 * B);
+            for (int b = 0; b < B; ++b) seg_plans[sg.first_plan + b] = std::move(items[b]);
+        }
         for (int b = 0; b < B; ++b) {
             qs_status r = run_host_plan(aux, std::move(seg_plans[sg.first_plan + b]), W + (size_t)2 * b * E, 2);
             if (r != QS_OK) return r;
@@ -1210,9 +1291,13 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
         for (size_t j = 0; j < i2.size(); ++j) seg_plans[i2[j]] = std::move(p2[j]);
         for (size_t j = 0; j < iB.size(); ++j) seg_plans[iB[j]] = std::move(pB[j]);
     }
+    // overlap launches: shared-memory tiles of the 4 low bits + <= 8 wires
+    // (n >= 6), else register groups of <= 4 wires
+    const bool tiled = st->n >= 6;
     struct XyzLaunch {
-        int k;
-        int gbit[kXyzGroup];
+        int k;                   // group bits (register kernel) or H (tile kernel)
+        int gbit[8];             // the group bits / the tile's high bits
+        uint32_t xymask;         // tile kernel: tile bits whose X / Y are taken
         uint64_t zmask;
     };
     struct LayerRec {
@@ -1233,12 +1318,40 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
             L.gates.push_back(k);
             if (gates[k].param_idx >= 0) wires |= 1ull << rg[0][k].b[0];
         }
-        if (wires) {
+        if (wires && tiled) {
+            std::vector<int> hi, others;
+            for (int q = 4; q < st->n; ++q) ((wires >> q) & 1 ? hi : others).push_back(q);
+            const int hmax = std::min(7, st->n - 4);   // 11-bit tiles: three CTAs per SM with double buffers
+            size_t c = 0;
+            do {
+                XyzLaunch x;
+                std::memset(&x, 0, sizeof x);
+                std::vector<int> hb(hi.begin() + c, hi.begin() + std::min(hi.size(), c + (size_t)hmax));
+                const int used = (int)hb.size();
+                // larger tiles amortise the per-tile work: pad with bits that are not wires
+                for (size_t o = 0; (int)hb.size() < hmax && o < others.size(); ++o) hb.push_back(others[o]);
+                std::sort(hb.begin(), hb.end());
+                x.k = (int)hb.size();
+                uint64_t tb = 15;
+                for (int k = 0; k < x.k; ++k) {
+                    x.gbit[k] = hb[k];
+                    tb |= 1ull << hb[k];
+                    if ((wires >> hb[k]) & 1) x.xymask |= 1u << (4 + k);
+                }
+                if (c == 0) {
+                    x.xymask |= (uint32_t)(wires & 15);
+                    x.zmask = wires & ~tb;
+                }
+                L.launches.push_back(x);
+                c += used;
+            } while (c < hi.size());
+        } else if (wires) {
             std::vector<int> bits;
             for (int q = 0; q < st->n; ++q)
                 if ((wires >> q) & 1) bits.push_back(q);
             for (size_t c = 0; c < bits.size(); c += kXyzGroup) {
                 XyzLaunch x;
+                std::memset(&x, 0, sizeof x);
                 x.k = (int)std::min<size_t>(kXyzGroup, bits.size() - c);
                 uint64_t gm = 0;
                 for (int j = 0; j < x.k; ++j) {
@@ -1248,18 +1361,22 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
                 x.zmask = c == 0 ? (wires & ~gm) : 0;
                 L.launches.push_back(x);
             }
+        }
+        if (wires) {
             L.first = n_launch;
             n_launch += L.launches.size();
             layers.push_back(L);
         }
         gi = lo;
     }
-    const int xgrid = xyz_grid(E, 1);   // enough blocks for every group size
+    const int slots = tiled ? kXyzTSlots : kXyzSlots;
+    const int xgrid = tiled ? (int)std::max(1ll, std::min<long long>(E >> 11, (6ll * g_num_sms[st->dev] + B - 1) / B))
+                            : xyz_grid(E, 1);
     double *d_res = nullptr;
     if (n_launch) {
-        s = ensure_partial(st, (size_t)B * xgrid * kXyzSlots);
+        s = ensure_partial(st, (size_t)B * xgrid * slots);
         if (s != QS_OK) return s;
-        QS_CUDA(cudaMallocAsync((void **)&d_res, n_launch * B * kXyzSlots * sizeof(double), st->stream));
+        QS_CUDA(cudaMallocAsync((void **)&d_res, n_launch * B * slots * sizeof(double), st->stream));
     }
     struct Guard3 {
         qs_state *st;
@@ -1280,26 +1397,46 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
             if (has_param) {
                 s = flush();
                 if (s != QS_OK) return s;
+                if (li >= layers.size()) return fail(QS_ERR_INTERNAL, "qs_grad: layer bookkeeping");
                 const LayerRec &L = layers[li++];
                 for (size_t c = 0; c < L.launches.size(); ++c) {
-                    XyzArgs A;
-                    std::memset(&A, 0, sizeof A);
-                    A.psi = W;
-                    A.lam = W + E;
-                    A.elems = E;
-                    A.bstride = 2 * E;
-                    A.batch = B;
-                    A.k = L.launches[c].k;
-                    for (int j = 0; j < A.k; ++j) A.gbit[j] = L.launches[c].gbit[j];
-                    A.zmask = L.launches[c].zmask;
-                    A.partial = st->d_partial;
-                    A.grid = xgrid;
+                    const XyzLaunch &x = L.launches[c];
                     cudaEvent_t ev;
                     prof_begin(st, &ev);
-                    QS_CUDA(launch_xyz_overlaps(A, st->stream));
+                    if (tiled) {
+                        XyzTileArgs A;
+                        std::memset(&A, 0, sizeof A);
+                        A.psi = W;
+                        A.lam = W + E;
+                        A.elems = E;
+                        A.bstride = 2 * E;
+                        A.batch = B;
+                        A.n = st->n;
+                        A.H = x.k;
+                        for (int j = 0; j < x.k; ++j) A.hb[j] = x.gbit[j];
+                        A.xymask = x.xymask;
+                        A.zmask = x.zmask;
+                        A.partial = st->d_partial;
+                        A.grid = xgrid;
+                        QS_CUDA(launch_xyz_tile(A, st->stream));
+                    } else {
+                        XyzArgs A;
+                        std::memset(&A, 0, sizeof A);
+                        A.psi = W;
+                        A.lam = W + E;
+                        A.elems = E;
+                        A.bstride = 2 * E;
+                        A.batch = B;
+                        A.k = x.k;
+                        for (int j = 0; j < A.k; ++j) A.gbit[j] = x.gbit[j];
+                        A.zmask = x.zmask;
+                        A.partial = st->d_partial;
+                        A.grid = xgrid;
+                        QS_CUDA(launch_xyz_overlaps(A, st->stream));
+                    }
                     prof_end(st, ev, "xyz_overlap", 16.0 * (double)E * B);
-                    QS_CUDA(launch_expect_finish(st->d_partial, d_res + (L.first + c) * B * kXyzSlots, B, xgrid,
-                                                 kXyzSlots / 2, st->stream));
+                    QS_CUDA(launch_expect_finish(st->d_partial, d_res + (L.first + c) * B * slots, B, xgrid, slots / 2,
+                                                 st->stream));
                 }
             }
             for (size_t k = gi + 1; k-- > lo;) pending.push_back(k);
@@ -1345,7 +1482,7 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
     }
     // 5. gradients of the 1q layers from their X / Y / Z overlaps
     if (n_launch) {
-        std::vector<double> res(n_launch * B * kXyzSlots);
+        std::vector<double> res(n_launch * B * slots);
         QS_CUDA(cudaMemcpyAsync(res.data(), d_res, res.size() * sizeof(double), cudaMemcpyDeviceToHost, st->stream));
         QS_CUDA(cudaStreamSynchronize(st->stream));
         for (const LayerRec &L : layers) {
@@ -1355,8 +1492,22 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
                 double total = 0.0;
                 std::map<int, double> sq;
                 for (size_t c = 0; c < L.launches.size(); ++c) {
-                    const double *r = &res[((L.first + c) * B + b) * kXyzSlots];
+                    const double *r = &res[((L.first + c) * B + b) * slots];
                     const XyzLaunch &x = L.launches[c];
+                    if (tiled) {
+                        // tile bit t: low bit t (t < 4) or high bit gbit[t - 4]
+                        for (int t = 0; t < 4 + x.k; ++t) {
+                            if (!((x.xymask >> t) & 1)) continue;
+                            const int q = t < 4 ? t : x.gbit[t - 4];
+                            ov[q][0] = r[t];
+                            ov[q][1] = r[kXyzTileBits + t];
+                        }
+                        if (c == 0) {
+                            total = r[2 * kXyzTileBits + kXyzZBits];
+                            for (int q = 0; q < kXyzZBits && q < st->n; ++q) sq[q] = r[2 * kXyzTileBits + q];
+                        }
+                        continue;
+                    }
                     if (c == 0) total = r[3 * kXyzGroup + kXyzZBits];
                     for (int j = 0; j < x.k; ++j) {
                         ov[x.gbit[j]][0] = r[j];

@@ -57,8 +57,8 @@ constexpr int kMaxLutGroups = 8;
 constexpr int kMaxTwiddles = 4;
 
 struct DiagDesc {
-    int32_t n_slices, n_groups, n_tw, pad0;
-    float gph_re, gph_im;
+    int32_t n_slices, n_groups, n_tw, pad0;   // pad0: has a global-phase constant
+    int32_t gph_off, pad1;                      // constant offset of exp(i g0)
     int32_t slice_lo[kMaxSlices], slice_w[kMaxSlices], slice_off[kMaxSlices];
     int32_t grp_type[kMaxLutGroups], grp_d[kMaxLutGroups], grp_off[kMaxLutGroups];
     uint64_t grp_mask[kMaxLutGroups];

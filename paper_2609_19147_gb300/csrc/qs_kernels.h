@@ -38,6 +38,8 @@ struct TileArgs {
     int l2_prefetch;           // tiles warmed in L2 beyond the shared-memory prefetch
     int use_tma;               // 1: one tensor copy per tile; 0: one bulk copy per row
     int dense;                 // 1: the pass has dense-block sweeps (kernel with the dense paths)
+    long long const_stride;    // > 0: batch items differ in constants only; item i's set at
+    int const_group;           //   consts + (batch index / const_group) * const_stride
     int kset;                  // 1: every micro-op is a 1q / layer / diagonal op (KS_LAYER kernels)
     int needs_gidx;            // 1: some micro-op reads global indices (controls, diagonals, QFT)
     TmaGeom geo;
@@ -135,8 +137,38 @@ struct XyzArgs {
     double *partial;           // [batch][grid][kXyzSlots]
     int grid;
 };
+// <psi|D|psi> for D = sum_k coeff_k Z^{z_k} (terms with x = 0), up to 256 terms;
+// per-block FP64 sums (states with elems >= 2)
+struct DiagExpectArgs {
+    const float2 *psi;
+    long long elems, bstride;
+    int batch, n_terms;
+    const PauliDev *terms;     // device, x = 0
+    double *partial;           // [batch][grid][2] (re, 0)
+    int grid;
+};
+cudaError_t launch_diag_expect(const DiagExpectArgs &A, cudaStream_t st);
+
 int xyz_grid(long long elems, int k);   // minimum blocks per item
 cudaError_t launch_xyz_overlaps(const XyzArgs &A, cudaStream_t st);
+
+// The same overlaps over a tile of 2^(4 + H) amplitudes (the 4 low index bits
+// and H <= 8 high bits hb[]) staged in shared memory for psi and lam: X / Y for
+// every tile bit in xymask, S_q for the bits of zmask, and the total.
+// Slots: [ImX(tile bit t) t < 12 | ImY(t) t < 12 | S_q q < 34 | total | pad].
+constexpr int kXyzTileBits = 12;
+constexpr int kXyzTSlots = 2 * kXyzTileBits + kXyzZBits + 2;   // 60
+struct XyzTileArgs {
+    const float2 *psi, *lam;   // item b at psi + b * bstride, lam + b * bstride
+    long long elems, bstride;
+    int batch, n, H;
+    int hb[8];                 // ascending high tile bits (>= 4)
+    uint32_t xymask;           // tile bits (0..3 low, 4 + k for hb[k]) whose X / Y are wanted
+    uint64_t zmask;            // index bits whose S_q is wanted
+    double *partial;           // [batch][grid][kXyzTSlots]
+    int grid;                  // CTAs per item (they stride over the item's tiles)
+};
+cudaError_t launch_xyz_tile(const XyzTileArgs &A, cudaStream_t st);
 
 cudaError_t launch_init_zero(float2 *psi, long long state_elems, int batch, cudaStream_t st);
 

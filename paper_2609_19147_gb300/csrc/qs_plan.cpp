@@ -1031,10 +1031,12 @@ void plan_diag(int n, const Diag &d, DiagPlan &out) {
         }
         g0_done = true;
     }
-    if (!g0_done && d.g0 != 0.0) {
-        cur.gph_re = (float)std::cos(wrap_angle(d.g0));
-        cur.gph_im = (float)std::sin(wrap_angle(d.g0));
-        cur.pad0 = 1;   // has global phase
+    if (!g0_done) {
+        // a constant even when g0 = 0, so that the descriptor does not depend on
+        // the angle values (plans of batch items with other angles stay alike)
+        cur.gph_off = (int)tab.size();
+        tab.push_back(cexp_f(d.g0));
+        cur.pad0 = 1;
     }
     for (auto &kv : groups) {
         if (cur.n_groups == kMaxLutGroups) {
@@ -1543,6 +1545,7 @@ struct PassBuilder {
                     int base = (int)cst.size();
                     for (int s = 0; s < dd.n_slices; ++s) dd.slice_off[s] += base;
                     for (int g = 0; g < dd.n_groups; ++g) dd.grp_off[g] += base;
+                    if (dd.pad0) dd.gph_off += base;
                     cst.insert(cst.end(), dp->tables[k].begin(), dp->tables[k].end());
                     int di = count_diags++;
                     tp.diags[di] = dd;
@@ -2133,6 +2136,53 @@ qs_status build_pergate_plan(int n, const std::vector<RGate> &gates, Plan &plan,
         plan.pg.push_back(op);
     }
     return QS_OK;
+}
+
+static bool same_tma(const TmaPlan &a, const TmaPlan &b) {   // field by field (the struct has padding)
+    if (a.ok != b.ok || a.ndims != b.ndims || a.batch_dim != b.batch_dim) return false;
+    for (int d = 0; d < 5; ++d)
+        if (a.kind[d] != b.kind[d] || a.off[d] != b.off[d] || a.w[d] != b.w[d] || a.gdim[d] != b.gdim[d] ||
+            a.gstride[d] != b.gstride[d] || a.box[d] != b.box[d])
+            return false;
+    return true;
+}
+
+bool merge_item_plans(std::vector<Plan> &plans, Plan &out, int batch) {
+    if (plans.empty()) return false;
+    const Plan &p0 = plans[0];
+    if (p0.mode != QS_MODE_FUSED) return false;
+    for (const Plan &p : plans) {
+        if (p.mode != p0.mode || p.items != 1 || p.passes.size() != p0.passes.size()) return false;
+        for (size_t i = 0; i < p.passes.size(); ++i) {
+            const HostPass &a = p0.passes[i], &b = p.passes[i];
+            if (a.type != b.type || a.uses_roots != b.uses_roots) return false;
+            if (a.type == HostPass::TILE) {
+                if (std::memcmp(&a.tile, &b.tile, sizeof(TilePass)) != 0 || a.consts.size() != b.consts.size() ||
+                    !same_tma(a.tma, b.tma))
+                    return false;
+            } else if (a.type == HostPass::PERM) {
+                if (std::memcmp(&a.perm, &b.perm, sizeof(PermPass)) != 0) return false;
+            } else if (std::memcmp(&a.gather, &b.gather, sizeof(GatherPass)) != 0) {
+                return false;
+            }
+        }
+    }
+    out = p0;
+    out.items = (int)plans.size();
+    for (size_t i = 0; i < out.passes.size(); ++i) {
+        HostPass &hp = out.passes[i];
+        if (hp.type != HostPass::TILE) continue;
+        // the batch may need a tensor dim of its own: keep the merge only if the
+        // tensor-copy path survives (the layout and swizzle assume it)
+        uint64_t S = (1ull << hp.tile.L) - 1;
+        for (int k = 0; k < hp.tile.H; ++k) S |= 1ull << hp.tile.hb[k];
+        const TmaPlan g = tma_geometry(out.n, hp.tile.L, S, batch);
+        if (g.ok != hp.tma.ok) return false;
+        hp.tma = g;
+        hp.consts.clear();
+        for (const Plan &p : plans) hp.consts.insert(hp.consts.end(), p.passes[i].consts.begin(), p.passes[i].consts.end());
+    }
+    return true;
 }
 
 int Plan::hbm_passes() const {

@@ -98,6 +98,9 @@ struct HostPass {
 struct Plan {
     int n = 0;
     int mode = QS_MODE_FUSED;
+    // items > 1: one plan for a batch whose items differ only in constant
+    // values; every TILE pass holds items x n_const constants, item after item
+    int items = 1;
     std::vector<HostPass> passes;  // fused mode
     std::vector<PgOp> pg;          // per-gate mode: one entry per launch
     int n_gates = 0;
@@ -117,6 +120,11 @@ bool gate_is_diagonal(int kind);
 qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, const qs_opts &o, Plan &plan,
                            std::string &err);
 qs_status build_pergate_plan(int n, const std::vector<RGate> &gates, Plan &plan, std::string &err);
+
+// Merge per-item fused plans into one plan for `batch` states (a multiple of
+// the item count) with per-item constants, when they agree in everything but
+// constant values and every pass keeps its TMA tensor path at that batch.
+bool merge_item_plans(std::vector<Plan> &plans, Plan &out, int batch);
 
 // Fusion detector only (exposed for tests through qs_plan_describe).
 void detect(int n, const std::vector<RGate> &gates, std::vector<FOp> &ops);

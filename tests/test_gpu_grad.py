@@ -90,7 +90,7 @@ def test_vqe_ansatz_n10_against_param_shift_and_fd():
 def test_vqe_config_full_size_sampled():
     # n = 24, 12 layers, 576 parameters, batch 32: energies of all items
     # against qs_expect on the forward states, and oracle parameter shift on
-    # two sampled parameters of one item
+    # two sampled parameters of one item (energy within the oracle tolerance)
     n, L, B = 24, 12, 32
     gl = W.vqe_ansatz_gates(n, L)
     theta = W.vqe_params(n, L, B, 6)
@@ -100,7 +100,9 @@ def test_vqe_config_full_size_sampled():
     e2 = st.expect(terms)
     st.close()
     assert np.all(np.isfinite(g)) and g.shape == (B, 2 * n * L)
-    assert np.max(np.abs(e - e2)) < 1e-9
+    # qs_grad takes E = Re <psi|H psi> from the FP32 lam = H psi; qs_expect sums
+    # the Pauli terms directly: the two differ by FP32 rounding only
+    assert np.max(np.abs(e - e2)) < 1e-5
     assert np.max(np.abs(g)) <= sum(abs(t[0]) for t in terms)
     idx = [5, 2 * n * L - 2]
     ps = oracle.param_shift_grad(n, gl, theta[3], terms, indices=idx)
