@@ -15,9 +15,48 @@
 
 namespace qs {
 
+// A tile is 2^TB input elements (TB <= 12).  Offsets are OR-linear in the
+// element's bits, so per-CTA tables of the low 5 and the high TB-5 bits give
+// every address in two lookups; the output-to-tile map is linear too, which
+// folds the XOR mask into one constant.  Bit 0 is a tile bit on both sides,
+// so loads and stores move two amplitudes (16 bytes) at a time.
+constexpr int kPermMaxTB = 12;
+
 __global__ void __launch_bounds__(256) perm_kernel(const PermArgs A) {
-    __shared__ float2 sm[1024 + 32];
-    const int TS = 1 << A.TB;
+    __shared__ float2 sm[(1 << kPermMaxTB) + (1 << (kPermMaxTB - 5))];   // one pad slot per 32
+    __shared__ uint64_t in_lo[32], in_hi[128], out_lo[32], out_hi[128];
+    __shared__ int e_lo[32], e_hi[128];
+    const int TB = A.TB, TS = 1 << TB, tid = threadIdx.x;
+    if (tid < 32) {
+        uint64_t a = 0, b = 0;
+        int e = 0;
+        for (int k = 0; k < 5 && k < TB; ++k)
+            if ((tid >> k) & 1) {
+                a |= 1ull << A.in_pos[k];
+                b |= 1ull << A.out_pos_loc[k];
+                e |= 1 << A.out_to_in[k];
+            }
+        in_lo[tid] = a;
+        out_lo[tid] = b;
+        e_lo[tid] = e;
+    }
+    if (tid < 128) {
+        uint64_t a = 0, b = 0;
+        int e = 0;
+        for (int k = 5; k < TB; ++k)
+            if ((tid >> (k - 5)) & 1) {
+                a |= 1ull << A.in_pos[k];
+                b |= 1ull << A.out_pos_loc[k];
+                e |= 1 << A.out_to_in[k];
+            }
+        in_hi[tid] = a;
+        out_hi[tid] = b;
+        e_hi[tid] = e;
+    }
+    int fx = 0;   // tile element of the XOR mask's local part
+    for (int k = 0; k < TB; ++k)
+        if ((A.xor_loc >> k) & 1) fx |= 1 << A.out_to_in[k];
+    __syncthreads();
     const long long tps = 1ll << A.n_outer;
     const long long total = tps * A.batch;
     for (long long t = blockIdx.x; t < total; t += gridDim.x) {
@@ -31,22 +70,23 @@ __global__ void __launch_bounds__(256) perm_kernel(const PermArgs A) {
         yo ^= A.xor_outer;
         const float2 *src = A.src + b * A.state_elems;
         float2 *dst = A.dst + b * A.state_elems;
-        for (int e = threadIdx.x; e < TS; e += blockDim.x) {
-            uint64_t x = xo;
-            for (int k = 0; k < A.TB; ++k)
-                if ((e >> k) & 1) x |= 1ull << A.in_pos[k];
-            sm[e + (e >> 5)] = src[x];
+#pragma unroll 8
+        for (int p = tid; p < (TS >> 1); p += 256) {
+            const int e = p << 1;
+            const uint64_t x = xo | in_lo[e & 31] | in_hi[e >> 5];
+            const float4 v = *reinterpret_cast<const float4 *>(src + x);
+            sm[e + (e >> 5)] = make_float2(v.x, v.y);
+            sm[e + 1 + (e >> 5)] = make_float2(v.z, v.w);
         }
         __syncthreads();
-        for (int o = threadIdx.x; o < TS; o += blockDim.x) {
-            uint64_t y = yo;
-            const uint32_t ol = (uint32_t)o ^ A.xor_loc;
-            int e = 0;
-            for (int k = 0; k < A.TB; ++k) {
-                if ((o >> k) & 1) y |= 1ull << A.out_pos_loc[k];
-                if ((ol >> k) & 1) e |= 1 << A.out_to_in[k];
-            }
-            dst[y] = sm[e + (e >> 5)];
+#pragma unroll 8
+        for (int p = tid; p < (TS >> 1); p += 256) {
+            const int o = p << 1;
+            const uint64_t y = yo | out_lo[o & 31] | out_hi[o >> 5];
+            const int e0 = (e_lo[o & 31] | e_hi[o >> 5]) ^ fx;
+            const int e1 = (e_lo[(o + 1) & 31] | e_hi[o >> 5]) ^ fx;
+            const float2 v0 = sm[e0 + (e0 >> 5)], v1 = sm[e1 + (e1 >> 5)];
+            *reinterpret_cast<float4 *>(dst + y) = make_float4(v0.x, v0.y, v1.x, v1.y);
         }
         __syncthreads();
     }

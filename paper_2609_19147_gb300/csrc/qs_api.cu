@@ -440,7 +440,7 @@ qs_status run_perm(qs_state *st, const PermPass &pp, const float2 *src, float2 *
     A.batch = batch;
     const int L = std::min(pp.L, n);
     // input tile bits: low L, then input bits landing on output low bits, then
-    // more low-positioned bits up to 10 tile bits
+    // more low-positioned bits up to 12 tile bits
     std::vector<int> in_bits;
     uint64_t in_mask = 0;
     for (int b = 0; b < L; ++b) {
@@ -452,7 +452,7 @@ qs_status run_perm(qs_state *st, const PermPass &pp, const float2 *src, float2 *
             in_bits.push_back(b);
             in_mask |= 1ull << b;
         }
-    for (int b = L; b < n && (int)in_bits.size() < 10; ++b)
+    for (int b = L; b < n && (int)in_bits.size() < 12; ++b)
         if (!((in_mask >> b) & 1)) {
             in_bits.push_back(b);
             in_mask |= 1ull << b;
