@@ -12,8 +12,10 @@ path's time for the same circuits, the HBM roofline of the dominant kernel,
 the oracle's CPU baseline and an end-to-end (host buffer) figure.  Outside
 the timed step it reports the metric's other rows: adjoint gradients per
 second on the VQE config (n = 24, 576 parameters, batch 32), the dense
-5-qubit-block precisions on 30q TFIM (10 Strang steps), and batched QAOA
-instances per second (512 graphs x 8 angle sets).
+5-qubit-block precisions on 30q TFIM (10 Strang steps), batched QAOA
+instances per second (512 graphs x 8 angle sets) and the 28-qubit layered
+suite's per-layer HBM rates (each layer family alone, then 20 layers plus
+the QFT and WHT tail).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -208,9 +210,53 @@ def _time_cuda(torch, stream, fn, reps=1):
     return a.elapsed_time(b) / 1e3 / reps
 
 
+def suite_rows(qs, torch, peak):
+    """The 28-qubit layered suite: each layer family alone (Haar U(2) on every
+    qubit, ascending CNOT ladder, random-angle ZZ bonds, radix-4 QFT with
+    swaps, WHT), then 20 layers of the first three plus the QFT and the WHT.
+    Per family: layer time, HBM passes, the layer's own rate (one read and one
+    write of the state / layer time) and each kernel's rate over the bytes its
+    launches move (library events on the state's stream), as a fraction of the
+    measured copy bandwidth."""
+    n = 28
+    sb = (1 << n) * 8
+    s28 = qs.State(n)
+    s28.provide_scratch()
+    rng = np.random.default_rng(2)
+    s28.apply([W.Gate("U", (q,), (), W.haar_u2(rng)) for q in range(n)])
+    fams = [("u2_layer", [W.Gate("U", (q,), (), W.haar_u2(rng)) for q in range(n)]),
+            ("cnot_ladder", W.cnot_ladder(n)),
+            ("zz_layer", [W.Gate("RZZ", (b, b + 1), (float(rng.uniform(0.0, 2.0 * np.pi)),)) for b in range(n - 1)]),
+            ("qft", W.qft_gates(n, swaps=True)),
+            ("wht", W.wht_gates(n)),
+            ("suite_20_layers_qft_wht", W.suite28_gates(n, 20, 1, tail=True))]
+    out = {"workload": "28q layered suite, complex64, seeded (Haar U(2) seed 2, suite seed 1)",
+           "peak_GBps": peak}
+    for name, gl in fams:
+        cg = qs.CGates(gl)
+        s28.apply(cg)
+        torch.cuda.synchronize()
+        reps = 1 if name.startswith("suite") else 5
+        s28.profile(True)
+        t = _time_cuda(torch, s28.stream, lambda: s28.apply(cg), reps=reps)
+        prof = s28.profile_read()
+        s28.profile(False)
+        _, passes = qs.plan_describe(n, cg)
+        row = {"gates": len(gl), "s": t, "passes": passes}
+        if not name.startswith("suite"):
+            row["layer_GBps"] = round(2 * sb / t / 1e9, 1)
+        row["kernels"] = {k: {"launches": int(v[0]) // reps, "GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1),
+                              "frac": round(v[2] / (v[1] * 1e-3) / 1e9 / peak, 3)}
+                          for k, v in prof.items() if v[1] > 0 and v[2] > 0}
+        out[name] = row
+    s28.close()
+    return out
+
+
 def extra_rows(qs, torch, st, tfim, stream):
-    """grads/s of the adjoint config, the dense-block precisions on 30q TFIM
-    and the batched QAOA config; each after one untimed call."""
+    """grads/s of the adjoint config, the dense-block precisions on 30q TFIM,
+    the batched QAOA config and the 28q layered suite; each after one untimed
+    call."""
     out = {}
     n = N_QUBITS
     # adjoint gradients: n = 24, 12 layers of RY.RZ + CNOT ring, 576 params, batch 32
@@ -263,6 +309,7 @@ def extra_rows(qs, torch, st, tfim, stream):
     qt = time.perf_counter() - t0
     out["qaoa"] = {"config": "512 random 3-regular graphs (seed 5), n ~ U{14,...,24} even, p=4, 8 angle sets",
                    "instances": int(cut.size), "s": qt, "items_per_s": cut.size / qt}
+    out["suite28"] = suite_rows(qs, torch, peaks()[0])
     return out
 
 
@@ -436,7 +483,7 @@ def main():
     ap.add_argument("--no-pergate", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the grads / dense / QAOA rows")
+    ap.add_argument("--no-extra", action="store_true", help="skip the grads / dense / QAOA / 28q suite rows")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

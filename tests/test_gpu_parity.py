@@ -315,3 +315,41 @@ def test_heisenberg_layers_basis_conjugated(n):
         gl += [W.Gate("RXX", (0, n - 1), (0.3,)), W.Gate("H", (n // 2,)), W.Gate("RYY", (1, n - 2), (0.7,))]
     psi0 = W.random_state(n, 41)
     _assert_close(_run(n, gl, psi0), _ref(n, gl, psi0))
+
+
+def test_suite28_full_size_one_layer_and_full_suite():
+    # the 28q layered suite at full size, in the launch configuration the
+    # benchmark times: one layer (Haar U(2) on every qubit, CNOT ladder,
+    # random ZZ bonds) from a Haar product state against the oracle's full
+    # state; then 20 layers + QFT + WHT, fused against the per-gate path (norm
+    # and relative L2: after 20 layers every amplitude is ~2^-14)
+    n = 28
+    rng = np.random.default_rng(28)
+    vs = [W.haar_u2(rng)[:, 0] for _ in range(n)]
+    hi, lo = vs[0], vs[n // 2]
+    for v in vs[1:n // 2]:
+        hi = np.kron(hi, v)
+    for v in vs[n // 2 + 1:]:
+        lo = np.kron(lo, v)
+    psi0 = np.outer(hi, lo).reshape(-1).astype(np.complex64)
+    del hi, lo
+    gl = W.suite28_gates(n, 1, 5, tail=False)
+    st = qs.State(n)
+    st.set(psi0)
+    st.apply(gl)
+    got = st.get()[0]
+    ref = oracle.simulate(n, gl, psi0.astype(np.complex128))
+    _assert_close(got, ref)
+    del got, ref
+    suite = qs.CGates(W.suite28_gates(n, 20, 1, tail=True))
+    st.set(psi0)
+    st.apply(suite)
+    a = st.tensor[0].clone()
+    st.set(psi0)
+    st.apply(suite, mode="pergate")
+    b = st.tensor[0]
+    rel = float((torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item())
+    norm = float(torch.linalg.vector_norm(a).item())
+    st.close()
+    assert abs(norm - 1) < 1e-5
+    assert rel <= 1e-5, rel
