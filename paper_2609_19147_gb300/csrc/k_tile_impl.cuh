@@ -334,35 +334,68 @@ __device__ __forceinline__ void disp_u2(int ma, int mb, float2 (&a)[1 << R], con
     }
 }
 
-// layers: the same 2x2 family on every group bit in `mask`, straight-line code
-template <int R, int M = 0>
-__device__ __forceinline__ void layer_rxc(float2 (&a)[1 << R], const float2 *k0, uint32_t mask) {
+// layers: the same 2x2 family on every group bit in `mask`; the coefficients
+// of group bit M sit at k0 + stride * M (RXC 1, U1R 2, U1 4, H none)
+template <int KIND>
+struct LayerOp;
+template <>
+struct LayerOp<MK_RXC> {
+    template <int R, int M>
+    static __device__ __forceinline__ void run(float2 (&a)[1 << R], const float2 *k0, const Grp<R> &) {
+        op_rxc<R, M>(a, k0 + M);
+    }
+};
+template <>
+struct LayerOp<MK_U1R> {
+    template <int R, int M>
+    static __device__ __forceinline__ void run(float2 (&a)[1 << R], const float2 *k0, const Grp<R> &) {
+        op_u1r<R, M>(a, k0 + 2 * M);
+    }
+};
+template <>
+struct LayerOp<MK_U1> {
+    template <int R, int M>
+    static __device__ __forceinline__ void run(float2 (&a)[1 << R], const float2 *k0, const Grp<R> &G) {
+        op_u1<R, M>(a, k0 + 4 * M, 0ull, 0ull, 0ull, G);
+    }
+};
+template <>
+struct LayerOp<MK_H> {
+    template <int R, int M>
+    static __device__ __forceinline__ void run(float2 (&a)[1 << R], const float2 *, const Grp<R> &) {
+        op_h<R, M>(a);
+    }
+};
+
+// runtime mask: one branch per group bit
+template <int KIND, int R, int M = 0>
+__device__ __forceinline__ void layer_bits(float2 (&a)[1 << R], const float2 *k0, uint32_t mask, const Grp<R> &G) {
     if constexpr (M < R) {
-        if ((mask >> M) & 1) op_rxc<R, M>(a, k0 + M);
-        layer_rxc<R, M + 1>(a, k0, mask);
+        if ((mask >> M) & 1) LayerOp<KIND>::template run<R, M>(a, k0, G);
+        layer_bits<KIND, R, M + 1>(a, k0, mask, G);
     }
 }
-template <int R, int M = 0>
-__device__ __forceinline__ void layer_u1r(float2 (&a)[1 << R], const float2 *k0, uint32_t mask) {
+
+// compile-time mask: straight-line code over the set bits
+template <int KIND, int R, uint32_t MASK, int M = 0>
+__device__ __forceinline__ void layer_fixed(float2 (&a)[1 << R], const float2 *k0, const Grp<R> &G) {
     if constexpr (M < R) {
-        if ((mask >> M) & 1) op_u1r<R, M>(a, k0 + 2 * M);
-        layer_u1r<R, M + 1>(a, k0, mask);
+        if constexpr ((MASK >> M) & 1) LayerOp<KIND>::template run<R, M>(a, k0, G);
+        layer_fixed<KIND, R, MASK, M + 1>(a, k0, G);
     }
 }
-template <int R, int M = 0>
-__device__ __forceinline__ void layer_u1(float2 (&a)[1 << R], const float2 *k0, uint32_t mask, const Grp<R> &G) {
-    if constexpr (M < R) {
-        if ((mask >> M) & 1) op_u1<R, M>(a, k0 + 4 * M, 0ull, 0ull, 0ull, G);
-        layer_u1<R, M + 1>(a, k0, mask, G);
+
+template <int R>
+__device__ __forceinline__ void run_layer(int kind, float2 (&a)[1 << R], const float2 *k0, uint32_t mask,
+                                          const Grp<R> &G) {
+    switch (kind) {
+        case MK_RXC: layer_bits<MK_RXC, R>(a, k0, mask, G); break;
+        case MK_U1R: layer_bits<MK_U1R, R>(a, k0, mask, G); break;
+        case MK_U1: layer_bits<MK_U1, R>(a, k0, mask, G); break;
+        default: layer_bits<MK_H, R>(a, k0, mask, G); break;
     }
 }
-template <int R, int M = 0>
-__device__ __forceinline__ void layer_h(float2 (&a)[1 << R], uint32_t mask) {
-    if constexpr (M < R) {
-        if ((mask >> M) & 1) op_h<R, M>(a);
-        layer_h<R, M + 1>(a, mask);
-    }
-}
+
 // QFT stages from the highest group bit down (the gate stream's order)
 template <int R, int M = R - 1>
 __device__ __forceinline__ void layer_qft(float2 (&a)[1 << R], const float2 *k0, uint32_t mask, uint64_t ppack,
@@ -543,6 +576,37 @@ __device__ __forceinline__ void apply_diagq(const SweepCtx &c, const MicroOp &op
 constexpr int KS_ALL = 0;
 constexpr int KS_LAYER = 1;
 
+// A sweep whose only micro-op is one layer on every group bit (or on all
+// but group bit 0, the pair bit of 16-byte accesses) runs as straight-line
+// code from load to store: with no control-flow merge between the bits and
+// the store, the amplitudes are not moved back into fixed registers after
+// each bit.  Code 1 + 2 * (U1, H, RXC, U1R) + (all but bit 0); 0: the
+// general path.  (Sweeps that pair the layer with a diagonal keep the general
+// path: the second inlined copy of the diagonal code cost more than the
+// merges it saved.)
+template <int R>
+__device__ __forceinline__ int straight_code(const SweepCtx &c, int op_begin, int op_end, float scale) {
+    if (R != 4 || op_end - op_begin != 1) return 0;
+    const MicroOp &o = c.micro[op_begin];
+    if (o.kind != MK_LAYER || (o.a != MK_H && scale != 1.f)) return 0;
+    const uint32_t full = (1u << R) - 1, mask = (uint32_t)o.b;
+    if (mask != full && mask != (full & ~1u)) return 0;
+    const int ki = o.a == MK_U1 ? 0 : o.a == MK_H ? 1 : o.a == MK_RXC ? 2 : 3;
+    return 1 + 2 * ki + (mask == full ? 0 : 1);
+}
+
+template <int KIND, int R, uint32_t MASK>
+__device__ __forceinline__ void layer_store(const SweepCtx &c, bool vec, int saddr, const int (&gs)[R],
+                                            float2 (&a)[1 << R], const float2 *k0, const Grp<R> &G, float scale) {
+    layer_fixed<KIND, R, MASK>(a, k0, G);
+    if constexpr (KIND == MK_H) {
+        const float2 sc = make_float2(scale, scale);
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j) a[j] = __fmul2_rn(a[j], sc);
+    }
+    sweep_store<R>(c, vec, saddr, gs, a);
+}
+
 template <int R, int NT, int KS = KS_ALL>
 __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int sidx) {
     int gs[R];
@@ -559,6 +623,8 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
     const uint64_t *tg = c.tab_g + sidx * kItemTab;
     const int op_begin = S.op_begin, op_end = S.op_end;
     const float scale = S.scale;
+    const int fast = KS == KS_LAYER ? straight_code<R>(c, op_begin, op_end, scale) : 0;
+    const float2 *k0f = c.cs + c.micro[op_begin].cst;
     for (int item = threadIdx.x; item < n_items; item += NT) {
         const int i0 = item & 31, i1 = 32 + ((item >> 5) & 31), i2 = 64 + ((item >> 10) & 15);
         const int saddr = ts[i0] ^ ts[i1] ^ ts[i2];
@@ -567,21 +633,27 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
         auto gbase = [&]() { return c.tile_gbase | tg[i0] | tg[i1] | tg[i2]; };
         float2 a[1 << R];
         sweep_load<R>(c, vec, saddr, gs, a);
+        if constexpr (R == 4 && KS == KS_LAYER) {
+            if (fast) {
+                constexpr uint32_t F = (1u << R) - 1, HI = F & ~1u;
+                switch (fast) {
+                    case 1: layer_store<MK_U1, R, F>(c, vec, saddr, gs, a, k0f, G, scale); break;
+                    case 2: layer_store<MK_U1, R, HI>(c, vec, saddr, gs, a, k0f, G, scale); break;
+                    case 3: layer_store<MK_H, R, F>(c, vec, saddr, gs, a, k0f, G, scale); break;
+                    case 4: layer_store<MK_H, R, HI>(c, vec, saddr, gs, a, k0f, G, scale); break;
+                    case 5: layer_store<MK_RXC, R, F>(c, vec, saddr, gs, a, k0f, G, scale); break;
+                    case 6: layer_store<MK_RXC, R, HI>(c, vec, saddr, gs, a, k0f, G, scale); break;
+                    case 7: layer_store<MK_U1R, R, F>(c, vec, saddr, gs, a, k0f, G, scale); break;
+                    default: layer_store<MK_U1R, R, HI>(c, vec, saddr, gs, a, k0f, G, scale); break;
+                }
+                continue;
+            }
+        }
         for (int oi = op_begin; oi < op_end; ++oi) {
             const MicroOp &op = c.micro[oi];
             if constexpr (KS == KS_LAYER) {
                 switch (op.kind) {
-                    case MK_LAYER: {
-                        const float2 *k0 = c.cs + op.cst;
-                        const uint32_t mask = (uint32_t)op.b;
-                        switch (op.a) {
-                            case MK_RXC: layer_rxc<R>(a, k0, mask); break;
-                            case MK_U1R: layer_u1r<R>(a, k0, mask); break;
-                            case MK_U1: layer_u1<R>(a, k0, mask, G); break;
-                            default: layer_h<R>(a, mask); break;
-                        }
-                        break;
-                    }
+                    case MK_LAYER: run_layer<R>(op.a, a, c.cs + op.cst, (uint32_t)op.b, G); break;
                     case MK_RXC: disp_rxc<R>(op.a, a, c.cs + op.cst); break;
                     case MK_U1R: disp_u1r<R>(op.a, a, c.cs + op.cst); break;
                     case MK_H: disp_h<R>(op.a, a); break;
@@ -613,17 +685,7 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
                         disp_qft<R>(op.a, a, c.cs + op.cst, w);
                         break;
                     }
-                    case MK_LAYER: {
-                        const float2 *k0 = c.cs + op.cst;
-                        const uint32_t mask = (uint32_t)op.b;
-                        switch (op.a) {
-                            case MK_RXC: layer_rxc<R>(a, k0, mask); break;
-                            case MK_U1R: layer_u1r<R>(a, k0, mask); break;
-                            case MK_U1: layer_u1<R>(a, k0, mask, G); break;
-                            default: layer_h<R>(a, mask); break;
-                        }
-                        break;
-                    }
+                    case MK_LAYER: run_layer<R>(op.a, a, c.cs + op.cst, (uint32_t)op.b, G); break;
                     case MK_QFTL:
                         layer_qft<R>(a, c.cs + op.cst, (uint32_t)op.b, op.cmask, gbase(), c.roots);
                         break;
