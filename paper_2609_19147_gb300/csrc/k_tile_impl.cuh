@@ -214,8 +214,9 @@ __device__ __forceinline__ void op_rxc(float2 (&a)[1 << R], const float2 *cs) {
 // amplitude; the same roundings as the scalar FMUL + FFMA)
 template <int R, int M>
 __device__ __forceinline__ void op_u1r(float2 (&a)[1 << R], const float2 *cs) {
-    const float2 m00 = make_float2(cs[0].x, cs[0].x), m01 = make_float2(cs[0].y, cs[0].y);
-    const float2 m10 = make_float2(cs[1].x, cs[1].x), m11 = make_float2(cs[1].y, cs[1].y);
+    // the four entries are stored as packed pairs (m, m): no register moves
+    const float2 m00 = cs[0], m01 = cs[1];
+    const float2 m10 = cs[2], m11 = cs[3];
 #pragma unroll
     for (int j = 0; j < (1 << R); ++j) {
         if ((j >> M) & 1) continue;
@@ -335,7 +336,7 @@ __device__ __forceinline__ void disp_u2(int ma, int mb, float2 (&a)[1 << R], con
 }
 
 // layers: the same 2x2 family on every group bit in `mask`; the coefficients
-// of group bit M sit at k0 + stride * M (RXC 1, U1R 2, U1 4, H none)
+// of group bit M sit at k0 + stride * M (RXC 1, U1R 4, U1 4, H none)
 template <int KIND>
 struct LayerOp;
 template <>
@@ -349,7 +350,7 @@ template <>
 struct LayerOp<MK_U1R> {
     template <int R, int M>
     static __device__ __forceinline__ void run(float2 (&a)[1 << R], const float2 *k0, const Grp<R> &) {
-        op_u1r<R, M>(a, k0 + 2 * M);
+        op_u1r<R, M>(a, k0 + 4 * M);
     }
 };
 template <>
@@ -428,10 +429,6 @@ struct SweepCtx {
     uint64_t tile_gbase;     // global index of tile-local 0 (within the state)
 };
 
-__device__ __forceinline__ uint64_t glob_contrib(const SweepCtx &c, int tb) {
-    return tb < c.L ? (1ull << tb) : (1ull << c.hb[tb - c.L]);
-}
-
 template <int R>
 __device__ __forceinline__ void sweep_load(const SweepCtx &c, bool vec, int saddr, const int (&gs)[R],
                                            float2 (&a)[1 << R]) {
@@ -479,6 +476,43 @@ __device__ __forceinline__ void sweep_store(const SweepCtx &c, bool vec, int sad
                 if ((j >> m) & 1) o ^= gs[m];
             c.buf[o] = a[j];
         }
+    }
+}
+
+// the item's element offsets, computed once for both the load and the store
+template <int R>
+__device__ __forceinline__ void group_offsets(int saddr, const int (&gs)[R], int (&o)[1 << R]) {
+    o[0] = saddr;
+#pragma unroll
+    for (int m = 0; m < R; ++m)
+#pragma unroll
+        for (int j = 0; j < (1 << m); ++j) o[j | (1 << m)] = o[j] ^ gs[m];
+}
+
+template <int R>
+__device__ __forceinline__ void load_at(const SweepCtx &c, bool vec, const int (&o)[1 << R], float2 (&a)[1 << R]) {
+    if (vec) {
+#pragma unroll
+        for (int j = 0; j < (1 << R); j += 2) {
+            const float4 v = *reinterpret_cast<const float4 *>(c.buf + o[j]);
+            a[j] = make_float2(v.x, v.y);
+            a[j + 1] = make_float2(v.z, v.w);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j) a[j] = c.buf[o[j]];
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void store_at(const SweepCtx &c, bool vec, const int (&o)[1 << R], const float2 (&a)[1 << R]) {
+    if (vec) {
+#pragma unroll
+        for (int j = 0; j < (1 << R); j += 2)
+            *reinterpret_cast<float4 *>(c.buf + o[j]) = make_float4(a[j].x, a[j].y, a[j + 1].x, a[j + 1].y);
+    } else {
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j) c.buf[o[j]] = a[j];
     }
 }
 
@@ -596,7 +630,7 @@ __device__ __forceinline__ int straight_code(const SweepCtx &c, int op_begin, in
 }
 
 template <int KIND, int R, uint32_t MASK>
-__device__ __forceinline__ void layer_store(const SweepCtx &c, bool vec, int saddr, const int (&gs)[R],
+__device__ __forceinline__ void layer_store(const SweepCtx &c, bool vec, const int (&o)[1 << R],
                                             float2 (&a)[1 << R], const float2 *k0, const Grp<R> &G, float scale) {
     layer_fixed<KIND, R, MASK>(a, k0, G);
     if constexpr (KIND == MK_H) {
@@ -604,23 +638,23 @@ __device__ __forceinline__ void layer_store(const SweepCtx &c, bool vec, int sad
 #pragma unroll
         for (int j = 0; j < (1 << R); ++j) a[j] = __fmul2_rn(a[j], sc);
     }
-    sweep_store<R>(c, vec, saddr, gs, a);
+    store_at<R>(c, vec, o, a);
 }
 
 template <int R, int NT, int KS = KS_ALL>
 __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int sidx) {
+    const int *ts = c.tab_s + sidx * kItemTab;
+    const uint64_t *tg = c.tab_g + sidx * kItemTab;
     int gs[R];
-    Grp<R> G;
+    Grp<R> G0;   // global-index bit of each group bit (read by controlled ops and diagonals)
 #pragma unroll
     for (int m = 0; m < R; ++m) {
-        gs[m] = c.contrib[S.gbit[m]];
-        G.gg[m] = glob_contrib(c, S.gbit[m]);
+        gs[m] = ts[kItemTab - kGroupTab + m];
+        G0.gg[m] = KS == KS_LAYER ? 0ull : tg[kItemTab - kGroupTab + m];
     }
     const int nb = c.T - R;
     const int n_items = 1 << nb;
     const bool vec = S.vec != 0;
-    const int *ts = c.tab_s + sidx * kItemTab;
-    const uint64_t *tg = c.tab_g + sidx * kItemTab;
     const int op_begin = S.op_begin, op_end = S.op_end;
     const float scale = S.scale;
     const int fast = KS == KS_LAYER ? straight_code<R>(c, op_begin, op_end, scale) : 0;
@@ -632,23 +666,32 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
         // diagonals and QFT twiddles read it)
         auto gbase = [&]() { return c.tile_gbase | tg[i0] | tg[i1] | tg[i2]; };
         float2 a[1 << R];
-        sweep_load<R>(c, vec, saddr, gs, a);
+        Grp<R> G = G0;
         if constexpr (R == 4 && KS == KS_LAYER) {
             if (fast) {
+                int o[1 << R];
+                group_offsets<R>(saddr, gs, o);
+                load_at<R>(c, vec, o, a);
                 constexpr uint32_t F = (1u << R) - 1, HI = F & ~1u;
                 switch (fast) {
-                    case 1: layer_store<MK_U1, R, F>(c, vec, saddr, gs, a, k0f, G, scale); break;
-                    case 2: layer_store<MK_U1, R, HI>(c, vec, saddr, gs, a, k0f, G, scale); break;
-                    case 3: layer_store<MK_H, R, F>(c, vec, saddr, gs, a, k0f, G, scale); break;
-                    case 4: layer_store<MK_H, R, HI>(c, vec, saddr, gs, a, k0f, G, scale); break;
-                    case 5: layer_store<MK_RXC, R, F>(c, vec, saddr, gs, a, k0f, G, scale); break;
-                    case 6: layer_store<MK_RXC, R, HI>(c, vec, saddr, gs, a, k0f, G, scale); break;
-                    case 7: layer_store<MK_U1R, R, F>(c, vec, saddr, gs, a, k0f, G, scale); break;
-                    default: layer_store<MK_U1R, R, HI>(c, vec, saddr, gs, a, k0f, G, scale); break;
+                    case 1: layer_store<MK_U1, R, F>(c, vec, o, a, k0f, G, scale); break;
+                    case 2: layer_store<MK_U1, R, HI>(c, vec, o, a, k0f, G, scale); break;
+                    case 3: layer_store<MK_H, R, F>(c, vec, o, a, k0f, G, scale); break;
+                    case 4: layer_store<MK_H, R, HI>(c, vec, o, a, k0f, G, scale); break;
+                    case 5: layer_store<MK_RXC, R, F>(c, vec, o, a, k0f, G, scale); break;
+                    case 6: layer_store<MK_RXC, R, HI>(c, vec, o, a, k0f, G, scale); break;
+                    case 7: layer_store<MK_U1R, R, F>(c, vec, o, a, k0f, G, scale); break;
+                    default: layer_store<MK_U1R, R, HI>(c, vec, o, a, k0f, G, scale); break;
                 }
                 continue;
             }
         }
+        if constexpr (KS == KS_LAYER) {
+            // loaded here: the straight-line layers above never read them
+#pragma unroll
+            for (int m = 0; m < R; ++m) G.gg[m] = tg[kItemTab - kGroupTab + m];
+        }
+        sweep_load<R>(c, vec, saddr, gs, a);
         for (int oi = op_begin; oi < op_end; ++oi) {
             const MicroOp &op = c.micro[oi];
             if constexpr (KS == KS_LAYER) {
@@ -1037,6 +1080,14 @@ __global__ void __launch_bounds__(NT, MINB)
     // shared-memory offsets and OR of the global index bits of those tile bits
     for (int e = tid; e < n_sweeps * kItemTab; e += NT) {
         const int sw = e / kItemTab, idx = e - sw * kItemTab;
+        if (idx >= kItemTab - kGroupTab) {
+            // the sweep's group bits
+            const int m = idx - (kItemTab - kGroupTab);
+            const int tb = m < s_sweeps[sw].r ? s_sweeps[sw].gbit[m] : -1;
+            s_tab_s[e] = tb < 0 ? 0 : s_contrib[tb];
+            s_tab_g[e] = tb < 0 ? 0ull : (tb < L ? (1ull << tb) : (1ull << s_hb[tb - L]));
+            continue;
+        }
         const int part = idx < 32 ? 0 : (idx < 64 ? 1 : 2);
         const int v = idx - 32 * part;
         const int nb = T - s_sweeps[sw].r;

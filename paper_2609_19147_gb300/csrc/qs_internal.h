@@ -74,7 +74,9 @@ enum MicroKind : int32_t {
                   // exp(i pi x_p (x & bits[lo, p)) / 2^p); group part at cst
     MK_H = 4,     // Hadamard on group bit a (sign-only butterfly)
     MK_RXC = 5,   // [[c, i s], [i s, c]] on group bit a (RX family): consts c, s
-    MK_U1R = 6,   // real 2x2 on group bit a (RY family): consts m00, m01, m10, m11
+    MK_U1R = 6,   // real 2x2 on group bit a (RY family): consts (m00, m00), (m01, m01),
+                  // (m10, m10), (m11, m11) at an even offset (two 16-byte loads, each
+                  // entry already the packed FP32x2 operand)
     MK_LAYER = 7, // commuting 2x2 ops of one kind (a = MK_RXC / MK_U1R / MK_U1 / MK_H)
                   // on the group bits in mask b; constants per bit m at cst + m * stride
     MK_QFTL = 8,  // QFT stages (ladders down to bit 0) on the group bits in mask b,
@@ -88,8 +90,11 @@ enum MicroKind : int32_t {
 };
 constexpr int kMaxCouple = 16;
 
-// item-address tables per sweep (shared memory): item bits 0-4, 5-9, 10-13
-constexpr int kItemTab = 32 + 32 + 16;
+// item-address tables per sweep (shared memory): item bits 0-4, 5-9, 10-13,
+// then the sweep's group bits (kGroupTab entries: shared-memory offset and
+// global index bit of group bit m)
+constexpr int kGroupTab = 8;
+constexpr int kItemTab = 32 + 32 + 16 + kGroupTab;
 
 struct MicroOp {
     int32_t kind;

@@ -1087,7 +1087,7 @@ OpCost op_cost(int n, const FOp &f, int R, const DiagPlan *dp, int dprec) {
     OpCost c;
     switch (f.kind) {
         case F_DENSE: c.n_const = dense_const_size(dprec) + 1; break;   // + alignment padding
-        case F_U1: c.n_const = 4; break;
+        case F_U1: c.n_const = 5; break;   // 4 entries + the even-offset pad of the real form
         case F_U2: c.n_const = 16; break;
         case F_QFT: c.n_const = 1 << R; break;
         case F_DIAG:
@@ -1507,8 +1507,12 @@ struct PassBuilder {
                         cst.push_back(float2{(float)m[0].real(), (float)m[1].imag()});
                     } else if (real) {
                         mo.kind = MK_U1R;
-                        cst.push_back(float2{(float)m[0].real(), (float)m[1].real()});
-                        cst.push_back(float2{(float)m[2].real(), (float)m[3].real()});
+                        if (cst.size() & 1) cst.push_back(float2{0.f, 0.f});
+                        mo.cst = (int)cst.size();
+                        for (int e = 0; e < 4; ++e) {
+                            const float v = (float)m[e].real();
+                            cst.push_back(float2{v, v});
+                        }
                     } else {
                         mo.kind = MK_U1;
                         for (int e = 0; e < 4; ++e) {
@@ -1705,13 +1709,14 @@ struct PassBuilder {
                         mask |= 1u << tp.micro[j].a;
                         ++j;
                     }
-                    const int stride = lk == MK_RXC ? 1 : lk == MK_U1R ? 2 : lk == MK_U1 ? 4 : 0;
-                    if (j - i >= 2 && (int)cst.size() + R * stride <= kMaxConst) {
+                    const int stride = lk == MK_RXC ? 1 : lk == MK_U1R ? 4 : lk == MK_U1 ? 4 : 0;
+                    if (j - i >= 2 && (int)cst.size() + R * stride + 1 <= kMaxConst) {
                         MicroOp L;
                         std::memset(&L, 0, sizeof L);
                         L.kind = MK_LAYER;
                         L.a = lk;
                         L.b = (int)mask;
+                        if (lk == MK_U1R && (cst.size() & 1)) cst.push_back(float2{0.f, 0.f});
                         L.cst = (int)cst.size();
                         for (int m = 0; m < R * stride; ++m) cst.push_back(float2{0.f, 0.f});
                         for (int k = i; k < j; ++k) {
