@@ -219,6 +219,28 @@ typedef struct qs_graph {
 qs_status qs_qaoa_maxcut(const qs_graph *graphs, size_t n_graphs, int n_sets, int p, const double *gammas,
                          const double *betas, double *out, void *cuda_stream);
 
+/* Autotuner for the fused executor's tile passes (the tile shape, qubits per
+ * pass and register-group depth that the kernels of Sec. 5 are built
+ * around): applies the circuit to a private copy of the state under each
+ * candidate configuration -- tile_qubits T in {12, 13}, low_qubits L in
+ * {4, 5}, group_qubits R in {4, 5} (R = 5 only with dense blocks), and the
+ * planner's own choice (all three 0) -- one untimed call, then `reps` calls
+ * timed with CUDA events on the state's stream, and writes the fastest into
+ * *best (the remaining fields copied from *base, which may be NULL) and its
+ * milliseconds per call into *best_ms (may be NULL).  The state's amplitudes
+ * are left unchanged.  A choice is kept per (GPU name, n, batch, gate
+ * structure -- kinds, wires and parameter slots, not angle values -- and
+ * dense settings); repeating a request returns the kept choice without
+ * timing anything (*best_ms = the time measured then).  cache_path (may be
+ * NULL) names a text file of earlier choices, one per line, read on first
+ * use and appended to after each new measurement.  Needs device memory for
+ * one more copy of the state (and its scratch buffer if the plan has
+ * permutation passes); synchronises the state's stream.  Errors:
+ * QS_ERR_INVALID_ARG (NULL st or best, reps outside [1, 100], base->mode not
+ * QS_MODE_FUSED, invalid gates or parameters), QS_ERR_OOM, QS_ERR_CUDA. */
+qs_status qs_autotune(qs_state *st, const qs_gate *gates, size_t n_gates, const double *params, int n_params,
+                      const qs_opts *base, int reps, const char *cache_path, qs_opts *best, double *best_ms);
+
 /* Test hook: write the detector's plan for an n-qubit circuit as text
  * (one line per pass: family, qubits, op count) into buf (NUL-terminated,
  * truncated to len).  Needs no GPU.  *passes (if non-NULL) receives the

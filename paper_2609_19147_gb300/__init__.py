@@ -87,6 +87,8 @@ _SIGS = {
     "qs_profile_read": ([_vp, ctypes.POINTER(QsProfileRecord), _i32, ctypes.POINTER(_i32)], _i32),
     "qs_expect_noalloc": ([_vp, _i32, _i32, ctypes.POINTER(QsPauli), _sz, _dp, _vp], _i32),
     "qs_qaoa_maxcut": ([ctypes.POINTER(QsGraph), _sz, _i32, _i32, _dp, _dp, _dp, _vp], _i32),
+    "qs_autotune": ([_vp, ctypes.POINTER(QsGate), _sz, _dp, _i32, ctypes.POINTER(QsOpts), _i32, ctypes.c_char_p,
+                     ctypes.POINTER(QsOpts), _dp], _i32),
     "qs_last_error": ([], ctypes.c_char_p),
     "qs_version": ([], ctypes.c_char_p),
 }
@@ -234,6 +236,26 @@ class State:
                                          ctypes.byref(o)))
         else:
             _check(_lib.qs_apply_circuit(self.h, cg.arr, cg.n, None, 0, ctypes.byref(o)))
+
+    def autotune(self, gates, params: Optional[np.ndarray] = None, reps: int = 2, cache_path: Optional[str] = None,
+                 dense=None, block_qubits: int = 0) -> dict:
+        """Time the circuit under the candidate tile shapes on a copy of this
+        state (the state is unchanged) and return the fastest as keyword
+        arguments for apply(), plus 'ms' (milliseconds per call)."""
+        cg = gates if isinstance(gates, CGates) else CGates(gates)
+        base = _opts("fused", 0, 0, 0, dense, block_qubits)
+        out = QsOpts()
+        ms = ctypes.c_double(0.0)
+        cp = cache_path.encode() if cache_path else None
+        if params is not None:
+            p = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(self.batch, -1))
+            _check(_lib.qs_autotune(self.h, cg.arr, cg.n, p.ctypes.data_as(_dp), p.shape[1], ctypes.byref(base),
+                                    int(reps), cp, ctypes.byref(out), ctypes.byref(ms)))
+        else:
+            _check(_lib.qs_autotune(self.h, cg.arr, cg.n, None, 0, ctypes.byref(base), int(reps), cp,
+                                    ctypes.byref(out), ctypes.byref(ms)))
+        return {"tile_qubits": out.tile_qubits, "low_qubits": out.low_qubits, "group_qubits": out.group_qubits,
+                "ms": ms.value}
 
     def expect(self, terms) -> np.ndarray:
         arr, k = _paulis(terms)

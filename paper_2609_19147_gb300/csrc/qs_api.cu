@@ -636,6 +636,35 @@ qs_status ensure_terms(qs_state *st, size_t n) {
     return QS_OK;
 }
 
+// <psi_b| sum_k coeff_k Z^{z_k} |psi_b> for every batch item b (terms with
+// x = 0, 1..256 of them) into d_dst[2 b] (real part; d_dst[2 b + 1] = 0),
+// enqueued on the state's stream without waiting for the result.
+qs_status diag_expect_async(qs_state *st, const std::vector<PauliDev> &hz, double *d_dst) {
+    const int B = st->batch;
+    const int grid = std::max(1, std::min<int>((int)((st->elems / 2 + 255) / 256), g_num_sms[st->dev] * 4));
+    qs_status s = ensure_partial(st, (size_t)B * grid * 2);
+    if (s == QS_OK) s = ensure_terms(st, hz.size());
+    if (s != QS_OK) return s;
+    QS_CUDA(cudaMemcpyAsync(st->d_terms, hz.data(), hz.size() * sizeof(PauliDev), cudaMemcpyHostToDevice,
+                            st->stream));
+    DiagExpectArgs A;
+    std::memset(&A, 0, sizeof A);
+    A.psi = st->home;
+    A.elems = st->elems;
+    A.bstride = st->elems;
+    A.batch = B;
+    A.n_terms = (int)hz.size();
+    A.terms = st->d_terms;
+    A.partial = st->d_partial;
+    A.grid = grid;
+    cudaEvent_t ev;
+    prof_begin(st, &ev);
+    QS_CUDA(launch_diag_expect(A, st->stream));
+    prof_end(st, ev, "diag_expect", 8.0 * (double)st->elems * B);
+    QS_CUDA(launch_expect_finish(st->d_partial, d_dst, B, grid, 1, st->stream));
+    return QS_OK;
+}
+
 // Pauli terms in index-bit space
 struct TermIdx {
     double coeff;
@@ -1023,30 +1052,11 @@ qs_status qs_expect(qs_state *st, const qs_pauli *terms, size_t n_terms, double 
     }
     if (!dz.empty()) {
         const int B = st->batch;
-        const int grid = std::max(1, std::min<int>((int)((st->elems / 2 + 255) / 256), g_num_sms[st->dev] * 4));
-        s = ensure_partial(st, (size_t)B * grid * 2);
-        if (s == QS_OK) s = ensure_out(st, (size_t)B * 2);
-        if (s == QS_OK) s = ensure_terms(st, dz.size());
-        if (s != QS_OK) return s;
         std::vector<PauliDev> hz;
         for (auto &x : dz) hz.push_back({x.coeff, 0, x.z});
-        QS_CUDA(cudaMemcpyAsync(st->d_terms, hz.data(), hz.size() * sizeof(PauliDev), cudaMemcpyHostToDevice,
-                                st->stream));
-        DiagExpectArgs A;
-        std::memset(&A, 0, sizeof A);
-        A.psi = st->home;
-        A.elems = st->elems;
-        A.bstride = st->elems;
-        A.batch = B;
-        A.n_terms = (int)hz.size();
-        A.terms = st->d_terms;
-        A.partial = st->d_partial;
-        A.grid = grid;
-        cudaEvent_t ev;
-        prof_begin(st, &ev);
-        QS_CUDA(launch_diag_expect(A, st->stream));
-        prof_end(st, ev, "diag_expect", 8.0 * (double)st->elems * B);
-        QS_CUDA(launch_expect_finish(st->d_partial, st->d_out, B, grid, 1, st->stream));
+        s = ensure_out(st, (size_t)B * 2);
+        if (s == QS_OK) s = diag_expect_async(st, hz, st->d_out);
+        if (s != QS_OK) return s;
         std::vector<double> r((size_t)B * 2);
         QS_CUDA(cudaMemcpyAsync(r.data(), st->d_out, r.size() * sizeof(double), cudaMemcpyDeviceToHost, st->stream));
         QS_CUDA(cudaStreamSynchronize(st->stream));
@@ -1664,8 +1674,18 @@ qs_status qs_qaoa_maxcut(const qs_graph *graphs, size_t n_graphs, int n_sets, in
     }
 
     // ---- larger states: fused tile passes, all angle sets of a graph as one batch ----
+    // Everything is enqueued on one stream and the results stay on the device
+    // until the end, so the host plans graph g + 1 while the GPU runs graph g.
     std::map<int, qs_state *> states;
     qs_status rs = QS_OK;
+    size_t n_large = 0;
+    for (size_t g = 0; g < n_graphs; ++g)
+        if (graphs[g].n > kQaoaMaxSmallN) ++n_large;
+    double *d_res = nullptr;   // (re, im) per (graph, angle set)
+    if (n_large && cudaMalloc(&d_res, n_out * 2 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QS_ERR_OOM, "qs_qaoa_maxcut: device allocation failed");
+    }
     for (size_t g = 0; g < n_graphs && rs == QS_OK; ++g) {
         const qs_graph &G = graphs[g];
         if (G.n <= kQaoaMaxSmallN) continue;
@@ -1700,13 +1720,30 @@ qs_status qs_qaoa_maxcut(const qs_graph *graphs, size_t n_graphs, int n_sets, in
                 prm[(size_t)a * 2 * p + 2 * l] = -gammas[(g * n_sets + a) * p + l];
                 prm[(size_t)a * 2 * p + 2 * l + 1] = 2.0 * betas[(g * n_sets + a) * p + l];
             }
-        std::vector<qs_pauli> terms;
-        terms.push_back({0.5 * G.n_edges, 0, 0});
+        // <H_C> = |E| / 2 - 1/2 sum_edges <Z_u Z_v>: Z-only terms (index bit of qubit q is n - 1 - q)
+        std::vector<PauliDev> hz;
+        hz.push_back({0.5 * G.n_edges, 0, 0});
         for (int e = 0; e < G.n_edges; ++e)
-            terms.push_back({-0.5, 0, (1ull << G.edges[2 * e]) | (1ull << G.edges[2 * e + 1])});
+            hz.push_back({-0.5, 0, (1ull << (G.n - 1 - G.edges[2 * e])) | (1ull << (G.n - 1 - G.edges[2 * e + 1]))});
         rs = qs_init_zero(S);
         if (rs == QS_OK) rs = qs_apply_circuit(S, gl.data(), gl.size(), prm.data(), 2 * p, nullptr);
-        if (rs == QS_OK) rs = qs_expect(S, terms.data(), terms.size(), out + g * n_sets);
+        if (rs == QS_OK) rs = diag_expect_async(S, hz, d_res + g * n_sets * 2);
+    }
+    if (rs == QS_OK && n_large) {
+        std::vector<double> r(n_out * 2);
+        cudaError_t e = cudaMemcpyAsync(r.data(), d_res, r.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rs = fail(QS_ERR_CUDA, std::string("qaoa results: ") + cudaGetErrorString(e));
+        for (auto &kv : states)
+            if (rs == QS_OK) rs = check_err_word(kv.second);
+        if (rs == QS_OK)
+            for (size_t g = 0; g < n_graphs; ++g)
+                if (graphs[g].n > kQaoaMaxSmallN)
+                    for (int a = 0; a < n_sets; ++a) out[g * n_sets + a] = r[(g * n_sets + a) * 2];
+    }
+    if (d_res) {
+        cudaStreamSynchronize(st);
+        cudaFree(d_res);
     }
     for (auto &kv : states) qs_free(kv.second);
     return rs;
@@ -1775,3 +1812,178 @@ qs_status qs_profile_read(qs_state *st, qs_profile_record *out, int cap, int *co
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+namespace {
+struct TuneChoice {
+    int T = 0, L = 0, R = 0;
+    double ms = 0.0;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune;   // key -> choice
+std::map<std::string, bool> g_tune_files;   // cache files already read
+
+std::string gpu_name(int dev) {
+    cudaDeviceProp pr;
+    if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return "unknown";
+    }
+    std::string s(pr.name);
+    for (char &ch : s)
+        if (ch == ' ' || ch == '\t') ch = '_';
+    return s;
+}
+
+// structure of a circuit: kinds, wires and parameter slots (not angle values)
+uint64_t gate_structure_key(const qs_gate *g, size_t n_gates) {
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n_gates; ++i) {
+        const int32_t rec[6] = {g[i].kind, g[i].nw, g[i].w[0], g[i].nw > 1 ? g[i].w[1] : -1,
+                                g[i].nw > 2 ? g[i].w[2] : -1, g[i].param_idx >= 0 ? g[i].param_idx : -1};
+        h = fnv1a(rec, sizeof rec, h);
+    }
+    return h;
+}
+
+void read_tune_file(const std::string &path) {
+    if (g_tune_files.count(path)) return;
+    g_tune_files[path] = true;
+    FILE *f = std::fopen(path.c_str(), "r");
+    if (!f) return;
+    char line[512];
+    while (std::fgets(line, sizeof line, f)) {
+        char tag[32], key[400];
+        TuneChoice c;
+        // "qs-autotune <key with '|' separators> T L R ms"
+        if (std::sscanf(line, "%31s %399s %d %d %d %lf", tag, key, &c.T, &c.L, &c.R, &c.ms) == 6 &&
+            std::strcmp(tag, "qs-autotune") == 0)
+            g_tune[key] = c;
+    }
+    std::fclose(f);
+}
+}  // namespace
+
+extern "C" qs_status qs_autotune(qs_state *st, const qs_gate *gates, size_t n_gates, const double *params,
+                                 int n_params, const qs_opts *base, int reps, const char *cache_path, qs_opts *best,
+                                 double *best_ms) {
+    if (!st || !best) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+    if (reps < 1 || reps > 100) return fail(QS_ERR_INVALID_ARG, "reps must be in [1, 100]");
+    if (n_gates && !gates) return fail(QS_ERR_INVALID_ARG, "gates == NULL");
+    const qs_opts b = default_opts(base);
+    if (b.mode != QS_MODE_FUSED) return fail(QS_ERR_INVALID_ARG, "the autotuner tunes the fused executor");
+    {   // validate before allocating anything
+        std::vector<RGate> rg;
+        std::string err;
+        const int items = params && has_param_gates(gates, n_gates) ? st->batch : 1;
+        for (int bi = 0; bi < items; ++bi) {
+            qs_status s = resolve_gates(st->n, gates, n_gates, params, n_params, bi, rg, err);
+            if (s != QS_OK) return fail(s, err);
+        }
+    }
+    char kbuf[400];
+    std::snprintf(kbuf, sizeof kbuf, "%s|n%d|b%d|g%016llx|d%d|k%d", gpu_name(st->dev).c_str(), st->n, st->batch,
+                  (unsigned long long)gate_structure_key(gates, n_gates), b.dense_prec, b.block_qubits);
+    const std::string key(kbuf);
+    auto fill = [&](const TuneChoice &c) {
+        *best = b;
+        best->tile_qubits = c.T;
+        best->low_qubits = c.L;
+        best->group_qubits = c.R;
+        if (best_ms) *best_ms = c.ms;
+    };
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (cache_path) read_tune_file(cache_path);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            fill(it->second);
+            return QS_OK;
+        }
+    }
+    // candidates: the planner's choice first, then the explicit shapes
+    std::vector<std::array<int, 3>> cand;
+    cand.push_back({0, 0, 0});
+    const int Rs[2] = {4, 5};
+    for (int T : {12, 13})
+        for (int L : {4, 5})
+            for (int R : Rs) {
+                if (b.dense_prec != QS_DENSE_OFF && R != 5) continue;
+                const int t = std::min(T, st->n), l = std::min(L, t), r = std::min(R, t);
+                std::array<int, 3> c = {t, l, r};
+                if (std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
+            }
+    // a private copy of the state, on the same stream
+    QS_CUDA(cudaStreamSynchronize(st->stream));
+    qs_state *tr = nullptr;
+    qs_status s = qs_alloc(st->n, st->batch, &tr);
+    if (s != QS_OK) return s;
+    cudaStreamSynchronize(nullptr);
+    tr->stream = st->stream;
+    const size_t bytes = (size_t)st->elems * st->batch * sizeof(float2);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TuneChoice win;
+    bool have = false;
+    cudaError_t ce = cudaMemcpyAsync(tr->home, st->home, bytes, cudaMemcpyDeviceToDevice, st->stream);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) s = fail(QS_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
+    for (size_t i = 0; i < cand.size() && s == QS_OK; ++i) {
+        qs_opts o = b;
+        o.tile_qubits = cand[i][0];
+        o.low_qubits = cand[i][1];
+        o.group_qubits = cand[i][2];
+        qs_status r = qs_apply_circuit(tr, gates, n_gates, params, n_params, &o);
+        // a shape this circuit cannot use (the gates themselves were validated above)
+        if (r == QS_ERR_INTERNAL || r == QS_ERR_UNSUPPORTED || (r == QS_ERR_INVALID_ARG && i > 0)) continue;
+        if (r != QS_OK) {
+            s = r;
+            break;
+        }
+        cudaEventRecord(e0, tr->stream);
+        for (int k = 0; k < reps && r == QS_OK; ++k) r = qs_apply_circuit(tr, gates, n_gates, params, n_params, &o);
+        cudaEventRecord(e1, tr->stream);
+        ce = cudaEventSynchronize(e1);
+        if (r != QS_OK) {
+            s = r;
+            break;
+        }
+        if (ce != cudaSuccess) {
+            s = fail(QS_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = (double)ms / reps;
+        if (!have || per < win.ms) {
+            win.T = cand[i][0];
+            win.L = cand[i][1];
+            win.R = cand[i][2];
+            win.ms = per;
+            have = true;
+        }
+    }
+    if (s == QS_OK) s = check_err_word(tr);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(st->stream);
+    tr->stream = nullptr;
+    qs_free(tr);
+    if (s != QS_OK) return s;
+    if (!have) return fail(QS_ERR_INTERNAL, "autotune: no candidate configuration could run");
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = win;
+        if (cache_path) {
+            FILE *f = std::fopen(cache_path, "a");
+            if (f) {
+                std::fprintf(f, "qs-autotune %s %d %d %d %.6f\n", key.c_str(), win.T, win.L, win.R, win.ms);
+                std::fclose(f);
+            }
+        }
+    }
+    fill(win);
+    return QS_OK;
+}
