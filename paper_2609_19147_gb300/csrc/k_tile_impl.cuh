@@ -11,11 +11,13 @@
 // box of extent 1 in every gap).  When the bit set needs more than 5 dims the
 // pass falls back to one bulk copy per 2^L-amplitude row.
 //
-// Tiles rotate through 2-6 shared buffers: while the warps process tile k,
+// Tiles rotate through 1-6 shared buffers: while the warps process tile k,
 // the loads of the next tiles and the stores of the previous ones are in
 // flight.  Thread 0 issues the copies; the buffer it refills was stored
 // NB - D tiles ago (D = tiles loaded ahead), so waiting for that store to
-// have read shared memory rarely stalls.
+// have read shared memory rarely stalls.  With one buffer (D = 0, two CTAs
+// per SM) a tile is loaded once the previous store has read the buffer, and
+// the SM's other CTA computes meanwhile.
 //
 // Passes with dense-block sweeps and passes whose micro-ops are all 1q-layer
 // or diagonal ops run in their own instantiations (DENSE, KS), which keeps

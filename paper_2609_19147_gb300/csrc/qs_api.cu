@@ -357,15 +357,26 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     const int buf_bytes = 8 << tp.T;
     off = al(off, 1024);
     A.off_buf0 = off;
-    // two co-resident CTAs per SM for 12-bit tiles with 4-bit groups: one
-    // computes while the other waits on its copies
-    A.ctas_per_sm = (tp.T == 12 && tp.R == 4) ? 2 : 1;
-    const int limit = (A.ctas_per_sm == 2 ? 113 * 1024 : 227 * 1024) - 1024;   // 1 KB for the base alignment
-    // as many tile buffers as fit (<= 6)
-    A.n_buf = std::min(A.ctas_per_sm == 2 ? 3 : 6, (limit - off) / buf_bytes);
-    if (A.n_buf > kMaxTileBuffers) A.n_buf = kMaxTileBuffers;
-    if (A.n_buf < 2) return fail(QS_ERR_INTERNAL, "tile pass needs too much shared memory");
-    A.prefetch = std::max(1, A.n_buf - 2);
+    // Two co-resident CTAs per SM for 4-bit groups on 12- and 13-bit tiles:
+    // while one CTA's warps run their sweeps, the other's copies are in flight
+    // and its warps sit at a different phase of their own sweeps, so the SM's
+    // shared-memory, FP32 and TMA work overlap instead of lining up behind
+    // each barrier.  12-bit tiles keep three buffers per CTA; a 13-bit tile
+    // (64 KB) leaves room for one buffer per CTA, loaded after the previous
+    // tile's store has left it (no prefetch inside the CTA).  One CTA with
+    // up to 6 buffers when two do not fit.
+    int cps = (tp.R == 4 && (tp.T == 12 || tp.T == 13)) ? 2 : 1;
+    int limit = (cps == 2 ? 113 * 1024 : 227 * 1024) - 1024;   // 1 KB for the base alignment
+    int nb = std::min(cps == 2 ? 3 : 6, (limit - off) / buf_bytes);
+    if (cps == 2 && nb < 1) {
+        cps = 1;
+        limit = 227 * 1024 - 1024;
+        nb = std::min(6, (limit - off) / buf_bytes);
+    }
+    A.ctas_per_sm = cps;
+    A.n_buf = std::min(nb, kMaxTileBuffers);
+    if (A.n_buf < (cps == 2 ? 1 : 2)) return fail(QS_ERR_INTERNAL, "tile pass needs too much shared memory");
+    A.prefetch = A.n_buf == 1 ? 0 : std::max(1, A.n_buf - 2);
     off += A.n_buf * buf_bytes;
     if (off > limit) return fail(QS_ERR_INTERNAL, "tile pass needs too much shared memory");
     off += 1024;
@@ -391,7 +402,7 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
         s = encode_map(hp.tma, dst, tp.swizzle != 0, &tmd);
         if (s != QS_OK) return s;
     }
-    A.threads = (tp.R == 4 && tp.T >= 13) ? 512 : 256;
+    A.threads = (tp.R == 4 && tp.T >= 13 && A.ctas_per_sm == 1) ? 512 : 256;
     for (int k = 0; k < tp.n_sweeps; ++k)
         if (tp.sweeps[k].dense) A.dense = 1;
     A.kset = 1;

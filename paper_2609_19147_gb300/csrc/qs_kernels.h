@@ -31,8 +31,8 @@ struct TileArgs {
     int n_outer;               // number of non-tile index bits
     int outer_pos[kMaxQubits]; // their positions, ascending
     int off_desc, off_consts, off_roots, off_buf0;   // dynamic smem layout
-    int n_buf;                 // tile buffers (2..8), each 8 * 2^T bytes from off_buf0
-    int prefetch;              // tiles loaded ahead of the one being processed (1..n_buf-1)
+    int n_buf;                 // tile buffers (1..6), each 8 * 2^T bytes from off_buf0
+    int prefetch;              // tiles loaded ahead of the one being processed (0..n_buf-1; 0 when n_buf = 1)
     int threads;               // 256, or 512 for 4-bit register groups on 13-bit tiles
     int ctas_per_sm;           // 2: two co-resident CTAs (12-bit tiles, 4-bit groups)
     int l2_prefetch;           // tiles warmed in L2 beyond the shared-memory prefetch
