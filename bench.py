@@ -215,7 +215,8 @@ def _time_cuda(torch, stream, fn, reps=1):
 def suite_rows(qs, torch, peak):
     """The 28-qubit layered suite: each layer family alone (Haar U(2) on every
     qubit, ascending CNOT ladder, random-angle ZZ bonds, radix-4 QFT with
-    swaps, WHT), then 20 layers of the first three plus the QFT and the WHT.
+    swaps, WHT), then 20 layers of the first three plus the QFT and the WHT,
+    each with the tile shape the autotuner picks for it.
     Per family: layer time, HBM passes, the layer's own rate (one read and one
     write of the state / layer time) and each kernel's rate over the bytes its
     launches move (library events on the state's stream), as a fraction of the
@@ -236,15 +237,17 @@ def suite_rows(qs, torch, peak):
            "peak_GBps": peak}
     for name, gl in fams:
         cg = qs.CGates(gl)
-        s28.apply(cg)
+        tuned = s28.autotune(cg, reps=2)
+        kw = {k: v for k, v in tuned.items() if k != "ms"}
+        s28.apply(cg, **kw)
         torch.cuda.synchronize()
         reps = 1 if name.startswith("suite") else 5
         s28.profile(True)
-        t = _time_cuda(torch, s28.stream, lambda: s28.apply(cg), reps=reps)
+        t = _time_cuda(torch, s28.stream, lambda: s28.apply(cg, **kw), reps=reps)
         prof = s28.profile_read()
         s28.profile(False)
-        _, passes = qs.plan_describe(n, cg)
-        row = {"gates": len(gl), "s": t, "passes": passes}
+        _, passes = qs.plan_describe(n, cg, **kw)
+        row = {"gates": len(gl), "s": t, "passes": passes, "tile_shape": kw}
         if not name.startswith("suite"):
             row["layer_GBps"] = round(2 * sb / t / 1e9, 1)
         row["kernels"] = {k: {"launches": int(v[0]) // reps, "GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1),

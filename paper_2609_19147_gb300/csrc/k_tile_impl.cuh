@@ -622,7 +622,7 @@ constexpr int KS_LAYER = 1;
 // merges it saved.)
 template <int R>
 __device__ __forceinline__ int straight_code(const SweepCtx &c, int op_begin, int op_end, float scale) {
-    if (R != 4 || op_end - op_begin != 1) return 0;
+    if ((R != 4 && R != 5) || op_end - op_begin != 1) return 0;
     const MicroOp &o = c.micro[op_begin];
     if (o.kind != MK_LAYER || (o.a != MK_H && scale != 1.f)) return 0;
     const uint32_t full = (1u << R) - 1, mask = (uint32_t)o.b;
@@ -669,7 +669,7 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
         auto gbase = [&]() { return c.tile_gbase | tg[i0] | tg[i1] | tg[i2]; };
         float2 a[1 << R];
         Grp<R> G = G0;
-        if constexpr (R == 4 && KS == KS_LAYER) {
+        if constexpr ((R == 4 || R == 5) && KS == KS_LAYER) {
             if (fast) {
                 int o[1 << R];
                 group_offsets<R>(saddr, gs, o);

@@ -357,7 +357,20 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     const int buf_bytes = 8 << tp.T;
     off = al(off, 1024);
     A.off_buf0 = off;
-    // Two co-resident CTAs per SM for 4-bit groups on 12- and 13-bit tiles:
+    for (int k = 0; k < tp.n_sweeps; ++k)
+        if (tp.sweeps[k].dense) A.dense = 1;
+    A.kset = 1;
+    for (int k = 0; k < tp.n_micro; ++k) {
+        const MicroOp &mo = tp.micro[k];
+        if (mo.kind == MK_DIAG || mo.kind == MK_DIAGQ || mo.kind == MK_QFT || mo.kind == MK_QFTL || mo.cmask)
+            A.needs_gidx = 1;
+        if (!(mo.kind == MK_LAYER || mo.kind == MK_RXC || mo.kind == MK_U1R || mo.kind == MK_H || mo.kind == MK_U1 ||
+              mo.kind == MK_DIAG || mo.kind == MK_DIAGQ))
+            A.kset = 0;
+    }
+    // Two co-resident CTAs per SM for 4-bit groups on 12- and 13-bit tiles,
+    // and for 5-bit groups of layer/diagonal passes on 13-bit tiles (128
+    // threads each, whose 255 registers just fill the register file twice):
     // while one CTA's warps run their sweeps, the other's copies are in flight
     // and its warps sit at a different phase of their own sweeps, so the SM's
     // shared-memory, FP32 and TMA work overlap instead of lining up behind
@@ -365,7 +378,7 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     // (64 KB) leaves room for one buffer per CTA, loaded after the previous
     // tile's store has left it (no prefetch inside the CTA).  One CTA with
     // up to 6 buffers when two do not fit.
-    int cps = (tp.R == 4 && (tp.T == 12 || tp.T == 13)) ? 2 : 1;
+    int cps = ((tp.R == 4 && (tp.T == 12 || tp.T == 13)) || (tp.R == 5 && tp.T == 13 && A.kset && !A.dense)) ? 2 : 1;
     int limit = (cps == 2 ? 113 * 1024 : 227 * 1024) - 1024;   // 1 KB for the base alignment
     int nb = std::min(cps == 2 ? 3 : 6, (limit - off) / buf_bytes);
     if (cps == 2 && nb < 1) {
@@ -402,18 +415,7 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
         s = encode_map(hp.tma, dst, tp.swizzle != 0, &tmd);
         if (s != QS_OK) return s;
     }
-    A.threads = (tp.R == 4 && tp.T >= 13 && A.ctas_per_sm == 1) ? 512 : 256;
-    for (int k = 0; k < tp.n_sweeps; ++k)
-        if (tp.sweeps[k].dense) A.dense = 1;
-    A.kset = 1;
-    for (int k = 0; k < tp.n_micro; ++k) {
-        const MicroOp &mo = tp.micro[k];
-        if (mo.kind == MK_DIAG || mo.kind == MK_DIAGQ || mo.kind == MK_QFT || mo.kind == MK_QFTL || mo.cmask)
-            A.needs_gidx = 1;
-        if (!(mo.kind == MK_LAYER || mo.kind == MK_RXC || mo.kind == MK_U1R || mo.kind == MK_H || mo.kind == MK_U1 ||
-              mo.kind == MK_DIAG || mo.kind == MK_DIAGQ))
-            A.kset = 0;
-    }
+    A.threads = (tp.R == 4 && tp.T >= 13 && A.ctas_per_sm == 1) ? 512 : (tp.R == 5 && A.ctas_per_sm == 2) ? 128 : 256;
     if (A.dense && (tp.R != 5 || A.ctas_per_sm != 1)) return fail(QS_ERR_INTERNAL, "dense pass without 5-bit groups");
     if (A.dense) A.threads = 256;
     {
@@ -424,7 +426,10 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
             e = getenv("QS_TILE_PREFETCH");
             d_env = e ? atoi(e) : -1;
         }
-        A.l2_prefetch = pf_env >= 0 ? pf_env : 2;
+        // L2 warm-up of later tiles helps the multi-buffer CTAs; with one buffer
+        // per CTA the prefetched lines were partly evicted before their load
+        // (40% extra DRAM reads on 28q TFIM passes) and bought no time
+        A.l2_prefetch = pf_env >= 0 ? pf_env : (A.n_buf == 1 ? 0 : 2);
         if (d_env > 0 && d_env < A.n_buf) A.prefetch = d_env;
     }
     long long total = A.n_tiles * batch;
