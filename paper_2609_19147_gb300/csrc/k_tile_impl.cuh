@@ -606,6 +606,43 @@ __device__ __forceinline__ void apply_diagq(const SweepCtx &c, const MicroOp &op
     for (int j = 0; j < (1 << R); ++j) a[j] = cmul(a[j], cmul(z[j], q[j]));
 }
 
+// MK_DIAGC: count-indexed phase table.  The item's counts at group bits 0 are
+// popcounts (edge distance classes, the single-bit mask); each set group bit
+// adds its increment (from its neighbours outside the group and its own
+// single-bit term) and the edges inside the group add Qc[j]; the counts are
+// built by doubling over the group bits, so each amplitude costs one table
+// read and one complex multiply.
+template <int R>
+__device__ __forceinline__ void apply_diagc(const SweepCtx &c, const MicroOp &op, uint64_t x0,
+                                            float2 (&a)[1 << R]) {
+    const float2 *lut = c.cs + op.cst;
+    const uint64_t *dat = reinterpret_cast<const uint64_t *>(c.cs + op.lo);
+    const bool cz = op.b != 0;
+    const uint64_t degs = dat[R], mz = dat[R + 1], zinc = dat[R + 2];
+    int c0 = op.p * __popcll(x0 & mz);
+    for (int k = 0; k < op.a; ++k) {
+        const uint64_t m = dat[R + 3 + 2 * k];
+        const int d = (int)dat[R + 4 + 2 * k];
+        const uint64_t f = cz ? (x0 & (x0 >> d)) : (x0 ^ (x0 >> d));
+        c0 += __popcll(f & m);
+    }
+    int cnt[1 << R];
+    cnt[0] = c0;
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+        const int s = __popcll(x0 & dat[m]);
+        const int dm = (cz ? s : (int)((degs >> (6 * m)) & 63) - 2 * s) + (int)((zinc >> (12 * m)) & 4095);
+#pragma unroll
+        for (int j = 0; j < (1 << m); ++j) cnt[j | (1 << m)] = cnt[j] + dm;
+    }
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) {
+        const uint64_t qw = j < 16 ? op.cmask : op.cval;
+        const int q = (int)((qw >> (4 * (j & 15))) & 15);
+        a[j] = cmul(a[j], lut[cnt[j] + q]);
+    }
+}
+
 // Kernel op sets: KS_ALL compiles every micro-op kind; KS_LAYER only those of
 // 1q-layer and diagonal passes (Trotter / QAOA / random-layer circuits),
 // which keeps the code small and the register allocation tight.
@@ -705,6 +742,7 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
                     case MK_U1: disp_u1<R>(op.a, a, c.cs + op.cst, op.cmask, op.cval, gbase(), G); break;
                     case MK_DIAG: apply_diag<R>(c, op, gbase(), G, a); break;
                     case MK_DIAGQ: apply_diagq<R>(c, op, gbase(), a); break;
+                    case MK_DIAGC: apply_diagc<R>(c, op, gbase(), a); break;
                     default: break;
                 }
             } else {
@@ -739,6 +777,9 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
                         break;
                     case MK_DIAGQ:
                         apply_diagq<R>(c, op, gbase(), a);
+                        break;
+                    case MK_DIAGC:
+                        apply_diagc<R>(c, op, gbase(), a);
                         break;
                     default:
                         break;

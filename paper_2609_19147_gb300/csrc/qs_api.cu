@@ -362,10 +362,11 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     A.kset = 1;
     for (int k = 0; k < tp.n_micro; ++k) {
         const MicroOp &mo = tp.micro[k];
-        if (mo.kind == MK_DIAG || mo.kind == MK_DIAGQ || mo.kind == MK_QFT || mo.kind == MK_QFTL || mo.cmask)
+        if (mo.kind == MK_DIAG || mo.kind == MK_DIAGQ || mo.kind == MK_DIAGC || mo.kind == MK_QFT ||
+            mo.kind == MK_QFTL || (mo.cmask && mo.kind != MK_DIAGC))
             A.needs_gidx = 1;
         if (!(mo.kind == MK_LAYER || mo.kind == MK_RXC || mo.kind == MK_U1R || mo.kind == MK_H || mo.kind == MK_U1 ||
-              mo.kind == MK_DIAG || mo.kind == MK_DIAGQ))
+              mo.kind == MK_DIAG || mo.kind == MK_DIAGQ || mo.kind == MK_DIAGC))
             A.kset = 0;
     }
     // Two co-resident CTAs per SM for 4-bit groups on 12- and 13-bit tiles,

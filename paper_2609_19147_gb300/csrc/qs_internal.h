@@ -87,8 +87,20 @@ enum MicroKind : int32_t {
                   // terms), times prod over set group bits m of the couplings of bit m to
                   // other bits: (cmask >> 6m) & 63 entries at lo + 2 m kMaxCouple, each a
                   // pair (bit index as int bits, exp(i beta)) applied where that bit is set
+    MK_DIAGC = 10, // diagonal exp(i (g0 + gamma c1(x) + h c2(x))): c1 = number of edges
+                  // (u, v) of an edge set with x_u != x_v (b = 0, ZZ type) or x_u = x_v = 1
+                  // (b = 1, CZ type), c2 = popcount(x & Mz); table LUT[c1 + p c2] at cst
+                  // (p = |E| + 1).  Per item c1(x_0) (group bits 0) = sum over a = n_cls
+                  // distance classes of popcount(f_d(x_0) & M_d); group bit m adds delta_m
+                  // (ZZ: deg_m - 2 popcount(x_0 & N_m); CZ: popcount(x_0 & N_m); N_m = its
+                  // neighbours outside the group) plus p if it is in Mz; the edges inside
+                  // the group add Qc[j] (4 bits per j, packed in cmask for j < 16 and cval
+                  // for j >= 16).  Data at lo (uint64 slots): N_m (R slots), the R degrees
+                  // (6 bits each), Mz, the R Mz increments (12 bits each), then per class
+                  // M_d and d.
 };
 constexpr int kMaxCouple = 16;
+constexpr int kMaxCountClasses = 24;
 
 // item-address tables per sweep (shared memory): item bits 0-4, 5-9, 10-13,
 // then the sweep's group bits (kGroupTab entries: shared-memory offset and

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <set>
 #include <sstream>
 
 namespace qs {
@@ -968,7 +969,73 @@ float2 cexp_f(double ph) {
 struct DiagPlan {            // one Diag split into device descriptors
     std::vector<DiagDesc> descs;
     std::vector<std::vector<float2>> tables;   // per desc: its constants (offsets relative)
+    bool count = false;        // applied as a count lookup (MK_DIAGC) instead
+    int count_const = 0;       // its constants per sweep that applies it
 };
+
+// The count form of a diagonal (sweep-independent part of MK_DIAGC):
+// phase(x) = g0 + gamma c1(x) + h c2(x), c1 = edges whose bits differ (zz)
+// or are both set (!zz), c2 = popcount(x & mz).
+struct CountForm {
+    bool zz = true;
+    double gamma = 0.0, h = 0.0;
+    uint64_t mz = 0;
+    std::map<int, uint64_t> cls;   // distance d -> mask of lower endpoints
+    int stride = 1, n_z = 0;
+};
+
+bool count_form(const Diag &dg, CountForm &cf) {
+    if (dg.pairs.empty() && dg.a.empty()) return false;
+    const double w = dg.pairs.empty() ? 0.0 : dg.pairs.begin()->second;
+    for (auto &kv : dg.pairs)
+        if (std::fabs(kv.second - w) > 1e-12 * std::fabs(w)) return false;
+    std::map<int, int> deg;
+    for (auto &kv : dg.pairs) {
+        deg[kv.first.first]++;
+        deg[kv.first.second]++;
+    }
+    // ZZ type: pair weight -2 gamma, single-bit weight gamma deg(b); CZ type:
+    // pair weight gamma.  What is left of the single-bit weights must be one
+    // value h on a set of bits.
+    auto residual_ok = [&](double gam_deg, uint64_t &mz, double &h) {
+        mz = 0;
+        h = 0.0;
+        bool first = true;
+        std::set<int> bits;
+        for (auto &kv : dg.a) bits.insert(kv.first);
+        for (auto &kv : deg) bits.insert(kv.first);
+        for (int b : bits) {
+            auto it = dg.a.find(b);
+            const double have = it == dg.a.end() ? 0.0 : it->second;
+            const double want = gam_deg * (deg.count(b) ? deg[b] : 0);
+            const double r = have - want;
+            if (std::fabs(r) <= 1e-12 * std::max(1.0, std::fabs(want))) continue;
+            if (first) {
+                h = r;
+                first = false;
+            } else if (std::fabs(r - h) > 1e-12 * std::max(1.0, std::fabs(h))) {
+                return false;
+            }
+            mz |= 1ull << b;
+        }
+        return true;
+    };
+    cf.zz = residual_ok(-w / 2, cf.mz, cf.h);
+    if (!cf.zz && !residual_ok(0.0, cf.mz, cf.h)) return false;
+    cf.gamma = cf.zz ? -w / 2 : w;
+    cf.cls.clear();
+    for (auto &kv : dg.pairs) cf.cls[kv.first.second - kv.first.first] |= 1ull << kv.first.first;
+    cf.stride = (int)dg.pairs.size() + 1;
+    cf.n_z = __builtin_popcountll(cf.mz);
+    if ((int)cf.cls.size() > kMaxCountClasses || cf.stride > 4095) return false;
+    if ((size_t)cf.stride * (cf.n_z + 1) > 2048) return false;
+    return true;
+}
+
+// constants of one MK_DIAGC op: the table, alignment, and the data slots
+int count_const_size(const CountForm &cf, int R) {
+    return cf.stride * (cf.n_z + 1) + 1 + R + 3 + 2 * (int)cf.cls.size();
+}
 
 // Slices: window s covers bits [8s, 8s+w), w = min(9, n-8s).  A single-bit
 // term on b goes to slice b/8; a pair (b, c) goes to slice b/8 when c is
@@ -1091,6 +1158,12 @@ OpCost op_cost(int n, const FOp &f, int R, const DiagPlan *dp, int dprec) {
         case F_U2: c.n_const = 16; break;
         case F_QFT: c.n_const = 1 << R; break;
         case F_DIAG:
+            if (dp->count) {
+                c.n_const = dp->count_const;
+                c.n_diag = 0;
+                c.n_micro = 1;
+                break;
+            }
             c.n_const = (int)diag_const_size(*dp);
             c.n_diag = (int)dp->descs.size();
             c.n_micro = c.n_diag;
@@ -1544,6 +1617,16 @@ struct PassBuilder {
             }
             case F_DIAG: {
                 if (open < 0) need_bits(0);
+                if (dp->count) {   // completed per sweep at finalize (to_diagc)
+                    MicroOp mo;
+                    std::memset(&mo, 0, sizeof mo);
+                    mo.kind = MK_DIAGC;
+                    mo.cst = (int)count_src.size();
+                    count_src.push_back(&f.diag);
+                    tp.micro[tp.n_micro++] = mo;
+                    tp.sweeps[open].op_end = tp.n_micro;
+                    break;
+                }
                 for (size_t k = 0; k < dp->descs.size(); ++k) {
                     DiagDesc dd = dp->descs[k];
                     int base = (int)cst.size();
@@ -1568,6 +1651,86 @@ struct PassBuilder {
     }
     int count_diags = 0;
     const Diag *diag_src[kMaxDiag] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<const Diag *> count_src;   // MK_DIAGC ops before finalize: cst = index here
+    bool count_failed = false;
+    // A diagonal g0 + gamma c1(x) + h c2(x) (count_form: uniform-angle RZZ sets
+    // such as TFIM chains and QAOA cost layers, uniform CZ / CP sets, uniform
+    // single-qubit phases) is applied as a count lookup (Sec. 5.1 phase LUT
+    // indexed by popcounts): one table entry and one complex multiply per
+    // amplitude.  Fills the sweep-dependent part of the MK_DIAGC op.
+    bool to_diagc(MicroOp &mo, const Sweep &sw, const Diag &dg) {
+        CountForm cf;
+        if (!count_form(dg, cf)) return false;
+        int gb[kMaxGroup];
+        uint64_t gm = 0;
+        for (int m = 0; m < sw.r; ++m) {
+            gb[m] = __builtin_ctzll(glob_of_local(tp, sw.gbit[m]));
+            gm |= 1ull << gb[m];
+        }
+        // neighbours outside the group, edges inside it
+        uint64_t nb[kMaxGroup] = {0, 0, 0, 0, 0};
+        uint64_t qc[2] = {0, 0};
+        std::vector<std::pair<int, int>> inner;
+        for (auto &kv : dg.pairs) {
+            const int u = kv.first.first, v = kv.first.second;
+            const bool iu = (gm >> u) & 1, iv = (gm >> v) & 1;
+            for (int m = 0; m < sw.r; ++m) {
+                if (iu && !iv && gb[m] == u) nb[m] |= 1ull << v;
+                if (iv && !iu && gb[m] == v) nb[m] |= 1ull << u;
+            }
+            if (iu && iv) {
+                int mu = 0, mv = 0;
+                for (int m = 0; m < sw.r; ++m) {
+                    if (gb[m] == u) mu = m;
+                    if (gb[m] == v) mv = m;
+                }
+                inner.push_back({mu, mv});
+            }
+        }
+        for (int j = 0; j < (1 << sw.r); ++j) {
+            uint64_t q = 0;
+            for (auto &e : inner) {
+                const int bu = (j >> e.first) & 1, bv = (j >> e.second) & 1;
+                q += cf.zz ? (uint64_t)(bu ^ bv) : (uint64_t)(bu & bv);
+            }
+            if (q > 15) return false;   // at most C(5, 2) = 10 edges inside a group
+            qc[j >> 4] |= q << (4 * (j & 15));
+        }
+        uint64_t degs = 0, zinc = 0;
+        for (int m = 0; m < sw.r; ++m) {
+            degs |= (uint64_t)__builtin_popcountll(nb[m]) << (6 * m);
+            if ((cf.mz >> gb[m]) & 1) zinc |= (uint64_t)cf.stride << (12 * m);
+        }
+        const int lut = (int)cst.size();
+        const size_t n_e = dg.pairs.size();
+        for (int c2 = 0; c2 <= cf.n_z; ++c2)
+            for (size_t c1 = 0; c1 <= n_e; ++c1) cst.push_back(cexp_f(dg.g0 + cf.gamma * (double)c1 + cf.h * c2));
+        if (cst.size() & 1) cst.push_back(float2{0.f, 0.f});   // 16-byte aligned data
+        const int dat = (int)cst.size();
+        auto slot64 = [&](uint64_t v) {
+            float2 f;
+            std::memcpy(&f, &v, 8);
+            cst.push_back(f);
+        };
+        for (int m = 0; m < sw.r; ++m) slot64(nb[m]);
+        slot64(degs);
+        slot64(cf.mz);
+        slot64(zinc);
+        for (auto &kv : cf.cls) {
+            slot64(kv.second);
+            slot64((uint64_t)kv.first);
+        }
+        mo.kind = MK_DIAGC;
+        mo.cst = lut;
+        mo.lo = dat;
+        mo.a = (int)cf.cls.size();
+        mo.b = cf.zz ? 0 : 1;
+        mo.p = cf.stride;
+        mo.cmask = qc[0];
+        mo.cval = qc[1];
+        return true;
+    }
+
     // A diagonal whose sweep group spans more than two slice tables (or a LUT
     // group) would take the per-amplitude general path; factor it instead as
     // (tables at group bits 0) x Q(group bits) x couplings(group bit, other bit).
@@ -1641,6 +1804,10 @@ struct PassBuilder {
             for (int i = sw.op_begin; i < sw.op_end; ++i) {
                 MicroOp &mo = tp.micro[i];
                 if (mo.kind == MK_H || mo.kind == MK_QFT) n_butterfly++;
+                if (mo.kind == MK_DIAGC) {
+                    if (!to_diagc(mo, sw, *count_src[mo.cst])) count_failed = true;
+                    continue;
+                }
                 if (mo.kind == MK_DIAG) {
                     const DiagDesc &d = tp.diags[mo.cst];
                     uint32_t ds = 0, dg = 0;
@@ -1908,6 +2075,11 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
             ops2.push_back(f);
             continue;
         }
+        CountForm cf0;
+        if (count_form(f.diag, cf0)) {   // one count lookup, whatever its size
+            ops2.push_back(f);
+            continue;
+        }
         DiagPlan dp;
         plan_diag(n, f.diag, dp);
         if ((int)dp.descs.size() <= kMaxDiag && (int)diag_const_size(dp) <= kMaxConst / 2) {
@@ -1931,8 +2103,16 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
     ops.swap(ops2);
     for (FOp &f : ops) f.cache_masks();
     std::vector<DiagPlan> dplans(ops.size());
-    for (size_t i = 0; i < ops.size(); ++i)
-        if (ops[i].kind == F_DIAG) plan_diag(n, ops[i].diag, dplans[i]);
+    for (size_t i = 0; i < ops.size(); ++i) {
+        if (ops[i].kind != F_DIAG) continue;
+        CountForm cf;
+        if (count_form(ops[i].diag, cf)) {
+            dplans[i].count = true;
+            dplans[i].count_const = count_const_size(cf, R);
+        } else {
+            plan_diag(n, ops[i].diag, dplans[i]);
+        }
+    }
 
     std::vector<int> rem(ops.size());
     for (size_t i = 0; i < ops.size(); ++i) rem[i] = (int)i;
@@ -2023,6 +2203,10 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
             if (pb.tp.n_sweeps >= kMaxSweeps - 1) break;   // guarded by taken limit
         }
         pb.finalize();
+        if (pb.count_failed) {
+            err = "count-table diagonal could not be placed (internal)";
+            return QS_ERR_INTERNAL;
+        }
         pb.hp.note = "tile";
         plan.passes.push_back(pb.hp);
         std::vector<int> nrem(deferred);
@@ -2211,7 +2395,7 @@ std::string Plan::describe() const {
                 const MicroOp &mo = t.micro[k];
                 if (mo.kind == MK_LAYER) cnt[mo.a] += __builtin_popcount((unsigned)mo.b);
                 else if (mo.kind == MK_QFTL) cnt[MK_QFT] += __builtin_popcount((unsigned)mo.b);
-                else if (mo.kind == MK_DIAGQ) cnt[MK_DIAG]++;
+                else if (mo.kind == MK_DIAGQ || mo.kind == MK_DIAGC) cnt[MK_DIAG]++;
                 else cnt[mo.kind]++;
             }
             os << "TILE T=" << t.T << " L=" << t.L << " hb=[";
@@ -2219,15 +2403,17 @@ std::string Plan::describe() const {
             os << "] tma=" << (hp.tma.ok ? 1 : 0) << " sweeps=" << t.n_sweeps
                << " U1=" << cnt[MK_U1] + cnt[MK_H] + cnt[MK_RXC] + cnt[MK_U1R] << " U2=" << cnt[MK_U2]
                << " DIAG=" << cnt[MK_DIAG] << " QFT=" << cnt[MK_QFT];
-            int nd = 0, slow = 0, fq = 0;
+            int nd = 0, slow = 0, fq = 0, fc = 0;
             for (int k = 0; k < t.n_sweeps; ++k) nd += t.sweeps[k].dense ? 1 : 0;
             for (int k = 0; k < t.n_micro; ++k) {
                 if (t.micro[k].kind == MK_DIAG && (t.micro[k].b != 0 || __builtin_popcount((unsigned)t.micro[k].a) > 2))
                     slow++;
                 if (t.micro[k].kind == MK_DIAGQ) fq++;
+                if (t.micro[k].kind == MK_DIAGC) fc++;
             }
             if (nd) os << " DENSE=" << nd;
             if (fq) os << " DIAGQ=" << fq;
+            if (fc) os << " DIAGC=" << fc;
             if (slow) os << " DIAG_GENERAL=" << slow;
             os << " consts=" << t.n_const << "\n";
         } else if (hp.type == HostPass::PERM) {

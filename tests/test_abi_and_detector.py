@@ -198,3 +198,22 @@ def test_pauli_pair_layers_are_basis_conjugated(qs):
         assert sum(int(m) for m in re.findall(r"DIAG=(\d+)", text)) >= 1
     text, _ = _passes(qs, n, [W.Gate("RXX", (3, 9), (0.4,))])
     assert sum(int(m) for m in re.findall(r"U2=(\d+)", text)) == 1
+
+
+def test_uniform_pair_sums_become_count_lookups(qs):
+    # uniform-angle RZZ chains (TFIM, including the S phases of conjugated RX
+    # layers), uniform CZ rings and uniform RZZ on a random graph take the
+    # count-table diagonal; random-angle ZZ bonds keep the factored tables
+    n = 30
+    tf = W.tfim_gates(n, 4, 0.05, 1.0, W.tfim_fields(n, 3), order=2)
+    text, _ = _passes(qs, n, tf)
+    d = sum(int(m) for m in re.findall(r" DIAG=(\d+)", text))
+    assert sum(int(m) for m in re.findall(r"DIAGC=(\d+)", text)) == d > 0, text
+    ring = [W.Gate("CZ", (b, (b + 1) % 20)) for b in range(20)] + [W.Gate("H", (q,)) for q in range(20)]
+    assert "DIAGC=" in _passes(qs, 20, ring)[0]
+    g = W.random_regular3_graph(18, np.random.default_rng(4))
+    gl = [W.Gate("RZZ", (u, v), (0.3,)) for u, v in g] + [W.Gate("RX", (q,), (0.2,)) for q in range(18)]
+    assert "DIAGC=" in _passes(qs, 18, gl)[0]
+    rng = np.random.default_rng(2)
+    rz = [W.Gate("RZZ", (b, b + 1), (float(rng.uniform(0, 6)),)) for b in range(27)]
+    assert "DIAGC=" not in _passes(qs, 28, rz)[0]

@@ -353,3 +353,26 @@ def test_suite28_full_size_one_layer_and_full_suite():
     st.close()
     assert abs(norm - 1) < 1e-5
     assert rel <= 1e-5, rel
+
+
+@pytest.mark.parametrize("n", [14, 22])
+def test_count_table_diagonals(n):
+    # uniform pair sums as count lookups: a ZZ chain and a ZZ random 3-regular
+    # graph (mismatch counts), a CZ ring and a CP clique on 5 qubits inside one
+    # register group (both-set counts, Qc up to 10), each with a uniform
+    # single-qubit phase on some qubits, between RY / RX layers
+    rng = np.random.default_rng(n)
+    g = W.random_regular3_graph(n, rng)
+    gl = [W.Gate("RY", (q,), (float(rng.uniform(0, 6)),)) for q in range(n)]
+    gl += [W.Gate("RZZ", (b, b + 1), (0.37,)) for b in range(n - 1)]
+    gl += [W.Gate("RX", (q,), (float(rng.uniform(0, 6)),)) for q in range(n)]
+    gl += [W.Gate("RZZ", (u, v), (-0.81,)) for u, v in g] + [W.Gate("RZ", (q,), (0.29,)) for q in range(0, n, 3)]
+    gl += [W.Gate("RY", (q,), (float(rng.uniform(0, 6)),)) for q in range(n)]
+    gl += [W.Gate("CZ", (b, (b + 1) % n)) for b in range(n)] + [W.Gate("S", (q,)) for q in range(1, n, 2)]
+    gl += [W.Gate("RX", (q,), (float(rng.uniform(0, 6)),)) for q in range(n)]
+    gl += [W.Gate("CP", (i, j), (1.1,)) for i in range(n - 5, n) for j in range(i + 1, n)]
+    gl += [W.Gate("RY", (q,), (float(rng.uniform(0, 6)),)) for q in range(n)]
+    text, _ = qs.plan_describe(n, gl)
+    assert "DIAGC=" in text, text
+    psi0 = W.random_state(n, 5)
+    _assert_close(_run(n, gl, psi0), _ref(n, gl, psi0))
