@@ -148,9 +148,84 @@ struct qs_state {
     bool prof = false;
     std::map<std::string, ProfRec> prof_recs;
     std::vector<PendingEv> prof_pending;
+    // page-locked staging for host -> device uploads (plans, term tables): a
+    // copy from pageable memory waits for the stream's earlier work, one from
+    // page-locked memory does not.  A chunk is reused once the event recorded
+    // after its last copy has completed.
+    struct Pinned {
+        char *p = nullptr;
+        size_t cap = 0, used = 0;
+        cudaEvent_t ev = nullptr;
+    };
+    std::vector<Pinned> pinned;
+    size_t pin_cur = 0;
+    // qs_grad's (psi, lam) pair workspace, kept between calls: mapping and
+    // unmapping 2 x batch x 2^n amplitudes every call cost more than the sweep
+    float2 *grad_ws = nullptr;
+    size_t grad_ws_bytes = 0;
 };
 
 namespace {
+
+// Copy `bytes` from host memory to device memory on the state's stream
+// without waiting for the stream: the data goes through a page-locked chunk.
+qs_status h2d_async(qs_state *st, void *dst, const void *src, size_t bytes) {
+    if (bytes == 0) return QS_OK;
+    constexpr size_t kChunk = 4u << 20;
+    constexpr size_t kMaxChunks = 16;
+    const size_t need = (bytes + 255) & ~(size_t)255;
+    qs_state::Pinned *c = nullptr;
+    if (st->pin_cur < st->pinned.size() && st->pinned[st->pin_cur].used + need <= st->pinned[st->pin_cur].cap)
+        c = &st->pinned[st->pin_cur];
+    for (size_t i = 0; !c && i < st->pinned.size(); ++i) {   // a chunk whose copies have completed
+        qs_state::Pinned &q = st->pinned[i];
+        if (q.cap >= need && cudaEventQuery(q.ev) == cudaSuccess) {
+            q.used = 0;
+            st->pin_cur = i;
+            c = &q;
+        }
+    }
+    cudaGetLastError();   // cudaEventQuery's cudaErrorNotReady
+    if (!c && st->pinned.size() < kMaxChunks) {
+        qs_state::Pinned q;
+        q.cap = std::max(kChunk, need);
+        if (cudaMallocHost((void **)&q.p, q.cap) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(QS_ERR_OOM, "page-locked staging allocation failed");
+        }
+        QS_CUDA(cudaEventCreateWithFlags(&q.ev, cudaEventDisableTiming));
+        st->pinned.push_back(q);
+        st->pin_cur = st->pinned.size() - 1;
+        c = &st->pinned.back();
+    }
+    if (!c) {   // all chunks in flight: wait for the one with room
+        for (size_t i = 0; i < st->pinned.size() && !c; ++i)
+            if (st->pinned[i].cap >= need) {
+                QS_CUDA(cudaEventSynchronize(st->pinned[i].ev));
+                st->pinned[i].used = 0;
+                st->pin_cur = i;
+                c = &st->pinned[i];
+            }
+        if (!c) {   // larger than every chunk: plain copy
+            QS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st->stream));
+            return QS_OK;
+        }
+    }
+    char *stage = c->p + c->used;
+    c->used += need;
+    std::memcpy(stage, src, bytes);
+    QS_CUDA(cudaMemcpyAsync(dst, stage, bytes, cudaMemcpyHostToDevice, st->stream));
+    QS_CUDA(cudaEventRecord(c->ev, st->stream));
+    return QS_OK;
+}
+
+void free_pinned(qs_state *st) {
+    for (auto &q : st->pinned) {
+        if (q.ev) cudaEventDestroy(q.ev);
+        if (q.p) cudaFreeHost(q.p);
+    }
+    st->pinned.clear();
+}
 
 void free_plan(qs_state *st, DevicePlan *dp) {
     for (auto p : dp->d_tile) cudaFreeAsync(p, st->stream);
@@ -167,7 +242,8 @@ qs_status upload_plan(qs_state *st, DevicePlan &dp) {
         if (!p.pg.empty()) {
             size_t b = p.pg.size() * sizeof(PgOp);
             QS_CUDA(cudaMallocAsync((void **)&dp.d_pg, b, st->stream));
-            QS_CUDA(cudaMemcpyAsync(dp.d_pg, p.pg.data(), b, cudaMemcpyHostToDevice, st->stream));
+            qs_status r = h2d_async(st, dp.d_pg, p.pg.data(), b);
+            if (r != QS_OK) return r;
             dp.bytes += b;
         }
         return QS_OK;
@@ -179,23 +255,23 @@ qs_status upload_plan(qs_state *st, DevicePlan &dp) {
         const HostPass &hp = p.passes[i];
         if (hp.type == HostPass::TILE) {
             QS_CUDA(cudaMallocAsync((void **)&dp.d_tile[i], sizeof(TilePass), st->stream));
-            QS_CUDA(cudaMemcpyAsync(dp.d_tile[i], &hp.tile, sizeof(TilePass), cudaMemcpyHostToDevice, st->stream));
+            qs_status r = h2d_async(st, dp.d_tile[i], &hp.tile, sizeof(TilePass));
+            if (r != QS_OK) return r;
             dp.bytes += sizeof(TilePass);
             if (!hp.consts.empty()) {
                 size_t b = hp.consts.size() * sizeof(float2);
                 QS_CUDA(cudaMallocAsync((void **)&dp.d_consts[i], b, st->stream));
-                QS_CUDA(cudaMemcpyAsync(dp.d_consts[i], hp.consts.data(), b, cudaMemcpyHostToDevice, st->stream));
+                r = h2d_async(st, dp.d_consts[i], hp.consts.data(), b);
+                if (r != QS_OK) return r;
                 dp.bytes += b;
             }
         } else if (hp.type == HostPass::GATHER) {
             QS_CUDA(cudaMallocAsync((void **)&dp.d_gather[i], sizeof(GatherPass), st->stream));
-            QS_CUDA(cudaMemcpyAsync(dp.d_gather[i], &hp.gather, sizeof(GatherPass), cudaMemcpyHostToDevice,
-                                    st->stream));
+            qs_status r = h2d_async(st, dp.d_gather[i], &hp.gather, sizeof(GatherPass));
+            if (r != QS_OK) return r;
             dp.bytes += sizeof(GatherPass);
         }
     }
-    // the sources are pageable host memory owned by the cached plan, which is
-    // not modified after upload (pageable copies are staged before returning)
     return QS_OK;
 }
 
@@ -662,8 +738,8 @@ qs_status diag_expect_async(qs_state *st, const std::vector<PauliDev> &hz, doubl
     qs_status s = ensure_partial(st, (size_t)B * grid * 2);
     if (s == QS_OK) s = ensure_terms(st, hz.size());
     if (s != QS_OK) return s;
-    QS_CUDA(cudaMemcpyAsync(st->d_terms, hz.data(), hz.size() * sizeof(PauliDev), cudaMemcpyHostToDevice,
-                            st->stream));
+    s = h2d_async(st, st->d_terms, hz.data(), hz.size() * sizeof(PauliDev));
+    if (s != QS_OK) return s;
     DiagExpectArgs A;
     std::memset(&A, 0, sizeof A);
     A.psi = st->home;
@@ -742,8 +818,8 @@ qs_status overlaps(qs_state *st, const float2 *psi, const float2 *phi, int batch
             }
         }
     }
-    QS_CUDA(cudaMemcpyAsync(st->d_terms, hterms.data(), hterms.size() * sizeof(PauliDev), cudaMemcpyHostToDevice,
-                            st->stream));
+    s = h2d_async(st, st->d_terms, hterms.data(), hterms.size() * sizeof(PauliDev));
+    if (s != QS_OK) return s;
     for (size_t c = 0; c < chunks.size(); ++c) {
         ExpectArgs A;
         std::memset(&A, 0, sizeof A);
@@ -870,6 +946,8 @@ qs_status qs_free(qs_state *st) {
     if (st->d_partial) cudaFree(st->d_partial);
     if (st->d_out) cudaFree(st->d_out);
     if (st->d_terms) cudaFree(st->d_terms);
+    if (st->grad_ws) cudaFree(st->grad_ws);
+    free_pinned(st);
     delete st;
     return QS_OK;
 }
@@ -1147,6 +1225,93 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
     std::vector<TermIdx> t;
     qs_status s = convert_terms(st->n, terms, n_terms, t);
     if (s != QS_OK) return s;
+    qs_opts fo = default_opts(nullptr);
+    // Un-apply segments: the gates between two gradient points, latest first.
+    // Their plans (per item when the segment carries parameters, else one for
+    // all pairs) are built up front on host threads.
+    struct Segment {
+        std::vector<size_t> gates;
+        bool per_item = false;
+        size_t first_plan = 0;
+    };
+    std::vector<Segment> segs;
+    std::vector<size_t> pending;   // gates to un-apply, latest first
+    auto close_segment = [&]() {
+        if (pending.empty()) return;
+        Segment sg;
+        sg.gates.swap(pending);
+        for (size_t gi : sg.gates)
+            if (gates[gi].param_idx >= 0) sg.per_item = true;
+        segs.push_back(std::move(sg));
+    };
+    size_t next_seg = 0;
+    std::vector<Plan> seg_plans;
+    // dry run of the sweep: the segments in execution order
+    for (size_t gi = n_gates; gi-- > 0;) {
+        if (rg[0][gi].nw == 1) {
+            size_t lo = gi;
+            while (lo > 0 && rg[0][lo - 1].nw == 1) --lo;
+            bool has_param = false;
+            for (size_t k = lo; k <= gi; ++k)
+                if (gates[k].param_idx >= 0) has_param = true;
+            if (has_param) close_segment();
+            for (size_t k = gi + 1; k-- > lo;) pending.push_back(k);
+            gi = lo;
+            continue;
+        }
+        if (gates[gi].param_idx >= 0) close_segment();
+        pending.push_back(gi);
+    }
+    pending.clear();   // the gates before the first gradient point are never un-applied
+    // the un-apply plans are built on host threads while the GPU runs the
+    // forward circuit and the Hamiltonian
+    qs_status seg_status = QS_OK;
+    std::string seg_err;
+    std::thread seg_thread([&]() {
+        {
+            std::vector<std::vector<RGate>> lists;
+            for (Segment &sg : segs) {
+                sg.first_plan = lists.size();
+                for (int b = 0; b < (sg.per_item ? B : 1); ++b) {
+                    std::vector<RGate> inv;
+                    for (size_t gi : sg.gates) invert_gate(rg[b][gi], inv);
+                    lists.push_back(std::move(inv));
+                }
+            }
+            // per-item segments run on a pair (batch 2), shared ones on all pairs
+            std::vector<std::vector<RGate>> l2, lB;
+            std::vector<size_t> i2, iB;
+            for (const Segment &sg : segs)
+                for (int b = 0; b < (sg.per_item ? B : 1); ++b) {
+                    const size_t i = sg.first_plan + b;
+                    if (sg.per_item) {
+                        i2.push_back(i);
+                        l2.push_back(lists[i]);
+                    } else {
+                        iB.push_back(i);
+                        lB.push_back(lists[i]);
+                    }
+                }
+            std::vector<Plan> p2, pB;
+            std::string err;
+            qs_status r = build_plans_parallel(st->n, 2, l2, fo, p2, err);
+            if (r == QS_OK) r = build_plans_parallel(st->n, 2 * B, lB, fo, pB, err);
+            if (r != QS_OK) {
+                seg_status = r;
+                seg_err = err;
+                return;
+            }
+            seg_plans.resize(lists.size());
+            for (size_t j = 0; j < i2.size(); ++j) seg_plans[i2[j]] = std::move(p2[j]);
+            for (size_t j = 0; j < iB.size(); ++j) seg_plans[iB[j]] = std::move(pB[j]);
+        }
+    });
+    struct Joiner {
+        std::thread &t;
+        ~Joiner() {
+            if (t.joinable()) t.join();
+        }
+    } joiner{seg_thread};
     // 1. forward: psi = U(theta)|0>, one fused plan per item (built in parallel)
     QS_CUDA(launch_init_zero(st->home, st->elems, B, st->stream));
     qs_opts o = default_opts(nullptr);
@@ -1172,48 +1337,80 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
     //    executor; the caller's state keeps psi(theta)
     const long long E = st->elems;
     const size_t pair_bytes = (size_t)E * 2 * B * sizeof(float2);
-    float2 *W = nullptr;
-    if (cudaMallocAsync((void **)&W, pair_bytes, st->stream) != cudaSuccess)
-        return fail(QS_ERR_OOM, "qs_grad: no memory for the adjoint states");
+    if (st->grad_ws_bytes < pair_bytes) {
+        if (st->grad_ws) {
+            cudaStreamSynchronize(st->stream);
+            cudaFree(st->grad_ws);
+            st->grad_ws = nullptr;
+            st->grad_ws_bytes = 0;
+        }
+        if (cudaMalloc((void **)&st->grad_ws, pair_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            st->grad_ws = nullptr;
+            return fail(QS_ERR_OOM, "qs_grad: no memory for the adjoint states");
+        }
+        st->grad_ws_bytes = pair_bytes;
+    }
+    float2 *W = st->grad_ws;
     qs_state *aux = nullptr;
     struct Guard {
-        qs_state *st;
-        float2 *w;
         qs_state **aux;
         ~Guard() {
             if (*aux) qs_free(*aux);
-            cudaFreeAsync(w, st->stream);
         }
-    } guard{st, W, &aux};
+    } guard{&aux};
     QS_CUDA(cudaMemcpy2DAsync(W, 2 * E * sizeof(float2), st->home, E * sizeof(float2), E * sizeof(float2), B,
                               cudaMemcpyDeviceToDevice, st->stream));
-    {
-        std::vector<PauliDev> hp;
-        for (auto &x : t) hp.push_back({x.coeff, x.x, x.z});
-        std::stable_sort(hp.begin(), hp.end(), [](const PauliDev &a, const PauliDev &b) { return a.x < b.x; });
-        s = ensure_terms(st, std::max<size_t>(hp.size(), 1));
-        if (s != QS_OK) return s;
-        if (!hp.empty()) {
-            QS_CUDA(cudaMemcpyAsync(st->d_terms, hp.data(), hp.size() * sizeof(PauliDev), cudaMemcpyHostToDevice,
-                                    st->stream));
-            cudaEvent_t ev;
-            prof_begin(st, &ev);
-            QS_CUDA(launch_apply_pauli_sum(W, W + E, E, B, st->d_terms, (int)hp.size(), st->stream, 2 * E));
-            prof_end(st, ev, "pauli_sum", 16.0 * (double)E * B);
-            QS_CUDA(cudaStreamSynchronize(st->stream));   // the host term array goes out of scope
-        } else {
-            QS_CUDA(cudaMemset2DAsync(W + E, 2 * E * sizeof(float2), 0, E * sizeof(float2), B, st->stream));
-        }
+    // lam = H psi; the term array (H's terms, then the identity used for the
+    // energy) stays alive until the call ends, so nothing waits here
+    std::vector<PauliDev> hp;
+    for (auto &x : t) hp.push_back({x.coeff, x.x, x.z});
+    std::stable_sort(hp.begin(), hp.end(), [](const PauliDev &a, const PauliDev &b) { return a.x < b.x; });
+    const int n_h = (int)hp.size();
+    hp.push_back({1.0, 0, 0});
+    s = ensure_terms(st, hp.size());
+    if (s != QS_OK) return s;
+    s = h2d_async(st, st->d_terms, hp.data(), hp.size() * sizeof(PauliDev));
+    if (s != QS_OK) return s;
+    if (n_h) {
+        cudaEvent_t ev;
+        prof_begin(st, &ev);
+        QS_CUDA(launch_apply_pauli_sum(W, W + E, E, B, st->d_terms, n_h, st->stream, 2 * E));
+        prof_end(st, ev, "pauli_sum", 16.0 * (double)E * B);
+    } else {
+        QS_CUDA(cudaMemset2DAsync(W + E, 2 * E * sizeof(float2), 0, E * sizeof(float2), B, st->stream));
     }
+    // E_b = Re sum_x conj(lam_x) psi_x into a device array, read with the gradients
+    double *d_en = nullptr;
+    QS_CUDA(cudaMallocAsync((void **)&d_en, (size_t)B * 2 * sizeof(double), st->stream));
+    struct Guard2 {
+        qs_state *st;
+        double *p;
+        ~Guard2() {
+            if (p) cudaFreeAsync(p, st->stream);
+        }
+    } guard2{st, d_en};
     {
-        std::vector<TermIdx> one(1);
-        one[0].coeff = 1.0;
-        one[0].x = one[0].z = 0;
-        one[0].ny = 0;
-        std::vector<double> S;
-        s = overlaps(st, W, W + E, B, one, S, 2 * E);   // sum_x conj(lam_x) psi_x
+        const int grid = std::max(1, std::min<int>((int)((E + 255) / 256), g_num_sms[st->dev] * 4));
+        s = ensure_partial(st, (size_t)B * grid * 2);
         if (s != QS_OK) return s;
-        for (int b = 0; b < B; ++b) energy[b] = S[(size_t)b * 2];
+        ExpectArgs A;
+        std::memset(&A, 0, sizeof A);
+        A.psi = W;
+        A.lam = W + E;
+        A.state_elems = E;
+        A.bstride = 2 * E;
+        A.batch = B;
+        A.xmask = 0;
+        A.n_terms = 1;
+        A.terms = st->d_terms + n_h;
+        A.partial = st->d_partial;
+        A.grid = grid;
+        cudaEvent_t ev;
+        prof_begin(st, &ev);
+        QS_CUDA(launch_expect_group(A, st->stream));
+        prof_end(st, ev, "expect", 16.0 * (double)E * B);
+        QS_CUDA(launch_expect_finish(st->d_partial, d_en, B, grid, 1, st->stream));
     }
     s = qs_wrap(W, st->n, 2 * B, st->stream, &aux);
     if (s != QS_OK) return s;
@@ -1229,27 +1426,8 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
     //    per item (batch = the pair) when they carry parameters, otherwise
     //    once for all pairs.  Parameterised 2q gates (RZZ, CP) take their own
     //    overlap of generator terms.
-    qs_opts fo = default_opts(nullptr);
-    // Un-apply segments: the gates between two gradient points, latest first.
-    // Their plans (per item when the segment carries parameters, else one for
-    // all pairs) are built up front on host threads.
-    struct Segment {
-        std::vector<size_t> gates;
-        bool per_item = false;
-        size_t first_plan = 0;
-    };
-    std::vector<Segment> segs;
-    std::vector<size_t> pending;   // gates to un-apply, latest first
-    auto close_segment = [&]() {
-        if (pending.empty()) return;
-        Segment sg;
-        sg.gates.swap(pending);
-        for (size_t gi : sg.gates)
-            if (gates[gi].param_idx >= 0) sg.per_item = true;
-        segs.push_back(std::move(sg));
-    };
-    size_t next_seg = 0;
-    std::vector<Plan> seg_plans;
+    seg_thread.join();
+    if (seg_status != QS_OK) return fail(seg_status, seg_err);
     auto flush = [&]() -> qs_status {
         if (pending.empty()) return QS_OK;
         pending.clear();
@@ -1268,56 +1446,6 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
         }
         return QS_OK;
     };
-    // dry run of the sweep: the segments in execution order
-    for (size_t gi = n_gates; gi-- > 0;) {
-        if (rg[0][gi].nw == 1) {
-            size_t lo = gi;
-            while (lo > 0 && rg[0][lo - 1].nw == 1) --lo;
-            bool has_param = false;
-            for (size_t k = lo; k <= gi; ++k)
-                if (gates[k].param_idx >= 0) has_param = true;
-            if (has_param) close_segment();
-            for (size_t k = gi + 1; k-- > lo;) pending.push_back(k);
-            gi = lo;
-            continue;
-        }
-        if (gates[gi].param_idx >= 0) close_segment();
-        pending.push_back(gi);
-    }
-    pending.clear();   // the gates before the first gradient point are never un-applied
-    {
-        std::vector<std::vector<RGate>> lists;
-        for (Segment &sg : segs) {
-            sg.first_plan = lists.size();
-            for (int b = 0; b < (sg.per_item ? B : 1); ++b) {
-                std::vector<RGate> inv;
-                for (size_t gi : sg.gates) invert_gate(rg[b][gi], inv);
-                lists.push_back(std::move(inv));
-            }
-        }
-        // per-item segments run on a pair (batch 2), shared ones on all pairs
-        std::vector<std::vector<RGate>> l2, lB;
-        std::vector<size_t> i2, iB;
-        for (const Segment &sg : segs)
-            for (int b = 0; b < (sg.per_item ? B : 1); ++b) {
-                const size_t i = sg.first_plan + b;
-                if (sg.per_item) {
-                    i2.push_back(i);
-                    l2.push_back(lists[i]);
-                } else {
-                    iB.push_back(i);
-                    lB.push_back(lists[i]);
-                }
-            }
-        std::vector<Plan> p2, pB;
-        std::string err;
-        s = build_plans_parallel(st->n, 2, l2, fo, p2, err);
-        if (s == QS_OK) s = build_plans_parallel(st->n, 2 * B, lB, fo, pB, err);
-        if (s != QS_OK) return fail(s, err);
-        seg_plans.resize(lists.size());
-        for (size_t j = 0; j < i2.size(); ++j) seg_plans[i2[j]] = std::move(p2[j]);
-        for (size_t j = 0; j < iB.size(); ++j) seg_plans[iB[j]] = std::move(pB[j]);
-    }
     // overlap launches: shared-memory tiles of the 4 low bits + <= 8 wires
     // (n >= 6), else register groups of <= 4 wires
     const bool tiled = st->n >= 6;
@@ -1348,7 +1476,10 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
         if (wires && tiled) {
             std::vector<int> hi, others;
             for (int q = 4; q < st->n; ++q) ((wires >> q) & 1 ? hi : others).push_back(q);
-            const int hmax = std::min(7, st->n - 4);   // 11-bit tiles: three CTAs per SM with double buffers
+            // 11-bit tiles (three CTAs per SM with double buffers) for large
+            // states; up to 21 qubits 12-bit tiles, whose fewer launches win
+            // (n = 20: 54 -> 38 ms per 32-item batch; n = 24: 504 vs 595 ms)
+            const int hmax = std::min(st->n <= 21 ? 8 : 7, st->n - 4);
             size_t c = 0;
             do {
                 XyzLaunch x;
@@ -1507,7 +1638,13 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
         }
         pending.push_back(gi);
     }
-    // 5. gradients of the 1q layers from their X / Y / Z overlaps
+    // 5. the energies, and the gradients of the 1q layers from their X / Y / Z overlaps
+    {
+        std::vector<double> en((size_t)B * 2);
+        QS_CUDA(cudaMemcpyAsync(en.data(), d_en, en.size() * sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+        QS_CUDA(cudaStreamSynchronize(st->stream));
+        for (int b = 0; b < B; ++b) energy[b] = en[(size_t)b * 2];
+    }
     if (n_launch) {
         std::vector<double> res(n_launch * B * slots);
         QS_CUDA(cudaMemcpyAsync(res.data(), d_res, res.size() * sizeof(double), cudaMemcpyDeviceToHost, st->stream));
