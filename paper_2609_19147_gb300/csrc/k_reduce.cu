@@ -167,6 +167,103 @@ __global__ void __launch_bounds__(256) pauli_sum_kernel(const float2 *psi, float
     }
 }
 
+template <int H>
+__global__ void __launch_bounds__(256) pauli_sum_tile_kernel(const PsumTileArgs A) {
+    constexpr int TB = 4 + H, TN = 1 << TB, ROWS = 1 << H;
+    extern __shared__ float2 tile[];                 // TN amplitudes
+    __shared__ uint64_t rowoff[ROWS];                // global bits of each row's high-bit pattern
+    __shared__ float2 coef[kPsumMaxTerms];           // coeff_k i^ny_k (-1)^popcount(x_k & z_k), FP32
+    __shared__ int xl[kPsumMaxTerms], zl[kPsumMaxTerms];   // x and z masks in tile-local bits
+    __shared__ float sgn[kPsumMaxTerms];             // the tile's outer-bit parity of z_k, as a sign
+    const int tid = threadIdx.x;
+    for (int r = tid; r < ROWS; r += blockDim.x) {
+        uint64_t o = 0;
+        for (int k = 0; k < H; ++k)
+            if ((r >> k) & 1) o |= 1ull << A.hb[k];
+        rowoff[r] = o;
+    }
+    auto to_local = [&](uint64_t m) {
+        int v = (int)(m & 15);
+        for (int h = 0; h < H; ++h)
+            if ((m >> A.hb[h]) & 1) v |= 1 << (4 + h);
+        return v;
+    };
+    for (int k = tid; k < A.n_terms; k += blockDim.x) {
+        const PauliDev t = A.terms[k];
+        xl[k] = to_local(t.x);
+        zl[k] = to_local(t.z);
+        // (-1)^popcount((y ^ x) & z) = (-1)^popcount(x & z) (-1)^popcount(y & z)
+        const double c = (__popcll(t.x & t.z) & 1) ? -t.coeff : t.coeff;
+        const float cf = (float)c;
+        switch (__popcll(t.x & t.z) & 3) {   // times i^ny
+            case 0: coef[k] = make_float2(cf, 0.f); break;
+            case 1: coef[k] = make_float2(0.f, cf); break;
+            case 2: coef[k] = make_float2(-cf, 0.f); break;
+            default: coef[k] = make_float2(0.f, -cf); break;
+        }
+    }
+    const int b = blockIdx.y;
+    const float2 *p = A.psi + (long long)b * A.bstride;
+    float2 *l = A.lam + (long long)b * A.bstride;
+    const long long n_tiles = A.elems >> TB;
+    for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        uint64_t g0 = 0;
+        for (int i = 0; i < A.n_outer; ++i)
+            if ((t >> i) & 1) g0 |= 1ull << A.outer[i];
+        __syncthreads();   // the previous tile's reads are done
+        for (int k = tid; k < A.n_terms; k += blockDim.x)
+            sgn[k] = (__popcll(g0 & A.terms[k].z) & 1) ? -1.f : 1.f;
+        // rows of 16 amplitudes are contiguous: 16-byte loads
+        for (int e = tid; e < TN / 2; e += blockDim.x) {
+            const int row = e >> 3, col = (e & 7) * 2;
+            const float4 v = *reinterpret_cast<const float4 *>(p + (g0 | rowoff[row] | (uint64_t)col));
+            tile[row * 16 + col] = make_float2(v.x, v.y);
+            tile[row * 16 + col + 1] = make_float2(v.z, v.w);
+        }
+        __syncthreads();
+        for (int j = tid; j < TN; j += blockDim.x) {
+            float accr = 0.f, acci = 0.f;
+            for (int k = 0; k < A.n_terms; ++k) {
+                const float2 v = tile[j ^ xl[k]];
+                const float sg = (__popc(j & zl[k]) & 1) ? -sgn[k] : sgn[k];
+                const float cr = coef[k].x * sg, ci = coef[k].y * sg;
+                accr = fmaf(cr, v.x, fmaf(-ci, v.y, accr));
+                acci = fmaf(cr, v.y, fmaf(ci, v.x, acci));
+            }
+            const uint64_t y = g0 | rowoff[j >> 4] | (uint64_t)(j & 15);
+            if (A.accumulate) {
+                const float2 o = l[y];
+                accr += o.x;
+                acci += o.y;
+            }
+            l[y] = make_float2(accr, acci);
+        }
+    }
+}
+
+template <int H>
+static cudaError_t psum_tile_launch(const PsumTileArgs &A, cudaStream_t st) {
+    const int smem = (1 << (4 + H)) * (int)sizeof(float2);
+    dim3 grid((unsigned)A.grid, (unsigned)A.batch);
+    pauli_sum_tile_kernel<H><<<grid, 256, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pauli_sum_tile(const PsumTileArgs &A, cudaStream_t st) {
+    if (A.H < 1 || A.H > 7 || A.grid < 1 || A.batch < 1 || A.n_terms < 1 || A.n_terms > kPsumMaxTerms ||
+        (A.elems >> (4 + A.H)) < 1)
+        return cudaErrorInvalidValue;
+    switch (A.H) {
+        case 1: return psum_tile_launch<1>(A, st);
+        case 2: return psum_tile_launch<2>(A, st);
+        case 3: return psum_tile_launch<3>(A, st);
+        case 4: return psum_tile_launch<4>(A, st);
+        case 5: return psum_tile_launch<5>(A, st);
+        case 6: return psum_tile_launch<6>(A, st);
+        default: return psum_tile_launch<7>(A, st);
+    }
+}
+
 cudaError_t launch_apply_pauli_sum(const float2 *psi, float2 *lam, long long elems, int batch,
                                    const PauliDev *terms, int n_terms, cudaStream_t st, long long bstride) {
     long long blocks = (elems + 255) / 256;

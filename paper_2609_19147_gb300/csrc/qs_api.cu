@@ -1204,6 +1204,65 @@ void invert_gate(const RGate &g, std::vector<RGate> &out) {
 }  // namespace
 
 
+namespace {
+// Tile bit sets for lam = H psi on shared-memory tiles: every term's x mask
+// must lie in the 4 low index bits plus the H high bits of one pass.  Terms
+// are regrouped pass by pass (diagonal terms in the first pass); returns false
+// when a mask does not fit or more than 6 passes would be needed.
+struct PsumPass {
+    std::vector<int> hb;      // ascending high bits
+    size_t first, count;      // range in the regrouped term array
+};
+bool plan_psum_passes(int n, const std::vector<PauliDev> &terms, std::vector<PauliDev> &out,
+                      std::vector<PsumPass> &passes) {
+    if (n < 8 || terms.empty()) return false;
+    const int H = std::min(7, n - 4);
+    std::vector<uint64_t> sets;                 // high-bit set of each pass
+    std::vector<std::vector<PauliDev>> groups;
+    std::vector<PauliDev> diag;
+    for (const PauliDev &t : terms) {
+        const uint64_t hx = t.x & ~15ull;
+        if (hx == 0) {
+            diag.push_back(t);
+            continue;
+        }
+        if (__builtin_popcountll(hx) > H) return false;
+        size_t g = 0;
+        for (; g < sets.size(); ++g)
+            if (__builtin_popcountll(sets[g] | hx) <= H) break;
+        if (g == sets.size()) {
+            sets.push_back(0);
+            groups.emplace_back();
+        }
+        sets[g] |= hx;
+        groups[g].push_back(t);
+    }
+    if (sets.empty()) {
+        sets.push_back(0);
+        groups.emplace_back();
+    }
+    groups[0].insert(groups[0].begin(), diag.begin(), diag.end());
+    out.clear();
+    passes.clear();
+    for (size_t g = 0; g < sets.size(); ++g) {
+        uint64_t S = sets[g];
+        for (int b = 4; b < n && __builtin_popcountll(S) < H; ++b) S |= 1ull << b;   // fill the tile
+        std::vector<int> hb;
+        for (int b = 4; b < n; ++b)
+            if ((S >> b) & 1) hb.push_back(b);
+        for (size_t i = 0; i < groups[g].size(); i += kPsumMaxTerms) {
+            PsumPass ps;
+            ps.hb = hb;
+            ps.first = out.size();
+            ps.count = std::min<size_t>(kPsumMaxTerms, groups[g].size() - i);
+            out.insert(out.end(), groups[g].begin() + i, groups[g].begin() + i + ps.count);
+            passes.push_back(ps);
+        }
+    }
+    return passes.size() <= 6;
+}
+}  // namespace
+
 qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const double *params, int n_params,
                   const qs_pauli *terms, size_t n_terms, double *energy, double *grad) {
     if (!st || !energy || !grad || (n_terms && !terms) || (n_gates && !gates))
@@ -1366,13 +1425,45 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
     std::vector<PauliDev> hp;
     for (auto &x : t) hp.push_back({x.coeff, x.x, x.z});
     std::stable_sort(hp.begin(), hp.end(), [](const PauliDev &a, const PauliDev &b) { return a.x < b.x; });
+    // shared-memory tiles when the x masks fit a few tile bit sets
+    std::vector<PauliDev> regrouped;
+    std::vector<PsumPass> ppass;
+    const bool tiled_sum = plan_psum_passes(st->n, hp, regrouped, ppass);
+    if (tiled_sum) hp = regrouped;
     const int n_h = (int)hp.size();
     hp.push_back({1.0, 0, 0});
     s = ensure_terms(st, hp.size());
     if (s != QS_OK) return s;
     s = h2d_async(st, st->d_terms, hp.data(), hp.size() * sizeof(PauliDev));
     if (s != QS_OK) return s;
-    if (n_h) {
+    if (n_h && tiled_sum) {
+        for (size_t k = 0; k < ppass.size(); ++k) {
+            PsumTileArgs A;
+            std::memset(&A, 0, sizeof A);
+            A.psi = W;
+            A.lam = W + E;
+            A.elems = E;
+            A.bstride = 2 * E;
+            A.batch = B;
+            A.H = (int)ppass[k].hb.size();
+            uint64_t tb = 15;
+            for (int j = 0; j < A.H; ++j) {
+                A.hb[j] = ppass[k].hb[j];
+                tb |= 1ull << A.hb[j];
+            }
+            for (int b = 0; b < st->n; ++b)
+                if (!((tb >> b) & 1)) A.outer[A.n_outer++] = b;
+            A.terms = st->d_terms + ppass[k].first;
+            A.n_terms = (int)ppass[k].count;
+            A.accumulate = k > 0;
+            const long long n_tiles = E >> (4 + A.H);
+            A.grid = (int)std::max(1ll, std::min<long long>(n_tiles, (8ll * g_num_sms[st->dev] + B - 1) / B));
+            cudaEvent_t ev;
+            prof_begin(st, &ev);
+            QS_CUDA(launch_pauli_sum_tile(A, st->stream));
+            prof_end(st, ev, "pauli_sum", (k ? 24.0 : 16.0) * (double)E * B);
+        }
+    } else if (n_h) {
         cudaEvent_t ev;
         prof_begin(st, &ev);
         QS_CUDA(launch_apply_pauli_sum(W, W + E, E, B, st->d_terms, n_h, st->stream, 2 * E));

@@ -120,6 +120,27 @@ cudaError_t launch_expect_finish(const double *partial, double *out, int batch, 
 cudaError_t launch_apply_pauli_sum(const float2 *psi, float2 *lam, long long state_elems, int batch,
                                    const PauliDev *terms, int n_terms, cudaStream_t st, long long bstride = 0);
 
+// The same sum over tiles of 2^(4 + H) amplitudes (the 4 low index bits and
+// the H <= 8 high bits hb[]) staged in shared memory: every term's x mask lies
+// in the tile's bits, so psi[y ^ x] is read from the tile.  A sum whose x
+// masks need several bit sets runs as several such passes, the later ones
+// adding into lam (accumulate = 1).
+constexpr int kPsumMaxTerms = 64;
+struct PsumTileArgs {
+    const float2 *psi;
+    float2 *lam;               // item b at psi + b * bstride, lam + b * bstride
+    long long elems, bstride;
+    int batch, H;
+    int hb[8];                 // ascending high tile bits (>= 4)
+    int n_outer;
+    int outer[kMaxQubits];     // the other index bits, ascending
+    const PauliDev *terms;     // device, <= kPsumMaxTerms, x masks inside the tile
+    int n_terms;
+    int accumulate;
+    int grid;                  // CTAs per item (they stride over the item's tiles)
+};
+cudaError_t launch_pauli_sum_tile(const PsumTileArgs &A, cudaStream_t st);
+
 // Adjoint-method overlaps of one state pair (psi_b, lam_b) per batch item:
 // for the k <= 4 group bits g_j, Im<lam|X_j|psi> and Im<lam|Y_j|psi> (pairs in
 // registers) and S_j = sum_{x_gj = 1} Im(conj(lam_x) psi_x); for the bits of
