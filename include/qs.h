@@ -193,9 +193,11 @@ qs_status qs_expect(qs_state *st, const qs_pauli *terms, size_t n_terms, double 
  * grad: batch x n_params doubles (zero for unused indices).  Parameterised
  * gates must be QS_RX, QS_RY, QS_RZ, QS_RZZ or QS_CP (else
  * QS_ERR_UNSUPPORTED); each index may feed several gates (contributions add).
- * Needs device memory for two states per batch item (the psi / lambda pairs of
- * the reverse sweep), allocated at the first call and kept with the state
- * until qs_free (a later call with a larger batch x 2^n reallocates it).
+ * Workspace: when the device has room, K + 1 states per batch item (K =
+ * gradient points: psi is stored at each during the forward pass and the
+ * reverse sweep un-applies only lambda); otherwise two (the psi / lambda
+ * pairs, both un-applied).  It is allocated at the first call and kept with
+ * the state until qs_free (a later call that needs more reallocates it).
  * Synchronous. */
 qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates,
                   const double *params, int n_params,

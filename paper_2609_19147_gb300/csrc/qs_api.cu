@@ -1305,7 +1305,9 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
     };
     size_t next_seg = 0;
     std::vector<Plan> seg_plans;
-    // dry run of the sweep: the segments in execution order
+    // dry run of the sweep: the segments in execution order, and the gradient
+    // points (the last gate index of each point's layer or 2q gate), latest first
+    std::vector<size_t> gpts;
     for (size_t gi = n_gates; gi-- > 0;) {
         if (rg[0][gi].nw == 1) {
             size_t lo = gi;
@@ -1313,15 +1315,38 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
             bool has_param = false;
             for (size_t k = lo; k <= gi; ++k)
                 if (gates[k].param_idx >= 0) has_param = true;
-            if (has_param) close_segment();
+            if (has_param) {
+                close_segment();
+                gpts.push_back(gi);
+            }
             for (size_t k = gi + 1; k-- > lo;) pending.push_back(k);
             gi = lo;
             continue;
         }
-        if (gates[gi].param_idx >= 0) close_segment();
+        if (gates[gi].param_idx >= 0) {
+            close_segment();
+            gpts.push_back(gi);
+        }
         pending.push_back(gi);
     }
     pending.clear();   // the gates before the first gradient point are never un-applied
+    // Checkpoint mode, when the device has room for one copy of the states per
+    // gradient point: the forward pass stores psi at every gradient point and
+    // the reverse sweep un-applies only lambda (half the work of un-applying
+    // the (psi, lambda) pairs).  Otherwise the pairs are un-applied.
+    const long long E = st->elems;
+    const size_t K = gpts.size();
+    const size_t ck_bytes = (K + 1) * (size_t)B * E * sizeof(float2);
+    bool ckpt = false;
+    {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+            const size_t held = st->grad_ws_bytes;
+            ckpt = K > 0 && fr + held > ck_bytes + ((size_t)2 << 30);
+        }
+        cudaGetLastError();
+    }
+    const int un_b = ckpt ? 1 : 2;   // states per item in an un-apply launch
     // the un-apply plans are built on host threads while the GPU runs the
     // forward circuit and the Hamiltonian
     qs_status seg_status = QS_OK;
@@ -1353,8 +1378,8 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
                 }
             std::vector<Plan> p2, pB;
             std::string err;
-            qs_status r = build_plans_parallel(st->n, 2, l2, fo, p2, err);
-            if (r == QS_OK) r = build_plans_parallel(st->n, 2 * B, lB, fo, pB, err);
+            qs_status r = build_plans_parallel(st->n, un_b, l2, fo, p2, err);
+            if (r == QS_OK) r = build_plans_parallel(st->n, un_b * B, lB, fo, pB, err);
             if (r != QS_OK) {
                 seg_status = r;
                 seg_err = err;
@@ -1371,46 +1396,68 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
             if (t.joinable()) t.join();
         }
     } joiner{seg_thread};
-    // 1. forward: psi = U(theta)|0>, one fused plan per item (built in parallel)
-    QS_CUDA(launch_init_zero(st->home, st->elems, B, st->stream));
-    qs_opts o = default_opts(nullptr);
-    {
-        std::vector<Plan> fwd;
-        std::string err;
-        s = build_plans_parallel(st->n, 1, rg, o, fwd, err);
-        if (s != QS_OK) return fail(s, err);
-        Plan merged;
-        if (B > 1 && merge_item_plans(fwd, merged, B)) {   // one launch per pass, per-item constants
-            s = run_host_plan(st, std::move(merged), st->home, B);
-            if (s != QS_OK) return s;
-        } else {
-            for (int b = 0; b < B; ++b) {
-                s = run_host_plan(st, std::move(fwd[b]), st->home + (size_t)b * st->elems, 1);
-                if (s != QS_OK) return s;
-            }
-        }
-    }
-    // 2. the energy comes with lam = H psi below: E = Re <psi|lam>
-    // 3. the reverse sweep works on pairs (psi_b, lam_b) stored next to each
-    //    other, so that an item's pair is a batch of two states for the fused
-    //    executor; the caller's state keeps psi(theta)
-    const long long E = st->elems;
-    const size_t pair_bytes = (size_t)E * 2 * B * sizeof(float2);
-    if (st->grad_ws_bytes < pair_bytes) {
+    // workspace: checkpoint mode = K checkpoints then lambda (B states each);
+    // pair mode = (psi_b, lam_b) pairs next to each other, so that an item's
+    // pair is a batch of two states for the fused executor
+    const size_t ws_bytes = ckpt ? ck_bytes : (size_t)E * 2 * B * sizeof(float2);
+    if (st->grad_ws_bytes < ws_bytes) {
         if (st->grad_ws) {
             cudaStreamSynchronize(st->stream);
             cudaFree(st->grad_ws);
             st->grad_ws = nullptr;
             st->grad_ws_bytes = 0;
         }
-        if (cudaMalloc((void **)&st->grad_ws, pair_bytes) != cudaSuccess) {
+        if (cudaMalloc((void **)&st->grad_ws, ws_bytes) != cudaSuccess) {
             cudaGetLastError();
             st->grad_ws = nullptr;
             return fail(QS_ERR_OOM, "qs_grad: no memory for the adjoint states");
         }
-        st->grad_ws_bytes = pair_bytes;
+        st->grad_ws_bytes = ws_bytes;
     }
     float2 *W = st->grad_ws;
+    float2 *Lam = ckpt ? W + K * (size_t)B * E : W + E;   // lambda of item 0
+    const long long ls = ckpt ? E : 2 * E;                // item stride of psi / lambda buffers
+    auto ckpt_at = [&](size_t c) { return W + c * (size_t)B * E; };   // c = 0: earliest point
+    // 1. forward: psi = U(theta)|0>; per item plans built in parallel and merged
+    QS_CUDA(launch_init_zero(st->home, st->elems, B, st->stream));
+    qs_opts o = default_opts(nullptr);
+    auto run_forward = [&](size_t g_begin, size_t g_end) -> qs_status {   // gates [g_begin, g_end)
+        if (g_end <= g_begin) return QS_OK;
+        bool pi = false;
+        for (size_t i = g_begin; i < g_end; ++i)
+            if (gates[i].param_idx >= 0) pi = true;
+        std::vector<std::vector<RGate>> lists(pi ? B : 1);
+        for (size_t b = 0; b < lists.size(); ++b)
+            lists[b].assign(rg[b].begin() + g_begin, rg[b].begin() + g_end);
+        std::vector<Plan> fwd;
+        std::string err;
+        qs_status r = build_plans_parallel(st->n, pi ? 1 : B, lists, o, fwd, err);
+        if (r != QS_OK) return fail(r, err);
+        if (!pi) return run_host_plan(st, std::move(fwd[0]), st->home, B);
+        Plan merged;
+        if (B > 1 && merge_item_plans(fwd, merged, B)) return run_host_plan(st, std::move(merged), st->home, B);
+        for (int b = 0; b < B; ++b) {
+            r = run_host_plan(st, std::move(fwd[b]), st->home + (size_t)b * E, 1);
+            if (r != QS_OK) return r;
+        }
+        return QS_OK;
+    };
+    if (ckpt) {   // chunks ending at the gradient points, psi stored after each
+        size_t g0 = 0;
+        for (size_t c = 0; c < K; ++c) {
+            const size_t e = gpts[K - 1 - c] + 1;
+            s = run_forward(g0, e);
+            if (s != QS_OK) return s;
+            QS_CUDA(cudaMemcpyAsync(ckpt_at(c), st->home, (size_t)B * E * sizeof(float2), cudaMemcpyDeviceToDevice,
+                                    st->stream));
+            g0 = e;
+        }
+        s = run_forward(g0, n_gates);
+    } else {
+        s = run_forward(0, n_gates);
+    }
+    if (s != QS_OK) return s;
+    // 2. the energy comes with lam = H psi below: E = Re <psi|lam>
     qs_state *aux = nullptr;
     struct Guard {
         qs_state **aux;
@@ -1418,8 +1465,10 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
             if (*aux) qs_free(*aux);
         }
     } guard{&aux};
-    QS_CUDA(cudaMemcpy2DAsync(W, 2 * E * sizeof(float2), st->home, E * sizeof(float2), E * sizeof(float2), B,
-                              cudaMemcpyDeviceToDevice, st->stream));
+    const float2 *Psi0 = ckpt ? st->home : W;   // psi(theta) next to lambda for the energy
+    if (!ckpt)
+        QS_CUDA(cudaMemcpy2DAsync(W, 2 * E * sizeof(float2), st->home, E * sizeof(float2), E * sizeof(float2), B,
+                                  cudaMemcpyDeviceToDevice, st->stream));
     // lam = H psi; the term array (H's terms, then the identity used for the
     // energy) stays alive until the call ends, so nothing waits here
     std::vector<PauliDev> hp;
@@ -1440,10 +1489,10 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
         for (size_t k = 0; k < ppass.size(); ++k) {
             PsumTileArgs A;
             std::memset(&A, 0, sizeof A);
-            A.psi = W;
-            A.lam = W + E;
+            A.psi = Psi0;
+            A.lam = Lam;
             A.elems = E;
-            A.bstride = 2 * E;
+            A.bstride = ls;
             A.batch = B;
             A.H = (int)ppass[k].hb.size();
             uint64_t tb = 15;
@@ -1466,10 +1515,10 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
     } else if (n_h) {
         cudaEvent_t ev;
         prof_begin(st, &ev);
-        QS_CUDA(launch_apply_pauli_sum(W, W + E, E, B, st->d_terms, n_h, st->stream, 2 * E));
+        QS_CUDA(launch_apply_pauli_sum(Psi0, Lam, E, B, st->d_terms, n_h, st->stream, ls));
         prof_end(st, ev, "pauli_sum", 16.0 * (double)E * B);
     } else {
-        QS_CUDA(cudaMemset2DAsync(W + E, 2 * E * sizeof(float2), 0, E * sizeof(float2), B, st->stream));
+        QS_CUDA(cudaMemset2DAsync(Lam, ls * sizeof(float2), 0, E * sizeof(float2), B, st->stream));
     }
     // E_b = Re sum_x conj(lam_x) psi_x into a device array, read with the gradients
     double *d_en = nullptr;
@@ -1487,10 +1536,10 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
         if (s != QS_OK) return s;
         ExpectArgs A;
         std::memset(&A, 0, sizeof A);
-        A.psi = W;
-        A.lam = W + E;
+        A.psi = Psi0;
+        A.lam = Lam;
         A.state_elems = E;
-        A.bstride = 2 * E;
+        A.bstride = ls;
         A.batch = B;
         A.xmask = 0;
         A.n_terms = 1;
@@ -1503,7 +1552,7 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
         prof_end(st, ev, "expect", 16.0 * (double)E * B);
         QS_CUDA(launch_expect_finish(st->d_partial, d_en, B, grid, 1, st->stream));
     }
-    s = qs_wrap(W, st->n, 2 * B, st->stream, &aux);
+    s = ckpt ? qs_wrap(Lam, st->n, B, st->stream, &aux) : qs_wrap(W, st->n, 2 * B, st->stream, &aux);
     if (s != QS_OK) return s;
     for (size_t i = 0; i < (size_t)B * n_params; ++i) grad[i] = 0.0;
 
@@ -1523,16 +1572,19 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
         if (pending.empty()) return QS_OK;
         pending.clear();
         const Segment &sg = segs[next_seg++];
-        if (!sg.per_item) return run_host_plan(aux, std::move(seg_plans[sg.first_plan]), W, 2 * B);
-        if (B > 1) {   // the items' plans merged: one launch per pass over all pairs
+        // checkpoint mode: lambda only (B states); pair mode: all pairs (2B)
+        float2 *base = ckpt ? Lam : W;
+        const int nb = un_b * B;
+        if (!sg.per_item) return run_host_plan(aux, std::move(seg_plans[sg.first_plan]), base, nb);
+        if (B > 1) {   // the items' plans merged: one launch per pass over all items
             std::vector<Plan> items(std::make_move_iterator(seg_plans.begin() + sg.first_plan),
                                     std::make_move_iterator(seg_plans.begin() + sg.first_plan + B));
             Plan merged;
-            if (merge_item_plans(items, merged, 2 * B)) return run_host_plan(aux, std::move(merged), W, 2 * B);
+            if (merge_item_plans(items, merged, nb)) return run_host_plan(aux, std::move(merged), base, nb);
             for (int b = 0; b < B; ++b) seg_plans[sg.first_plan + b] = std::move(items[b]);
         }
         for (int b = 0; b < B; ++b) {
-            qs_status r = run_host_plan(aux, std::move(seg_plans[sg.first_plan + b]), W + (size_t)2 * b * E, 2);
+            qs_status r = run_host_plan(aux, std::move(seg_plans[sg.first_plan + b]), base + (size_t)b * ls, un_b);
             if (r != QS_OK) return r;
         }
         return QS_OK;
@@ -1634,7 +1686,9 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
             if (p) cudaFreeAsync(p, st->stream);
         }
     } guard3{st, d_res};
-    size_t li = 0;
+    size_t li = 0, gp = 0;   // layers done, gradient points done
+    // psi at the current gradient point: its checkpoint, or the pairs' psi
+    auto psi_now = [&]() -> const float2 * { return ckpt ? ckpt_at(K - 1 - gp) : W; };
     for (size_t gi = n_gates; gi-- > 0;) {
         const RGate &r0 = rg[0][gi];
         if (r0.nw == 1) {
@@ -1646,7 +1700,7 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
             if (has_param) {
                 s = flush();
                 if (s != QS_OK) return s;
-                if (li >= layers.size()) return fail(QS_ERR_INTERNAL, "qs_grad: layer bookkeeping");
+                if (li >= layers.size() || (ckpt && gp >= K)) return fail(QS_ERR_INTERNAL, "qs_grad: layer bookkeeping");
                 const LayerRec &L = layers[li++];
                 for (size_t c = 0; c < L.launches.size(); ++c) {
                     const XyzLaunch &x = L.launches[c];
@@ -1655,10 +1709,10 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
                     if (tiled) {
                         XyzTileArgs A;
                         std::memset(&A, 0, sizeof A);
-                        A.psi = W;
-                        A.lam = W + E;
+                        A.psi = psi_now();
+                        A.lam = Lam;
                         A.elems = E;
-                        A.bstride = 2 * E;
+                        A.bstride = ls;
                         A.batch = B;
                         A.n = st->n;
                         A.H = x.k;
@@ -1671,10 +1725,10 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
                     } else {
                         XyzArgs A;
                         std::memset(&A, 0, sizeof A);
-                        A.psi = W;
-                        A.lam = W + E;
+                        A.psi = psi_now();
+                        A.lam = Lam;
                         A.elems = E;
-                        A.bstride = 2 * E;
+                        A.bstride = ls;
                         A.batch = B;
                         A.k = x.k;
                         for (int j = 0; j < A.k; ++j) A.gbit[j] = x.gbit[j];
@@ -1687,6 +1741,7 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
                     QS_CUDA(launch_expect_finish(st->d_partial, d_res + (L.first + c) * B * slots, B, xgrid, slots / 2,
                                                  st->stream));
                 }
+                ++gp;
             }
             for (size_t k = gi + 1; k-- > lo;) pending.push_back(k);
             gi = lo;
@@ -1695,6 +1750,7 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
         if (gates[gi].param_idx >= 0) {   // RZZ / CP: generator overlap at the post-gate states
             s = flush();
             if (s != QS_OK) return s;
+            if (ckpt && gp >= K) return fail(QS_ERR_INTERNAL, "qs_grad: gradient point bookkeeping");
             std::vector<TermIdx> gt;
             auto term = [&](double c, uint64_t x, uint64_t z) {
                 TermIdx q;
@@ -1714,7 +1770,7 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
                 term(0.25, 0, ba | bb);
             }
             std::vector<double> S;
-            s = overlaps(st, W, W + E, B, gt, S, 2 * E);
+            s = overlaps(st, psi_now(), Lam, B, gt, S, ls);
             if (s != QS_OK) return s;
             for (int b = 0; b < B; ++b) {
                 double im_tot = 0.0;
@@ -1726,6 +1782,7 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
                 // R(t) = exp(-i t G/2): dE/dt = Im<lam|G|psi>;  CP(t) = exp(i t P11): dE/dt = -2 Im<lam|P11|psi>
                 grad[(size_t)b * n_params + gates[gi].param_idx] += gates[gi].kind == QS_CP ? -2.0 * im_tot : im_tot;
             }
+            ++gp;
         }
         pending.push_back(gi);
     }
