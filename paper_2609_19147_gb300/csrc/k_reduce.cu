@@ -464,26 +464,19 @@ __global__ void __launch_bounds__(kXyzTThreads) xyz_tile_kernel(const XyzTileArg
         }
         __syncthreads();   // tile k is in shared memory for every thread
         const float2 *ps = xts + (size_t)(k & 1) * 2 * E, *ls = ps + E;
-        // Z parts: Im(conj(lam) psi) into the total and the set tile bits
+        // Z parts (Im(conj(lam) psi) into the total and the set tile bits) come
+        // with the first pair sweep, which holds 16 amplitudes per item
         float tot = 0.f;
         float zt[T];
 #pragma unroll
         for (int t = 0; t < T; ++t) zt[t] = 0.f;
-        for (int e = tid; e < E; e += kXyzTThreads) {
-            const int o = xt_off(e >> 4, e & 15);
-            const float2 p = ps[o], l = ls[o];
-            const float im = l.x * p.y - l.y * p.x;
-            tot += im;
-#pragma unroll
-            for (int t = 0; t < T; ++t)
-                if ((e >> t) & 1) zt[t] += im;
-        }
         // pair sweeps over 4 tile bits at a time
 #pragma unroll
         for (int sw = 0; sw < 3; ++sw) {
             if (4 * sw >= T) break;
             const int g0 = 4 * sw, ng = (T - g0) < 4 ? (T - g0) : 4;
-            if (!((A.xymask >> g0) & ((1u << ng) - 1))) continue;
+            const bool xy = ((A.xymask >> g0) & ((1u << ng) - 1)) != 0;
+            if (sw > 0 && !xy) continue;
             const int items = E >> ng;
             for (int it = tid; it < items; it += kXyzTThreads) {
                 const int lo = it & ((1 << g0) - 1), hi = it >> g0;
@@ -496,6 +489,29 @@ __global__ void __launch_bounds__(kXyzTThreads) xyz_tile_kernel(const XyzTileArg
                     const int o = xt_off(e >> 4, e & 15);
                     p[j] = ps[o];
                     l[j] = ls[o];
+                }
+                if (sw == 0) {   // g0 = 0: j holds tile bits 0..ng-1, the item the rest
+                    float im[16], it_sum = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        if (j >= (1 << ng)) break;
+                        im[j] = l[j].x * p[j].y - l[j].y * p[j].x;
+                        it_sum += im[j];
+                    }
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        if (m >= ng) break;
+                        float z = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (j < (1 << ng) && ((j >> m) & 1)) z += im[j];
+                        zt[m] += z;
+                    }
+#pragma unroll
+                    for (int t = 4; t < T; ++t)
+                        if ((e0 >> t) & 1) zt[t] += it_sum;
+                    tot += it_sum;
+                    if (!xy) continue;
                 }
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
