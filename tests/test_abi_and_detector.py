@@ -217,3 +217,17 @@ def test_uniform_pair_sums_become_count_lookups(qs):
     rng = np.random.default_rng(2)
     rz = [W.Gate("RZZ", (b, b + 1), (float(rng.uniform(0, 6)),)) for b in range(27)]
     assert "DIAGC=" not in _passes(qs, 28, rz)[0]
+
+
+def test_qaoa_cost_layers_and_tfim_pass_count(qs):
+    # every cost layer of a QAOA circuit on a 3-regular graph is a count
+    # lookup, and the 30q TFIM workload keeps its 201 HBM passes (100 Strang
+    # steps: the light-cone fusion of consecutive steps)
+    n = 20
+    edges = W.random_regular3_graph(n, np.random.default_rng(9))
+    gl = W.qaoa_gates(n, edges, [0.4, 0.7, 1.1, 0.2], [0.3, 0.5, 0.9, 1.3])
+    text, _ = _passes(qs, n, gl)
+    d = sum(int(m) for m in re.findall(r" DIAG=(\d+)", text))
+    assert sum(int(m) for m in re.findall(r"DIAGC=(\d+)", text)) == d >= 4, text
+    tf = W.tfim_gates(30, 100, 0.05, 1.0, W.tfim_fields(30, 3), order=2)
+    assert _passes(qs, 30, tf)[1] == 201
