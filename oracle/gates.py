@@ -9,7 +9,7 @@ mapping theta = -2 J dt of Sec. 4.1 fixes RZZ(theta) = exp(-i theta/2 Z(x)Z).
 Multi-qubit matrices are indexed with the first listed wire as the most
 significant bit (controls first).
 
-Only tests/, the graft smoke check and the bench's CPU-baseline leg may use
+Only tests/, __graft_entry__.smoke() and the bench's CPU-baseline legs may use
 this package; the CUDA path never imports it.
 """
 from __future__ import annotations

@@ -9,7 +9,7 @@
  * multiplies them by the matrix and scatters them back.  No fusion, no
  * tables, no special cases.
  *
- * Only tests/, the graft smoke check and the bench's CPU-baseline leg load
+ * Only tests/, __graft_entry__.smoke() and the bench's CPU-baseline legs load
  * this library.  It shares no code with the CUDA path.
  */
 #include <complex.h>
