@@ -1346,6 +1346,30 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
         }
         cudaGetLastError();
     }
+    // workspace: checkpoint mode = K checkpoints then lambda (B states each);
+    // pair mode = (psi_b, lam_b) pairs next to each other, so that an item's
+    // pair is a batch of two states for the fused executor.  Allocated before
+    // the un-apply plans are built (their batch depends on the mode); when the
+    // checkpoints cannot be allocated after all, pair mode is used.
+    auto ensure_ws = [&](size_t bytes) {
+        if (st->grad_ws_bytes >= bytes) return true;
+        if (st->grad_ws) {
+            cudaStreamSynchronize(st->stream);
+            cudaFree(st->grad_ws);
+            st->grad_ws = nullptr;
+            st->grad_ws_bytes = 0;
+        }
+        if (cudaMalloc((void **)&st->grad_ws, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            st->grad_ws = nullptr;
+            return false;
+        }
+        st->grad_ws_bytes = bytes;
+        return true;
+    };
+    if (ckpt && !ensure_ws(ck_bytes)) ckpt = false;
+    if (!ckpt && !ensure_ws((size_t)E * 2 * B * sizeof(float2)))
+        return fail(QS_ERR_OOM, "qs_grad: no memory for the adjoint states");
     const int un_b = ckpt ? 1 : 2;   // states per item in an un-apply launch
     // the un-apply plans are built on host threads while the GPU runs the
     // forward circuit and the Hamiltonian
@@ -1396,24 +1420,6 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
             if (t.joinable()) t.join();
         }
     } joiner{seg_thread};
-    // workspace: checkpoint mode = K checkpoints then lambda (B states each);
-    // pair mode = (psi_b, lam_b) pairs next to each other, so that an item's
-    // pair is a batch of two states for the fused executor
-    const size_t ws_bytes = ckpt ? ck_bytes : (size_t)E * 2 * B * sizeof(float2);
-    if (st->grad_ws_bytes < ws_bytes) {
-        if (st->grad_ws) {
-            cudaStreamSynchronize(st->stream);
-            cudaFree(st->grad_ws);
-            st->grad_ws = nullptr;
-            st->grad_ws_bytes = 0;
-        }
-        if (cudaMalloc((void **)&st->grad_ws, ws_bytes) != cudaSuccess) {
-            cudaGetLastError();
-            st->grad_ws = nullptr;
-            return fail(QS_ERR_OOM, "qs_grad: no memory for the adjoint states");
-        }
-        st->grad_ws_bytes = ws_bytes;
-    }
     float2 *W = st->grad_ws;
     float2 *Lam = ckpt ? W + K * (size_t)B * E : W + E;   // lambda of item 0
     const long long ls = ckpt ? E : 2 * E;                // item stride of psi / lambda buffers
