@@ -231,3 +231,38 @@ def test_qaoa_cost_layers_and_tfim_pass_count(qs):
     assert sum(int(m) for m in re.findall(r"DIAGC=(\d+)", text)) == d >= 4, text
     tf = W.tfim_gates(30, 100, 0.05, 1.0, W.tfim_fields(30, 3), order=2)
     assert _passes(qs, 30, tf)[1] == 201
+
+
+def test_planner_fuzz_all_option_combinations(qs):
+    # random circuits over the whole vocabulary, uniform-angle layers and
+    # random graphs, planned under every tile shape / group size / dense
+    # precision: the planner either succeeds with at least one pass for a
+    # non-trivial circuit or rejects an invalid option with INVALID_ARG --
+    # never another status (no internal scheduling failure)
+    rng = np.random.default_rng(2024)
+    shapes = [(0, 0, 0), (13, 4, 4), (13, 5, 5), (12, 4, 5), (12, 5, 4), (10, 3, 3), (8, 2, 2), (13, 4, 1)]
+    precs = [None, "fp32", "tf32x3", "bf16"]
+    for trial in range(200):
+        n = int(rng.integers(2, 23))
+        kind = trial % 3
+        if kind == 0:
+            gl = W.random_circuit(n, int(rng.integers(5, 120)), int(rng.integers(1 << 30)))
+        elif kind == 1:
+            th = float(rng.uniform(-3, 3))
+            gl = [W.Gate("RY", (q,), (float(rng.uniform(0, 6)),)) for q in range(n)]
+            gl += [W.Gate("RZZ", (b, b + 1), (th,)) for b in range(n - 1)]
+            gl += [W.Gate("RZ", (q,), (0.3,)) for q in range(0, n, 2)]
+            gl += [W.Gate("RX", (q,), (float(rng.uniform(0, 6)),)) for q in range(n)]
+        else:
+            m = n + (n & 1) if n >= 4 else 4
+            edges = W.random_regular3_graph(m, rng)
+            gl = W.qaoa_gates(m, edges, [0.5, 1.2], [0.3, 0.8])
+            n = m
+        t, lq, r = shapes[int(rng.integers(len(shapes)))]
+        prec = precs[int(rng.integers(len(precs)))]
+        try:
+            text, passes = qs.plan_describe(n, gl, tile_qubits=t, low_qubits=lq, group_qubits=r, dense=prec)
+        except qs.QsError as e:
+            assert e.status == qs.QS_ERR_INVALID_ARG, (trial, n, t, lq, r, prec, str(e))
+            continue
+        assert passes >= 0 and text.startswith("FUSED"), (trial, text[:200])
