@@ -1,0 +1,78 @@
+"""The fusion detector's ops (and the dense-block regrouping) reproduce the
+gate-by-gate product, checked on the host in complex128: a C++ program links
+the planner, applies the detector's ops by their definitions and compares
+with applying every gate's full matrix in order.  Circuits: random gate lists
+over the whole vocabulary (n = 1..9), QFTs, Trotter and Heisenberg layers,
+QAOA layers, CNOT ladders and GHZ chains."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import __graft_entry__
+    __graft_entry__._build_lib_module().build()
+    import paper_2609_19147_gb300 as m
+    return m
+
+
+def _circuits():
+    out = []
+    rng = np.random.default_rng(17)
+    for n in range(1, 10):
+        for s in range(4):
+            out.append((n, W.random_circuit(n, 30 + 10 * s, 1000 * n + s)))
+    for n in (3, 6, 9):
+        out.append((n, W.qft_gates(n, swaps=True)))
+        out.append((n, W.tfim_gates(n, 3, 0.1, 1.0, W.tfim_fields(n, 3), order=2)))
+        out.append((n, W.tfim_gates(n, 2, 0.1, 1.0, 0.7, order=1)))
+        out.append((n, W.cnot_ladder(n) + W.ghz_gates(n)))
+        hz = []
+        for b in range(n - 1):
+            t = float(rng.uniform(0, 1))
+            hz += [W.Gate("RXX", (b, b + 1), (t,)), W.Gate("RYY", (b, b + 1), (t,)), W.Gate("RZZ", (b, b + 1), (t,))]
+        out.append((n, hz))
+    for n in (4, 6, 8):
+        edges = W.random_regular3_graph(n, rng)
+        out.append((n, W.qaoa_gates(n, edges, [0.4, 1.1], [0.7, 0.2])))
+    return out
+
+
+def test_detector_ops_match_gate_product(tmp_path, qs):
+    gxx = shutil.which("g++")
+    if gxx is None or not os.path.isdir("/usr/local/cuda/include"):
+        pytest.skip("needs g++ and the CUDA headers")
+    lines = []
+    for n, gl in _circuits():
+        cg = qs.CGates(gl)
+        lines.append(f"n {n} {cg.n}")
+        for i in range(cg.n):
+            g = cg.arr[i]
+            row = [g.kind, g.nw, g.w[0], g.w[1], g.w[2], repr(g.p[0]), repr(g.p[1]), repr(g.p[2])]
+            if g.dense:
+                row += [1] + [repr(g.dense[e]) for e in range(8)]
+            else:
+                row += [0]
+            lines.append(" ".join(str(x) for x in row))
+    src = tmp_path / "circuits.txt"
+    src.write_text("\n".join(lines) + "\n")
+    csrc = os.path.join(ROOT, "paper_2609_19147_gb300", "csrc")
+    exe = str(tmp_path / "check")
+    subprocess.check_call([gxx, "-O2", "-std=c++17", "-I", os.path.join(ROOT, "include"), "-I", csrc,
+                           "-I", "/usr/local/cuda/include",
+                           os.path.join(ROOT, "tests", "cpp", "detector_semantics_check.cpp"),
+                           os.path.join(csrc, "qs_plan.cpp"), "-o", exe, "-lpthread"])
+    out = subprocess.run([exe, str(src)], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0 and out.stdout.startswith("OK"), out.stdout + out.stderr
+    f = out.stdout.split()
+    assert int(f[1]) == len(_circuits())
+    counts = [int(x) for x in f[3:9]]      # U1, U2, DIAG, QFT, GF2, DENSE: every op kind was exercised
+    assert all(c > 0 for c in counts), out.stdout
