@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from gate_text import gate_lines
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -52,16 +53,9 @@ def test_detector_ops_match_gate_product(tmp_path, qs):
         pytest.skip("needs g++ and the CUDA headers")
     lines = []
     for n, gl in _circuits():
-        cg = qs.CGates(gl)
-        lines.append(f"n {n} {cg.n}")
-        for i in range(cg.n):
-            g = cg.arr[i]
-            row = [g.kind, g.nw, g.w[0], g.w[1], g.w[2], repr(g.p[0]), repr(g.p[1]), repr(g.p[2])]
-            if g.dense:
-                row += [1] + [repr(g.dense[e]) for e in range(8)]
-            else:
-                row += [0]
-            lines.append(" ".join(str(x) for x in row))
+        gl_text = gate_lines(qs, gl)
+        lines.append(f"n {n} {len(gl_text)}")
+        lines += gl_text
     src = tmp_path / "circuits.txt"
     src.write_text("\n".join(lines) + "\n")
     csrc = os.path.join(ROOT, "paper_2609_19147_gb300", "csrc")

@@ -1,0 +1,143 @@
+"""Fused plans checked on the host, pass by pass, against the oracle.
+
+A C++ program links the planner, builds the plan the executor would run
+(tile passes with sweeps, micro-ops, diagonal tables, count tables, QFT
+ladders, dense blocks in FP32 / 3xTF32 / BF16 constant layouts; permutation
+and gather passes), and interprets every pass on a complex128 state by the
+contracts the pass descriptors document, checking their structural
+invariants (tile and sweep bits, tensor-copy boxes, swizzled offsets,
+constant bounds and alignment) on the way.  The final state must match the
+complex128 oracle's gate-by-gate evolution of the same seeded input.
+
+Tolerances: constants are complex64 (relative error 2^-24 per entry), so a
+plan of a few hundred ops drifts by at most ~1e-5 relative (L2); 1e-4 is
+asserted.  BF16 dense blocks round U and X to 8-bit mantissas (2^-9 relative
+per block), so plans with them are held to 3e-2, enough to expose a wrong
+operand layout (an O(1) error)."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gate_text import gate_lines
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import __graft_entry__
+    __graft_entry__._build_lib_module().build()
+    import paper_2609_19147_gb300 as m
+    return m
+
+
+def _heisenberg(n, rng, rounds=2):
+    g = []
+    for _ in range(rounds):
+        for b in range(n - 1):
+            t = float(rng.uniform(-1, 1))
+            g += [W.Gate("RXX", (b, b + 1), (t,)), W.Gate("RYY", (b, b + 1), (t,)), W.Gate("RZZ", (b, b + 1), (t,))]
+        g += [W.Gate("RZ", (q,), (float(rng.uniform(-1, 1)),)) for q in range(n)]
+    return g
+
+
+def _zz_random_angles(n, rng):
+    g = [W.Gate("H", (q,)) for q in range(n)]
+    for _ in range(3 * n):
+        u, v = (int(x) for x in rng.choice(n, size=2, replace=False))
+        g.append(W.Gate("RZZ", (u, v), (float(rng.uniform(-3, 3)),)))
+    g += [W.Gate("RX", (q,), (0.3,)) for q in range(n)]
+    return g
+
+
+def _cases():
+    """(name, n, gates, (T, L, R, dense_prec, block_qubits))"""
+    rng = np.random.default_rng(23)
+    out = []
+    # random circuits over the whole vocabulary, several tile shapes and group sizes
+    shapes = [(0, 0, 0), (8, 4, 5), (8, 2, 3), (7, 3, 4), (6, 1, 2), (9, 4, 1), (10, 3, 5)]
+    for i, n in enumerate((9, 10, 11, 12)):
+        for j, sh in enumerate(shapes):
+            if (i + j) % 2 == 0:
+                out.append((f"random n={n} {sh}", n, W.random_circuit(n, 90, 300 + 10 * i + j), sh + (0, 0)))
+    # structured families at n = 14 (several tiles per pass)
+    n = 14
+    tf = W.tfim_gates(n, 4, 0.1, 1.0, W.tfim_fields(n, 3), order=2)
+    qaoa = W.qaoa_gates(n, W.random_regular3_graph(n, rng), [0.4, 1.1], [0.7, 0.2])
+    for sh in ((12, 4, 4), (13, 4, 5), (13, 4, 4), (9, 3, 3), (0, 0, 0)):
+        out.append((f"tfim {sh}", n, tf, sh + (0, 0)))
+        out.append((f"qaoa {sh}", n, qaoa, sh + (0, 0)))
+    for sh in ((13, 4, 5), (12, 4, 4), (10, 2, 3), (0, 0, 0)):
+        out.append((f"qft {sh}", n, W.qft_gates(n, swaps=True), sh + (0, 0)))
+    out.append(("suite", 13, W.suite28_gates(13, 2, 5), (12, 4, 4, 0, 0)))
+    out.append(("suite", 13, W.suite28_gates(13, 2, 6), (13, 4, 5, 0, 0)))
+    out.append(("ghz + ladder", 12, W.ghz_gates(12) + W.cnot_ladder(12) + W.wht_gates(12), (10, 4, 4, 0, 0)))
+    out.append(("controlled", 9, W.random_circuit(9, 80, 77, kinds=["CCX", "CSWAP", "CX", "CH", "CRY", "CY", "H"]),
+                (7, 2, 5, 0, 0)))
+    out.append(("heisenberg", 12, _heisenberg(12, rng), (10, 4, 5, 0, 0)))
+    out.append(("zz random angles", 12, _zz_random_angles(12, rng), (9, 4, 4, 0, 0)))
+    out.append(("zz random angles r5", 12, _zz_random_angles(12, rng), (12, 4, 5, 0, 0)))
+    # dense blocks in every precision and block size
+    for prec in (1, 2, 3):
+        for k in (3, 4, 5):
+            out.append((f"dense p={prec} k={k} random", 11, W.random_circuit(11, 80, 900 + 3 * prec + k),
+                        (9, 4, 5, prec, k)))
+        out.append((f"dense p={prec} tfim", 14, tf, (13, 4, 5, prec, 5)))
+    return out
+
+
+def test_plans_interpreted_on_host_match_oracle(tmp_path, qs):
+    gxx = shutil.which("g++")
+    if gxx is None or not os.path.isdir("/usr/local/cuda/include"):
+        pytest.skip("needs g++ and the CUDA headers")
+    cases = _cases()
+    lines, expect = [], []
+    for i, (name, n, gl, (T, L, R, prec, blk)) in enumerate(cases):
+        rng = np.random.default_rng(1000 + i)
+        psi0 = rng.standard_normal(2 ** n) + 1j * rng.standard_normal(2 ** n)
+        psi0 /= np.linalg.norm(psi0)
+        fin, fout = tmp_path / f"in{i}.bin", tmp_path / f"out{i}.bin"
+        psi0.astype(np.complex128).tofile(fin)
+        text = gate_lines(qs, gl)
+        lines.append(f"case {n} {T} {L} {R} {prec} {blk} {len(text)} {fin} {fout}")
+        lines += text
+        expect.append(oracle.simulate(n, gl, psi0.copy()))
+    src = tmp_path / "cases.txt"
+    src.write_text("\n".join(lines) + "\n")
+    csrc = os.path.join(ROOT, "paper_2609_19147_gb300", "csrc")
+    exe = str(tmp_path / "check")
+    subprocess.check_call([gxx, "-O2", "-std=c++17", "-I", os.path.join(ROOT, "include"), "-I", csrc,
+                           "-I", "/usr/local/cuda/include",
+                           os.path.join(ROOT, "tests", "cpp", "plan_interpret_check.cpp"),
+                           os.path.join(csrc, "qs_plan.cpp"), "-o", exe, "-lpthread"])
+    out = subprocess.run([exe, str(src)], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stdout[-3000:] + out.stderr[-2000:]
+    rows = [l.split() for l in out.stdout.splitlines() if l.startswith("CASE")]
+    assert len(rows) == len(cases)
+    micro = np.zeros(11, dtype=np.int64)
+    dense = np.zeros(3, dtype=np.int64)
+    kinds = {"perm": 0, "gather": 0, "tma": 0, "rows": 0, "swz": 0}
+    worst = []
+    for i, (name, n, gl, cfg) in enumerate(cases):
+        r = rows[i]
+        f = dict(zip(r[2:16:2], r[3:16:2]))
+        for k in kinds:
+            kinds[k] += int(f[k])
+        mi = r.index("micro")
+        micro += np.array([int(x) for x in r[mi + 1:mi + 12]])
+        di = r.index("dense")
+        dense += np.array([int(x) for x in r[di + 1:di + 4]])
+        got = np.fromfile(tmp_path / f"out{i}.bin", dtype=np.complex128)
+        err = np.linalg.norm(got - expect[i]) / np.linalg.norm(expect[i])
+        tol = 3e-2 if cfg[3] == 3 else 1e-4
+        worst.append((err, name))
+        assert err < tol, (name, cfg, err)
+    # every pass type, copy form and micro-op kind was exercised
+    assert all(v > 0 for v in kinds.values()), kinds
+    assert all(micro > 0), micro
+    assert all(dense > 0), dense
