@@ -13,11 +13,16 @@
 //     aligned innermost coordinate, legal box extents and 16-byte strides;
 //   * every constant read inside the pass's table; 16-byte constant loads at
 //     even offsets; control masks off the target bits.
+// Batches of parameter vectors: one plan per item, merged into one batched
+// plan with per-item constants (as the executor does when the items' plans
+// agree in structure); each item's state runs with its own constants and the
+// TMA boxes are checked at the batch coordinate of every item.
 // Input: a case file, one case per block:
-//   case <n> <T> <L> <R> <dense_prec> <block> <count> <psi0.bin> <out.bin>
-//   then <count> gate lines: kind nw w0 w1 w2 p0 p1 p2 has_dense [8 doubles]
-// psi0 / out: 2^n complex128.  Prints one "CASE <i> ..." line per case with
-// the pass and micro-op counts, or "FAIL <i> <reason>" and exits 1.
+//   case <n> <T> <L> <R> <dense_prec> <block> <count> <B> <P> <psi0.bin> <out.bin>
+//   then <count> gate lines: kind nw w0 w1 w2 p0 p1 p2 param_idx has_dense [8 doubles]
+//   then B x P parameter values (item after item)
+// psi0 / out: B x 2^n complex128.  Prints one "CASE <i> ..." line per case
+// with the pass and micro-op counts, or "FAIL <i> <reason>" and exits 1.
 #include <cmath>
 #include <complex>
 #include <cstdint>
@@ -78,9 +83,13 @@ double bf16_half(uint32_t w, int half) {
 
 class TileRun {
   public:
-    TileRun(int n, const HostPass &hp, Counts &cnt) : n_(n), hp_(hp), P_(hp.tile), cnt_(cnt) {}
+    // item: which item's constants; batch: states in the tensor the boxes address
+    TileRun(int n, const HostPass &hp, Counts &cnt, int item, int items, int batch)
+        : n_(n), hp_(hp), P_(hp.tile), cnt_(cnt), item_(item), items_(items), batch_(batch) {}
 
-    void run(std::vector<C> &psi) {
+    // psi: the item's state, at position `bi` of the batch
+    void run(C *psi, int bi) {
+        bi_ = bi;
         structure();
         const int T = P_.T;
         std::vector<uint64_t> outer;
@@ -103,6 +112,7 @@ class TileRun {
     const HostPass &hp_;
     const TilePass &P_;
     Counts &cnt_;
+    int item_, items_, batch_, bi_ = 0;
     uint64_t tilebits_ = 0;
     int gbit_[kMaxTileBits];   // global bit of tile-local bit k
 
@@ -117,12 +127,12 @@ class TileRun {
         return g;
     }
     C K(long i) {
-        need(i >= 0 && i < P_.n_const, "constant index " + std::to_string(i) + " outside the table");
-        return C(hp_.consts[i].x, hp_.consts[i].y);
+        const float2 &v = Kraw(i);
+        return C(v.x, v.y);
     }
     const float2 &Kraw(long i) {
         need(i >= 0 && i < P_.n_const, "constant index " + std::to_string(i) + " outside the table");
-        return hp_.consts[i];
+        return hp_.consts[(size_t)item_ * P_.n_const + i];
     }
 
     void structure() {
@@ -140,7 +150,7 @@ class TileRun {
         bool dense = false;
         for (int s = 0; s < P_.n_sweeps; ++s) dense |= P_.sweeps[s].dense != DS_NONE;
         need(P_.n_const >= 0 && P_.n_const <= (dense ? kMaxConstDense : kMaxConst), "constant count");
-        need((long)hp_.consts.size() == (long)P_.n_const, "constant vector size");
+        need((long)hp_.consts.size() == (long)items_ * P_.n_const, "constant vector size");
         // shared-memory offsets: XOR-linear, one-to-one over [0, 2^T)
         std::vector<uint32_t> basis;
         for (int k = 0; k < T; ++k) {
@@ -166,6 +176,7 @@ class TileRun {
             need(g.box[0] * 8 % 16 == 0, "inner box extent not a multiple of 16 bytes");
             if (P_.swizzle) need(g.box[0] * 8 <= 128, "inner box wider than the swizzle span");
             uint64_t vol = 1;
+            need(batch_ == 1 || g.batch_dim >= 0, "batched tensor copy without a batch dim");
             for (int d = 0; d < 5; ++d) {
                 need(g.box[d] >= 1 && g.box[d] <= 256 && g.box[d] <= g.gdim[d], "box extent");
                 if (d >= 1) need(g.gstride[d] % 16 == 0, "stride not a multiple of 16 bytes");
@@ -188,6 +199,7 @@ class TileRun {
         for (int d = 0; d < 5; ++d) {
             long long v = 0;
             if (d < g.ndims && g.kind[d] == 1) v = (long long)((ti >> g.off[d]) & ((1ull << g.w[d]) - 1));
+            if (d < g.ndims && d == g.batch_dim) v += (long long)bi_ << g.w[d];
             c[d] = v;
             need(v + g.box[d] <= (long long)g.gdim[d], "box outside the tensor");
         }
@@ -201,8 +213,9 @@ class TileRun {
                             const uint64_t e[5] = {e0, e1, e2, e3, e4};
                             uint64_t byte = (c[0] + e0) * 8;
                             for (int d = 1; d < 5; ++d) byte += (c[d] + e[d]) * g.gstride[d];
-                            need(byte % 8 == 0 && byte / 8 == (base | glob(t)), "box element of tile " +
-                                                                                    std::to_string(ti));
+                            const uint64_t want = ((uint64_t)bi_ << n_) + (base | glob(t));
+                            need(byte % 8 == 0 && byte / 8 == want, "box element of tile " + std::to_string(ti) +
+                                                                         " of item " + std::to_string(bi_));
                         }
     }
 
@@ -524,7 +537,7 @@ class TileRun {
     }
 };
 
-void run_perm(int n, const PermPass &pp, std::vector<C> &psi) {
+void run_perm(int n, const PermPass &pp, C *psi) {
     if (pp.n != n) throw Fail{"perm n"};
     uint64_t used = 0;
     for (int b = 0; b < n; ++b) {
@@ -532,29 +545,31 @@ void run_perm(int n, const PermPass &pp, std::vector<C> &psi) {
         used |= 1ull << pp.out_pos[b];
     }
     if (popc(used) != n) throw Fail{"perm is not a permutation"};
-    std::vector<C> out(psi.size());
-    for (uint64_t x = 0; x < psi.size(); ++x) {
+    const uint64_t N = 1ull << n;
+    std::vector<C> out(N);
+    for (uint64_t x = 0; x < N; ++x) {
         uint64_t y = 0;
         for (int b = 0; b < n; ++b)
             if ((x >> b) & 1) y |= 1ull << pp.out_pos[b];
         out[y ^ pp.xor_mask] = psi[x];
     }
-    psi.swap(out);
+    std::copy(out.begin(), out.end(), psi);
 }
 
-void run_gather(int n, const GatherPass &gp, std::vector<C> &psi) {
+void run_gather(int n, const GatherPass &gp, C *psi) {
     if (gp.n != n || gp.n_slices < 1 || gp.n_slices > 5 || 8 * gp.n_slices < n) throw Fail{"gather slices"};
-    std::vector<C> out(psi.size());
-    std::vector<char> hit(psi.size(), 0);
-    for (uint64_t y = 0; y < psi.size(); ++y) {
+    const uint64_t N = 1ull << n;
+    std::vector<C> out(N);
+    std::vector<char> hit(N, 0);
+    for (uint64_t y = 0; y < N; ++y) {
         uint64_t x = gp.c;
         for (int k = 0; k < gp.n_slices; ++k) x ^= gp.tab[k][(y >> (8 * k)) & 255];
-        if (x >= psi.size()) throw Fail{"gather source outside the state"};
+        if (x >= N) throw Fail{"gather source outside the state"};
         if (hit[x]) throw Fail{"gather is not a bijection"};
         hit[x] = 1;
         out[y] = psi[x];
     }
-    psi.swap(out);
+    std::copy(out.begin(), out.end(), psi);
 }
 
 }  // namespace
@@ -563,16 +578,17 @@ int main(int argc, char **argv) {
     if (argc < 2) return 2;
     FILE *fp = std::fopen(argv[1], "r");
     if (!fp) return 2;
-    int n, T, L, R, dprec, block, cnt, ci = 0;
+    int n, T, L, R, dprec, block, cnt, B, NP, ci = 0;
     char in_path[4096], out_path[4096];
-    while (std::fscanf(fp, " case %d %d %d %d %d %d %d %4095s %4095s", &n, &T, &L, &R, &dprec, &block, &cnt, in_path,
-                       out_path) == 9) {
+    while (std::fscanf(fp, " case %d %d %d %d %d %d %d %d %d %4095s %4095s", &n, &T, &L, &R, &dprec, &block, &cnt, &B,
+                       &NP, in_path, out_path) == 11) {
         std::vector<qs_gate> gl(cnt);
         std::vector<std::vector<double>> dense(cnt);
         for (int i = 0; i < cnt; ++i) {
-            int kind, nw, w0, w1, w2, hd;
+            int kind, nw, w0, w1, w2, pidx, hd;
             double p0, p1, p2;
-            if (std::fscanf(fp, "%d %d %d %d %d %lf %lf %lf %d", &kind, &nw, &w0, &w1, &w2, &p0, &p1, &p2, &hd) != 9)
+            if (std::fscanf(fp, "%d %d %d %d %d %lf %lf %lf %d %d", &kind, &nw, &w0, &w1, &w2, &p0, &p1, &p2, &pidx,
+                            &hd) != 10)
                 return 2;
             qs_gate &g = gl[i];
             std::memset(&g, 0, sizeof g);
@@ -584,7 +600,7 @@ int main(int argc, char **argv) {
             g.p[0] = p0;
             g.p[1] = p1;
             g.p[2] = p2;
-            g.param_idx = -1;
+            g.param_idx = pidx;
             if (hd) {
                 dense[i].resize(8);
                 for (int e = 0; e < 8; ++e)
@@ -592,12 +608,9 @@ int main(int argc, char **argv) {
                 g.dense = dense[i].data();
             }
         }
-        std::vector<RGate> rg;
-        std::string err;
-        if (resolve_gates(n, gl.data(), gl.size(), nullptr, 0, 0, rg, err) != QS_OK) {
-            std::printf("FAIL %d resolve: %s\n", ci, err.c_str());
-            return 1;
-        }
+        std::vector<double> params((size_t)B * NP);
+        for (auto &v : params)
+            if (std::fscanf(fp, "%lf", &v) != 1) return 2;
         qs_opts o;
         std::memset(&o, 0, sizeof o);
         o.mode = QS_MODE_FUSED;
@@ -606,44 +619,70 @@ int main(int argc, char **argv) {
         o.group_qubits = R;
         o.dense_prec = dprec;
         o.block_qubits = block;
-        Plan plan;
-        if (build_fused_plan(n, 1, rg, o, plan, err) != QS_OK) {
-            std::printf("FAIL %d plan: %s\n", ci, err.c_str());
-            return 1;
+        std::string err;
+        std::vector<Plan> plans(B);
+        for (int bi = 0; bi < B; ++bi) {
+            std::vector<RGate> rg;
+            if (resolve_gates(n, gl.data(), gl.size(), NP ? params.data() : nullptr, NP, bi, rg, err) != QS_OK) {
+                std::printf("FAIL %d resolve: %s\n", ci, err.c_str());
+                return 1;
+            }
+            if (build_fused_plan(n, 1, rg, o, plans[bi], err) != QS_OK) {
+                std::printf("FAIL %d plan: %s\n", ci, err.c_str());
+                return 1;
+            }
         }
+        // batched items run as one merged plan when the items' plans agree in structure
+        std::vector<Plan> run_plans;
+        bool merged = false;
+        if (B > 1) {
+            Plan m;
+            std::vector<Plan> copy = plans;
+            if (merge_item_plans(copy, m, B)) {
+                run_plans.push_back(std::move(m));
+                merged = true;
+            }
+        }
+        if (!merged) run_plans = plans;
         const size_t N = (size_t)1 << n;
-        std::vector<C> psi(N);
+        std::vector<C> psi(N * B);
         FILE *fi = std::fopen(in_path, "rb");
-        if (!fi || std::fread(psi.data(), sizeof(C), N, fi) != N) return 2;
+        if (!fi || std::fread(psi.data(), sizeof(C), psi.size(), fi) != psi.size()) return 2;
         std::fclose(fi);
         Counts c;
         size_t pi = 0;
+        size_t n_passes = run_plans[0].passes.size();
         try {
-            if (plan.items != 1) throw Fail{"single-item plan expected"};
-            for (; pi < plan.passes.size(); ++pi) {
-                const HostPass &hp = plan.passes[pi];
-                switch (hp.type) {
-                    case HostPass::TILE: TileRun(n, hp, c).run(psi); break;
-                    case HostPass::PERM:
-                        run_perm(n, hp.perm, psi);
-                        c.perm++;
-                        break;
-                    case HostPass::GATHER:
-                        run_gather(n, hp.gather, psi);
-                        c.gather++;
-                        break;
+            for (int bi = 0; bi < B; ++bi) {
+                const Plan &plan = merged ? run_plans[0] : run_plans[bi];
+                if (plan.items != (merged ? B : 1)) throw Fail{"plan items"};
+                C *st = psi.data() + (size_t)bi * N;
+                for (pi = 0; pi < plan.passes.size(); ++pi) {
+                    const HostPass &hp = plan.passes[pi];
+                    switch (hp.type) {
+                        case HostPass::TILE:
+                            TileRun(n, hp, c, merged ? bi : 0, plan.items, merged ? B : 1).run(st, merged ? bi : 0);
+                            break;
+                        case HostPass::PERM:
+                            run_perm(n, hp.perm, st);
+                            c.perm++;
+                            break;
+                        case HostPass::GATHER:
+                            run_gather(n, hp.gather, st);
+                            c.gather++;
+                            break;
+                    }
                 }
             }
         } catch (const Fail &f) {
-            std::printf("FAIL %d pass %zu (%s): %s\n", ci, pi, pi < plan.passes.size() ? plan.passes[pi].note.c_str() : "",
-                        f.why.c_str());
+            std::printf("FAIL %d pass %zu: %s\n", ci, pi, f.why.c_str());
             return 1;
         }
         FILE *fo = std::fopen(out_path, "wb");
-        if (!fo || std::fwrite(psi.data(), sizeof(C), N, fo) != N) return 2;
+        if (!fo || std::fwrite(psi.data(), sizeof(C), psi.size(), fo) != psi.size()) return 2;
         std::fclose(fo);
-        std::printf("CASE %d passes %zu tile %ld perm %ld gather %ld tma %ld rows %ld swz %ld sweeps %ld micro", ci,
-                    plan.passes.size(), c.tile, c.perm, c.gather, c.tma, c.rows, c.swz, c.sweeps);
+        std::printf("CASE %d passes %zu tile %ld perm %ld gather %ld tma %ld rows %ld swz %ld sweeps %ld merged %d micro",
+                    ci, n_passes, c.tile, c.perm, c.gather, c.tma, c.rows, c.swz, c.sweeps, merged ? 1 : 0);
         for (int k = 0; k <= MK_DIAGC; ++k) std::printf(" %ld", c.micro[k]);
         std::printf(" dense %ld %ld %ld\n", c.dense[1], c.dense[2], c.dense[3]);
         ++ci;

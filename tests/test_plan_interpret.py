@@ -7,7 +7,10 @@ and gather passes), and interprets every pass on a complex128 state by the
 contracts the pass descriptors document, checking their structural
 invariants (tile and sweep bits, tensor-copy boxes, swizzled offsets,
 constant bounds and alignment) on the way.  The final state must match the
-complex128 oracle's gate-by-gate evolution of the same seeded input.
+complex128 oracle's gate-by-gate evolution of the same seeded input.  Batches
+of parameter vectors run as the executor runs them: one plan per item, merged
+into one plan with per-item constants and a batch coordinate in the tensor
+copies.
 
 Tolerances: constants are complex64 (relative error 2^-24 per entry), so a
 plan of a few hundred ops drifts by at most ~1e-5 relative (L2); 1e-4 is
@@ -55,8 +58,24 @@ def _zz_random_angles(n, rng):
     return g
 
 
+def _param_layers(n, layers):
+    """Layers of parameterised RX / RY / RZ, RZZ and CP (angles from a vector)."""
+    g, k = [], 0
+    for _ in range(layers):
+        for q in range(n):
+            g.append(W.Gate(("RX", "RY", "RZ")[q % 3], (q,), (0.0,), None, k))
+            k += 1
+        for q in range(0, n - 1, 2):
+            g.append(W.Gate("RZZ", (q, q + 1), (0.0,), None, k))
+            k += 1
+        for q in range(1, n - 1, 2):
+            g.append(W.Gate("CP", (q, q + 1), (0.0,), None, k))
+            k += 1
+    return g, k
+
+
 def _cases():
-    """(name, n, gates, (T, L, R, dense_prec, block_qubits))"""
+    """(name, n, gates, (T, L, R, dense_prec, block_qubits)[, params (B x P)])"""
     rng = np.random.default_rng(23)
     out = []
     # random circuits over the whole vocabulary, several tile shapes and group sizes
@@ -88,6 +107,13 @@ def _cases():
             out.append((f"dense p={prec} k={k} random", 11, W.random_circuit(11, 80, 900 + 3 * prec + k),
                         (9, 4, 5, prec, k)))
         out.append((f"dense p={prec} tfim", 14, tf, (13, 4, 5, prec, 5)))
+    # batches of parameter vectors (per-item constants in one merged plan)
+    vqe = W.vqe_ansatz_gates(12, 3)
+    for sh in ((12, 4, 4), (10, 3, 5), (0, 0, 0)):
+        out.append((f"vqe batch {sh}", 12, vqe, sh + (0, 0), W.vqe_params(12, 3, 4, 8)))
+    pl, k = _param_layers(11, 3)
+    out.append(("param layers batch", 11, pl, (9, 4, 4, 0, 0), rng.uniform(-3, 3, size=(3, k))))
+    out.append(("param layers batch dense", 11, pl, (9, 4, 5, 1, 4), rng.uniform(-3, 3, size=(2, k))))
     return out
 
 
@@ -97,16 +123,21 @@ def test_plans_interpreted_on_host_match_oracle(tmp_path, qs):
         pytest.skip("needs g++ and the CUDA headers")
     cases = _cases()
     lines, expect = [], []
-    for i, (name, n, gl, (T, L, R, prec, blk)) in enumerate(cases):
+    for i, case in enumerate(cases):
+        name, n, gl, (T, L, R, prec, blk) = case[:4]
+        params = case[4] if len(case) > 4 else np.zeros((1, 0))
+        B, P = params.shape
         rng = np.random.default_rng(1000 + i)
-        psi0 = rng.standard_normal(2 ** n) + 1j * rng.standard_normal(2 ** n)
-        psi0 /= np.linalg.norm(psi0)
+        psi0 = rng.standard_normal((B, 2 ** n)) + 1j * rng.standard_normal((B, 2 ** n))
+        psi0 /= np.linalg.norm(psi0, axis=1, keepdims=True)
         fin, fout = tmp_path / f"in{i}.bin", tmp_path / f"out{i}.bin"
         psi0.astype(np.complex128).tofile(fin)
-        text = gate_lines(qs, gl)
-        lines.append(f"case {n} {T} {L} {R} {prec} {blk} {len(text)} {fin} {fout}")
+        text = gate_lines(qs, gl, pidx=True)
+        lines.append(f"case {n} {T} {L} {R} {prec} {blk} {len(text)} {B} {P} {fin} {fout}")
         lines += text
-        expect.append(oracle.simulate(n, gl, psi0.copy()))
+        lines += [" ".join(repr(float(v)) for v in row) for row in params if P]
+        expect.append(np.stack([oracle.simulate(n, gl, psi0[b].copy(), theta=params[b] if P else None)
+                                for b in range(B)]))
     src = tmp_path / "cases.txt"
     src.write_text("\n".join(lines) + "\n")
     csrc = os.path.join(ROOT, "paper_2609_19147_gb300", "csrc")
@@ -123,17 +154,20 @@ def test_plans_interpreted_on_host_match_oracle(tmp_path, qs):
     dense = np.zeros(3, dtype=np.int64)
     kinds = {"perm": 0, "gather": 0, "tma": 0, "rows": 0, "swz": 0}
     worst = []
-    for i, (name, n, gl, cfg) in enumerate(cases):
+    for i, case in enumerate(cases):
+        name, n, gl, cfg = case[:4]
         r = rows[i]
-        f = dict(zip(r[2:16:2], r[3:16:2]))
+        f = dict(zip(r[2:20:2], r[3:20:2]))
+        if len(case) > 4 and case[4].shape[0] > 1:
+            assert f["merged"] == "1", (name, "item plans did not merge")
         for k in kinds:
             kinds[k] += int(f[k])
         mi = r.index("micro")
         micro += np.array([int(x) for x in r[mi + 1:mi + 12]])
         di = r.index("dense")
         dense += np.array([int(x) for x in r[di + 1:di + 4]])
-        got = np.fromfile(tmp_path / f"out{i}.bin", dtype=np.complex128)
-        err = np.linalg.norm(got - expect[i]) / np.linalg.norm(expect[i])
+        got = np.fromfile(tmp_path / f"out{i}.bin", dtype=np.complex128).reshape(expect[i].shape)
+        err = np.max(np.linalg.norm(got - expect[i], axis=1) / np.linalg.norm(expect[i], axis=1))
         tol = 3e-2 if cfg[3] == 3 else 1e-4
         worst.append((err, name))
         assert err < tol, (name, cfg, err)
