@@ -253,6 +253,34 @@ qs_status qs_autotune(qs_state *st, const qs_gate *gates, size_t n_gates, const 
 qs_status qs_plan_describe(int n, const qs_gate *gates, size_t n_gates,
                            const qs_opts *opts, char *buf, size_t len, int *passes);
 
+/* OpenQASM 2.0 import (Sec. 3.3 "OpenQASM Integration"; App. B.1): the
+ * unitary subset of the NUL-terminated program `src` as gate records for
+ * qs_apply_circuit / qs_plan_describe.  Needs no GPU.
+ *  - Registers are laid end to end in declaration order (the first qreg
+ *    holds qubits 0..k-1, the next continues from k); *n_qubits receives the
+ *    total.
+ *  - Gate names map to the kinds above: the primitives U (U3) and CX, and
+ *    the standard-library names (id, x, y, z, h, s, sdg, t, tdg, sx, rx, ry,
+ *    rz, u1 / p, u2, u3 / u, cx, cy, cz, ch, swap, iswap, crx, cry, crz,
+ *    cu1 / cp, rzz, rxx, ryy, ccx, cswap), with this library's matrices
+ *    (global phases may differ from a textual expansion of qelib1.inc).
+ *  - `gate` definitions in the program take precedence over those names;
+ *    they are inlined recursively with parameters and arguments bound.
+ *  - A call on whole registers applies the gate once per index.
+ *  - Barriers are skipped.  Measurements are accepted after the last unitary
+ *    gate only; the records describe the state before them.
+ * On success *gates receives a library-allocated array of *n_gates records
+ * (param_idx -1, dense NULL; NULL when the program applies no gate), to be
+ * released with qs_qasm_free.  Errors (outputs then NULL / 0, message with
+ * the line number in qs_last_error): QS_ERR_INVALID_ARG (a NULL argument,
+ * syntax, undeclared names, wrong qubit or parameter counts, a repeated
+ * qubit, registers of different sizes in one call), QS_ERR_UNSUPPORTED (a gate
+ * that is neither defined nor in the list, opaque gates, reset, if, a gate
+ * after a measurement, an include other than qelib1.inc, more than 63 qubits). */
+qs_status qs_qasm_parse(const char *src, qs_gate **gates, size_t *n_gates, int *n_qubits);
+/* Release an array from qs_qasm_parse; NULL is a no-op. */
+void qs_qasm_free(qs_gate *gates);
+
 /* Per-kernel-family timing with CUDA events recorded on the state's stream
  * around each launch.  enable != 0 turns it on and clears the counters. */
 qs_status qs_profile_enable(qs_state *st, int enable);

@@ -89,6 +89,9 @@ _SIGS = {
     "qs_qaoa_maxcut": ([ctypes.POINTER(QsGraph), _sz, _i32, _i32, _dp, _dp, _dp, _vp], _i32),
     "qs_autotune": ([_vp, ctypes.POINTER(QsGate), _sz, _dp, _i32, ctypes.POINTER(QsOpts), _i32, ctypes.c_char_p,
                      ctypes.POINTER(QsOpts), _dp], _i32),
+    "qs_qasm_parse": ([ctypes.c_char_p, ctypes.POINTER(ctypes.POINTER(QsGate)), ctypes.POINTER(_sz),
+                       ctypes.POINTER(_i32)], _i32),
+    "qs_qasm_free": ([ctypes.POINTER(QsGate)], None),
     "qs_last_error": ([], ctypes.c_char_p),
     "qs_version": ([], ctypes.c_char_p),
 }
@@ -170,6 +173,44 @@ def plan_describe(n: int, gates, mode: str = "fused", tile_qubits: int = 0, low_
     o = _opts(mode, tile_qubits, low_qubits, group_qubits, dense, block_qubits)
     _check(_lib.qs_plan_describe(n, cg.arr, cg.n, ctypes.byref(o), buf, len(buf), ctypes.byref(passes)))
     return buf.value.decode(), passes.value
+
+
+# --- OpenQASM 2.0 import --------------------------------------------------------------
+_KIND_NAME = {v: k for k, v in KIND.items()}
+_N_PARAMS = {"RX": 1, "RY": 1, "RZ": 1, "P": 1, "U2": 2, "U3": 3, "CRX": 1, "CRY": 1, "CRZ": 1, "CP": 1,
+             "RZZ": 1, "RXX": 1, "RYY": 1}
+
+
+class GateRecord(tuple):
+    """(kind, wires, params): the fields CGates and the gate-list consumers read."""
+    __slots__ = ()
+
+    def __new__(cls, kind, wires, params):
+        return super().__new__(cls, (kind, tuple(wires), tuple(params)))
+
+    kind = property(lambda self: self[0])
+    wires = property(lambda self: self[1])
+    params = property(lambda self: self[2])
+    matrix = None
+    pidx = -1
+
+
+def parse_qasm(src: str):
+    """OpenQASM 2.0 program -> (n_qubits, [GateRecord]) through qs_qasm_parse
+    (the library's parser; no GPU needed)."""
+    arr = ctypes.POINTER(QsGate)()
+    n_gates = _sz(0)
+    n_qubits = _i32(0)
+    _check(_lib.qs_qasm_parse(src.encode(), ctypes.byref(arr), ctypes.byref(n_gates), ctypes.byref(n_qubits)))
+    try:
+        out = []
+        for i in range(n_gates.value):
+            g = arr[i]
+            name = _KIND_NAME[g.kind]
+            out.append(GateRecord(name, [g.w[m] for m in range(g.nw)], [g.p[m] for m in range(_N_PARAMS.get(name, 0))]))
+    finally:
+        _lib.qs_qasm_free(arr)
+    return n_qubits.value, out
 
 
 # --- device state ----------------------------------------------------------------

@@ -26,6 +26,7 @@
 #include "qs_internal.h"
 #include "qs_kernels.h"
 #include "qs_plan.h"
+#include "qs_qasm.h"
 
 using namespace qs;
 
@@ -2056,6 +2057,29 @@ qs_status qs_qaoa_maxcut(const qs_graph *graphs, size_t n_graphs, int n_sets, in
     for (auto &kv : states) qs_free(kv.second);
     return rs;
 }
+
+qs_status qs_qasm_parse(const char *src, qs_gate **gates, size_t *n_gates, int *n_qubits) {
+    if (gates) *gates = nullptr;
+    if (n_gates) *n_gates = 0;
+    if (n_qubits) *n_qubits = 0;
+    if (!src || !gates || !n_gates || !n_qubits) return fail(QS_ERR_INVALID_ARG, "NULL argument");
+    std::vector<qs_gate> out;
+    int nq = 0;
+    std::string err;
+    const qs_status s = parse_qasm(src, out, nq, err);
+    if (s != QS_OK) return fail(s, err);
+    if (!out.empty()) {
+        qs_gate *a = static_cast<qs_gate *>(std::malloc(out.size() * sizeof(qs_gate)));
+        if (!a) return fail(QS_ERR_OOM, "gate array allocation failed");
+        std::memcpy(a, out.data(), out.size() * sizeof(qs_gate));
+        *gates = a;
+    }
+    *n_gates = out.size();
+    *n_qubits = nq;
+    return QS_OK;
+}
+
+void qs_qasm_free(qs_gate *gates) { std::free(gates); }
 
 qs_status qs_plan_describe(int n, const qs_gate *gates, size_t n_gates, const qs_opts *opts, char *buf, size_t len,
                            int *passes) {
