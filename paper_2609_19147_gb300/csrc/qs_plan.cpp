@@ -39,7 +39,7 @@ static int kind_arity(int k) {
 bool gate_is_diagonal(int k) {
     switch (k) {
         case QS_I: case QS_Z: case QS_S: case QS_SDG: case QS_T: case QS_TDG: case QS_RZ: case QS_P:
-        case QS_CZ: case QS_CRZ: case QS_CP: case QS_RZZ:
+        case QS_CZ: case QS_CRZ: case QS_CP: case QS_RZZ: case K_DIAG2:
             return true;
         default:
             return false;
@@ -175,6 +175,10 @@ void gate_matrix(const RGate &g, cd *M) {
     const int K = 1 << g.nw;
     for (int i = 0; i < K * K; ++i) M[i] = 0;
     for (int i = 0; i < K; ++i) M[i * K + i] = 1;
+    if (g.kind == K_DIAG2) {
+        for (int i = 0; i < 4; ++i) M[i * 4 + i] = std::polar(1.0, g.dense[i].real());
+        return;
+    }
     const cd I(0, 1);
     auto ctrl1 = [&](int kind1, double ang) {   // controlled 2x2 in the lower-right block
         cd U[4];
@@ -235,6 +239,9 @@ static void diag_phases(const RGate &g, double *ph) {
         case QS_CP: ph[0] = ph[1] = ph[2] = 0; ph[3] = t; break;
         case QS_CRZ: ph[0] = ph[1] = 0; ph[2] = -t / 2; ph[3] = t / 2; break;
         case QS_RZZ: ph[0] = ph[3] = -t / 2; ph[1] = ph[2] = t / 2; break;
+        case K_DIAG2:
+            for (int k = 0; k < 4; ++k) ph[k] = g.dense[k].real();
+            break;
         default: ph[0] = ph[1] = ph[2] = ph[3] = 0;
     }
 }
@@ -592,9 +599,117 @@ static void conjugate_pauli_pair_runs(int n, const std::vector<RGate> &in, std::
     }
 }
 
+// Decomposed two-qubit diagonals (App. B.1: imported circuits spell CPHASE
+// and ZZ terms out as CX . diagonal . CX, which hides them from the layer
+// detectors).  A sandwich CX(c,t) . M . CX(c,t), where every gate of M
+// either misses c and t or is diagonal on wires within {c, t}, equals M with
+// each of those diagonals conjugated, phi'(xc, xt) = phi(xc, xc ^ xt) (CX
+// maps xt to xc ^ xt and is its own inverse), and both CX removed.  The
+// conjugated diagonals, and the runs of unconjugated diagonal gates on
+// {c, t} right before and right after the sandwich, multiply into one
+// two-qubit diagonal gate at the second CX's place (only adjacent runs, so
+// that a gate stream spelling one CPHASE per sandwich gives one CPHASE each).  So u1 / cx / u1 / cx
+// / u1 spelling CPHASE(l) becomes diag(1, 1, 1, e^{il}) exactly (the +-l/2
+// terms cancel exactly in FP64), and cx / rz / cx becomes RZZ.  Circuits
+// without such a sandwich pass through unchanged.
+static void fold_cx_sandwiches(int n, const std::vector<RGate> &in, std::vector<RGate> &out) {
+    constexpr size_t kReach = 64;   // gates scanned on each side: linear time
+    std::vector<RGate> g(in);
+    std::vector<char> dead(g.size(), 0);
+    auto touches = [](const RGate &x, int c, int t) {
+        for (int m = 0; m < x.nw; ++m)
+            if (x.b[m] == c || x.b[m] == t) return true;
+        return false;
+    };
+    auto diag_within = [](const RGate &x, int c, int t) {
+        if (!gate_is_diagonal(x.kind)) return false;
+        for (int m = 0; m < x.nw; ++m)
+            if (x.b[m] != c && x.b[m] != t) return false;
+        return true;
+    };
+    // phases of a diagonal gate within {c, t} as a function of (xc, xt), index xc * 2 + xt
+    auto phases = [](const RGate &x, int c, double ph[4]) {
+        double p[4];
+        diag_phases(x, p);
+        for (int s = 0; s < 4; ++s) {
+            const int xc = s >> 1, xt = s & 1;
+            if (x.nw == 1) {
+                ph[s] = p[x.b[0] == c ? xc : xt];
+            } else {
+                const int v0 = x.b[0] == c ? xc : xt, v1 = x.b[1] == c ? xc : xt;
+                ph[s] = p[v0 * 2 + v1];
+            }
+        }
+    };
+    bool any = false;
+    for (size_t i = 0; i < g.size(); ++i) {
+        if (dead[i] || g[i].kind != QS_CX) continue;
+        const int c = g[i].b[0], t = g[i].b[1];
+        size_t j = i + 1, seen = 0;
+        bool found = false;
+        for (; j < g.size() && seen < kReach; ++j) {
+            if (dead[j]) continue;
+            ++seen;
+            const RGate &x = g[j];
+            if (!touches(x, c, t)) continue;
+            if (x.kind == QS_CX && x.b[0] == c && x.b[1] == t) {
+                found = true;
+                break;
+            }
+            if (diag_within(x, c, t)) continue;
+            break;
+        }
+        if (!found) continue;
+        double ph[4] = {0, 0, 0, 0}, p[4];
+        seen = 0;
+        for (size_t k = i; k-- > 0 && seen < kReach;) {   // just before the sandwich
+            if (dead[k]) continue;
+            ++seen;
+            if (!diag_within(g[k], c, t)) break;
+            phases(g[k], c, p);
+            for (int s = 0; s < 4; ++s) ph[s] += p[s];
+            dead[k] = 1;
+        }
+        for (size_t k = i + 1; k < j; ++k) {   // inside: conjugated by the CX
+            if (dead[k] || !touches(g[k], c, t)) continue;
+            phases(g[k], c, p);
+            for (int s = 0; s < 4; ++s) ph[s] += p[(s & 2) | ((s >> 1) ^ (s & 1))];
+            dead[k] = 1;
+        }
+        seen = 0;
+        for (size_t k = j + 1; k < g.size() && seen < kReach; ++k) {   // just after the sandwich
+            if (dead[k]) continue;
+            ++seen;
+            if (!diag_within(g[k], c, t)) break;
+            phases(g[k], c, p);
+            for (int s = 0; s < 4; ++s) ph[s] += p[s];
+            dead[k] = 1;
+        }
+        RGate d;
+        d.kind = K_DIAG2;
+        d.nw = 2;
+        d.b[0] = c;
+        d.b[1] = t;
+        d.q[0] = n - 1 - c;
+        d.q[1] = n - 1 - t;
+        for (int s = 0; s < 4; ++s) d.dense[s] = cd(ph[s], 0.0);
+        dead[i] = 1;
+        g[j] = d;
+        any = true;
+    }
+    if (!any) {
+        out = in;
+        return;
+    }
+    out.clear();
+    for (size_t k = 0; k < g.size(); ++k)
+        if (!dead[k]) out.push_back(g[k]);
+}
+
 void detect(int n, const std::vector<RGate> &gates, std::vector<FOp> &ops) {
-    std::vector<RGate> conj;
-    conjugate_pauli_pair_runs(n, gates, conj);
+    std::vector<RGate> folded, conj;
+    fold_cx_sandwiches(n, gates, folded);
+    conjugate_pauli_pair_runs(n, folded, conj);
     std::vector<FOp> raw;
     Detector det(n, raw);
     for (const RGate &g : conj) det.gate(g);

@@ -26,6 +26,10 @@ struct RGate {
     cd dense[4];
 };
 
+// Internal kind of the fused detector (never accepted from callers): a
+// two-qubit diagonal with phases dense[k].real(), k = x_b0 * 2 + x_b1.
+constexpr int K_DIAG2 = 1000;
+
 // Diagonal phase as a quadratic form over the index bits (FP64, radians):
 //   phase(x) = g0 + sum_b a[b] x_b + sum_{b<c} pairs[(b,c)] x_b x_c
 // Every diagonal gate of the library (Z, S, T, RZ, P, CZ, CP, CRZ, RZZ) is of

@@ -3,7 +3,8 @@ gate-by-gate product, checked on the host in complex128: a C++ program links
 the planner, applies the detector's ops by their definitions and compares
 with applying every gate's full matrix in order.  Circuits: random gate lists
 over the whole vocabulary (n = 1..9), QFTs, Trotter and Heisenberg layers,
-QAOA layers, CNOT ladders and GHZ chains."""
+QAOA layers, CNOT ladders and GHZ chains, and circuits whose two-qubit
+diagonals are spelled out as CX . diagonal . CX (folded by the detector)."""
 import os
 import shutil
 import subprocess
@@ -44,6 +45,13 @@ def _circuits():
     for n in (4, 6, 8):
         edges = W.random_regular3_graph(n, rng)
         out.append((n, W.qaoa_gates(n, edges, [0.4, 1.1], [0.7, 0.2])))
+        out.append((n, W.spell_out_2q(W.qaoa_gates(n, edges, [0.4], [0.7]))))
+    # decomposed two-qubit diagonals (CX . diagonal . CX), folded by the detector
+    for n in (3, 6, 9):
+        out.append((n, W.spell_out_2q(W.qft_gates(n, swaps=True))))
+        out.append((n, W.spell_out_2q(W.tfim_gates(n, 2, 0.1, 1.0, 0.7, order=2))))
+    for n in range(2, 10):
+        out.append((n, W.cx_sandwich_circuit(n, 40, 500 + n)))
     return out
 
 

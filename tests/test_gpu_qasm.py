@@ -4,7 +4,9 @@ both modes and match the complex128 oracle run on the same parsed records.
 
 Programs (synthetic, written here): a layered circuit over two registers
 with nested user-defined gates, register-wide calls, barriers and trailing
-measurements; a cat state; a QFT written with cu1 and swaps.  Tolerances as
+measurements; a cat state; a QFT written with cu1 and swaps; a QFT with
+cu1 spelled out as u1 / cx.  Circuits of random CX . diagonal . CX blocks
+check the detector's fold of such blocks.  Tolerances as
 in the other parity tests: max |d| <= 2e-5, relative L2 <= 1e-5,
 fidelity >= 1 - 1e-6."""
 import numpy as np
@@ -59,12 +61,23 @@ def _qft(n):
     return s
 
 
+def _decomposed_qft(n):
+    # cu1 spelled out as u1 / cx (App. B.1), folded back into CPHASE by the detector
+    s = f"OPENQASM 2.0;\ninclude \"qelib1.inc\";\nqreg q[{n}];\n"
+    for g in W.spell_out_2q(W.qft_gates(n)):
+        name = {"H": "h", "P": "u1", "CX": "cx", "SWAP": "swap"}[g.kind]
+        prm = f"({g.params[0]!r})" if g.params else ""
+        s += f"{name}{prm} " + ", ".join(f"q[{w}]" for w in g.wires) + ";\n"
+    return s
+
+
 @pytest.mark.parametrize("name,src,mode", [
     ("layered 10+8", _layered(10, 8, 6, 31), "fused"),
     ("layered 10+8", _layered(10, 8, 6, 31), "pergate"),
     ("layered 12+9", _layered(12, 9, 4, 32), "fused"),
     ("cat 22", _cat(22), "fused"),
     ("qft 19", _qft(19), "fused"),
+    ("decomposed qft 18", _decomposed_qft(18), "fused"),
 ])
 def test_imported_programs_match_oracle(name, src, mode):
     n, gates = qs.parse_qasm(src)
@@ -79,3 +92,18 @@ def test_imported_programs_match_oracle(name, src, mode):
     rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     fid = abs(np.vdot(ref, got)) ** 2 / (np.vdot(got, got).real * np.vdot(ref, ref).real)
     assert d <= 2e-5 and rel <= 1e-5 and fid >= 1 - 1e-6, (name, d, rel, fid)
+
+
+@pytest.mark.parametrize("n,seed", [(12, 1), (17, 2), (20, 3)])
+def test_cx_sandwich_circuits_match_oracle(n, seed):
+    # CX . diagonal . CX blocks folded into two-qubit diagonals by the detector
+    gates = W.cx_sandwich_circuit(n, 80, 900 + seed)
+    psi0 = W.random_state(n, seed)
+    st = qs.State(n)
+    st.set(psi0.astype(np.complex64))
+    st.apply(gates)
+    got = st.get()[0].astype(np.complex128)
+    st.close()
+    ref = oracle.simulate(n, gates, psi0.astype(np.complex64).astype(np.complex128))
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert np.max(np.abs(got - ref)) <= 2e-5 and rel <= 1e-5, rel

@@ -107,6 +107,13 @@ def _cases():
             out.append((f"dense p={prec} k={k} random", 11, W.random_circuit(11, 80, 900 + 3 * prec + k),
                         (9, 4, 5, prec, k)))
         out.append((f"dense p={prec} tfim", 14, tf, (13, 4, 5, prec, 5)))
+    # two-qubit diagonals spelled out as CX . diagonal . CX (folded by the detector)
+    out.append(("spelled qft", 14, W.spell_out_2q(W.qft_gates(14)), (13, 4, 5, 0, 0)))
+    out.append(("spelled tfim", 14, W.spell_out_2q(tf), (12, 4, 4, 0, 0)))
+    out.append(("spelled qaoa", 14, W.spell_out_2q(qaoa), (13, 4, 5, 0, 0)))
+    for n, sh in ((10, (8, 4, 4)), (11, (9, 3, 5)), (12, (0, 0, 0))):
+        out.append((f"cx sandwiches n={n}", n, W.cx_sandwich_circuit(n, 60, 700 + n), sh + (0, 0)))
+    out.append(("cx sandwiches dense", 11, W.cx_sandwich_circuit(11, 60, 720), (9, 4, 5, 2, 4)))
     # batches of parameter vectors (per-item constants in one merged plan)
     vqe = W.vqe_ansatz_gates(12, 3)
     for sh in ((12, 4, 4), (10, 3, 5), (0, 0, 0)):

@@ -315,3 +315,61 @@ def bind_params(gates: Sequence[Gate], theta: np.ndarray) -> List[Gate]:
         else:
             out.append(gt)
     return out
+
+
+def spell_out_2q(gates: Sequence[Gate]) -> List[Gate]:
+    """The two-qubit diagonals written the way imported circuits often carry
+    them (App. B.1: a QFT arriving as cx + rz / u1 sequences): CP(l) on
+    (c, t) as P(l/2) c, CX(c, t), P(-l/2) t, CX(c, t), P(l/2) t; RZZ(t) on
+    (a, b) as CX(a, b), RZ(t) b, CX(a, b); CZ as CP(pi); other gates as they are."""
+    out: List[Gate] = []
+    for g in gates:
+        if g.kind in ("CP", "CZ"):
+            c, t = g.wires
+            lam = float(g.params[0]) if g.kind == "CP" else float(np.pi)
+            out += [Gate("P", (c,), (lam / 2,)), Gate("CX", (c, t)), Gate("P", (t,), (-lam / 2,)),
+                    Gate("CX", (c, t)), Gate("P", (t,), (lam / 2,))]
+        elif g.kind == "RZZ":
+            a, b = g.wires
+            out += [Gate("CX", (a, b)), Gate("RZ", (b,), tuple(g.params)), Gate("CX", (a, b))]
+        else:
+            out.append(g)
+    return out
+
+
+def cx_sandwich_circuit(n: int, n_blocks: int, seed: int) -> List[Gate]:
+    """Random CX(c, t) . M . CX(c, t) blocks: M mixes diagonal gates on c and t
+    (Z, S, T, RZ, P, CZ, CP, RZZ, CRZ in either wire order) with gates on other
+    qubits; some blocks carry a non-diagonal gate on c or t (no longer a
+    diagonal sandwich) and some stand next to diagonal gates on (c, t)."""
+    rng = np.random.default_rng(seed)
+    diag1 = ("Z", "S", "T", "RZ", "P")
+    diag2 = ("CZ", "CP", "RZZ", "CRZ")
+    other = ("H", "RX", "RY", "SX", "U3", "CX", "CRY")
+    g: List[Gate] = []
+
+    def rand_gate(kinds, wires):
+        k = kinds[int(rng.integers(len(kinds)))]
+        w = tuple(int(x) for x in rng.permutation(wires)[:arity(k)])
+        return Gate(k, w, tuple(float(x) for x in rng.uniform(-np.pi, np.pi, size=N_PARAMS.get(k, 0))))
+
+    for _ in range(n_blocks):
+        c, t = (int(x) for x in rng.choice(n, size=2, replace=False))
+        rest = [q for q in range(n) if q not in (c, t)]
+        if rng.random() < 0.5:
+            g.append(rand_gate(diag1, [c, t]))
+        g.append(Gate("CX", (c, t)))
+        for _ in range(int(rng.integers(0, 5))):
+            r = rng.random()
+            if r < 0.35:
+                g.append(rand_gate(diag1, [c, t]))
+            elif r < 0.6:
+                g.append(rand_gate(diag2, [c, t]))
+            elif r < 0.9 and len(rest) >= 2:
+                g.append(rand_gate(other, rest))
+            elif r >= 0.9:
+                g.append(rand_gate(("H", "RX"), [c, t]))
+        g.append(Gate("CX", (c, t)))
+        if rng.random() < 0.5:
+            g.append(rand_gate(diag1 + diag2, [c, t]))
+    return g
