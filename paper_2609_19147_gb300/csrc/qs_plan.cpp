@@ -2313,9 +2313,13 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
         // pad the tile to T bits with the lowest unused high bits
         for (int b = L; b < n && popc64(S) < T; ++b) S |= 1ull << b;
         PassBuilder pb(n, L, T, R, S, batch, dprec);
+        // the sweep estimate above can fall short of the builder's grouping:
+        // ops the pass has no room for stay in the queue (below)
+        std::vector<char> placed(ops.size(), 0);
         for (int id : taken) {
             pb.add(ops[id], ops[id].kind == F_DIAG ? &dplans[id] : nullptr);
-            if (pb.tp.n_sweeps >= kMaxSweeps - 1) break;   // guarded by taken limit
+            placed[id] = 1;
+            if (pb.tp.n_sweeps >= kMaxSweeps - 1 || pb.tp.n_micro >= kMaxMicro - 16) break;
         }
         pb.finalize();
         if (pb.count_failed) {
@@ -2324,7 +2328,12 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
         }
         pb.hp.note = "tile";
         plan.passes.push_back(pb.hp);
-        std::vector<int> nrem(deferred);
+        // everything scanned but not placed, in stream order: the deferred ops
+        // and any taken op past the builder's limit (each placed op commutes
+        // with every deferred op before it, so the order stays exact)
+        std::vector<int> nrem;
+        for (size_t k = 0; k < j; ++k)
+            if (!placed[rem[k]]) nrem.push_back(rem[k]);
         nrem.insert(nrem.end(), rem.begin() + j, rem.end());
         rem.swap(nrem);
     }

@@ -373,3 +373,176 @@ def cx_sandwich_circuit(n: int, n_blocks: int, seed: int) -> List[Gate]:
         if rng.random() < 0.5:
             g.append(rand_gate(diag1 + diag2, [c, t]))
     return g
+
+
+# ----------------------------------------------------------------------------
+# the end-to-end workload sweep (App. sweep table: every gate-based family of
+# the paper's suite).  The paper names the families; the circuits below are
+# this package's own seeded readings of them (sizes, step counts, angles).
+# ----------------------------------------------------------------------------
+def long_range_ising_gates(n: int, steps: int, dt: float, J: float = 1.0, h: float = 0.5,
+                           alpha: float = 1.5) -> List[Gate]:
+    """All-to-all Ising with couplings J / d^alpha over distance d (Sec. 5.1:
+    n(n-1)/2 bonds in n-1 equal-angle distance groups), first order: per step
+    RZZ(-2 J_d dt) on every pair, then RX(2 h dt) on every qubit."""
+    g: List[Gate] = []
+    for _ in range(steps):
+        for i in range(n):
+            for j in range(i + 1, n):
+                g.append(Gate("RZZ", (i, j), (-2.0 * J * dt / float(j - i) ** alpha,)))
+        g += [Gate("RX", (q,), (2.0 * h * dt,)) for q in range(n)]
+    return g
+
+
+def heisenberg_gates(n: int, steps: int, dt: float, J: float = 1.0, delta: float = 1.0,
+                     fields=None) -> List[Gate]:
+    """H = J sum_i (X_i X_{i+1} + Y_i Y_{i+1} + delta Z_i Z_{i+1}) (+ sum_i h_i Z_i)
+    on an open chain, first order: per step the XX terms on every bond, then
+    the YY terms, then the ZZ terms (same-family runs, Sec. 5.1), then RZ(2 h_i dt)."""
+    g: List[Gate] = []
+    for _ in range(steps):
+        g += [Gate("RXX", (b, b + 1), (2.0 * J * dt,)) for b in range(n - 1)]
+        g += [Gate("RYY", (b, b + 1), (2.0 * J * dt,)) for b in range(n - 1)]
+        g += [Gate("RZZ", (b, b + 1), (2.0 * J * delta * dt,)) for b in range(n - 1)]
+        if fields is not None:
+            g += [Gate("RZ", (q,), (2.0 * float(fields[q]) * dt,)) for q in range(n)]
+    return g
+
+
+def heisenberg_ladder_gates(n: int, steps: int, dt: float, J: float = 1.0) -> List[Gate]:
+    """Two-leg ladder (legs q and q + n/2, rungs between them), first order with
+    the XX, YY and ZZ terms of each bond in turn (no same-family run exists)."""
+    half = n // 2
+    bonds = [(q, q + 1) for q in range(half - 1)] + [(q, q + 1) for q in range(half, n - 1)]
+    bonds += [(q, q + half) for q in range(half)]
+    g: List[Gate] = []
+    for _ in range(steps):
+        for a, b in bonds:
+            g += [Gate("RXX", (a, b), (2.0 * J * dt,)), Gate("RYY", (a, b), (2.0 * J * dt,)),
+                  Gate("RZZ", (a, b), (2.0 * J * dt,))]
+    return g
+
+
+def rotation_entangler_gates(n: int, layers: int, seed: int, rot=("RY", "RZ"), ent: str = "CX",
+                             final: bool = True) -> List[Gate]:
+    """Hardware-efficient layers: the rotations `rot` on every qubit with angles
+    ~ U[0, 2 pi), then `ent` on (q, q+1) for q = 0..n-2; a last rotation layer
+    when `final` (EfficientSU2: RY RZ + CX; RealAmplitudes: RY + CX; QCBM:
+    RX RZ + CX; QNN layer: RY + CZ)."""
+    rng = np.random.default_rng(seed)
+    g: List[Gate] = []
+    for _ in range(layers):
+        for r in rot:
+            g += [Gate(r, (q,), (float(rng.uniform(0, 2 * np.pi)),)) for q in range(n)]
+        g += [Gate(ent, (q, q + 1)) for q in range(n - 1)]
+    if final:
+        for r in rot:
+            g += [Gate(r, (q,), (float(rng.uniform(0, 2 * np.pi)),)) for q in range(n)]
+    return g
+
+
+def graph_state_gates(n: int, seed: int, chords: int = 0) -> List[Gate]:
+    """H on every qubit, then CZ on the ring edges and `chords` random extra edges."""
+    rng = np.random.default_rng(seed)
+    edges = [(q, (q + 1) % n) for q in range(n)]
+    while len(edges) < n + chords:
+        u, v = (int(x) for x in rng.choice(n, size=2, replace=False))
+        if (u, v) not in edges and (v, u) not in edges:
+            edges.append((u, v))
+    return [Gate("H", (q,)) for q in range(n)] + [Gate("CZ", e) for e in edges]
+
+
+def qpe_gates(n: int, phi: float) -> List[Gate]:
+    """Phase estimation of U = P(phi) on qubit n-1 (eigenstate |1>, prepared by
+    X) with counting qubits 0..n-2: H on each, CP(phi 2^k) from counting qubit
+    n-2-k to the target (the controlled-power ladder, angles up to
+    phi 2^(n-2)), then the inverse QFT on the counting register (the QFT's
+    gates in reverse order with negated angles)."""
+    m = n - 1
+    g: List[Gate] = [Gate("X", (n - 1,))] + [Gate("H", (q,)) for q in range(m)]
+    for k in range(m):
+        g.append(Gate("CP", (m - 1 - k, n - 1), (phi * float(2 ** k),)))
+    inv = []
+    for gt in reversed(qft_gates(m, swaps=True)):
+        inv.append(Gate(gt.kind, gt.wires, tuple(-p for p in gt.params)))
+    return g + inv
+
+
+def qpe_exact_phase(n: int, seed: int) -> float:
+    """A phase 2 pi j / 2^(n-1) that n-1 counting qubits resolve exactly (j seeded)."""
+    m = n - 1
+    j = int(np.random.default_rng(seed).integers(1, 2 ** m))
+    return 2.0 * np.pi * j / float(2 ** m)
+
+
+def deutsch_jozsa_gates(n: int, seed: int) -> List[Gate]:
+    """Inputs 0..n-2, ancilla n-1: X and H on the ancilla, H on the inputs, a
+    balanced oracle (CX from the inputs in a random nonzero mask to the
+    ancilla, X on a random subset of inputs around it), H on the inputs."""
+    rng = np.random.default_rng(seed)
+    m = n - 1
+    mask = [q for q in range(m) if rng.random() < 0.5] or [0]
+    flip = [q for q in range(m) if rng.random() < 0.3]
+    g = [Gate("X", (m,)), Gate("H", (m,))] + [Gate("H", (q,)) for q in range(m)]
+    g += [Gate("X", (q,)) for q in flip]
+    g += [Gate("CX", (q, m)) for q in mask]
+    g += [Gate("X", (q,)) for q in flip]
+    return g + [Gate("H", (q,)) for q in range(m)]
+
+
+def w_state_gates(n: int) -> List[Gate]:
+    """W state by the controlled-rotation cascade: X on qubit 0, then for
+    k = 0..n-2: CRY(2 arccos sqrt(1 / (n - k))) from k to k+1, CX(k+1, k)."""
+    g = [Gate("X", (0,))]
+    for k in range(n - 1):
+        g.append(Gate("CRY", (k, k + 1), (2.0 * float(np.arccos(np.sqrt(1.0 / (n - k)))),)))
+        g.append(Gate("CX", (k + 1, k)))
+    return g
+
+
+def amplitude_estimation_gates(n: int, rounds: int, seed: int) -> List[Gate]:
+    """Single CZ gates between short single-qubit blocks (the structure the
+    paper's amplitude-estimation row has): per round and qubit q, RY and H on
+    q, then CZ(q, q+1)."""
+    rng = np.random.default_rng(seed)
+    g: List[Gate] = []
+    for _ in range(rounds):
+        for q in range(n - 1):
+            g += [Gate("RY", (q,), (float(rng.uniform(0, np.pi)),)), Gate("H", (q,)), Gate("CZ", (q, q + 1))]
+    return g
+
+
+def sweep_workloads(n: int, seed: int = 11):
+    """The sweep's gate-based families at n qubits: (name, gates)."""
+    rng = np.random.default_rng(seed)
+    f = tfim_fields(n, seed)
+    out = [
+        ("tfim_2nd_order", tfim_gates(n, 20, 0.05, 1.0, f, order=2)),
+        ("tfim_1st_order", tfim_gates(n, 20, 0.05, 1.0, 0.5, order=1)),
+        ("tfim_random_field", tfim_gates(n, 20, 0.05, 1.0, rng.uniform(0.0, 2.0, size=n), order=1)),
+        ("long_range_ising", long_range_ising_gates(n, 4, 0.05)),
+        ("heisenberg_chain", heisenberg_gates(n, 10, 0.05)),
+        ("heisenberg_xxz", heisenberg_gates(n, 10, 0.05, delta=0.5)),
+        ("heisenberg_random_field", heisenberg_gates(n, 10, 0.05, fields=rng.uniform(-1, 1, size=n))),
+        ("heisenberg_2leg_ladder", heisenberg_ladder_gates(n, 4, 0.05)),
+        ("variational_ansatz", [Gate(x.kind, x.wires, x.params) for x in
+                                bind_params(vqe_ansatz_gates(n, 6), vqe_params(n, 6, 1, seed)[0])]),
+        ("efficient_su2", rotation_entangler_gates(n, 4, seed, ("RY", "RZ"), "CX")),
+        ("real_amplitudes", rotation_entangler_gates(n, 4, seed + 1, ("RY",), "CX")),
+        ("qcbm", rotation_entangler_gates(n, 9, seed + 2, ("RX", "RZ"), "CX", final=False)),
+        ("qnn_layer", rotation_entangler_gates(n, 2, seed + 3, ("RY",), "CZ")),
+        ("ghz", ghz_gates(n)),
+        ("graph_state", graph_state_gates(n, seed, chords=n // 2)),
+        ("qft", qft_gates(n, swaps=True)),
+        ("qft_entangled_input", ghz_gates(n) + qft_gates(n, swaps=True)),
+        ("phase_estimation", qpe_gates(n, qpe_exact_phase(n, seed))),
+        ("phase_estimation_inexact", qpe_gates(n, 0.4)),   # ladder angles up to 0.4 * 2^(n-2) rad
+        ("qaoa_ring", qaoa_gates(n, [(q, (q + 1) % n) for q in range(n)], [0.4, 0.8, 1.1, 0.3],
+                                 [0.7, 0.5, 0.2, 0.9])),
+        ("deutsch_jozsa", deutsch_jozsa_gates(n, seed)),
+        ("random_circuit", random_circuit(n, 10 * n, seed, [k for k in ONE_QUBIT + TWO_QUBIT + THREE_QUBIT
+                                                             if k != "U"])),
+        ("amplitude_estimation", amplitude_estimation_gates(n, 3, seed)),
+        ("w_state", w_state_gates(n)),
+    ]
+    return out
