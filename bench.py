@@ -15,9 +15,10 @@ circuit runs with the tile shape the library's autotuner picks for it
 the timed step it reports the metric's other rows: adjoint gradients per
 second on the VQE config (n = 24, 576 parameters, batch 32), the dense
 5-qubit-block precisions on 30q TFIM (10 Strang steps), batched QAOA
-instances per second (512 graphs x 8 angle sets) and the 28-qubit layered
+instances per second (512 graphs x 8 angle sets), the 28-qubit layered
 suite's per-layer HBM rates (each layer family alone, then 20 layers plus
-the QFT and WHT tail).
+the QFT and WHT tail) and the 25-qubit end-to-end sweep over the paper's
+gate-based suite (fused against per-gate time per family; --no-sweep skips it).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -258,6 +259,43 @@ def suite_rows(qs, torch, peak):
     return out
 
 
+def sweep_rows(qs, torch, n=25, budget_s=150.0):
+    """The end-to-end sweep over the paper's gate-based suite at 25 qubits
+    (workloads.sweep_workloads: TFIM, long-range Ising, Heisenberg variants,
+    variational ansatze, QCBM, GHZ, graph state, QFT, phase estimation, QAOA
+    ring, Deutsch-Jozsa, random circuit, amplitude estimation, W state): per
+    family the fused and per-gate times (CUDA events, after one untimed run
+    each), their ratio, the fused plan's HBM passes, and the relative L2
+    distance between the two paths' states from |0...0>.  Families left when
+    the time budget runs out are listed, not timed."""
+    st = qs.State(n)
+    st.provide_scratch()
+    t_start = time.perf_counter()
+    rows, skipped = {}, []
+    for name, gl in W.sweep_workloads(n):
+        if time.perf_counter() - t_start > budget_s:
+            skipped.append(name)
+            continue
+        cg = qs.CGates(gl)
+        _, passes = qs.plan_describe(n, cg)
+        st.zero()
+        st.apply(cg)
+        fused_state = st.tensor.clone()
+        st.zero()
+        st.apply(cg, mode="pergate")
+        rel = (torch.linalg.vector_norm(st.tensor - fused_state) / torch.linalg.vector_norm(fused_state)).item()
+        del fused_state
+        tf = _time_cuda(torch, st.stream, lambda: st.apply(cg), reps=2)
+        tp = _time_cuda(torch, st.stream, lambda: st.apply(cg, mode="pergate"), reps=1)
+        rows[name] = {"gates": len(gl), "passes": passes, "fused_s": tf, "pergate_s": tp,
+                      "speedup": tp / tf, "rel_l2_fused_vs_pergate": rel}
+    st.close()
+    out = {"n_qubits": n, "rows": rows, "budget_s": budget_s}
+    if skipped:
+        out["skipped_time_budget"] = skipped
+    return out
+
+
 def extra_rows(qs, torch, st, tfim, stream):
     """grads/s of the adjoint config, the dense-block precisions on 30q TFIM,
     the batched QAOA config and the 28q layered suite; each after one untimed
@@ -444,6 +482,11 @@ def run_gpu(args):
     extra = {}
     if rank == 0 and not args.no_extra:
         extra = extra_rows(qs, torch, st, tfim, stream)
+    if rank == 0 and not args.no_sweep:
+        try:
+            extra["sweep25"] = sweep_rows(qs, torch)
+        except Exception as e:   # the sweep never costs the step's line
+            extra["sweep25"] = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     if rank != 0:
         st.close()
@@ -519,6 +562,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the grads / dense / QAOA / 28q suite rows")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the 25-qubit end-to-end workload sweep")
     ap.add_argument("--profile-case", choices=["tfim28"], default=None,
                     help="run a small fixed workload for ncu captures instead of the benchmark")
     args = ap.parse_args()
