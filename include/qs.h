@@ -274,9 +274,12 @@ qs_status qs_plan_describe(int n, const qs_gate *gates, size_t n_gates,
  * released with qs_qasm_free.  Errors (outputs then NULL / 0, message with
  * the line number in qs_last_error): QS_ERR_INVALID_ARG (a NULL argument,
  * syntax, undeclared names, wrong qubit or parameter counts, a repeated
- * qubit, registers of different sizes in one call), QS_ERR_UNSUPPORTED (a gate
+ * qubit, registers of different sizes in one call, an angle that is not
+ * finite), QS_ERR_UNSUPPORTED (a gate
  * that is neither defined nor in the list, opaque gates, reset, if, a gate
- * after a measurement, an include other than qelib1.inc, more than 63 qubits). */
+ * after a measurement, an include other than qelib1.inc, more than 63 qubits,
+ * more than 2^25 gate applications counting inlined ones, definitions nested
+ * more than 64 deep, expressions nested more than 200 deep). */
 qs_status qs_qasm_parse(const char *src, qs_gate **gates, size_t *n_gates, int *n_qubits);
 /* Release an array from qs_qasm_parse; NULL is a no-op. */
 void qs_qasm_free(qs_gate *gates);

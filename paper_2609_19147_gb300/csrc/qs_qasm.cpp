@@ -158,10 +158,13 @@ struct Cursor {
 
 // expression grammar: sum := term (('+'|'-') term)*; term := unary (('*'|'/') unary)*;
 // unary := '-' unary | power; power := atom ('^' unary)?
+constexpr int kMaxExprDepth = 200;   // nesting of parentheses, signs and powers
+
 class Expr {
   public:
     Expr(Cursor &c, const std::map<std::string, double> &env) : c_(c), env_(env) {}
     double sum() {
+        Depth guard(this);
         double v = term();
         while (c_.is_sym("+") || c_.is_sym("-")) {
             const bool plus = c_.next().s == "+";
@@ -174,6 +177,14 @@ class Expr {
   private:
     Cursor &c_;
     const std::map<std::string, double> &env_;
+    int depth_ = 0;
+    struct Depth {
+        Expr *e;
+        explicit Depth(Expr *x) : e(x) {
+            if (++e->depth_ > kMaxExprDepth) bad(e->c_.peek().line, "expression nested too deeply", QS_ERR_UNSUPPORTED);
+        }
+        ~Depth() { --e->depth_; }
+    };
     double term() {
         double v = unary();
         while (c_.is_sym("*") || c_.is_sym("/")) {
@@ -184,6 +195,7 @@ class Expr {
         return v;
     }
     double unary() {
+        Depth guard(this);
         if (c_.is_sym("-")) {
             c_.next();
             return -unary();
@@ -273,6 +285,7 @@ struct GateDef {
 
 constexpr int kMaxQubitsQasm = 63;
 constexpr int kMaxInlineDepth = 64;
+constexpr long long kMaxCalls = 1ll << 25;   // gate applications, inlined ones included
 
 class Program {
   public:
@@ -294,6 +307,7 @@ class Program {
     std::set<std::string> opaque_;
     int nq_ = 0;
     bool measured_ = false;
+    long long calls_ = 0;
 
     bool declared(const std::string &name) const {
         return qregs_.count(name) || cregs_.count(name) || defs_.count(name) || opaque_.count(name);
@@ -461,7 +475,8 @@ class Program {
     // `limit`: inside a body, only gates defined before index `limit` (-1: any)
     void apply(const std::string &name, const std::vector<double> &prm, const std::vector<int> &q, int line,
                int depth, int limit) {
-        if (depth > kMaxInlineDepth) bad(line, "gate definitions nested too deeply");
+        if (depth > kMaxInlineDepth) bad(line, "gate definitions nested too deeply", QS_ERR_UNSUPPORTED);
+        if (++calls_ > kMaxCalls) bad(line, "more than 2^25 gate applications", QS_ERR_UNSUPPORTED);
         for (size_t i = 0; i < q.size(); ++i)
             for (size_t j = i + 1; j < q.size(); ++j)
                 if (q[i] == q[j]) bad(line, "gate '" + name + "' repeats a qubit");
@@ -483,6 +498,8 @@ class Program {
         if ((int)prm.size() != g.np)
             bad(line, "gate '" + name + "' takes " + std::to_string(g.np) + " parameter(s)");
         if (measured_) bad(line, "a unitary gate after a measurement", QS_ERR_UNSUPPORTED);
+        for (double v : prm)
+            if (!std::isfinite(v)) bad(line, "gate '" + name + "': angle is not finite");
         qs_gate r;
         std::memset(&r, 0, sizeof r);
         r.kind = g.kind;
