@@ -82,7 +82,8 @@ typedef struct qs_gate {
     double p[3];         /* angles in radians                                */
     int32_t param_idx;   /* -1: fixed; else p[0] := params[b*n_params + idx] */
     int32_t reserved;    /* 0                                                */
-    const double *dense; /* QS_U only: row-major 2x2 complex128 as (re, im)  */
+    const double *dense; /* QS_U only: row-major 2x2 complex128 as (re, im);
+                            finite entries; unitarity is the caller's     */
 } qs_gate;
 
 /* One Pauli term coeff * P, P = prod_q sigma_q from (x_mask, z_mask). */

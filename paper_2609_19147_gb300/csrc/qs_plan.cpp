@@ -120,7 +120,14 @@ qs_status resolve_gates(int n, const qs_gate *gates, size_t n_gates, const doubl
                 err = buf;
                 return QS_ERR_INVALID_ARG;
             }
-            for (int e = 0; e < 4; ++e) r.dense[e] = cd(g.dense[2 * e], g.dense[2 * e + 1]);
+            for (int e = 0; e < 4; ++e) {
+                if (!std::isfinite(g.dense[2 * e]) || !std::isfinite(g.dense[2 * e + 1])) {
+                    snprintf(buf, sizeof buf, "gate %zu: non-finite matrix entry", i);
+                    err = buf;
+                    return QS_ERR_INVALID_ARG;
+                }
+                r.dense[e] = cd(g.dense[2 * e], g.dense[2 * e + 1]);
+            }
         }
         for (int m = 0; m < 3; ++m)
             if (!std::isfinite(r.p[m])) {

@@ -65,6 +65,11 @@ def test_validation_rejects_bad_gates(qs):
     assert _status(qs, 4, g) == qs.QS_ERR_INVALID_ARG
     g = qs.CGates([W.Gate("RX", (0,), (np.nan,))])
     assert _status(qs, 4, g) == qs.QS_ERR_INVALID_ARG
+    g = qs.CGates([W.Gate("U", (0,), (), np.array([[np.inf, 0], [0, 1]]))])   # non-finite matrix entry
+    assert _status(qs, 4, g) == qs.QS_ERR_INVALID_ARG
+    g = qs.CGates([W.Gate("CZ", (0, 1))])
+    g.arr[0].kind = 1000                                                         # the detector's internal kind
+    assert _status(qs, 4, g) == qs.QS_ERR_INVALID_ARG
     # parameter index without a parameter vector
     assert _status(qs, 4, [W.Gate("RX", (0,), (0.0,), None, 0)]) == qs.QS_ERR_INVALID_ARG
 
