@@ -18,7 +18,10 @@
 // agree in structure); each item's state runs with its own constants and the
 // TMA boxes are checked at the batch coordinate of every item.
 // Input: a case file, one case per block:
-//   case <n> <T> <L> <R> <dense_prec> <block> <count> <B> <P> <psi0.bin> <out.bin>
+//   case <n> <T> <L> <R> <dense_prec> <block> <mode> <count> <B> <P> <psi0.bin> <out.bin>
+//   (mode: QS_MODE_FUSED or QS_MODE_PERGATE, whose one-op-per-launch plans
+//   are applied by their own contract: each op over the subspace
+//   (x & cmask) == cval)
 //   then <count> gate lines: kind nw w0 w1 w2 p0 p1 p2 param_idx has_dense [8 doubles]
 //   then B x P parameter values (item after item)
 // psi0 / out: B x 2^n complex128.  Prints one "CASE <i> ..." line per case
@@ -51,7 +54,7 @@ int popc(uint64_t x) {
 struct Counts {
     long micro[11] = {0};
     long dense[4] = {0};
-    long tile = 0, perm = 0, gather = 0, tma = 0, rows = 0, swz = 0, sweeps = 0;
+    long tile = 0, perm = 0, gather = 0, tma = 0, rows = 0, swz = 0, sweeps = 0, pergate = 0;
 };
 
 struct Fail {
@@ -572,16 +575,70 @@ void run_gather(int n, const GatherPass &gp, C *psi) {
     std::copy(out.begin(), out.end(), psi);
 }
 
+// one per-gate launch: U1 = 2x2 on bit t0, U2 = 4x4 on (t0 = matrix MSB, t1),
+// PHASE = amp *= m[bit t0 | bit t1 << 1] (nbits_phase of them; 0: m[0]),
+// SWAP = exchange of bits t0 and t1; every op only where (x & cmask) == cval
+void run_pergate(int n, const PgOp &op, C *psi) {
+    const uint64_t N = 1ull << n;
+    auto M = [&](int e) { return C(op.m[e].x, op.m[e].y); };
+    if ((op.cval & ~op.cmask) != 0) throw Fail{"per-gate control value outside its mask"};
+    const uint64_t b0 = op.t0 >= 0 ? 1ull << op.t0 : 0, b1 = op.t1 >= 0 ? 1ull << op.t1 : 0;
+    switch (op.kind) {
+        case PG_U1:
+            if (op.t0 < 0 || op.t0 >= n || (op.cmask & b0)) throw Fail{"per-gate U1 target"};
+            for (uint64_t x = 0; x < N; ++x) {
+                if ((x & b0) || (x & op.cmask) != op.cval) continue;
+                const C a0 = psi[x], a1 = psi[x | b0];
+                psi[x] = M(0) * a0 + M(1) * a1;
+                psi[x | b0] = M(2) * a0 + M(3) * a1;
+            }
+            break;
+        case PG_U2: {
+            if (op.t0 < 0 || op.t1 < 0 || op.t0 >= n || op.t1 >= n || op.t0 == op.t1 || (op.cmask & (b0 | b1)))
+                throw Fail{"per-gate U2 targets"};
+            for (uint64_t x = 0; x < N; ++x) {
+                if ((x & (b0 | b1)) || (x & op.cmask) != op.cval) continue;
+                const uint64_t id[4] = {x, x | b1, x | b0, x | b0 | b1};
+                C v[4], w[4];
+                for (int i = 0; i < 4; ++i) v[i] = psi[id[i]];
+                for (int r = 0; r < 4; ++r) w[r] = M(4 * r) * v[0] + M(4 * r + 1) * v[1] + M(4 * r + 2) * v[2] +
+                                                   M(4 * r + 3) * v[3];
+                for (int i = 0; i < 4; ++i) psi[id[i]] = w[i];
+            }
+            break;
+        }
+        case PG_PHASE:
+            if (op.nbits_phase < 0 || op.nbits_phase > 2) throw Fail{"per-gate phase bits"};
+            for (uint64_t x = 0; x < N; ++x) {
+                if ((x & op.cmask) != op.cval) continue;
+                int idx = 0;
+                if (op.nbits_phase >= 1) idx |= (int)((x >> op.t0) & 1);
+                if (op.nbits_phase >= 2) idx |= (int)((x >> op.t1) & 1) << 1;
+                psi[x] *= M(idx);
+            }
+            break;
+        case PG_SWAP:
+            if (op.t0 < 0 || op.t1 < 0 || op.t0 == op.t1 || (op.cmask & (b0 | b1))) throw Fail{"per-gate swap bits"};
+            for (uint64_t x = 0; x < N; ++x) {
+                if ((x & (b0 | b1)) || (x & op.cmask) != op.cval) continue;
+                std::swap(psi[x | b0], psi[x | b1]);
+            }
+            break;
+        default:
+            throw Fail{"per-gate op kind"};
+    }
+}
+
 }  // namespace
 
 int main(int argc, char **argv) {
     if (argc < 2) return 2;
     FILE *fp = std::fopen(argv[1], "r");
     if (!fp) return 2;
-    int n, T, L, R, dprec, block, cnt, B, NP, ci = 0;
+    int n, T, L, R, dprec, block, mode, cnt, B, NP, ci = 0;
     char in_path[4096], out_path[4096];
-    while (std::fscanf(fp, " case %d %d %d %d %d %d %d %d %d %4095s %4095s", &n, &T, &L, &R, &dprec, &block, &cnt, &B,
-                       &NP, in_path, out_path) == 11) {
+    while (std::fscanf(fp, " case %d %d %d %d %d %d %d %d %d %d %4095s %4095s", &n, &T, &L, &R, &dprec, &block, &mode,
+                       &cnt, &B, &NP, in_path, out_path) == 12) {
         std::vector<qs_gate> gl(cnt);
         std::vector<std::vector<double>> dense(cnt);
         for (int i = 0; i < cnt; ++i) {
@@ -627,7 +684,9 @@ int main(int argc, char **argv) {
                 std::printf("FAIL %d resolve: %s\n", ci, err.c_str());
                 return 1;
             }
-            if (build_fused_plan(n, 1, rg, o, plans[bi], err) != QS_OK) {
+            const qs_status ps = mode == QS_MODE_PERGATE ? build_pergate_plan(n, rg, plans[bi], err)
+                                                         : build_fused_plan(n, 1, rg, o, plans[bi], err);
+            if (ps != QS_OK) {
                 std::printf("FAIL %d plan: %s\n", ci, err.c_str());
                 return 1;
             }
@@ -635,7 +694,7 @@ int main(int argc, char **argv) {
         // batched items run as one merged plan when the items' plans agree in structure
         std::vector<Plan> run_plans;
         bool merged = false;
-        if (B > 1) {
+        if (B > 1 && mode != QS_MODE_PERGATE) {
             Plan m;
             std::vector<Plan> copy = plans;
             if (merge_item_plans(copy, m, B)) {
@@ -651,12 +710,17 @@ int main(int argc, char **argv) {
         std::fclose(fi);
         Counts c;
         size_t pi = 0;
-        size_t n_passes = run_plans[0].passes.size();
+        size_t n_passes = mode == QS_MODE_PERGATE ? run_plans[0].pg.size() : run_plans[0].passes.size();
         try {
             for (int bi = 0; bi < B; ++bi) {
                 const Plan &plan = merged ? run_plans[0] : run_plans[bi];
                 if (plan.items != (merged ? B : 1)) throw Fail{"plan items"};
                 C *st = psi.data() + (size_t)bi * N;
+                if (plan.mode == QS_MODE_PERGATE) {
+                    for (pi = 0; pi < plan.pg.size(); ++pi) run_pergate(n, plan.pg[pi], st);
+                    c.pergate += (long)plan.pg.size();
+                    continue;
+                }
                 for (pi = 0; pi < plan.passes.size(); ++pi) {
                     const HostPass &hp = plan.passes[pi];
                     switch (hp.type) {
@@ -684,7 +748,7 @@ int main(int argc, char **argv) {
         std::printf("CASE %d passes %zu tile %ld perm %ld gather %ld tma %ld rows %ld swz %ld sweeps %ld merged %d micro",
                     ci, n_passes, c.tile, c.perm, c.gather, c.tma, c.rows, c.swz, c.sweeps, merged ? 1 : 0);
         for (int k = 0; k <= MK_DIAGC; ++k) std::printf(" %ld", c.micro[k]);
-        std::printf(" dense %ld %ld %ld\n", c.dense[1], c.dense[2], c.dense[3]);
+        std::printf(" dense %ld %ld %ld pergate %ld\n", c.dense[1], c.dense[2], c.dense[3], c.pergate);
         ++ci;
     }
     return 0;

@@ -2,8 +2,9 @@
 list of cases and returns, per case, the final states and the interpreter's
 pass / micro-op counts.
 
-A case is (name, n, gates, (T, L, R, dense_prec, block_qubits)[, params]),
-params a B x P array of parameter vectors (one state per row)."""
+A case is (name, n, gates, (T, L, R, dense_prec, block_qubits[, mode])[, params]),
+mode 0 = fused (default) or 1 = per-gate, params a B x P array of parameter
+vectors (one state per row)."""
 import os
 import shutil
 import subprocess
@@ -25,13 +26,15 @@ def interpret(qs, cases, workdir, psi0s):
     interpreter's message if a plan breaks an invariant."""
     lines = []
     for i, case in enumerate(cases):
-        name, n, gl, (T, L, R, prec, blk) = case[:4]
+        name, n, gl, cfg = case[:4]
+        T, L, R, prec, blk = cfg[:5]
+        mode = cfg[5] if len(cfg) > 5 else 0
         params = case[4] if len(case) > 4 else np.zeros((1, 0))
         B, P = params.shape
         fin, fout = os.path.join(workdir, f"in{i}.bin"), os.path.join(workdir, f"out{i}.bin")
         np.ascontiguousarray(psi0s[i], dtype=np.complex128).tofile(fin)
         text = gate_lines(qs, gl, pidx=True)
-        lines.append(f"case {n} {T} {L} {R} {prec} {blk} {len(text)} {B} {P} {fin} {fout}")
+        lines.append(f"case {n} {T} {L} {R} {prec} {blk} {mode} {len(text)} {B} {P} {fin} {fout}")
         lines += text
         lines += [" ".join(repr(float(v)) for v in row) for row in params if P]
     src = os.path.join(workdir, "cases.txt")
@@ -54,6 +57,7 @@ def interpret(qs, cases, workdir, psi0s):
         mi, di = r.index("micro"), r.index("dense")
         counts["micro"] = [int(x) for x in r[mi + 1:mi + 12]]
         counts["dense"] = [int(x) for x in r[di + 1:di + 4]]
+        counts["pergate"] = int(r[r.index("pergate") + 1])
         shape = np.asarray(psi0s[i]).shape
         states = np.fromfile(os.path.join(workdir, f"out{i}.bin"), dtype=np.complex128).reshape(shape)
         res.append((states, counts))

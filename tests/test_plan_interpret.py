@@ -116,6 +116,13 @@ def _cases():
     out.append(("random 10q 600 gates", 10, W.random_circuit(10, 600, 77), (10, 4, 5, 0, 0)))
     out.append(("qaoa 12q p=12", 12, W.qaoa_gates(12, W.random_regular3_graph(12, rng), list(np.linspace(0.1, 1, 12)),
                                                  list(np.linspace(1, 0.1, 12))), (0, 0, 0, 0, 0)))
+    # per-gate plans (the baseline path: one launch per gate over its subspace)
+    for n in (3, 8, 11):
+        out.append((f"pergate random n={n}", n, W.random_circuit(n, 120, 1200 + n), (0, 0, 0, 0, 0, 1)))
+    out.append(("pergate qft", 12, W.qft_gates(12), (0, 0, 0, 0, 0, 1)))
+    out.append(("pergate tfim", 12, W.tfim_gates(12, 3, 0.1, 1.0, 0.7, order=2), (0, 0, 0, 0, 0, 1)))
+    out.append(("pergate sandwiches", 10, W.cx_sandwich_circuit(10, 40, 1300), (0, 0, 0, 0, 0, 1)))
+    out.append(("pergate vqe batch", 10, W.vqe_ansatz_gates(10, 2), (0, 0, 0, 0, 0, 1), W.vqe_params(10, 2, 3, 9)))
     # batches of parameter vectors (per-item constants in one merged plan)
     vqe = W.vqe_ansatz_gates(12, 3)
     for sh in ((12, 4, 4), (10, 3, 5), (0, 0, 0)):
@@ -144,11 +151,11 @@ def test_plans_interpreted_on_host_match_oracle(tmp_path, qs):
     res = plan_host.interpret(qs, cases, str(tmp_path), psi0s)
     micro = np.zeros(11, dtype=np.int64)
     dense = np.zeros(3, dtype=np.int64)
-    kinds = {"perm": 0, "gather": 0, "tma": 0, "rows": 0, "swz": 0}
+    kinds = {"perm": 0, "gather": 0, "tma": 0, "rows": 0, "swz": 0, "pergate": 0}
     for i, case in enumerate(cases):
         name, n, gl, cfg = case[:4]
         got, f = res[i]
-        if len(case) > 4 and case[4].shape[0] > 1:
+        if len(case) > 4 and case[4].shape[0] > 1 and len(cfg) < 6:
             assert f["merged"] == 1, (name, "item plans did not merge")
         for k in kinds:
             kinds[k] += f[k]
