@@ -126,7 +126,12 @@ enum qs_dense_prec {
 typedef struct qs_opts {
     int32_t mode;         /* enum qs_mode                                    */
     int32_t tile_qubits;  /* qubits per tile pass, 0 = default (13)          */
-    int32_t low_qubits;   /* contiguous low bits per tile row, 0 = default   */
+    int32_t low_qubits;   /* contiguous low bits per tile row, 0 = default;
+                             the planner clamps the shape: tile_qubits <= 13
+                             and <= n; a tile smaller than the state keeps
+                             >= 2 high bits (with dense blocks: >= the block
+                             size), raising tile_qubits to 3 (block size + 1)
+                             or lowering low_qubits as needed              */
     int32_t group_qubits; /* tile bits held in registers per sweep (1..5),
                              0 = default (5)                                 */
     int32_t dense_prec;   /* enum qs_dense_prec, 0 = off                      */

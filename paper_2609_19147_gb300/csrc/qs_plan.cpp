@@ -2112,6 +2112,20 @@ static void build_perm_or_gather(int n, const FOp &f, HostPass &hp) {
 static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &detected, int n_gates,
                                       const qs_opts &o, Plan &plan, std::string &err);
 
+// Tile shape actually used for T tile bits with L low bits: T <= 13 (two
+// 2^13-amplitude buffers fill the 227 KB of shared memory) and <= n, L in
+// [1, T]; a tile that does not cover the whole state keeps at least two
+// high-bit slots (so that a 4x4 op on any two high bits fits a pass): T >= 3
+// and L <= T - 2.
+static void clamp_tile_shape(int n, int &T, int &L) {
+    if (T > 13) T = 13;
+    if (T > n) T = n;
+    if (T < n && T < 3) T = std::min(n, 3);
+    if (L > T) L = T;
+    if (T < n && L > T - 2) L = T - 2;
+    if (L < 1) L = 1;
+}
+
 // Default tile shape: 12-bit tiles with 4-bit register groups (two CTAs per
 // SM hide each other's copy latency) unless they need more HBM passes than
 // 13-bit tiles with 5-bit groups.
@@ -2131,12 +2145,19 @@ qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, co
         // dense blocks: cells of <= k bits laid out so that the cells of one
         // tile window (the low bits plus T - L high bits) share a pass
         qs_opts c = o;
+        const int k = o.block_qubits > 0 ? o.block_qubits : 5;
         if (c.tile_qubits <= 0) c.tile_qubits = 13;
         c.tile_qubits = std::max(5, std::min(c.tile_qubits, std::min(n, 13)));
         if (c.low_qubits <= 0) c.low_qubits = 4;
-        c.low_qubits = std::min(c.low_qubits, c.tile_qubits);
+        // a block may hold k high bits (its ops' bits, controls included, need
+        // not share a cell): a tile that does not cover the state keeps k
+        // high-bit slots
+        if (c.tile_qubits < n) {
+            c.tile_qubits = std::max(c.tile_qubits, std::min(n, k + 1));
+            if (c.tile_qubits < n) c.low_qubits = std::max(1, std::min(c.low_qubits, c.tile_qubits - k));
+        }
+        clamp_tile_shape(n, c.tile_qubits, c.low_qubits);
         c.group_qubits = 5;   // dense passes run in the 5-bit-group kernel
-        const int k = o.block_qubits > 0 ? o.block_qubits : 5;
         int cell_of[64];
         for (int b = 0; b < 64; ++b) cell_of[b] = 63;
         dense_cells(n, c.tile_qubits, c.low_qubits, k, cell_of);
@@ -2181,10 +2202,7 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
 
     int T = o.tile_qubits > 0 ? o.tile_qubits : 13;
     int L = o.low_qubits > 0 ? o.low_qubits : 4;
-    if (T > 13) T = 13;   // two 2^13-amplitude buffers fill the 227 KB of shared memory
-    if (T > n) T = n;
-    if (L > T) L = T;
-    if (L < 1) L = 1;
+    clamp_tile_shape(n, T, L);
     int R = o.group_qubits > 0 ? std::min(o.group_qubits, kMaxGroup) : kMaxGroup;
     R = std::min(R, T);
     const int dprec = o.dense_prec;
