@@ -1,12 +1,13 @@
 """The end-to-end sweep's workloads (the paper's gate-based suite: TFIM,
 long-range Ising, Heisenberg chain / XXZ / random field / 2-leg ladder,
 variational ansatze, QCBM, GHZ, graph state, QFT, phase estimation, QAOA
-ring, Deutsch-Jozsa, random circuit, amplitude estimation, W state).
+ring, Deutsch-Jozsa, random circuit, amplitude estimation, W state, Grover
+search with a CCX V-chain).
 
 1. The generators are pinned by what their circuits must do, evaluated with
    the oracle: W-state amplitudes, phase estimation of a dyadic phase landing
    on one index, a balanced Deutsch-Jozsa oracle never returning the zero
-   input, graph-state stabilisers, magnetisation conservation of the
+   input, Grover's sin^2((2k+1) theta) with clean ancillas, graph-state stabilisers, magnetisation conservation of the
    bond-by-bond Heisenberg ladder, the first-order error law of the
    layer-ordered Heisenberg chains against exact evolution, and the
    long-range Ising phases from their closed form.
@@ -51,6 +52,16 @@ def test_exact_phase_estimation_lands_on_one_index():
     # the inexact phase spreads over several indices
     p = np.abs(oracle.simulate(7, W.qpe_gates(7, 0.4))) ** 2
     assert np.max(p) < 0.99 and abs(p.sum() - 1) < 1e-12
+
+
+def test_grover_vchain_success_probability():
+    # sin^2((2k+1) theta), sin theta = 2^(-m/2), on m data qubits; the V-chain ancillas end in |0>
+    for n, marked, k in ((5, 2, 1), (9, 37, 3), (10, 5, 2)):
+        m = (n + 3) // 2
+        p = np.abs(oracle.simulate(n, W.grover_vchain_gates(n, marked, k))) ** 2
+        th = np.arcsin(2.0 ** (-m / 2))
+        assert abs(p[marked << (n - m)] - np.sin((2 * k + 1) * th) ** 2) < 1e-12
+        assert abs(p.reshape(2 ** m, -1)[:, 0].sum() - 1) < 1e-12
 
 
 def test_deutsch_jozsa_balanced_oracle():

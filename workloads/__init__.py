@@ -512,6 +512,41 @@ def amplitude_estimation_gates(n: int, rounds: int, seed: int) -> List[Gate]:
     return g
 
 
+def grover_vchain_gates(n: int, marked: int, iterations: int) -> List[Gate]:
+    """Grover search on m = (n + 3) // 2 data qubits (0..m-1) with m - 3
+    ancillas (m..2m-4) for the multi-controlled Z, built from CCX as a V-chain:
+    the ancillas collect the AND of the controls, CCX onto the last data
+    qubit between H gates flips the phase, and the chain is undone, leaving the
+    ancillas in |0>.  Start H on the data; per iteration: the oracle (X on the
+    data qubits where `marked`, read with qubit 0 as its most significant
+    bit, is 0, then MCZ, then the X again) and the diffusion H X MCZ X H."""
+    m = (n + 3) // 2
+    if m < 3 or 2 * m - 3 > n:
+        raise ValueError("grover_vchain_gates needs n >= 3")
+    data = list(range(m))
+    anc = list(range(m, 2 * m - 3))
+
+    def mcz():
+        c, t = data[:-1], data[-1]
+        chain: List[Gate] = []
+        if len(c) == 2:
+            core = [Gate("CCX", (c[0], c[1], t))]
+        else:
+            chain.append(Gate("CCX", (c[0], c[1], anc[0])))
+            for i in range(2, len(c) - 1):
+                chain.append(Gate("CCX", (c[i], anc[i - 2], anc[i - 1])))
+            core = [Gate("CCX", (c[-1], anc[len(c) - 3], t))]
+        return [Gate("H", (t,))] + chain + core + list(reversed(chain)) + [Gate("H", (t,))]
+
+    zeros = [q for q in data if not (marked >> (m - 1 - q)) & 1]
+    g: List[Gate] = [Gate("H", (q,)) for q in data]
+    for _ in range(iterations):
+        g += [Gate("X", (q,)) for q in zeros] + mcz() + [Gate("X", (q,)) for q in zeros]
+        g += [Gate("H", (q,)) for q in data] + [Gate("X", (q,)) for q in data] + mcz()
+        g += [Gate("X", (q,)) for q in data] + [Gate("H", (q,)) for q in data]
+    return g
+
+
 def sweep_workloads(n: int, seed: int = 11):
     """The sweep's gate-based families at n qubits: (name, gates)."""
     rng = np.random.default_rng(seed)
@@ -544,5 +579,6 @@ def sweep_workloads(n: int, seed: int = 11):
                                                              if k != "U"])),
         ("amplitude_estimation", amplitude_estimation_gates(n, 3, seed)),
         ("w_state", w_state_gates(n)),
+        ("grover_search", grover_vchain_gates(n, int(rng.integers(1, 2 ** ((n + 3) // 2))), 2)),
     ]
     return out
