@@ -2,12 +2,13 @@
 long-range Ising, Heisenberg chain / XXZ / random field / 2-leg ladder,
 variational ansatze, QCBM, GHZ, graph state, QFT, phase estimation, QAOA
 ring, Deutsch-Jozsa, random circuit, amplitude estimation, W state, Grover
-search with a CCX V-chain).
+search with a CCX V-chain, coined quantum walk).
 
 1. The generators are pinned by what their circuits must do, evaluated with
    the oracle: W-state amplitudes, phase estimation of a dyadic phase landing
    on one index, a balanced Deutsch-Jozsa oracle never returning the zero
-   input, Grover's sin^2((2k+1) theta) with clean ancillas, graph-state stabilisers, magnetisation conservation of the
+   input, Grover's sin^2((2k+1) theta) with clean ancillas, the quantum walk
+   against the classical amplitude recursion, graph-state stabilisers, magnetisation conservation of the
    bond-by-bond Heisenberg ladder, the first-order error law of the
    layer-ordered Heisenberg chains against exact evolution, and the
    long-range Ising phases from their closed form.
@@ -62,6 +63,28 @@ def test_grover_vchain_success_probability():
         th = np.arcsin(2.0 ** (-m / 2))
         assert abs(p[marked << (n - m)] - np.sin((2 * k + 1) * th) ** 2) < 1e-12
         assert abs(p.reshape(2 ** m, -1)[:, 0].sum() - 1) < 1e-12
+
+
+def test_quantum_walk_matches_classical_recursion():
+    # amplitudes psi(c, x) of the coined walk on the 2^p cycle, step: coin H, x +- 1
+    for n, steps in ((6, 5), (9, 4)):
+        p = n // 2
+        amp = np.zeros((2, 2 ** p), complex)
+        amp[:, 0] = np.array([1, 1j]) / np.sqrt(2)
+        for _ in range(steps):
+            h0, h1 = (amp[0] + amp[1]) / np.sqrt(2), (amp[0] - amp[1]) / np.sqrt(2)
+            amp = np.stack([np.roll(h0, -1), np.roll(h1, 1)])
+        psi0 = np.zeros(2 ** n, complex)
+        psi0[0], psi0[1 << (n - 1)] = 1 / np.sqrt(2), 1j / np.sqrt(2)
+        psi = oracle.simulate(n, W.quantum_walk_gates(n, steps), psi0)
+        want = np.zeros(2 ** n, complex)
+        for c in range(2):
+            for x in range(2 ** p):
+                idx = c << (n - 1)
+                for j in range(p):
+                    idx |= ((x >> j) & 1) << (n - 2 - j)   # position bit j = qubit 1 + j
+                want[idx] = amp[c, x]
+        assert np.max(np.abs(psi - want)) < 1e-12
 
 
 def test_deutsch_jozsa_balanced_oracle():

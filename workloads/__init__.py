@@ -547,6 +547,40 @@ def grover_vchain_gates(n: int, marked: int, iterations: int) -> List[Gate]:
     return g
 
 
+def quantum_walk_gates(n: int, steps: int) -> List[Gate]:
+    """Coined walk on a cycle of 2^p positions, p = n // 2: coin qubit 0,
+    position bits r_j = qubit 1 + j (r_0 least significant), p - 1 ancillas
+    after them.  One step: H on the coin, then position + 1 where the coin is
+    1 and position - 1 where it is 0 (mod 2^p).  The increment is the carry
+    chain: the ancillas collect coin AND r_0 AND ... AND r_j (CCX V-chain), each
+    r_{j+1} flips by CX from the chain, highest first, while the chain is
+    undone, and r_0 flips by CX from the coin; the decrement is the increment
+    between X layers on the position and the coin."""
+    p = n // 2
+    if p < 2:
+        raise ValueError("quantum_walk_gates needs n >= 4")
+    coin, r = 0, [1 + j for j in range(p)]
+    a = [1 + p + j for j in range(p - 1)]
+
+    def increment() -> List[Gate]:
+        g = [Gate("CCX", (coin, r[0], a[0]))]
+        for j in range(1, p - 1):
+            g.append(Gate("CCX", (a[j - 1], r[j], a[j])))
+        for j in range(p - 2, -1, -1):
+            g.append(Gate("CX", (a[j], r[j + 1])))
+            g.append(Gate("CCX", (a[j - 1], r[j], a[j])) if j > 0 else Gate("CCX", (coin, r[0], a[0])))
+        g.append(Gate("CX", (coin, r[0])))
+        return g
+
+    g: List[Gate] = []
+    for _ in range(steps):
+        g.append(Gate("H", (coin,)))
+        g += increment()
+        flip = [Gate("X", (q,)) for q in [coin] + r]
+        g += flip + increment() + flip
+    return g
+
+
 def sweep_workloads(n: int, seed: int = 11):
     """The sweep's gate-based families at n qubits: (name, gates)."""
     rng = np.random.default_rng(seed)
@@ -580,5 +614,6 @@ def sweep_workloads(n: int, seed: int = 11):
         ("amplitude_estimation", amplitude_estimation_gates(n, 3, seed)),
         ("w_state", w_state_gates(n)),
         ("grover_search", grover_vchain_gates(n, int(rng.integers(1, 2 ** ((n + 3) // 2))), 2)),
+        ("quantum_walk", quantum_walk_gates(n, 4)),
     ]
     return out
