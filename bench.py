@@ -263,7 +263,9 @@ def sweep_rows(qs, torch, n=25, budget_s=150.0):
     """The end-to-end sweep over the paper's gate-based suite at 25 qubits
     (workloads.sweep_workloads: TFIM, long-range Ising, Heisenberg variants,
     variational ansatze, QCBM, GHZ, graph state, QFT, phase estimation, QAOA
-    ring, Deutsch-Jozsa, random circuit, amplitude estimation, W state): per
+    ring, Deutsch-Jozsa, random circuit, amplitude estimation, W state,
+    Grover, quantum walk; plus the variational ansatz with its TFIM energy
+    <H> evaluated, the paper's "VQE ansatz + energy" row): per
     family the fused and per-gate times (CUDA events, after one untimed run
     each), their ratio, the fused plan's HBM passes, and the relative L2
     distance between the two paths' states from |0...0>.  Families left when
@@ -272,23 +274,44 @@ def sweep_rows(qs, torch, n=25, budget_s=150.0):
     st.provide_scratch()
     t_start = time.perf_counter()
     rows, skipped = {}, []
-    for name, gl in W.sweep_workloads(n):
+    families = list(W.sweep_workloads(n))
+    # the paper's "VQE ansatz + energy" row: the ansatz and <H> of the TFIM (J = h = 1)
+    vqe = dict(families)["variational_ansatz"]
+    families.append(("vqe_ansatz_energy", vqe))
+    terms = W.tfim_paulis(n, 1.0, 1.0)
+    for name, gl in families:
         if time.perf_counter() - t_start > budget_s:
             skipped.append(name)
             continue
-        cg = qs.CGates(gl)
-        _, passes = qs.plan_describe(n, cg)
-        st.zero()
-        st.apply(cg)
-        fused_state = st.tensor.clone()
-        st.zero()
-        st.apply(cg, mode="pergate")
-        rel = (torch.linalg.vector_norm(st.tensor - fused_state) / torch.linalg.vector_norm(fused_state)).item()
-        del fused_state
-        tf = _time_cuda(torch, st.stream, lambda: st.apply(cg), reps=2)
-        tp = _time_cuda(torch, st.stream, lambda: st.apply(cg, mode="pergate"), reps=1)
-        rows[name] = {"gates": len(gl), "passes": passes, "fused_s": tf, "pergate_s": tp,
-                      "speedup": tp / tf, "rel_l2_fused_vs_pergate": rel}
+        try:
+            cg = qs.CGates(gl)
+            _, passes = qs.plan_describe(n, cg)
+            energy = name == "vqe_ansatz_energy"
+            st.zero()
+            st.apply(cg)
+            fused_state = st.tensor.clone()
+            st.zero()
+            st.apply(cg, mode="pergate")
+            rel = (torch.linalg.vector_norm(st.tensor - fused_state) /
+                   torch.linalg.vector_norm(fused_state)).item()
+            del fused_state
+
+            def fused():
+                st.apply(cg)
+                if energy:
+                    st.expect(terms)
+
+            def pergate():
+                st.apply(cg, mode="pergate")
+                if energy:
+                    st.expect(terms)
+
+            tf = _time_cuda(torch, st.stream, fused, reps=2)
+            tp = _time_cuda(torch, st.stream, pergate, reps=1)
+            rows[name] = {"gates": len(gl), "passes": passes, "fused_s": tf, "pergate_s": tp,
+                          "speedup": tp / tf, "rel_l2_fused_vs_pergate": rel}
+        except Exception as e:   # one family's failure keeps the others
+            rows[name] = {"error": f"{type(e).__name__}: {e}"[:200]}
     st.close()
     out = {"n_qubits": n, "rows": rows, "budget_s": budget_s}
     if skipped:
