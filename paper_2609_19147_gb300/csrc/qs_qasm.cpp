@@ -11,7 +11,8 @@
 // program (inlined with its parameters and arguments bound, recursively,
 // using only gates defined before it), else the library's own gates under
 // their OpenQASM names (the primitives U and CX and the standard-library
-// names: cx -> CX, cu1 / cp -> CPHASE, u1 / p -> P, ...), else an error.
+// names: cx -> CX, cu1 / cp -> CPHASE, u1 / p -> P, ...; cu3 as the exact
+// two-CX construction of controlled-U3 from RZ, RY, CX and P), else an error.
 // A call whose arguments are whole registers applies the gate once per index
 // (all register arguments of one call have the same size; single-qubit
 // arguments are repeated).
@@ -486,6 +487,10 @@ class Program {
             return;
         }
         auto b = builtins().find(name);
+        if (b == builtins().end() && name == "cu3" && d == defs_.end()) {
+            cu3(prm, q, line);
+            return;
+        }
         if (b == builtins().end()) {
             if (d != defs_.end()) bad(line, "gate '" + name + "' is used before its definition");
             if (opaque_.count(name)) bad(line, "opaque gate '" + name + "'", QS_ERR_UNSUPPORTED);
@@ -497,19 +502,44 @@ class Program {
             bad(line, "gate '" + name + "' takes " + std::to_string(g.nq) + " qubit(s)");
         if ((int)prm.size() != g.np)
             bad(line, "gate '" + name + "' takes " + std::to_string(g.np) + " parameter(s)");
+        emit(name, g.kind, prm, q, line);
+    }
+
+    void emit(const std::string &name, uint16_t kind, const std::vector<double> &prm, const std::vector<int> &q,
+              int line) {
         if (measured_) bad(line, "a unitary gate after a measurement", QS_ERR_UNSUPPORTED);
         for (double v : prm)
             if (!std::isfinite(v)) bad(line, "gate '" + name + "': angle is not finite");
         qs_gate r;
         std::memset(&r, 0, sizeof r);
-        r.kind = g.kind;
-        r.nw = (uint8_t)g.nq;
-        for (int i = 0; i < g.nq; ++i) r.w[i] = q[i];
-        if (g.kind != QS_I)
-            for (int i = 0; i < g.np; ++i) r.p[i] = prm[i];
+        r.kind = kind;
+        r.nw = (uint8_t)q.size();
+        for (size_t i = 0; i < q.size(); ++i) r.w[i] = q[i];
+        if (kind != QS_I)
+            for (size_t i = 0; i < prm.size() && i < 3; ++i) r.p[i] = prm[i];
         r.param_idx = -1;
         r.dense = nullptr;
         out_.push_back(r);
+    }
+
+    // cu3(theta, phi, lambda) c, t: controlled-U3, U3 = e^{i(phi+lambda)/2} RZ(phi) RY(theta) RZ(lambda).
+    // With A = RZ(phi) RY(theta/2), B = RY(-theta/2) RZ(-(phi+lambda)/2) and
+    // C = RZ((lambda-phi)/2): A B C = I and A X B X C = e^{-i(phi+lambda)/2} U3, so
+    // controlled-U3 = P((phi+lambda)/2) on c after C, CX, B, CX, A on t (the
+    // two-CX construction of a controlled single-qubit gate), exactly.
+    void cu3(const std::vector<double> &prm, const std::vector<int> &q, int line) {
+        if (q.size() != 2) bad(line, "gate 'cu3' takes 2 qubit(s)");
+        if (prm.size() != 3) bad(line, "gate 'cu3' takes 3 parameter(s)");
+        const double th = prm[0], ph = prm[1], la = prm[2];
+        const int c = q[0], t = q[1];
+        emit("cu3", QS_RZ, {(la - ph) / 2}, {t}, line);
+        emit("cu3", QS_CX, {}, {c, t}, line);
+        emit("cu3", QS_RZ, {-(ph + la) / 2}, {t}, line);
+        emit("cu3", QS_RY, {-th / 2}, {t}, line);
+        emit("cu3", QS_CX, {}, {c, t}, line);
+        emit("cu3", QS_RY, {th / 2}, {t}, line);
+        emit("cu3", QS_RZ, {ph}, {t}, line);
+        emit("cu3", QS_P, {(ph + la) / 2}, {c}, line);
     }
 
     void expand(const std::string &name, const GateDef &d, const std::vector<double> &prm,

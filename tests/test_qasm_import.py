@@ -107,6 +107,24 @@ def test_user_gates_inline_to_the_gates_they_spell_out(qs):
                              oracle.simulate(1, [W.Gate("RZ", (0,), (1.1,))], _state(1, 4)))
 
 
+def test_cu3_is_controlled_u3(qs):
+    # controlled-U3 = diag(I, U3): the importer spells it with RZ, RY, CX and P, exactly
+    from oracle import gates as G
+    for t, p, l, c, tg in ((0.3, 1.1, -0.7, 2, 0), (2.5, -2.0, 0.4, 0, 1), (np.pi, 0.0, np.pi / 3, 1, 2)):
+        n, parsed = qs.parse_qasm(f"OPENQASM 2.0; qreg q[3]; cu3({t!r}, {p!r}, {l!r}) q[{c}], q[{tg}];")
+        psi0 = _state(3, 9)
+        want = psi0.reshape(2, 2, 2).copy()   # axes: qubits 0, 1, 2
+        sl = [slice(None)] * 3
+        sl[c] = 1
+        sub = want[tuple(sl)]                  # the control = 1 half, axes in qubit order without c
+        ax = [q for q in range(3) if q != c].index(tg)
+        want[tuple(sl)] = np.moveaxis(np.tensordot(G.matrix("U3", (t, p, l)), sub, axes=([1], [ax])), 0, ax)
+        assert np.allclose(oracle.simulate(3, parsed, psi0), want.reshape(-1), atol=1e-14)
+    # a program's own cu3 definition takes precedence
+    _, parsed = qs.parse_qasm("OPENQASM 2.0; qreg q[2]; gate cu3(a, b, c) x, y { cx x, y; } cu3(1, 2, 3) q[0], q[1];")
+    assert [g.kind for g in parsed] == ["CX"]
+
+
 def test_registers_broadcast_and_statements_skipped(qs):
     src = """OPENQASM 2.0;
     include "qelib1.inc";   // line comment
@@ -136,7 +154,8 @@ def test_registers_broadcast_and_statements_skipped(qs):
 
 
 @pytest.mark.parametrize("src,status,line", [
-    ("qreg q[2]; cu3(1, 2, 3) q[0], q[1];", 2, 1),                          # not in the gate set
+    ("qreg q[4]; c3x q[0], q[1], q[2], q[3];", 2, 1),                       # not in the gate set
+    ("qreg q[2]; cu3(1, 2) q[0], q[1];", 1, 1),                               # cu3 parameter count
     ("qreg q[2];\nh q[2];", 1, 2),                                            # index out of range
     ("qreg q[2];\n\ncx q[1], q[1];", 1, 3),                                   # repeated qubit
     ("qreg q[2]; creg c[2]; measure q -> c;\nh q[0];", 2, 2),               # gate after a measurement
