@@ -271,3 +271,20 @@ def test_planner_fuzz_all_option_combinations(qs):
             assert e.status == qs.QS_ERR_INVALID_ARG, (trial, n, t, lq, r, prec, str(e))
             continue
         assert passes >= 0 and text.startswith("FUSED"), (trial, text[:200])
+
+
+def test_c_program_uses_the_abi(qs, tmp_path):
+    # qs.h compiles as C11 and a C program links libqs.so and calls it (no GPU needed)
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("needs gcc")
+    lib_dir = os.path.dirname(qs.LIB_PATH)
+    exe = str(tmp_path / "c_abi_check")
+    subprocess.check_call([gcc, "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "cpp", "c_abi_check.c"), "-L", lib_dir, "-lqs",
+                           "-Wl,-rpath," + lib_dir, "-o", exe])
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0 and out.stdout.startswith("OK"), out.stdout + out.stderr
+
