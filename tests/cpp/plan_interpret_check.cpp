@@ -24,8 +24,10 @@
 //   (x & cmask) == cval)
 //   then <count> gate lines: kind nw w0 w1 w2 p0 p1 p2 param_idx has_dense [8 doubles]
 //   then B x P parameter values (item after item)
-// psi0 / out: B x 2^n complex128.  Prints one "CASE <i> ..." line per case
+// psi0 / out: B x 2^n complex128, or "-" for both: structure only (every
+// invariant, the boxes of 8 sampled tiles per pass; no state).  Prints one "CASE <i> ..." line per case
 // with the pass and micro-op counts, or "FAIL <i> <reason>" and exits 1.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdint>
@@ -107,6 +109,33 @@ class TileRun {
             for (uint64_t t = 0; t < tile.size(); ++t) tile[t] = psi[base | glob(t)];
             for (int s = 0; s < P_.n_sweeps; ++s) sweep(P_.sweeps[s], tile, base);
             for (uint64_t t = 0; t < tile.size(); ++t) psi[base | glob(t)] = tile[t];
+        }
+    }
+
+    // structure only (states too large for the host): every invariant of the
+    // pass, the tensor-copy box of 8 sampled tiles (the first, the last, six
+    // pseudo-random ones), and the sweeps run on a zero tile of each (constant
+    // bounds, micro-op and diagonal invariants)
+    void check_only(int bi, uint64_t seed) {
+        bi_ = bi;
+        structure();
+        std::vector<uint64_t> outer;
+        for (int b = 0; b < n_; ++b)
+            if (!((tilebits_ >> b) & 1)) outer.push_back(b);
+        std::vector<C> tile((size_t)1 << P_.T);
+        const uint64_t n_tiles = 1ull << outer.size();
+        uint64_t x = seed * 0x9E3779B97F4A7C15ull + 1;
+        for (int k = 0; k < 8; ++k) {
+            x ^= x << 13;
+            x ^= x >> 7;
+            x ^= x << 17;
+            const uint64_t ti = k == 0 ? 0 : k == 1 ? n_tiles - 1 : x % n_tiles;
+            uint64_t base = 0;
+            for (size_t i = 0; i < outer.size(); ++i)
+                if ((ti >> i) & 1) base |= 1ull << outer[i];
+            if (hp_.tma.ok) check_box(ti, base);
+            std::fill(tile.begin(), tile.end(), C(0.0));
+            for (int s = 0; s < P_.n_sweeps; ++s) sweep(P_.sweeps[s], tile, base);
         }
     }
 
@@ -704,10 +733,13 @@ int main(int argc, char **argv) {
         }
         if (!merged) run_plans = plans;
         const size_t N = (size_t)1 << n;
-        std::vector<C> psi(N * B);
-        FILE *fi = std::fopen(in_path, "rb");
-        if (!fi || std::fread(psi.data(), sizeof(C), psi.size(), fi) != psi.size()) return 2;
-        std::fclose(fi);
+        const bool structure_only = std::strcmp(in_path, "-") == 0;   // no state: invariants only
+        std::vector<C> psi(structure_only ? 0 : N * B);
+        if (!structure_only) {
+            FILE *fi = std::fopen(in_path, "rb");
+            if (!fi || std::fread(psi.data(), sizeof(C), psi.size(), fi) != psi.size()) return 2;
+            std::fclose(fi);
+        }
         Counts c;
         size_t pi = 0;
         size_t n_passes = mode == QS_MODE_PERGATE ? run_plans[0].pg.size() : run_plans[0].passes.size();
@@ -715,6 +747,30 @@ int main(int argc, char **argv) {
             for (int bi = 0; bi < B; ++bi) {
                 const Plan &plan = merged ? run_plans[0] : run_plans[bi];
                 if (plan.items != (merged ? B : 1)) throw Fail{"plan items"};
+                if (structure_only) {
+                    for (pi = 0; pi < plan.passes.size(); ++pi) {
+                        const HostPass &hp = plan.passes[pi];
+                        if (hp.type == HostPass::TILE) {
+                            TileRun(n, hp, c, merged ? bi : 0, plan.items, merged ? B : 1)
+                                .check_only(merged ? bi : 0, pi + 1);
+                        } else if (hp.type == HostPass::PERM) {
+                            uint64_t used = 0;
+                            for (int b = 0; b < n; ++b) used |= 1ull << hp.perm.out_pos[b];
+                            if (hp.perm.n != n || used != ((n >= 64) ? ~0ull : (1ull << n) - 1))
+                                throw Fail{"perm is not a permutation"};
+                            c.perm++;
+                        } else {
+                            const GatherPass &gp = hp.gather;
+                            if (gp.n != n || gp.n_slices < 1 || gp.n_slices > 5 || 8 * gp.n_slices < n)
+                                throw Fail{"gather slices"};
+                            for (int k = 0; k < gp.n_slices; ++k)
+                                for (int v = 0; v < 256; ++v)
+                                    if (gp.tab[k][v] >> n) throw Fail{"gather table outside the state"};
+                            c.gather++;
+                        }
+                    }
+                    continue;
+                }
                 C *st = psi.data() + (size_t)bi * N;
                 if (plan.mode == QS_MODE_PERGATE) {
                     for (pi = 0; pi < plan.pg.size(); ++pi) run_pergate(n, plan.pg[pi], st);
@@ -742,9 +798,11 @@ int main(int argc, char **argv) {
             std::printf("FAIL %d pass %zu: %s\n", ci, pi, f.why.c_str());
             return 1;
         }
-        FILE *fo = std::fopen(out_path, "wb");
-        if (!fo || std::fwrite(psi.data(), sizeof(C), psi.size(), fo) != psi.size()) return 2;
-        std::fclose(fo);
+        if (!structure_only) {
+            FILE *fo = std::fopen(out_path, "wb");
+            if (!fo || std::fwrite(psi.data(), sizeof(C), psi.size(), fo) != psi.size()) return 2;
+            std::fclose(fo);
+        }
         std::printf("CASE %d passes %zu tile %ld perm %ld gather %ld tma %ld rows %ld swz %ld sweeps %ld merged %d micro",
                     ci, n_passes, c.tile, c.perm, c.gather, c.tma, c.rows, c.swz, c.sweeps, merged ? 1 : 0);
         for (int k = 0; k <= MK_DIAGC; ++k) std::printf(" %ld", c.micro[k]);
