@@ -341,10 +341,11 @@ class Program {
             if (declared(name)) bad(line, "'" + name + "' is declared twice");
             if (size < 1) bad(line, "register size must be positive");
             if (w == "qreg") {
-                if (nq_ + size > kMaxQubitsQasm) bad(line, "more than 63 qubits", QS_ERR_UNSUPPORTED);
+                if (size > kMaxQubitsQasm - nq_) bad(line, "more than 63 qubits", QS_ERR_UNSUPPORTED);
                 qregs_[name] = {nq_, (int)size};
                 nq_ += (int)size;
             } else {
+                if (size > (1 << 20)) bad(line, "creg larger than 2^20 bits", QS_ERR_UNSUPPORTED);
                 cregs_[name] = (int)size;
             }
         } else if (w == "gate") {

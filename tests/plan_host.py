@@ -1,6 +1,7 @@
 """Runs the host plan interpreter (tests/cpp/plan_interpret_check.cpp) over a
 list of cases and returns, per case, the final states and the interpreter's
-pass / micro-op counts.
+pass / micro-op counts.  With QS_HOST_SANITIZE=1 in the environment the
+interpreter and the planner are built with AddressSanitizer and UBSan.
 
 A case is (name, n, gates, (T, L, R, dense_prec, block_qubits[, mode])[, params]),
 mode 0 = fused (default) or 1 = per-gate, params a B x P array of parameter
@@ -47,11 +48,14 @@ def interpret(qs, cases, workdir, psi0s):
         f.write("\n".join(lines) + "\n")
     csrc = os.path.join(ROOT, "paper_2609_19147_gb300", "csrc")
     exe = os.path.join(workdir, "plan_interpret_check")
-    subprocess.check_call([shutil.which("g++"), "-O2", "-std=c++17", "-I", os.path.join(ROOT, "include"), "-I", csrc,
+    # QS_HOST_SANITIZE=1: build the interpreter and the planner with AddressSanitizer and UBSan
+    san = ["-O1", "-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=undefined"] \
+        if os.environ.get("QS_HOST_SANITIZE") == "1" else ["-O2"]
+    subprocess.check_call([shutil.which("g++")] + san + ["-std=c++17", "-I", os.path.join(ROOT, "include"), "-I", csrc,
                            "-I", "/usr/local/cuda/include",
                            os.path.join(ROOT, "tests", "cpp", "plan_interpret_check.cpp"),
                            os.path.join(csrc, "qs_plan.cpp"), "-o", exe, "-lpthread"])
-    out = subprocess.run([exe, src], capture_output=True, text=True, timeout=900)
+    out = subprocess.run([exe, src], capture_output=True, text=True, timeout=3000)
     assert out.returncode == 0, out.stdout[-3000:] + out.stderr[-2000:]
     rows = [l.split() for l in out.stdout.splitlines() if l.startswith("CASE")]
     assert len(rows) == len(cases)

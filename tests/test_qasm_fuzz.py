@@ -30,3 +30,24 @@ def test_parser_survives_fuzzing(built):
     line = [l for l in r.stdout.splitlines() if l.startswith("FUZZ")][-1]
     stats = dict(kv.split("=") for kv in line.split()[1:])
     assert int(stats["ok"]) > 50 and int(stats["err"]) > 500, stats
+
+
+def test_parser_mutation_fuzz_under_sanitizers(tmp_path):
+    # the parser alone, in-process, under AddressSanitizer and UBSan
+    import shutil
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("needs g++")
+    exe = str(tmp_path / "qasm_mutation_fuzz")
+    csrc = os.path.join(ROOT, "paper_2609_19147_gb300", "csrc")
+    r = subprocess.run([gxx, "-std=c++17", "-O1", "-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=undefined",
+                        "-I", os.path.join(ROOT, "include"), "-I", csrc,
+                        os.path.join(HERE, "cpp", "qasm_mutation_fuzz.cpp"), os.path.join(csrc, "qs_qasm.cpp"),
+                        "-o", exe], capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("no sanitizer runtime: " + r.stderr[-200:])
+    out = subprocess.run([exe, "5", "6000"], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stdout[-1000:] + out.stderr[-3000:]
+    ok, err = (int(kv.split("=")[1]) for kv in out.stdout.split())
+    assert ok + err == 6000 and ok > 20
+
