@@ -2254,19 +2254,23 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
         }
     }
 
+    // the ops still to schedule are rem[head..]: a pass moves `head` past what
+    // it placed (O(ops scanned) per pass, not O(ops left))
     std::vector<int> rem(ops.size());
     for (size_t i = 0; i < ops.size(); ++i) rem[i] = (int)i;
+    size_t head = 0;
+    std::vector<char> placed(ops.size(), 0);
     const uint64_t lowmask = (L >= 64) ? ~0ull : ((1ull << L) - 1);
     const int kLookahead = 4096, kMaxDeferred = 96;
 
-    while (!rem.empty()) {
-        const FOp &f0 = ops[rem[0]];
+    while (head < rem.size()) {
+        const FOp &f0 = ops[rem[head]];
         if (f0.kind == F_GF2) {
             HostPass hp;
             build_perm_or_gather(n, f0, hp);
             hp.note = hp.type == HostPass::PERM ? "perm" : "gather";
             plan.passes.push_back(hp);
-            rem.erase(rem.begin());
+            ++head;
             continue;
         }
         uint64_t S = lowmask;
@@ -2277,8 +2281,8 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
         int sim_sweeps = 0;          // mirrors PassBuilder::need_bits grouping
         uint64_t sim_group = 0;
         bool sim_open = false;
-        for (; j < rem.size() && (int)j < kLookahead; ++j) {
-            const FOp &f = ops[rem[j]];
+        for (; head + j < rem.size() && (int)j < kLookahead; ++j) {
+            const FOp &f = ops[rem[head + j]];
             if (f.kind == F_GF2) break;
             bool ok = true;
             for (int d : deferred)
@@ -2288,7 +2292,7 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
                 }
             if (ok) {
                 uint64_t need = f.cN & ~S;
-                OpCost c = op_cost(n, f, R, f.kind == F_DIAG ? &dplans[rem[j]] : nullptr, dprec);
+                OpCost c = op_cost(n, f, R, f.kind == F_DIAG ? &dplans[rem[head + j]] : nullptr, dprec);
                 uint64_t nb = f.cN;
                 int ns = sim_sweeps;
                 uint64_t ng = sim_group;
@@ -2321,11 +2325,11 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
                     c_const += c.n_const;
                     c_micro += c.n_micro;
                     c_diag += c.n_diag;
-                    taken.push_back(rem[j]);
+                    taken.push_back(rem[head + j]);
                     continue;
                 }
             }
-            deferred.push_back(rem[j]);
+            deferred.push_back(rem[head + j]);
             if ((int)deferred.size() >= kMaxDeferred) {
                 ++j;
                 break;
@@ -2340,7 +2344,6 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
         PassBuilder pb(n, L, T, R, S, batch, dprec);
         // the sweep estimate above can fall short of the builder's grouping:
         // ops the pass has no room for stay in the queue (below)
-        std::vector<char> placed(ops.size(), 0);
         for (int id : taken) {
             pb.add(ops[id], ops[id].kind == F_DIAG ? &dplans[id] : nullptr);
             placed[id] = 1;
@@ -2356,11 +2359,12 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
         // everything scanned but not placed, in stream order: the deferred ops
         // and any taken op past the builder's limit (each placed op commutes
         // with every deferred op before it, so the order stays exact)
-        std::vector<int> nrem;
+        std::vector<int> carry;
         for (size_t k = 0; k < j; ++k)
-            if (!placed[rem[k]]) nrem.push_back(rem[k]);
-        nrem.insert(nrem.end(), rem.begin() + j, rem.end());
-        rem.swap(nrem);
+            if (!placed[rem[head + k]]) carry.push_back(rem[head + k]);
+        for (int id : taken) placed[id] = 0;
+        head += j - carry.size();
+        std::copy(carry.begin(), carry.end(), rem.begin() + head);
     }
     return QS_OK;
 }
