@@ -48,7 +48,7 @@ typedef int32_t qs_status;
 enum {
     QS_OK = 0,
     QS_ERR_INVALID_ARG = 1,  /* bad pointer, size, wire, kind or arity      */
-    QS_ERR_UNSUPPORTED = 2,  /* valid request outside what this build does  */
+    QS_ERR_UNSUPPORTED = 2,  /* valid request the library does not support  */
     QS_ERR_OOM = 3,          /* device allocation failed / cap exceeded     */
     QS_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed        */
     QS_ERR_TIMEOUT = 5,      /* a bounded device wait ran out               */
