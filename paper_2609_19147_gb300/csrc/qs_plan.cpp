@@ -1426,6 +1426,56 @@ TmaPlan tma_geometry(int n, int L, uint64_t S, int batch) {
     return g;
 }
 
+// Complete a tile's bit set S (the low bits and the high bits its ops need)
+// to T bits.  The lowest unused high bits, unless that leaves more than the 5
+// tensor dims one TMA copy can take (each run of tile bits and each gap of
+// other bits is a dim): then the smallest gaps below the highest tile bit are
+// filled first, which merges runs, and the rest of the room extends the top
+// run upward.  Where neither fits the tensor copy, the default stays (the
+// pass then copies its tile row by row).
+static uint64_t pad_tile_bits(int n, int L, int T, uint64_t S, int batch) {
+    uint64_t def = S;
+    for (int b = L; b < n && popc64(def) < T; ++b) def |= 1ull << b;
+    if (tma_geometry(n, L, def, batch).ok) return def;
+    int top = -1;
+    for (int b = n - 1; b >= L; --b)
+        if ((S >> b) & 1) {
+            top = b;
+            break;
+        }
+    if (top < 0) return def;
+    int slack = T - popc64(S);
+    std::vector<std::pair<int, int>> gaps;   // (length, first bit) of the runs of other bits in [L, top)
+    for (int b = L; b < top;) {
+        if ((S >> b) & 1) {
+            ++b;
+            continue;
+        }
+        int e = b;
+        while (e < top && !((S >> e) & 1)) ++e;
+        gaps.push_back({e - b, b});
+        b = e;
+    }
+    std::sort(gaps.begin(), gaps.end());
+    uint64_t P = S;
+    for (auto &g : gaps)
+        if (g.first <= slack) {
+            for (int b = g.second; b < g.second + g.first; ++b) P |= 1ull << b;
+            slack -= g.first;
+        }
+    for (int b = top + 1; b < n && slack > 0; ++b)
+        if (!((P >> b) & 1)) {
+            P |= 1ull << b;
+            --slack;
+        }
+    for (int b = L; b < n && slack > 0; ++b)
+        if (!((P >> b) & 1)) {
+            P |= 1ull << b;
+            --slack;
+        }
+    return tma_geometry(n, L, P, batch).ok ? P : def;
+}
+
 // FP64 -> TF32 (FP32 with 10 explicit mantissa bits), round to nearest even
 float tf32_round(double x) {
     float f = (float)x;
@@ -2339,8 +2389,7 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
             err = "scheduler could not place an op (internal)";
             return QS_ERR_INTERNAL;
         }
-        // pad the tile to T bits with the lowest unused high bits
-        for (int b = L; b < n && popc64(S) < T; ++b) S |= 1ull << b;
+        S = pad_tile_bits(n, L, T, S, batch);
         PassBuilder pb(n, L, T, R, S, batch, dprec);
         // the sweep estimate above can fall short of the builder's grouping:
         // ops the pass has no room for stay in the queue (below)
