@@ -12,7 +12,8 @@
 // using only gates defined before it), else the library's own gates under
 // their OpenQASM names (the primitives U and CX and the standard-library
 // names: cx -> CX, cu1 / cp -> CPHASE, u1 / p -> P, ...; cu3 as the exact
-// two-CX construction of controlled-U3 from RZ, RY, CX and P), else an error.
+// two-CX construction of controlled-U3 from RZ, RY, CX and P; c3x / c4x as
+// exact ancilla-free phase polynomials of CX and P between H), else an error.
 // A call whose arguments are whole registers applies the gate once per index
 // (all register arguments of one call have the same size; single-qubit
 // arguments are repeated).
@@ -492,6 +493,13 @@ class Program {
             cu3(prm, q, line);
             return;
         }
+        if (b == builtins().end() && (name == "c3x" || name == "c4x") && d == defs_.end()) {
+            const int k = name == "c3x" ? 3 : 4;
+            if ((int)q.size() != k + 1) bad(line, "gate '" + name + "' takes " + std::to_string(k + 1) + " qubit(s)");
+            if (!prm.empty()) bad(line, "gate '" + name + "' takes 0 parameter(s)");
+            mcx(q, line);
+            return;
+        }
         if (b == builtins().end()) {
             if (d != defs_.end()) bad(line, "gate '" + name + "' is used before its definition");
             if (opaque_.count(name)) bad(line, "opaque gate '" + name + "'", QS_ERR_UNSUPPORTED);
@@ -521,6 +529,32 @@ class Program {
         r.param_idx = -1;
         r.dense = nullptr;
         out_.push_back(r);
+    }
+
+    // X on the last of q controlled by all the others (m = |q| qubits), with no
+    // ancilla: H on the target turns it into the phase pi x_1 ... x_m, and
+    // x_1 ... x_m = 2^(1-m) sum over nonempty subsets S of (-1)^(|S|+1)
+    // (parity of x over S) (inclusion-exclusion over parities).  Each
+    // parity is gathered onto the highest qubit of S by CX from the others,
+    // takes P(+-pi / 2^(m-1)), and the CX are undone.
+    void mcx(const std::vector<int> &q, int line) {
+        const int m = (int)q.size(), t = q[m - 1];
+        emit("mcx", QS_H, {}, {t}, line);
+        for (unsigned S = 1; S < (1u << m); ++S) {
+            int top = -1, size = 0;
+            for (int i = 0; i < m; ++i)
+                if ((S >> i) & 1) {
+                    top = i;
+                    ++size;
+                }
+            const double ang = ((size & 1) ? 1.0 : -1.0) * M_PI / (double)(1u << (m - 1));
+            for (int i = 0; i < top; ++i)
+                if ((S >> i) & 1) emit("mcx", QS_CX, {}, {q[i], q[top]}, line);
+            emit("mcx", QS_P, {ang}, {q[top]}, line);
+            for (int i = top - 1; i >= 0; --i)
+                if ((S >> i) & 1) emit("mcx", QS_CX, {}, {q[i], q[top]}, line);
+        }
+        emit("mcx", QS_H, {}, {t}, line);
     }
 
     // cu3(theta, phi, lambda) c, t: controlled-U3, U3 = e^{i(phi+lambda)/2} RZ(phi) RY(theta) RZ(lambda).

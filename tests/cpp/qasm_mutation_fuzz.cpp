@@ -21,7 +21,7 @@ int main(int argc, char **argv) {
     const char *vocab[] = {"OPENQASM", "2.0", "include", "\"qelib1.inc\"", "qreg", "creg", "gate", "opaque", "barrier",
                            "measure", "q", "r", "a", "b", "t", "[", "]", "(", ")", "{", "}", ";", ",", "->", "+", "-",
                            "*", "/", "^", "pi", "sin", "sqrt", "0", "1", "7", "1e308", "99999999999999999999",
-                           "h", "cx", "u3", "cu3", "zz", "lay", "U", "CX", "//", "/*", "*/", "\"", "\n", "((((", "----"};
+                           "h", "cx", "u3", "cu3", "c3x", "c4x", "zz", "lay", "U", "CX", "//", "/*", "*/", "\"", "\n", "((((", "----"};
     long ok = 0, err = 0;
     const int iters = argc > 2 ? atoi(argv[2]) : 20000;
     for (int it = 0; it < iters; ++it) {

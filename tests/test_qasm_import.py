@@ -125,6 +125,21 @@ def test_cu3_is_controlled_u3(qs):
     assert [g.kind for g in parsed] == ["CX"]
 
 
+def test_c3x_c4x_are_multi_controlled_x(qs):
+    # X on the last qubit where all the others are 1, exactly, with no ancilla
+    for name, k, order in (("c3x", 3, (4, 0, 2, 1)), ("c4x", 4, (5, 1, 3, 0, 2))):
+        n = k + 2
+        _, parsed = qs.parse_qasm(f"OPENQASM 2.0; qreg q[{n}]; {name} " + ", ".join(f"q[{i}]" for i in order) + ";")
+        psi0 = _state(n, k)
+        want = psi0.copy()
+        ctrl, tgt = order[:-1], order[-1]
+        for x in range(2 ** n):
+            if all((x >> (n - 1 - c)) & 1 for c in ctrl) and not (x >> (n - 1 - tgt)) & 1:
+                y = x | (1 << (n - 1 - tgt))
+                want[x], want[y] = psi0[y], psi0[x]
+        assert np.allclose(oracle.simulate(n, parsed, psi0), want, atol=1e-14)
+
+
 def test_registers_broadcast_and_statements_skipped(qs):
     src = """OPENQASM 2.0;
     include "qelib1.inc";   // line comment
@@ -154,7 +169,8 @@ def test_registers_broadcast_and_statements_skipped(qs):
 
 
 @pytest.mark.parametrize("src,status,line", [
-    ("qreg q[4]; c3x q[0], q[1], q[2], q[3];", 2, 1),                       # not in the gate set
+    ("qreg q[4]; rc3x q[0], q[1], q[2], q[3];", 2, 1),                      # not in the gate set
+    ("qreg q[4]; c3x q[0], q[1], q[2];", 1, 1),                               # c3x qubit count
     ("qreg q[2]; cu3(1, 2) q[0], q[1];", 1, 1),                               # cu3 parameter count
     ("qreg q[2];\nh q[2];", 1, 2),                                            # index out of range
     ("qreg q[2];\n\ncx q[1], q[1];", 1, 3),                                   # repeated qubit
