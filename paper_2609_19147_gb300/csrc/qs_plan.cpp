@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <set>
 #include <sstream>
 
@@ -2390,15 +2391,30 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
             return QS_ERR_INTERNAL;
         }
         S = pad_tile_bits(n, L, T, S, batch);
-        PassBuilder pb(n, L, T, R, S, batch, dprec);
-        // the sweep estimate above can fall short of the builder's grouping:
-        // ops the pass has no room for stay in the queue (below)
-        for (int id : taken) {
-            pb.add(ops[id], ops[id].kind == F_DIAG ? &dplans[id] : nullptr);
-            placed[id] = 1;
-            if (pb.tp.n_sweeps >= kMaxSweeps - 1 || pb.tp.n_micro >= kMaxMicro - 16) break;
+        // the sweep and constant estimates above can fall short of what the
+        // builder makes: ops past its sweep / micro-op limit stay in the
+        // queue (below), and a pass whose constants come out over the budget
+        // (the optional factored diagonals of finalize and the count tables
+        // share it) is rebuilt from a shorter prefix of its ops
+        size_t limit = taken.size();
+        std::unique_ptr<PassBuilder> pbp;
+        for (;;) {
+            pbp.reset(new PassBuilder(n, L, T, R, S, batch, dprec));
+            size_t added = 0;
+            for (size_t k = 0; k < limit; ++k) {
+                const int id = taken[k];
+                pbp->add(ops[id], ops[id].kind == F_DIAG ? &dplans[id] : nullptr);
+                ++added;
+                if (pbp->tp.n_sweeps >= kMaxSweeps - 1 || pbp->tp.n_micro >= kMaxMicro - 16) break;
+            }
+            pbp->finalize();
+            if (pbp->tp.n_const <= max_const || added <= 1) {
+                for (size_t k = 0; k < added; ++k) placed[taken[k]] = 1;
+                break;
+            }
+            limit = added - std::max<size_t>(1, added / 8);
         }
-        pb.finalize();
+        PassBuilder &pb = *pbp;
         if (pb.count_failed) {
             err = "count-table diagonal could not be placed (internal)";
             return QS_ERR_INTERNAL;
