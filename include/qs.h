@@ -271,7 +271,8 @@ qs_status qs_plan_describe(int n, const qs_gate *gates, size_t n_gates,
  *    cu1 / cp, rzz, rxx, ryy, ccx, cswap), with this library's matrices
  *    (global phases may differ from a textual expansion of qelib1.inc);
  *    cu3 becomes controlled-U3 exactly, spelled with RZ, RY, CX and P;
- *    c3x / c4x become exact ancilla-free phase polynomials (CX, P, H).
+ *    c3x / c4x become exact ancilla-free phase polynomials (CX, P, H);
+ *    sxdg becomes SX^3.
  *  - `gate` definitions in the program take precedence over those names;
  *    they are inlined recursively with parameters and arguments bound.
  *  - A call on whole registers applies the gate once per index.

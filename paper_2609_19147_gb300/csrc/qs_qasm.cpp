@@ -13,7 +13,8 @@
 // their OpenQASM names (the primitives U and CX and the standard-library
 // names: cx -> CX, cu1 / cp -> CPHASE, u1 / p -> P, ...; cu3 as the exact
 // two-CX construction of controlled-U3 from RZ, RY, CX and P; c3x / c4x as
-// exact ancilla-free phase polynomials of CX and P between H), else an error.
+// exact ancilla-free phase polynomials of CX and P between H; sxdg as SX^3),
+// else an error.
 // A call whose arguments are whole registers applies the gate once per index
 // (all register arguments of one call have the same size; single-qubit
 // arguments are repeated).
@@ -491,6 +492,12 @@ class Program {
         auto b = builtins().find(name);
         if (b == builtins().end() && name == "cu3" && d == defs_.end()) {
             cu3(prm, q, line);
+            return;
+        }
+        if (b == builtins().end() && name == "sxdg" && d == defs_.end()) {   // SX^4 = X^2 = I: SX^-1 = SX^3
+            if (q.size() != 1) bad(line, "gate 'sxdg' takes 1 qubit(s)");
+            if (!prm.empty()) bad(line, "gate 'sxdg' takes 0 parameter(s)");
+            for (int r = 0; r < 3; ++r) emit("sxdg", QS_SX, {}, {q[0]}, line);
             return;
         }
         if (b == builtins().end() && (name == "c3x" || name == "c4x") && d == defs_.end()) {

@@ -140,6 +140,15 @@ def test_c3x_c4x_are_multi_controlled_x(qs):
         assert np.allclose(oracle.simulate(n, parsed, psi0), want, atol=1e-14)
 
 
+def test_sxdg_is_the_inverse_of_sx(qs):
+    from oracle import gates as G
+    _, parsed = qs.parse_qasm("OPENQASM 2.0; qreg q[2]; sxdg q[1]; sx q[1]; sxdg q[0];")
+    psi0 = _state(2, 6)
+    want = psi0.reshape(2, 2).copy()
+    want = np.tensordot(G.matrix("SX", ()).conj().T, want, axes=([1], [0]))   # sxdg on qubit 0
+    assert np.allclose(oracle.simulate(2, parsed, psi0), want.reshape(-1), atol=1e-14)
+
+
 def test_registers_broadcast_and_statements_skipped(qs):
     src = """OPENQASM 2.0;
     include "qelib1.inc";   // line comment
