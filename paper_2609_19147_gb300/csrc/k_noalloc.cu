@@ -1,25 +1,31 @@
 // qs_expect_noalloc: Pauli expectation values for callers that must not
 // allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured (allocation is not a capturable operation), plug-ins that
-// live inside a host application owning every device allocation through its
-// own arena, and latency-critical loops where an allocation's implicit
-// synchronisation is unacceptable.  qs_expect needs device scratch for its
-// per-block partial sums and allocates it on first use; this entry point runs
-// the same reduction kernels with that scratch taken from a fixed array
-// compiled into the library instead.
+// Some callers cannot call cudaMalloc.  A plug-in that runs inside a host
+// application which owns every device allocation (a serving runtime or a
+// simulation host with its own arena and memory accounting) is not allowed to
+// allocate behind the host's back.  A process that has sized its state vector
+// to fill the GPU has no room left for a late allocation, which would fail
+// with out-of-memory.  And a real-time loop cannot take the implicit device
+// synchronisation of cudaMalloc / cudaFree.  qs_expect needs device scratch
+// for its per-block partial sums and allocates it on first use; this entry
+// point runs the same reduction kernels with that scratch taken from a fixed
+// array compiled into the library instead.
 //
 // The array is a file-scope static __device__ buffer of 694,272 bytes
-// (678 KiB; limits: batch <= 16, n_terms <= 256): every GPU
-// that loads the library holds it until the process exits.  Host code cannot
-// use the array's name as a device address, so the first call on each device
-// looks the address up with cudaGetSymbolAddress (with that device current)
-// and caches it; make that first call before any stream capture.  All calls
-// share the one array and it keeps the previous call's contents, so calls
-// whose work overlaps on the GPU (different streams, or different host
-// threads) race on it.  Nothing needs clearing between calls: every slot a
-// call reads is written earlier in the same call.
+// (678 KiB; limits: batch <= 16, n_terms <= 256): every GPU that loads the
+// library holds it until the process exits.  Host code cannot use the
+// array's name as a device address, so the first call on each device (per
+// CUDA context) looks the address up with cudaGetSymbolAddress, with that
+// device current, and keeps it; that first call should come before any
+// stream capture.  All calls share the one array and it keeps the previous
+// call's contents, so calls whose work overlaps on the GPU (different
+// streams, or different host threads) race on it.  Nothing needs clearing
+// between calls: every slot a call reads is written earlier in the same
+// call.  The call is synchronous: it waits for its stream before it returns
+// the sums in host memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -45,8 +51,31 @@ constexpr size_t kNaBytes = (kNaPartialDoubles + kNaOutDoubles) * sizeof(double)
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
+// The array's device address, looked up once per (device, context).  The
+// module holding the array is loaded once per context, so a context created
+// after cudaDeviceReset, or a caller's own non-primary context, can place it
+// elsewhere: the address is kept per context, not only per device.
+struct NaAddr {
+    int dev;
+    CUcontext ctx;
+    unsigned char *addr;
+};
 std::mutex g_na_mu;
-unsigned char *g_na_addr[64] = {nullptr};   // per device, from cudaGetSymbolAddress
+NaAddr g_na_addr[64];
+int g_na_count = 0;
+PFN_cuCtxGetCurrent_v4000 g_na_get_ctx = nullptr;
+
+bool na_current_ctx(CUcontext *out) {
+    if (!g_na_get_ctx) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        g_na_get_ctx = (PFN_cuCtxGetCurrent_v4000)fn;
+    }
+    return g_na_get_ctx(out) == CUDA_SUCCESS;
+}
 
 qs_status na_fail(qs_status s, const char *msg) {
     qs::set_last_error(msg);   // reported by qs_last_error()
@@ -65,20 +94,25 @@ extern "C" qs_status qs_expect_noalloc(const void *dev_state, int n, int batch, 
         return na_fail(QS_ERR_UNSUPPORTED, "n_terms exceeds the no-alloc maximum of 256");
     cudaStream_t st = (cudaStream_t)cuda_stream;
 
-    // set-up, once per device, with that device current
+    // set-up, once per device and context, with that device current
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
-        return na_fail(QS_ERR_CUDA, "cudaGetDevice failed");
-    unsigned char *base;
+    if (cudaGetDevice(&dev) != cudaSuccess) return na_fail(QS_ERR_CUDA, "cudaGetDevice failed");
+    unsigned char *base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_na_mu);
-        if (!g_na_addr[dev]) {
+        CUcontext ctx = nullptr;
+        if (!na_current_ctx(&ctx)) return na_fail(QS_ERR_CUDA, "cuCtxGetCurrent failed");
+        for (int i = 0; i < g_na_count && ctx; ++i)
+            if (g_na_addr[i].dev == dev && g_na_addr[i].ctx == ctx) base = g_na_addr[i].addr;
+        if (!base) {
             void *p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) return na_fail(QS_ERR_CUDA, "cudaGetSymbolAddress failed");
-            g_na_addr[dev] = static_cast<unsigned char *>(p);
+            base = static_cast<unsigned char *>(p);
+            // the lookup binds the device's primary context when none was current
+            if (!na_current_ctx(&ctx) || !ctx) return na_fail(QS_ERR_CUDA, "no current CUDA context");
+            if (g_na_count < 64) g_na_addr[g_na_count++] = NaAddr{dev, ctx, base};
         }
-        base = g_na_addr[dev];
     }
     double *d_partial = reinterpret_cast<double *>(base);
     double *d_out = d_partial + kNaPartialDoubles;
