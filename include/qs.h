@@ -141,13 +141,16 @@ typedef struct qs_opts {
 typedef struct qs_state qs_state;
 
 /* Allocate `batch` states of n qubits in device memory owned by the library,
- * each initialised to |0...0>.  n in [1, 33]; batch >= 1.  Errors:
+ * each initialised to |0...0> (Sec. 3.2.1 state management: an n-qubit
+ * register starts in |0...0> and is held as 2^n amplitudes; Sec. 2.1 for the
+ * state-vector representation).  n in [1, 33]; batch >= 1.  Errors:
  * QS_ERR_INVALID_ARG (out == NULL, batch < 1), QS_ERR_UNSUPPORTED (n out of
  * range), QS_ERR_OOM (allocation failed).  Free with qs_free. */
 qs_status qs_alloc(int n, int batch, qs_state **out);
 
 /* Wrap caller-owned device memory (e.g. a torch tensor) of batch * 2^n
- * complex64 amplitudes, 16-byte aligned.  The library never frees
+ * complex64 amplitudes, 16-byte aligned (the amplitude array of Sec. 3.2.1,
+ * owned by the caller instead of the library).  The library never frees
  * `dev_ptr`; `cuda_stream` (a cudaStream_t, may be NULL) becomes the state's
  * stream.  The contents are left as they are. */
 qs_status qs_wrap(void *dev_ptr, int n, int batch, void *cuda_stream, qs_state **out);
@@ -168,16 +171,20 @@ qs_status qs_set_scratch(qs_state *st, void *dev_ptr, size_t bytes);
 /* Device pointer of the amplitudes (batch * 2^n complex64). */
 qs_status qs_device_ptr(const qs_state *st, void **out);
 
-/* Reset every state of the batch to |0...0>; asynchronous. */
+/* Reset every state of the batch to |0...0> (Sec. 3.2.1); asynchronous. */
 qs_status qs_init_zero(qs_state *st);
 
 /* Copy batch * 2^n complex64 amplitudes in (src) or out (dst); `is_device`
- * says whether the pointer is device memory.  Synchronous: returns after
+ * says whether the pointer is device memory (Sec. 3.2.1: the amplitudes of
+ * the state are readable and settable as one array, index bit n-1-q =
+ * qubit q).  Synchronous: returns after
  * the copy is complete. */
 qs_status qs_set_amplitudes(qs_state *st, const void *src, int is_device);
 qs_status qs_get_amplitudes(const qs_state *st, void *dst, int is_device);
 
-/* Apply the gate list to every state of the batch, in order.
+/* Apply the gate list to every state of the batch, in order (Sec. 3.2.2
+ * gate application on the reshaped state; Sec. 5.1 layer families and
+ * Sec. 5.2 semantics-preserving fusion, which the fused mode follows).
  * params: NULL, or batch x n_params doubles (row b resolves param_idx for
  * state b).  Every gate is validated before anything runs: kind and nw
  * consistent, wires distinct and in [0, n), param_idx < n_params, dense != NULL
@@ -194,7 +201,14 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates,
 qs_status qs_expect(qs_state *st, const qs_pauli *terms, size_t n_terms, double *out);
 
 /* Adjoint-method gradient of E_b(theta) = <psi_b(theta)|H|psi_b(theta)> with
- * psi_b(theta) = U(theta_b)|0...0>, H = sum_k coeff_k P_k.  The state is
+ * psi_b(theta) = U(theta_b)|0...0>, H = sum_k coeff_k P_k.  The paper's
+ * variational algorithms (Sec. 3.2.3, VQE with a hardware-efficient ansatz)
+ * take gradients by parameter shift, two energy evaluations per parameter;
+ * this call returns all of them from one reverse sweep instead (the adjoint
+ * method of Jones and Gacon 2020, arXiv:2009.02823: lambda = H psi carried
+ * back through the inverse gates, dE/dt = Im <lambda| G |psi> at each
+ * rotation exp(-i t G / 2)).  The results equal the parameter-shift values
+ * up to float rounding.  The state is
  * overwritten: on return it holds psi_b(theta).  energy: batch doubles;
  * grad: batch x n_params doubles (zero for unused indices).  Parameterised
  * gates must be QS_RX, QS_RY, QS_RZ, QS_RZZ or QS_CP (else
@@ -308,27 +322,29 @@ typedef struct qs_profile_record {
 qs_status qs_profile_read(qs_state *st, qs_profile_record *out, int cap, int *count);
 
 /* Pauli expectation values without any device allocation.  The paper has
- * no counterpart: this call exists for callers that cannot call cudaMalloc --
- * code running while a CUDA graph is being captured (allocation is not a
- * capturable operation), plug-ins inside a host application that owns every
- * device allocation through its own arena, and latency-critical loops that
- * cannot afford an allocation's implicit synchronisation.  It computes what
- * qs_expect computes (out[b] = <psi_b| sum_k coeff_k P_k |psi_b>, FP64
- * accumulation), but takes the state as a plain device pointer and keeps its
- * scratch (block partial sums, finished sums, the term table) in one
- * file-scope static __device__ array of 694,272 bytes compiled into the
- * library.  Every GPU that loads the library holds that array until the
- * process exits.
+ * no counterpart: this call exists for callers that cannot call cudaMalloc.
+ * A plug-in inside a host application that owns every device allocation
+ * through its own arena may not allocate behind the host's back; a process
+ * that sized its states to fill the GPU has no room for a late allocation;
+ * a real-time loop cannot take the implicit device synchronisation of
+ * cudaMalloc / cudaFree.  It computes what qs_expect computes
+ * (out[b] = <psi_b| sum_k coeff_k P_k |psi_b>, FP64 accumulation), but takes
+ * the state as a plain device pointer and keeps its scratch (block partial
+ * sums, finished sums, the term table) in one file-scope static __device__
+ * array of 694,272 bytes compiled into the library.  Every GPU that loads
+ * the library holds that array until the process exits.
  *   dev_state: device pointer, batch * 2^n complex64, 16-byte aligned (read only)
  *   n in [1, 33]; batch in [1, 16]; n_terms <= 256 (larger -> QS_ERR_UNSUPPORTED,
- *   nothing launched); out: host array of batch doubles; cuda_stream: the
- *   cudaStream_t to run on (NULL = legacy default).  Synchronous.
- * The first call on each device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current); make that first call
- * before any stream capture.  All calls share the one array and it keeps the
- * previous call's contents: calls whose work overlaps on the GPU (other
- * streams, other host threads) race on it.  Nothing in it needs clearing --
- * every slot a call reads is written earlier in the same call.
+ *   nothing launched); n_terms == 0 gives out[b] = 0; out: host array of
+ *   batch doubles; cuda_stream: the cudaStream_t to run on (NULL = legacy
+ *   default).  Synchronous: returns after the stream has finished the sums.
+ * The first call on each device (per CUDA context) looks up the array's
+ * device address with cudaGetSymbolAddress, with that device current, and
+ * keeps it; that first call should come before any stream capture.  All
+ * calls share the one array and it keeps the previous call's contents:
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it.  Nothing in it needs clearing -- every slot a call reads is
+ * written earlier in the same call.
  * Calls no cudaMalloc, cudaFree or other allocating routine. */
 qs_status qs_expect_noalloc(const void *dev_state, int n, int batch, const qs_pauli *terms, size_t n_terms,
                             double *out, void *cuda_stream);
