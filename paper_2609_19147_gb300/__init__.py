@@ -353,32 +353,60 @@ def qaoa_maxcut(instances, stream=None) -> np.ndarray:
     return out
 
 
+_AUTOGRAD_FN = None
+_GRAD_STATES = {}   # (device index, n, batch) -> State kept between calls
+
+
+def _grad_state(device, n: int, batch: int) -> "State":
+    """The State that QSExpectation runs on: one per (device, n, batch), kept
+    so that repeated calls (a training loop) reuse its device memory and the
+    adjoint workspace that qs_grad keeps with it."""
+    import torch
+    idx = device.index if device.index is not None else torch.cuda.current_device()
+    key = (idx, int(n), int(batch))
+    st = _GRAD_STATES.get(key)
+    if st is None or st.h is None:
+        with torch.cuda.device(idx):
+            st = State(n, batch=batch)
+        _GRAD_STATES[key] = st
+    return st
+
+
 def _autograd():
+    global _AUTOGRAD_FN
+    if _AUTOGRAD_FN is not None:
+        return _AUTOGRAD_FN
     import torch
 
     class QSExpectation(torch.autograd.Function):
         """E_b(theta_b) = <psi(theta_b)|H|psi(theta_b)> for a batch of parameter
-        vectors; the backward pass uses the library's adjoint-method gradient."""
+        vectors; the backward pass uses the library's adjoint-method gradient
+        (computed in the same qs_grad call as the energies).  Energies and the
+        saved gradients live on the device of `params` (a CUDA device; CPU
+        params run on the current CUDA device and get CPU results).  The
+        angles go to the host once per call: the planner reduces them and
+        builds the phase tables in FP64 there."""
 
         @staticmethod
         def forward(ctx, params, n, gates, terms):
-            p = params.detach().cpu().numpy().astype(np.float64)
-            st = State(n, batch=p.shape[0])
-            try:
-                e, g = st.grad(gates, p, terms)
-            finally:
-                st.close()
-            ctx.save_for_backward(torch.from_numpy(g).to(params.dtype))
-            return torch.from_numpy(e).to(params.dtype)
+            dev = params.device if params.is_cuda else torch.device("cuda", torch.cuda.current_device())
+            p = params.detach().to("cpu", torch.float64).numpy().reshape(params.shape[0], -1)
+            st = _grad_state(dev, n, p.shape[0])
+            e, g = st.grad(gates, p, terms)
+            ctx.save_for_backward(torch.from_numpy(g).to(device=params.device, dtype=params.dtype))
+            return torch.from_numpy(e).to(device=params.device, dtype=params.dtype)
 
         @staticmethod
         def backward(ctx, gout):
             (g,) = ctx.saved_tensors
-            return gout.reshape(-1, 1).to(g.device) * g, None, None, None
+            return gout.reshape(-1, 1).to(g.device, g.dtype) * g, None, None, None
 
+    _AUTOGRAD_FN = QSExpectation
     return QSExpectation
 
 
 def qs_expectation(params, n: int, gates, terms):
-    """Differentiable batched energy: params (batch, P) torch tensor -> (batch,)."""
-    return _autograd().apply(params, n, gates, terms)
+    """Differentiable batched energy: params (batch, P) torch tensor -> (batch,),
+    on the device of `params`."""
+    cg = gates if isinstance(gates, CGates) else CGates(gates)
+    return _autograd().apply(params, n, cg, terms)

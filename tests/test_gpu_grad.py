@@ -107,3 +107,30 @@ def test_vqe_config_full_size_sampled():
     idx = [5, 2 * n * L - 2]
     ps = oracle.param_shift_grad(n, gl, theta[3], terms, indices=idx)
     assert np.max(np.abs(g[3][idx] - ps)) < 2e-5, (g[3][idx], ps)
+
+
+def test_autograd_function_against_param_shift_fd_and_chain_rule():
+    # qs_expectation (the torch.autograd.Function over qs_grad) driven through
+    # torch.autograd.grad at n = 10: energies against the oracle, gradients
+    # against oracle parameter shift and finite differences, and the chain rule
+    # with a non-unit upstream gradient; results stay on the CUDA device
+    n, L, B = 10, 3, 3
+    gl = W.vqe_ansatz_gates(n, L)
+    theta = W.vqe_params(n, L, B, 17)
+    terms = W.tfim_paulis(n, 1.0, 1.0)
+    p = torch.tensor(theta, dtype=torch.float64, device="cuda", requires_grad=True)
+    e = qs.qs_expectation(p, n, gl, terms)
+    assert e.is_cuda and e.shape == (B,)
+    w = torch.tensor([0.5, -2.0, 3.0], dtype=torch.float64, device="cuda")
+    (gp,) = torch.autograd.grad((w * e).sum(), p)
+    assert gp.is_cuda and gp.shape == p.shape
+    gp = gp.cpu().numpy()
+    for b in range(B):
+        assert abs(e[b].item() - oracle.energy(n, gl, theta[b], terms)) < 1e-5
+        ps = oracle.param_shift_grad(n, gl, theta[b], terms)
+        assert np.max(np.abs(gp[b] - w[b].item() * ps)) < 2e-5 * abs(w[b].item())
+    fd = oracle.finite_diff_grad(n, gl, theta[1], terms, indices=range(0, 2 * n * L, 5))
+    assert np.max(np.abs(gp[1][::5] / w[1].item() - fd)) < 2e-5
+    # a second call reuses the cached state and gives the same energies
+    e2 = qs.qs_expectation(p.detach(), n, gl, terms)
+    assert torch.allclose(e2, e.detach(), rtol=0, atol=1e-12)
