@@ -139,12 +139,14 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # oracle (CPU) timing: bounded samples of the same workload
 # ---------------------------------------------------------------------------
-def oracle_sample(n_qft_gates=40, n_tfim_gates=40):
+def oracle_sample(n_qft_gates=40, n_tfim_gates=40, threads=None, n=None):
     """Time the complex128 oracle on a bounded sample at full size and scale
     per gate to the whole step: the oracle applies every gate as one full
-    pass, so its cost is linear in the gate count."""
+    pass, so its cost is linear in the gate count.  `threads` limits the
+    OpenMP threads (None: all cores); `n` samples a smaller state and scales
+    by 2^(30 - n)."""
     import oracle
-    n = N_QUBITS
+    n = N_QUBITS if n is None else n
     avail = 0
     try:
         for ln in open("/proc/meminfo"):
@@ -162,18 +164,26 @@ def oracle_sample(n_qft_gates=40, n_tfim_gates=40):
     psi = np.zeros(1 << n, dtype=np.complex128)
     psi[0] = 1.0
     oracle.build()
-    t0 = time.perf_counter()
-    oracle.apply_gates(psi, n, qft[:n_qft_gates])
-    t_qft = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.apply_gates(psi, n, tfim[:n_tfim_gates])
-    t_tfim = time.perf_counter() - t0
+    all_cores = oracle.threads()
+    if threads:
+        oracle.set_threads(threads)
+    try:
+        cores = threads or all_cores
+        t0 = time.perf_counter()
+        oracle.apply_gates(psi, n, qft[:n_qft_gates])
+        t_qft = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.apply_gates(psi, n, tfim[:n_tfim_gates])
+        t_tfim = time.perf_counter() - t0
+    finally:
+        if threads:
+            oracle.set_threads(all_cores)
     qft_full = t_qft * len(qft) / n_qft_gates * scale_n
     tfim_full = t_tfim * len(tfim) / n_tfim_gates * scale_n
     sample = (f"first {n_qft_gates} of {len(qft)} QFT gates and first {n_tfim_gates} of {len(tfim)} TFIM gates "
-              f"at n={n}, complex128, time scaled by gate count" +
+              f"at n={n}, complex128, {cores} thread(s), time scaled by gate count" +
               (f" and x{scale_n:g} for n={N_QUBITS}" if scale_n != 1 else ""))
-    return {"s_per_step": qft_full + tfim_full, "qft_s": qft_full, "tfim_s": tfim_full, "cores": oracle.threads(),
+    return {"s_per_step": qft_full + tfim_full, "qft_s": qft_full, "tfim_s": tfim_full, "cores": cores,
             "sample": sample, "measured_s": t_qft + t_tfim}
 
 
@@ -186,7 +196,7 @@ def run_reference(args):
         oracle_sample(1, 1)
     last = None
     for _ in range(args.steps):
-        last = oracle_sample(8, 8)
+        last = oracle_sample(16, 16)
         vals.append(last["s_per_step"])
     v = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/step (QFT+TFIM 30q)",
@@ -194,7 +204,8 @@ def run_reference(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
             "data": "synthetic", "config": {"workload": WORKLOAD},
             "cpu_baseline": {"value": v, "unit": "s/step (QFT+TFIM 30q)", "cores": last["cores"], "kind": "oracle",
-                             "sample": last["sample"]},
+                             "sample": last["sample"] + f"; one sample per step, mean of {len(vals)}",
+                             "std_over_steps": float(np.std(vals)) if len(vals) > 1 else None},
             "e2e": {"value": v, "unit": "s/step (QFT+TFIM 30q)", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -534,6 +545,10 @@ def run_gpu(args):
         o = oracle_sample()
         cpu = {"value": o["s_per_step"], "unit": "s/step (QFT+TFIM 30q)", "cores": o["cores"], "kind": "oracle",
                "sample": o["sample"]}
+        # the same oracle on one core: 6 + 6 gates at 28 qubits, scaled x4
+        # (one core is compute bound, so its time is linear in 2^n)
+        o1 = oracle_sample(6, 6, threads=1, n=28)
+        cpu["one_core"] = {"value": o1["s_per_step"], "cores": 1, "sample": o1["sample"]}
     line = {
         "metric": METRIC, "value": value, "unit": "s/step (QFT+TFIM 30q)", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,

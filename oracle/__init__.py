@@ -62,12 +62,19 @@ def _load():
         lib.orc_vdot.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         lib.orc_max_threads.restype = ctypes.c_int
+        lib.orc_set_threads.restype = None
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
         _lib = lib
     return _lib
 
 
 def threads() -> int:
     return int(_load().orc_max_threads())
+
+
+def set_threads(t: int) -> None:
+    """Thread count of the C core's parallel loops (for timing)."""
+    _load().orc_set_threads(int(t))
 
 
 def zero_state(n: int) -> np.ndarray:

@@ -88,6 +88,19 @@ void orc_vdot(int64_t dim, const double complex *a, const double complex *b, dou
     *out_im = im;
 }
 
+/* Thread count of the parallel loops above (timing only; results do not
+ * depend on it beyond the order of the vdot reduction). */
+void orc_set_threads(int t)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (t > 0)
+        omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP
