@@ -2408,9 +2408,17 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
                 if (pbp->tp.n_sweeps >= kMaxSweeps - 1 || pbp->tp.n_micro >= kMaxMicro - 16) break;
             }
             pbp->finalize();
-            if (pbp->tp.n_const <= max_const || added <= 1) {
+            if (pbp->tp.n_const <= max_const) {
                 for (size_t k = 0; k < added; ++k) placed[taken[k]] = 1;
                 break;
+            }
+            if (added <= 1) {
+                // one op alone needs more constants than a pass holds: the
+                // kernel sizes its shared memory from them, so refuse here
+                err = "an op needs " + std::to_string(pbp->tp.n_const) + " pass constants, more than the " +
+                      std::to_string(max_const) + " a tile pass holds (op kind " + std::to_string(ops[taken[0]].kind) +
+                      ")";
+                return QS_ERR_UNSUPPORTED;
             }
             limit = added - std::max<size_t>(1, added / 8);
         }
