@@ -1,7 +1,7 @@
 // Tile-pass launcher: picks the kernel instantiation for the pass (register
 // group size R, threads, CTAs per SM, dense sweeps, op set); the
 // instantiations live in k_tile_r123.cu, k_tile_r4.cu, k_tile_r5.cu,
-// k_tile_layer4.cu, k_tile_layer5.cu and k_tile_dense.cu.
+// k_tile_layer4.cu, k_tile_layer5.cu, k_tile_dense.cu and k_tile_ws.cu.
 #include <cuda.h>
 
 #include <string>
@@ -22,6 +22,7 @@ QS_TILE_TU(r5)
 QS_TILE_TU(dense)
 QS_TILE_TU(layer4)
 QS_TILE_TU(layer5)
+QS_TILE_TU(ws)
 #undef QS_TILE_TU
 
 void tile_kernel_smem_config(int bytes) {
@@ -31,6 +32,7 @@ void tile_kernel_smem_config(int bytes) {
     tile_smem_config_dense(bytes);
     tile_smem_config_layer4(bytes);
     tile_smem_config_layer5(bytes);
+    tile_smem_config_ws(bytes);
 }
 
 // R = register group size; 4-bit groups on 13-bit tiles run 512 threads (16
@@ -40,6 +42,7 @@ cudaError_t launch_tile_pass(int R, const TileArgs &A, const void *tm_src, const
     const CUtensorMap &ms = *reinterpret_cast<const CUtensorMap *>(tm_src);
     const CUtensorMap &md = *reinterpret_cast<const CUtensorMap *>(tm_dst);
     cudaGetLastError();
+    if (A.ws) return launch_tile_ws(R, A, ms, md, grid, smem_bytes, st);
     if (A.dense) return launch_tile_dense(R, A, ms, md, grid, smem_bytes, st);
     if (A.kset == 1 && R == 4) return launch_tile_layer4(R, A, ms, md, grid, smem_bytes, st);
     if (A.kset == 1 && R == 5) return launch_tile_layer5(R, A, ms, md, grid, smem_bytes, st);
@@ -50,7 +53,8 @@ cudaError_t launch_tile_pass(int R, const TileArgs &A, const void *tm_src, const
 
 std::string tile_kernel_attrs(int R, const TileArgs &A) {
     cudaFuncAttributes fa;
-    cudaError_t e = A.dense                ? tile_attrs_dense(R, A, &fa)
+    cudaError_t e = A.ws                   ? tile_attrs_ws(R, A, &fa)
+                    : A.dense              ? tile_attrs_dense(R, A, &fa)
                     : A.kset == 1 && R == 4 ? tile_attrs_layer4(R, A, &fa)
                     : A.kset == 1 && R == 5 ? tile_attrs_layer5(R, A, &fa)
                     : R == 5 ? tile_attrs_r5(R, A, &fa)

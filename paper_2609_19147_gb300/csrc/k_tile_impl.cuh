@@ -429,6 +429,7 @@ struct SweepCtx {
     const int *tab_s;        // smem: per-sweep item-address tables (shared-memory offsets)
     const uint64_t *tab_g;   // smem: per-sweep item-address tables (global index bits)
     uint64_t tile_gbase;     // global index of tile-local 0 (within the state)
+    int lt;                  // thread index within the threads that share the sweeps
 };
 
 template <int R>
@@ -698,7 +699,7 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
     const float scale = S.scale;
     const int fast = KS == KS_LAYER ? straight_code<R>(c, op_begin, op_end, scale) : 0;
     const float2 *k0f = c.cs + c.micro[op_begin].cst;
-    for (int item = threadIdx.x; item < n_items; item += NT) {
+    for (int item = c.lt; item < n_items; item += NT) {
         const int i0 = item & 31, i1 = 32 + ((item >> 5) & 31), i2 = 64 + ((item >> 10) & 15);
         const int saddr = ts[i0] ^ ts[i1] ^ ts[i2];
         // global index of the item's group element 0 (only ops with controls,
@@ -821,7 +822,7 @@ __device__ __forceinline__ void dense_fp32(const SweepCtx &c, const Sweep &S, in
     const int ncols = 1 << (c.T - 5);
     const int *ts = c.tab_s + sidx * kItemTab;
     const float4 *U = reinterpret_cast<const float4 *>(c.cs + S.dcst);
-    for (int m = threadIdx.x; m < ncols; m += NT) {
+    for (int m = c.lt; m < ncols; m += NT) {
         const int co = dense_coloff(ts, m);
         float2 x[32];
 #pragma unroll
@@ -881,7 +882,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float2 v) {
 // FP64); the product keeps U_hi X_hi + U_hi X_lo + U_lo X_hi.
 template <int MT, int NT>
 __device__ __forceinline__ void dense_tf32x3(const SweepCtx &c, const Sweep &S, int sidx) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = c.lt & 31, warp = c.lt >> 5;
     const int q = lane & 3, gq = lane >> 2;
     const bool lane_im = (gq & 1) != 0;   // this lane's B column is an imaginary part
     const int rlo = ((q & 1) ? c.contrib[S.gbit[0]] : 0) ^ ((q & 2) ? c.contrib[S.gbit[1]] : 0);
@@ -966,7 +967,7 @@ __device__ __forceinline__ void dense_tf32x3(const SweepCtx &c, const Sweep &S, 
 // 8s..8s+7; U's operand registers come pre-packed from the host.
 template <int MT, int NT>
 __device__ __forceinline__ void dense_bf16(const SweepCtx &c, const Sweep &S, int sidx) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = c.lt & 31, warp = c.lt >> 5;
     const int q = lane & 3, gq = lane >> 2;
     const int rlo = ((q & 1) ? c.contrib[S.gbit[0]] : 0) ^ ((q & 2) ? c.contrib[S.gbit[1]] : 0);
     const int g2 = c.contrib[S.gbit[2]], g3 = c.contrib[S.gbit[3]], g4 = c.contrib[S.gbit[4]];
@@ -1063,34 +1064,59 @@ __device__ __forceinline__ void tile_coords(const TmaGeom &g, long long ti, long
     }
 }
 
-// DENSE: the pass has dense-block sweeps (a separate instantiation, so that
-// the register budget of the other passes does not grow with the dense code)
-template <int R, int NT, int MINB = 1, bool DENSE = false, int KS = KS_ALL>
-__global__ void __launch_bounds__(NT, MINB)
-    tile_pass_kernel(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst,
-                     const TileArgs A) {
-    extern __shared__ __align__(1024) unsigned char sm_raw[];
+// Shared-memory layout of a tile pass (base aligned to 1024 bytes for the
+// 128-byte swizzle):
+//   [0, 64)      full[8]   mbarriers: tile loaded into buffer b
+//   [64, 176)    hb[14], contrib[14]
+//   [176, 240)   empty[8]  mbarriers: consumers done with buffer b
+//   [240, 244)   abort flag
+//   off_desc     sweeps | micro-ops | diagonals | item tables (global bits, smem offsets)
+//   off_consts   constants (cs_copies consecutive copies of n_const entries,
+//                each copy 128-byte aligned)
+//   off_roots    QFT roots (when used)
+//   off_buf0     n_buf tile buffers of 8 * 2^T bytes
+struct TileShared {
+    uint64_t *full, *empty;
+    int *abort_flag;
+    int *s_hb, *s_contrib;
+    Sweep *s_sweeps;
+    MicroOp *s_micro;
+    DiagDesc *s_diags;
+    uint64_t *s_tab_g;
+    int *s_tab_s;
+    float2 *cs, *roots, *buf0;
+};
+
+__device__ __forceinline__ int const_copy_stride(int n_const) { return (n_const + 15) & ~15; }
+
+// Stage the pass descriptor, the constants (cs_copies copies of item 0's set)
+// and the roots in shared memory, initialise the mbarriers and build the
+// item-address tables.  Every thread of the CTA takes part; ends with a
+// barrier.
+template <int NT>
+__device__ __forceinline__ TileShared stage_tile_pass(const TileArgs &A, unsigned char *sm_raw, int cs_copies) {
+    TileShared S;
     // the 128-byte swizzle needs 1024-byte aligned tile buffers: align the base
     unsigned char *sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
-    uint64_t *full = reinterpret_cast<uint64_t *>(sm);          // [kMaxTileBuffers]
-    int *s_hb = reinterpret_cast<int *>(sm + 64);
-    int *s_contrib = s_hb + kMaxTileBits;
-    Sweep *s_sweeps = reinterpret_cast<Sweep *>(sm + A.off_desc);
+    S.full = reinterpret_cast<uint64_t *>(sm);
+    S.s_hb = reinterpret_cast<int *>(sm + 64);
+    S.s_contrib = S.s_hb + kMaxTileBits;
+    S.empty = reinterpret_cast<uint64_t *>(sm + 176);
+    S.abort_flag = reinterpret_cast<int *>(sm + 240);
+    S.s_sweeps = reinterpret_cast<Sweep *>(sm + A.off_desc);
     const TilePass &P = *A.pass;
     const int n_sweeps = P.n_sweeps, n_micro = P.n_micro;
-    MicroOp *s_micro = reinterpret_cast<MicroOp *>(s_sweeps + n_sweeps);
-    DiagDesc *s_diags = reinterpret_cast<DiagDesc *>(s_micro + n_micro);
-    uint64_t *s_tab_g = reinterpret_cast<uint64_t *>(s_diags + kMaxDiag);
-    int *s_tab_s = reinterpret_cast<int *>(s_tab_g + n_sweeps * kItemTab);
-    float2 *cs = reinterpret_cast<float2 *>(sm + A.off_consts);
-    float2 *roots = reinterpret_cast<float2 *>(sm + A.off_roots);
-    float2 *buf0 = reinterpret_cast<float2 *>(sm + A.off_buf0);
-    const int NB = A.n_buf;
+    S.s_micro = reinterpret_cast<MicroOp *>(S.s_sweeps + n_sweeps);
+    S.s_diags = reinterpret_cast<DiagDesc *>(S.s_micro + n_micro);
+    S.s_tab_g = reinterpret_cast<uint64_t *>(S.s_diags + kMaxDiag);
+    S.s_tab_s = reinterpret_cast<int *>(S.s_tab_g + n_sweeps * kItemTab);
+    S.cs = reinterpret_cast<float2 *>(sm + A.off_consts);
+    S.roots = reinterpret_cast<float2 *>(sm + A.off_roots);
+    S.buf0 = reinterpret_cast<float2 *>(sm + A.off_buf0);
     const int tid = threadIdx.x;
-    const int L = P.L, H = P.H, T = P.T;
-    const int tile_elems = 1 << T;
-    const uint32_t tile_bytes = 8u << T;
-    const long long total = A.n_tiles * (long long)A.batch;
+    const int L = P.L, T = P.T;
+    Sweep *s_sweeps = S.s_sweeps;
+    int *s_hb = S.s_hb, *s_contrib = S.s_contrib;
 
     // stage the pass descriptor and constants in shared memory
     {
@@ -1099,23 +1125,29 @@ __global__ void __launch_bounds__(NT, MINB)
         const int nw_s = n_sweeps * (int)(sizeof(Sweep) / 4);
         for (int i = tid; i < nw_s; i += NT) dst[i] = src[i];
         src = reinterpret_cast<const int *>(P.micro);
-        dst = reinterpret_cast<int *>(s_micro);
+        dst = reinterpret_cast<int *>(S.s_micro);
         const int nw_m = n_micro * (int)(sizeof(MicroOp) / 4);
         for (int i = tid; i < nw_m; i += NT) dst[i] = src[i];
         src = reinterpret_cast<const int *>(P.diags);
-        dst = reinterpret_cast<int *>(s_diags);
+        dst = reinterpret_cast<int *>(S.s_diags);
         const int nw_d = kMaxDiag * (int)(sizeof(DiagDesc) / 4);
         for (int i = tid; i < nw_d; i += NT) dst[i] = src[i];
     }
-    for (int i = tid; i < P.n_const; i += NT) cs[i] = A.consts[i];
+    for (int i = tid; i < P.n_const; i += NT) S.cs[i] = A.consts[i];
+    for (int cpy = 1; cpy < cs_copies; ++cpy)
+        for (int i = tid; i < P.n_const; i += NT) S.cs[cpy * const_copy_stride(P.n_const) + i] = A.consts[i];
     if (A.off_roots)
-        for (int i = tid; i < kRootsEntries; i += NT) roots[i] = A.roots[i];
+        for (int i = tid; i < kRootsEntries; i += NT) S.roots[i] = A.roots[i];
     if (tid < kMaxTileBits) {
         s_hb[tid] = P.hb[tid];
         s_contrib[tid] = P.smem_contrib[tid];
     }
     if (tid == 0) {
-        for (int b = 0; b < kMaxTileBuffers; ++b) mbar_init(&full[b], 1);
+        for (int b = 0; b < kMaxTileBuffers; ++b) {
+            mbar_init(&S.full[b], 1);
+            mbar_init(&S.empty[b], 1);
+        }
+        *S.abort_flag = 0;
         fence_mbar_init();
     }
     __syncthreads();
@@ -1127,8 +1159,8 @@ __global__ void __launch_bounds__(NT, MINB)
             // the sweep's group bits
             const int m = idx - (kItemTab - kGroupTab);
             const int tb = m < s_sweeps[sw].r ? s_sweeps[sw].gbit[m] : -1;
-            s_tab_s[e] = tb < 0 ? 0 : s_contrib[tb];
-            s_tab_g[e] = tb < 0 ? 0ull : (tb < L ? (1ull << tb) : (1ull << s_hb[tb - L]));
+            S.s_tab_s[e] = tb < 0 ? 0 : s_contrib[tb];
+            S.s_tab_g[e] = tb < 0 ? 0ull : (tb < L ? (1ull << tb) : (1ull << s_hb[tb - L]));
             continue;
         }
         const int part = idx < 32 ? 0 : (idx < 64 ? 1 : 2);
@@ -1144,11 +1176,36 @@ __global__ void __launch_bounds__(NT, MINB)
                 go |= tb < L ? (1ull << tb) : (1ull << s_hb[tb - L]);
             }
         }
-        s_tab_s[e] = so;
-        s_tab_g[e] = go;
+        S.s_tab_s[e] = so;
+        S.s_tab_g[e] = go;
     }
     fence_proxy_async();
     __syncthreads();
+    return S;
+}
+
+// DENSE: the pass has dense-block sweeps (a separate instantiation, so that
+// the register budget of the other passes does not grow with the dense code)
+template <int R, int NT, int MINB = 1, bool DENSE = false, int KS = KS_ALL>
+__global__ void __launch_bounds__(NT, MINB)
+    tile_pass_kernel(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst,
+                     const TileArgs A) {
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    const TileShared S = stage_tile_pass<NT>(A, sm_raw, 1);
+    uint64_t *full = S.full;
+    const int *s_hb = S.s_hb;
+    const int *s_contrib = S.s_contrib;
+    const Sweep *s_sweeps = S.s_sweeps;
+    float2 *cs = S.cs;
+    float2 *buf0 = S.buf0;
+    const TilePass &P = *A.pass;
+    const int n_sweeps = P.n_sweeps;
+    const int NB = A.n_buf;
+    const int tid = threadIdx.x;
+    const int L = P.L, H = P.H, T = P.T;
+    const int tile_elems = 1 << T;
+    const uint32_t tile_bytes = 8u << T;
+    const long long total = A.n_tiles * (long long)A.batch;
     if ((long long)blockIdx.x >= total) return;
     const long long stride = gridDim.x;
     const int n_mine = (int)((total - 1 - blockIdx.x) / stride + 1);   // tiles of this CTA
@@ -1203,16 +1260,17 @@ __global__ void __launch_bounds__(NT, MINB)
         for (int k = 0; k < D && k < n_mine; ++k) load(k);
 
     SweepCtx c;
+    c.lt = tid;
     c.T = T;
     c.L = L;
     c.contrib = s_contrib;
     c.hb = s_hb;
     c.cs = cs;
-    c.roots = roots;
-    c.micro = s_micro;
-    c.diags = s_diags;
-    c.tab_s = s_tab_s;
-    c.tab_g = s_tab_g;
+    c.roots = S.roots;
+    c.micro = S.s_micro;
+    c.diags = S.s_diags;
+    c.tab_s = S.s_tab_s;
+    c.tab_g = S.s_tab_g;
     long long cur_item = 0;   // constants of item 0 are staged above
     for (int k = 0; k < n_mine; ++k) {
         if (tid == 0 && k + D < n_mine) {
@@ -1262,6 +1320,185 @@ __global__ void __launch_bounds__(NT, MINB)
         if (tid == 0) store(k);
     }
     if (tid == 0) bulk_wait_all0();
+}
+
+// ---------------------------------------------------------------------------
+// Warp-specialised tile pass: one CTA per SM, NB (>= 3) tile buffers, a
+// producer warpgroup and two consumer groups of NTG threads.
+//
+// The producer's lane 0 walks this CTA's tiles in order: it loads tile j into
+// buffer j % NB as soon as the consumers of tile j - NB are done with that
+// buffer and its store has read it out.  Consumer group g takes the tiles
+// k = g, g + 2, ... : it waits for the tile's load, runs the sweeps with a
+// named barrier of its own between them, and signals the buffer's empty
+// barrier.  The two groups work on different tiles at different phases of
+// their sweeps (the shared-memory, FP32 and TMA work of the SM overlap
+// instead of lining up behind one barrier), and the load of a group's next
+// tile is issued while the other group still computes, so neither group waits
+// for a load issued after its own previous tile.
+//
+// Every wait is bounded (2 s): a waiter that gives up records QS_ERR_TIMEOUT,
+// raises the CTA's abort flag (which ends the other waits) and returns; the
+// producer lets the copies it issued land before it returns.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool mbar_wait_abortable(uint64_t *bar, uint32_t parity, const volatile int *abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 255 && (*abort_flag || globaltimer() - t0 > 2000000000ull)) return false;
+    }
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// barrier among the `count` threads that use named barrier `id`
+__device__ __forceinline__ void named_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+// the same barrier, returning whether any of them passed p = true
+__device__ __forceinline__ bool named_sync_or(int id, int count, bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\t"
+        "setp.ne.u32 pi, %1, 0;\n\t"
+        "bar.red.or.pred po, %2, %3, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+
+// Register split: the CTA launches 2 NTG + 128 threads at kWsLaunchRegs
+// registers each; the producer warpgroup (only its first thread works) drops
+// to kWsProducerRegs and the consumers rise to kWsConsumerRegs.  With
+// NTG = 256: 640 x 96 = 61,440 registers at launch >= 128 x 24 + 512 x 112 =
+// 60,416 after the split (per SM sub-partition: 4 x 32 x 112 + 32 x 24 =
+// 15,104 <= 16,384).
+constexpr int kWsProducerRegs = 24;
+constexpr int kWsConsumerRegs = 112;
+
+template <int R, int NTG, bool DENSE = false, int KS = KS_ALL>
+__global__ void __launch_bounds__(2 * NTG + 128, 1)
+    tile_pass_ws_kernel(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst,
+                        const TileArgs A) {
+    constexpr int NT = 2 * NTG + 128;
+    static_assert(NTG == 256, "the register split below is sized for two 256-thread groups");
+    extern __shared__ __align__(1024) unsigned char sm_raw[];
+    const int per_item = A.const_stride != 0;
+    const TileShared S = stage_tile_pass<NT>(A, sm_raw, per_item ? 2 : 1);
+    const TilePass &P = *A.pass;
+    const int n_sweeps = P.n_sweeps;
+    const int NB = A.n_buf;
+    const int tid = threadIdx.x;
+    const int T = P.T;
+    const int tile_elems = 1 << T;
+    const uint32_t tile_bytes = 8u << T;
+    const long long total = A.n_tiles * (long long)A.batch;
+    if ((long long)blockIdx.x >= total) return;
+    const long long stride = gridDim.x;
+    const int n_mine = (int)((total - 1 - blockIdx.x) / stride + 1);   // tiles of this CTA
+    volatile int *abort_flag = S.abort_flag;
+
+    if (tid >= 2 * NTG) {
+        // producer warpgroup: its first thread issues every copy (one tensor
+        // copy per tile)
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kWsProducerRegs));
+        if (tid != 2 * NTG) return;
+        auto coords = [&](int k, int c[5]) {
+            const long long t = blockIdx.x + (long long)k * stride;
+            const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
+            tile_coords(A.geo, ti, bi, c);
+        };
+        int loaded = 0;
+        bool ok = true;
+        for (int j = 0; j < n_mine + NB; ++j) {
+            const int b = j % NB;
+            if (j >= NB) {
+                // tile j - NB: its consumers are done; store it from buffer b
+                if (!mbar_wait_abortable(&S.empty[b], (uint32_t)(((j - NB) / NB) & 1), abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                int c[5];
+                coords(j - NB, c);
+                tma_store_5d(&tm_dst, c, S.buf0 + (size_t)b * tile_elems);
+                bulk_commit();
+                if (j >= n_mine) continue;
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            }
+            if (j < n_mine) {
+                int c[5];
+                coords(j, c);
+                mbar_arrive_expect_tx(&S.full[b], tile_bytes);
+                tma_load_5d(S.buf0 + (size_t)b * tile_elems, &tm_src, c, &S.full[b]);
+                loaded = j + 1;
+            }
+        }
+        if (!ok) {
+            atomicCAS(A.err, 0, (int)QS_ERR_TIMEOUT);
+            *abort_flag = 1;
+            // let the last load of every buffer land before the CTA leaves
+            for (int j = loaded - NB < 0 ? 0 : loaded - NB; j < loaded; ++j)
+                mbar_wait_bounded(&S.full[j % NB], (uint32_t)((j / NB) & 1));
+        }
+        bulk_wait_all0();
+        return;
+    }
+
+    // consumer group g
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsConsumerRegs));
+    const int g = tid / NTG;
+    const int bar_id = 1 + g;
+    float2 *cs = S.cs + (per_item ? g * const_copy_stride(P.n_const) : 0);
+    SweepCtx c;
+    c.lt = tid - g * NTG;
+    c.T = T;
+    c.L = P.L;
+    c.contrib = S.s_contrib;
+    c.hb = S.s_hb;
+    c.cs = cs;
+    c.roots = S.roots;
+    c.micro = S.s_micro;
+    c.diags = S.s_diags;
+    c.tab_s = S.s_tab_s;
+    c.tab_g = S.s_tab_g;
+    long long cur_item = 0;   // constants of item 0 are staged above
+    for (int k = g; k < n_mine; k += 2) {
+        const int b = k % NB;
+        const bool ok = mbar_wait_abortable(&S.full[b], (uint32_t)((k / NB) & 1), abort_flag);
+        if (named_sync_or(bar_id, NTG, !ok)) {
+            if (c.lt == 0) {
+                atomicCAS(A.err, 0, (int)QS_ERR_TIMEOUT);
+                *abort_flag = 1;
+            }
+            return;
+        }
+        const long long t = blockIdx.x + (long long)k * stride;
+        const long long ti = t % A.n_tiles;
+        if (per_item) {
+            // per-item constants: this group's copy is restaged when its tile
+            // starts another item (its previous tile ended at a group barrier)
+            const long long item = (t / A.n_tiles) / A.const_group;
+            if (item != cur_item) {
+                const float2 *src = A.consts + item * A.const_stride;
+                for (int i = c.lt; i < P.n_const; i += NTG) cs[i] = src[i];
+                named_sync(bar_id, NTG);
+                cur_item = item;
+            }
+        }
+        c.buf = S.buf0 + (size_t)b * tile_elems;
+        c.tile_gbase = A.needs_gidx ? tile_base(A, ti) : 0;
+        for (int s = 0; s < n_sweeps; ++s) {
+            if (DENSE && S.s_sweeps[s].dense) run_dense<NTG>(c, S.s_sweeps[s], s);
+            else run_sweep<R, NTG, KS>(c, S.s_sweeps[s], s);
+            if (s + 1 < n_sweeps) named_sync(bar_id, NTG);
+        }
+        fence_proxy_async();   // generic-proxy writes before the async-proxy store
+        named_sync(bar_id, NTG);
+        if (c.lt == 0) mbar_arrive(&S.empty[b]);
+    }
 }
 
 }  // namespace qs

@@ -417,23 +417,6 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     for (int b = 0; b < st->n; ++b)
         if (!((tilebits >> b) & 1)) A.outer_pos[A.n_outer++] = b;
     A.err = st->d_err;
-    // shared memory (after aligning the base to 1024 bytes in the kernel):
-    // [mbarriers, flags, hb, contrib | descriptor | constants | roots | 2-3 tile buffers]
-    auto al = [](int v, int a) { return (v + a - 1) / a * a; };
-    int off = 256;
-    A.off_desc = off;
-    off += tp.n_sweeps * (int)sizeof(Sweep) + tp.n_micro * (int)sizeof(MicroOp) + kMaxDiag * (int)sizeof(DiagDesc);
-    off += tp.n_sweeps * kItemTab * (8 + 4);   // item-address tables
-    off = al(off, 128);
-    A.off_consts = off;
-    off = al(off + tp.n_const * 8, 128);   // one item's constants
-    if (hp.uses_roots) {
-        A.off_roots = off;
-        off += kRootsEntries * 8;
-    }
-    const int buf_bytes = 8 << tp.T;
-    off = al(off, 1024);
-    A.off_buf0 = off;
     for (int k = 0; k < tp.n_sweeps; ++k)
         if (tp.sweeps[k].dense) A.dense = 1;
     A.kset = 1;
@@ -446,6 +429,47 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
               mo.kind == MK_DIAG || mo.kind == MK_DIAGQ || mo.kind == MK_DIAGC))
             A.kset = 0;
     }
+    // shared memory (after aligning the base to 1024 bytes in the kernel):
+    // [mbarriers, flags, hb, contrib | descriptor | constants | roots | tile buffers]
+    auto al = [](int v, int a) { return (v + a - 1) / a * a; };
+    const int buf_bytes = 8 << tp.T;
+    auto layout = [&](int const_copies) {
+        int off = 256;
+        A.off_desc = off;
+        off += tp.n_sweeps * (int)sizeof(Sweep) + tp.n_micro * (int)sizeof(MicroOp) +
+               kMaxDiag * (int)sizeof(DiagDesc);
+        off += tp.n_sweeps * kItemTab * (8 + 4);   // item-address tables
+        off = al(off, 128);
+        A.off_consts = off;
+        // one item's constants (per copy, 16-entry aligned as the kernel indexes them)
+        off = al(off + const_copies * al(tp.n_const, 16) * 8, 128);
+        A.off_roots = 0;
+        if (hp.uses_roots) {
+            A.off_roots = off;
+            off += kRootsEntries * 8;
+        }
+        off = al(off, 1024);
+        A.off_buf0 = off;
+        return off;
+    };
+    // Warp-specialised kernel (one CTA per SM, a producer warpgroup and two
+    // consumer groups over three or more tile buffers) for 13-bit tiles with
+    // 4-bit groups on the tensor-copy path, when three buffers fit.
+    static int ws_env = -2;
+    if (ws_env == -2) {
+        const char *e = getenv("QS_TILE_WS");
+        ws_env = e ? atoi(e) : -1;
+    }
+    const int ws_limit = 227 * 1024 - 1024;
+    const int ws_copies = dp.host.items > 1 ? 2 : 1;
+    if (ws_env != 0 && hp.tma.ok && tp.T == 13 && tp.R == 4 && !A.dense &&
+        layout(ws_copies) + 3 * buf_bytes <= ws_limit) {
+        A.ws = 1;
+        A.ctas_per_sm = 1;
+        A.n_buf = std::min(kMaxTileBuffers, std::min(4, (ws_limit - A.off_buf0) / buf_bytes));
+        A.prefetch = 0;
+    }
+    int off = A.ws ? A.off_buf0 : layout(1);
     // Two co-resident CTAs per SM for 4-bit groups on 12- and 13-bit tiles,
     // and for 5-bit groups of layer/diagonal passes on 13-bit tiles (128
     // threads each, whose 255 registers just fill the register file twice):
@@ -456,18 +480,21 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     // (64 KB) leaves room for one buffer per CTA, loaded after the previous
     // tile's store has left it (no prefetch inside the CTA).  One CTA with
     // up to 6 buffers when two do not fit.
-    int cps = ((tp.R == 4 && (tp.T == 12 || tp.T == 13)) || (tp.R == 5 && tp.T == 13 && A.kset && !A.dense)) ? 2 : 1;
-    int limit = (cps == 2 ? 113 * 1024 : 227 * 1024) - 1024;   // 1 KB for the base alignment
-    int nb = std::min(cps == 2 ? 3 : 6, (limit - off) / buf_bytes);
-    if (cps == 2 && nb < 1) {
-        cps = 1;
-        limit = 227 * 1024 - 1024;
-        nb = std::min(6, (limit - off) / buf_bytes);
+    int limit = 227 * 1024 - 1024;
+    if (!A.ws) {
+        int cps = ((tp.R == 4 && (tp.T == 12 || tp.T == 13)) || (tp.R == 5 && tp.T == 13 && A.kset && !A.dense)) ? 2 : 1;
+        limit = (cps == 2 ? 113 * 1024 : 227 * 1024) - 1024;   // 1 KB for the base alignment
+        int nb = std::min(cps == 2 ? 3 : 6, (limit - off) / buf_bytes);
+        if (cps == 2 && nb < 1) {
+            cps = 1;
+            limit = 227 * 1024 - 1024;
+            nb = std::min(6, (limit - off) / buf_bytes);
+        }
+        A.ctas_per_sm = cps;
+        A.n_buf = std::min(nb, kMaxTileBuffers);
+        if (A.n_buf < (cps == 2 ? 1 : 2)) return fail(QS_ERR_INTERNAL, "tile pass needs too much shared memory");
+        A.prefetch = A.n_buf == 1 ? 0 : std::max(1, A.n_buf - 2);
     }
-    A.ctas_per_sm = cps;
-    A.n_buf = std::min(nb, kMaxTileBuffers);
-    if (A.n_buf < (cps == 2 ? 1 : 2)) return fail(QS_ERR_INTERNAL, "tile pass needs too much shared memory");
-    A.prefetch = A.n_buf == 1 ? 0 : std::max(1, A.n_buf - 2);
     off += A.n_buf * buf_bytes;
     if (off > limit) return fail(QS_ERR_INTERNAL, "tile pass needs too much shared memory");
     off += 1024;
@@ -494,6 +521,7 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
         if (s != QS_OK) return s;
     }
     A.threads = (tp.R == 4 && tp.T >= 13 && A.ctas_per_sm == 1) ? 512 : (tp.R == 5 && A.ctas_per_sm == 2) ? 128 : 256;
+    if (A.ws) A.threads = 2 * 256 + 128;
     if (A.dense && (tp.R != 5 || A.ctas_per_sm != 1)) return fail(QS_ERR_INTERNAL, "dense pass without 5-bit groups");
     if (A.dense) A.threads = 256;
     {

@@ -42,6 +42,7 @@ struct TileArgs {
     int const_group;           //   consts + (batch index / const_group) * const_stride
     int kset;                  // 1: every micro-op is a 1q / layer / diagonal op (KS_LAYER kernels)
     int needs_gidx;            // 1: some micro-op reads global indices (controls, diagonals, QFT)
+    int ws;                    // 1: warp-specialised kernel (a producer warp and two consumer groups)
     TmaGeom geo;
     int *err;                  // device status word
 };
