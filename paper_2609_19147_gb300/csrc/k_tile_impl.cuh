@@ -229,6 +229,22 @@ __device__ __forceinline__ void op_u1r(float2 (&a)[1 << R], const float2 *cs) {
     }
 }
 
+// real rotation c [[1, t], [-t, 1]] without its factor c (folded into the
+// sweep scale): one packed FMA per amplitude, (t, t) and (-t, -t) stored as
+// the FP32x2 operands
+template <int R, int M>
+__device__ __forceinline__ void op_rot(float2 (&a)[1 << R], const float2 *cs) {
+    const float2 t = cs[0], nt = cs[1];
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) {
+        if ((j >> M) & 1) continue;
+        const int k = j | (1 << M);
+        const float2 a0 = a[j], a1 = a[k];
+        a[j] = __ffma2_rn(t, a1, a0);
+        a[k] = __ffma2_rn(nt, a0, a1);
+    }
+}
+
 // unnormalised Hadamard butterfly (the 1/sqrt 2 is folded into the sweep
 // scale): one packed add and one packed a0 - a1 (an exact FMA with -1)
 template <int R, int M>
@@ -302,6 +318,13 @@ __device__ __forceinline__ void disp_u1r(int m, float2 (&a)[1 << R], const float
     }
 }
 template <int R, int M = 0>
+__device__ __forceinline__ void disp_rot(int m, float2 (&a)[1 << R], const float2 *cs) {
+    if constexpr (M < R) {
+        if (m == M) op_rot<R, M>(a, cs);
+        else disp_rot<R, M + 1>(m, a, cs);
+    }
+}
+template <int R, int M = 0>
 __device__ __forceinline__ void disp_h(int m, float2 (&a)[1 << R]) {
     if constexpr (M < R) {
         if (m == M) op_h<R, M>(a);
@@ -338,7 +361,7 @@ __device__ __forceinline__ void disp_u2(int ma, int mb, float2 (&a)[1 << R], con
 }
 
 // layers: the same 2x2 family on every group bit in `mask`; the coefficients
-// of group bit M sit at k0 + stride * M (RXC 1, U1R 4, U1 4, H none)
+// of group bit M sit at k0 + stride * M (RXC 1, U1R 4, U1 4, ROT 2, H none)
 template <int KIND>
 struct LayerOp;
 template <>
@@ -360,6 +383,13 @@ struct LayerOp<MK_U1> {
     template <int R, int M>
     static __device__ __forceinline__ void run(float2 (&a)[1 << R], const float2 *k0, const Grp<R> &G) {
         op_u1<R, M>(a, k0 + 4 * M, 0ull, 0ull, 0ull, G);
+    }
+};
+template <>
+struct LayerOp<MK_ROT> {
+    template <int R, int M>
+    static __device__ __forceinline__ void run(float2 (&a)[1 << R], const float2 *k0, const Grp<R> &) {
+        op_rot<R, M>(a, k0 + 2 * M);
     }
 };
 template <>
@@ -395,6 +425,7 @@ __device__ __forceinline__ void run_layer(int kind, float2 (&a)[1 << R], const f
         case MK_RXC: layer_bits<MK_RXC, R>(a, k0, mask, G); break;
         case MK_U1R: layer_bits<MK_U1R, R>(a, k0, mask, G); break;
         case MK_U1: layer_bits<MK_U1, R>(a, k0, mask, G); break;
+        case MK_ROT: layer_bits<MK_ROT, R>(a, k0, mask, G); break;
         default: layer_bits<MK_H, R>(a, k0, mask, G); break;
     }
 }
@@ -654,7 +685,7 @@ constexpr int KS_LAYER = 1;
 // but group bit 0, the pair bit of 16-byte accesses) runs as straight-line
 // code from load to store: with no control-flow merge between the bits and
 // the store, the amplitudes are not moved back into fixed registers after
-// each bit.  Code 1 + 2 * (U1, H, RXC, U1R) + (all but bit 0); 0: the
+// each bit.  Code 1 + 2 * (U1, H, RXC, U1R, ROT) + (all but bit 0); 0: the
 // general path.  (Sweeps that pair the layer with a diagonal keep the general
 // path: the second inlined copy of the diagonal code cost more than the
 // merges it saved.)
@@ -662,10 +693,10 @@ template <int R>
 __device__ __forceinline__ int straight_code(const SweepCtx &c, int op_begin, int op_end, float scale) {
     if ((R != 4 && R != 5) || op_end - op_begin != 1) return 0;
     const MicroOp &o = c.micro[op_begin];
-    if (o.kind != MK_LAYER || (o.a != MK_H && scale != 1.f)) return 0;
+    if (o.kind != MK_LAYER || (o.a != MK_H && o.a != MK_ROT && scale != 1.f)) return 0;
     const uint32_t full = (1u << R) - 1, mask = (uint32_t)o.b;
     if (mask != full && mask != (full & ~1u)) return 0;
-    const int ki = o.a == MK_U1 ? 0 : o.a == MK_H ? 1 : o.a == MK_RXC ? 2 : 3;
+    const int ki = o.a == MK_U1 ? 0 : o.a == MK_H ? 1 : o.a == MK_RXC ? 2 : o.a == MK_U1R ? 3 : 4;
     return 1 + 2 * ki + (mask == full ? 0 : 1);
 }
 
@@ -673,7 +704,7 @@ template <int KIND, int R, uint32_t MASK>
 __device__ __forceinline__ void layer_store(const SweepCtx &c, bool vec, const int (&o)[1 << R],
                                             float2 (&a)[1 << R], const float2 *k0, const Grp<R> &G, float scale) {
     layer_fixed<KIND, R, MASK>(a, k0, G);
-    if constexpr (KIND == MK_H) {
+    if constexpr (KIND == MK_H || KIND == MK_ROT) {
         const float2 sc = make_float2(scale, scale);
 #pragma unroll
         for (int j = 0; j < (1 << R); ++j) a[j] = __fmul2_rn(a[j], sc);
@@ -681,8 +712,153 @@ __device__ __forceinline__ void layer_store(const SweepCtx &c, bool vec, const i
     store_at<R>(c, vec, o, a);
 }
 
+// ---------------------------------------------------------------------------
+// Rotation sweep programs (1q-layer / diagonal passes): a sweep whose
+// micro-ops are one of
+//   1: ROT layer                 2: DIAGC, ROT layer
+//   3: ROT layer, DIAGC          4: ROT layer, DIAGC, ROT layer
+// with every ROT layer on all R group bits (the planner pads missing bits with
+// t = 0, an exact identity) runs a loop specialised for that program: the
+// layers' tangents and the diagonal's per-sweep data sit in registers for the
+// whole sweep, and no per-item dispatch remains.
+// ---------------------------------------------------------------------------
+template <int R>
+__device__ __forceinline__ int rot_program(const SweepCtx &c, int op_begin, int op_end) {
+    constexpr int F = (1 << R) - 1;
+    auto rot = [&](int i) { return c.micro[i].kind == MK_LAYER && c.micro[i].a == MK_ROT && c.micro[i].b == F; };
+    auto dgc = [&](int i) { return c.micro[i].kind == MK_DIAGC; };
+    const int n = op_end - op_begin, b = op_begin;
+    if (n == 1 && rot(b)) return 1;
+    if (n == 2 && dgc(b) && rot(b + 1)) return 2;
+    if (n == 2 && rot(b) && dgc(b + 1)) return 3;
+    if (n == 3 && rot(b) && dgc(b + 1) && rot(b + 2)) return 4;
+    return 0;
+}
+
+// the count-table diagonal of one sweep with its per-sweep data in registers
+template <int R>
+struct DiagcRegs {
+    const float2 *lut;
+    const uint64_t *cls;   // per distance class: mask, distance
+    uint64_t nbr[R], degs, mz, zinc, q_lo, q_hi;
+    int n_cls, stride;
+    bool cz;
+    __device__ __forceinline__ void init(const SweepCtx &c, const MicroOp &op) {
+        lut = c.cs + op.cst;
+        const uint64_t *dat = reinterpret_cast<const uint64_t *>(c.cs + op.lo);
+#pragma unroll
+        for (int m = 0; m < R; ++m) nbr[m] = dat[m];
+        degs = dat[R];
+        mz = dat[R + 1];
+        zinc = dat[R + 2];
+        cls = dat + R + 3;
+        n_cls = op.a;
+        stride = op.p;
+        cz = op.b != 0;
+        q_lo = op.cmask;
+        q_hi = op.cval;
+    }
+    __device__ __forceinline__ void apply(uint64_t x0, float2 (&a)[1 << R]) const {
+        int c0 = stride * __popcll(x0 & mz);
+        for (int k = 0; k < n_cls; ++k) {
+            const uint64_t f = cz ? (x0 & (x0 >> (int)cls[2 * k + 1])) : (x0 ^ (x0 >> (int)cls[2 * k + 1]));
+            c0 += __popcll(f & cls[2 * k]);
+        }
+        int cnt[1 << R];
+        cnt[0] = c0;
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            const int s = __popcll(x0 & nbr[m]);
+            const int dm = (cz ? s : (int)((degs >> (6 * m)) & 63) - 2 * s) + (int)((zinc >> (12 * m)) & 4095);
+#pragma unroll
+            for (int j = 0; j < (1 << m); ++j) cnt[j | (1 << m)] = cnt[j] + dm;
+        }
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j) {
+            const int q = (int)(((j < 16 ? q_lo : q_hi) >> (4 * (j & 15))) & 15);
+            a[j] = cmul(a[j], lut[cnt[j] + q]);
+        }
+    }
+};
+
+// a ROT layer on all R group bits with the tangents in registers
+template <int R, int M = 0>
+__device__ __forceinline__ void rot_layer_regs(float2 (&a)[1 << R], const float2 (&t)[R]) {
+    if constexpr (M < R) {
+        const float2 tp = t[M], tn = make_float2(-t[M].x, -t[M].y);
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j) {
+            if ((j >> M) & 1) continue;
+            const int k = j | (1 << M);
+            const float2 a0 = a[j], a1 = a[k];
+            a[j] = __ffma2_rn(tp, a1, a0);
+            a[k] = __ffma2_rn(tn, a0, a1);
+        }
+        rot_layer_regs<R, M + 1>(a, t);
+    }
+}
+
+template <int R, int NT, int PROG, bool VEC>
+__device__ __forceinline__ void rot_sweep(const SweepCtx &c, const Sweep &S, int sidx) {
+    const int *ts = c.tab_s + sidx * kItemTab;
+    const uint64_t *tg = c.tab_g + sidx * kItemTab;
+    int gs[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) gs[m] = ts[kItemTab - kGroupTab + m];
+    const int b = S.op_begin;
+    const int i_l1 = PROG == 2 ? b + 1 : b;
+    float2 t1[R], t2[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) t1[m] = c.cs[c.micro[i_l1].cst + 2 * m];
+    if constexpr (PROG == 4) {
+#pragma unroll
+        for (int m = 0; m < R; ++m) t2[m] = c.cs[c.micro[b + 2].cst + 2 * m];
+    }
+    DiagcRegs<R> dg;
+    if constexpr (PROG >= 2) dg.init(c, c.micro[PROG == 2 ? b : b + 1]);
+    const float2 sc = make_float2(S.scale, S.scale);
+    const int n_items = 1 << (c.T - R);
+    for (int item = c.lt; item < n_items; item += NT) {
+        const int i0 = item & 31, i1 = 32 + ((item >> 5) & 31), i2 = 64 + ((item >> 10) & 15);
+        int o[1 << R];
+        group_offsets<R>(ts[i0] ^ ts[i1] ^ ts[i2], gs, o);
+        float2 a[1 << R];
+        load_at<R>(c, VEC, o, a);
+        uint64_t x0 = 0;
+        if constexpr (PROG >= 2) x0 = c.tile_gbase | tg[i0] | tg[i1] | tg[i2];
+        if constexpr (PROG == 2) dg.apply(x0, a);
+        rot_layer_regs<R>(a, t1);
+        if constexpr (PROG == 3 || PROG == 4) dg.apply(x0, a);
+        if constexpr (PROG == 4) rot_layer_regs<R>(a, t2);
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j) a[j] = __fmul2_rn(a[j], sc);
+        store_at<R>(c, VEC, o, a);
+    }
+}
+
+template <int R, int NT>
+__device__ __forceinline__ bool run_rot_program(const SweepCtx &c, const Sweep &S, int sidx) {
+    const int prog = rot_program<R>(c, S.op_begin, S.op_end);
+    if (!prog) return false;
+    const int k = 2 * (prog - 1) + (S.vec ? 1 : 0);
+    switch (k) {
+        case 0: rot_sweep<R, NT, 1, false>(c, S, sidx); break;
+        case 1: rot_sweep<R, NT, 1, true>(c, S, sidx); break;
+        case 2: rot_sweep<R, NT, 2, false>(c, S, sidx); break;
+        case 3: rot_sweep<R, NT, 2, true>(c, S, sidx); break;
+        case 4: rot_sweep<R, NT, 3, false>(c, S, sidx); break;
+        case 5: rot_sweep<R, NT, 3, true>(c, S, sidx); break;
+        case 6: rot_sweep<R, NT, 4, false>(c, S, sidx); break;
+        default: rot_sweep<R, NT, 4, true>(c, S, sidx); break;
+    }
+    return true;
+}
+
 template <int R, int NT, int KS = KS_ALL>
 __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int sidx) {
+    if constexpr ((R == 4 || R == 5) && KS == KS_LAYER) {
+        if (run_rot_program<R, NT>(c, S, sidx)) return;
+    }
     const int *ts = c.tab_s + sidx * kItemTab;
     const uint64_t *tg = c.tab_g + sidx * kItemTab;
     int gs[R];
@@ -721,7 +897,9 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
                     case 5: layer_store<MK_RXC, R, F>(c, vec, o, a, k0f, G, scale); break;
                     case 6: layer_store<MK_RXC, R, HI>(c, vec, o, a, k0f, G, scale); break;
                     case 7: layer_store<MK_U1R, R, F>(c, vec, o, a, k0f, G, scale); break;
-                    default: layer_store<MK_U1R, R, HI>(c, vec, o, a, k0f, G, scale); break;
+                    case 8: layer_store<MK_U1R, R, HI>(c, vec, o, a, k0f, G, scale); break;
+                    case 9: layer_store<MK_ROT, R, F>(c, vec, o, a, k0f, G, scale); break;
+                    default: layer_store<MK_ROT, R, HI>(c, vec, o, a, k0f, G, scale); break;
                 }
                 continue;
             }
@@ -739,6 +917,7 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
                     case MK_LAYER: run_layer<R>(op.a, a, c.cs + op.cst, (uint32_t)op.b, G); break;
                     case MK_RXC: disp_rxc<R>(op.a, a, c.cs + op.cst); break;
                     case MK_U1R: disp_u1r<R>(op.a, a, c.cs + op.cst); break;
+                    case MK_ROT: disp_rot<R>(op.a, a, c.cs + op.cst); break;
                     case MK_H: disp_h<R>(op.a, a); break;
                     case MK_U1: disp_u1<R>(op.a, a, c.cs + op.cst, op.cmask, op.cval, gbase(), G); break;
                     case MK_DIAG: apply_diag<R>(c, op, gbase(), G, a); break;
@@ -759,6 +938,9 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
                         break;
                     case MK_U1R:
                         disp_u1r<R>(op.a, a, c.cs + op.cst);
+                        break;
+                    case MK_ROT:
+                        disp_rot<R>(op.a, a, c.cs + op.cst);
                         break;
                     case MK_U2:
                         disp_u2<R>(op.a, op.b, a, c.cs + op.cst, op.cmask, op.cval, gbase(), G);
@@ -1370,21 +1552,23 @@ __device__ __forceinline__ bool named_sync_or(int id, int count, bool p) {
     return r != 0;
 }
 
-// Register split: the CTA launches 2 NTG + 128 threads at kWsLaunchRegs
-// registers each; the producer warpgroup (only its first thread works) drops
-// to kWsProducerRegs and the consumers rise to kWsConsumerRegs.  With
-// NTG = 256: 640 x 96 = 61,440 registers at launch >= 128 x 24 + 512 x 112 =
-// 60,416 after the split (per SM sub-partition: 4 x 32 x 112 + 32 x 24 =
-// 15,104 <= 16,384).
+// Register split: the CTA launches 2 NTG + 128 threads; the producer
+// warpgroup (only its first thread works) drops to 24 registers and the
+// consumers rise to ws_consumer_regs(NTG).  The launch total bounds the split
+// (setmaxnreg.inc draws on the registers the CTA was launched with):
+//   NTG = 256: 640 threads x 96 = 61,440 >= 128 x 24 + 512 x 112 = 60,416;
+//              per SM sub-partition 4 x 32 x 112 + 32 x 24 = 15,104 <= 16,384
+//   NTG = 128: 384 threads x 168 = 64,512 >= 128 x 24 + 256 x 240 = 64,512;
+//              per SM sub-partition 2 x 32 x 240 + 32 x 24 = 16,128 <= 16,384
 constexpr int kWsProducerRegs = 24;
-constexpr int kWsConsumerRegs = 112;
+constexpr int ws_consumer_regs(int ntg) { return ntg == 256 ? 112 : 240; }
 
 template <int R, int NTG, bool DENSE = false, int KS = KS_ALL>
 __global__ void __launch_bounds__(2 * NTG + 128, 1)
     tile_pass_ws_kernel(const __grid_constant__ CUtensorMap tm_src, const __grid_constant__ CUtensorMap tm_dst,
                         const TileArgs A) {
     constexpr int NT = 2 * NTG + 128;
-    static_assert(NTG == 256, "the register split below is sized for two 256-thread groups");
+    static_assert(NTG == 256 || NTG == 128, "the register split is sized for groups of 256 or 128 threads");
     extern __shared__ __align__(1024) unsigned char sm_raw[];
     const int per_item = A.const_stride != 0;
     const TileShared S = stage_tile_pass<NT>(A, sm_raw, per_item ? 2 : 1);
@@ -1448,7 +1632,7 @@ __global__ void __launch_bounds__(2 * NTG + 128, 1)
     }
 
     // consumer group g
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsConsumerRegs));
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(ws_consumer_regs(NTG)));
     const int g = tid / NTG;
     const int bar_id = 1 + g;
     float2 *cs = S.cs + (per_item ? g * const_copy_stride(P.n_const) : 0);

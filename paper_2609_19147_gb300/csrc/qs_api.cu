@@ -425,7 +425,8 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
         if (mo.kind == MK_DIAG || mo.kind == MK_DIAGQ || mo.kind == MK_DIAGC || mo.kind == MK_QFT ||
             mo.kind == MK_QFTL || (mo.cmask && mo.kind != MK_DIAGC))
             A.needs_gidx = 1;
-        if (!(mo.kind == MK_LAYER || mo.kind == MK_RXC || mo.kind == MK_U1R || mo.kind == MK_H || mo.kind == MK_U1 ||
+        if (!(mo.kind == MK_LAYER || mo.kind == MK_RXC || mo.kind == MK_U1R || mo.kind == MK_ROT || mo.kind == MK_H ||
+              mo.kind == MK_U1 ||
               mo.kind == MK_DIAG || mo.kind == MK_DIAGQ || mo.kind == MK_DIAGC))
             A.kset = 0;
     }
@@ -454,7 +455,7 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     };
     // Warp-specialised kernel (one CTA per SM, a producer warpgroup and two
     // consumer groups over three or more tile buffers) for 13-bit tiles with
-    // 4-bit groups on the tensor-copy path, when three buffers fit.
+    // 4- or 5-bit groups on the tensor-copy path, when three buffers fit.
     static int ws_env = -2;
     if (ws_env == -2) {
         const char *e = getenv("QS_TILE_WS");
@@ -462,7 +463,7 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     }
     const int ws_limit = 227 * 1024 - 1024;
     const int ws_copies = dp.host.items > 1 ? 2 : 1;
-    if (ws_env != 0 && hp.tma.ok && tp.T == 13 && tp.R == 4 && !A.dense &&
+    if (ws_env != 0 && hp.tma.ok && tp.T == 13 && (tp.R == 4 || tp.R == 5) && !A.dense &&
         layout(ws_copies) + 3 * buf_bytes <= ws_limit) {
         A.ws = 1;
         A.ctas_per_sm = 1;
@@ -521,7 +522,7 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
         if (s != QS_OK) return s;
     }
     A.threads = (tp.R == 4 && tp.T >= 13 && A.ctas_per_sm == 1) ? 512 : (tp.R == 5 && A.ctas_per_sm == 2) ? 128 : 256;
-    if (A.ws) A.threads = 2 * 256 + 128;
+    if (A.ws) A.threads = tile_ws_threads(tp.R);
     if (A.dense && (tp.R != 5 || A.ctas_per_sm != 1)) return fail(QS_ERR_INTERNAL, "dense pass without 5-bit groups");
     if (A.dense) A.threads = 256;
     {
@@ -1050,15 +1051,17 @@ qs_status run_host_plan(qs_state *st, Plan &&plan, float2 *home, int batch) {
 
 // Fused plans for many gate lists at once, on up to 16 host threads (the
 // planner keeps no shared state between calls).
+// item_plans: the lists are the items of one batch, whose plans are to be
+// merged (see build_fused_plan).
 qs_status build_plans_parallel(int n, int batch, const std::vector<std::vector<RGate>> &lists, const qs_opts &o,
-                               std::vector<Plan> &out, std::string &err) {
+                               std::vector<Plan> &out, std::string &err, bool item_plans) {
     out.assign(lists.size(), Plan());
     std::vector<qs_status> st(lists.size(), QS_OK);
     std::vector<std::string> errs(lists.size());
     std::atomic<size_t> next(0);
     auto work = [&]() {
         for (size_t i; (i = next.fetch_add(1)) < lists.size();)
-            st[i] = build_fused_plan(n, batch, lists[i], o, out[i], errs[i]);
+            st[i] = build_fused_plan(n, batch, lists[i], o, out[i], errs[i], item_plans);
     };
     const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
     const size_t nt = std::min<size_t>(hw, lists.size());
@@ -1109,7 +1112,7 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, c
             for (int bi = 0; bi < st->batch && all_cached; ++bi) all_cached = st->cache.count(keys[bi]) != 0;
             if (!all_cached) {
                 std::string err;
-                s = build_plans_parallel(st->n, 1, resolved, o, built, err);
+                s = build_plans_parallel(st->n, 1, resolved, o, built, err, true);
                 if (s != QS_OK) return fail(s, err);
                 Plan merged;
                 if (merge_item_plans(built, merged, st->batch)) {
@@ -1431,8 +1434,8 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
                 }
             std::vector<Plan> p2, pB;
             std::string err;
-            qs_status r = build_plans_parallel(st->n, un_b, l2, fo, p2, err);
-            if (r == QS_OK) r = build_plans_parallel(st->n, un_b * B, lB, fo, pB, err);
+            qs_status r = build_plans_parallel(st->n, un_b, l2, fo, p2, err, true);
+            if (r == QS_OK) r = build_plans_parallel(st->n, un_b * B, lB, fo, pB, err, false);
             if (r != QS_OK) {
                 seg_status = r;
                 seg_err = err;
@@ -1466,7 +1469,7 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
             lists[b].assign(rg[b].begin() + g_begin, rg[b].begin() + g_end);
         std::vector<Plan> fwd;
         std::string err;
-        qs_status r = build_plans_parallel(st->n, pi ? 1 : B, lists, o, fwd, err);
+        qs_status r = build_plans_parallel(st->n, pi ? 1 : B, lists, o, fwd, err, pi);
         if (r != QS_OK) return fail(r, err);
         if (!pi) return run_host_plan(st, std::move(fwd[0]), st->home, B);
         Plan merged;

@@ -98,6 +98,9 @@ enum MicroKind : int32_t {
                   // for j >= 16).  Data at lo (uint64 slots): N_m (R slots), the R degrees
                   // (6 bits each), Mz, the R Mz increments (12 bits each), then per class
                   // M_d and d.
+    MK_ROT = 11,  // real rotation c [[1, t], [-t, 1]] (|t| <= 1) on group bit a: consts
+                  // (t, t), (-t, -t) (packed FP32x2 operands); the factor c is folded into
+                  // the sweep scale, so the op is one packed FMA per amplitude
 };
 constexpr int kMaxCouple = 16;
 constexpr int kMaxCountClasses = 24;

@@ -50,6 +50,7 @@ struct TileArgs {
 cudaError_t launch_tile_pass(int R, const TileArgs &A, const void *tm_src, const void *tm_dst, int grid,
                              int smem_bytes, cudaStream_t st);
 void tile_kernel_smem_config(int bytes);
+int tile_ws_threads(int R);   // threads per CTA of the warp-specialised tile kernel (R = 4 or 5)
 std::string tile_kernel_attrs(int R, const TileArgs &A);
 
 // per-gate kernels: op per state (op_stride = 1) or shared (op_stride = 0)

@@ -1499,6 +1499,10 @@ uint16_t bf16_bits(double x) {
     return (uint16_t)(u >> 16);
 }
 
+// Set while build_fused_plan builds one of several per-item plans: the pass
+// builder then keeps to micro-op forms that do not depend on angle values.
+thread_local bool t_item_plan = false;
+
 struct PassBuilder {
     int n, L, T, R, dprec;
     HostPass hp;
@@ -1746,8 +1750,19 @@ struct PassBuilder {
                                m[1] == m[2];
                     bool real = f.cmask == 0 && m[0].imag() == 0 && m[1].imag() == 0 && m[2].imag() == 0 &&
                                 m[3].imag() == 0;
+                    // a real rotation c [[1, t], [-t, 1]] with |t| <= 1: one packed FMA per
+                    // amplitude, c folded into the sweep scale (finalize)
+                    bool rot = !t_item_plan && real && m[0] == m[3] && m[1] == -m[2] && m[0].real() != 0.0 &&
+                               std::abs(m[1].real()) <= std::abs(m[0].real());
                     if (h) {
                         mo.kind = MK_H;
+                    } else if (rot) {
+                        mo.kind = MK_ROT;
+                        const double c = m[0].real(), t = m[1].real() / c;
+                        cst.push_back(float2{(float)t, (float)t});
+                        cst.push_back(float2{(float)-t, (float)-t});
+                        // c travels to finalize in the (otherwise unused) control value
+                        std::memcpy(&mo.cval, &c, sizeof c);
                     } else if (rxc) {
                         mo.kind = MK_RXC;
                         cst.push_back(float2{(float)m[0].real(), (float)m[1].imag()});
@@ -1974,9 +1989,16 @@ struct PassBuilder {
             uint64_t ggl = 0;
             for (int m = 0; m < sw.r; ++m) ggl |= glob_of_local(tp, sw.gbit[m]);
             int n_butterfly = 0;
+            double rot_scale = 1.0;   // product of the factors c of the sweep's rotations
             for (int i = sw.op_begin; i < sw.op_end; ++i) {
                 MicroOp &mo = tp.micro[i];
                 if (mo.kind == MK_H || mo.kind == MK_QFT) n_butterfly++;
+                if (mo.kind == MK_ROT) {
+                    double c;
+                    std::memcpy(&c, &mo.cval, sizeof c);
+                    rot_scale *= c;
+                    mo.cval = 0;
+                }
                 if (mo.kind == MK_DIAGC) {
                     if (!to_diagc(mo, sw, *count_src[mo.cst])) count_failed = true;
                     continue;
@@ -2019,7 +2041,7 @@ struct PassBuilder {
                     }
                 }
             }
-            sw.scale = (float)std::pow(kSqrtHalf, (double)n_butterfly);
+            sw.scale = (float)(std::pow(kSqrtHalf, (double)n_butterfly) * rot_scale);
         }
         merge_layers();
         tp.n_const = (int)cst.size();
@@ -2038,7 +2060,8 @@ struct PassBuilder {
                 const MicroOp &m0 = tp.micro[i];
                 auto layer_kind = [&](const MicroOp &m) {
                     if (m.cmask) return -1;
-                    if (m.kind == MK_RXC || m.kind == MK_U1R || m.kind == MK_U1 || m.kind == MK_H) return (int)m.kind;
+                    if (m.kind == MK_RXC || m.kind == MK_U1R || m.kind == MK_U1 || m.kind == MK_H || m.kind == MK_ROT)
+                        return (int)m.kind;
                     return -1;
                 };
                 const int lk = layer_kind(m0);
@@ -2049,8 +2072,9 @@ struct PassBuilder {
                         mask |= 1u << tp.micro[j].a;
                         ++j;
                     }
-                    const int stride = lk == MK_RXC ? 1 : lk == MK_U1R ? 4 : lk == MK_U1 ? 4 : 0;
-                    if (j - i >= 2 && (int)cst.size() + R * stride + 1 <= kMaxConst) {
+                    const int stride = lk == MK_RXC ? 1 : lk == MK_U1R ? 4 : lk == MK_U1 ? 4 : lk == MK_ROT ? 2 : 0;
+                    // a lone rotation becomes a one-bit layer too (see the padding below)
+                    if (j - i >= (lk == MK_ROT ? 1 : 2) && (int)cst.size() + R * stride + 1 <= kMaxConst) {
                         MicroOp L;
                         std::memset(&L, 0, sizeof L);
                         L.kind = MK_LAYER;
@@ -2101,6 +2125,22 @@ struct PassBuilder {
             }
             sw.op_begin = begin;
             sw.op_end = (int)out.size();
+            // A sweep of rotation layers and count-table diagonals in one of the
+            // kernel's rotation programs (layer; diagonal, layer; layer,
+            // diagonal; layer, diagonal, layer) gets its layers on all R group
+            // bits: the constants of a bit without a rotation are t = 0 (set
+            // above), an exact identity, and the sweep runs as straight-line code.
+            auto rot_layer = [&](const MicroOp &m) { return m.kind == MK_LAYER && m.a == MK_ROT; };
+            auto diagc = [&](const MicroOp &m) { return m.kind == MK_DIAGC; };
+            const int n_ops = sw.op_end - sw.op_begin;
+            const MicroOp *o = out.data() + begin;
+            const bool program = sw.r == R && ((n_ops == 1 && rot_layer(o[0])) ||
+                                               (n_ops == 2 && diagc(o[0]) && rot_layer(o[1])) ||
+                                               (n_ops == 2 && rot_layer(o[0]) && diagc(o[1])) ||
+                                               (n_ops == 3 && rot_layer(o[0]) && diagc(o[1]) && rot_layer(o[2])));
+            if (program)
+                for (int k = begin; k < sw.op_end; ++k)
+                    if (rot_layer(out[k])) out[k].b = (1 << R) - 1;
         }
         tp.n_micro = (int)out.size();
         for (int k = 0; k < tp.n_micro; ++k) tp.micro[k] = out[k];
@@ -2181,7 +2221,11 @@ static void clamp_tile_shape(int n, int &T, int &L) {
 // SM hide each other's copy latency) unless they need more HBM passes than
 // 13-bit tiles with 5-bit groups.
 qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, const qs_opts &o, Plan &plan,
-                           std::string &err) {
+                           std::string &err, bool item_plan) {
+    struct ItemPlanScope {   // the pass builder reads the flag on this thread
+        explicit ItemPlanScope(bool v) { t_item_plan = v; }
+        ~ItemPlanScope() { t_item_plan = false; }
+    } item_scope(item_plan);
     if (o.dense_prec < QS_DENSE_OFF || o.dense_prec > QS_DENSE_BF16) {
         err = "dense_prec must be one of QS_DENSE_OFF / FP32 / TF32X3 / BF16";
         return QS_ERR_INVALID_ARG;
@@ -2627,7 +2671,7 @@ std::string Plan::describe() const {
             os << "TILE T=" << t.T << " L=" << t.L << " hb=[";
             for (int k = 0; k < t.H; ++k) os << (k ? "," : "") << t.hb[k];
             os << "] tma=" << (hp.tma.ok ? 1 : 0) << " sweeps=" << t.n_sweeps
-               << " U1=" << cnt[MK_U1] + cnt[MK_H] + cnt[MK_RXC] + cnt[MK_U1R] << " U2=" << cnt[MK_U2]
+               << " U1=" << cnt[MK_U1] + cnt[MK_H] + cnt[MK_RXC] + cnt[MK_U1R] + cnt[MK_ROT] << " U2=" << cnt[MK_U2]
                << " DIAG=" << cnt[MK_DIAG] << " QFT=" << cnt[MK_QFT];
             int nd = 0, slow = 0, fq = 0, fc = 0;
             for (int k = 0; k < t.n_sweeps; ++k) nd += t.sweeps[k].dense ? 1 : 0;

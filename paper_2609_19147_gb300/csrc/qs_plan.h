@@ -121,8 +121,12 @@ qs_status resolve_gates(int n, const qs_gate *gates, size_t n_gates, const doubl
 void gate_matrix(const RGate &g, cd *M);
 bool gate_is_diagonal(int kind);
 
+// item_plan: the plan is one of several per-item plans that merge_item_plans
+// is to combine (they must agree in everything but constant values), so no
+// micro-op form is chosen by angle value (the real-rotation form MK_ROT, whose
+// factor sits in the sweep scale, is left out).
 qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, const qs_opts &o, Plan &plan,
-                           std::string &err);
+                           std::string &err, bool item_plan = false);
 qs_status build_pergate_plan(int n, const std::vector<RGate> &gates, Plan &plan, std::string &err);
 
 // Merge per-item fused plans into one plan for `batch` states (a multiple of

@@ -54,7 +54,7 @@ int popc(uint64_t x) {
 }
 
 struct Counts {
-    long micro[11] = {0};
+    long micro[12] = {0};
     long dense[4] = {0};
     long tile = 0, perm = 0, gather = 0, tma = 0, rows = 0, swz = 0, sweeps = 0, pergate = 0;
 };
@@ -339,6 +339,14 @@ class TileRun {
             case MK_U1:
                 u1(m, r, a, K(k0 + 4 * m), K(k0 + 4 * m + 1), K(k0 + 4 * m + 2), K(k0 + 4 * m + 3), 0, 0, no);
                 break;
+            case MK_ROT: {
+                // [[1, t], [-t, 1]]; the factor c is in the sweep scale
+                const float2 q0 = Kraw(k0 + 2 * m), q1 = Kraw(k0 + 2 * m + 1);
+                need(q0.x == q0.y && q1.x == q1.y && q1.x == -q0.x, "rotation not packed as (t, t), (-t, -t)");
+                need(std::abs(q0.x) <= 1.f, "rotation tangent above 1");
+                u1(m, r, a, 1.0, q0.x, q1.x, 1.0, 0, 0, no);
+                break;
+            }
             case MK_H:
                 u1(m, r, a, 1.0, 1.0, 1.0, -1.0, 0, 0, no);
                 break;
@@ -360,8 +368,12 @@ class TileRun {
 
     template <class GI>
     void op(const MicroOp &o, int r, const uint64_t *gg, uint64_t gbase, std::vector<C> &a, GI &gidx, bool first) {
-        need(o.kind >= 0 && o.kind <= MK_DIAGC, "micro-op kind");
-        if (first) cnt_.micro[o.kind]++;
+        need(o.kind >= 0 && o.kind <= MK_ROT, "micro-op kind");
+        if (first) {
+            cnt_.micro[o.kind]++;
+            // a layer also exercises its op kind (lone rotations become one-bit layers)
+            if (o.kind == MK_LAYER && o.a >= 0 && o.a <= MK_ROT) cnt_.micro[o.a]++;
+        }
         uint64_t gmask = 0;
         for (int m = 0; m < r; ++m) gmask |= gg[m];
         switch (o.kind) {
@@ -372,7 +384,9 @@ class TileRun {
             case MK_H:
             case MK_RXC:
             case MK_U1R:
-                layer_bit(o.kind, o.a, r, a, o.cst - (o.kind == MK_RXC ? o.a : o.kind == MK_U1R ? 4 * o.a : 0));
+            case MK_ROT:
+                layer_bit(o.kind, o.a, r, a,
+                          o.cst - (o.kind == MK_RXC ? o.a : o.kind == MK_U1R ? 4 * o.a : o.kind == MK_ROT ? 2 * o.a : 0));
                 break;
             case MK_U2: {
                 need(o.a >= 0 && o.a < r && o.b >= 0 && o.b < r && o.a != o.b, "4x4 bits");
@@ -714,7 +728,7 @@ int main(int argc, char **argv) {
                 return 1;
             }
             const qs_status ps = mode == QS_MODE_PERGATE ? build_pergate_plan(n, rg, plans[bi], err)
-                                                         : build_fused_plan(n, 1, rg, o, plans[bi], err);
+                                                         : build_fused_plan(n, 1, rg, o, plans[bi], err, B > 1);
             if (ps != QS_OK) {
                 std::printf("FAIL %d plan: %s\n", ci, err.c_str());
                 return 1;
@@ -805,7 +819,7 @@ int main(int argc, char **argv) {
         }
         std::printf("CASE %d passes %zu tile %ld perm %ld gather %ld tma %ld rows %ld swz %ld sweeps %ld merged %d micro",
                     ci, n_passes, c.tile, c.perm, c.gather, c.tma, c.rows, c.swz, c.sweeps, merged ? 1 : 0);
-        for (int k = 0; k <= MK_DIAGC; ++k) std::printf(" %ld", c.micro[k]);
+        for (int k = 0; k <= MK_ROT; ++k) std::printf(" %ld", c.micro[k]);
         std::printf(" dense %ld %ld %ld pergate %ld\n", c.dense[1], c.dense[2], c.dense[3], c.pergate);
         ++ci;
     }
