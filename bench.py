@@ -577,14 +577,20 @@ def run_gpu(args):
 def profile_case(args):
     """A small fixed workload for ncu captures (no timing, no JSON line):
     tfim28 = 2 Strang steps of the TFIM at 28 qubits with 13-qubit tiles and
-    4-bit groups (the tile shape of the 30q TFIM passes), applied twice."""
+    4-bit groups (the tile shape of the 30q TFIM passes), applied twice;
+    qft28 = the 28-qubit gate-stream QFT with swaps (13-qubit tiles, 4-bit
+    groups), applied twice."""
     import torch
     import paper_2609_19147_gb300 as qs
     n = 28
-    gl = W.tfim_gates(n, 2, TFIM_DT, 1.0, W.tfim_fields(n, 3), order=2)
+    if args.profile_case == "qft28":
+        gl = W.qft_gates(n, swaps=True)
+    else:
+        gl = W.tfim_gates(n, 2, TFIM_DT, 1.0, W.tfim_fields(n, 3), order=2)
     st = qs.State(n)
+    st.provide_scratch()
     for _ in range(2):
-        st.apply(gl, tile_qubits=13, group_qubits=4)
+        st.apply(gl, tile_qubits=13, low_qubits=4, group_qubits=4)
     torch.cuda.synchronize()
     st.close()
     return 0
@@ -601,7 +607,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the grads / dense / QAOA / 28q suite rows")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 25-qubit end-to-end workload sweep")
-    ap.add_argument("--profile-case", choices=["tfim28"], default=None,
+    ap.add_argument("--profile-case", choices=["tfim28", "qft28"], default=None,
                     help="run a small fixed workload for ncu captures instead of the benchmark")
     args = ap.parse_args()
     if args.profile_case:

@@ -735,23 +735,19 @@ __device__ __forceinline__ int rot_program(const SweepCtx &c, int op_begin, int 
     return 0;
 }
 
-// the count-table diagonal of one sweep with its per-sweep data in registers
+// the count-table diagonal of one sweep: its op read once per sweep, its
+// data (neighbour masks, degrees, classes) read from shared memory per item
+// (held in registers it would crowd out the amplitudes)
 template <int R>
 struct DiagcRegs {
     const float2 *lut;
-    const uint64_t *cls;   // per distance class: mask, distance
-    uint64_t nbr[R], degs, mz, zinc, q_lo, q_hi;
+    const uint64_t *dat;
+    uint64_t q_lo, q_hi;
     int n_cls, stride;
     bool cz;
     __device__ __forceinline__ void init(const SweepCtx &c, const MicroOp &op) {
         lut = c.cs + op.cst;
-        const uint64_t *dat = reinterpret_cast<const uint64_t *>(c.cs + op.lo);
-#pragma unroll
-        for (int m = 0; m < R; ++m) nbr[m] = dat[m];
-        degs = dat[R];
-        mz = dat[R + 1];
-        zinc = dat[R + 2];
-        cls = dat + R + 3;
+        dat = reinterpret_cast<const uint64_t *>(c.cs + op.lo);
         n_cls = op.a;
         stride = op.p;
         cz = op.b != 0;
@@ -759,6 +755,8 @@ struct DiagcRegs {
         q_hi = op.cval;
     }
     __device__ __forceinline__ void apply(uint64_t x0, float2 (&a)[1 << R]) const {
+        const uint64_t degs = dat[R], mz = dat[R + 1], zinc = dat[R + 2];
+        const uint64_t *cls = dat + R + 3;
         int c0 = stride * __popcll(x0 & mz);
         for (int k = 0; k < n_cls; ++k) {
             const uint64_t f = cz ? (x0 & (x0 >> (int)cls[2 * k + 1])) : (x0 ^ (x0 >> (int)cls[2 * k + 1]));
@@ -768,7 +766,7 @@ struct DiagcRegs {
         cnt[0] = c0;
 #pragma unroll
         for (int m = 0; m < R; ++m) {
-            const int s = __popcll(x0 & nbr[m]);
+            const int s = __popcll(x0 & dat[m]);
             const int dm = (cz ? s : (int)((degs >> (6 * m)) & 63) - 2 * s) + (int)((zinc >> (12 * m)) & 4095);
 #pragma unroll
             for (int j = 0; j < (1 << m); ++j) cnt[j | (1 << m)] = cnt[j] + dm;
@@ -820,10 +818,13 @@ __device__ __forceinline__ void rot_sweep(const SweepCtx &c, const Sweep &S, int
     const int n_items = 1 << (c.T - R);
     for (int item = c.lt; item < n_items; item += NT) {
         const int i0 = item & 31, i1 = 32 + ((item >> 5) & 31), i2 = 64 + ((item >> 10) & 15);
-        int o[1 << R];
-        group_offsets<R>(ts[i0] ^ ts[i1] ^ ts[i2], gs, o);
+        const int saddr = ts[i0] ^ ts[i1] ^ ts[i2];
         float2 a[1 << R];
-        load_at<R>(c, VEC, o, a);
+        {
+            int o[1 << R];
+            group_offsets<R>(saddr, gs, o);
+            load_at<R>(c, VEC, o, a);
+        }
         uint64_t x0 = 0;
         if constexpr (PROG >= 2) x0 = c.tile_gbase | tg[i0] | tg[i1] | tg[i2];
         if constexpr (PROG == 2) dg.apply(x0, a);
@@ -832,6 +833,9 @@ __device__ __forceinline__ void rot_sweep(const SweepCtx &c, const Sweep &S, int
         if constexpr (PROG == 4) rot_layer_regs<R>(a, t2);
 #pragma unroll
         for (int j = 0; j < (1 << R); ++j) a[j] = __fmul2_rn(a[j], sc);
+        // the offsets again (cheaper than holding 2^R registers through the ops)
+        int o[1 << R];
+        group_offsets<R>(saddr, gs, o);
         store_at<R>(c, VEC, o, a);
     }
 }

@@ -1719,7 +1719,37 @@ struct PassBuilder {
                     }
         }
     }
+    // Uncontrolled one-qubit ops on distinct bits commute, so a run of them
+    // (a layer) is held back and added in the order that fills the open sweep
+    // first: the layer's ops on the open group's bits join it, e.g. the
+    // sweep that holds a diagonal applies the next layer on its own bits too.
+    std::vector<FOp> pend;
+    uint64_t pend_bits = 0;
+    int pending_ops() const { return (int)pend.size(); }
     void add(const FOp &f, const DiagPlan *dp) {
+        if (f.kind == F_U1 && f.cmask == 0) {
+            if ((pend_bits >> f.t0) & 1) flush_pending();
+            pend.push_back(f);
+            pend_bits |= 1ull << f.t0;
+            return;
+        }
+        flush_pending();
+        add_now(f, dp);
+    }
+    void flush_pending() {
+        if (pend.empty()) return;
+        std::vector<FOp> ops;
+        ops.swap(pend);
+        pend_bits = 0;
+        std::vector<char> in_open(ops.size(), 0);
+        if (open >= 0)
+            for (size_t i = 0; i < ops.size(); ++i) in_open[i] = (cur_group >> tile_local(tp, ops[i].t0)) & 1;
+        for (size_t i = 0; i < ops.size(); ++i)
+            if (in_open[i]) add_now(ops[i], nullptr);
+        for (size_t i = 0; i < ops.size(); ++i)
+            if (!in_open[i]) add_now(ops[i], nullptr);
+    }
+    void add_now(const FOp &f, const DiagPlan *dp) {
         switch (f.kind) {
             case F_DENSE:
                 add_dense(f);
@@ -1980,6 +2010,7 @@ struct PassBuilder {
         return true;
     }
     void finalize() {
+        flush_pending();
         close_sweep();
         // convert tile-local bit references to group indices, fill QFT
         // tables, fold butterfly normalisations, mark diagonal factors that
@@ -2449,7 +2480,10 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
                 const int id = taken[k];
                 pbp->add(ops[id], ops[id].kind == F_DIAG ? &dplans[id] : nullptr);
                 ++added;
-                if (pbp->tp.n_sweeps >= kMaxSweeps - 1 || pbp->tp.n_micro >= kMaxMicro - 16) break;
+                // held-back layer ops may each still open a sweep
+                if (pbp->tp.n_sweeps + pbp->pending_ops() >= kMaxSweeps - 1 ||
+                    pbp->tp.n_micro + pbp->pending_ops() >= kMaxMicro - 16)
+                    break;
             }
             pbp->finalize();
             if (pbp->tp.n_const <= max_const) {
