@@ -461,7 +461,16 @@ struct SweepCtx {
     const uint64_t *tab_g;   // smem: per-sweep item-address tables (global index bits)
     uint64_t tile_gbase;     // global index of tile-local 0 (within the state)
     int lt;                  // thread index within the threads that share the sweeps
+    int n_const;             // constants staged (device checks)
+    int tile_elems;          // 2^T (device checks)
+    int *err;                // device status word (device checks)
 };
+
+#ifdef QS_DEVICE_CHECKS
+#define QS_DCHECK(ctx, cond, code) (((cond)) ? true : (atomicCAS((ctx).err, 0, (code)), false))
+#else
+#define QS_DCHECK(ctx, cond, code) true
+#endif
 
 template <int R>
 __device__ __forceinline__ void sweep_load(const SweepCtx &c, bool vec, int saddr, const int (&gs)[R],
@@ -473,6 +482,7 @@ __device__ __forceinline__ void sweep_load(const SweepCtx &c, bool vec, int sadd
 #pragma unroll
             for (int m = 1; m < R; ++m)
                 if ((j >> m) & 1) o ^= gs[m];
+            if (!QS_DCHECK(c, o >= 0 && o + 1 < c.tile_elems && !(o & 1), 1010)) continue;
             const float4 v = *reinterpret_cast<const float4 *>(c.buf + o);
             a[j] = make_float2(v.x, v.y);
             a[j + 1] = make_float2(v.z, v.w);
@@ -484,6 +494,7 @@ __device__ __forceinline__ void sweep_load(const SweepCtx &c, bool vec, int sadd
 #pragma unroll
             for (int m = 0; m < R; ++m)
                 if ((j >> m) & 1) o ^= gs[m];
+            if (!QS_DCHECK(c, o >= 0 && o < c.tile_elems, 1011)) continue;
             a[j] = c.buf[o];
         }
     }
@@ -499,7 +510,8 @@ __device__ __forceinline__ void sweep_store(const SweepCtx &c, bool vec, int sad
 #pragma unroll
             for (int m = 1; m < R; ++m)
                 if ((j >> m) & 1) o ^= gs[m];
-            *reinterpret_cast<float4 *>(c.buf + o) = make_float4(a[j].x, a[j].y, a[j + 1].x, a[j + 1].y);
+            if (QS_DCHECK(c, o >= 0 && o + 1 < c.tile_elems && !(o & 1), 1012))
+                *reinterpret_cast<float4 *>(c.buf + o) = make_float4(a[j].x, a[j].y, a[j + 1].x, a[j + 1].y);
         }
     } else {
 #pragma unroll
@@ -508,7 +520,7 @@ __device__ __forceinline__ void sweep_store(const SweepCtx &c, bool vec, int sad
 #pragma unroll
             for (int m = 0; m < R; ++m)
                 if ((j >> m) & 1) o ^= gs[m];
-            c.buf[o] = a[j];
+            if (QS_DCHECK(c, o >= 0 && o < c.tile_elems, 1013)) c.buf[o] = a[j];
         }
     }
 }
@@ -528,13 +540,23 @@ __device__ __forceinline__ void load_at(const SweepCtx &c, bool vec, const int (
     if (vec) {
 #pragma unroll
         for (int j = 0; j < (1 << R); j += 2) {
+            if (!QS_DCHECK(c, o[j] >= 0 && o[j] + 1 < c.tile_elems && !(o[j] & 1), 1001)) {
+                a[j] = a[j + 1] = make_float2(0.f, 0.f);
+                continue;
+            }
             const float4 v = *reinterpret_cast<const float4 *>(c.buf + o[j]);
             a[j] = make_float2(v.x, v.y);
             a[j + 1] = make_float2(v.z, v.w);
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < (1 << R); ++j) a[j] = c.buf[o[j]];
+        for (int j = 0; j < (1 << R); ++j) {
+            if (!QS_DCHECK(c, o[j] >= 0 && o[j] < c.tile_elems, 1002)) {
+                a[j] = make_float2(0.f, 0.f);
+                continue;
+            }
+            a[j] = c.buf[o[j]];
+        }
     }
 }
 
@@ -543,10 +565,12 @@ __device__ __forceinline__ void store_at(const SweepCtx &c, bool vec, const int 
     if (vec) {
 #pragma unroll
         for (int j = 0; j < (1 << R); j += 2)
-            *reinterpret_cast<float4 *>(c.buf + o[j]) = make_float4(a[j].x, a[j].y, a[j + 1].x, a[j + 1].y);
+            if (QS_DCHECK(c, o[j] >= 0 && o[j] + 1 < c.tile_elems && !(o[j] & 1), 1003))
+                *reinterpret_cast<float4 *>(c.buf + o[j]) = make_float4(a[j].x, a[j].y, a[j + 1].x, a[j + 1].y);
     } else {
 #pragma unroll
-        for (int j = 0; j < (1 << R); ++j) c.buf[o[j]] = a[j];
+        for (int j = 0; j < (1 << R); ++j)
+            if (QS_DCHECK(c, o[j] >= 0 && o[j] < c.tile_elems, 1004)) c.buf[o[j]] = a[j];
     }
 }
 
@@ -671,6 +695,7 @@ __device__ __forceinline__ void apply_diagc(const SweepCtx &c, const MicroOp &op
     for (int j = 0; j < (1 << R); ++j) {
         const uint64_t qw = j < 16 ? op.cmask : op.cval;
         const int q = (int)((qw >> (4 * (j & 15))) & 15);
+        if (!QS_DCHECK(c, cnt[j] + q >= 0 && op.cst + cnt[j] + q < c.n_const, 1009)) continue;
         a[j] = cmul(a[j], lut[cnt[j] + q]);
     }
 }
@@ -745,7 +770,14 @@ struct DiagcRegs {
     uint64_t q_lo, q_hi;
     int n_cls, stride;
     bool cz;
+#ifdef QS_DEVICE_CHECKS
+    const SweepCtx *ctx;
+#endif
     __device__ __forceinline__ void init(const SweepCtx &c, const MicroOp &op) {
+#ifdef QS_DEVICE_CHECKS
+        ctx = &c;
+        QS_DCHECK(c, op.cst >= 0 && op.lo >= 0 && op.lo + R + 3 + 2 * op.a <= c.n_const, 1005);
+#endif
         lut = c.cs + op.cst;
         dat = reinterpret_cast<const uint64_t *>(c.cs + op.lo);
         n_cls = op.a;
@@ -774,6 +806,9 @@ struct DiagcRegs {
 #pragma unroll
         for (int j = 0; j < (1 << R); ++j) {
             const int q = (int)(((j < 16 ? q_lo : q_hi) >> (4 * (j & 15))) & 15);
+#ifdef QS_DEVICE_CHECKS
+            if (!QS_DCHECK(*ctx, cnt[j] + q >= 0 && (lut - ctx->cs) + cnt[j] + q < ctx->n_const, 1006)) continue;
+#endif
             a[j] = cmul(a[j], lut[cnt[j] + q]);
         }
     }
@@ -806,6 +841,8 @@ __device__ __forceinline__ void rot_sweep(const SweepCtx &c, const Sweep &S, int
     const int b = S.op_begin;
     const int i_l1 = PROG == 2 ? b + 1 : b;
     float2 t1[R], t2[R];
+    QS_DCHECK(c, c.micro[i_l1].cst >= 0 && c.micro[i_l1].cst + 2 * R <= c.n_const, 1007);
+    if constexpr (PROG == 4) QS_DCHECK(c, c.micro[b + 2].cst >= 0 && c.micro[b + 2].cst + 2 * R <= c.n_const, 1008);
 #pragma unroll
     for (int m = 0; m < R; ++m) t1[m] = c.cs[c.micro[i_l1].cst + 2 * m];
     if constexpr (PROG == 4) {
@@ -1447,6 +1484,9 @@ __global__ void __launch_bounds__(NT, MINB)
 
     SweepCtx c;
     c.lt = tid;
+    c.n_const = P.n_const;
+    c.tile_elems = tile_elems;
+    c.err = A.err;
     c.T = T;
     c.L = L;
     c.contrib = s_contrib;
@@ -1517,7 +1557,12 @@ __global__ void __launch_bounds__(NT, MINB)
 // buffer and its store has read it out.  Consumer group g takes the tiles
 // k = g, g + 2, ... : it waits for the tile's load, runs the sweeps with a
 // named barrier of its own between them, and signals the buffer's empty
-// barrier.  The two groups work on different tiles at different phases of
+// barrier.  A load completes on the barrier of its (buffer, group) pair,
+// full[2 b + g]: with an odd buffer count a buffer alternates between the
+// groups, and a shared barrier would let a group that is one tile ahead take
+// the completed phase of a load two uses back (the same parity) while the
+// other group's load into that buffer is still in flight.  On its own pair
+// barrier a group waits for every phase in order, so parity is exact.  The two groups work on different tiles at different phases of
 // their sweeps (the shared-memory, FP32 and TMA work of the SM overlap
 // instead of lining up behind one barrier), and the load of a group's next
 // tile is issued while the other group still computes, so neither group waits
@@ -1588,6 +1633,8 @@ __global__ void __launch_bounds__(2 * NTG + 128, 1)
     const long long stride = gridDim.x;
     const int n_mine = (int)((total - 1 - blockIdx.x) / stride + 1);   // tiles of this CTA
     volatile int *abort_flag = S.abort_flag;
+    // tiles between two uses of a (buffer, group) barrier: lcm(NB, 2)
+    const int pair_period = (NB & 1) ? 2 * NB : NB;
 
     if (tid >= 2 * NTG) {
         // producer warpgroup: its first thread issues every copy (one tensor
@@ -1619,8 +1666,9 @@ __global__ void __launch_bounds__(2 * NTG + 128, 1)
             if (j < n_mine) {
                 int c[5];
                 coords(j, c);
-                mbar_arrive_expect_tx(&S.full[b], tile_bytes);
-                tma_load_5d(S.buf0 + (size_t)b * tile_elems, &tm_src, c, &S.full[b]);
+                uint64_t *fb = &S.full[2 * b + (j & 1)];
+                mbar_arrive_expect_tx(fb, tile_bytes);
+                tma_load_5d(S.buf0 + (size_t)b * tile_elems, &tm_src, c, fb);
                 loaded = j + 1;
             }
         }
@@ -1629,7 +1677,7 @@ __global__ void __launch_bounds__(2 * NTG + 128, 1)
             *abort_flag = 1;
             // let the last load of every buffer land before the CTA leaves
             for (int j = loaded - NB < 0 ? 0 : loaded - NB; j < loaded; ++j)
-                mbar_wait_bounded(&S.full[j % NB], (uint32_t)((j / NB) & 1));
+                mbar_wait_bounded(&S.full[2 * (j % NB) + (j & 1)], (uint32_t)((j / pair_period) & 1));
         }
         bulk_wait_all0();
         return;
@@ -1642,6 +1690,9 @@ __global__ void __launch_bounds__(2 * NTG + 128, 1)
     float2 *cs = S.cs + (per_item ? g * const_copy_stride(P.n_const) : 0);
     SweepCtx c;
     c.lt = tid - g * NTG;
+    c.n_const = P.n_const;
+    c.tile_elems = tile_elems;
+    c.err = A.err;
     c.T = T;
     c.L = P.L;
     c.contrib = S.s_contrib;
@@ -1655,7 +1706,7 @@ __global__ void __launch_bounds__(2 * NTG + 128, 1)
     long long cur_item = 0;   // constants of item 0 are staged above
     for (int k = g; k < n_mine; k += 2) {
         const int b = k % NB;
-        const bool ok = mbar_wait_abortable(&S.full[b], (uint32_t)((k / NB) & 1), abort_flag);
+        const bool ok = mbar_wait_abortable(&S.full[2 * b + g], (uint32_t)((k / pair_period) & 1), abort_flag);
         if (named_sync_or(bar_id, NTG, !ok)) {
             if (c.lt == 0) {
                 atomicCAS(A.err, 0, (int)QS_ERR_TIMEOUT);
