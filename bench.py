@@ -577,9 +577,9 @@ def run_gpu(args):
 def profile_case(args):
     """A small fixed workload for ncu captures (no timing, no JSON line):
     tfim28 = 2 Strang steps of the TFIM at 28 qubits with 13-qubit tiles and
-    4-bit groups (the tile shape of the 30q TFIM passes), applied twice;
-    qft28 = the 28-qubit gate-stream QFT with swaps (13-qubit tiles, 4-bit
-    groups), applied twice."""
+    5-bit groups (the tile shape the autotuner picks for the 30q TFIM),
+    applied twice; qft28 = the 28-qubit gate-stream QFT with swaps (the same
+    shape), applied twice."""
     import torch
     import paper_2609_19147_gb300 as qs
     n = 28
@@ -590,7 +590,7 @@ def profile_case(args):
     st = qs.State(n)
     st.provide_scratch()
     for _ in range(2):
-        st.apply(gl, tile_qubits=13, low_qubits=4, group_qubits=4)
+        st.apply(gl, tile_qubits=13, low_qubits=4, group_qubits=5)
     torch.cuda.synchronize()
     st.close()
     return 0

@@ -730,9 +730,11 @@ __device__ __forceinline__ void layer_store(const SweepCtx &c, bool vec, const i
                                             float2 (&a)[1 << R], const float2 *k0, const Grp<R> &G, float scale) {
     layer_fixed<KIND, R, MASK>(a, k0, G);
     if constexpr (KIND == MK_H || KIND == MK_ROT) {
-        const float2 sc = make_float2(scale, scale);
+        if (scale != 1.f) {
+            const float2 sc = make_float2(scale, scale);
 #pragma unroll
-        for (int j = 0; j < (1 << R); ++j) a[j] = __fmul2_rn(a[j], sc);
+            for (int j = 0; j < (1 << R); ++j) a[j] = __fmul2_rn(a[j], sc);
+        }
     }
     store_at<R>(c, vec, o, a);
 }
@@ -831,7 +833,7 @@ __device__ __forceinline__ void rot_layer_regs(float2 (&a)[1 << R], const float2
     }
 }
 
-template <int R, int NT, int PROG, bool VEC>
+template <int R, int NT, int PROG, bool VEC, bool SCALED>
 __device__ __forceinline__ void rot_sweep(const SweepCtx &c, const Sweep &S, int sidx) {
     const int *ts = c.tab_s + sidx * kItemTab;
     const uint64_t *tg = c.tab_g + sidx * kItemTab;
@@ -857,22 +859,22 @@ __device__ __forceinline__ void rot_sweep(const SweepCtx &c, const Sweep &S, int
         const int i0 = item & 31, i1 = 32 + ((item >> 5) & 31), i2 = 64 + ((item >> 10) & 15);
         const int saddr = ts[i0] ^ ts[i1] ^ ts[i2];
         float2 a[1 << R];
-        {
-            int o[1 << R];
-            group_offsets<R>(saddr, gs, o);
-            load_at<R>(c, VEC, o, a);
-        }
+        int o[1 << R];
+        group_offsets<R>(saddr, gs, o);
+        load_at<R>(c, VEC, o, a);
         uint64_t x0 = 0;
         if constexpr (PROG >= 2) x0 = c.tile_gbase | tg[i0] | tg[i1] | tg[i2];
         if constexpr (PROG == 2) dg.apply(x0, a);
         rot_layer_regs<R>(a, t1);
         if constexpr (PROG == 3 || PROG == 4) dg.apply(x0, a);
         if constexpr (PROG == 4) rot_layer_regs<R>(a, t2);
+        if constexpr (SCALED) {
 #pragma unroll
-        for (int j = 0; j < (1 << R); ++j) a[j] = __fmul2_rn(a[j], sc);
-        // the offsets again (cheaper than holding 2^R registers through the ops)
-        int o[1 << R];
-        group_offsets<R>(saddr, gs, o);
+            for (int j = 0; j < (1 << R); ++j) a[j] = __fmul2_rn(a[j], sc);
+        }
+        // with 4-bit groups (112 registers) the offsets are formed again
+        // rather than held through the ops
+        if constexpr (R == 4) group_offsets<R>(saddr, gs, o);
         store_at<R>(c, VEC, o, a);
     }
 }
@@ -881,16 +883,24 @@ template <int R, int NT>
 __device__ __forceinline__ bool run_rot_program(const SweepCtx &c, const Sweep &S, int sidx) {
     const int prog = rot_program<R>(c, S.op_begin, S.op_end);
     if (!prog) return false;
-    const int k = 2 * (prog - 1) + (S.vec ? 1 : 0);
+    const int k = 4 * (prog - 1) + (S.vec ? 2 : 0) + (S.scale != 1.f ? 1 : 0);
     switch (k) {
-        case 0: rot_sweep<R, NT, 1, false>(c, S, sidx); break;
-        case 1: rot_sweep<R, NT, 1, true>(c, S, sidx); break;
-        case 2: rot_sweep<R, NT, 2, false>(c, S, sidx); break;
-        case 3: rot_sweep<R, NT, 2, true>(c, S, sidx); break;
-        case 4: rot_sweep<R, NT, 3, false>(c, S, sidx); break;
-        case 5: rot_sweep<R, NT, 3, true>(c, S, sidx); break;
-        case 6: rot_sweep<R, NT, 4, false>(c, S, sidx); break;
-        default: rot_sweep<R, NT, 4, true>(c, S, sidx); break;
+        case 0: rot_sweep<R, NT, 1, false, false>(c, S, sidx); break;
+        case 1: rot_sweep<R, NT, 1, false, true>(c, S, sidx); break;
+        case 2: rot_sweep<R, NT, 1, true, false>(c, S, sidx); break;
+        case 3: rot_sweep<R, NT, 1, true, true>(c, S, sidx); break;
+        case 4: rot_sweep<R, NT, 2, false, false>(c, S, sidx); break;
+        case 5: rot_sweep<R, NT, 2, false, true>(c, S, sidx); break;
+        case 6: rot_sweep<R, NT, 2, true, false>(c, S, sidx); break;
+        case 7: rot_sweep<R, NT, 2, true, true>(c, S, sidx); break;
+        case 8: rot_sweep<R, NT, 3, false, false>(c, S, sidx); break;
+        case 9: rot_sweep<R, NT, 3, false, true>(c, S, sidx); break;
+        case 10: rot_sweep<R, NT, 3, true, false>(c, S, sidx); break;
+        case 11: rot_sweep<R, NT, 3, true, true>(c, S, sidx); break;
+        case 12: rot_sweep<R, NT, 4, false, false>(c, S, sidx); break;
+        case 13: rot_sweep<R, NT, 4, false, true>(c, S, sidx); break;
+        case 14: rot_sweep<R, NT, 4, true, false>(c, S, sidx); break;
+        default: rot_sweep<R, NT, 4, true, true>(c, S, sidx); break;
     }
     return true;
 }

@@ -1871,6 +1871,7 @@ struct PassBuilder {
     const Diag *diag_src[kMaxDiag] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<const Diag *> count_src;   // MK_DIAGC ops before finalize: cst = index here
     bool count_failed = false;
+    std::vector<std::pair<int, int>> count_luts;   // (offset, entries) of the count tables built
     // A diagonal g0 + gamma c1(x) + h c2(x) (count_form: uniform-angle RZZ sets
     // such as TFIM chains and QAOA cost layers, uniform CZ / CP sets, uniform
     // single-qubit phases) is applied as a count lookup (Sec. 5.1 phase LUT
@@ -1923,6 +1924,7 @@ struct PassBuilder {
         const size_t n_e = dg.pairs.size();
         for (int c2 = 0; c2 <= cf.n_z; ++c2)
             for (size_t c1 = 0; c1 <= n_e; ++c1) cst.push_back(cexp_f(dg.g0 + cf.gamma * (double)c1 + cf.h * c2));
+        count_luts.push_back({lut, (int)((cf.n_z + 1) * (n_e + 1))});
         if (cst.size() & 1) cst.push_back(float2{0.f, 0.f});   // 16-byte aligned data
         const int dat = (int)cst.size();
         auto slot64 = [&](uint64_t v) {
@@ -2012,6 +2014,7 @@ struct PassBuilder {
     void finalize() {
         flush_pending();
         close_sweep();
+        std::vector<double> sw_scale(tp.n_sweeps, 1.0);
         // convert tile-local bit references to group indices, fill QFT
         // tables, fold butterfly normalisations, mark diagonal factors that
         // depend on the group bits
@@ -2072,7 +2075,37 @@ struct PassBuilder {
                     }
                 }
             }
-            sw.scale = (float)(std::pow(kSqrtHalf, (double)n_butterfly) * rot_scale);
+            sw_scale[s] = std::pow(kSqrtHalf, (double)n_butterfly) * rot_scale;
+        }
+        // The sweeps' scale factors commute with every op, so the pass applies
+        // their product once: folded into its first count table when it has one
+        // (the table's entries are multiplied in FP64 and rounded once), else
+        // on its last sweep.
+        // (Kept per sweep when the unscaled values could leave FP32's range:
+        // any partial product outside [2^-40, 2^40].)
+        double total = 1.0;
+        bool foldable = true;
+        int last = -1;
+        for (int s = 0; s < tp.n_sweeps; ++s) {
+            total *= sw_scale[s];
+            if (!(total >= 0x1p-40 && total <= 0x1p40)) foldable = false;
+            if (!tp.sweeps[s].dense) last = s;
+        }
+        if (foldable && last >= 0) {
+            for (int s = 0; s < tp.n_sweeps; ++s) tp.sweeps[s].scale = 1.f;
+            if (total != 1.0) {
+                if (!count_luts.empty()) {
+                    const auto &lt = count_luts.front();
+                    for (int e = 0; e < lt.second; ++e) {
+                        float2 &v = cst[lt.first + e];
+                        v = float2{(float)((double)v.x * total), (float)((double)v.y * total)};
+                    }
+                } else {
+                    tp.sweeps[last].scale = (float)total;
+                }
+            }
+        } else {
+            for (int s = 0; s < tp.n_sweeps; ++s) tp.sweeps[s].scale = (float)sw_scale[s];
         }
         merge_layers();
         tp.n_const = (int)cst.size();

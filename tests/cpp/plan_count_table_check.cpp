@@ -8,7 +8,9 @@
 // single-bit increments and packed inner-edge counts) must equal
 // exp(i phase(x)), with phase(x) evaluated from the gate definitions:
 // RZZ(t) = exp(-i t/2 Z Z) and RZ(p) = exp(-i p/2 Z) on the index bit
-// n - 1 - q of qubit q.  Prints "OK <checked>" or the first mismatch.
+// n - 1 - q of qubit q, times one positive factor per table (the planner
+// folds the pass's normalisation factors into its first count table).
+// Prints "OK <checked>" or the first mismatch.
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -98,6 +100,7 @@ static int run_case(int n, int degree_edges, bool cz, unsigned seed, long long &
                 std::vector<uint64_t> dat(R + 3 + 2 * op.a);
                 std::memcpy(dat.data(), cs + op.lo, dat.size() * 8);
                 const uint64_t full = (n == 64) ? ~0ull : ((1ull << n) - 1);
+                double scale = -1.0;   // the table's common factor, from its first entry
                 for (int trial = 0; trial < 64; ++trial) {
                     const uint64_t x0 = rng() & full & ~gm;
                     int c0 = op.p * __builtin_popcountll(x0 & dat[R + 1]);
@@ -120,8 +123,13 @@ static int run_case(int n, int degree_edges, bool cz, unsigned seed, long long &
                         const uint64_t qw = j < 16 ? op.cmask : op.cval;
                         c += (int)((qw >> (4 * (j & 15))) & 15);
                         const float2 t = cs[op.cst + c];
-                        const std::complex<double> want = std::polar(1.0, phase(x));
+                        if (scale < 0) scale = std::abs(std::complex<double>(t.x, t.y));
+                        const std::complex<double> want = std::polar(scale, phase(x));
                         const double err2 = std::abs(std::complex<double>(t.x, t.y) - want);
+                        if (!(scale > 0x1p-40 && scale < 0x1p40)) {
+                            std::printf("TABLE FACTOR %g out of range\n", scale);
+                            return 1;
+                        }
                         if (!(err2 < 1e-6)) {
                             std::printf("MISMATCH n=%d cz=%d x=%llx idx=%d got=(%g,%g) want=(%g,%g)\n", n, (int)cz,
                                         (unsigned long long)x, c, t.x, t.y, want.real(), want.imag());

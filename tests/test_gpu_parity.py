@@ -376,3 +376,33 @@ def test_count_table_diagonals(n):
     assert "DIAGC=" in text, text
     psi0 = W.random_state(n, 5)
     _assert_close(_run(n, gl, psi0), _ref(n, gl, psi0))
+
+
+def test_tile_pipeline_deterministic_across_autotune_shapes():
+    # the 30q TFIM (10 Strang steps) under every shape the autotuner tries,
+    # back to back on one state as the autotuner runs them: each shape applied
+    # three times from the same input gives bit-identical states (a race in
+    # the tile pipeline shows up as a difference), and the shapes agree with
+    # one another to float rounding; the norm stays 1
+    n = 30
+    gl = qs.CGates(W.tfim_gates(n, 10, 0.05, 1.0, W.tfim_fields(n, 3), order=2))
+    st = qs.State(n)
+    st.provide_scratch()
+    idx = torch.arange(0, 1 << n, 4099, device="cuda")
+    ref = None
+    for T, L, R in [(0, 0, 0), (12, 4, 4), (12, 4, 5), (12, 5, 4), (12, 5, 5), (13, 4, 4), (13, 4, 5),
+                    (13, 5, 4), (13, 5, 5)]:
+        outs = []
+        for _ in range(3):
+            st.zero()
+            st.apply(gl, tile_qubits=T, low_qubits=L, group_qubits=R)
+            outs.append(st.tensor[0][idx].clone())
+        for o in outs[1:]:
+            assert torch.equal(o, outs[0]), (T, L, R)
+        assert abs(float(torch.linalg.vector_norm(st.tensor[0]).item()) - 1) < 1e-5
+        if ref is None:
+            ref = outs[0]
+        else:
+            d = float((outs[0] - ref).abs().max().item())
+            assert d < 2e-6, (T, L, R, d)
+    st.close()
