@@ -461,6 +461,9 @@ struct SweepCtx {
     const uint64_t *tab_g;   // smem: per-sweep item-address tables (global index bits)
     uint64_t tile_gbase;     // global index of tile-local 0 (within the state)
     int lt;                  // thread index within the threads that share the sweeps
+    uint32_t tmem;           // tensor-memory base of the dense tensor-core sweeps
+    uint64_t *mma_bar;       // smem mbarrier their MMAs complete on
+    uint32_t *mma_phase;     // smem: its current phase parity
     int n_const;             // constants staged (device checks)
     int tile_elems;          // 2^T (device checks)
     int *err;                // device status word (device checks)
@@ -1083,13 +1086,6 @@ __device__ __forceinline__ void dense_fp32(const SweepCtx &c, const Sweep &S, in
 // x rounded to TF32 (10 explicit mantissa bits, ties away from zero) with
 // integer operations; x - hi is then exact in FP32
 __device__ __forceinline__ uint32_t tf32_hi(float x) { return (__float_as_uint(x) + 0x1000u) & 0xffffe000u; }
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
@@ -1102,98 +1098,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float2 v) {
     uint32_t r;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(v.y), "f"(v.x));
     return r;
-}
-
-// Tensor cores, as the real GEMM Y^T = X^T B with X^T the columns x 64 matrix
-// of (re, im) parts and B the 64 x 64 real form of U^T.  A warp takes 16 * MT
-// columns (MT m16 tiles) and all 64 outputs (8 n8 tiles).  Operand order
-// within a TF32 k-step s (block rows 4s..4s+3): k = 0-3 real parts, 4-7
-// imaginary parts, so that one 8-byte load gives a lane both halves of an
-// amplitude; n = 2 * output row + (re, im), so that the accumulator pair of a
-// lane is one output amplitude.  Split precision: X = X_hi + X_lo in TF32
-// (both rounded to nearest here), U = U_hi + U_lo (rounded on the host from
-// FP64); the product keeps U_hi X_hi + U_hi X_lo + U_lo X_hi.
-template <int MT, int NT>
-__device__ __forceinline__ void dense_tf32x3(const SweepCtx &c, const Sweep &S, int sidx) {
-    const int lane = c.lt & 31, warp = c.lt >> 5;
-    const int q = lane & 3, gq = lane >> 2;
-    const bool lane_im = (gq & 1) != 0;   // this lane's B column is an imaginary part
-    const int rlo = ((q & 1) ? c.contrib[S.gbit[0]] : 0) ^ ((q & 2) ? c.contrib[S.gbit[1]] : 0);
-    const int g2 = c.contrib[S.gbit[2]], g3 = c.contrib[S.gbit[3]], g4 = c.contrib[S.gbit[4]];
-    int rhi[8];
-#pragma unroll
-    for (int s = 0; s < 8; ++s) rhi[s] = ((s & 1) ? g2 : 0) ^ ((s & 2) ? g3 : 0) ^ ((s & 4) ? g4 : 0);
-    // U[4t + lane/8][4s + q] as (hi, lo) at pair (4t + lane/8) * 32 + 4 (s ^ f) + q,
-    // f = bit 0 of the row
-    const float4 *Ut = reinterpret_cast<const float4 *>(c.cs + S.dcst);
-    const int ub = (lane >> 3) * 32 + q, uf = (lane >> 3) & 1;
-    const int ncols = 1 << (c.T - 5);
-    const int *ts = c.tab_s + sidx * kItemTab;
-    for (int mb = warp * 16 * MT; mb < ncols; mb += (NT / 32) * 16 * MT) {
-        int co[MT][2];
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt) {
-            co[mt][0] = dense_coloff(ts, mb + 16 * mt + gq) ^ rlo;
-            co[mt][1] = dense_coloff(ts, mb + 16 * mt + gq + 8) ^ rlo;
-        }
-        // U_hi X_hi and the two small cross terms accumulate apart: the tensor
-        // core's FP32 accumulation truncates, and chaining the cross terms
-        // onto the large sum would truncate at full magnitude 3x as often
-        // (a norm shrink that compounds over many blocks)
-        float acc[MT][8][4], acs[MT][8][4];
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int t = 0; t < 8; ++t)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[mt][t][e] = acs[mt][t][e] = 0.f;
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            uint32_t ah[MT][4], al[MT][4];
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt) {
-                const float2 x0 = c.buf[rhi[s] ^ co[mt][0]], x1 = c.buf[rhi[s] ^ co[mt][1]];
-                const float v[4] = {x0.x, x1.x, x0.y, x1.y};
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    ah[mt][e] = tf32_hi(v[e]);
-                    // rounded too: the tensor core would truncate (a bias toward
-                    // zero that compounds over many blocks)
-                    al[mt][e] = tf32_hi(v[e] - __uint_as_float(ah[mt][e]));
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const float4 u = Ut[ub + 128 * t + 4 * (s ^ uf)];   // (hi.re, hi.im, lo.re, lo.im)
-                const uint32_t bh0 = __float_as_uint(lane_im ? u.y : u.x);
-                const uint32_t bh1 = __float_as_uint(lane_im ? u.x : -u.y);
-                const uint32_t bl0 = __float_as_uint(lane_im ? u.w : u.z);
-                const uint32_t bl1 = __float_as_uint(lane_im ? u.z : -u.w);
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt) {
-                    mma_tf32(acs[mt][t], al[mt], bh0, bh1);
-                    mma_tf32(acs[mt][t], ah[mt], bl0, bl1);
-                    mma_tf32(acc[mt][t], ah[mt], bh0, bh1);
-                }
-            }
-        }
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int t = 0; t < 8; ++t)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[mt][t][e] += acs[mt][t][e];
-        // every load of these columns precedes the stores (in place); tiles of
-        // fewer than 16 columns (T < 9) alias columns >= ncols onto real ones,
-        // which only the lanes of real columns store
-#pragma unroll
-        for (int t = 0; t < 8; ++t)
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt) {
-                if (mb + 16 * mt + gq < ncols) c.buf[rhi[t] ^ co[mt][0]] = make_float2(acc[mt][t][0], acc[mt][t][1]);
-                if (mb + 16 * mt + gq + 8 < ncols) c.buf[rhi[t] ^ co[mt][1]] = make_float2(acc[mt][t][2], acc[mt][t][3]);
-            }
-    }
 }
 
 // Tensor cores in BF16 (m16n8k16): k = 2 * block row + (re, im) over rows
@@ -1252,20 +1156,198 @@ __device__ __forceinline__ void dense_bf16(const SweepCtx &c, const Sweep &S, in
     }
 }
 
+// ---------------------------------------------------------------------------
+// 3xTF32 dense blocks on the fifth-generation tensor cores (tcgen05)
+//
+// The block's 32 x 32 complex matrix U times the tile viewed as X, 32 rows (the
+// block's 5 group bits) by up to 256 columns (the item bits).  Thread m (of
+// 256) gathers column m from shared memory at the sweep's XOR offsets (any
+// five tile bits), splits each real and imaginary part into TF32 hi + lo
+// (round to nearest) and writes them into tensor memory as the MMA's A
+// operand, row m: columns [0, 32) hi re, [32, 64) hi im, [64, 96) lo re,
+// [96, 128) lo im, 256 columns per M-tile of 128 rows.  B is U's real and
+// imaginary parts (hi and lo, TF32-rounded on the host from FP64), each a
+// 32 x 32 K-major matrix in shared memory with the 128-byte swizzle.  One
+// thread issues, per M-tile and K-step of 8,
+//   Dre += Xre Ure - Xim Uim,   Dim += Xre Uim + Xim Ure
+// (the minus sign through the descriptor's negate-B bit), the hi x hi products
+// into one pair of accumulators and the two small cross terms (lo x hi, hi x
+// lo) into another: the tensor core's FP32 accumulation truncates, so chaining
+// the small terms onto the large sum would bias the result toward zero.  The
+// accumulators (FP32, in tensor memory) come back with tcgen05.ld, are added
+// and stored to the same positions of the tile.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 1024-byte
+// atoms of 8 rows x 128 bytes (stride 1024 bytes), version 1
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3fff) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major,
+// N and M, optional negation of B
+__device__ __forceinline__ constexpr uint32_t tc_idesc_tf32(int M, int N, bool neg_b) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((neg_b ? 1u : 0u) << 14) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                            int accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+        "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+        "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+constexpr int kTmemCols = 512;   // two M-tiles x (A hi, A lo, D main, D cross) x (re, im) x 32
+
+// returns false (on every thread) when the MMAs did not complete in time
 template <int NT>
-__device__ __forceinline__ void run_dense(const SweepCtx &c, const Sweep &S, int sidx) {
+__device__ __forceinline__ bool dense_tc_tf32x3(const SweepCtx &c, const Sweep &S, int sidx) {
+    static_assert(NT == 256, "two warpgroups: one per M-tile of 128 columns");
+    const int m = c.lt, warp = m >> 5, mt = m >> 7;
+    const int ncols = 1 << (c.T - 5);
+    const int *ts = c.tab_s + sidx * kItemTab;
+    int g[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) g[q] = c.contrib[S.gbit[q]];
+    const bool mine = m < ncols;
+    const int co = mine ? dense_coloff(ts, m) : 0;
+    const uint32_t lane_col = c.tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(256 * mt);
+    {
+        uint32_t hr[32], hi[32], lr[32], li[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            const float2 x = mine ? c.buf[co ^ dense_rowoff(g, r)] : make_float2(0.f, 0.f);
+            hr[r] = tf32_hi(x.x);
+            hi[r] = tf32_hi(x.y);
+            lr[r] = tf32_hi(x.x - __uint_as_float(hr[r]));
+            li[r] = tf32_hi(x.y - __uint_as_float(hi[r]));
+        }
+        tc_st32(lane_col + 0, hr);
+        tc_st32(lane_col + 32, hi);
+        tc_st32(lane_col + 64, lr);
+        tc_st32(lane_col + 96, li);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    if (c.lt == 0) {
+        tc_fence_after();
+        // B matrices 0 Re U hi, 1 Im U hi, 2 Re U lo, 3 Im U lo (4 KB each)
+        const uint32_t sb = smem_u32(c.cs + S.dcst);
+        constexpr uint32_t id = tc_idesc_tf32(128, 32, false), idn = tc_idesc_tf32(128, 32, true);
+        const int n_mt = ncols > 128 ? 2 : 1;
+        for (int t = 0; t < n_mt; ++t) {
+            const uint32_t b0 = c.tmem + (uint32_t)(256 * t);
+            const uint32_t ahr = b0, ahi = b0 + 32, alr = b0 + 64, ali = b0 + 96;
+            const uint32_t dmr = b0 + 128, dmi = b0 + 160, dcr = b0 + 192, dci = b0 + 224;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t ko = 8 * k;
+                const uint64_t ure = tc_smem_desc(sb + 32 * k), uim = tc_smem_desc(sb + 4096 + 32 * k);
+                const uint64_t urel = tc_smem_desc(sb + 8192 + 32 * k), uiml = tc_smem_desc(sb + 12288 + 32 * k);
+                const int acc = k > 0;
+                tc_mma_tf32(dmr, ahr + ko, ure, id, acc);
+                tc_mma_tf32(dmr, ahi + ko, uim, idn, 1);
+                tc_mma_tf32(dmi, ahr + ko, uim, id, acc);
+                tc_mma_tf32(dmi, ahi + ko, ure, id, 1);
+                tc_mma_tf32(dcr, alr + ko, ure, id, acc);
+                tc_mma_tf32(dcr, ali + ko, uim, idn, 1);
+                tc_mma_tf32(dcr, ahr + ko, urel, id, 1);
+                tc_mma_tf32(dcr, ahi + ko, uiml, idn, 1);
+                tc_mma_tf32(dci, alr + ko, uim, id, acc);
+                tc_mma_tf32(dci, ali + ko, ure, id, 1);
+                tc_mma_tf32(dci, ahr + ko, uiml, id, 1);
+                tc_mma_tf32(dci, ahi + ko, urel, id, 1);
+            }
+        }
+        tc_commit(c.mma_bar);
+    }
+    const bool ok = mbar_wait_bounded(c.mma_bar, *c.mma_phase);
+    if (__syncthreads_or(!ok)) return false;
+    tc_fence_after();
+    if (c.lt == 0) *c.mma_phase ^= 1u;   // read by every thread above; written after the barrier
+    {
+        uint32_t dr[32], di[32], er[32], ei[32];
+        tc_ld32(lane_col + 128, dr);
+        tc_ld32(lane_col + 160, di);
+        tc_ld32(lane_col + 192, er);
+        tc_ld32(lane_col + 224, ei);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (mine) {
+#pragma unroll
+            for (int r = 0; r < 32; ++r)
+                c.buf[co ^ dense_rowoff(g, r)] = make_float2(__uint_as_float(dr[r]) + __uint_as_float(er[r]),
+                                                             __uint_as_float(di[r]) + __uint_as_float(ei[r]));
+        }
+    }
+    tc_fence_before();
+    return true;
+}
+
+// tensor memory for the dense sweeps: allocated by warp 0 (all of it: one
+// dense CTA per SM), the base address broadcast through shared memory
+__device__ __forceinline__ uint32_t tc_alloc(uint32_t *slot) {
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                     "n"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    return *slot;
+}
+__device__ __forceinline__ void tc_dealloc(uint32_t base) {
+    tc_fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "n"(kTmemCols));
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ bool run_dense(const SweepCtx &c, const Sweep &S, int sidx) {
     // two m16 tiles per warp when every warp still gets work
     const bool two = (1 << (c.T - 5)) >= 32 * (NT / 32);
     switch (S.dense) {
         case DS_FP32: dense_fp32<NT>(c, S, sidx); break;
-        case DS_TF32X3:   // one m16 tile per warp: two accumulator sets fit in registers
-            dense_tf32x3<1, NT>(c, S, sidx);
+        case DS_TF32X3:
+            if constexpr (NT == 256) return dense_tc_tf32x3<NT>(c, S, sidx);
             break;
         default:
             if (two) dense_bf16<2, NT>(c, S, sidx);
             else dense_bf16<1, NT>(c, S, sidx);
             break;
     }
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -1303,6 +1385,7 @@ __device__ __forceinline__ void tile_coords(const TmaGeom &g, long long ti, long
 //   [64, 176)    hb[14], contrib[14]
 //   [176, 240)   empty[8]  mbarriers: consumers done with buffer b
 //   [240, 244)   abort flag
+//   [244, 252)   tensor-memory base, phase of the dense sweeps' MMA barrier
 //   off_desc     sweeps | micro-ops | diagonals | item tables (global bits, smem offsets)
 //   off_consts   constants (cs_copies consecutive copies of n_const entries,
 //                each copy 128-byte aligned)
@@ -1311,6 +1394,7 @@ __device__ __forceinline__ void tile_coords(const TmaGeom &g, long long ti, long
 struct TileShared {
     uint64_t *full, *empty;
     int *abort_flag;
+    uint32_t *tmem_slot, *mma_phase;
     int *s_hb, *s_contrib;
     Sweep *s_sweeps;
     MicroOp *s_micro;
@@ -1336,6 +1420,8 @@ __device__ __forceinline__ TileShared stage_tile_pass(const TileArgs &A, unsigne
     S.s_contrib = S.s_hb + kMaxTileBits;
     S.empty = reinterpret_cast<uint64_t *>(sm + 176);
     S.abort_flag = reinterpret_cast<int *>(sm + 240);
+    S.tmem_slot = reinterpret_cast<uint32_t *>(sm + 244);
+    S.mma_phase = reinterpret_cast<uint32_t *>(sm + 248);
     S.s_sweeps = reinterpret_cast<Sweep *>(sm + A.off_desc);
     const TilePass &P = *A.pass;
     const int n_sweeps = P.n_sweeps, n_micro = P.n_micro;
@@ -1381,6 +1467,7 @@ __device__ __forceinline__ TileShared stage_tile_pass(const TileArgs &A, unsigne
             mbar_init(&S.empty[b], 1);
         }
         *S.abort_flag = 0;
+        *S.mma_phase = 0;
         fence_mbar_init();
     }
     __syncthreads();
@@ -1494,6 +1581,12 @@ __global__ void __launch_bounds__(NT, MINB)
 
     SweepCtx c;
     c.lt = tid;
+    c.tmem = 0;
+    c.mma_bar = &S.empty[0];   // the empty barriers are unused by this kernel
+    c.mma_phase = S.mma_phase;
+    if constexpr (DENSE) {
+        if (A.tmem) c.tmem = tc_alloc(S.tmem_slot);
+    }
     c.n_const = P.n_const;
     c.tile_elems = tile_elems;
     c.err = A.err;
@@ -1521,14 +1614,23 @@ __global__ void __launch_bounds__(NT, MINB)
             load(k + D);
         }
         if (tid == 0 && A.use_tma && k + D + PF < n_mine) l2pf(k + D + PF);
-        const bool ok = mbar_wait_bounded(&full[k % NB], (uint32_t)((k / NB) & 1));
-        if (__syncthreads_or(!ok)) {
+        // a bounded wait that ran out (here or in a dense sweep's MMAs): record it,
+        // let this CTA's copies in flight land, free the tensor memory, return
+        auto abort_pass = [&](bool mma_pending) {
             if (tid == 0) {
                 atomicCAS(A.err, 0, (int)QS_ERR_TIMEOUT);
                 for (int kk = k + 1; kk < k + D && kk < n_mine; ++kk)
                     mbar_wait_bounded(&full[kk % NB], (uint32_t)((kk / NB) & 1));
                 bulk_wait_all0();
+                if (mma_pending) mbar_wait_bounded(c.mma_bar, *c.mma_phase);   // the MMAs, once more
             }
+            if constexpr (DENSE) {
+                if (A.tmem) tc_dealloc(c.tmem);
+            }
+        };
+        const bool ok = mbar_wait_bounded(&full[k % NB], (uint32_t)((k / NB) & 1));
+        if (__syncthreads_or(!ok)) {
+            abort_pass(false);
             return;
         }
         const long long t = blockIdx.x + (long long)k * stride;
@@ -1547,8 +1649,14 @@ __global__ void __launch_bounds__(NT, MINB)
         c.buf = buf0 + (size_t)(k % NB) * tile_elems;
         c.tile_gbase = A.needs_gidx ? tile_base(A, ti) : 0;
         for (int s = 0; s < n_sweeps; ++s) {
-            if (DENSE && s_sweeps[s].dense) run_dense<NT>(c, s_sweeps[s], s);
-            else run_sweep<R, NT, KS>(c, s_sweeps[s], s);
+            if (DENSE && s_sweeps[s].dense) {
+                if (!run_dense<NT>(c, s_sweeps[s], s)) {   // uniform over the CTA
+                    abort_pass(true);
+                    return;
+                }
+            } else {
+                run_sweep<R, NT, KS>(c, s_sweeps[s], s);
+            }
             if (s + 1 < n_sweeps) __syncthreads();
         }
         fence_proxy_async();   // generic-proxy writes before the async-proxy store
@@ -1556,6 +1664,9 @@ __global__ void __launch_bounds__(NT, MINB)
         if (tid == 0) store(k);
     }
     if (tid == 0) bulk_wait_all0();
+    if constexpr (DENSE) {
+        if (A.tmem) tc_dealloc(c.tmem);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1700,6 +1811,9 @@ __global__ void __launch_bounds__(2 * NTG + 128, 1)
     float2 *cs = S.cs + (per_item ? g * const_copy_stride(P.n_const) : 0);
     SweepCtx c;
     c.lt = tid - g * NTG;
+    c.tmem = 0;
+    c.mma_bar = nullptr;
+    c.mma_phase = nullptr;
     c.n_const = P.n_const;
     c.tile_elems = tile_elems;
     c.err = A.err;

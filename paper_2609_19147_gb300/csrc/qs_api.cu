@@ -417,8 +417,10 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
     for (int b = 0; b < st->n; ++b)
         if (!((tilebits >> b) & 1)) A.outer_pos[A.n_outer++] = b;
     A.err = st->d_err;
-    for (int k = 0; k < tp.n_sweeps; ++k)
+    for (int k = 0; k < tp.n_sweeps; ++k) {
         if (tp.sweeps[k].dense) A.dense = 1;
+        if (tp.sweeps[k].dense == DS_TF32X3) A.tmem = 1;
+    }
     A.kset = 1;
     for (int k = 0; k < tp.n_micro; ++k) {
         const MicroOp &mo = tp.micro[k];
@@ -440,7 +442,8 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
         off += tp.n_sweeps * (int)sizeof(Sweep) + tp.n_micro * (int)sizeof(MicroOp) +
                kMaxDiag * (int)sizeof(DiagDesc);
         off += tp.n_sweeps * kItemTab * (8 + 4);   // item-address tables
-        off = al(off, 128);
+        // dense tensor-core operands in the constants need 1024-byte alignment
+        off = al(off, A.dense ? 1024 : 128);
         A.off_consts = off;
         // one item's constants (per copy, 16-entry aligned as the kernel indexes them)
         off = al(off + const_copies * al(tp.n_const, 16) * 8, 128);

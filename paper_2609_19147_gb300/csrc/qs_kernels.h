@@ -43,6 +43,7 @@ struct TileArgs {
     int kset;                  // 1: every micro-op is a 1q / layer / diagonal op (KS_LAYER kernels)
     int needs_gidx;            // 1: some micro-op reads global indices (controls, diagonals, QFT)
     int ws;                    // 1: warp-specialised kernel (a producer warp and two consumer groups)
+    int tmem;                  // 1: dense sweeps on the tcgen05 tensor cores (tensor memory allocated)
     TmaGeom geo;
     int *err;                  // device status word
 };

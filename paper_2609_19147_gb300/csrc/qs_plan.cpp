@@ -1605,7 +1605,8 @@ struct PassBuilder {
         for (int tb = 0; tb < T; ++tb)
             if (!((used >> tb) & 1)) cols.push_back(tb);
         int order[5] = {0, 1, 2, 3, 4};   // group bit q is G[order[q]]
-        if (dprec == DS_FP32) {
+        if (dprec == DS_FP32 || dprec == DS_TF32X3) {
+            // a thread per column (its 32 amplitudes at the group bits' offsets)
             for (int q = 0; q < 5; ++q) sw.gbit[q] = G[q];
             sw.vec = 0;
             choose_item_bits(tp, sw);
@@ -1688,16 +1689,24 @@ struct PassBuilder {
         if (dprec == DS_FP32) {
             for (int e = 0; e < 32 * 32; ++e) cst.push_back(float2{(float)U[e].real(), (float)U[e].imag()});
         } else if (dprec == DS_TF32X3) {
-            std::vector<float2> t(2 * 32 * 32, float2{0.f, 0.f});
+            // tcgen05 B operands: Re U hi, Im U hi, Re U lo, Im U lo, each 32 x 32
+            // K-major (row = output i, 32 inputs j of 4 bytes) with the 128-byte
+            // swizzle (16-byte chunk j / 4 of row i at chunk (j / 4) ^ (i % 8)),
+            // starting on a 1024-byte boundary of the constant table
+            while (cst.size() % 128) cst.push_back(float2{0.f, 0.f});
+            sw.dcst = (int)cst.size();
+            std::vector<float> t(4 * 32 * 32, 0.f);
             for (int i = 0; i < 32; ++i)
                 for (int j = 0; j < 32; ++j) {
                     const cd u = U[i * 32 + j];
                     const float hr = tf32_round(u.real()), hm = tf32_round(u.imag());
-                    const int e = 2 * (i * 32 + (j ^ ((i & 1) << 2)));
-                    t[e] = float2{hr, hm};
-                    t[e + 1] = float2{tf32_round(u.real() - (double)hr), tf32_round(u.imag() - (double)hm)};
+                    const int e = i * 32 + (((j >> 2) ^ (i & 7)) << 2) + (j & 3);
+                    t[e] = hr;
+                    t[1024 + e] = hm;
+                    t[2048 + e] = tf32_round(u.real() - (double)hr);
+                    t[3072 + e] = tf32_round(u.imag() - (double)hm);
                 }
-            cst.insert(cst.end(), t.begin(), t.end());
+            for (int e = 0; e < 4 * 1024; e += 2) cst.push_back(float2{t[e], t[e + 1]});
         } else {
             // m16n8k16 B operand: k = 2 * row + (0: re, 1: im) within a 16-wide
             // k-step, n = 2 * out_row + (0: re, 1: im) within an 8-wide n-tile

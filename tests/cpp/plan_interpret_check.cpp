@@ -533,11 +533,17 @@ class TileRun {
             for (int o = 0; o < 32; ++o)
                 for (int i = 0; i < 32; ++i) put_complex(o, i, K(S.dcst + o * 32 + i));
         } else if (S.dense == DS_TF32X3) {
+            // tensor-core B operands: Re U hi, Im U hi, Re U lo, Im U lo, each 32 x 32
+            // floats K-major (row = output o), 128-byte swizzle, 1024-byte aligned
+            need(S.dcst % 128 == 0, "tensor-core operands not on a 1024-byte boundary");
+            auto f = [&](int mat, int o, int i) {
+                const long e = 1024L * mat + o * 32 + (((i >> 2) ^ (o & 7)) << 2) + (i & 3);
+                const float2 v = Kraw(S.dcst + e / 2);
+                return (double)((e & 1) ? v.y : v.x);
+            };
             for (int o = 0; o < 32; ++o)
-                for (int i = 0; i < 32; ++i) {
-                    const long e = S.dcst + 2L * (o * 32 + (i ^ ((o & 1) << 2)));
-                    put_complex(o, i, K(e) + K(e + 1));
-                }
+                for (int i = 0; i < 32; ++i)
+                    put_complex(o, i, C(f(0, o, i) + f(2, o, i), f(1, o, i) + f(3, o, i)));
         } else {
             // m16n8k16 B fragments (PTX ISA): register h of lane l holds k = 2 (l % 4) + 8 h + {0, 1},
             // n = l / 4; k-step s covers input rows 8 s .. 8 s + 7, n-tile t output rows 4 t .. 4 t + 3
