@@ -579,7 +579,8 @@ def profile_case(args):
     tfim28 = 2 Strang steps of the TFIM at 28 qubits with 13-qubit tiles and
     5-bit groups (the tile shape the autotuner picks for the 30q TFIM),
     applied twice; qft28 = the 28-qubit gate-stream QFT with swaps (the same
-    shape), applied twice."""
+    shape), applied twice; dense28 = the tfim28 circuit as dense 5-qubit
+    blocks in 3xTF32 on the tensor cores, applied twice."""
     import torch
     import paper_2609_19147_gb300 as qs
     n = 28
@@ -590,7 +591,10 @@ def profile_case(args):
     st = qs.State(n)
     st.provide_scratch()
     for _ in range(2):
-        st.apply(gl, tile_qubits=13, low_qubits=4, group_qubits=5)
+        if args.profile_case == "dense28":
+            st.apply(gl, dense="tf32x3")
+        else:
+            st.apply(gl, tile_qubits=13, low_qubits=4, group_qubits=5)
     torch.cuda.synchronize()
     st.close()
     return 0
@@ -607,7 +611,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the grads / dense / QAOA / 28q suite rows")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 25-qubit end-to-end workload sweep")
-    ap.add_argument("--profile-case", choices=["tfim28", "qft28"], default=None,
+    ap.add_argument("--profile-case", choices=["tfim28", "qft28", "dense28"], default=None,
                     help="run a small fixed workload for ncu captures instead of the benchmark")
     args = ap.parse_args()
     if args.profile_case:
