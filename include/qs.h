@@ -236,11 +236,16 @@ typedef struct qs_graph {
  * H_M = sum_q X_q).  For graph g and angle set a (n_sets per graph):
  *   |psi> = prod_{l=1..p} e^{-i beta_l H_M} e^{-i gamma_l H_C} |+>^n,
  *   out[g * n_sets + a] = <psi|H_C|psi>   (FP64 accumulation).
- * gammas / betas: n_graphs x n_sets x p doubles (row-major).  Graphs with
- * n <= 14 run in one persistent launch with the state in shared memory;
- * larger ones (n <= 30) run through the fused tile-pass executor, one graph
- * (all its angle sets as a batch) at a time.  Limits: p <= 16, <= 64 edges
- * per graph.  Allocates its own device memory; synchronous on cuda_stream. */
+ * gammas / betas: n_graphs x n_sets x p doubles (row-major).  Every
+ * instance with n <= 24 runs in one persistent launch that needs no host
+ * planning: CTAs take instances (largest first) from a device work counter;
+ * a state with n <= 14 stays in the CTA's shared memory, a larger one lives
+ * in the CTA's slot of device memory and moves through shared memory in
+ * 2^14-amplitude tiles, two passes per layer.  Graphs with 24 < n <= 30 run
+ * through the fused tile-pass executor, one graph (all its angle sets as a
+ * batch) at a time.  Limits: p <= 16, <= 64 edges per graph.  Allocates its
+ * own device memory (one state of the largest n above 14 per SM for the
+ * persistent launch); synchronous on cuda_stream. */
 qs_status qs_qaoa_maxcut(const qs_graph *graphs, size_t n_graphs, int n_sets, int p, const double *gammas,
                          const double *betas, double *out, void *cuda_stream);
 

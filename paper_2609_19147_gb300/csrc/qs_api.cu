@@ -1937,13 +1937,18 @@ qs_status qs_qaoa_maxcut(const qs_graph *graphs, size_t n_graphs, int n_sets, in
     if (s != QS_OK) return s;
     const size_t n_out = n_graphs * (size_t)n_sets;
 
-    // ---- small states: one persistent launch over all of them ----
+    // ---- every instance with n <= 24: one persistent launch, largest first ----
     std::vector<QaoaItem> items;
     std::vector<uint32_t> masks;
     std::vector<float2> luts, mix;
-    for (size_t g = 0; g < n_graphs; ++g) {
+    std::vector<size_t> order(n_graphs);
+    for (size_t g = 0; g < n_graphs; ++g) order[g] = g;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return graphs[a].n > graphs[b].n; });
+    int n_slot = 0;   // largest n kept in a device-memory slot
+    for (size_t g : order) {
         const qs_graph &G = graphs[g];
-        if (G.n > kQaoaMaxSmallN) continue;
+        if (G.n > kQaoaMaxPersistentN) continue;
+        if (G.n > kQaoaMaxSmallN) n_slot = std::max(n_slot, G.n);
         const int eo = (int)masks.size();
         for (int e = 0; e < G.n_edges; ++e)
             masks.push_back((1u << (G.n - 1 - G.edges[2 * e])) | (1u << (G.n - 1 - G.edges[2 * e + 1])));
@@ -1970,7 +1975,7 @@ qs_status qs_qaoa_maxcut(const qs_graph *graphs, size_t n_graphs, int n_sets, in
     if (!items.empty()) {
         QaoaItem *d_items = nullptr;
         uint32_t *d_masks = nullptr;
-        float2 *d_luts = nullptr, *d_mix = nullptr;
+        float2 *d_luts = nullptr, *d_mix = nullptr, *d_slots = nullptr;
         double *d_out = nullptr;
         int *d_counter = nullptr;
         auto cleanup = [&]() {
@@ -1980,13 +1985,18 @@ qs_status qs_qaoa_maxcut(const qs_graph *graphs, size_t n_graphs, int n_sets, in
             cudaFree(d_mix);
             cudaFree(d_out);
             cudaFree(d_counter);
+            cudaFree(d_slots);
         };
+        const int grid = (int)std::min<size_t>(items.size(), (size_t)g_num_sms[dev]);
+        const long long slot_elems = n_slot ? (1ll << n_slot) : 0;
         bool okm = cudaMalloc(&d_items, items.size() * sizeof(QaoaItem)) == cudaSuccess &&
                    cudaMalloc(&d_masks, std::max<size_t>(1, masks.size()) * sizeof(uint32_t)) == cudaSuccess &&
                    cudaMalloc(&d_luts, luts.size() * sizeof(float2)) == cudaSuccess &&
                    cudaMalloc(&d_mix, mix.size() * sizeof(float2)) == cudaSuccess &&
                    cudaMalloc(&d_out, n_out * sizeof(double)) == cudaSuccess &&
-                   cudaMalloc(&d_counter, sizeof(int)) == cudaSuccess;
+                   cudaMalloc(&d_counter, sizeof(int)) == cudaSuccess &&
+                   (!slot_elems ||
+                    cudaMalloc(&d_slots, (size_t)grid * (size_t)slot_elems * sizeof(float2)) == cudaSuccess);
         if (!okm) {
             cudaGetLastError();
             cleanup();
@@ -1998,7 +2008,7 @@ qs_status qs_qaoa_maxcut(const qs_graph *graphs, size_t n_graphs, int n_sets, in
         cudaMemcpyAsync(d_luts, luts.data(), luts.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(d_mix, mix.data(), mix.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
         cudaMemsetAsync(d_counter, 0, sizeof(int), st);
-        QaoaSmallArgs A;
+        QaoaArgs A;
         A.items = d_items;
         A.n_items = (int)items.size();
         A.p = p;
@@ -2007,23 +2017,24 @@ qs_status qs_qaoa_maxcut(const qs_graph *graphs, size_t n_graphs, int n_sets, in
         A.mix = d_mix;
         A.out = d_out;
         A.counter = d_counter;
-        const int grid = (int)std::min<size_t>(items.size(), (size_t)g_num_sms[dev]);
-        cudaError_t e = launch_qaoa_small(A, grid, st);
+        A.slots = d_slots;
+        A.slot_elems = slot_elems;
+        cudaError_t e = launch_qaoa(A, grid, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(hout.data(), d_out, n_out * sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         cleanup();
-        if (e != cudaSuccess) return fail(QS_ERR_CUDA, std::string("qaoa small-state kernel: ") + cudaGetErrorString(e));
+        if (e != cudaSuccess) return fail(QS_ERR_CUDA, std::string("qaoa kernel: ") + cudaGetErrorString(e));
         for (const QaoaItem &it : items) out[it.out_idx] = hout[it.out_idx];
     }
 
-    // ---- larger states: fused tile passes, all angle sets of a graph as one batch ----
+    // ---- states above 24 qubits: fused tile passes, all angle sets of a graph as one batch ----
     // Everything is enqueued on one stream and the results stay on the device
     // until the end, so the host plans graph g + 1 while the GPU runs graph g.
     std::map<int, qs_state *> states;
     qs_status rs = QS_OK;
     size_t n_large = 0;
     for (size_t g = 0; g < n_graphs; ++g)
-        if (graphs[g].n > kQaoaMaxSmallN) ++n_large;
+        if (graphs[g].n > kQaoaMaxPersistentN) ++n_large;
     double *d_res = nullptr;   // (re, im) per (graph, angle set)
     if (n_large && cudaMalloc(&d_res, n_out * 2 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
@@ -2031,7 +2042,7 @@ qs_status qs_qaoa_maxcut(const qs_graph *graphs, size_t n_graphs, int n_sets, in
     }
     for (size_t g = 0; g < n_graphs && rs == QS_OK; ++g) {
         const qs_graph &G = graphs[g];
-        if (G.n <= kQaoaMaxSmallN) continue;
+        if (G.n <= kQaoaMaxPersistentN) continue;
         qs_state *S = states[G.n];
         if (!S) {
             rs = qs_alloc(G.n, n_sets, &S);
@@ -2081,7 +2092,7 @@ qs_status qs_qaoa_maxcut(const qs_graph *graphs, size_t n_graphs, int n_sets, in
             if (rs == QS_OK) rs = check_err_word(kv.second);
         if (rs == QS_OK)
             for (size_t g = 0; g < n_graphs; ++g)
-                if (graphs[g].n > kQaoaMaxSmallN)
+                if (graphs[g].n > kQaoaMaxPersistentN)
                     for (int a = 0; a < n_sets; ++a) out[g * n_sets + a] = r[(g * n_sets + a) * 2];
     }
     if (d_res) {

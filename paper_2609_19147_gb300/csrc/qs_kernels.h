@@ -196,8 +196,10 @@ cudaError_t launch_xyz_tile(const XyzTileArgs &A, cudaStream_t st);
 
 cudaError_t launch_init_zero(float2 *psi, long long state_elems, int batch, cudaStream_t st);
 
-// batched QAOA MaxCut, small states (n <= 14) in shared memory
+// batched QAOA MaxCut: one persistent launch over every instance; states with
+// n <= 14 in shared memory, n <= 24 in a per-CTA slot of device memory
 constexpr int kQaoaMaxSmallN = 14;
+constexpr int kQaoaMaxPersistentN = 24;
 constexpr int kQaoaMaxEdges = 64;
 constexpr int kQaoaMaxP = 16;
 struct QaoaItem {
@@ -207,7 +209,7 @@ struct QaoaItem {
     int mix_off;       // into mix: p entries (cos beta_l, -sin beta_l)
     int out_idx;
 };
-struct QaoaSmallArgs {
+struct QaoaArgs {
     const QaoaItem *items;
     int n_items;
     int p;
@@ -216,9 +218,11 @@ struct QaoaSmallArgs {
     const float2 *mix;
     double *out;
     int *counter;                 // work queue head (zeroed before launch)
+    float2 *slots;                // grid x slot_elems amplitudes (states with n > 14)
+    long long slot_elems;         // 2^(largest n above 14), 0 if none
 };
-int qaoa_small_smem_bytes();
-cudaError_t launch_qaoa_small(const QaoaSmallArgs &A, int grid, cudaStream_t st);
+int qaoa_smem_bytes();
+cudaError_t launch_qaoa(const QaoaArgs &A, int grid, cudaStream_t st);
 
 // message for qs_last_error() on this host thread
 void set_last_error(const char *msg);

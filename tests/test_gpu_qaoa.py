@@ -70,3 +70,20 @@ def test_qaoa_config_batch_sampled():
                 assert abs(got[i, a] - _oracle_cut(inst, a)) <= 1e-4
             if inst["n"] == 20:
                 checked = 99
+
+
+def test_qaoa_every_size_in_one_launch_matches_oracle():
+    # one batch with every even n from 14 to 24 (the shared-memory states and
+    # the device-memory slots of the persistent launch, pass B with one and
+    # two high sweeps), p = 4, against the oracle's full state
+    rng = np.random.default_rng(21)
+    insts = []
+    for n in (24, 14, 16, 18, 20, 22):
+        edges = W.random_regular3_graph(n, rng)
+        ang = rng.uniform(0, np.pi, size=(2, 2, 4))
+        insts.append({"n": n, "edges": edges, "gammas": ang[:, 0, :], "betas": ang[:, 1, :]})
+    got = qs.qaoa_maxcut(insts)
+    for i, inst in enumerate(insts):
+        for a in ((0,) if inst["n"] == 24 else (0, 1)):
+            ref = _oracle_cut(inst, a)
+            assert abs(got[i, a] - ref) <= 1e-4, (inst["n"], a, got[i, a], ref)
