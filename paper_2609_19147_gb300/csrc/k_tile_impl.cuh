@@ -1532,20 +1532,28 @@ __global__ void __launch_bounds__(NT, MINB)
     const int rows = 1 << H;
     const uint32_t row_bytes = 8u << L;
 
-    // thread 0 issues every copy (TMA path: one instruction per tile)
+    // warp 0 issues the copies: with the tensor map its first lane (one
+    // instruction per tile); without one (bit sets needing more than 5 tensor
+    // dims) all 32 lanes share the tile's row copies, lane 0 posting the
+    // expected bytes first.  Every lane commits and later waits on its own
+    // bulk store groups.
+    const int lane = tid & 31;
     auto load = [&](int k) {
         const int b = k % NB;
         float2 *dstbuf = buf0 + (size_t)b * tile_elems;
         const long long t = blockIdx.x + (long long)k * stride;
         const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
-        mbar_arrive_expect_tx(&full[b], tile_bytes);
+        if (lane == 0) mbar_arrive_expect_tx(&full[b], tile_bytes);
         if (A.use_tma) {
-            int c[5];
-            tile_coords(A.geo, ti, bi, c);
-            tma_load_5d(dstbuf, &tm_src, c, &full[b]);
+            if (lane == 0) {
+                int c[5];
+                tile_coords(A.geo, ti, bi, c);
+                tma_load_5d(dstbuf, &tm_src, c, &full[b]);
+            }
         } else {
+            __syncwarp();
             const float2 *src = A.src + bi * A.state_elems + tile_base(A, ti);
-            for (int r = 0; r < rows; ++r)
+            for (int r = lane; r < rows; r += 32)
                 bulk_g2s(dstbuf + ((size_t)r << L), src + row_offset(r, H, s_hb), row_bytes, &full[b]);
         }
     };
@@ -1554,12 +1562,14 @@ __global__ void __launch_bounds__(NT, MINB)
         const long long t = blockIdx.x + (long long)k * stride;
         const long long bi = t / A.n_tiles, ti = t - bi * A.n_tiles;
         if (A.use_tma) {
-            int c[5];
-            tile_coords(A.geo, ti, bi, c);
-            tma_store_5d(&tm_dst, c, srcbuf);
+            if (lane == 0) {
+                int c[5];
+                tile_coords(A.geo, ti, bi, c);
+                tma_store_5d(&tm_dst, c, srcbuf);
+            }
         } else {
             float2 *dst = A.dst + bi * A.state_elems + tile_base(A, ti);
-            for (int r = 0; r < rows; ++r)
+            for (int r = lane; r < rows; r += 32)
                 bulk_s2g(dst + row_offset(r, H, s_hb), srcbuf + ((size_t)r << L), row_bytes);
         }
         bulk_commit();
@@ -1576,7 +1586,7 @@ __global__ void __launch_bounds__(NT, MINB)
     };
     if (tid == 0 && A.use_tma)
         for (int k = D; k < D + PF && k < n_mine; ++k) l2pf(k);
-    if (tid == 0)
+    if (tid < 32)
         for (int k = 0; k < D && k < n_mine; ++k) load(k);
 
     SweepCtx c;
@@ -1602,7 +1612,7 @@ __global__ void __launch_bounds__(NT, MINB)
     c.tab_g = S.s_tab_g;
     long long cur_item = 0;   // constants of item 0 are staged above
     for (int k = 0; k < n_mine; ++k) {
-        if (tid == 0 && k + D < n_mine) {
+        if (tid < 32 && k + D < n_mine) {
             // buffer (k+D) % NB last held tile k+D-NB, stored at the end of
             // iteration k+D-NB: allow the NB-D-1 newer stores to stay in flight
             switch (NB - D - 1) {
@@ -1621,9 +1631,9 @@ __global__ void __launch_bounds__(NT, MINB)
                 atomicCAS(A.err, 0, (int)QS_ERR_TIMEOUT);
                 for (int kk = k + 1; kk < k + D && kk < n_mine; ++kk)
                     mbar_wait_bounded(&full[kk % NB], (uint32_t)((kk / NB) & 1));
-                bulk_wait_all0();
                 if (mma_pending) mbar_wait_bounded(c.mma_bar, *c.mma_phase);   // the MMAs, once more
             }
+            if (tid < 32) bulk_wait_all0();
             if constexpr (DENSE) {
                 if (A.tmem) tc_dealloc(c.tmem);
             }
@@ -1661,9 +1671,9 @@ __global__ void __launch_bounds__(NT, MINB)
         }
         fence_proxy_async();   // generic-proxy writes before the async-proxy store
         __syncthreads();
-        if (tid == 0) store(k);
+        if (tid < 32) store(k);
     }
-    if (tid == 0) bulk_wait_all0();
+    if (tid < 32) bulk_wait_all0();
     if constexpr (DENSE) {
         if (A.tmem) tc_dealloc(c.tmem);
     }
