@@ -908,10 +908,129 @@ __device__ __forceinline__ bool run_rot_program(const SweepCtx &c, const Sweep &
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// U(2) layer sweeps (MK_ZYZ): every group bit's 2x2 unitary was factored on the
+// host into output phases, a real rotation and input phases.  Per item: one
+// product with the input-phase table (the phases of all R bits at once), R
+// rotation layers at one packed FMA per amplitude and bit, one product with
+// the output-phase table.  A bit whose rotation ran in cotangent form leaves
+// its pair exchanged; the store undoes the exchange by writing to the
+// exchanged offsets (an XOR of the group bits' offsets, formed once per sweep),
+// and the planner stored the output-phase table in the exchanged order.
+// ---------------------------------------------------------------------------
+template <int R, int M = 0>
+__device__ __forceinline__ void zyz_rot_regs(float2 (&a)[1 << R], const float2 (&k)[2 * R]) {
+    if constexpr (M < R) {
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j) {
+            if ((j >> M) & 1) continue;
+            const int q = j | (1 << M);
+            const float2 a0 = a[j], a1 = a[q];
+            a[j] = __ffma2_rn(k[2 * M], a1, a0);
+            a[q] = __ffma2_rn(k[2 * M + 1], a0, a1);
+        }
+        zyz_rot_regs<R, M + 1>(a, k);
+    }
+}
+
+// the general path's form (any R, after other ops): the exchange undone in
+// registers with uniform branches
+template <int R>
+__device__ __forceinline__ void apply_zyz(const SweepCtx &c, const MicroOp &op, float2 (&a)[1 << R]) {
+    constexpr int P = 1 << R;
+    if (!QS_DCHECK(c, op.cst >= 0 && op.cst + 2 * P + 2 * R + 1 <= c.n_const, 1014)) return;
+    const float2 *pin = c.cs + op.cst, *pout = pin + P, *kk = pout + P;
+    float2 k[2 * R];
+#pragma unroll
+    for (int m = 0; m < 2 * R; ++m) k[m] = kk[m];
+    const int form = __float_as_int(kk[2 * R].x);
+#pragma unroll
+    for (int j = 1; j < P; ++j) a[j] = cmul(a[j], pin[j]);
+    zyz_rot_regs<R>(a, k);
+#pragma unroll
+    for (int j = 0; j < P; ++j) a[j] = cmul(a[j], pout[j]);
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+        if (!((form >> m) & 1)) continue;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            if ((j >> m) & 1) continue;
+            const float2 t = a[j];
+            a[j] = a[j | (1 << m)];
+            a[j | (1 << m)] = t;
+        }
+    }
+}
+
+template <int R, int NT, bool VEC, bool SW0>
+__device__ __forceinline__ void zyz_sweep(const SweepCtx &c, const Sweep &S, int sidx, const MicroOp &op) {
+    constexpr int P = 1 << R;
+    const int *ts = c.tab_s + sidx * kItemTab;
+    int gs[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) gs[m] = ts[kItemTab - kGroupTab + m];
+    const float2 *pin = c.cs + op.cst, *pout = pin + P, *kk = pout + P;
+    float2 k[2 * R];
+#pragma unroll
+    for (int m = 0; m < 2 * R; ++m) k[m] = kk[m];
+    const int form = __float_as_int(kk[2 * R].x);
+    // offset XOR that moves element i to element i ^ form (with 16-byte pairs,
+    // bit 0 is the swap inside the pair: SW0)
+    int fo = 0;
+#pragma unroll
+    for (int m = VEC ? 1 : 0; m < R; ++m)
+        if ((form >> m) & 1) fo ^= gs[m];
+    const int n_items = 1 << (c.T - R);
+    for (int item = c.lt; item < n_items; item += NT) {
+        const int i0 = item & 31, i1 = 32 + ((item >> 5) & 31), i2 = 64 + ((item >> 10) & 15);
+        const int saddr = ts[i0] ^ ts[i1] ^ ts[i2];
+        float2 a[P];
+        int o[P];
+        group_offsets<R>(saddr, gs, o);
+        load_at<R>(c, VEC, o, a);
+#pragma unroll
+        for (int j = 1; j < P; ++j) a[j] = cmul(a[j], pin[j]);
+        zyz_rot_regs<R>(a, k);
+#pragma unroll
+        for (int j = 0; j < P; ++j) a[j] = cmul(a[j], pout[j]);
+        // a[i] is element i ^ form: its offset is that of element i from the
+        // item base saddr ^ fo
+        group_offsets<R>(saddr ^ fo, gs, o);
+        if constexpr (VEC) {
+#pragma unroll
+            for (int j = 0; j < P; j += 2)
+                if (QS_DCHECK(c, o[j] >= 0 && o[j] + 1 < c.tile_elems && !(o[j] & 1), 1015)) {
+                    const float2 lo = SW0 ? a[j + 1] : a[j], hi = SW0 ? a[j] : a[j + 1];
+                    *reinterpret_cast<float4 *>(c.buf + o[j]) = make_float4(lo.x, lo.y, hi.x, hi.y);
+                }
+        } else {
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                if (QS_DCHECK(c, o[j] >= 0 && o[j] < c.tile_elems, 1015)) c.buf[o[j]] = a[j];
+        }
+    }
+}
+
+template <int R, int NT>
+__device__ __forceinline__ bool run_zyz_program(const SweepCtx &c, const Sweep &S, int sidx) {
+    if (S.op_end - S.op_begin != 1 || S.scale != 1.f) return false;
+    const MicroOp &op = c.micro[S.op_begin];
+    if (op.kind != MK_ZYZ) return false;
+    if (!QS_DCHECK(c, op.cst >= 0 && op.cst + 2 * (1 << R) + 2 * R + 1 <= c.n_const, 1014)) return true;
+    const bool sw0 = (__float_as_int(c.cs[op.cst + 2 * (1 << R) + 2 * R].x) & 1) != 0;
+    if (!S.vec) zyz_sweep<R, NT, false, false>(c, S, sidx, op);
+    else if (!sw0) zyz_sweep<R, NT, true, false>(c, S, sidx, op);
+    else zyz_sweep<R, NT, true, true>(c, S, sidx, op);
+    return true;
+}
+
 template <int R, int NT, int KS = KS_ALL>
 __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int sidx) {
     if constexpr ((R == 4 || R == 5) && KS == KS_LAYER) {
         if (run_rot_program<R, NT>(c, S, sidx)) return;
+    }
+    if constexpr ((R == 4 || R == 5) && KS == KS_LAYER) {
+        if (run_zyz_program<R, NT>(c, S, sidx)) return;
     }
     const int *ts = c.tab_s + sidx * kItemTab;
     const uint64_t *tg = c.tab_g + sidx * kItemTab;
@@ -977,6 +1096,7 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
                     case MK_DIAG: apply_diag<R>(c, op, gbase(), G, a); break;
                     case MK_DIAGQ: apply_diagq<R>(c, op, gbase(), a); break;
                     case MK_DIAGC: apply_diagc<R>(c, op, gbase(), a); break;
+                    case MK_ZYZ: apply_zyz<R>(c, op, a); break;
                     default: break;
                 }
             } else {
@@ -1017,6 +1137,9 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
                         break;
                     case MK_DIAGC:
                         apply_diagc<R>(c, op, gbase(), a);
+                        break;
+                    case MK_ZYZ:
+                        apply_zyz<R>(c, op, a);
                         break;
                     default:
                         break;

@@ -428,7 +428,7 @@ qs_status run_tile(qs_state *st, const DevicePlan &dp, size_t i, const float2 *s
             mo.kind == MK_QFTL || (mo.cmask && mo.kind != MK_DIAGC))
             A.needs_gidx = 1;
         if (!(mo.kind == MK_LAYER || mo.kind == MK_RXC || mo.kind == MK_U1R || mo.kind == MK_ROT || mo.kind == MK_H ||
-              mo.kind == MK_U1 ||
+              mo.kind == MK_U1 || mo.kind == MK_ZYZ ||
               mo.kind == MK_DIAG || mo.kind == MK_DIAGQ || mo.kind == MK_DIAGC))
             A.kset = 0;
     }

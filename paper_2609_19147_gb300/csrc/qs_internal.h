@@ -101,6 +101,15 @@ enum MicroKind : int32_t {
     MK_ROT = 11,  // real rotation c [[1, t], [-t, 1]] (|t| <= 1) on group bit a: consts
                   // (t, t), (-t, -t) (packed FP32x2 operands); the factor c is folded into
                   // the sweep scale, so the op is one packed FMA per amplitude
+    MK_ZYZ = 12,  // a 2x2 unitary on every group bit, each factored (FP64, on the host) as
+                  // U = diag(e^{i a}, e^{i b}) [[c, -s], [s, c]] diag(1, e^{i d}); consts at
+                  // cst: PIN[2^R] = prod_m (x_m ? e^{i d_m} : 1), POUT[2^R], then per group
+                  // bit m the packed pairs (k0, k0), (k1, k1), then one entry whose x holds
+                  // the form mask F as int bits.  Per amplitude vector: a[j] *= PIN[j]; per
+                  // bit (a0, a1) <- (a0 + k0 a1, a1 + k1 a0) from the old values; a[j] *=
+                  // POUT[j]; the result a[j] is element j ^ F.  Bit m clear: k = -+s/c
+                  // (|c| >= |s|); set: k = +-c/s, which leaves the bit's pair exchanged.
+                  // POUT holds the output phases and the rotations' factors, permuted by F
 };
 constexpr int kMaxCouple = 16;
 constexpr int kMaxCountClasses = 24;

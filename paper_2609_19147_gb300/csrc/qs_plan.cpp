@@ -1821,6 +1821,9 @@ struct PassBuilder {
                             v.y = (float)m[e].imag();
                             cst.push_back(v);
                         }
+                        // the FP64 matrix, for a layer that becomes MK_ZYZ (merge_layers)
+                        mo.p = (int)u1_fp64.size();
+                        u1_fp64.push_back({m[0], m[1], m[2], m[3]});
                     }
                 } else if (f.kind == F_U2) {
                     mo.kind = MK_U2;
@@ -1880,6 +1883,7 @@ struct PassBuilder {
     const Diag *diag_src[kMaxDiag] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<const Diag *> count_src;   // MK_DIAGC ops before finalize: cst = index here
     bool count_failed = false;
+    std::vector<std::array<cd, 4>> u1_fp64;   // FP64 matrices of the MK_U1 ops (index in MicroOp::p)
     std::vector<std::pair<int, int>> count_luts;   // (offset, entries) of the count tables built
     // A diagonal g0 + gamma c1(x) + h c2(x) (count_form: uniform-angle RZZ sets
     // such as TFIM chains and QAOA cost layers, uniform CZ / CP sets, uniform
@@ -2144,6 +2148,91 @@ struct PassBuilder {
                     while (j < sw.op_end && layer_kind(tp.micro[j]) == lk && !((mask >> tp.micro[j].a) & 1)) {
                         mask |= 1u << tp.micro[j].a;
                         ++j;
+                    }
+                    // a layer of 2x2 unitaries that is the whole sweep (on all R group
+                    // bits) becomes one MK_ZYZ op: phases, rotations, phases
+                    // (unitary matrices only: the factorisation assumes it), the sweep's
+                    // scale folded into the output phases
+                    if (lk == MK_U1 && i == sw.op_begin && j == sw.op_end && sw.r == R && !sw.dense) {
+                        std::vector<std::array<cd, 4>> mats(R, std::array<cd, 4>{cd(1, 0), cd(0, 0), cd(0, 0), cd(1, 0)});
+                        bool unitary = true;
+                        for (int k = i; k < j; ++k) {
+                            const auto &u = u1_fp64[tp.micro[k].p];
+                            mats[tp.micro[k].a] = u;
+                            // U^H U = I to 1e-9
+                            const cd g00 = std::conj(u[0]) * u[0] + std::conj(u[2]) * u[2];
+                            const cd g11 = std::conj(u[1]) * u[1] + std::conj(u[3]) * u[3];
+                            const cd g01 = std::conj(u[0]) * u[1] + std::conj(u[2]) * u[3];
+                            if (std::abs(g00 - 1.0) > 1e-9 || std::abs(g11 - 1.0) > 1e-9 || std::abs(g01) > 1e-9)
+                                unitary = false;
+                        }
+                        const int P = 1 << R;
+                        if (unitary && (int)cst.size() + 2 * P + 2 * R + 1 <= kMaxConst) {
+                            MicroOp Z;
+                            std::memset(&Z, 0, sizeof Z);
+                            Z.kind = MK_ZYZ;
+                            Z.cst = (int)cst.size();
+                            std::vector<cd> pin(P, cd(1, 0)), pout(P, cd(1, 0));
+                            std::vector<float2> kk;
+                            int form = 0;
+                            for (int m = 0; m < R; ++m) {
+                                const auto &u = mats[m];
+                                double c = std::abs(u[0]), sn = std::abs(u[2]);
+                                const double nr = std::hypot(c, sn);
+                                c /= nr;
+                                sn /= nr;
+                                double a, b, d;   // U = diag(e^{ia}, e^{ib}) [[c, -s], [s, c]] diag(1, e^{id})
+                                if (sn == 0.0) {
+                                    a = std::arg(u[0]);
+                                    b = std::arg(u[3]);
+                                    d = 0.0;
+                                } else if (c == 0.0) {
+                                    a = 0.0;
+                                    b = std::arg(u[2]);
+                                    d = std::arg(-u[1]);
+                                } else {
+                                    a = std::arg(u[0]);
+                                    b = std::arg(u[2]);
+                                    d = std::arg(-u[1]) - a;
+                                }
+                                const bool cot = sn > c;
+                                double k0, k1, f;
+                                if (!cot) {
+                                    k0 = -sn / c;
+                                    k1 = sn / c;
+                                    f = c;
+                                } else {
+                                    // cotangent form: the kernel computes the pair
+                                    // (a0 + (c/s) a1, a1 - (c/s) a0), the two outputs exchanged
+                                    k0 = c / sn;
+                                    k1 = -c / sn;
+                                    f = sn;
+                                    form |= 1 << m;
+                                }
+                                kk.push_back(float2{(float)k0, (float)k0});
+                                kk.push_back(float2{(float)k1, (float)k1});
+                                const cd e0 = std::polar(f * (cot ? -1.0 : 1.0), a), e1 = std::polar(f, b);
+                                const cd ed = std::polar(1.0, d);
+                                for (int jj = 0; jj < P; ++jj) {
+                                    pout[jj] *= ((jj >> m) & 1) ? e1 : e0;
+                                    if ((jj >> m) & 1) pin[jj] *= ed;
+                                }
+                            }
+                            const double scl = sw.scale;
+                            sw.scale = 1.f;
+                            for (int jj = 0; jj < P; ++jj) cst.push_back(float2{(float)pin[jj].real(), (float)pin[jj].imag()});
+                            // output phases in the order of the exchanged results: entry i
+                            // multiplies the value that is stored as element i ^ form
+                            for (int jj = 0; jj < P; ++jj)
+                                cst.push_back(float2{(float)(pout[jj ^ form].real() * scl), (float)(pout[jj ^ form].imag() * scl)});
+                            cst.insert(cst.end(), kk.begin(), kk.end());
+                            float fm;
+                            std::memcpy(&fm, &form, sizeof fm);
+                            cst.push_back(float2{fm, 0.f});
+                            out.push_back(Z);
+                            i = j;
+                            continue;
+                        }
                     }
                     const int stride = lk == MK_RXC ? 1 : lk == MK_U1R ? 4 : lk == MK_U1 ? 4 : lk == MK_ROT ? 2 : 0;
                     // a lone rotation becomes a one-bit layer too (see the padding below)
@@ -2747,7 +2836,8 @@ std::string Plan::describe() const {
             os << "TILE T=" << t.T << " L=" << t.L << " hb=[";
             for (int k = 0; k < t.H; ++k) os << (k ? "," : "") << t.hb[k];
             os << "] tma=" << (hp.tma.ok ? 1 : 0) << " sweeps=" << t.n_sweeps
-               << " U1=" << cnt[MK_U1] + cnt[MK_H] + cnt[MK_RXC] + cnt[MK_U1R] + cnt[MK_ROT] << " U2=" << cnt[MK_U2]
+               << " U1=" << cnt[MK_U1] + cnt[MK_H] + cnt[MK_RXC] + cnt[MK_U1R] + cnt[MK_ROT] << " ZYZ=" << cnt[MK_ZYZ]
+               << " U2=" << cnt[MK_U2]
                << " DIAG=" << cnt[MK_DIAG] << " QFT=" << cnt[MK_QFT];
             int nd = 0, slow = 0, fq = 0, fc = 0;
             for (int k = 0; k < t.n_sweeps; ++k) nd += t.sweeps[k].dense ? 1 : 0;

@@ -54,7 +54,7 @@ int popc(uint64_t x) {
 }
 
 struct Counts {
-    long micro[12] = {0};
+    long micro[13] = {0};
     long dense[4] = {0};
     long tile = 0, perm = 0, gather = 0, tma = 0, rows = 0, swz = 0, sweeps = 0, pergate = 0;
 };
@@ -368,7 +368,7 @@ class TileRun {
 
     template <class GI>
     void op(const MicroOp &o, int r, const uint64_t *gg, uint64_t gbase, std::vector<C> &a, GI &gidx, bool first) {
-        need(o.kind >= 0 && o.kind <= MK_ROT, "micro-op kind");
+        need(o.kind >= 0 && o.kind <= MK_ZYZ, "micro-op kind");
         if (first) {
             cnt_.micro[o.kind]++;
             // a layer also exercises its op kind (lone rotations become one-bit layers)
@@ -410,6 +410,28 @@ class TileRun {
                 need(gg[o.a] == (1ull << o.p), "QFT stage bit is not the group bit");
                 const uint64_t mk = (o.p > o.lo) ? (((1ull << o.p) - 1) & ~((1ull << o.lo) - 1)) : 0;
                 qft(o.a, r, a, o.cst, twiddle(gbase & mk, o.p));
+                break;
+            }
+            case MK_ZYZ: {
+                // input phases, rotations in one-FMA form, output phases, then
+                // element j of the result is the computed value j ^ F
+                const int P = 1 << r;
+                need(o.cst >= 0, "U(2) layer constants");
+                auto no = [](int) { return 0ull; };
+                for (int j = 0; j < P; ++j) a[j] *= K(o.cst + j);
+                for (int m = 0; m < r; ++m) {
+                    const float2 q0 = Kraw(o.cst + 2 * P + 2 * m), q1 = Kraw(o.cst + 2 * P + 2 * m + 1);
+                    need(q0.x == q0.y && q1.x == q1.y && q1.x == -q0.x, "U(2) rotation not packed as (k, k), (-k, -k)");
+                    need(std::abs(q0.x) <= 1.f, "U(2) rotation coefficient above 1");
+                    u1(m, r, a, 1.0, q0.x, q1.x, 1.0, 0, 0, no);
+                }
+                for (int j = 0; j < P; ++j) a[j] *= K(o.cst + P + j);
+                int F;
+                const float2 fe = Kraw(o.cst + 2 * P + 2 * r);
+                std::memcpy(&F, &fe.x, 4);
+                need(F >= 0 && F < P, "U(2) exchange mask");
+                std::vector<C> b(a);
+                for (int j = 0; j < P; ++j) a[j ^ F] = b[j];
                 break;
             }
             case MK_LAYER: {
@@ -825,7 +847,7 @@ int main(int argc, char **argv) {
         }
         std::printf("CASE %d passes %zu tile %ld perm %ld gather %ld tma %ld rows %ld swz %ld sweeps %ld merged %d micro",
                     ci, n_passes, c.tile, c.perm, c.gather, c.tma, c.rows, c.swz, c.sweeps, merged ? 1 : 0);
-        for (int k = 0; k <= MK_ROT; ++k) std::printf(" %ld", c.micro[k]);
+        for (int k = 0; k <= MK_ZYZ; ++k) std::printf(" %ld", c.micro[k]);
         std::printf(" dense %ld %ld %ld pergate %ld\n", c.dense[1], c.dense[2], c.dense[3], c.pergate);
         ++ci;
     }

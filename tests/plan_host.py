@@ -64,7 +64,7 @@ def interpret(qs, cases, workdir, psi0s):
         r = rows[i]
         counts = {k: int(v) for k, v in zip(r[2:20:2], r[3:20:2])}
         mi, di = r.index("micro"), r.index("dense")
-        counts["micro"] = [int(x) for x in r[mi + 1:mi + 13]]
+        counts["micro"] = [int(x) for x in r[mi + 1:mi + 14]]
         counts["dense"] = [int(x) for x in r[di + 1:di + 4]]
         counts["pergate"] = int(r[r.index("pergate") + 1])
         if psi0s[i] is None:

@@ -91,6 +91,22 @@ def test_qft_stages_fuse_into_few_passes(qs):
     assert p == 480
 
 
+def test_u2_layers_become_phase_rotation_phase_sweeps(qs):
+    # a sweep whose only op is a layer of general 2x2 unitaries on all its
+    # group bits is planned as phases, rotations, phases (one ZYZ op per sweep)
+    rng = np.random.default_rng(3)
+    n = 20
+    gl = [W.Gate("U", (q,), (), W.haar_u2(rng)) for q in range(n)]
+    text, _ = _passes(qs, n, gl)
+    zyz = [int(x) for x in re.findall(r"ZYZ=(\d+)", text)]
+    assert sum(zyz) >= 4 and all(int(x) == 0 for x in re.findall(r" U1=(\d+)", text)), text
+    # the factorisation holds for unitary matrices only: a scaled layer keeps
+    # the general 2x2 form
+    text, _ = _passes(qs, n, [W.Gate("U", (q,), (), 0.9 * W.haar_u2(rng)) for q in range(n)])
+    assert all(int(x) == 0 for x in re.findall(r"ZYZ=(\d+)", text)), text
+    assert sum(int(x) for x in re.findall(r" U1=(\d+)", text)) == n, text
+
+
 def test_h_layer_pass_count_app_a(qs):
     # App. A: radix-4 Walsh takes ceil(25/4) = 7 passes; tiles of 13 qubits take 3
     text, p = _passes(qs, 25, W.wht_gates(25))

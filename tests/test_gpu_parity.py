@@ -84,6 +84,38 @@ def test_haar_layers(n):
     _assert_close(_run(n, gl, psi0), _ref(n, gl, psi0))
 
 
+def _u2_of(c, s, rng):
+    """diag(e^{ia}, e^{ib}) [[c, -s], [s, c]] diag(1, e^{id}) with random phases."""
+    a, b, d = rng.uniform(0.0, 2.0 * np.pi, 3)
+    return np.diag(np.exp(1j * np.array([a, b]))) @ np.array([[c, -s], [s, c]]) @ np.diag([1.0, np.exp(1j * d)])
+
+
+def _u2_branch_matrix(kind, rng):
+    # every branch of the phases-rotation-phases factorisation: Haar, diagonal
+    # (s = 0), anti-diagonal (c = 0), |c| > |s|, |s| > |c|, |c| = |s|
+    if kind == 0:
+        return W.haar_u2(rng)
+    th = {1: 0.0, 2: np.pi / 2, 3: 0.3, 4: 1.2, 5: np.pi / 4}[kind]
+    return _u2_of(np.cos(th), np.sin(th), rng)
+
+
+@pytest.mark.parametrize("tq,lq", [(0, 0), (13, 4), (12, 5), (13, 6), (10, 3)])
+def test_u2_layers_every_factorisation_branch(tq, lq):
+    # U(2) layers (split by CZ ladders so that they do not fuse) whose matrices
+    # rotate through the branches, so that every group bit, the 16-byte pair
+    # bit included, meets each rotation form
+    n = 19
+    rng = np.random.default_rng(11)
+    gl = []
+    for layer in range(7):
+        gl += [W.Gate("U", (q,), (), _u2_branch_matrix((q + layer) % 6, rng)) for q in range(n)]
+        gl += [W.Gate("CZ", (q, q + 1)) for q in range(n - 1)]
+    # a scaled (non-unitary) layer keeps the general 2x2 path
+    gl += [W.Gate("U", (q,), (), 0.97 * W.haar_u2(rng)) for q in range(n)]
+    psi0 = W.random_state(n, 12)
+    _assert_close(_run(n, gl, psi0, tile_qubits=tq, low_qubits=lq), _ref(n, gl, psi0))
+
+
 @pytest.mark.parametrize("n", [10, 19, 21])
 def test_qft_random_state(n):
     psi0 = W.random_state(n, 40 + n)

@@ -149,7 +149,7 @@ def test_plans_interpreted_on_host_match_oracle(tmp_path, qs):
         expect.append(np.stack([oracle.simulate(n, gl, psi0[b].copy(), theta=params[b] if P else None)
                                 for b in range(B)]))
     res = plan_host.interpret(qs, cases, str(tmp_path), psi0s)
-    micro = np.zeros(12, dtype=np.int64)
+    micro = np.zeros(13, dtype=np.int64)
     dense = np.zeros(3, dtype=np.int64)
     kinds = {"perm": 0, "gather": 0, "tma": 0, "rows": 0, "swz": 0, "pergate": 0}
     for i, case in enumerate(cases):
