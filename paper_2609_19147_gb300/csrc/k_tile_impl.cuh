@@ -933,10 +933,10 @@ __device__ __forceinline__ void zyz_rot_regs(float2 (&a)[1 << R], const float2 (
     }
 }
 
-// the general path's form (any R, after other ops): the exchange undone in
-// registers with uniform branches
+// the general path's form (the sweep's last op, after others): the exchange is
+// left to the store (zyz_exchange); as any other op it is undone in registers
 template <int R>
-__device__ __forceinline__ void apply_zyz(const SweepCtx &c, const MicroOp &op, float2 (&a)[1 << R]) {
+__device__ __forceinline__ void apply_zyz(const SweepCtx &c, const MicroOp &op, float2 (&a)[1 << R], bool last) {
     constexpr int P = 1 << R;
     if (!QS_DCHECK(c, op.cst >= 0 && op.cst + 2 * P + 2 * R + 1 <= c.n_const, 1014)) return;
     const float2 *pin = c.cs + op.cst, *pout = pin + P, *kk = pout + P;
@@ -949,6 +949,7 @@ __device__ __forceinline__ void apply_zyz(const SweepCtx &c, const MicroOp &op, 
     zyz_rot_regs<R>(a, k);
 #pragma unroll
     for (int j = 0; j < P; ++j) a[j] = cmul(a[j], pout[j]);
+    if (last) return;
 #pragma unroll
     for (int m = 0; m < R; ++m) {
         if (!((form >> m) & 1)) continue;
@@ -960,6 +961,26 @@ __device__ __forceinline__ void apply_zyz(const SweepCtx &c, const MicroOp &op, 
             a[j | (1 << m)] = t;
         }
     }
+}
+
+// a sweep that ends with MK_ZYZ: its store goes to the exchanged offsets,
+// item base saddr ^ fo (fo over the group bits in the form mask, bit 0 left
+// out with 16-byte pairs), and with the pair bit exchanged (sw0) it swaps the
+// two halves of each 16-byte store
+template <int R>
+__device__ __forceinline__ void zyz_exchange(const SweepCtx &c, const Sweep &S, const int (&gs)[R], int &fo,
+                                             bool &sw0) {
+    fo = 0;
+    sw0 = false;
+    if (S.op_end <= S.op_begin) return;
+    const MicroOp &op = c.micro[S.op_end - 1];
+    if (op.kind != MK_ZYZ) return;
+    if (!QS_DCHECK(c, op.cst >= 0 && op.cst + 2 * (1 << R) + 2 * R + 1 <= c.n_const, 1014)) return;
+    const int form = __float_as_int(c.cs[op.cst + 2 * (1 << R) + 2 * R].x);
+#pragma unroll
+    for (int m = 0; m < R; ++m)
+        if (((form >> m) & 1) && !(m == 0 && S.vec)) fo ^= gs[m];
+    sw0 = S.vec && (form & 1);
 }
 
 template <int R, int NT, bool VEC, bool SW0>
@@ -1048,6 +1069,9 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
     const float scale = S.scale;
     const int fast = KS == KS_LAYER ? straight_code<R>(c, op_begin, op_end, scale) : 0;
     const float2 *k0f = c.cs + c.micro[op_begin].cst;
+    int zfo;
+    bool zsw0;
+    zyz_exchange<R>(c, S, gs, zfo, zsw0);
     for (int item = c.lt; item < n_items; item += NT) {
         const int i0 = item & 31, i1 = 32 + ((item >> 5) & 31), i2 = 64 + ((item >> 10) & 15);
         const int saddr = ts[i0] ^ ts[i1] ^ ts[i2];
@@ -1096,7 +1120,7 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
                     case MK_DIAG: apply_diag<R>(c, op, gbase(), G, a); break;
                     case MK_DIAGQ: apply_diagq<R>(c, op, gbase(), a); break;
                     case MK_DIAGC: apply_diagc<R>(c, op, gbase(), a); break;
-                    case MK_ZYZ: apply_zyz<R>(c, op, a); break;
+                    case MK_ZYZ: apply_zyz<R>(c, op, a, oi == op_end - 1); break;
                     default: break;
                 }
             } else {
@@ -1139,7 +1163,7 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
                         apply_diagc<R>(c, op, gbase(), a);
                         break;
                     case MK_ZYZ:
-                        apply_zyz<R>(c, op, a);
+                        apply_zyz<R>(c, op, a, oi == op_end - 1);
                         break;
                     default:
                         break;
@@ -1151,7 +1175,15 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
 #pragma unroll
             for (int j = 0; j < (1 << R); ++j) a[j] = __fmul2_rn(a[j], sc);
         }
-        sweep_store<R>(c, vec, saddr, gs, a);
+        if (zsw0) {
+#pragma unroll
+            for (int j = 0; j < (1 << R); j += 2) {
+                const float2 t = a[j];
+                a[j] = a[j + 1];
+                a[j + 1] = t;
+            }
+        }
+        sweep_store<R>(c, vec, saddr ^ zfo, gs, a);
     }
 }
 

@@ -2149,11 +2149,14 @@ struct PassBuilder {
                         mask |= 1u << tp.micro[j].a;
                         ++j;
                     }
-                    // a layer of 2x2 unitaries that is the whole sweep (on all R group
-                    // bits) becomes one MK_ZYZ op: phases, rotations, phases
-                    // (unitary matrices only: the factorisation assumes it), the sweep's
-                    // scale folded into the output phases
-                    if (lk == MK_U1 && i == sw.op_begin && j == sw.op_end && sw.r == R && !sw.dense) {
+                    // a layer of two or more 2x2 unitaries that ends its sweep, or any
+                    // that is the whole sweep (the kernel's straight-line program),
+                    // becomes one MK_ZYZ op on all R group bits (identity on the others):
+                    // phases, rotations, phases (unitary matrices only: the
+                    // factorisation assumes it), the sweep's scale folded into the
+                    // output phases.  It is last so that the kernel can undo the
+                    // exchanged pairs of cotangent-form rotations at the store.
+                    if (lk == MK_U1 && (j - i >= 2 || i == sw.op_begin) && j == sw.op_end && sw.r == R && !sw.dense) {
                         std::vector<std::array<cd, 4>> mats(R, std::array<cd, 4>{cd(1, 0), cd(0, 0), cd(0, 0), cd(1, 0)});
                         bool unitary = true;
                         for (int k = i; k < j; ++k) {
