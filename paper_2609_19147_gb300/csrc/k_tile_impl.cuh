@@ -799,22 +799,27 @@ struct DiagcRegs {
             const uint64_t f = cz ? (x0 & (x0 >> (int)cls[2 * k + 1])) : (x0 ^ (x0 >> (int)cls[2 * k + 1]));
             c0 += __popcll(f & cls[2 * k]);
         }
-        int cnt[1 << R];
-        cnt[0] = c0;
+        int dm[R];
 #pragma unroll
         for (int m = 0; m < R; ++m) {
             const int s = __popcll(x0 & dat[m]);
-            const int dm = (cz ? s : (int)((degs >> (6 * m)) & 63) - 2 * s) + (int)((zinc >> (12 * m)) & 4095);
-#pragma unroll
-            for (int j = 0; j < (1 << m); ++j) cnt[j | (1 << m)] = cnt[j] + dm;
+            dm[m] = (cz ? s : (int)((degs >> (6 * m)) & 63) - 2 * s) + (int)((zinc >> (12 * m)) & 4095);
         }
+        // the group elements in Gray-code order: one running count, one add
+        // or subtract per element (no table of 2^R counts held in registers)
+        int cnt = c0;
 #pragma unroll
-        for (int j = 0; j < (1 << R); ++j) {
+        for (int i = 0; i < (1 << R); ++i) {
+            const int j = i ^ (i >> 1);
+            if (i > 0) {
+                const int m = __ffs(i) - 1;
+                cnt += ((j >> m) & 1) ? dm[m] : -dm[m];
+            }
             const int q = (int)(((j < 16 ? q_lo : q_hi) >> (4 * (j & 15))) & 15);
 #ifdef QS_DEVICE_CHECKS
-            if (!QS_DCHECK(*ctx, cnt[j] + q >= 0 && (lut - ctx->cs) + cnt[j] + q < ctx->n_const, 1006)) continue;
+            if (!QS_DCHECK(*ctx, cnt + q >= 0 && (lut - ctx->cs) + cnt + q < ctx->n_const, 1006)) continue;
 #endif
-            a[j] = cmul(a[j], lut[cnt[j] + q]);
+            a[j] = cmul(a[j], lut[cnt + q]);
         }
     }
 };
@@ -1045,14 +1050,8 @@ __device__ __forceinline__ bool run_zyz_program(const SweepCtx &c, const Sweep &
     return true;
 }
 
-template <int R, int NT, int KS = KS_ALL>
-__device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int sidx) {
-    if constexpr ((R == 4 || R == 5) && KS == KS_LAYER) {
-        if (run_rot_program<R, NT>(c, S, sidx)) return;
-    }
-    if constexpr ((R == 4 || R == 5) && KS == KS_LAYER) {
-        if (run_zyz_program<R, NT>(c, S, sidx)) return;
-    }
+template <int R, int NT, int KS>
+__device__ __forceinline__ void run_sweep_general(const SweepCtx &c, const Sweep &S, int sidx) {
     const int *ts = c.tab_s + sidx * kItemTab;
     const uint64_t *tg = c.tab_g + sidx * kItemTab;
     int gs[R];
@@ -1185,6 +1184,15 @@ __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int
         }
         sweep_store<R>(c, vec, saddr ^ zfo, gs, a);
     }
+}
+
+template <int R, int NT, int KS = KS_ALL>
+__device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int sidx) {
+    if constexpr ((R == 4 || R == 5) && KS == KS_LAYER) {
+        if (run_rot_program<R, NT>(c, S, sidx)) return;
+        if (run_zyz_program<R, NT>(c, S, sidx)) return;
+    }
+    run_sweep_general<R, NT, KS>(c, S, sidx);
 }
 
 // ---------------------------------------------------------------------------

@@ -1564,8 +1564,12 @@ struct PassBuilder {
             sw.gbit[sw.r++] = 0;
             cur_group |= 1ull;
         }
-        for (int tb = T - 1; tb >= 0 && sw.r < std::min(R, T); --tb)
-            if (!((cur_group >> tb) & 1)) {
+        // (padding bits that share a bank bit with a group bit last)
+        for (int pass = 0; pass < 2; ++pass)
+            for (int tb = T - 1; tb >= 0 && sw.r < std::min(R, T); --tb) {
+                if ((cur_group >> tb) & 1) continue;
+                const int partner = tp.swizzle ? swizzle_partner(tb) : -1;
+                if (pass == 0 && partner >= 0 && ((cur_group >> partner) & 1)) continue;
                 sw.gbit[sw.r++] = tb;
                 cur_group |= 1ull << tb;
             }
@@ -1755,8 +1759,46 @@ struct PassBuilder {
             for (size_t i = 0; i < ops.size(); ++i) in_open[i] = (cur_group >> tile_local(tp, ops[i].t0)) & 1;
         for (size_t i = 0; i < ops.size(); ++i)
             if (in_open[i]) add_now(ops[i], nullptr);
+        // The rest fill groups of R bits in the order given.  With the 128-byte
+        // swizzle, tile bits t and t + 3 (t = 1..3) select the same bank bit of
+        // an access; a group that holds both leaves a warp's lanes one bank bit
+        // short (two-way conflicts on every access of the sweep), so each group
+        // is filled with the first remaining op whose partner it does not hold.
+        std::vector<size_t> rest;
         for (size_t i = 0; i < ops.size(); ++i)
-            if (!in_open[i]) add_now(ops[i], nullptr);
+            if (!in_open[i]) rest.push_back(i);
+        if (tp.swizzle) {
+            std::vector<size_t> order;
+            uint64_t grp = open >= 0 ? cur_group : 0;
+            int room = open >= 0 ? std::max(0, R - popc64(cur_group)) : R;
+            while (!rest.empty()) {
+                if (room == 0) {
+                    grp = 0;
+                    room = R;
+                }
+                size_t pick = 0;
+                for (size_t k = 0; k < rest.size(); ++k) {
+                    const int tb = tile_local(tp, ops[rest[k]].t0);
+                    const int partner = swizzle_partner(tb);
+                    if (partner < 0 || !((grp >> partner) & 1)) {
+                        pick = k;
+                        break;
+                    }
+                }
+                grp |= 1ull << tile_local(tp, ops[rest[pick]].t0);
+                --room;
+                order.push_back(rest[pick]);
+                rest.erase(rest.begin() + (long)pick);
+            }
+            rest.swap(order);
+        }
+        for (size_t i : rest) add_now(ops[i], nullptr);
+    }
+    // the tile bit whose 128-byte-swizzle contribution shares a bank bit with tb
+    static int swizzle_partner(int tb) {
+        if (tb >= 1 && tb <= 3) return tb + 3;
+        if (tb >= 4 && tb <= 6) return tb - 3;
+        return -1;
     }
     void add_now(const FOp &f, const DiagPlan *dp) {
         switch (f.kind) {
