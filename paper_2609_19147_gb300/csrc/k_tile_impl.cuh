@@ -261,16 +261,21 @@ __device__ __forceinline__ void op_h(float2 (&a)[1 << R]) {
 }
 
 // QFT stage: butterfly on bit M, then the ladder phase on the bit-M = 1 half:
-// item twiddle w times the group-bit twiddle gtab[k]
+// item twiddle w times the group-bit twiddle gtab[k].  The group-bit twiddle
+// sees only the group bits below M, so the 2^(R-1) products take 2^M distinct
+// values, formed once per item.
 template <int R, int M>
 __device__ __forceinline__ void op_qft(float2 (&a)[1 << R], const float2 *gtab, float2 w) {
+    float2 wk[1 << M];
+#pragma unroll
+    for (int q = 0; q < (1 << M); ++q) wk[q] = cmul(w, gtab[q | (1 << M)]);
 #pragma unroll
     for (int j = 0; j < (1 << R); ++j) {
         if ((j >> M) & 1) continue;
         const int k = j | (1 << M);
         const float2 a0 = a[j], a1 = a[k];
         a[j] = __fadd2_rn(a0, a1);
-        a[k] = cmul(__ffma2_rn(a1, make_float2(-1.f, -1.f), a0), cmul(w, gtab[k]));
+        a[k] = cmul(__ffma2_rn(a1, make_float2(-1.f, -1.f), a0), wk[j & ((1 << M) - 1)]);
     }
 }
 
