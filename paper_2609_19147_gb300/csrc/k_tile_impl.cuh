@@ -582,6 +582,27 @@ __device__ __forceinline__ void store_at(const SweepCtx &c, bool vec, const int 
     }
 }
 
+// 16-byte pairs written as two 8-byte stores (explicit, so that they are not
+// merged back): the results of the packed FMAs sit in register pairs, and one
+// 16-byte store would first need each two pairs moved into an aligned quad
+__device__ __forceinline__ void st_shared_f2(float2 *p, float2 v) {
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(smem_u32(p)), "f"(v.x), "f"(v.y) : "memory");
+}
+template <int R>
+__device__ __forceinline__ void store_at_pairs(const SweepCtx &c, bool vec, const int (&o)[1 << R],
+                                               const float2 (&a)[1 << R]) {
+    if (vec) {
+#pragma unroll
+        for (int j = 0; j < (1 << R); j += 2)
+            if (QS_DCHECK(c, o[j] >= 0 && o[j] + 1 < c.tile_elems && !(o[j] & 1), 1003)) {
+                st_shared_f2(c.buf + o[j], a[j]);
+                st_shared_f2(c.buf + o[j] + 1, a[j + 1]);
+            }
+    } else {
+        store_at<R>(c, false, o, a);
+    }
+}
+
 // MK_DIAG on a register group: the static factor (slices / LUT groups that do
 // not see the group bits) once per item, the rest per amplitude
 template <int R>
@@ -775,11 +796,13 @@ __device__ __forceinline__ int rot_program(const SweepCtx &c, int op_begin, int 
 // (held in registers it would crowd out the amplitudes)
 template <int R>
 struct DiagcRegs {
-    const float2 *lut;
+    const char *lut;   // the count table, addressed in bytes
     const uint64_t *dat;
-    uint64_t q_lo, q_hi;
     int n_cls, stride;
     bool cz;
+    int s8;                       // 8 x the weight of a neighbour count (+1 both-set, -2 mismatch)
+    int base8[R];                 // 8 x each group bit's increment without its neighbour term
+    uint32_t q8[(1 << R) / 4];    // 8 x the intra-group entry of element j, one byte per element
 #ifdef QS_DEVICE_CHECKS
     const SweepCtx *ctx;
 #endif
@@ -788,43 +811,56 @@ struct DiagcRegs {
         ctx = &c;
         QS_DCHECK(c, op.cst >= 0 && op.lo >= 0 && op.lo + R + 3 + 2 * op.a <= c.n_const, 1005);
 #endif
-        lut = c.cs + op.cst;
+        lut = reinterpret_cast<const char *>(c.cs + op.cst);
         dat = reinterpret_cast<const uint64_t *>(c.cs + op.lo);
         n_cls = op.a;
         stride = op.p;
         cz = op.b != 0;
-        q_lo = op.cmask;
-        q_hi = op.cval;
+        s8 = cz ? 8 : -16;
+        const uint64_t degs = dat[R], zinc = dat[R + 2];
+#pragma unroll
+        for (int m = 0; m < R; ++m)
+            base8[m] = 8 * ((cz ? 0 : (int)((degs >> (6 * m)) & 63)) + (int)((zinc >> (12 * m)) & 4095));
+#pragma unroll
+        for (int w = 0; w < (1 << R) / 4; ++w) {
+            uint32_t v = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int j = 4 * w + b;
+                const uint32_t q = (uint32_t)(((j < 16 ? op.cmask : op.cval) >> (4 * (j & 15))) & 15);
+                v |= (8u * q) << (8 * b);
+            }
+            q8[w] = v;
+        }
     }
     __device__ __forceinline__ void apply(uint64_t x0, float2 (&a)[1 << R]) const {
-        const uint64_t degs = dat[R], mz = dat[R + 1], zinc = dat[R + 2];
+        const uint64_t mz = dat[R + 1];
         const uint64_t *cls = dat + R + 3;
         int c0 = stride * __popcll(x0 & mz);
         for (int k = 0; k < n_cls; ++k) {
             const uint64_t f = cz ? (x0 & (x0 >> (int)cls[2 * k + 1])) : (x0 ^ (x0 >> (int)cls[2 * k + 1]));
             c0 += __popcll(f & cls[2 * k]);
         }
-        int dm[R];
+        int dm8[R];
 #pragma unroll
-        for (int m = 0; m < R; ++m) {
-            const int s = __popcll(x0 & dat[m]);
-            dm[m] = (cz ? s : (int)((degs >> (6 * m)) & 63) - 2 * s) + (int)((zinc >> (12 * m)) & 4095);
-        }
-        // the group elements in Gray-code order: one running count, one add
-        // or subtract per element (no table of 2^R counts held in registers)
-        int cnt = c0;
+        for (int m = 0; m < R; ++m) dm8[m] = base8[m] + s8 * __popcll(x0 & dat[m]);
+        // the group elements in Gray-code order: one running byte offset, one
+        // add or subtract per element, plus the element's intra-group entry
+        int off = 8 * c0;
 #pragma unroll
         for (int i = 0; i < (1 << R); ++i) {
             const int j = i ^ (i >> 1);
             if (i > 0) {
                 const int m = __ffs(i) - 1;
-                cnt += ((j >> m) & 1) ? dm[m] : -dm[m];
+                off += ((j >> m) & 1) ? dm8[m] : -dm8[m];
             }
-            const int q = (int)(((j < 16 ? q_lo : q_hi) >> (4 * (j & 15))) & 15);
+            const int o = off + (int)__byte_perm(q8[j >> 2], 0u, 0x4440u | (uint32_t)(j & 3));
 #ifdef QS_DEVICE_CHECKS
-            if (!QS_DCHECK(*ctx, cnt + q >= 0 && (lut - ctx->cs) + cnt + q < ctx->n_const, 1006)) continue;
+            if (!QS_DCHECK(*ctx, o >= 0 && (lut - reinterpret_cast<const char *>(ctx->cs)) + o + 8 <=
+                                               8LL * ctx->n_const, 1006))
+                continue;
 #endif
-            a[j] = cmul(a[j], lut[cnt + q]);
+            a[j] = cmul(a[j], *reinterpret_cast<const float2 *>(lut + o));
         }
     }
 };
@@ -888,7 +924,7 @@ __device__ __forceinline__ void rot_sweep(const SweepCtx &c, const Sweep &S, int
         // with 4-bit groups (112 registers) the offsets are formed again
         // rather than held through the ops
         if constexpr (R == 4) group_offsets<R>(saddr, gs, o);
-        store_at<R>(c, VEC, o, a);
+        store_at_pairs<R>(c, VEC, o, a);
     }
 }
 
