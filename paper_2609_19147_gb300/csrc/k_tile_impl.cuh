@@ -865,10 +865,13 @@ struct DiagcRegs {
     }
 };
 
-// a ROT layer on all R group bits with the tangents in registers
-template <int R, int M = 0>
+// a ROT layer on the group bits in MASK with the tangents in registers (the
+// other group bits carry t = 0: identities, skipped)
+template <int R, uint32_t MASK = (1u << R) - 1, int M = 0>
 __device__ __forceinline__ void rot_layer_regs(float2 (&a)[1 << R], const float2 (&t)[R]) {
-    if constexpr (M < R) {
+    if constexpr (M < R && !((MASK >> M) & 1)) {
+        rot_layer_regs<R, MASK, M + 1>(a, t);
+    } else if constexpr (M < R) {
         const float2 tp = t[M], tn = make_float2(-t[M].x, -t[M].y);
 #pragma unroll
         for (int j = 0; j < (1 << R); ++j) {
@@ -878,11 +881,11 @@ __device__ __forceinline__ void rot_layer_regs(float2 (&a)[1 << R], const float2
             a[j] = __ffma2_rn(tp, a1, a0);
             a[k] = __ffma2_rn(tn, a0, a1);
         }
-        rot_layer_regs<R, M + 1>(a, t);
+        rot_layer_regs<R, MASK, M + 1>(a, t);
     }
 }
 
-template <int R, int NT, int PROG, bool VEC, bool SCALED>
+template <int R, int NT, int PROG, bool VEC, bool SCALED, uint32_t MASK1 = (1u << R) - 1>
 __device__ __forceinline__ void rot_sweep(const SweepCtx &c, const Sweep &S, int sidx) {
     const int *ts = c.tab_s + sidx * kItemTab;
     const uint64_t *tg = c.tab_g + sidx * kItemTab;
@@ -914,7 +917,7 @@ __device__ __forceinline__ void rot_sweep(const SweepCtx &c, const Sweep &S, int
         uint64_t x0 = 0;
         if constexpr (PROG >= 2) x0 = c.tile_gbase | tg[i0] | tg[i1] | tg[i2];
         if constexpr (PROG == 2) dg.apply(x0, a);
-        rot_layer_regs<R>(a, t1);
+        rot_layer_regs<R, MASK1>(a, t1);
         if constexpr (PROG == 3 || PROG == 4) dg.apply(x0, a);
         if constexpr (PROG == 4) rot_layer_regs<R>(a, t2);
         if constexpr (SCALED) {
@@ -928,16 +931,29 @@ __device__ __forceinline__ void rot_sweep(const SweepCtx &c, const Sweep &S, int
     }
 }
 
+template <int R, int NT, int PROG, bool VEC, bool SCALED>
+__device__ __forceinline__ void rot_sweep_masked(const SweepCtx &c, const Sweep &S, int sidx, int mc) {
+    constexpr uint32_t F = (1u << R) - 1;
+    if (mc == 1) rot_sweep<R, NT, PROG, VEC, SCALED, 7u>(c, S, sidx);
+    else if (mc == 2) rot_sweep<R, NT, PROG, VEC, SCALED, F & ~1u>(c, S, sidx);
+    else rot_sweep<R, NT, PROG, VEC, SCALED, F>(c, S, sidx);
+}
+
 template <int R, int NT>
 __device__ __forceinline__ bool run_rot_program(const SweepCtx &c, const Sweep &S, int sidx) {
     const int prog = rot_program<R>(c, S.op_begin, S.op_end);
     if (!prog) return false;
+    // the first layer's own bits: the lowest three, or all but bit 0, run
+    // without the padded identities (programs 1 and 4)
+    constexpr uint32_t F = (1u << R) - 1;
+    const uint32_t own = (uint32_t)c.micro[prog == 2 ? S.op_begin + 1 : S.op_begin].lo & F;
+    const int mc = (prog == 1 || prog == 4) ? (own == 7u ? 1 : own == (F & ~1u) ? 2 : 0) : 0;
     const int k = 4 * (prog - 1) + (S.vec ? 2 : 0) + (S.scale != 1.f ? 1 : 0);
     switch (k) {
-        case 0: rot_sweep<R, NT, 1, false, false>(c, S, sidx); break;
-        case 1: rot_sweep<R, NT, 1, false, true>(c, S, sidx); break;
-        case 2: rot_sweep<R, NT, 1, true, false>(c, S, sidx); break;
-        case 3: rot_sweep<R, NT, 1, true, true>(c, S, sidx); break;
+        case 0: rot_sweep_masked<R, NT, 1, false, false>(c, S, sidx, mc); break;
+        case 1: rot_sweep_masked<R, NT, 1, false, true>(c, S, sidx, mc); break;
+        case 2: rot_sweep_masked<R, NT, 1, true, false>(c, S, sidx, mc); break;
+        case 3: rot_sweep_masked<R, NT, 1, true, true>(c, S, sidx, mc); break;
         case 4: rot_sweep<R, NT, 2, false, false>(c, S, sidx); break;
         case 5: rot_sweep<R, NT, 2, false, true>(c, S, sidx); break;
         case 6: rot_sweep<R, NT, 2, true, false>(c, S, sidx); break;
@@ -946,10 +962,10 @@ __device__ __forceinline__ bool run_rot_program(const SweepCtx &c, const Sweep &
         case 9: rot_sweep<R, NT, 3, false, true>(c, S, sidx); break;
         case 10: rot_sweep<R, NT, 3, true, false>(c, S, sidx); break;
         case 11: rot_sweep<R, NT, 3, true, true>(c, S, sidx); break;
-        case 12: rot_sweep<R, NT, 4, false, false>(c, S, sidx); break;
-        case 13: rot_sweep<R, NT, 4, false, true>(c, S, sidx); break;
-        case 14: rot_sweep<R, NT, 4, true, false>(c, S, sidx); break;
-        default: rot_sweep<R, NT, 4, true, true>(c, S, sidx); break;
+        case 12: rot_sweep_masked<R, NT, 4, false, false>(c, S, sidx, mc); break;
+        case 13: rot_sweep_masked<R, NT, 4, false, true>(c, S, sidx, mc); break;
+        case 14: rot_sweep_masked<R, NT, 4, true, false>(c, S, sidx, mc); break;
+        default: rot_sweep_masked<R, NT, 4, true, true>(c, S, sidx, mc); break;
     }
     return true;
 }

@@ -77,8 +77,10 @@ enum MicroKind : int32_t {
     MK_U1R = 6,   // real 2x2 on group bit a (RY family): consts (m00, m00), (m01, m01),
                   // (m10, m10), (m11, m11) at an even offset (two 16-byte loads, each
                   // entry already the packed FP32x2 operand)
-    MK_LAYER = 7, // commuting 2x2 ops of one kind (a = MK_RXC / MK_U1R / MK_U1 / MK_H)
-                  // on the group bits in mask b; constants per bit m at cst + m * stride
+    MK_LAYER = 7, // commuting 2x2 ops of one kind (a = MK_RXC / MK_U1R / MK_U1 / MK_H / MK_ROT)
+                  // on the group bits in mask b; constants per bit m at cst + m * stride.
+                  // A ROT layer of a rotation program has b = all group bits (the others
+                  // identities, t = 0) and its own bits in lo
     MK_QFTL = 8,  // QFT stages (ladders down to bit 0) on the group bits in mask b,
                   // applied from the highest group bit down; p of bit m = (p >> 6m) & 63
                   // (p is a packed 64-bit field: use cmask); group table of bit m at cst + m * 2^R

@@ -2345,9 +2345,14 @@ struct PassBuilder {
                                                (n_ops == 2 && diagc(o[0]) && rot_layer(o[1])) ||
                                                (n_ops == 2 && rot_layer(o[0]) && diagc(o[1])) ||
                                                (n_ops == 3 && rot_layer(o[0]) && diagc(o[1]) && rot_layer(o[2])));
+            // (the layer's own bits stay in `lo`: the kernel skips the padded ones
+            // when they are all group bits but the lowest three, or bit 0 alone)
             if (program)
                 for (int k = begin; k < sw.op_end; ++k)
-                    if (rot_layer(out[k])) out[k].b = (1 << R) - 1;
+                    if (rot_layer(out[k])) {
+                        out[k].lo = out[k].b;
+                        out[k].b = (1 << R) - 1;
+                    }
         }
         tp.n_micro = (int)out.size();
         for (int k = 0; k < tp.n_micro; ++k) tp.micro[k] = out[k];

@@ -436,6 +436,15 @@ class TileRun {
             }
             case MK_LAYER: {
                 need(o.b > 0 && o.b < (1 << r), "layer mask");
+                // a rotation program's layer: the bits outside its own (lo) are
+                // identities, which the kernel may skip
+                if (o.a == MK_ROT && o.lo) {
+                    need((o.lo & ~o.b) == 0, "rotation layer's own bits outside its mask");
+                    for (int m = 0; m < r; ++m)
+                        if (((o.b >> m) & 1) && !((o.lo >> m) & 1))
+                            need(Kraw(o.cst + 2 * m).x == 0.f && Kraw(o.cst + 2 * m + 1).x == 0.f,
+                                 "padded rotation bit is not the identity");
+                }
                 if (o.a == MK_U1R) need(o.cst % 2 == 0, "packed real 2x2 layer at an odd offset");
                 for (int m = 0; m < r; ++m)
                     if ((o.b >> m) & 1) layer_bit(o.a, m, r, a, o.cst);
