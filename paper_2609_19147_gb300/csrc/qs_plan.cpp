@@ -2499,6 +2499,49 @@ qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, co
     return QS_OK;
 }
 
+// Runs of uncontrolled one-qubit ops on distinct bits commute; the scheduler
+// takes ops into a pass in stream order, so a run's order decides which bits
+// share a tile.  Each run is ordered: the L tile-resident low bits, then the
+// a = (T - L) - b bits right above them, then the top b = (T - L) / 3 bits,
+// then the rest ascending.  The first pass of a layer then holds one long
+// contiguous block (rows of 2^(L+a) amplitudes) and a few top bits, and the
+// others contiguous middle blocks; a tile of top bits only (rows of 2^L
+// amplitudes, each in another far-apart page) streams ~15% slower through the
+// TMA.  (30q Trotter steps: 7.71 -> 7.30 ms with the same 201 passes.)
+// Only runs of real 2x2 ops (rotations, Hadamards) are reordered: with complex
+// layers the first pass of each layer also holds the random-angle diagonal
+// that precedes it, and with the low bits in that sweep's group its slice-table
+// lookups vary across a warp's lanes (28q layered suite: 79 -> 88 ms).
+static void order_layer_runs(int n, int T, int L, std::vector<FOp> &ops) {
+    const int b = std::max(0, (T - L) / 3), a = std::max(0, (T - L) - b);
+    std::vector<int> rank(n, 0);
+    int r = 0;
+    for (int q = 0; q < L && q < n; ++q) rank[q] = r++;
+    for (int q = L; q < L + a && q < n; ++q) rank[q] = r++;
+    for (int q = n - 1; q >= n - b && q >= L + a; --q) rank[q] = r++;
+    for (int q = L + a; q < n - b; ++q) rank[q] = r++;
+    auto one_q = [&](const FOp &f) {
+        return f.kind == F_U1 && f.cmask == 0 && f.t0 >= 0 && f.t0 < n && f.m[0].imag() == 0.0 &&
+               f.m[1].imag() == 0.0 && f.m[2].imag() == 0.0 && f.m[3].imag() == 0.0;
+    };
+    size_t i = 0;
+    while (i < ops.size()) {
+        if (!one_q(ops[i])) {
+            ++i;
+            continue;
+        }
+        size_t j = i;
+        uint64_t seen = 0;
+        while (j < ops.size() && one_q(ops[j]) && !((seen >> ops[j].t0) & 1)) {
+            seen |= 1ull << ops[j].t0;
+            ++j;
+        }
+        std::stable_sort(ops.begin() + (long)i, ops.begin() + (long)j,
+                         [&](const FOp &x, const FOp &y) { return rank[x.t0] < rank[y.t0]; });
+        i = j;
+    }
+}
+
 static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &detected, int n_gates,
                                       const qs_opts &o, Plan &plan, std::string &err) {
     plan = Plan();
@@ -2548,6 +2591,7 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
         }
     }
     ops.swap(ops2);
+    order_layer_runs(n, T, L, ops);
     for (FOp &f : ops) f.cache_masks();
     std::vector<DiagPlan> dplans(ops.size());
     for (size_t i = 0; i < ops.size(); ++i) {
