@@ -19,8 +19,9 @@ LIB = os.path.join(OUT_DIR, "libqs.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 # the tile-pass kernel instantiations are split over several units (compiled
-# in parallel): k_tile_r5.cu and k_tile_dense.cu take the longest
-SOURCES = ["k_tile_dense.cu", "k_tile_r5.cu", "k_tile_ws.cu", "k_tile_r4.cu", "k_tile_layer4.cu", "k_tile_layer5.cu", "k_tile_r123.cu",
+# in parallel): k_tile_ws5l.cu, k_tile_r5.cu and k_tile_dense.cu take the longest
+SOURCES = ["k_tile_ws5l.cu", "k_tile_dense.cu", "k_tile_r5.cu", "k_tile_ws5a.cu", "k_tile_ws4l.cu", "k_tile_ws4a.cu",
+           "k_tile_ws.cu", "k_tile_r4.cu", "k_tile_layer4.cu", "k_tile_layer5.cu", "k_tile_r123.cu",
            "qs_api.cu", "qs_plan.cpp", "qs_qasm.cpp",
            "k_tile.cu", "k_pergate.cu", "k_permgather.cu", "k_reduce.cu", "k_noalloc.cu", "k_qaoa.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

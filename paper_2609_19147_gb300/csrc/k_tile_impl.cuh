@@ -895,8 +895,9 @@ __device__ __forceinline__ void rot_sweep(const SweepCtx &c, const Sweep &S, int
     const int b = S.op_begin;
     const int i_l1 = PROG == 2 ? b + 1 : b;
     float2 t1[R], t2[R];
-    QS_DCHECK(c, c.micro[i_l1].cst >= 0 && c.micro[i_l1].cst + 2 * R <= c.n_const, 1007);
-    if constexpr (PROG == 4) QS_DCHECK(c, c.micro[b + 2].cst >= 0 && c.micro[b + 2].cst + 2 * R <= c.n_const, 1008);
+    (void)QS_DCHECK(c, c.micro[i_l1].cst >= 0 && c.micro[i_l1].cst + 2 * R <= c.n_const, 1007);
+    if constexpr (PROG == 4)
+        (void)QS_DCHECK(c, c.micro[b + 2].cst >= 0 && c.micro[b + 2].cst + 2 * R <= c.n_const, 1008);
 #pragma unroll
     for (int m = 0; m < R; ++m) t1[m] = c.cs[c.micro[i_l1].cst + 2 * m];
     if constexpr (PROG == 4) {
@@ -931,29 +932,43 @@ __device__ __forceinline__ void rot_sweep(const SweepCtx &c, const Sweep &S, int
     }
 }
 
-template <int R, int NT, int PROG, bool VEC, bool SCALED>
+template <int R, int NT, int PROG, bool VEC, bool SCALED, bool MASKED>
 __device__ __forceinline__ void rot_sweep_masked(const SweepCtx &c, const Sweep &S, int sidx, int mc) {
     constexpr uint32_t F = (1u << R) - 1;
+    if constexpr (!MASKED) {
+        rot_sweep<R, NT, PROG, VEC, SCALED, F>(c, S, sidx);
+        return;
+    }
     if (mc == 1) rot_sweep<R, NT, PROG, VEC, SCALED, 7u>(c, S, sidx);
     else if (mc == 2) rot_sweep<R, NT, PROG, VEC, SCALED, F & ~1u>(c, S, sidx);
+    else if (R == 5 && mc == 3) rot_sweep<R, NT, PROG, VEC, SCALED, 0xfu & F>(c, S, sidx);
+    else if (R == 5 && mc == 4) rot_sweep<R, NT, PROG, VEC, SCALED, 0xeu & F>(c, S, sidx);
     else rot_sweep<R, NT, PROG, VEC, SCALED, F>(c, S, sidx);
 }
 
-template <int R, int NT>
+// MASKED: instantiate the programs whose first layer skips padded identities
+// (the warp-specialised kernel; the others keep one form per program)
+template <int R, int NT, bool MASKED>
 __device__ __forceinline__ bool run_rot_program(const SweepCtx &c, const Sweep &S, int sidx) {
     const int prog = rot_program<R>(c, S.op_begin, S.op_end);
     if (!prog) return false;
-    // the first layer's own bits: the lowest three, or all but bit 0, run
-    // without the padded identities (programs 1 and 4)
+    // the first layer's own bits: the lowest three or four group positions,
+    // or those above position 0, run without the padded identities
+    // (programs 1 and 4)
     constexpr uint32_t F = (1u << R) - 1;
     const uint32_t own = (uint32_t)c.micro[prog == 2 ? S.op_begin + 1 : S.op_begin].lo & F;
-    const int mc = (prog == 1 || prog == 4) ? (own == 7u ? 1 : own == (F & ~1u) ? 2 : 0) : 0;
+    const int mc = (!MASKED || (prog != 1 && prog != 4)) ? 0
+                   : own == 7u            ? 1
+                   : own == (F & ~1u)     ? 2
+                   : (R == 5 && own == 0xfu) ? 3
+                   : (R == 5 && own == 0xeu) ? 4
+                                             : 0;
     const int k = 4 * (prog - 1) + (S.vec ? 2 : 0) + (S.scale != 1.f ? 1 : 0);
     switch (k) {
-        case 0: rot_sweep_masked<R, NT, 1, false, false>(c, S, sidx, mc); break;
-        case 1: rot_sweep_masked<R, NT, 1, false, true>(c, S, sidx, mc); break;
-        case 2: rot_sweep_masked<R, NT, 1, true, false>(c, S, sidx, mc); break;
-        case 3: rot_sweep_masked<R, NT, 1, true, true>(c, S, sidx, mc); break;
+        case 0: rot_sweep_masked<R, NT, 1, false, false, MASKED>(c, S, sidx, mc); break;
+        case 1: rot_sweep_masked<R, NT, 1, false, true, MASKED>(c, S, sidx, mc); break;
+        case 2: rot_sweep_masked<R, NT, 1, true, false, MASKED>(c, S, sidx, mc); break;
+        case 3: rot_sweep_masked<R, NT, 1, true, true, MASKED>(c, S, sidx, mc); break;
         case 4: rot_sweep<R, NT, 2, false, false>(c, S, sidx); break;
         case 5: rot_sweep<R, NT, 2, false, true>(c, S, sidx); break;
         case 6: rot_sweep<R, NT, 2, true, false>(c, S, sidx); break;
@@ -962,10 +977,10 @@ __device__ __forceinline__ bool run_rot_program(const SweepCtx &c, const Sweep &
         case 9: rot_sweep<R, NT, 3, false, true>(c, S, sidx); break;
         case 10: rot_sweep<R, NT, 3, true, false>(c, S, sidx); break;
         case 11: rot_sweep<R, NT, 3, true, true>(c, S, sidx); break;
-        case 12: rot_sweep_masked<R, NT, 4, false, false>(c, S, sidx, mc); break;
-        case 13: rot_sweep_masked<R, NT, 4, false, true>(c, S, sidx, mc); break;
-        case 14: rot_sweep_masked<R, NT, 4, true, false>(c, S, sidx, mc); break;
-        default: rot_sweep_masked<R, NT, 4, true, true>(c, S, sidx, mc); break;
+        case 12: rot_sweep_masked<R, NT, 4, false, false, MASKED>(c, S, sidx, mc); break;
+        case 13: rot_sweep_masked<R, NT, 4, false, true, MASKED>(c, S, sidx, mc); break;
+        case 14: rot_sweep_masked<R, NT, 4, true, false, MASKED>(c, S, sidx, mc); break;
+        default: rot_sweep_masked<R, NT, 4, true, true, MASKED>(c, S, sidx, mc); break;
     }
     return true;
 }
@@ -1243,10 +1258,10 @@ __device__ __forceinline__ void run_sweep_general(const SweepCtx &c, const Sweep
     }
 }
 
-template <int R, int NT, int KS = KS_ALL>
+template <int R, int NT, int KS = KS_ALL, bool WS = false>
 __device__ __forceinline__ void run_sweep(const SweepCtx &c, const Sweep &S, int sidx) {
     if constexpr ((R == 4 || R == 5) && KS == KS_LAYER) {
-        if (run_rot_program<R, NT>(c, S, sidx)) return;
+        if (run_rot_program<R, NT, WS>(c, S, sidx)) return;
         if (run_zyz_program<R, NT>(c, S, sidx)) return;
     }
     run_sweep_general<R, NT, KS>(c, S, sidx);
@@ -2085,7 +2100,7 @@ __global__ void __launch_bounds__(2 * NTG + 128, 1)
         c.tile_gbase = A.needs_gidx ? tile_base(A, ti) : 0;
         for (int s = 0; s < n_sweeps; ++s) {
             if (DENSE && S.s_sweeps[s].dense) run_dense<NTG>(c, S.s_sweeps[s], s);
-            else run_sweep<R, NTG, KS>(c, S.s_sweeps[s], s);
+            else run_sweep<R, NTG, KS, true>(c, S.s_sweeps[s], s);
             if (s + 1 < n_sweeps) named_sync(bar_id, NTG);
         }
         fence_proxy_async();   // generic-proxy writes before the async-proxy store

@@ -1574,6 +1574,34 @@ struct PassBuilder {
                 cur_group |= 1ull << tb;
             }
         std::sort(sw.gbit, sw.gbit + sw.r);
+        // A sweep of rotations and diagonals: the bits of its first rotation run
+        // come right after tile bit 0 (which stays first: 16-byte pair
+        // accesses), so that a rotation program's first layer owns a contiguous
+        // run of low group positions and runs without its padded identities.
+        {
+            uint64_t first = 0;
+            bool ok = true, in_first = true;
+            for (int k = sw.op_begin; k < tp.n_micro; ++k) {
+                const int kd = tp.micro[k].kind;
+                if (kd == MK_ROT) {
+                    if (in_first) first |= 1ull << tp.micro[k].a;
+                } else if (kd == MK_DIAGC || kd == MK_DIAG || kd == MK_DIAGQ) {
+                    in_first = false;
+                } else {
+                    ok = false;
+                }
+            }
+            if (ok && first) {
+                int g[kMaxGroup], m = 0;
+                const bool b0 = sw.gbit[0] == 0;
+                if (b0) g[m++] = 0;
+                for (int j = b0 ? 1 : 0; j < sw.r; ++j)
+                    if ((first >> sw.gbit[j]) & 1) g[m++] = sw.gbit[j];
+                for (int j = b0 ? 1 : 0; j < sw.r; ++j)
+                    if (!((first >> sw.gbit[j]) & 1)) g[m++] = sw.gbit[j];
+                for (int j = 0; j < sw.r; ++j) sw.gbit[j] = g[j];
+            }
+        }
         sw.vec = (sw.r >= 2 && sw.gbit[0] == 0) ? 1 : 0;
         sw.op_end = tp.n_micro;
         choose_item_bits(tp, sw);
@@ -2346,7 +2374,8 @@ struct PassBuilder {
                                                (n_ops == 2 && rot_layer(o[0]) && diagc(o[1])) ||
                                                (n_ops == 3 && rot_layer(o[0]) && diagc(o[1]) && rot_layer(o[2])));
             // (the layer's own bits stay in `lo`: the kernel skips the padded ones
-            // when they are all group bits but the lowest three, or bit 0 alone)
+            // when they are the lowest three or four group positions, or those
+            // above position 0)
             if (program)
                 for (int k = begin; k < sw.op_end; ++k)
                     if (rot_layer(out[k])) {
