@@ -2536,7 +2536,11 @@ qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, co
 // contiguous block (rows of 2^(L+a) amplitudes) and a few top bits, and the
 // others contiguous middle blocks; a tile of top bits only (rows of 2^L
 // amplitudes, each in another far-apart page) streams ~15% slower through the
-// TMA.  (30q Trotter steps: 7.71 -> 7.30 ms with the same 201 passes.)
+// TMA.  (30q Trotter steps: 7.71 -> 7.30 ms with the same 201 passes.)  The
+// order is a second candidate plan (build_fused_plan_cfg keeps the one with
+// the lower locality cost): it can also fragment passes past the 5 tensor
+// dimensions of one copy (Heisenberg chains, where each layer's bits follow
+// the conjugated pair terms).
 // Only runs of real 2x2 ops (rotations, Hadamards) are reordered: with complex
 // layers the first pass of each layer also holds the random-angle diagonal
 // that precedes it, and with the low bits in that sweep's group its slice-table
@@ -2571,8 +2575,51 @@ static void order_layer_runs(int n, int T, int L, std::vector<FOp> &ops) {
     }
 }
 
+static qs_status build_fused_plan_once(int n, int batch, const std::vector<FOp> &detected, int n_gates,
+                                      const qs_opts &o, bool order, Plan &plan, std::string &err);
+
+// Locality cost of a plan's tile passes.  A tile with many bits among the
+// 2 MB-page bits (index bit 18 and up, for 8-byte amplitudes) whose rows also
+// reach the top of a state of 1 GB and more streams slowest through the TMA
+// (30q, one two-sweep pass: tile bits 20-28 3.44 ms, 18-26 3.10 ms, 4-8 with
+// 26-29 2.87 ms): such a pass costs its count of page bits.  A pass copied
+// row by row (more than 5 tensor dimensions) is counted apart.
+static void locality_cost(const Plan &p, int &row_copies, int &spread) {
+    row_copies = 0;
+    spread = 0;
+    for (const HostPass &hp : p.passes) {
+        if (hp.type != HostPass::TILE) continue;
+        if (!hp.tma.ok) ++row_copies;
+        const TilePass &tp = hp.tile;
+        int page_bits = 0, top = -1;
+        for (int k = 0; k < tp.H; ++k) {
+            if (tp.hb[k] >= 18) ++page_bits;
+            top = std::max(top, tp.hb[k]);
+        }
+        if (page_bits >= 6 && top >= 27) spread += page_bits;
+    }
+}
+
+// Plan with the scheduler's stream order and, for states of 2^28 amplitudes
+// and more, with the layer order below as well; the latter is kept when it
+// needs no more HBM passes and no more row-copy passes and has the lower
+// locality cost.
 static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &detected, int n_gates,
                                       const qs_opts &o, Plan &plan, std::string &err) {
+    qs_status s = build_fused_plan_once(n, batch, detected, n_gates, o, false, plan, err);
+    if (s != QS_OK || n < 28) return s;
+    Plan alt;
+    std::string err2;
+    if (build_fused_plan_once(n, batch, detected, n_gates, o, true, alt, err2) != QS_OK) return s;
+    int rc0, sp0, rc1, sp1;
+    locality_cost(plan, rc0, sp0);
+    locality_cost(alt, rc1, sp1);
+    if (alt.passes.size() <= plan.passes.size() && rc1 <= rc0 && sp1 < sp0) plan = std::move(alt);
+    return s;
+}
+
+static qs_status build_fused_plan_once(int n, int batch, const std::vector<FOp> &detected, int n_gates,
+                                      const qs_opts &o, bool order, Plan &plan, std::string &err) {
     plan = Plan();
     plan.n = n;
     plan.mode = QS_MODE_FUSED;
@@ -2620,7 +2667,7 @@ static qs_status build_fused_plan_cfg(int n, int batch, const std::vector<FOp> &
         }
     }
     ops.swap(ops2);
-    order_layer_runs(n, T, L, ops);
+    if (order) order_layer_runs(n, T, L, ops);
     for (FOp &f : ops) f.cache_masks();
     std::vector<DiagPlan> dplans(ops.size());
     for (size_t i = 0; i < ops.size(); ++i) {

@@ -107,6 +107,35 @@ def test_u2_layers_become_phase_rotation_phase_sweeps(qs):
     assert sum(int(x) for x in re.findall(r" U1=(\d+)", text)) == n, text
 
 
+def _tile_bit_sets(text):
+    out = []
+    for m in re.finditer(r"TILE T=\d+ L=\d+ hb=\[([\d,]*)\] tma=(\d)", text):
+        out.append(([int(x) for x in m.group(1).split(",") if x], m.group(2) == "1"))
+    return out
+
+
+def test_layer_order_for_locality_is_chosen_by_cost(qs):
+    # 30q Trotter steps: the real-rotation layers are ordered so that no pass
+    # keeps six or more 2 MB-page bits (index bit 18 and up) reaching bit 27
+    # or above, with the same pass count as the stream order
+    n = 30
+    gl = W.tfim_gates(n, 20, 0.05, 1.0, W.tfim_fields(n, 3), order=2)
+    kw = dict(tile_qubits=13, low_qubits=4, group_qubits=5)
+    text, p = _passes(qs, n, gl, **kw)
+    assert p == 41
+    for hb, tma in _tile_bit_sets(text):
+        assert tma
+        assert not (sum(b >= 18 for b in hb) >= 6 and max(hb) >= 27), hb
+    # Heisenberg chains: the reordered layers would fragment passes past one
+    # tensor copy; the stream order is kept (no row-by-row passes)
+    text, _ = _passes(qs, n, dict(W.sweep_workloads(n))["heisenberg_chain"], **kw)
+    assert all(tma for _, tma in _tile_bit_sets(text))
+    # below 2^28 amplitudes the stream order stands
+    n = 25
+    text25, _ = _passes(qs, n, W.tfim_gates(n, 4, 0.05, 1.0, W.tfim_fields(n, 3), order=2), **kw)
+    assert _tile_bit_sets(text25)[0][0] == list(range(16, 25))
+
+
 def test_h_layer_pass_count_app_a(qs):
     # App. A: radix-4 Walsh takes ceil(25/4) = 7 passes; tiles of 13 qubits take 3
     text, p = _passes(qs, 25, W.wht_gates(25))
