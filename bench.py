@@ -60,6 +60,17 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value over all ranks (a replicated step takes as long as
+    its slowest rank); `x` itself without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -461,10 +472,7 @@ def run_gpu(args):
     st.profile(False)
     qft_ms = float(np.mean([a.elapsed_time(b) for a, b, _ in qe]))
     tfim_ms = float(np.mean([b.elapsed_time(c) for _, b, c in qe]))
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     ms_per_step = ms / args.steps
     value = ms_per_step / 1e3
 
