@@ -99,8 +99,9 @@ def _u2_branch_matrix(kind, rng):
     return _u2_of(np.cos(th), np.sin(th), rng)
 
 
-@pytest.mark.parametrize("tq,lq", [(0, 0), (13, 4), (12, 5), (13, 6), (10, 3)])
-def test_u2_layers_every_factorisation_branch(tq, lq):
+@pytest.mark.parametrize("tq,lq,gq", [(0, 0, 0), (13, 4, 0), (12, 5, 0), (13, 6, 0), (10, 3, 0),
+                                      (13, 4, 4), (12, 4, 4), (13, 5, 4)])
+def test_u2_layers_every_factorisation_branch(tq, lq, gq):
     # U(2) layers (split by CZ ladders so that they do not fuse) whose matrices
     # rotate through the branches, so that every group bit, the 16-byte pair
     # bit included, meets each rotation form
@@ -113,7 +114,18 @@ def test_u2_layers_every_factorisation_branch(tq, lq):
     # a scaled (non-unitary) layer keeps the general 2x2 path
     gl += [W.Gate("U", (q,), (), 0.97 * W.haar_u2(rng)) for q in range(n)]
     psi0 = W.random_state(n, 12)
-    _assert_close(_run(n, gl, psi0, tile_qubits=tq, low_qubits=lq), _ref(n, gl, psi0))
+    _assert_close(_run(n, gl, psi0, tile_qubits=tq, low_qubits=lq, group_qubits=gq), _ref(n, gl, psi0))
+
+
+@pytest.mark.parametrize("tq,lq,gq", [(13, 4, 5), (13, 4, 4), (12, 4, 4), (12, 5, 5)])
+def test_rotation_programs_every_group_size_against_oracle(tq, lq, gq):
+    # Trotter steps whose rotation layers run as the specialised programs
+    # (padded identities skipped, count-table diagonal between two layers),
+    # at 4- and 5-bit register groups, against the oracle
+    n = 20
+    gl = W.tfim_gates(n, 6, 0.07, 1.0, W.tfim_fields(n, 13), order=2)
+    psi0 = W.random_state(n, 14)
+    _assert_close(_run(n, gl, psi0, tile_qubits=tq, low_qubits=lq, group_qubits=gq), _ref(n, gl, psi0))
 
 
 @pytest.mark.parametrize("n", [10, 19, 21])
