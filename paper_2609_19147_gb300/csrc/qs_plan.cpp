@@ -2508,12 +2508,16 @@ qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, co
     bool has_qft = false;
     for (const FOp &f : detected)
         if (f.kind == F_QFT) has_qft = true;
-    // candidates in order of measured per-pass speed for layer-type passes;
-    // QFT-stage passes run fastest with 5-bit groups
+    // candidates in order of measured per-pass speed for general passes (the
+    // first wins a tie in HBM passes); QFT-stage passes run fastest with 5-bit
+    // groups, and so do plans whose sweeps are specialised programs (three
+    // quarters or more: rotation or U(2) layer programs in the warp-specialised
+    // kernel; 25q Trotter, ansatz and QCBM circuits 16-30% faster than with
+    // 12-bit tiles and 4-bit groups).  With general sweeps the 4-bit groups
+    // stay ahead (25q random circuit 11.1 against 18.6 ms).
     const int cfg[3][2] = {{12, 4}, {13, 4}, {13, 5}};
-    const int n_cand = has_qft ? 3 : 2;
     Plan cand[3];
-    for (int i = 0; i < n_cand; ++i) {
+    for (int i = 0; i < 3; ++i) {
         qs_opts c = od;
         c.tile_qubits = cfg[i][0];
         c.group_qubits = cfg[i][1];
@@ -2521,9 +2525,19 @@ qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, co
         if (s != QS_OK) return s;
     }
     int best = 0;
-    for (int i = 1; i < n_cand; ++i)
+    for (int i = 1; i < 2; ++i)
         if (cand[i].passes.size() < cand[best].passes.size()) best = i;
-    if (best != 0 && has_qft && cand[2].passes.size() == cand[best].passes.size()) best = 2;
+    int n_sw = 0, n_prog = 0;
+    for (const HostPass &hp : cand[2].passes)
+        if (hp.type == HostPass::TILE) {
+            n_sw += hp.tile.n_sweeps;
+            n_prog += program_sweeps(hp.tile);
+        }
+    const bool all_programs = n_sw > 0 && 4 * n_prog >= 3 * n_sw;   // three quarters or more
+    if (best != 0 && has_qft && cand[2].passes.size() == cand[best].passes.size())
+        best = 2;
+    else if (all_programs && cand[2].passes.size() <= cand[best].passes.size())
+        best = 2;
     plan = std::move(cand[best]);
     return QS_OK;
 }
@@ -2984,6 +2998,26 @@ int Plan::hbm_passes() const {
     return (int)passes.size();
 }
 
+// sweeps of a tile pass that the kernel runs as a specialised program: a
+// rotation program (rotation layer on all group bits; count-table diagonal
+// and layer in either order; layer, diagonal, layer) or a lone U(2) layer op
+int program_sweeps(const TilePass &tp) {
+    const int F = (1 << tp.R) - 1;
+    int k = 0;
+    for (int s = 0; s < tp.n_sweeps; ++s) {
+        const Sweep &S = tp.sweeps[s];
+        if (S.dense) continue;
+        const MicroOp *o = tp.micro + S.op_begin;
+        const int n = S.op_end - S.op_begin;
+        auto rot = [&](int i) { return o[i].kind == MK_LAYER && o[i].a == MK_ROT && o[i].b == F; };
+        auto dgc = [&](int i) { return o[i].kind == MK_DIAGC; };
+        if ((n == 1 && rot(0)) || (n == 2 && dgc(0) && rot(1)) || (n == 2 && rot(0) && dgc(1)) ||
+            (n == 3 && rot(0) && dgc(1) && rot(2)) || (n == 1 && o[0].kind == MK_ZYZ && S.scale == 1.f))
+            ++k;
+    }
+    return k;
+}
+
 std::string Plan::describe() const {
     std::ostringstream os;
     if (mode == QS_MODE_PERGATE) {
@@ -3005,7 +3039,7 @@ std::string Plan::describe() const {
             }
             os << "TILE T=" << t.T << " L=" << t.L << " hb=[";
             for (int k = 0; k < t.H; ++k) os << (k ? "," : "") << t.hb[k];
-            os << "] tma=" << (hp.tma.ok ? 1 : 0) << " sweeps=" << t.n_sweeps
+            os << "] tma=" << (hp.tma.ok ? 1 : 0) << " sweeps=" << t.n_sweeps << " prog=" << program_sweeps(t)
                << " U1=" << cnt[MK_U1] + cnt[MK_H] + cnt[MK_RXC] + cnt[MK_U1R] + cnt[MK_ROT] << " ZYZ=" << cnt[MK_ZYZ]
                << " U2=" << cnt[MK_U2]
                << " DIAG=" << cnt[MK_DIAG] << " QFT=" << cnt[MK_QFT];

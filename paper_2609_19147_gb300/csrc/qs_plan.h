@@ -99,6 +99,8 @@ struct HostPass {
     std::string note;
 };
 
+int program_sweeps(const TilePass &tp);   // sweeps the kernel runs as a specialised program
+
 struct Plan {
     int n = 0;
     int mode = QS_MODE_FUSED;
