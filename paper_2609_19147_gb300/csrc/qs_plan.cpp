@@ -2509,12 +2509,15 @@ qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, co
     for (const FOp &f : detected)
         if (f.kind == F_QFT) has_qft = true;
     // candidates in order of measured per-pass speed for general passes (the
-    // first wins a tie in HBM passes); QFT-stage passes run fastest with 5-bit
-    // groups, and so do plans whose sweeps are specialised programs (three
-    // quarters or more: rotation or U(2) layer programs in the warp-specialised
-    // kernel; 25q Trotter, ansatz and QCBM circuits 16-30% faster than with
-    // 12-bit tiles and 4-bit groups).  With general sweeps the 4-bit groups
-    // stay ahead (25q random circuit 11.1 against 18.6 ms).
+    // first wins a tie in HBM passes).  13-bit tiles with 5-bit groups win a
+    // tie for QFT stages (25q QFT 0.60 against 0.73 ms) and for layer plans:
+    // every pass a tensor copy of uncontrolled one-qubit layers and diagonals,
+    // none evaluated factor by factor (the warp-specialised kernel's rotation,
+    // U(2) and straight-line layer sweeps; 25q Trotter, Heisenberg, ansatz,
+    // QCBM and QAOA circuits 9-31% faster than with 12-bit tiles and 4-bit
+    // groups).  Otherwise the 4-bit groups stay ahead (25q random circuit 11.1
+    // against 18.6 ms, long-range Ising 7.9 against 14.8 ms, quantum walk 13.4
+    // against 15.5 ms).
     const int cfg[3][2] = {{12, 4}, {13, 4}, {13, 5}};
     Plan cand[3];
     for (int i = 0; i < 3; ++i) {
@@ -2527,17 +2530,14 @@ qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, co
     int best = 0;
     for (int i = 1; i < 2; ++i)
         if (cand[i].passes.size() < cand[best].passes.size()) best = i;
-    int n_sw = 0, n_prog = 0;
+    bool layer_plan = true;
     for (const HostPass &hp : cand[2].passes)
-        if (hp.type == HostPass::TILE) {
-            n_sw += hp.tile.n_sweeps;
-            n_prog += program_sweeps(hp.tile);
-        }
-    const bool all_programs = n_sw > 0 && 4 * n_prog >= 3 * n_sw;   // three quarters or more
-    if (best != 0 && has_qft && cand[2].passes.size() == cand[best].passes.size())
-        best = 2;
-    else if (all_programs && cand[2].passes.size() <= cand[best].passes.size())
-        best = 2;
+        if (hp.type == HostPass::TILE &&
+            (!hp.tma.ok || !layer_only(hp.tile) || general_diags(hp.tile) > 0 ||
+             std::any_of(hp.tile.micro, hp.tile.micro + hp.tile.n_micro,
+                         [](const MicroOp &m) { return m.kind == MK_U1 && m.cmask != 0; })))
+            layer_plan = false;
+    if ((has_qft || layer_plan) && cand[2].passes.size() <= cand[best].passes.size()) best = 2;
     plan = std::move(cand[best]);
     return QS_OK;
 }
@@ -3018,6 +3018,44 @@ int program_sweeps(const TilePass &tp) {
     return k;
 }
 
+// sweeps whose only op is one layer on all group bits (or all but bit 0)
+// that the kernel runs as straight-line code from load to store
+int straight_sweeps(const TilePass &tp) {
+    if (tp.R != 4 && tp.R != 5) return 0;
+    const uint32_t F = (1u << tp.R) - 1;
+    int k = 0;
+    for (int s = 0; s < tp.n_sweeps; ++s) {
+        const Sweep &S = tp.sweeps[s];
+        if (S.dense || S.op_end - S.op_begin != 1) continue;
+        const MicroOp &o = tp.micro[S.op_begin];
+        if (o.kind != MK_LAYER || (o.a != MK_H && o.a != MK_ROT && S.scale != 1.f)) continue;
+        if ((uint32_t)o.b == F || (uint32_t)o.b == (F & ~1u)) ++k;
+    }
+    return k;
+}
+
+// every micro-op of the pass is a one-qubit layer kind or a diagonal (the
+// kernels compiled for that op set, KS_LAYER)
+bool layer_only(const TilePass &tp) {
+    for (int i = 0; i < tp.n_micro; ++i) {
+        const int k = tp.micro[i].kind;
+        if (!(k == MK_LAYER || k == MK_RXC || k == MK_U1R || k == MK_ROT || k == MK_H || k == MK_U1 ||
+              k == MK_ZYZ || k == MK_DIAG || k == MK_DIAGQ || k == MK_DIAGC))
+            return false;
+    }
+    return true;
+}
+
+// diagonal micro-ops that the kernel evaluates factor by factor per amplitude
+// (tables whose indices vary with more than two slices of the group)
+int general_diags(const TilePass &tp) {
+    int k = 0;
+    for (int i = 0; i < tp.n_micro; ++i)
+        if (tp.micro[i].kind == MK_DIAG && (tp.micro[i].b != 0 || __builtin_popcount((unsigned)tp.micro[i].a) > 2))
+            ++k;
+    return k;
+}
+
 std::string Plan::describe() const {
     std::ostringstream os;
     if (mode == QS_MODE_PERGATE) {
@@ -3039,7 +3077,7 @@ std::string Plan::describe() const {
             }
             os << "TILE T=" << t.T << " L=" << t.L << " hb=[";
             for (int k = 0; k < t.H; ++k) os << (k ? "," : "") << t.hb[k];
-            os << "] tma=" << (hp.tma.ok ? 1 : 0) << " sweeps=" << t.n_sweeps << " prog=" << program_sweeps(t)
+            os << "] tma=" << (hp.tma.ok ? 1 : 0) << " sweeps=" << t.n_sweeps << " R=" << t.R << " prog=" << program_sweeps(t) << " straight=" << straight_sweeps(t)
                << " U1=" << cnt[MK_U1] + cnt[MK_H] + cnt[MK_RXC] + cnt[MK_U1R] + cnt[MK_ROT] << " ZYZ=" << cnt[MK_ZYZ]
                << " U2=" << cnt[MK_U2]
                << " DIAG=" << cnt[MK_DIAG] << " QFT=" << cnt[MK_QFT];

@@ -100,6 +100,9 @@ struct HostPass {
 };
 
 int program_sweeps(const TilePass &tp);   // sweeps the kernel runs as a specialised program
+int straight_sweeps(const TilePass &tp);  // sweeps of one layer run as straight-line code
+int general_diags(const TilePass &tp);    // diagonals evaluated factor by factor per amplitude
+bool layer_only(const TilePass &tp);      // only one-qubit layer kinds and diagonals
 
 struct Plan {
     int n = 0;
