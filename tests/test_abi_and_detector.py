@@ -136,6 +136,19 @@ def test_layer_order_for_locality_is_chosen_by_cost(qs):
     assert _tile_bit_sets(text25)[0][0] == list(range(16, 25))
 
 
+def test_default_shape_takes_5_bit_groups_for_layer_plans(qs):
+    # on a tie in passes the planner takes 13-bit tiles with 5-bit groups for
+    # layer plans (uncontrolled one-qubit layers and diagonals) and QFT
+    # stages, and keeps 4-bit groups for circuits with controlled ops
+    fams = dict(W.sweep_workloads(25))
+    for name in ("tfim_2nd_order", "heisenberg_chain", "qaoa_ring", "variational_ansatz", "qft"):
+        text, _ = _passes(qs, 25, fams[name])
+        assert set(re.findall(r" R=(\d)", text)) == {"5"}, (name, text)
+    for name in ("random_circuit", "quantum_walk", "long_range_ising"):
+        text, _ = _passes(qs, 25, fams[name])
+        assert "5" not in set(re.findall(r" R=(\d)", text)), (name, text)
+
+
 def test_h_layer_pass_count_app_a(qs):
     # App. A: radix-4 Walsh takes ceil(25/4) = 7 passes; tiles of 13 qubits take 3
     text, p = _passes(qs, 25, W.wht_gates(25))
