@@ -2519,8 +2519,14 @@ qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, co
     // against 18.6 ms, long-range Ising 7.9 against 14.8 ms, quantum walk 13.4
     // against 15.5 ms).
     const int cfg[3][2] = {{12, 4}, {13, 4}, {13, 5}};
+    // the third candidate can win only for QFT stages or a layer plan: not
+    // built when an op is controlled or acts on two bits non-diagonally
+    bool may_layer = true;
+    for (const FOp &f : detected)
+        if ((f.kind == F_U1 && f.cmask != 0) || f.kind == F_U2 || f.kind == F_DENSE) may_layer = false;
+    const int n_cand = (has_qft || may_layer) ? 3 : 2;
     Plan cand[3];
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < n_cand; ++i) {
         qs_opts c = od;
         c.tile_qubits = cfg[i][0];
         c.group_qubits = cfg[i][1];
@@ -2530,14 +2536,14 @@ qs_status build_fused_plan(int n, int batch, const std::vector<RGate> &gates, co
     int best = 0;
     for (int i = 1; i < 2; ++i)
         if (cand[i].passes.size() < cand[best].passes.size()) best = i;
-    bool layer_plan = true;
+    bool layer_plan = n_cand == 3;
     for (const HostPass &hp : cand[2].passes)
         if (hp.type == HostPass::TILE &&
             (!hp.tma.ok || !layer_only(hp.tile) || general_diags(hp.tile) > 0 ||
              std::any_of(hp.tile.micro, hp.tile.micro + hp.tile.n_micro,
                          [](const MicroOp &m) { return m.kind == MK_U1 && m.cmask != 0; })))
             layer_plan = false;
-    if ((has_qft || layer_plan) && cand[2].passes.size() <= cand[best].passes.size()) best = 2;
+    if (n_cand == 3 && (has_qft || layer_plan) && cand[2].passes.size() <= cand[best].passes.size()) best = 2;
     plan = std::move(cand[best]);
     return QS_OK;
 }
