@@ -68,6 +68,27 @@ def _param_layers(n, layers):
     return g, k
 
 
+def _u2_branch_layers(n, rng, layers=6):
+    """U(2) layers split by CZ ladders whose matrices reach every branch of the
+    phases-rotation-phases factorisation: Haar, diagonal (s = 0), anti-diagonal
+    (c = 0), |c| > |s|, |s| > |c|, |c| = |s|."""
+    gl = []
+    for layer in range(layers):
+        for q in range(n):
+            kind = (q + layer) % 6
+            if kind == 0:
+                m = W.haar_u2(rng)
+            else:
+                th = {1: 0.0, 2: np.pi / 2, 3: 0.3, 4: 1.2, 5: np.pi / 4}[kind]
+                a, b, d = rng.uniform(0.0, 2.0 * np.pi, 3)
+                m = (np.diag(np.exp(1j * np.array([a, b]))) @ np.array([[np.cos(th), -np.sin(th)],
+                                                                         [np.sin(th), np.cos(th)]])
+                     @ np.diag([1.0, np.exp(1j * d)]))
+            gl.append(W.Gate("U", (q,), (), m))
+        gl += [W.Gate("CZ", (q, q + 1)) for q in range(n - 1)]
+    return gl
+
+
 def _cases():
     """(name, n, gates, (T, L, R, dense_prec, block_qubits)[, params (B x P)])"""
     rng = np.random.default_rng(23)
@@ -93,6 +114,8 @@ def _cases():
     out.append(("controlled", 9, W.random_circuit(9, 80, 77, kinds=["CCX", "CSWAP", "CX", "CH", "CRY", "CY", "H"]),
                 (7, 2, 5, 0, 0)))
     out.append(("heisenberg", 12, _heisenberg(12, rng), (10, 4, 5, 0, 0)))
+    out.append(("u2 branches r5", 12, _u2_branch_layers(12, rng), (10, 4, 5, 0, 0)))
+    out.append(("u2 branches r4", 12, _u2_branch_layers(12, rng), (9, 3, 4, 0, 0)))
     out.append(("zz random angles", 12, _zz_random_angles(12, rng), (9, 4, 4, 0, 0)))
     out.append(("zz random angles r5", 12, _zz_random_angles(12, rng), (12, 4, 5, 0, 0)))
     # dense blocks in every precision and block size
