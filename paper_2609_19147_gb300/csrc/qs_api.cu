@@ -1320,11 +1320,12 @@ qs_status qs_grad(qs_state *st, const qs_gate *gates, size_t n_gates, const doub
     qs_status s = convert_terms(st->n, terms, n_terms, t);
     if (s != QS_OK) return s;
     // the forward and un-apply plans: 13-bit tiles with 5-bit register groups
-    // (the warp-specialised kernel) from 13 qubits on (VQE config, n = 24,
-    // batch 32: 94 -> 104 gradient vectors/s against the planner's 12-bit
-    // choice for these per-item layer passes)
+    // (the warp-specialised kernel) from 20 qubits on, where every item has
+    // 128 tiles or more (VQE config, n = 24, batch 32: 94 -> 104 gradient
+    // vectors/s against the planner's 12-bit choice for these per-item layer
+    // passes)
     qs_opts fo = default_opts(nullptr);
-    if (st->n >= 13) {
+    if (st->n >= 20) {
         fo.tile_qubits = 13;
         fo.group_qubits = 5;
     }
